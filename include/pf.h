@@ -1,0 +1,242 @@
+/*
+ * pf.h -- C ABI of the Photon Field Networks hot path on B300 (sm_103a).
+ *
+ * Method: "Photon Field Networks for Dynamic Real-Time Volumetric Global
+ * Illumination" (Bauer, Wu, Ma; arXiv 2304.07338).  The four calls of the hot
+ * path follow the paper's statement of the problem:
+ *   pf_build_photon_cache  -- multi-phase photon tracing (Algorithm 1, Sec. 3.2)
+ *                             binned into per-(light, g) photon caches;
+ *   pf_train_field         -- training samples, radiance estimates and log
+ *                             targets (Sec. 3.3), field MLP (Sec. 3.4) trained
+ *                             with Adam on the relative MSE (Sec. 3.5);
+ *   pf_render_neural       -- volumetric path tracing with the field standing
+ *                             in for indirect light (Algorithm 2, Sec. 3.6);
+ *   pf_render_pathtraced   -- the plain multi-bounce path tracer the paper
+ *                             compares against (Sec. 4.3).
+ *
+ * Conventions
+ *   Memory.  Arguments named *_dev are device pointers on the context's device;
+ *     *_host are host pointers.  Volumes, transfer functions and output
+ *     images belong to the caller.  pf_cache and pf_field objects belong to the
+ *     library and are released with pf_cache_free / pf_field_free.  The
+ *     library allocates its own scratch (grown on demand, kept in the context).
+ *   Streams.  Every call is ordered on the context's stream.  Calls return
+ *     after enqueueing their kernels unless they write host memory (those
+ *     synchronise the stream first).  pf_sync waits for the stream.
+ *   Errors.  Every call returns a pf_status and never aborts.  pf_last_error
+ *     gives a message.  Device loops carry iteration limits; a kernel that
+ *     hits one records it in a device error word, which the next synchronising
+ *     call reports as PF_ERR_TIMEOUT (or PF_ERR_NUMERIC for a non-finite
+ *     value where none is allowed).
+ *   Volumes.  Scalar density on [0,1]^3, x-fastest, voxel (i,j,k) centred at
+ *     ((i+1/2)/nx, (j+1/2)/ny, (k+1/2)/nz); trilinear interpolation with
+ *     clamp-to-edge inside the box and zero outside.  The transfer function
+ *     is a linear RGBA table over density [0,1]: sigma_t = sigma_scale *
+ *     alpha(d), albedo = albedo * rgb(d).
+ *   Random numbers.  Philox4x32-10 (Salmon et al., SC'11), key = seed, counter
+ *     = (item, tag << 24 | sub, block).  Results are reproducible bit for bit
+ *     for a given seed, independent of launch configuration.
+ */
+#ifndef PF_H_
+#define PF_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PF_OK = 0,
+  PF_ERR_INVALID_ARG = 1,
+  PF_ERR_OOM = 2,
+  PF_ERR_CUDA = 3,
+  PF_ERR_TIMEOUT = 4,
+  PF_ERR_UNSUPPORTED = 5,
+  PF_ERR_NUMERIC = 6
+} pf_status;
+
+typedef struct pf_ctx pf_ctx;      /* one device + one stream + scratch */
+typedef struct pf_cache pf_cache;  /* photon records, CSR, caches (device) */
+typedef struct pf_field pf_field;  /* field weights, Adam state (device) */
+
+typedef enum { PF_F32 = 0, PF_F16 = 1, PF_U8 = 2 } pf_dtype;
+typedef enum { PF_PREC_F32 = 0, PF_PREC_BF16 = 1, PF_PREC_F16 = 2, PF_PREC_FP8 = 3 } pf_prec;
+typedef enum { PF_LIGHT_DIRECTIONAL = 0, PF_LIGHT_POINT = 1 } pf_light_kind;
+
+/* Scalar volume + transfer function (Algorithm 1: Volume, TransferFunction). */
+typedef struct {
+  int nx, ny, nz;
+  int dtype;                /* pf_dtype; u8 density = value / 255 */
+  const void* data_dev;     /* nx*ny*nz voxels, x fastest, caller-owned */
+  float sigma_scale;        /* sigma_t = sigma_scale * alpha(d) */
+  float albedo;             /* single-scattering albedo = albedo * rgb(d) */
+  const float* tf_lut_dev;  /* tf_n x 4 RGBA rows over d in [0,1], tf_n >= 2 */
+  int tf_n;
+  float majorant;           /* global max of sigma_t; 0 = let the library compute it */
+} pf_volume;
+
+/* Light source.  Directional: v = unit direction towards the light, rgb =
+ * irradiance.  Point: v = position, rgb = intensity (irradiance at distance r
+ * is rgb / r^2).  Light arrays are host memory, at most PF_MAX_LIGHTS. */
+typedef struct { int kind; float v[3]; float rgb[3]; } pf_light;
+#define PF_MAX_LIGHTS 16
+
+/* Pinhole camera (Algorithm 2 input `camera`); row 0 is the top row. */
+typedef struct { float eye[3], at[3], up[3]; float fovy_deg; int width, height; } pf_camera;
+
+/* Photon field (Sec. 3.4): 6-D query (x, y, z, theta', phi', g) with theta',
+ * phi' the outgoing direction in normalised spherical coordinates, frequency
+ * encoding with in_freqs frequencies per input (12 * in_freqs features),
+ * n_hidden ReLU layers of width `hidden` (64 or 128) without bias, a linear
+ * 3-wide output predicting L' (the log-encoded radiance, Sec. 3.3.2), and
+ * decode L = 10^(-psi L').  prec selects the hidden layers' arithmetic. */
+typedef struct {
+  int in_freqs;
+  int hidden;
+  int n_hidden;
+  int prec;                 /* pf_prec */
+  float psi;
+  uint64_t seed;            /* Kaiming-uniform initialisation */
+} pf_field_desc;
+
+/* Training (Sec. 3.5.1): Adam(beta1, beta2, eps), learning rate lr decayed by
+ * `decay` every `decay_every` steps from step ceil(decay_start_frac*steps). */
+typedef struct {
+  int steps;
+  int batch;
+  float lr, beta1, beta2, eps;
+  float decay, decay_start_frac;
+  int decay_every;
+  uint64_t seed;
+} pf_train_desc;
+
+/* Totals of a photon cache.  tally = emitted, escaped, absorbed, truncated
+ * (bounce cap) and Russian-roulette net power, three channels each (FP64). */
+typedef struct {
+  int64_t n_photons, n_records, n_keys, n_occupied;
+  int res, n_lights, n_g, max_bounces;
+  double tally[15];
+} pf_cache_info_t;
+
+/* ---------------------------------------------------------------- context */
+/* Create a context on `device` using `cuda_stream` (a cudaStream_t; NULL =
+ * legacy default stream). */
+pf_status pf_create(pf_ctx** out, int device, void* cuda_stream);
+pf_status pf_destroy(pf_ctx* ctx);
+pf_status pf_set_stream(pf_ctx* ctx, void* cuda_stream);
+const char* pf_last_error(const pf_ctx* ctx);
+/* Wait for the context's stream; report any device-side error word. */
+pf_status pf_sync(pf_ctx* ctx);
+
+/* Global majorant used by delta and ratio tracking: sigma_scale times the
+ * largest transfer-function alpha over densities [0, max voxel], times
+ * (1 + 2^-10).  Synchronises; writes one float to out_host. */
+pf_status pf_volume_majorant(pf_ctx* ctx, const pf_volume* vol, float* out_host);
+
+/* ---------------------------------------------------------------- photon caches */
+/* Multi-phase photon tracing (Algorithm 1; Sec. 3.2) on the GPU.
+ * photons_per_light_per_g photons are traced for every light and every g in
+ * g_set (host array); photon p belongs to light p / (n_g*N) and phase
+ * (p / N) % n_g.  Directional lights emit from a sqrt(3)-wide square one unit
+ * upstream of the box centre, point lights isotropically.  Delta tracking
+ * against the global majorant; at real interaction j the photon is recorded
+ * if j >= 2 (incoming direction, power before this vertex's albedo, cache
+ * bin floor(cache_res * x)), then scaled by the albedo, stopped at
+ * j == max_bounces, scattered by Henyey-Greenstein, and, for j >= 3 and
+ * use_rr != 0, Russian-rouletted with q = min(1, max_c P_c / max_c P_emit).
+ * Float arithmetic is IEEE single precision without contraction and with
+ * the library's own logarithm and sine/cosine, so bins and counts are
+ * reproducible on any IEEE machine.  cache_res must be a power of two in
+ * [1, 256]; the record count is bounded by n_photons * (max_bounces - 1).
+ * The result is library-owned; free it with pf_cache_free. */
+pf_status pf_build_photon_cache(pf_ctx* ctx, const pf_volume* vol, const pf_light* lights, int n_lights,
+                                const float* g_set, int n_g, uint64_t photons_per_light_per_g,
+                                int max_bounces, int cache_res, uint64_t seed, int use_rr, pf_cache** out);
+/* Synchronises; fills *out. */
+pf_status pf_cache_info(pf_ctx* ctx, const pf_cache* cache, pf_cache_info_t* out);
+/* Copies cache contents to caller buffers (each nullable):
+ *   counts_dev   [n_keys] u32   records per key, key = (l*n_g + gi)*res^3 + bin
+ *   flux_dev     [n_keys*3] f32 per-key power sums (FP64 accumulation)
+ *   rec_key_dev  [n_records] u32, rec_id_dev [n_records] u32 (photon id << 4 | slot,
+ *                slot = interaction index - 2), rec_dir_dev [n_records*3] f32,
+ *                rec_phi_dev [n_records*3] f32 -- the records grouped by key
+ *                (CSR order; order inside a key is unspecified)
+ *   occupied_dev [n_occupied] u32 cells with records and sigma > 0, ascending
+ *   cell_sigma_dev [res^3] f32   mean sigma_t of the voxel centres in each cell */
+pf_status pf_cache_export(pf_ctx* ctx, const pf_cache* cache, uint32_t* counts_dev, float* flux_dev,
+                          uint32_t* rec_key_dev, uint32_t* rec_id_dev, float* rec_dir_dev, float* rec_phi_dev,
+                          uint32_t* occupied_dev, float* cell_sigma_dev);
+pf_status pf_cache_free(pf_cache* cache);
+
+/* ---------------------------------------------------------------- training samples */
+/* Training queries (Sec. 3.3): cell uniform over the occupied cells, position
+ * uniform in the cell, outgoing direction uniform on the sphere, g uniform
+ * over the cache's g set.  q_dev [B*6] f32 = (x, y, z, theta', phi', g). */
+pf_status pf_sample_queries(pf_ctx* ctx, const pf_cache* cache, int64_t B, int step, uint64_t seed, float* q_dev);
+/* Radiance estimate per query (Sec. 3.3.1 estimator with the cache cell as
+ * the gather region): L_s = sum_l sum_{records of (l, g, cell(x))}
+ * p_g(dir . w) Phi / (V_cell * sigma_cell); then L' = -log10(L_s)/psi if
+ * L_s > 10^-psi else 1 (Sec. 3.3.2).  ls_dev, lp_dev [B*3] f32, nullable. */
+pf_status pf_estimate_targets(pf_ctx* ctx, const pf_cache* cache, const float* q_dev, int64_t B, float psi,
+                              float* ls_dev, float* lp_dev);
+
+/* ---------------------------------------------------------------- photon field */
+/* Create a field with seeded Kaiming-uniform weights (layer l, element e:
+ * u from Philox tag 4, item l, block e/4, lane e%4; w = (2u-1) sqrt(6/fan_in)). */
+pf_status pf_field_create(pf_ctx* ctx, const pf_field_desc* desc, pf_field** out);
+pf_status pf_field_free(pf_field* field);
+/* Number of float weights: layers [hidden x 12*in_freqs], (n_hidden-1) x
+ * [hidden x hidden], [3 x hidden], each row-major [out][in], concatenated. */
+int64_t pf_field_num_params(const pf_field* field);
+pf_status pf_field_get_weights(pf_ctx* ctx, const pf_field* field, float* dst_dev);
+pf_status pf_field_set_weights(pf_ctx* ctx, pf_field* field, const float* src_dev);
+/* fp8 fields: per-layer scales s_w = amax|W|/448 and activation scales
+ * s_a = amax(layer input)/448 over B calibration queries (unquantised pass). */
+pf_status pf_field_calibrate_fp8(pf_ctx* ctx, pf_field* field, const float* q_dev, int64_t B);
+/* Field forward pass: out_dev [B*3] = L' predictions for queries q_dev [B*6]. */
+pf_status pf_field_forward(pf_ctx* ctx, const pf_field* field, const float* q_dev, int64_t B, float* out_dev);
+/* Field backward pass: dw_dev [n_params] = sum_b (dL'_b/dW)^T dy_b (f32, bf16
+ * and f16 fields). */
+pf_status pf_field_backward(pf_ctx* ctx, const pf_field* field, const float* q_dev, const float* dy_dev,
+                            int64_t B, float* dw_dev);
+/* One Adam step (Sec. 3.5.1) on the field's master weights with gradient
+ * grad_dev [n_params]; t = the field's step counter + 1. */
+pf_status pf_field_adam(pf_ctx* ctx, pf_field* field, const float* grad_dev, float lr, float beta1, float beta2,
+                        float eps);
+/* Field training (Sec. 3.3-3.5): per step, fresh queries (step index as the
+ * Philox sub-stream), targets from the cache, forward, relative MSE
+ * (yhat-y)^2/(y^2+0.01) averaged over batch and channels, backward, Adam.
+ * loss_host [steps] (nullable) receives the loss of every step; synchronises
+ * at the end. */
+pf_status pf_train_field(pf_ctx* ctx, const pf_cache* cache, const pf_train_desc* desc, pf_field* field,
+                         float* loss_host);
+
+/* ---------------------------------------------------------------- rendering */
+/* Neural volumetric path tracing (Algorithm 2): per pixel and sample,
+ * RayGeneration (jittered pinhole ray, box test), VolumeSampling (first
+ * interaction), DirectIllumination (NEE towards every light), field query at
+ * the interaction with w = -ray direction, decode, and Compose
+ * L = 1/spp sum_k albedo_k (L_d,k + L_i,k).  step_vox > 0 selects ray
+ * marching with step step_vox voxels (stratified inverse-CDF free flight,
+ * marched shadow transmittance); step_vox == 0 selects delta tracking and
+ * ratio-tracking shadow rays.  field == NULL renders direct light only.
+ * out_rgb_dev [H*W*3] f32. */
+pf_status pf_render_neural(pf_ctx* ctx, const pf_volume* vol, const pf_light* lights, int n_lights, float g,
+                           const pf_camera* cam, int spp, float step_vox, uint64_t seed, const pf_field* field,
+                           float* out_rgb_dev);
+/* Plain multi-bounce path tracer (the paper's baseline): delta tracking,
+ * next-event estimation with ratio tracking at every real interaction,
+ * Henyey-Greenstein continuation, at most max_bounces interactions, Russian
+ * roulette from the third (use_rr).  out_rgb_dev [H*W*3] f32. */
+pf_status pf_render_pathtraced(pf_ctx* ctx, const pf_volume* vol, const pf_light* lights, int n_lights, float g,
+                               const pf_camera* cam, int spp, int max_bounces, uint64_t seed, int use_rr,
+                               float* out_rgb_dev);
+
+/* sqrt(sum (a-b)^2 / n) accumulated in FP64 on the device; synchronises. */
+pf_status pf_image_rmse(pf_ctx* ctx, const float* a_dev, const float* b_dev, int64_t n, double* out_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

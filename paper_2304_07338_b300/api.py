@@ -1,0 +1,295 @@
+"""Python binding of libpf (include/pf.h) with torch tensors as buffers.
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  Tensors supply device pointers; the context's stream is the
+torch current stream of its device unless one is given.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import (PfCacheInfo, PfCamera, PfError, PfFieldDesc, PfLight, PfTrainDesc, PfVolume)
+
+PREC = {"f32": 0, "bf16": 1, "f16": 2, "fp8": 3}
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _need(t: torch.Tensor, dtype, numel: Optional[int] = None, name: str = "tensor"):
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous CUDA %s tensor" % (name, dtype))
+    if numel is not None and t.numel() < numel:
+        raise ValueError("%s has %d elements, need %d" % (name, t.numel(), numel))
+
+
+class Context:
+    """pf_ctx: one device, one stream, the library's scratch."""
+
+    def __init__(self, device: int = 0, stream: Optional[torch.cuda.Stream] = None):
+        self.lib = _lib.load()
+        self.device = device
+        s = stream if stream is not None else torch.cuda.current_stream(device)
+        self.stream = s
+        h = C.c_void_p()
+        st = self.lib.pf_create(C.byref(h), device, C.c_void_p(s.cuda_stream))
+        if st != 0:
+            raise PfError(st, "pf_create failed")
+        self.h = h
+
+    def check(self, st: int):
+        if st != 0:
+            raise PfError(st, self.lib.pf_last_error(self.h).decode())
+
+    def sync(self):
+        self.check(self.lib.pf_sync(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Volume:
+    """Device-resident volume + transfer function (pf_volume)."""
+
+    def __init__(self, data: torch.Tensor, sigma_scale: float, albedo: float, tf: torch.Tensor,
+                 majorant: float = 0.0):
+        code = {torch.float32: 0, torch.float16: 1, torch.uint8: 2}[data.dtype]
+        if not data.is_cuda or not data.is_contiguous() or data.dim() != 3:
+            raise ValueError("volume data must be a contiguous 3-D CUDA tensor (nz, ny, nx)")
+        _need(tf, torch.float32, name="tf")
+        self.data, self.tf = data, tf
+        nz, ny, nx = data.shape
+        self.s = PfVolume(nx, ny, nz, code, data.data_ptr(), float(sigma_scale), float(albedo), tf.data_ptr(),
+                          int(tf.shape[0]), float(majorant))
+
+    @classmethod
+    def from_inputs(cls, vol, device="cuda"):
+        """From a paper_2304_07338_b300.inputs.Volume (numpy arrays)."""
+        data = torch.from_numpy(np.ascontiguousarray(vol.data)).to(device)
+        tf = torch.from_numpy(np.ascontiguousarray(vol.tf, np.float32)).to(device)
+        return cls(data, vol.sigma_scale, vol.albedo, tf)
+
+    def majorant(self, ctx: Context) -> float:
+        out = C.c_float()
+        ctx.check(ctx.lib.pf_volume_majorant(ctx.h, C.byref(self.s), C.byref(out)))
+        return out.value
+
+
+def _lights(lights) -> tuple:
+    arr = (PfLight * len(lights))()
+    for i, l in enumerate(lights):
+        arr[i].kind = int(l.kind)
+        for c in range(3):
+            arr[i].v[c] = float(l.v[c])
+            arr[i].rgb[c] = float(l.rgb[c])
+    return arr, len(lights)
+
+
+def _camera(cam) -> PfCamera:
+    c = PfCamera()
+    for i in range(3):
+        c.eye[i], c.at[i], c.up[i] = float(cam.eye[i]), float(cam.at[i]), float(cam.up[i])
+    c.fovy_deg, c.width, c.height = float(cam.fovy_deg), int(cam.width), int(cam.height)
+    return c
+
+
+class Cache:
+    """pf_cache: photon records (CSR by key), per-key counts and power sums."""
+
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.h = ctx, h
+        info = PfCacheInfo()
+        ctx.check(ctx.lib.pf_cache_info(ctx.h, h, C.byref(info)))
+        self.info = info
+
+    @property
+    def n_records(self):
+        return self.info.n_records
+
+    def tally(self) -> np.ndarray:
+        return np.array(self.info.tally[:]).reshape(5, 3)
+
+    def export(self):
+        i = self.info
+        dev = torch.device("cuda", self.ctx.device)
+        counts = torch.empty(i.n_keys, dtype=torch.int32, device=dev)
+        flux = torch.empty(i.n_keys * 3, dtype=torch.float32, device=dev)
+        nr = max(i.n_records, 1)
+        key = torch.empty(nr, dtype=torch.int32, device=dev)
+        rid = torch.empty(nr, dtype=torch.int32, device=dev)
+        rdir = torch.empty(nr * 3, dtype=torch.float32, device=dev)
+        rphi = torch.empty(nr * 3, dtype=torch.float32, device=dev)
+        occ = torch.empty(max(i.n_occupied, 1), dtype=torch.int32, device=dev)
+        csig = torch.empty(i.res ** 3, dtype=torch.float32, device=dev)
+        self.ctx.check(self.ctx.lib.pf_cache_export(self.ctx.h, self.h, *map(_ptr, (counts, flux, key, rid, rdir, rphi,
+                                                                                     occ, csig))))
+        torch.cuda.synchronize(dev)
+        n = i.n_records
+        return dict(counts=counts, flux=flux.view(-1, 3), key=key[:n], id=rid[:n], dir=rdir[:3 * n].view(-1, 3),
+                    phi=rphi[:3 * n].view(-1, 3), occupied=occ[:i.n_occupied], cell_sigma=csig)
+
+    def sample_queries(self, B: int, step: int, seed: int) -> torch.Tensor:
+        q = torch.empty(B * 6, dtype=torch.float32, device=torch.device("cuda", self.ctx.device))
+        self.ctx.check(self.ctx.lib.pf_sample_queries(self.ctx.h, self.h, B, step, seed, _ptr(q)))
+        return q.view(B, 6)
+
+    def estimate_targets(self, q: torch.Tensor, psi: float = 5.0):
+        _need(q, torch.float32, name="q")
+        B = q.numel() // 6
+        ls = torch.empty(B * 3, dtype=torch.float32, device=q.device)
+        lp = torch.empty(B * 3, dtype=torch.float32, device=q.device)
+        self.ctx.check(self.ctx.lib.pf_estimate_targets(self.ctx.h, self.h, _ptr(q), B, psi, _ptr(ls), _ptr(lp)))
+        return ls.view(B, 3), lp.view(B, 3)
+
+    def free(self):
+        if self.h:
+            self.ctx.lib.pf_cache_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def build_photon_cache(ctx: Context, vol: Volume, lights, g_set: Sequence[float], photons_per_light_per_g: int,
+                       max_bounces: int = 16, cache_res: int = 64, seed: int = 1, use_rr: bool = True) -> Cache:
+    la, n = _lights(lights)
+    g = (C.c_float * len(g_set))(*[float(x) for x in g_set])
+    h = C.c_void_p()
+    ctx.check(ctx.lib.pf_build_photon_cache(ctx.h, C.byref(vol.s), la, n, g, len(g_set), int(photons_per_light_per_g),
+                                            int(max_bounces), int(cache_res), int(seed), int(use_rr), C.byref(h)))
+    return Cache(ctx, h)
+
+
+class Field:
+    """pf_field: photon field network with library-owned weights."""
+
+    def __init__(self, ctx: Context, in_freqs=12, hidden=64, n_hidden=3, prec="f32", psi=5.0, seed=0):
+        self.ctx = ctx
+        self.prec = prec
+        self.desc = PfFieldDesc(int(in_freqs), int(hidden), int(n_hidden), PREC[prec] if isinstance(prec, str) else int(prec),
+                                float(psi), int(seed))
+        h = C.c_void_p()
+        ctx.check(ctx.lib.pf_field_create(ctx.h, C.byref(self.desc), C.byref(h)))
+        self.h = h
+        self.n_params = ctx.lib.pf_field_num_params(h)
+
+    @property
+    def psi(self):
+        return self.desc.psi
+
+    def get_weights(self) -> torch.Tensor:
+        w = torch.empty(self.n_params, dtype=torch.float32, device=torch.device("cuda", self.ctx.device))
+        self.ctx.check(self.ctx.lib.pf_field_get_weights(self.ctx.h, self.h, _ptr(w)))
+        return w
+
+    def set_weights(self, w: torch.Tensor):
+        _need(w, torch.float32, self.n_params, "weights")
+        self.ctx.check(self.ctx.lib.pf_field_set_weights(self.ctx.h, self.h, _ptr(w)))
+
+    def calibrate_fp8(self, q: torch.Tensor):
+        _need(q, torch.float32, name="q")
+        self.ctx.check(self.ctx.lib.pf_field_calibrate_fp8(self.ctx.h, self.h, _ptr(q), q.numel() // 6))
+
+    def forward(self, q: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        _need(q, torch.float32, name="q")
+        B = q.numel() // 6
+        if out is None:
+            out = torch.empty(B, 3, dtype=torch.float32, device=q.device)
+        self.ctx.check(self.ctx.lib.pf_field_forward(self.ctx.h, self.h, _ptr(q), B, _ptr(out)))
+        return out
+
+    def backward(self, q: torch.Tensor, dy: torch.Tensor) -> torch.Tensor:
+        _need(q, torch.float32, name="q")
+        _need(dy, torch.float32, name="dy")
+        B = q.numel() // 6
+        dw = torch.empty(self.n_params, dtype=torch.float32, device=q.device)
+        self.ctx.check(self.ctx.lib.pf_field_backward(self.ctx.h, self.h, _ptr(q), _ptr(dy), B, _ptr(dw)))
+        return dw
+
+    def adam(self, grad: torch.Tensor, lr: float, beta1=0.9, beta2=0.99, eps=1e-8):
+        _need(grad, torch.float32, self.n_params, "grad")
+        self.ctx.check(self.ctx.lib.pf_field_adam(self.ctx.h, self.h, _ptr(grad), lr, beta1, beta2, eps))
+
+    def train(self, cache: Cache, steps: int, batch: int, lr=1e-2, beta1=0.9, beta2=0.99, eps=1e-8, decay=0.92,
+              decay_start_frac=0.7, decay_every=25, seed=1) -> np.ndarray:
+        d = PfTrainDesc(steps, batch, lr, beta1, beta2, eps, decay, decay_start_frac, decay_every, seed)
+        loss = np.zeros(max(steps, 1), np.float32)
+        self.ctx.check(self.ctx.lib.pf_train_field(self.ctx.h, cache.h, C.byref(d), self.h,
+                                                   loss.ctypes.data_as(C.c_void_p)))
+        return loss[:steps]
+
+    def free(self):
+        if self.h:
+            self.ctx.lib.pf_field_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def render_neural(ctx: Context, vol: Volume, lights, g: float, cam, spp: int, step_vox: float, seed: int,
+                  field: Optional[Field] = None, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    la, n = _lights(lights)
+    c = _camera(cam)
+    if out is None:
+        out = torch.empty(cam.height, cam.width, 3, dtype=torch.float32, device=torch.device("cuda", ctx.device))
+    ctx.check(ctx.lib.pf_render_neural(ctx.h, C.byref(vol.s), la, n, float(g), C.byref(c), int(spp), float(step_vox),
+                                       int(seed), field.h if field is not None else None, _ptr(out)))
+    return out
+
+
+def render_pathtraced(ctx: Context, vol: Volume, lights, g: float, cam, spp: int, max_bounces: int = 16, seed: int = 1,
+                      use_rr: bool = True, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    la, n = _lights(lights)
+    c = _camera(cam)
+    if out is None:
+        out = torch.empty(cam.height, cam.width, 3, dtype=torch.float32, device=torch.device("cuda", ctx.device))
+    ctx.check(ctx.lib.pf_render_pathtraced(ctx.h, C.byref(vol.s), la, n, float(g), C.byref(c), int(spp),
+                                           int(max_bounces), int(seed), int(use_rr), _ptr(out)))
+    return out
+
+
+def image_rmse(ctx: Context, a: torch.Tensor, b: torch.Tensor) -> float:
+    _need(a, torch.float32, name="a")
+    _need(b, torch.float32, a.numel(), "b")
+    out = C.c_double()
+    ctx.check(ctx.lib.pf_image_rmse(ctx.h, _ptr(a), _ptr(b), a.numel(), C.byref(out)))
+    return out.value
+
+
+class FieldFunction(torch.autograd.Function):
+    """Differentiable field evaluation: y = P_phi(q) with gradients w.r.t. the
+    flat weight vector w, computed by the library's backward kernel."""
+
+    @staticmethod
+    def forward(ctx_, field: Field, q: torch.Tensor, w: torch.Tensor):
+        field.set_weights(w.detach().contiguous())
+        ctx_.field = field
+        ctx_.save_for_backward(q)
+        return field.forward(q.contiguous())
+
+    @staticmethod
+    def backward(ctx_, gy):
+        (q,) = ctx_.saved_tensors
+        dw = ctx_.field.backward(q.contiguous(), gy.contiguous().float())
+        return None, None, dw

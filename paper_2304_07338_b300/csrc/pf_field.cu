@@ -1,0 +1,654 @@
+// Photon field network (Sec. 3.4), its training samples (Sec. 3.3) and its
+// training loop (Sec. 3.5).
+//
+// This file holds the parts that are not tensor-core contractions:
+//   * seeded Kaiming-uniform initialisation;
+//   * the frequency encoding of the 6-D query;
+//   * a SIMT forward / backward (one thread per query, activations staged in
+//     shared memory column-per-thread) that serves float32 fields and rounds
+//     operands exactly as the tensor-core path specifies for the others;
+//   * the training-sample generator and grid-cell radiance estimate;
+//   * Adam and the training loop.
+// The bf16 / fp16 / fp8 contractions run on tcgen05 (pf_mlp_tc.cu).
+#include "pf_internal.h"
+#include "pf_field_common.cuh"
+#include <cmath>
+#include <vector>
+#include <algorithm>
+
+using namespace pff;
+
+// ------------------------------------------------------------------ init
+namespace {
+__device__ __forceinline__ void philox_block(uint64_t seed, uint32_t tag, uint64_t item, uint32_t sub, uint32_t block,
+                                             uint32_t o[4]) {
+  uint32_t x0 = (uint32_t)item, x1 = (uint32_t)(item >> 32), x2 = (tag << 24) | (sub & 0xFFFFFFu), x3 = block;
+  uint32_t a = (uint32_t)seed, b = (uint32_t)(seed >> 32);
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { a += 0x9E3779B9u; b += 0xBB67AE85u; }
+    uint32_t lo0 = 0xD2511F53u * x0, hi0 = __umulhi(0xD2511F53u, x0);
+    uint32_t lo1 = 0xCD9E8D57u * x2, hi1 = __umulhi(0xCD9E8D57u, x2);
+    uint32_t n0 = hi1 ^ x1 ^ a, n2 = hi0 ^ x3 ^ b;
+    x0 = n0; x1 = lo1; x2 = n2; x3 = lo0;
+  }
+  o[0] = x0; o[1] = x1; o[2] = x2; o[3] = x3;
+}
+
+// w = (2u - 1) sqrt(6 / fan_in) in FP64, rounded once (Kaiming-uniform).
+__global__ void k_init(float* w, int64_t off, int64_t n, int layer, int fan_in, uint64_t seed) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  uint32_t o[4];
+  philox_block(seed, 4, (uint64_t)layer, 0, (uint32_t)(e / 4), o);
+  double u = (double)(o[e % 4] >> 8) * (1.0 / 16777216.0);
+  double bound = sqrt(6.0 / (double)fan_in);
+  w[off + e] = (float)((2.0 * u - 1.0) * bound);
+}
+}  // namespace
+
+extern "C" pf_status pf_field_create(pf_ctx* ctx, const pf_field_desc* d, pf_field** out) {
+  if (!ctx || !d || !out) return PF_ERR_INVALID_ARG;
+  DeviceGuard dg(ctx->device);
+  *out = nullptr;
+  if (d->in_freqs < 1 || d->in_freqs > 16) return pf_fail(ctx, PF_ERR_INVALID_ARG, "in_freqs must be in [1, 16]");
+  if (d->hidden != 32 && d->hidden != 64 && d->hidden != 128)
+    return pf_fail(ctx, PF_ERR_INVALID_ARG, "hidden must be 32, 64 or 128");
+  if (d->n_hidden < 1 || d->n_hidden > 8) return pf_fail(ctx, PF_ERR_INVALID_ARG, "n_hidden must be in [1, 8]");
+  if (d->prec < 0 || d->prec > 3) return pf_fail(ctx, PF_ERR_INVALID_ARG, "unknown precision %d", d->prec);
+  if (!(d->psi > 0.f)) return pf_fail(ctx, PF_ERR_INVALID_ARG, "psi must be > 0");
+  pf_field* f = new pf_field();
+  f->ctx = ctx;
+  f->desc = *d;
+  f->n_in = 12 * d->in_freqs;
+  f->n_layers = d->n_hidden + 1;
+  int64_t off = 0;
+  for (int l = 0; l < f->n_layers; ++l) {
+    f->fan_in[l] = l == 0 ? f->n_in : d->hidden;
+    f->fan_out[l] = l == f->n_layers - 1 ? 3 : d->hidden;
+    f->layer_off[l] = off;
+    off += (int64_t)f->fan_in[l] * f->fan_out[l];
+  }
+  f->layer_off[f->n_layers] = off;
+  f->n_params = off;
+  size_t bytes = (size_t)off * sizeof(float);
+  if (cudaMalloc(&f->w, bytes) != cudaSuccess || cudaMalloc(&f->m, bytes) != cudaSuccess ||
+      cudaMalloc(&f->v, bytes) != cudaSuccess || cudaMalloc(&f->scales, 64 * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(f->w); cudaFree(f->m); cudaFree(f->v); cudaFree(f->scales);
+    delete f;
+    return pf_fail(ctx, PF_ERR_OOM, "field allocation failed");
+  }
+  cudaMemsetAsync(f->m, 0, bytes, ctx->stream);
+  cudaMemsetAsync(f->v, 0, bytes, ctx->stream);
+  cudaMemsetAsync(f->scales, 0, 64 * sizeof(float), ctx->stream);
+  for (int l = 0; l < f->n_layers; ++l) {
+    int64_t n = (int64_t)f->fan_in[l] * f->fan_out[l];
+    k_init<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(f->w, f->layer_off[l], n, l, f->fan_in[l], d->seed);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { pf_field_free(f); return pf_cuda_check(ctx, e, "field init"); }
+  pf_status st = pf_field_pack(ctx, f);
+  if (st != PF_OK) { pf_field_free(f); return st; }
+  *out = f;
+  return PF_OK;
+}
+
+extern "C" pf_status pf_field_free(pf_field* f) {
+  if (!f) return PF_OK;
+  DeviceGuard dg(f->ctx ? f->ctx->device : 0);
+  if (f->ctx) cudaStreamSynchronize(f->ctx->stream);
+  cudaFree(f->w); cudaFree(f->m); cudaFree(f->v); cudaFree(f->wq); cudaFree(f->scales);
+  delete f;
+  return PF_OK;
+}
+
+extern "C" int64_t pf_field_num_params(const pf_field* f) { return f ? f->n_params : -1; }
+
+extern "C" pf_status pf_field_get_weights(pf_ctx* ctx, const pf_field* f, float* dst) {
+  if (!ctx || !f || !dst) return PF_ERR_INVALID_ARG;
+  DeviceGuard dg(ctx->device);
+  PF_CUDA(ctx, cudaMemcpyAsync(dst, f->w, f->n_params * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
+  return PF_OK;
+}
+
+extern "C" pf_status pf_field_set_weights(pf_ctx* ctx, pf_field* f, const float* src) {
+  if (!ctx || !f || !src) return PF_ERR_INVALID_ARG;
+  DeviceGuard dg(ctx->device);
+  PF_CUDA(ctx, cudaMemcpyAsync(f->w, src, f->n_params * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
+  f->fp8_ready = 0;
+  return pf_field_pack(ctx, f);
+}
+
+// ------------------------------------------------------------------ SIMT forward / backward
+namespace {
+
+struct FieldView {
+  const float* w;
+  int64_t off[10];
+  int fan_in[10], fan_out[10];
+  int n_layers, n_in, hidden, in_freqs, prec;
+  float psi;
+  float s_a[8], s_w[8];
+};
+
+FieldView view_of(const pf_field* f) {
+  FieldView v;
+  v.w = f->w;
+  for (int l = 0; l <= f->n_layers && l < 10; ++l) v.off[l] = f->layer_off[l];
+  for (int l = 0; l < f->n_layers; ++l) { v.fan_in[l] = f->fan_in[l]; v.fan_out[l] = f->fan_out[l]; }
+  v.n_layers = f->n_layers; v.n_in = f->n_in; v.hidden = f->desc.hidden; v.in_freqs = f->desc.in_freqs;
+  v.prec = f->desc.prec; v.psi = f->desc.psi;
+  for (int l = 0; l < 8; ++l) { v.s_a[l] = f->scales_host[l]; v.s_w[l] = f->scales_host[16 + l]; }
+  return v;
+}
+
+constexpr int kSimtThreads = 64;   // forward: queries per block
+constexpr int kBwdThreads = 32;    // backward: queries per block (one warp)
+constexpr int kMaxK = 192;         // 12 * 16 frequencies
+
+// Operand rounding of the hidden layers (see pf_field_common.cuh).
+__device__ __forceinline__ float rin(float x, int prec, float s) { return round_prec(x, prec, s); }
+
+// Forward for one block of T queries; activations column-per-thread in
+// shared memory: buf[k * T + tid].  Returns the 3 outputs in y.  If keep is
+// given, the (rounded) input of layer l is kept at keep[(koff[l] + k) * T + tid].
+template <int T>
+__device__ void simt_forward(const FieldView& F, const float* q, int tid, float* bufA, float* bufB, float* keep,
+                             const int* koff, float y[3]) {
+  // encoding -> bufA (rounded to the first layer's input precision)
+  for (int d = 0; d < 6; ++d) {
+    float v = q[d];
+    for (int k = 0; k < F.in_freqs; ++k) {
+      float s, c;
+      sincospif(ldexpf(v, k), &s, &c);
+      int idx = d * 2 * F.in_freqs + 2 * k;
+      bufA[idx * T + tid] = s;
+      bufA[(idx + 1) * T + tid] = c;
+    }
+  }
+  float* in = bufA;
+  float* outb = bufB;
+  for (int l = 0; l < F.n_layers; ++l) {
+    const bool last = (l == F.n_layers - 1);
+    const int K = F.fan_in[l], N = F.fan_out[l];
+    const float* W = F.w + F.off[l];
+    if (!last) {
+      for (int k = 0; k < K; ++k) {
+        float r = rin(in[k * T + tid], F.prec, F.s_a[l]);
+        in[k * T + tid] = r;
+        if (keep) keep[((size_t)koff[l] + k) * T + tid] = r;
+      }
+    } else if (keep) {
+      for (int k = 0; k < K; ++k) keep[((size_t)koff[l] + k) * T + tid] = in[k * T + tid];
+    }
+    for (int n = 0; n < N; ++n) {
+      float acc = 0.f;
+      const float* wr = W + (size_t)n * K;
+      for (int k = 0; k < K; ++k) {
+        float wv = __ldg(wr + k);
+        if (!last) wv = rin(wv, F.prec, F.s_w[l]);
+        acc = fmaf(in[k * T + tid], wv, acc);
+      }
+      if (last) y[n] = acc;
+      else outb[n * T + tid] = fmaxf(acc, 0.f);
+    }
+    float* t = in; in = outb; outb = t;
+  }
+}
+
+__global__ void __launch_bounds__(kSimtThreads) k_simt_forward(FieldView F, const float* __restrict__ q, int64_t B_max,
+                                                             const uint32_t* __restrict__ B_dev, float* __restrict__ out,
+                                                             const uint32_t* __restrict__ slot_idx,
+                                                             const float* __restrict__ slot_alb, float* __restrict__ slot_li) {
+  extern __shared__ float sm[];
+  float* bufA = sm;
+  float* bufB = sm + kMaxK * kSimtThreads;
+  int64_t B = B_dev ? (int64_t)*B_dev : B_max;
+  int64_t b = (int64_t)blockIdx.x * kSimtThreads + threadIdx.x;
+  if ((int64_t)blockIdx.x * kSimtThreads >= B) return;
+  float qq[6];
+  bool act = b < B;
+  for (int d = 0; d < 6; ++d) qq[d] = act ? q[6 * b + d] : 0.5f;
+  float y[3];
+  simt_forward<kSimtThreads>(F, qq, threadIdx.x, bufA, bufB, nullptr, nullptr, y);
+  if (!act) return;
+  if (slot_idx) {
+    uint32_t s = slot_idx[b];
+    for (int c = 0; c < 3; ++c) slot_li[3 * (size_t)s + c] = slot_alb[3 * b + c] * exp10f(-F.psi * y[c]);
+  } else {
+    for (int c = 0; c < 3; ++c) out[3 * b + c] = y[c];
+  }
+}
+
+// Backward: each thread recomputes its forward, keeps every layer's input,
+// back-propagates dy and accumulates its dW contribution into shared memory
+// partials that are added to global dW once per block.
+// loss mode (targets != nullptr): dy = 2 (yhat - y) / (y^2 + 0.01) * inv_n and
+// the block's loss sum goes to *loss.
+__global__ void __launch_bounds__(kBwdThreads) k_simt_backward(FieldView F, const float* __restrict__ q,
+                                                            const float* __restrict__ dy_in,
+                                                            const float* __restrict__ targets, float inv_n,
+                                                            int64_t B, float* __restrict__ dw, float* loss) {
+  constexpr int T = kBwdThreads;
+  extern __shared__ float sm[];
+  int koff[10];
+  int rows = 0;
+  for (int l = 0; l < F.n_layers; ++l) { koff[l] = rows; rows += F.fan_in[l]; }
+  int kmax = F.n_in > F.hidden ? F.n_in : F.hidden;
+  float* bufA = sm;
+  float* bufB = bufA + (size_t)kmax * T;
+  float* keep = bufB + (size_t)kmax * T;
+  float* dcur = keep + (size_t)rows * T;
+  float* dnext = dcur + (size_t)kmax * T;
+  int tid = threadIdx.x;
+  int64_t b = (int64_t)blockIdx.x * T + tid;
+  bool act = b < B;
+  float qq[6];
+  for (int d = 0; d < 6; ++d) qq[d] = act ? q[6 * b + d] : 0.5f;
+  float y[3];
+  simt_forward<T>(F, qq, tid, bufA, bufB, keep, koff, y);
+  float g[3] = {0.f, 0.f, 0.f};
+  float lsum = 0.f;
+  if (act) {
+    if (targets) {
+      for (int c = 0; c < 3; ++c) {
+        float t = targets[3 * b + c];
+        float den = t * t + 0.01f;
+        float diff = y[c] - t;
+        lsum += diff * diff / den;
+        g[c] = 2.f * diff / den * inv_n;
+      }
+    } else {
+      for (int c = 0; c < 3; ++c) g[c] = dy_in[3 * b + c];
+    }
+  }
+  if (loss) {
+    for (int off = 16; off > 0; off >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, off);
+    if (tid == 0) atomicAdd(loss, lsum * inv_n);
+  }
+  for (int c = 0; c < 3; ++c) dcur[c * T + tid] = g[c];
+  for (int l = F.n_layers - 1; l >= 0; --l) {
+    const bool last = (l == F.n_layers - 1);
+    const int K = F.fan_in[l], N = F.fan_out[l];
+    const float* W = F.w + F.off[l];
+    const float* xin = keep + (size_t)koff[l] * T;
+    __syncwarp();
+    // dW[n][k] += sum over the block's queries of dcur[n] * xin[k]
+    for (int e = tid; e < N * K; e += T) {
+      int n = e / K, k = e % K;
+      float s = 0.f;
+      for (int t = 0; t < T; ++t) s = fmaf(dcur[n * T + t], xin[k * T + t], s);
+      atomicAdd(&dw[F.off[l] + e], s);
+    }
+    if (l == 0) break;
+    // gradient w.r.t. the input of layer l: W^T dcur, masked by the ReLU of
+    // layer l-1 (taken from the rounded activation) and rounded
+    for (int k = 0; k < K; ++k) {
+      float acc = 0.f;
+      for (int n = 0; n < N; ++n) {
+        float wv = __ldg(W + (size_t)n * K + k);
+        if (!last) wv = rin(wv, F.prec, F.s_w[l]);
+        acc = fmaf(dcur[n * T + tid], wv, acc);
+      }
+      float a = xin[k * T + tid];
+      float m = rin(a, F.prec, 1.f) > 0.f ? 1.f : 0.f;
+      dnext[k * T + tid] = rin(acc * m, F.prec, 1.f);
+    }
+    __syncwarp();
+    float* t = dcur; dcur = dnext; dnext = t;
+  }
+}
+
+size_t simt_fwd_smem() { return 2 * kMaxK * kSimtThreads * sizeof(float); }
+size_t simt_bwd_smem(const pf_field* f) {
+  int kmax = std::max(f->n_in, f->desc.hidden);
+  int64_t rows = 4 * (int64_t)kmax + (f->layer_off[f->n_layers] > 0 ? 0 : 0);
+  for (int l = 0; l < f->n_layers; ++l) rows += f->fan_in[l];
+  return (size_t)rows * kBwdThreads * sizeof(float);
+}
+
+}  // namespace
+
+pf_status pf_simt_forward(pf_ctx* ctx, const pf_field* f, const float* q, int64_t B_max, const uint32_t* B_dev,
+                          float* out, const uint32_t* slot_idx, const float* slot_alb, float* slot_li) {
+  if (B_max <= 0) return PF_OK;
+  FieldView F = view_of(f);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_simt_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)simt_fwd_smem());
+    attr = true;
+  }
+  unsigned grid = (unsigned)((B_max + kSimtThreads - 1) / kSimtThreads);
+  k_simt_forward<<<grid, kSimtThreads, simt_fwd_smem(), ctx->stream>>>(F, q, B_max, B_dev, out, slot_idx, slot_alb, slot_li);
+  PF_CUDA(ctx, cudaGetLastError());
+  return PF_OK;
+}
+
+pf_status pf_simt_backward(pf_ctx* ctx, const pf_field* f, const float* q, const float* dy, const float* targets,
+                           int64_t B, float* dw, float* loss) {
+  FieldView F = view_of(f);
+  size_t sm = simt_bwd_smem(f);
+  if (sm > 227 * 1024) return pf_fail(ctx, PF_ERR_UNSUPPORTED, "SIMT backward: network too deep for shared memory");
+  cudaFuncSetAttribute(k_simt_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  unsigned grid = (unsigned)((B + kBwdThreads - 1) / kBwdThreads);
+  float inv_n = targets ? 1.0f / (float)(3 * B) : 0.f;
+  k_simt_backward<<<grid, kBwdThreads, sm, ctx->stream>>>(F, q, dy, targets, inv_n, B, dw, loss);
+  PF_CUDA(ctx, cudaGetLastError());
+  return PF_OK;
+}
+
+// ------------------------------------------------------------------ fp8 calibration
+namespace {
+// amax of every hidden layer's input over the calibration queries, from the
+// unquantised float forward pass (one thread per query).
+__global__ void __launch_bounds__(kSimtThreads) k_calib(FieldView F, const float* __restrict__ q, int64_t B,
+                                                      unsigned int* amax) {
+  extern __shared__ float sm[];
+  float* bufA = sm;
+  float* bufB = sm + kMaxK * kSimtThreads;
+  int tid = threadIdx.x;
+  int64_t b = (int64_t)blockIdx.x * kSimtThreads + tid;
+  bool act = b < B;
+  for (int d = 0; d < 6; ++d) {
+    float v = act ? q[6 * b + d] : 0.f;
+    for (int k = 0; k < F.in_freqs; ++k) {
+      float s, c;
+      sincospif(ldexpf(v, k), &s, &c);
+      int idx = d * 2 * F.in_freqs + 2 * k;
+      bufA[idx * kSimtThreads + tid] = act ? s : 0.f;
+      bufA[(idx + 1) * kSimtThreads + tid] = act ? c : 0.f;
+    }
+  }
+  float* in = bufA;
+  float* outb = bufB;
+  for (int l = 0; l < F.n_layers - 1; ++l) {
+    const int K = F.fan_in[l], N = F.fan_out[l];
+    float m = 0.f;
+    for (int k = 0; k < K; ++k) m = fmaxf(m, fabsf(in[k * kSimtThreads + tid]));
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, off));
+    if ((tid & 31) == 0) atomicMax(&amax[l], __float_as_uint(m));
+    const float* W = F.w + F.off[l];
+    for (int n = 0; n < N; ++n) {
+      float acc = 0.f;
+      for (int k = 0; k < K; ++k) acc = fmaf(in[k * kSimtThreads + tid], __ldg(W + (size_t)n * K + k), acc);
+      outb[n * kSimtThreads + tid] = fmaxf(acc, 0.f);
+    }
+    float* t = in; in = outb; outb = t;
+  }
+}
+
+__global__ void k_wamax(const float* __restrict__ w, int64_t off, int64_t n, unsigned int* amax) {
+  float m = 0.f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(w[off + i]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(amax, __float_as_uint(m));
+}
+}  // namespace
+
+extern "C" pf_status pf_field_calibrate_fp8(pf_ctx* ctx, pf_field* f, const float* q, int64_t B) {
+  if (!ctx || !f || !q || B <= 0) return PF_ERR_INVALID_ARG;
+  DeviceGuard dg(ctx->device);
+  unsigned int* amax;
+  PF_TRY(pf_scratch(ctx, WS_REDUCE, 64 * sizeof(unsigned int), (void**)&amax));
+  PF_CUDA(ctx, cudaMemsetAsync(amax, 0, 64 * sizeof(unsigned int), ctx->stream));
+  FieldView F = view_of(f);
+  cudaFuncSetAttribute(k_calib, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)simt_fwd_smem());
+  k_calib<<<(unsigned)((B + kSimtThreads - 1) / kSimtThreads), kSimtThreads, simt_fwd_smem(), ctx->stream>>>(F, q, B, amax);
+  for (int l = 0; l < f->n_layers - 1; ++l) {
+    int64_t n = (int64_t)f->fan_in[l] * f->fan_out[l];
+    k_wamax<<<64, 256, 0, ctx->stream>>>(f->w, f->layer_off[l], n, amax + 16 + l);
+  }
+  PF_CUDA(ctx, cudaGetLastError());
+  unsigned int h[64];
+  PF_CUDA(ctx, cudaMemcpyAsync(h, amax, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+  PF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  for (int l = 0; l < f->n_layers - 1; ++l) {
+    float a, w;
+    memcpy(&a, &h[l], 4);
+    memcpy(&w, &h[16 + l], 4);
+    f->scales_host[l] = fmaxf(a, 1e-30f) / 448.0f;
+    f->scales_host[16 + l] = fmaxf(w, 1e-30f) / 448.0f;
+  }
+  PF_CUDA(ctx, cudaMemcpyAsync(f->scales, f->scales_host, 32 * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  f->fp8_ready = 1;
+  PF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return pf_field_pack(ctx, f);
+}
+
+// ------------------------------------------------------------------ public forward / backward
+pf_status pf_tc_available(const pf_field* f);
+pf_status pf_tc_forward(pf_ctx* ctx, const pf_field* f, const float* q, int64_t B_max, const uint32_t* B_dev, float* out,
+                        const uint32_t* slot_idx, const float* slot_alb, float* slot_li);
+pf_status pf_tc_backward(pf_ctx* ctx, const pf_field* f, const float* q, const float* dy, const float* targets,
+                         int64_t B, float* dw, float* loss);
+
+pf_status pf_field_forward_impl(pf_ctx* ctx, const pf_field* f, const float* q, int64_t B_max, const uint32_t* B_dev,
+                                float* out, const uint32_t* slot_idx, const float* slot_alb, float* slot_li) {
+  if (f->desc.prec == PF_PREC_FP8 && !f->fp8_ready)
+    return pf_fail(ctx, PF_ERR_INVALID_ARG, "fp8 field: call pf_field_calibrate_fp8 first");
+  if (pf_tc_available(f) == PF_OK) return pf_tc_forward(ctx, f, q, B_max, B_dev, out, slot_idx, slot_alb, slot_li);
+  return pf_simt_forward(ctx, f, q, B_max, B_dev, out, slot_idx, slot_alb, slot_li);
+}
+
+extern "C" pf_status pf_field_forward(pf_ctx* ctx, const pf_field* f, const float* q, int64_t B, float* out) {
+  if (!ctx || !f || !q || !out || B < 0) return pf_fail(ctx, PF_ERR_INVALID_ARG, "bad field forward arguments");
+  if (f->ctx != ctx) return pf_fail(ctx, PF_ERR_INVALID_ARG, "field belongs to another context");
+  DeviceGuard dg(ctx->device);
+  return pf_field_forward_impl(ctx, f, q, B, nullptr, out, nullptr, nullptr, nullptr);
+}
+
+pf_status pf_field_backward_impl(pf_ctx* ctx, const pf_field* f, const float* q, const float* dy, const float* targets,
+                                 int64_t B, float* dw, float* loss) {
+  if (f->desc.prec == PF_PREC_FP8) return pf_fail(ctx, PF_ERR_UNSUPPORTED, "fp8 fields are inference-only");
+  PF_CUDA(ctx, cudaMemsetAsync(dw, 0, f->n_params * sizeof(float), ctx->stream));
+  if (B == 0) return PF_OK;
+  if (pf_tc_available(f) == PF_OK) return pf_tc_backward(ctx, f, q, dy, targets, B, dw, loss);
+  return pf_simt_backward(ctx, f, q, dy, targets, B, dw, loss);
+}
+
+extern "C" pf_status pf_field_backward(pf_ctx* ctx, const pf_field* f, const float* q, const float* dy, int64_t B,
+                                       float* dw) {
+  if (!ctx || !f || !q || !dy || !dw || B < 0) return pf_fail(ctx, PF_ERR_INVALID_ARG, "bad field backward arguments");
+  if (f->ctx != ctx) return pf_fail(ctx, PF_ERR_INVALID_ARG, "field belongs to another context");
+  DeviceGuard dg(ctx->device);
+  return pf_field_backward_impl(ctx, f, q, dy, nullptr, B, dw, nullptr);
+}
+
+// ------------------------------------------------------------------ Adam
+namespace {
+__global__ void k_adam(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v, const float* __restrict__ g,
+                       int64_t n, float lr, float b1, float b2, float eps, float c1, float c2, uint32_t* err) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float gi = g[i];
+  if (!isfinite(gi)) { atomicOr(err, 2u); return; }
+  float mi = b1 * m[i] + (1.f - b1) * gi;
+  float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  float mh = mi / c1, vh = vi / c2;
+  w[i] = w[i] - lr * mh / (sqrtf(vh) + eps);
+}
+}  // namespace
+
+pf_status pf_adam_impl(pf_ctx* ctx, pf_field* f, const float* g, float lr, float b1, float b2, float eps) {
+  f->step += 1;
+  float c1 = (float)(1.0 - std::pow((double)b1, f->step));
+  float c2 = (float)(1.0 - std::pow((double)b2, f->step));
+  k_adam<<<(unsigned)((f->n_params + 255) / 256), 256, 0, ctx->stream>>>(f->w, f->m, f->v, g, f->n_params, lr, b1, b2,
+                                                                         eps, c1, c2, ctx->err_dev);
+  PF_CUDA(ctx, cudaGetLastError());
+  return pf_field_pack(ctx, f);
+}
+
+extern "C" pf_status pf_field_adam(pf_ctx* ctx, pf_field* f, const float* g, float lr, float b1, float b2, float eps) {
+  if (!ctx || !f || !g) return PF_ERR_INVALID_ARG;
+  DeviceGuard dg(ctx->device);
+  return pf_adam_impl(ctx, f, g, lr, b1, b2, eps);
+}
+
+// ------------------------------------------------------------------ training samples
+namespace {
+struct CacheView {
+  const uint64_t* offsets;
+  const float4* recs;
+  const uint32_t* occupied;
+  const float* cell_sigma;
+  int64_t n_occupied;
+  int res, n_lights, n_g;
+  float g_set[16];
+};
+
+CacheView cview(const pf_cache* c) {
+  CacheView v;
+  v.offsets = c->offsets; v.recs = c->recs; v.occupied = c->occupied; v.cell_sigma = c->cell_sigma;
+  v.n_occupied = c->n_occupied; v.res = c->res; v.n_lights = c->n_lights; v.n_g = c->n_g;
+  for (int i = 0; i < 16; ++i) v.g_set[i] = c->g_set[i];
+  return v;
+}
+
+// Query i of step s (Philox tag 3, item i, sub s): block 0 -> cell (integer
+// scaling of the top 24 bits), position in the cell; block 1 -> direction
+// (z = 1 - 2u, azimuth u turns) and phase index.
+__device__ __forceinline__ void sample_query(const CacheView& C, int64_t i, int step, uint64_t seed, float q[6]) {
+  uint32_t a[4], b[4];
+  philox_block(seed, 3, (uint64_t)i, (uint32_t)step, 0, a);
+  philox_block(seed, 3, (uint64_t)i, (uint32_t)step, 1, b);
+  uint64_t ci = ((uint64_t)(a[0] >> 8) * (uint64_t)C.n_occupied) >> 24;
+  uint32_t cell = C.occupied[ci];
+  int R = C.res;
+  int cx = (int)(cell % R), cy = (int)((cell / R) % R), cz = (int)(cell / ((uint32_t)R * R));
+  const float k24 = 5.9604644775390625e-08f;
+  q[0] = ((float)cx + (float)(a[1] >> 8) * k24) / (float)R;
+  q[1] = ((float)cy + (float)(a[2] >> 8) * k24) / (float)R;
+  q[2] = ((float)cz + (float)(a[3] >> 8) * k24) / (float)R;
+  float wz = 1.0f - 2.0f * ((float)(b[0] >> 8) * k24);
+  q[3] = acosf(fminf(fmaxf(wz, -1.f), 1.f)) * 0.318309886183790672f;
+  q[4] = (float)(b[1] >> 8) * k24;
+  int gi = (int)(((uint64_t)(b[2] >> 8) * (uint64_t)C.n_g) >> 24);
+  q[5] = C.g_set[gi];
+}
+
+// Grid-cell radiance estimate of query q (see pf_estimate_targets).
+__device__ __forceinline__ void estimate(const CacheView& C, const float q[6], float Ls[3]) {
+  int gi = 0;
+  for (int i = 0; i < C.n_g; ++i) if (C.g_set[i] == q[5]) gi = i;
+  float g = C.g_set[gi];
+  float st, ct, sp, cp;
+  sincospif(q[3], &st, &ct);
+  sincospif(2.0f * q[4], &sp, &cp);
+  float wx = st * cp, wy = st * sp, wz = ct;
+  int R = C.res;
+  int bx = min(max((int)floorf(q[0] * (float)R), 0), R - 1);
+  int by = min(max((int)floorf(q[1] * (float)R), 0), R - 1);
+  int bz = min(max((int)floorf(q[2] * (float)R), 0), R - 1);
+  int64_t nc = (int64_t)R * R * R;
+  int64_t cell = bx + (int64_t)R * (by + (int64_t)R * bz);
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+  float gg = g * g, c0 = 0.0795774715459476678f * (1.f - gg), c1 = 1.f + gg, c2 = 2.f * g;
+  for (int l = 0; l < C.n_lights; ++l) {
+    int64_t key = (int64_t)(l * C.n_g + gi) * nc + cell;
+    uint64_t e = C.offsets[key + 1];
+    for (uint64_t n = C.offsets[key]; n < e; ++n) {
+      float4 r0 = __ldg(&C.recs[2 * n]), r1 = __ldg(&C.recs[2 * n + 1]);
+      float mu = r0.z * wx + r0.w * wy + r1.x * wz;
+      float den = c1 - c2 * mu;
+      float p = c0 / (den * sqrtf(den));
+      a0 = fmaf(p, r1.y, a0); a1 = fmaf(p, r1.z, a1); a2 = fmaf(p, r1.w, a2);
+    }
+  }
+  float s = C.cell_sigma[cell];
+  float norm = s > 0.f ? 1.0f / ((1.0f / (float)nc) * s) : 0.f;
+  Ls[0] = a0 * norm; Ls[1] = a1 * norm; Ls[2] = a2 * norm;
+}
+
+__device__ __forceinline__ float log_encode(float L, float psi) {
+  return L > exp10f(-psi) ? -log10f(L) / psi : 1.0f;
+}
+
+__global__ void k_sample_queries(CacheView C, int64_t B, int step, uint64_t seed, float* __restrict__ q) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B) return;
+  float v[6];
+  sample_query(C, i, step, seed, v);
+  for (int d = 0; d < 6; ++d) q[6 * i + d] = v[d];
+}
+
+__global__ void k_estimate(CacheView C, const float* __restrict__ q, int64_t B, float psi, float* __restrict__ ls,
+                           float* __restrict__ lp) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B) return;
+  float v[6], L[3];
+  for (int d = 0; d < 6; ++d) v[d] = q[6 * i + d];
+  estimate(C, v, L);
+  for (int c = 0; c < 3; ++c) {
+    if (ls) ls[3 * i + c] = L[c];
+    if (lp) lp[3 * i + c] = log_encode(L[c], psi);
+  }
+}
+
+// Fused training-batch generator: queries and their log-encoded targets.
+__global__ void k_batch(CacheView C, int64_t B, int step, uint64_t seed, float psi, float* __restrict__ q,
+                        float* __restrict__ y) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B) return;
+  float v[6], L[3];
+  sample_query(C, i, step, seed, v);
+  estimate(C, v, L);
+  for (int d = 0; d < 6; ++d) q[6 * i + d] = v[d];
+  for (int c = 0; c < 3; ++c) y[3 * i + c] = log_encode(L[c], psi);
+}
+}  // namespace
+
+extern "C" pf_status pf_sample_queries(pf_ctx* ctx, const pf_cache* c, int64_t B, int step, uint64_t seed, float* q) {
+  if (!ctx || !c || !q || B < 0 || step < 0 || step >= (1 << 24)) return pf_fail(ctx, PF_ERR_INVALID_ARG, "bad query arguments");
+  if (c->n_occupied == 0) return pf_fail(ctx, PF_ERR_INVALID_ARG, "cache has no occupied cells");
+  DeviceGuard dg(ctx->device);
+  if (B == 0) return PF_OK;
+  k_sample_queries<<<(unsigned)((B + 255) / 256), 256, 0, ctx->stream>>>(cview(c), B, step, seed, q);
+  PF_CUDA(ctx, cudaGetLastError());
+  return PF_OK;
+}
+
+extern "C" pf_status pf_estimate_targets(pf_ctx* ctx, const pf_cache* c, const float* q, int64_t B, float psi, float* ls,
+                                         float* lp) {
+  if (!ctx || !c || !q || B < 0 || !(psi > 0.f)) return pf_fail(ctx, PF_ERR_INVALID_ARG, "bad estimate arguments");
+  DeviceGuard dg(ctx->device);
+  if (B == 0) return PF_OK;
+  k_estimate<<<(unsigned)((B + 255) / 256), 256, 0, ctx->stream>>>(cview(c), q, B, psi, ls, lp);
+  PF_CUDA(ctx, cudaGetLastError());
+  return PF_OK;
+}
+
+// ------------------------------------------------------------------ training loop
+extern "C" pf_status pf_train_field(pf_ctx* ctx, const pf_cache* c, const pf_train_desc* d, pf_field* f, float* loss_host) {
+  if (!ctx || !c || !d || !f) return PF_ERR_INVALID_ARG;
+  DeviceGuard dg(ctx->device);
+  if (d->steps < 0 || d->batch <= 0 || !(d->lr > 0.f) || d->decay_every <= 0)
+    return pf_fail(ctx, PF_ERR_INVALID_ARG, "bad training description");
+  if (c->n_occupied == 0) return pf_fail(ctx, PF_ERR_INVALID_ARG, "cache has no occupied cells");
+  if (f->desc.prec == PF_PREC_FP8) return pf_fail(ctx, PF_ERR_UNSUPPORTED, "fp8 fields are inference-only; train bf16/fp16");
+  int64_t B = d->batch;
+  float *q, *y, *g, *loss;
+  PF_TRY(pf_scratch(ctx, WS_QUERY, B * 6 * sizeof(float), (void**)&q));
+  PF_TRY(pf_scratch(ctx, WS_TARGET, B * 3 * sizeof(float), (void**)&y));
+  PF_TRY(pf_scratch(ctx, WS_GRAD, f->n_params * sizeof(float), (void**)&g));
+  PF_TRY(pf_scratch(ctx, WS_LOSS, (size_t)std::max(d->steps, 1) * sizeof(float), (void**)&loss));
+  PF_CUDA(ctx, cudaMemsetAsync(loss, 0, (size_t)std::max(d->steps, 1) * sizeof(float), ctx->stream));
+  CacheView C = cview(c);
+  int s0 = (int)std::ceil((double)d->decay_start_frac * d->steps);
+  for (int s = 0; s < d->steps; ++s) {
+    k_batch<<<(unsigned)((B + 255) / 256), 256, 0, ctx->stream>>>(C, B, s, d->seed, f->desc.psi, q, y);
+    PF_CUDA(ctx, cudaGetLastError());
+    PF_TRY(pf_field_backward_impl(ctx, f, q, nullptr, y, B, g, loss + s));
+    int k = s < s0 ? 0 : (s - s0) / d->decay_every + 1;
+    float lr = (float)((double)d->lr * std::pow((double)d->decay, k));
+    PF_TRY(pf_adam_impl(ctx, f, g, lr, d->beta1, d->beta2, d->eps));
+  }
+  if (loss_host && d->steps > 0)
+    PF_CUDA(ctx, cudaMemcpyAsync(loss_host, loss, d->steps * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+  PF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return pf_check_error_word(ctx);
+}

@@ -1,0 +1,348 @@
+// Neural volumetric path tracing (Algorithm 2) and the plain path tracer.
+//
+// Wavefront organisation on B300:
+//   k_camera_samples  one thread per (pixel, sample): RayGeneration, free
+//                     flight (VolumeSampling), next-event estimation
+//                     (DirectIllumination); writes albedo*L_d per sample slot
+//                     and appends the valid samples' field queries to a
+//                     compacted list (one atomic per warp);
+//   field forward     over the compacted list only (the paper's "compact the
+//                     samples buffer, discarding ... holes"), decode, times
+//                     albedo, written back to the sample's slot;
+//   k_compose         one thread per pixel, sums its samples in order.
+// The path tracer uses the same slot layout and an in-order per-pixel sum,
+// processed in chunks of samples so that any spp fits in bounded scratch.
+//
+// Compiled with -fmad=false: see pf_device.cuh.
+#include "pf_internal.h"
+#include "pf_device.cuh"
+#include <cmath>
+#include <vector>
+#include <algorithm>
+
+using namespace pfd;
+
+namespace {
+
+// -------------------------------------------------------------- camera samples
+template <int DT, bool MARCH>
+__global__ void __launch_bounds__(128) k_camera_samples(Vol V, DevLights L, CamF cam, float g, int spp, float h,
+                                                        uint64_t seed, int64_t n_slots, float* __restrict__ slot_ld,
+                                                        float* __restrict__ slot_li, float* __restrict__ cq,
+                                                        float* __restrict__ calb, uint32_t* __restrict__ cidx,
+                                                        uint32_t* __restrict__ ccount, uint32_t* err) {
+  int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool active = slot < n_slots;
+  int valid = 0;
+  V3 x = v3(0.f, 0.f, 0.f), wo = x, alb = x, Ld = x;
+  if (active) {
+    int k = (int)(slot % spp);
+    int64_t pix = slot / spp;
+    int px = (int)(pix % cam.W), py = (int)(pix / cam.W);
+    Rng rng(seed, TAG_CAMERA, (uint64_t)pix, (uint32_t)k);
+    float b0[4]; rng.uni4(b0);
+    V3 o, d;
+    camera_ray(cam, px, py, b0[0], b0[1], &o, &d);
+    wo = v3(-d.x, -d.y, -d.z);
+    float t0, t1;
+    if (box_hit(o, d, &t0, &t1)) {
+      float th = 0.f;
+      bool hit = false;
+      float jl[16];
+      if (MARCH) {
+        for (int b = 0; b < (L.n + 3) / 4; ++b) {
+          float w[4]; rng.uni4(w);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) if (4 * b + i < 16) jl[4 * b + i] = w[i];
+        }
+        float tau_star = -own_lnf(1.0f - b0[3]);
+        float tau = 0.f;
+        int nseg = (int)ceilf((t1 - t0) / h);
+        for (int s = 0; s < nseg; ++s) {
+          float s0 = t0 + (float)s * h;
+          float s1 = mn(t0 + (float)(s + 1) * h, t1);
+          float len = s1 - s0;
+          if (!(len > 0.f)) continue;
+          float sg = sigma_at<DT>(V, along(o, d, s0 + b0[2] * len));
+          if (sg > 0.f && tau + sg * len >= tau_star) {
+            th = s0 + (tau_star - tau) / sg;
+            hit = true;
+            break;
+          }
+          tau = tau + sg * len;
+        }
+      } else {
+        hit = delta_track<DT>(V, o, d, t0, t1, rng, &th, err);
+      }
+      if (hit) {
+        x = along(o, d, th);
+        float sig;
+        medium_at<DT>(V, x, &sig, &alb);
+        for (int l = 0; l < L.n; ++l) {
+          V3 wl, E; float dist;
+          light_geom(L.l[l], x, &wl, &dist, &E);
+          float a0, a1, tend = 0.f;
+          if (box_hit(x, wl, &a0, &a1)) tend = mn(a1, dist);
+          float T;
+          if (MARCH) {
+            float tau = 0.f;
+            if (tend > 0.f) {
+              int nseg = (int)ceilf(tend / h);
+              for (int s = 0; s < nseg; ++s) {
+                float s0 = (float)s * h;
+                float s1 = mn((float)(s + 1) * h, tend);
+                float len = s1 - s0;
+                if (!(len > 0.f)) continue;
+                tau = tau + sigma_at<DT>(V, along(x, wl, s0 + jl[l] * len)) * len;
+              }
+            }
+            T = expf(-tau);
+          } else {
+            T = ratio_track<DT>(V, x, wl, tend, rng, err);
+          }
+          float ph = hg_eval(g, dot(d, wl));
+          Ld = v3(Ld.x + ph * T * E.x, Ld.y + ph * T * E.y, Ld.z + ph * T * E.z);
+        }
+        valid = 1;
+      }
+    }
+    slot_ld[3 * slot + 0] = alb.x * Ld.x;
+    slot_ld[3 * slot + 1] = alb.y * Ld.y;
+    slot_ld[3 * slot + 2] = alb.z * Ld.z;
+    slot_li[3 * slot + 0] = 0.f;
+    slot_li[3 * slot + 1] = 0.f;
+    slot_li[3 * slot + 2] = 0.f;
+  }
+  if (cq == nullptr) return;
+  // warp-aggregated append of the valid samples' queries
+  unsigned ball = __ballot_sync(0xffffffffu, valid);
+  if (ball == 0) return;
+  int lane = threadIdx.x & 31;
+  uint32_t base = 0;
+  if (lane == 0) base = atomicAdd(ccount, (uint32_t)__popc(ball));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (valid) {
+    uint32_t i = base + __popc(ball & ((1u << lane) - 1u));
+    float th = acosf(fminf(fmaxf(wo.z, -1.f), 1.f)) * 0.318309886183790672f;
+    float ph = atan2f(wo.y, wo.x) * 0.159154943091895336f;
+    if (ph < 0.f) ph = ph + 1.0f;
+    cq[6 * (size_t)i + 0] = x.x; cq[6 * (size_t)i + 1] = x.y; cq[6 * (size_t)i + 2] = x.z;
+    cq[6 * (size_t)i + 3] = th;  cq[6 * (size_t)i + 4] = ph;  cq[6 * (size_t)i + 5] = g;
+    calb[3 * (size_t)i + 0] = alb.x; calb[3 * (size_t)i + 1] = alb.y; calb[3 * (size_t)i + 2] = alb.z;
+    cidx[i] = (uint32_t)slot;
+  }
+}
+
+__global__ void k_compose(const float* __restrict__ slot_ld, const float* __restrict__ slot_li, int64_t n_pix,
+                          int spp, float* __restrict__ out) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_pix) return;
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+  for (int k = 0; k < spp; ++k) {
+    size_t s = 3 * ((size_t)p * spp + k);
+    a0 = a0 + (slot_ld[s + 0] + slot_li[s + 0]);
+    a1 = a1 + (slot_ld[s + 1] + slot_li[s + 1]);
+    a2 = a2 + (slot_ld[s + 2] + slot_li[s + 2]);
+  }
+  out[3 * p + 0] = a0 / (float)spp;
+  out[3 * p + 1] = a1 / (float)spp;
+  out[3 * p + 2] = a2 / (float)spp;
+}
+
+// -------------------------------------------------------------- path tracer
+template <int DT>
+__global__ void __launch_bounds__(128) k_path_samples(Vol V, DevLights L, CamF cam, float g, int spp, int k0, int kc,
+                                                      int max_bounces, int use_rr, uint64_t seed, int64_t n_items,
+                                                      float* __restrict__ slot_rad, uint32_t* err) {
+  int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= n_items) return;
+  int k = k0 + (int)(it % kc);
+  int64_t pix = it / kc;
+  int px = (int)(pix % cam.W), py = (int)(pix / cam.W);
+  Rng rng(seed, TAG_CAMERA, (uint64_t)pix, (uint32_t)k);
+  float b0[4]; rng.uni4(b0);
+  V3 o, d;
+  camera_ray(cam, px, py, b0[0], b0[1], &o, &d);
+  V3 rad = v3(0.f, 0.f, 0.f);
+  float beta0 = 1.f, beta1 = 1.f, beta2 = 1.f;
+  float t0, t1;
+  if (box_hit(o, d, &t0, &t1)) {
+    float t = t0;
+    for (int j = 1; j <= max_bounces; ++j) {
+      float th;
+      if (!delta_track<DT>(V, o, d, t, t1, rng, &th, err)) break;
+      V3 x = along(o, d, th);
+      float sig; V3 alb;
+      medium_at<DT>(V, x, &sig, &alb);
+      V3 Lr = v3(0.f, 0.f, 0.f);
+      for (int l = 0; l < L.n; ++l) {
+        V3 wl, E; float dist;
+        light_geom(L.l[l], x, &wl, &dist, &E);
+        float a0, a1, tend = 0.f;
+        if (box_hit(x, wl, &a0, &a1)) tend = mn(a1, dist);
+        float T = ratio_track<DT>(V, x, wl, tend, rng, err);
+        float ph = hg_eval(g, dot(d, wl));
+        Lr = v3(Lr.x + ph * T * E.x, Lr.y + ph * T * E.y, Lr.z + ph * T * E.z);
+      }
+      float c0 = beta0 * alb.x, c1 = beta1 * alb.y, c2 = beta2 * alb.z;
+      rad = v3(rad.x + c0 * Lr.x, rad.y + c1 * Lr.y, rad.z + c2 * Lr.z);
+      beta0 = c0; beta1 = c1; beta2 = c2;
+      if (j == max_bounces) break;
+      float w[4]; rng.uni4(w);
+      V3 nd = hg_sample(g, d, w[0], w[1]);
+      if (use_rr && j >= 3) {
+        float q = mx(beta0, mx(beta1, beta2));
+        if (q > 1.f) q = 1.f;
+        if (!(w[2] < q)) break;
+        beta0 = beta0 / q; beta1 = beta1 / q; beta2 = beta2 / q;
+      }
+      o = x; d = nd;
+      float a0, a1;
+      if (!box_hit(o, d, &a0, &a1)) break;
+      t = 0.f; t1 = a1;
+    }
+  }
+  slot_rad[3 * it + 0] = rad.x;
+  slot_rad[3 * it + 1] = rad.y;
+  slot_rad[3 * it + 2] = rad.z;
+}
+
+// acc[p] += r[p][k] for the chunk's samples in order; on the last chunk,
+// out = acc / spp.
+__global__ void k_path_accumulate(const float* __restrict__ slot_rad, int64_t n_pix, int kc, int first, int last,
+                                  int spp, float* __restrict__ acc, float* __restrict__ out) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_pix) return;
+  float a0 = first ? 0.f : acc[3 * p], a1 = first ? 0.f : acc[3 * p + 1], a2 = first ? 0.f : acc[3 * p + 2];
+  for (int k = 0; k < kc; ++k) {
+    size_t s = 3 * ((size_t)p * kc + k);
+    a0 = a0 + slot_rad[s]; a1 = a1 + slot_rad[s + 1]; a2 = a2 + slot_rad[s + 2];
+  }
+  if (last) {
+    out[3 * p] = a0 / (float)spp; out[3 * p + 1] = a1 / (float)spp; out[3 * p + 2] = a2 / (float)spp;
+  } else {
+    acc[3 * p] = a0; acc[3 * p + 1] = a1; acc[3 * p + 2] = a2;
+  }
+}
+
+// Camera frame in double on the host, rounded once to float.
+CamF make_cam(const pf_camera* c) {
+  double eye[3] = {c->eye[0], c->eye[1], c->eye[2]};
+  double f[3] = {(double)c->at[0] - eye[0], (double)c->at[1] - eye[1], (double)c->at[2] - eye[2]};
+  double up[3] = {c->up[0], c->up[1], c->up[2]};
+  double fn = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+  for (int i = 0; i < 3; ++i) f[i] /= fn;
+  double r[3] = {f[1] * up[2] - f[2] * up[1], f[2] * up[0] - f[0] * up[2], f[0] * up[1] - f[1] * up[0]};
+  double rn = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+  for (int i = 0; i < 3; ++i) r[i] /= rn;
+  double u[3] = {r[1] * f[2] - r[2] * f[1], r[2] * f[0] - r[0] * f[2], r[0] * f[1] - r[1] * f[0]};
+  double th = std::tan(0.5 * (double)c->fovy_deg * M_PI / 180.0);
+  CamF o;
+  for (int i = 0; i < 3; ++i) { o.eye[i] = (float)eye[i]; o.f[i] = (float)f[i]; o.r[i] = (float)r[i]; o.u[i] = (float)u[i]; }
+  o.sy = (float)th;
+  o.sx = (float)(th * (double)c->width / (double)c->height);
+  o.W = c->width; o.H = c->height;
+  return o;
+}
+
+}  // namespace
+
+static pf_status check_cam(pf_ctx* ctx, const pf_camera* cam, int spp) {
+  if (!cam || cam->width <= 0 || cam->height <= 0 || spp <= 0 || spp > (1 << 24))
+    return pf_fail(ctx, PF_ERR_INVALID_ARG, "camera size and spp must be positive (spp < 2^24)");
+  if (!(cam->fovy_deg > 0.f && cam->fovy_deg < 180.f))
+    return pf_fail(ctx, PF_ERR_INVALID_ARG, "fovy_deg must lie in (0, 180)");
+  return PF_OK;
+}
+
+extern "C" pf_status pf_render_neural(pf_ctx* ctx, const pf_volume* vol, const pf_light* lights, int n_lights,
+                                      float g, const pf_camera* cam, int spp, float step_vox, uint64_t seed,
+                                      const pf_field* field, float* out_rgb_dev) {
+  if (!ctx) return PF_ERR_INVALID_ARG;
+  DeviceGuard dg(ctx->device);
+  PF_TRY(pf_check_volume(ctx, vol));
+  PF_TRY(pf_check_lights(ctx, lights, n_lights));
+  PF_TRY(check_cam(ctx, cam, spp));
+  if (!out_rgb_dev) return pf_fail(ctx, PF_ERR_INVALID_ARG, "out_rgb_dev is NULL");
+  if (!(step_vox >= 0.f) || !(g > -1.f && g < 1.f)) return pf_fail(ctx, PF_ERR_INVALID_ARG, "need step_vox >= 0 and |g| < 1");
+  if (field && field->ctx != ctx) return pf_fail(ctx, PF_ERR_INVALID_ARG, "field belongs to another context");
+  float maj;
+  PF_TRY(pf_majorant_impl(ctx, vol, &maj));
+  int64_t n_pix = (int64_t)cam->width * cam->height;
+  int64_t n_slots = n_pix * spp;
+  if (n_slots > (int64_t)0xFFFFFFFFll) return pf_fail(ctx, PF_ERR_INVALID_ARG, "width*height*spp must be < 2^32");
+  float *ld, *li, *cq = nullptr, *calb = nullptr;
+  uint32_t *cidx = nullptr, *ccount = nullptr;
+  PF_TRY(pf_scratch(ctx, WS_SLOT_LD, n_slots * 3 * sizeof(float), (void**)&ld));
+  PF_TRY(pf_scratch(ctx, WS_SLOT_LI, n_slots * 3 * sizeof(float), (void**)&li));
+  if (field) {
+    PF_TRY(pf_scratch(ctx, WS_COMPACT_Q, n_slots * 6 * sizeof(float), (void**)&cq));
+    PF_TRY(pf_scratch(ctx, WS_SLOT_ALB, n_slots * 3 * sizeof(float), (void**)&calb));
+    PF_TRY(pf_scratch(ctx, WS_COMPACT_IDX, n_slots * sizeof(uint32_t), (void**)&cidx));
+    PF_TRY(pf_scratch(ctx, WS_MISC, 256, (void**)&ccount));
+    PF_CUDA(ctx, cudaMemsetAsync(ccount, 0, sizeof(uint32_t), ctx->stream));
+  }
+  Vol V = pf_make_vol(vol, maj);
+  DevLights L = pf_make_lights(lights, n_lights);
+  CamF C = make_cam(cam);
+  int nmax = std::max(vol->nx, std::max(vol->ny, vol->nz));
+  float h = step_vox > 0.f ? step_vox / (float)nmax : 0.f;
+  dim3 blk(128), grd((unsigned)((n_slots + 127) / 128));
+  bool march = step_vox > 0.f;
+#define LAUNCH_CS(DT)                                                                                              \
+  if (march) k_camera_samples<DT, true><<<grd, blk, 0, ctx->stream>>>(V, L, C, g, spp, h, seed, n_slots, ld, li, cq, \
+                                                                      calb, cidx, ccount, ctx->err_dev);             \
+  else k_camera_samples<DT, false><<<grd, blk, 0, ctx->stream>>>(V, L, C, g, spp, h, seed, n_slots, ld, li, cq, calb, \
+                                                                 cidx, ccount, ctx->err_dev);
+  if (vol->dtype == PF_F32) { LAUNCH_CS(0) } else if (vol->dtype == PF_F16) { LAUNCH_CS(1) } else { LAUNCH_CS(2) }
+#undef LAUNCH_CS
+  PF_CUDA(ctx, cudaGetLastError());
+  if (field) {
+    // The number of valid samples is only known on the device; the field pass
+    // reads it from there and covers the worst case n_slots.
+    PF_TRY(pf_field_forward_impl(ctx, field, cq, n_slots, ccount, nullptr, cidx, calb, li));
+  }
+  k_compose<<<(unsigned)((n_pix + 127) / 128), 128, 0, ctx->stream>>>(ld, li, n_pix, spp, out_rgb_dev);
+  PF_CUDA(ctx, cudaGetLastError());
+  return PF_OK;
+}
+
+extern "C" pf_status pf_render_pathtraced(pf_ctx* ctx, const pf_volume* vol, const pf_light* lights, int n_lights,
+                                          float g, const pf_camera* cam, int spp, int max_bounces, uint64_t seed,
+                                          int use_rr, float* out_rgb_dev) {
+  if (!ctx) return PF_ERR_INVALID_ARG;
+  DeviceGuard dg(ctx->device);
+  PF_TRY(pf_check_volume(ctx, vol));
+  PF_TRY(pf_check_lights(ctx, lights, n_lights));
+  PF_TRY(check_cam(ctx, cam, spp));
+  if (!out_rgb_dev) return pf_fail(ctx, PF_ERR_INVALID_ARG, "out_rgb_dev is NULL");
+  if (max_bounces < 1 || max_bounces > 1024) return pf_fail(ctx, PF_ERR_INVALID_ARG, "max_bounces must be in [1, 1024]");
+  if (!(g > -1.f && g < 1.f)) return pf_fail(ctx, PF_ERR_INVALID_ARG, "|g| must be < 1");
+  float maj;
+  PF_TRY(pf_majorant_impl(ctx, vol, &maj));
+  int64_t n_pix = (int64_t)cam->width * cam->height;
+  // samples per chunk: keep the per-sample scratch within 2^26 slots
+  int64_t kc = std::max<int64_t>(1, std::min<int64_t>(spp, ((int64_t)1 << 26) / n_pix));
+  float *rad, *acc;
+  PF_TRY(pf_scratch(ctx, WS_SLOT_LD, (size_t)(n_pix * kc * 3) * sizeof(float), (void**)&rad));
+  PF_TRY(pf_scratch(ctx, WS_SLOT_ALB, (size_t)(n_pix * 3) * sizeof(float), (void**)&acc));
+  Vol V = pf_make_vol(vol, maj);
+  DevLights L = pf_make_lights(lights, n_lights);
+  CamF C = make_cam(cam);
+  for (int k0 = 0; k0 < spp; k0 += (int)kc) {
+    int kn = (int)std::min<int64_t>(kc, spp - k0);
+    int64_t n_items = n_pix * kn;
+    dim3 grd((unsigned)((n_items + 127) / 128));
+    if (vol->dtype == PF_F32)
+      k_path_samples<0><<<grd, 128, 0, ctx->stream>>>(V, L, C, g, spp, k0, kn, max_bounces, use_rr, seed, n_items, rad, ctx->err_dev);
+    else if (vol->dtype == PF_F16)
+      k_path_samples<1><<<grd, 128, 0, ctx->stream>>>(V, L, C, g, spp, k0, kn, max_bounces, use_rr, seed, n_items, rad, ctx->err_dev);
+    else
+      k_path_samples<2><<<grd, 128, 0, ctx->stream>>>(V, L, C, g, spp, k0, kn, max_bounces, use_rr, seed, n_items, rad, ctx->err_dev);
+    PF_CUDA(ctx, cudaGetLastError());
+    k_path_accumulate<<<(unsigned)((n_pix + 127) / 128), 128, 0, ctx->stream>>>(rad, n_pix, kn, k0 == 0, k0 + kn >= spp,
+                                                                                spp, acc, out_rgb_dev);
+    PF_CUDA(ctx, cudaGetLastError());
+  }
+  return PF_OK;
+}

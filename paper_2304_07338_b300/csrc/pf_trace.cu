@@ -1,0 +1,371 @@
+// Multi-phase photon tracing (Algorithm 1, Sec. 3.2) and the photon caches
+// the training-sample generator reads (Sec. 3.3).
+//
+// Pipeline (all stream-ordered, no host round trip except two scalars):
+//   k_trace_photons  one thread per photon; emission, delta tracking, HG
+//                    scattering, Russian roulette; record j (j >= 2) goes to
+//                    the photon's own slot p*(max_bounces-1) + j-2 -- so no
+//                    global append counter -- and bumps counts[key];
+//   scan(counts)     -> CSR offsets;
+//   k_scatter        slot records -> CSR order (position within a key taken
+//                    by an atomic cursor);
+//   k_key_flux       per-key power sums in FP64 -> float;
+//   k_cell_sigma     mean sigma_t over the voxel centres of every cache cell;
+//   k_occupancy + scan + k_occupied_list -> ascending occupied cells.
+// Compiled with -fmad=false: see pf_device.cuh.
+#include "pf_internal.h"
+#include "pf_device.cuh"
+#include <algorithm>
+#include <cmath>
+
+using namespace pfd;
+
+namespace {
+
+struct TraceArgs {
+  Vol V;
+  DevLights L;
+  float g_set[16];
+  int n_g, max_bounces, res, use_rr;
+  uint64_t N, seed, n_photons;
+};
+
+template <int DT>
+__global__ void __launch_bounds__(128) k_trace_photons(TraceArgs A, float4* __restrict__ slots,
+                                                       uint8_t* __restrict__ nrec, uint32_t* __restrict__ counts,
+                                                       double* __restrict__ tally, uint32_t* err) {
+  __shared__ double s_tally[15];
+  if (threadIdx.x < 15) s_tally[threadIdx.x] = 0.0;
+  __syncthreads();
+  uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double t_em[3] = {0, 0, 0}, t_es[3] = {0, 0, 0}, t_ab[3] = {0, 0, 0}, t_tr[3] = {0, 0, 0}, t_rr[3] = {0, 0, 0};
+  if (p < A.n_photons) {
+    const Vol& V = A.V;
+    int l = (int)(p / ((uint64_t)A.n_g * A.N));
+    int gi = (int)((p / A.N) % (uint64_t)A.n_g);
+    const DevLight& Lt = A.L.l[l];
+    float g = A.g_set[gi];
+    int S = A.max_bounces - 1 > 0 ? A.max_bounces - 1 : 1;
+    float4* my = slots + 2 * (size_t)p * S;
+    Rng rng(A.seed, TAG_PHOTON, p, 0);
+    float u[4]; rng.uni4(u);
+    V3 o, d;
+    float P0, P1, P2;
+    if (Lt.kind == 0) {
+      V3 v = normalize(v3(Lt.v[0], Lt.v[1], Lt.v[2]));
+      V3 e1, e2; onb(v, &e1, &e2);
+      float side = 1.7320508075688772f;
+      float a = (u[0] - 0.5f) * side, b = (u[1] - 0.5f) * side;
+      o = v3(0.5f + v.x + a * e1.x + b * e2.x, 0.5f + v.y + a * e1.y + b * e2.y, 0.5f + v.z + a * e1.z + b * e2.z);
+      d = v3(-v.x, -v.y, -v.z);
+      P0 = Lt.rgb[0] * 3.0f / (float)A.N; P1 = Lt.rgb[1] * 3.0f / (float)A.N; P2 = Lt.rgb[2] * 3.0f / (float)A.N;
+    } else {
+      float z = 1.0f - 2.0f * u[0];
+      float r = sqrtf(mx(0.0f, 1.0f - z * z));
+      float sp, cp; own_sincos2pif(u[1], &sp, &cp);
+      d = v3(r * cp, r * sp, z);
+      o = v3(Lt.v[0], Lt.v[1], Lt.v[2]);
+      const float fpi = 12.566370614359172f;
+      P0 = Lt.rgb[0] * fpi / (float)A.N; P1 = Lt.rgb[1] * fpi / (float)A.N; P2 = Lt.rgb[2] * fpi / (float)A.N;
+    }
+    t_em[0] = P0; t_em[1] = P1; t_em[2] = P2;
+    float pe_max = mx(P0, mx(P1, P2));
+    int n = 0, j = 0;
+    float t0 = 0.f, t1 = 0.f;
+    bool alive = true;
+    bool inside = box_hit(o, d, &t0, &t1);
+    float t = t0;
+    const uint32_t R = (uint32_t)A.res;
+    while (alive && inside) {
+      float th;
+      if (!delta_track<DT>(V, o, d, t, t1, rng, &th, err)) break;
+      V3 x = along(o, d, th);
+      j = j + 1;
+      float sig; V3 alb;
+      medium_at<DT>(V, x, &sig, &alb);
+      if (j >= 2) {
+        int bx = (int)floorf(x.x * (float)A.res), by = (int)floorf(x.y * (float)A.res), bz = (int)floorf(x.z * (float)A.res);
+        bx = min(max(bx, 0), A.res - 1); by = min(max(by, 0), A.res - 1); bz = min(max(bz, 0), A.res - 1);
+        uint32_t bin = (uint32_t)bx + R * ((uint32_t)by + R * (uint32_t)bz);
+        uint32_t key = (uint32_t)(l * A.n_g + gi) * (R * R * R) + bin;
+        my[2 * n + 0] = make_float4(__uint_as_float(key), __uint_as_float((uint32_t)(p << 4) | (uint32_t)n), d.x, d.y);
+        my[2 * n + 1] = make_float4(d.z, P0, P1, P2);
+        atomicAdd(&counts[key], 1u);
+        n = n + 1;
+      }
+      float Q0 = P0 * alb.x, Q1 = P1 * alb.y, Q2 = P2 * alb.z;
+      t_ab[0] += (double)P0 - (double)Q0; t_ab[1] += (double)P1 - (double)Q1; t_ab[2] += (double)P2 - (double)Q2;
+      P0 = Q0; P1 = Q1; P2 = Q2;
+      if (j == A.max_bounces) {
+        t_tr[0] += P0; t_tr[1] += P1; t_tr[2] += P2;
+        alive = false;
+        break;
+      }
+      float w[4]; rng.uni4(w);
+      V3 nd = hg_sample(g, d, w[0], w[1]);
+      if (A.use_rr && j >= 3) {
+        float q = mx(P0, mx(P1, P2)) / pe_max;
+        if (q > 1.0f) q = 1.0f;
+        if (!(w[2] < q)) {
+          t_rr[0] += P0; t_rr[1] += P1; t_rr[2] += P2;
+          alive = false;
+          break;
+        }
+        float n0 = P0 / q, n1 = P1 / q, n2 = P2 / q;
+        t_rr[0] -= (double)n0 - (double)P0; t_rr[1] -= (double)n1 - (double)P1; t_rr[2] -= (double)n2 - (double)P2;
+        P0 = n0; P1 = n1; P2 = n2;
+      }
+      o = x; d = nd;
+      float a0, a1;
+      if (!box_hit(o, d, &a0, &a1)) break;
+      t = 0.0f; t1 = a1;
+    }
+    if (alive) { t_es[0] += P0; t_es[1] += P1; t_es[2] += P2; }
+    nrec[p] = (uint8_t)n;
+  }
+  // block reduction of the FP64 tallies (warp shuffles, then shared atomics)
+  double* parts[5] = {t_em, t_es, t_ab, t_tr, t_rr};
+#pragma unroll
+  for (int a = 0; a < 5; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double v = parts[a][c];
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      if ((threadIdx.x & 31) == 0) atomicAdd(&s_tally[3 * a + c], v);
+    }
+  __syncthreads();
+  if (threadIdx.x < 15) atomicAdd(&tally[threadIdx.x], s_tally[threadIdx.x]);
+}
+
+// Move slot records into CSR order.
+__global__ void k_scatter(const float4* __restrict__ slots, const uint8_t* __restrict__ nrec, uint64_t n_photons, int S,
+                          const uint64_t* __restrict__ offsets, uint32_t* __restrict__ cursor, float4* __restrict__ recs) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t p = i / (uint64_t)S;
+  int s = (int)(i % (uint64_t)S);
+  if (p >= n_photons || s >= (int)nrec[p]) return;
+  float4 a = slots[2 * i], b = slots[2 * i + 1];
+  uint32_t key = __float_as_uint(a.x);
+  uint64_t pos = offsets[key] + atomicAdd(&cursor[key], 1u);
+  recs[2 * pos] = a;
+  recs[2 * pos + 1] = b;
+}
+
+// Per-key power sums: one warp per key, FP64 lanes, rounded once.
+__global__ void k_key_flux(const float4* __restrict__ recs, const uint64_t* __restrict__ offsets, int64_t n_keys,
+                           float* __restrict__ flux) {
+  int64_t key = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (key >= n_keys) return;
+  double s0 = 0, s1 = 0, s2 = 0;
+  for (uint64_t n = offsets[key] + lane; n < offsets[key + 1]; n += 32) {
+    float4 b = recs[2 * n + 1];
+    s0 += b.y; s1 += b.z; s2 += b.w;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    s0 += __shfl_down_sync(0xffffffffu, s0, off);
+    s1 += __shfl_down_sync(0xffffffffu, s1, off);
+    s2 += __shfl_down_sync(0xffffffffu, s2, off);
+  }
+  if (lane == 0) { flux[3 * key] = (float)s0; flux[3 * key + 1] = (float)s1; flux[3 * key + 2] = (float)s2; }
+}
+
+// First voxel index whose centre lies in cache cell c (axis of n voxels, res cells).
+__device__ __forceinline__ int cell_lo(int c, int n, int res) {
+  long long a = 2LL * n * c - res;
+  if (a <= 0) return 0;
+  return (int)((a + 2LL * res - 1) / (2LL * res));
+}
+
+template <int DT>
+__global__ void k_cell_sigma(Vol V, int res, float* __restrict__ out) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t nc = (int64_t)res * res * res;
+  if (c >= nc) return;
+  int cx = (int)(c % res), cy = (int)((c / res) % res), cz = (int)(c / ((int64_t)res * res));
+  int x0 = cell_lo(cx, V.nx, res), x1 = cx + 1 < res ? cell_lo(cx + 1, V.nx, res) : V.nx;
+  int y0 = cell_lo(cy, V.ny, res), y1 = cy + 1 < res ? cell_lo(cy + 1, V.ny, res) : V.ny;
+  int z0 = cell_lo(cz, V.nz, res), z1 = cz + 1 < res ? cell_lo(cz + 1, V.nz, res) : V.nz;
+  float sum = 0.f;
+  int cnt = 0;
+  for (int k = z0; k < z1; ++k)
+    for (int j = y0; j < y1; ++j)
+      for (int i = x0; i < x1; ++i) {
+        sum += V.sigma_scale * tf_alpha(V, voxel<DT>(V, i, j, k));
+        ++cnt;
+      }
+  if (cnt > 0) out[c] = sum / (float)cnt;
+  else out[c] = sigma_at<DT>(V, v3((cx + 0.5f) / res, (cy + 0.5f) / res, (cz + 0.5f) / res));
+}
+
+__global__ void k_occupancy(const uint32_t* __restrict__ counts, const float* __restrict__ csig, int64_t nc, int nlg,
+                            uint32_t* __restrict__ flag) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  uint32_t tot = 0;
+  for (int a = 0; a < nlg; ++a) tot += counts[(int64_t)a * nc + c];
+  flag[c] = (tot > 0 && csig[c] > 0.f) ? 1u : 0u;
+}
+
+__global__ void k_occupied_list(const uint32_t* __restrict__ flag, const uint64_t* __restrict__ pos, int64_t nc,
+                                uint32_t* __restrict__ occ) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc || !flag[c]) return;
+  occ[pos[c]] = (uint32_t)c;
+}
+
+}  // namespace
+
+static void free_cache(pf_cache* c) {
+  if (!c) return;
+  cudaFree(c->counts); cudaFree(c->offsets); cudaFree(c->recs); cudaFree(c->flux);
+  cudaFree(c->occupied); cudaFree(c->cell_sigma);
+  delete c;
+}
+
+extern "C" pf_status pf_build_photon_cache(pf_ctx* ctx, const pf_volume* vol, const pf_light* lights, int n_lights,
+                                           const float* g_set, int n_g, uint64_t N, int max_bounces, int res,
+                                           uint64_t seed, int use_rr, pf_cache** out) {
+  if (!ctx) return PF_ERR_INVALID_ARG;
+  DeviceGuard dg(ctx->device);
+  if (!out) return pf_fail(ctx, PF_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  PF_TRY(pf_check_volume(ctx, vol));
+  PF_TRY(pf_check_lights(ctx, lights, n_lights));
+  if (!g_set || n_g < 1 || n_g > 16) return pf_fail(ctx, PF_ERR_INVALID_ARG, "n_g must be in [1, 16]");
+  for (int i = 0; i < n_g; ++i)
+    if (!(g_set[i] > -1.f && g_set[i] < 1.f)) return pf_fail(ctx, PF_ERR_INVALID_ARG, "g values must lie in (-1, 1)");
+  if (max_bounces < 2 || max_bounces > 16) return pf_fail(ctx, PF_ERR_INVALID_ARG, "max_bounces must be in [2, 16]");
+  if (res < 1 || res > 256 || (res & (res - 1))) return pf_fail(ctx, PF_ERR_INVALID_ARG, "cache_res must be a power of two in [1, 256]");
+  uint64_t P = (uint64_t)n_lights * (uint64_t)n_g * N;
+  if (N == 0 || P >= (1ull << 28)) return pf_fail(ctx, PF_ERR_INVALID_ARG, "total photon count must be in [1, 2^28)");
+  int64_t nc = (int64_t)res * res * res;
+  int64_t n_keys = (int64_t)n_lights * n_g * nc;
+  if (n_keys >= (1ll << 32)) return pf_fail(ctx, PF_ERR_INVALID_ARG, "too many cache keys");
+  float maj;
+  PF_TRY(pf_majorant_impl(ctx, vol, &maj));
+
+  pf_cache* c = new pf_cache();
+  c->ctx = ctx; c->res = res; c->n_lights = n_lights; c->n_g = n_g; c->max_bounces = max_bounces;
+  c->n_photons = (int64_t)P; c->n_keys = n_keys;
+  for (int i = 0; i < n_g; ++i) c->g_set[i] = g_set[i];
+  int S = max_bounces - 1;
+  auto fail = [&](pf_status s) { free_cache(c); return s; };
+  float4* slots = nullptr;
+  uint8_t* nrec = nullptr;
+  uint32_t* cursor = nullptr;
+  double* tally_dev = nullptr;
+#define CK(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { cudaFree(slots); cudaFree(nrec); cudaFree(cursor); cudaFree(tally_dev); \
+  return fail(pf_cuda_check(ctx, e_, #call)); } } while (0)
+  CK(cudaMalloc(&slots, (size_t)P * S * 2 * sizeof(float4)));
+  CK(cudaMalloc(&nrec, (size_t)P));
+  CK(cudaMalloc(&c->counts, (size_t)n_keys * sizeof(uint32_t)));
+  CK(cudaMalloc(&cursor, (size_t)std::max<int64_t>(n_keys, nc) * sizeof(uint32_t)));
+  CK(cudaMalloc(&c->offsets, (size_t)(n_keys + 1) * sizeof(uint64_t)));
+  CK(cudaMalloc(&tally_dev, 15 * sizeof(double)));
+  CK(cudaMemsetAsync(c->counts, 0, (size_t)n_keys * sizeof(uint32_t), ctx->stream));
+  CK(cudaMemsetAsync(tally_dev, 0, 15 * sizeof(double), ctx->stream));
+
+  TraceArgs A;
+  A.V = pf_make_vol(vol, maj);
+  A.L = pf_make_lights(lights, n_lights);
+  for (int i = 0; i < 16; ++i) A.g_set[i] = i < n_g ? g_set[i] : 0.f;
+  A.n_g = n_g; A.max_bounces = max_bounces; A.res = res; A.use_rr = use_rr; A.N = N; A.seed = seed; A.n_photons = P;
+  unsigned grd = (unsigned)((P + 127) / 128);
+  if (vol->dtype == PF_F32) k_trace_photons<0><<<grd, 128, 0, ctx->stream>>>(A, slots, nrec, c->counts, tally_dev, ctx->err_dev);
+  else if (vol->dtype == PF_F16) k_trace_photons<1><<<grd, 128, 0, ctx->stream>>>(A, slots, nrec, c->counts, tally_dev, ctx->err_dev);
+  else k_trace_photons<2><<<grd, 128, 0, ctx->stream>>>(A, slots, nrec, c->counts, tally_dev, ctx->err_dev);
+  CK(cudaGetLastError());
+  pf_status st = pf_scan_u32(ctx, c->counts, c->offsets, n_keys);
+  if (st != PF_OK) { cudaFree(slots); cudaFree(nrec); cudaFree(cursor); cudaFree(tally_dev); return fail(st); }
+  uint64_t n_rec = 0;
+  CK(cudaMemcpyAsync(&n_rec, c->offsets + n_keys, sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(c->tally, tally_dev, 15 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  c->n_records = (int64_t)n_rec;
+  CK(cudaMalloc(&c->recs, (size_t)std::max<uint64_t>(n_rec, 1) * 2 * sizeof(float4)));
+  CK(cudaMemsetAsync(cursor, 0, (size_t)n_keys * sizeof(uint32_t), ctx->stream));
+  uint64_t n_slots = P * (uint64_t)S;
+  k_scatter<<<(unsigned)((n_slots + 255) / 256), 256, 0, ctx->stream>>>(slots, nrec, P, S, c->offsets, cursor, c->recs);
+  CK(cudaGetLastError());
+  CK(cudaMalloc(&c->flux, (size_t)n_keys * 3 * sizeof(float)));
+  k_key_flux<<<(unsigned)((n_keys * 32 + 255) / 256), 256, 0, ctx->stream>>>(c->recs, c->offsets, n_keys, c->flux);
+  CK(cudaGetLastError());
+  CK(cudaMalloc(&c->cell_sigma, (size_t)nc * sizeof(float)));
+  unsigned gc = (unsigned)((nc + 127) / 128);
+  if (vol->dtype == PF_F32) k_cell_sigma<0><<<gc, 128, 0, ctx->stream>>>(A.V, res, c->cell_sigma);
+  else if (vol->dtype == PF_F16) k_cell_sigma<1><<<gc, 128, 0, ctx->stream>>>(A.V, res, c->cell_sigma);
+  else k_cell_sigma<2><<<gc, 128, 0, ctx->stream>>>(A.V, res, c->cell_sigma);
+  CK(cudaGetLastError());
+  // occupancy flags reuse `cursor`; their exclusive scan gets its own buffer
+  uint64_t* opos = nullptr;
+  CK(cudaMalloc(&opos, (size_t)(nc + 1) * sizeof(uint64_t)));
+  cudaFree(slots);
+  slots = (float4*)opos;     // freed with the other temporaries below
+  k_occupancy<<<gc, 128, 0, ctx->stream>>>(c->counts, c->cell_sigma, nc, n_lights * n_g, cursor);
+  CK(cudaGetLastError());
+  st = pf_scan_u32(ctx, cursor, opos, nc);
+  if (st != PF_OK) { cudaFree(slots); cudaFree(nrec); cudaFree(cursor); cudaFree(tally_dev); return fail(st); }
+  uint64_t n_occ = 0;
+  CK(cudaMemcpyAsync(&n_occ, opos + nc, sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  c->n_occupied = (int64_t)n_occ;
+  CK(cudaMalloc(&c->occupied, (size_t)std::max<uint64_t>(n_occ, 1) * sizeof(uint32_t)));
+  k_occupied_list<<<gc, 128, 0, ctx->stream>>>(cursor, opos, nc, c->occupied);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->stream));
+#undef CK
+  cudaFree(slots); cudaFree(nrec); cudaFree(cursor); cudaFree(tally_dev);
+  pf_status es = pf_check_error_word(ctx);
+  if (es != PF_OK) { free_cache(c); return es; }
+  *out = c;
+  return PF_OK;
+}
+
+extern "C" pf_status pf_cache_info(pf_ctx* ctx, const pf_cache* c, pf_cache_info_t* out) {
+  if (!ctx || !c || !out) return PF_ERR_INVALID_ARG;
+  out->n_photons = c->n_photons; out->n_records = c->n_records; out->n_keys = c->n_keys;
+  out->n_occupied = c->n_occupied; out->res = c->res; out->n_lights = c->n_lights; out->n_g = c->n_g;
+  out->max_bounces = c->max_bounces;
+  for (int i = 0; i < 15; ++i) out->tally[i] = c->tally[i];
+  return PF_OK;
+}
+
+namespace {
+__global__ void k_export_recs(const float4* __restrict__ recs, int64_t n, uint32_t* key, uint32_t* id, float* dir, float* phi) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float4 a = recs[2 * i], b = recs[2 * i + 1];
+  if (key) key[i] = __float_as_uint(a.x);
+  if (id) id[i] = __float_as_uint(a.y);
+  if (dir) { dir[3 * i] = a.z; dir[3 * i + 1] = a.w; dir[3 * i + 2] = b.x; }
+  if (phi) { phi[3 * i] = b.y; phi[3 * i + 1] = b.z; phi[3 * i + 2] = b.w; }
+}
+}  // namespace
+
+extern "C" pf_status pf_cache_export(pf_ctx* ctx, const pf_cache* c, uint32_t* counts_dev, float* flux_dev,
+                                     uint32_t* rec_key_dev, uint32_t* rec_id_dev, float* rec_dir_dev,
+                                     float* rec_phi_dev, uint32_t* occupied_dev, float* cell_sigma_dev) {
+  if (!ctx || !c) return PF_ERR_INVALID_ARG;
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = ctx->stream;
+  if (counts_dev) PF_CUDA(ctx, cudaMemcpyAsync(counts_dev, c->counts, c->n_keys * 4, cudaMemcpyDeviceToDevice, s));
+  if (flux_dev) PF_CUDA(ctx, cudaMemcpyAsync(flux_dev, c->flux, c->n_keys * 12, cudaMemcpyDeviceToDevice, s));
+  if (occupied_dev && c->n_occupied)
+    PF_CUDA(ctx, cudaMemcpyAsync(occupied_dev, c->occupied, c->n_occupied * 4, cudaMemcpyDeviceToDevice, s));
+  if (cell_sigma_dev)
+    PF_CUDA(ctx, cudaMemcpyAsync(cell_sigma_dev, c->cell_sigma, (size_t)c->res * c->res * c->res * 4, cudaMemcpyDeviceToDevice, s));
+  if ((rec_key_dev || rec_id_dev || rec_dir_dev || rec_phi_dev) && c->n_records) {
+    k_export_recs<<<(unsigned)((c->n_records + 255) / 256), 256, 0, s>>>(c->recs, c->n_records, rec_key_dev, rec_id_dev,
+                                                                           rec_dir_dev, rec_phi_dev);
+    PF_CUDA(ctx, cudaGetLastError());
+  }
+  return PF_OK;
+}
+
+extern "C" pf_status pf_cache_free(pf_cache* c) {
+  if (!c) return PF_OK;
+  DeviceGuard dg(c->ctx ? c->ctx->device : 0);
+  free_cache(c);
+  return PF_OK;
+}

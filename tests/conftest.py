@@ -18,3 +18,15 @@ def orc():
     import oracle
     oracle.lib()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def pf_ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2304_07338_b300 import api, build
+    build.build()
+    ctx = api.Context(0)
+    yield ctx
+    ctx.close()

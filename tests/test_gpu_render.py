@@ -1,0 +1,125 @@
+"""GPU parity of the renderers against the oracle (Algorithm 2 and the
+path-tracing baseline), through the C ABI.
+
+  * ray-marched neural renderer, field off, plain-method scene at full size
+    (64^3 blobs, 128^2 x 4 spp): per-pixel relative error <= 1e-4 against the
+    FP64 oracle (error = |a-b| / max(|b|, 1e-3 max|b|));
+  * the same with the float32 field on: the field's input position inherits
+    the marcher's float32 rounding (~1e-7) and the 12-frequency encoding
+    multiplies it by up to 2^11 pi, so the tolerance is derived in the design doc;
+  * tracking renderer (delta + ratio tracking), field off, and the path
+    tracer: float32 arithmetic identical to the oracle's float32
+    instantiation, so pixels agree to float rounding of the final sums;
+  * edge cases: a camera that misses the box, one pixel, one sample.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2304_07338_b300 import api, inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel_err(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    den = np.maximum(np.abs(b), 1e-3 * np.abs(b).max())
+    return np.abs(a - b) / den
+
+
+def test_march_direct_matches_oracle_full_size(pf_ctx, orc):
+    sc = I.scene_small()
+    vol = api.Volume.from_inputs(sc.volume)
+    img = api.render_neural(pf_ctx, vol, sc.lights, sc.g, sc.camera, sc.spp, 0.5, seed=7)
+    pf_ctx.sync()
+    ref = orc.render_neural(sc.volume, sc.lights, sc.g, sc.camera, sc.spp, 0.5, 7)
+    err = _rel_err(img.cpu().numpy(), ref)
+    assert ref.max() > 0
+    assert err.max() <= 1e-4, err.max()
+
+
+def test_march_with_f32_field(pf_ctx, orc):
+    from oracle import field as F
+    sc = I.scene_small(64, 64, 64, 4)
+    vol = api.Volume.from_inputs(sc.volume)
+    fld = api.Field(pf_ctx, 12, 64, 3, "f32", 5.0, seed=3)
+    w = fld.get_weights().cpu().numpy()
+    desc = F.FieldDesc(12, 64, 3, F.PREC_F32, 5.0, 3)
+    assert np.array_equal(w, F.init_weights(desc))           # seeded init is bit-identical
+    img = api.render_neural(pf_ctx, vol, sc.lights, sc.g, sc.camera, sc.spp, 0.5, seed=5, field=fld)
+    pf_ctx.sync()
+    ref = orc.render_neural(sc.volume, sc.lights, sc.g, sc.camera, sc.spp, 0.5, 5, weights=w.astype(np.float64), desc=desc)
+    err = _rel_err(img.cpu().numpy(), ref)
+    assert np.median(err) < 1e-4
+    assert err.max() <= 5e-3, err.max()
+
+
+def test_tracking_direct_matches_float_oracle(pf_ctx, orc):
+    sc = I.scene_judge(32, 32, 24, 8)
+    vol = api.Volume.from_inputs(sc.volume)
+    for g in (0.0, 0.5):
+        img = api.render_neural(pf_ctx, vol, sc.lights, g, sc.camera, sc.spp, 0.0, seed=3)
+        pf_ctx.sync()
+        ref = orc.render_neural(sc.volume, sc.lights, g, sc.camera, sc.spp, 0.0, 3, fp32=True)
+        err = _rel_err(img.cpu().numpy(), ref)
+        assert err.max() <= 2e-6, (g, err.max())
+
+
+def test_path_tracer_matches_float_oracle(pf_ctx, orc):
+    sc = I.scene_judge(32, 24, 20, 6)
+    vol = api.Volume.from_inputs(sc.volume)
+    img = api.render_pathtraced(pf_ctx, vol, sc.lights, -0.5, sc.camera, sc.spp, 16, seed=11)
+    pf_ctx.sync()
+    ref = orc.path_trace(sc.volume, sc.lights, -0.5, sc.camera, sc.spp, 16, seed=11, fp32=True)
+    a = img.cpu().numpy()
+    assert ref.max() > 0
+    # same float operations in the same order: identical bits per pixel
+    assert np.array_equal(a.astype(np.float32), ref.astype(np.float32)), _rel_err(a, ref).max()
+
+
+def test_path_tracer_u8_and_f16_volumes(pf_ctx, orc):
+    sc = I.scene_judge(24, 16, 16, 4)
+    for dt in (np.uint8, np.float16):
+        data = sc.volume.data
+        data = (np.round(data * 255).astype(np.uint8) if dt == np.uint8 else data.astype(np.float16))
+        v = I.Volume(data, 20.0, 0.95, I.tf_piecewise_rgba(16))
+        vol = api.Volume.from_inputs(v)
+        img = api.render_pathtraced(pf_ctx, vol, sc.lights, 0.3, sc.camera, sc.spp, 16, seed=2)
+        pf_ctx.sync()
+        ref = orc.path_trace(v, sc.lights, 0.3, sc.camera, sc.spp, 16, seed=2, fp32=True)
+        assert np.array_equal(img.cpu().numpy().astype(np.float32), ref.astype(np.float32))
+
+
+def test_edge_cases(pf_ctx, orc):
+    sc = I.scene_small(16, 1, 1, 1)
+    vol = api.Volume.from_inputs(sc.volume)
+    # camera looking away from the box: black image
+    cam = I.Camera((0.5, 0.5, 3.0), (0.5, 0.5, 6.0), (0, 1, 0), 30.0, 5, 3)
+    img = api.render_neural(pf_ctx, vol, sc.lights, 0.0, cam, 2, 0.5, seed=1)
+    pt = api.render_pathtraced(pf_ctx, vol, sc.lights, 0.0, cam, 2, 4, seed=1)
+    pf_ctx.sync()
+    assert float(img.abs().max()) == 0.0 and float(pt.abs().max()) == 0.0
+    # one pixel, one sample
+    one = api.render_neural(pf_ctx, vol, sc.lights, 0.0, sc.camera, 1, 0.5, seed=4)
+    pf_ctx.sync()
+    ref = orc.render_neural(sc.volume, sc.lights, 0.0, sc.camera, 1, 0.5, 4)
+    assert _rel_err(one.cpu().numpy(), ref).max() <= 1e-4
+    # invalid arguments are rejected with a status, not a crash
+    with pytest.raises(api.PfError):
+        api.render_neural(pf_ctx, vol, sc.lights, 1.5, sc.camera, 1, 0.5, seed=4)
+    with pytest.raises(api.PfError):
+        api.render_pathtraced(pf_ctx, vol, sc.lights, 0.0, sc.camera, 0, 4, seed=4)
+    with pytest.raises(api.PfError):
+        api.render_neural(pf_ctx, vol, [], 0.0, sc.camera, 1, 0.5, seed=4)
+
+
+def test_rmse_reduction(pf_ctx):
+    g = torch.Generator().manual_seed(0)
+    a = torch.rand(1000003, generator=g).cuda()
+    b = torch.rand(1000003, generator=g).cuda()
+    r = api.image_rmse(pf_ctx, a, b)
+    want = math.sqrt(((a.double() - b.double()) ** 2).mean().item())
+    assert abs(r - want) < 1e-12 * want
