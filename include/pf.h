@@ -191,8 +191,9 @@ pf_status pf_field_free(pf_field* field);
 int64_t pf_field_num_params(const pf_field* field);
 pf_status pf_field_get_weights(pf_ctx* ctx, const pf_field* field, float* dst_dev);
 pf_status pf_field_set_weights(pf_ctx* ctx, pf_field* field, const float* src_dev);
-/* fp8 fields: per-layer scales s_w = amax|W|/448 and activation scales
- * s_a = amax(layer input)/448 over B calibration queries (unquantised pass). */
+/* fp8 fields: per-layer power-of-two scales s = 2^ceil(log2(amax/448)), with
+ * amax = max|W| for the weights and max|layer input| over B calibration
+ * queries (unquantised pass) for the activations; codes = e4m3(x / s). */
 pf_status pf_field_calibrate_fp8(pf_ctx* ctx, pf_field* field, const float* q_dev, int64_t B);
 /* Field forward pass: out_dev [B*3] = L' predictions for queries q_dev [B*6]. */
 pf_status pf_field_forward(pf_ctx* ctx, const pf_field* field, const float* q_dev, int64_t B, float* out_dev);
@@ -217,7 +218,7 @@ pf_status pf_train_field(pf_ctx* ctx, const pf_cache* cache, const pf_train_desc
  * RayGeneration (jittered pinhole ray, box test), VolumeSampling (first
  * interaction), DirectIllumination (NEE towards every light), field query at
  * the interaction with w = -ray direction, decode, and Compose
- * L = 1/spp sum_k albedo_k (L_d,k + L_i,k).  step_vox > 0 selects ray
+ * L = 1/spp sum_k albedo_k (L_d,k + L_i,k).  step_vox in [0.05, 64] selects ray
  * marching with step step_vox voxels (stratified inverse-CDF free flight,
  * marched shadow transmittance); step_vox == 0 selects delta tracking and
  * ratio-tracking shadow rays.  field == NULL renders direct light only.

@@ -17,9 +17,10 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
 Precision emulation (how the tensor-core field is specified): the input and
 the weights of every hidden layer are rounded to the field precision
-(bf16 / fp16 round-to-nearest-even; fp8 e4m3 with per-layer scales
-s_w = amax|W|/448 and activation scales s_a = amax(input)/448 from a
-calibration batch, saturating at +-448); products are accumulated exactly
+(bf16 / fp16 round-to-nearest-even; fp8 e4m3 codes of x / s with per-layer
+power-of-two scales s = 2^ceil(log2(amax/448)), amax taken over the weights
+and over a calibration batch's layer inputs, saturating at +-448); products
+are accumulated exactly
 (FP64 here, FP32 on the GPU); the 3-wide output layer runs in full precision
 on the unrounded last hidden activation.  In the backward pass the gradient
 with respect to every hidden pre-activation is rounded to the field precision
@@ -152,15 +153,22 @@ def query_from_sample(x: np.ndarray, wo: np.ndarray, g: float) -> np.ndarray:
 
 
 # ------------------------------------------------------------------ network
+def pow2_scale(amax: float) -> float:
+    """Smallest power of two s with amax / s <= 448 (e4m3's largest finite)."""
+    m, e = math.frexp(max(float(np.float32(amax)), 1e-30) / E4M3_MAX)
+    return math.ldexp(1.0, e - 1 if m == 0.5 else e)
+
+
 def fp8_calibrate(weights: np.ndarray, q_cal: np.ndarray, desc: FieldDesc):
-    """Per-layer fp8 scales: s_w = amax|W_l|/448, s_a = amax(layer input)/448
-    over the calibration queries, from the unquantised forward pass."""
+    """Per-layer fp8 scales, powers of two so that x / s is exact:
+    s_w from amax|W_l|, s_a from amax(layer input) over the calibration
+    queries of the unquantised forward pass."""
     ws = unflatten(weights, desc)
     h = encode(q_cal, desc.in_freqs)
     s_a, s_w = [], []
     for W in ws[:-1]:
-        s_a.append(max(float(np.abs(h).max()), 1e-30) / E4M3_MAX)
-        s_w.append(max(float(np.abs(W).max()), 1e-30) / E4M3_MAX)
+        s_a.append(pow2_scale(np.abs(h).max()))
+        s_w.append(pow2_scale(np.abs(W).max()))
         h = np.maximum(h @ W.T, 0.0)
     return np.array(s_a), np.array(s_w)
 

@@ -59,6 +59,7 @@ extern "C" pf_status pf_field_create(pf_ctx* ctx, const pf_field_desc* d, pf_fie
   if (!(d->psi > 0.f)) return pf_fail(ctx, PF_ERR_INVALID_ARG, "psi must be > 0");
   pf_field* f = new pf_field();
   f->ctx = ctx;
+  f->device = ctx->device;
   f->desc = *d;
   f->n_in = 12 * d->in_freqs;
   f->n_layers = d->n_hidden + 1;
@@ -96,8 +97,8 @@ extern "C" pf_status pf_field_create(pf_ctx* ctx, const pf_field_desc* d, pf_fie
 
 extern "C" pf_status pf_field_free(pf_field* f) {
   if (!f) return PF_OK;
-  DeviceGuard dg(f->ctx ? f->ctx->device : 0);
-  if (f->ctx) cudaStreamSynchronize(f->ctx->stream);
+  DeviceGuard dg(f->device);
+  cudaDeviceSynchronize();
   cudaFree(f->w); cudaFree(f->m); cudaFree(f->v); cudaFree(f->wq); cudaFree(f->scales);
   delete f;
   return PF_OK;
@@ -404,12 +405,18 @@ extern "C" pf_status pf_field_calibrate_fp8(pf_ctx* ctx, pf_field* f, const floa
   unsigned int h[64];
   PF_CUDA(ctx, cudaMemcpyAsync(h, amax, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
   PF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  // power-of-two scales 2^ceil(log2(amax / 448)): dividing by them is exact
+  auto pow2_scale = [](float amax) {
+    int e;
+    float m = std::frexp(std::max(amax, 1e-30f) / 448.0f, &e);
+    return std::ldexp(1.0f, m == 0.5f ? e - 1 : e);
+  };
   for (int l = 0; l < f->n_layers - 1; ++l) {
     float a, w;
     memcpy(&a, &h[l], 4);
     memcpy(&w, &h[16 + l], 4);
-    f->scales_host[l] = fmaxf(a, 1e-30f) / 448.0f;
-    f->scales_host[16 + l] = fmaxf(w, 1e-30f) / 448.0f;
+    f->scales_host[l] = pow2_scale(a);
+    f->scales_host[16 + l] = pow2_scale(w);
   }
   PF_CUDA(ctx, cudaMemcpyAsync(f->scales, f->scales_host, 32 * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
   f->fp8_ready = 1;

@@ -28,7 +28,8 @@ struct pf_ctx {
 };
 
 struct pf_cache {
-  pf_ctx* ctx = nullptr;
+  pf_ctx* ctx = nullptr;              // creating context (not dereferenced when freed)
+  int device = 0;
   int res = 0, n_lights = 0, n_g = 0, max_bounces = 0;
   int64_t n_photons = 0, n_records = 0, n_keys = 0, n_occupied = 0;
   float g_set[16] = {};
@@ -43,7 +44,8 @@ struct pf_cache {
 };
 
 struct pf_field {
-  pf_ctx* ctx = nullptr;
+  pf_ctx* ctx = nullptr;              // creating context (not dereferenced when freed)
+  int device = 0;
   pf_field_desc desc{};
   int n_in = 0, n_layers = 0;
   int64_t n_params = 0;

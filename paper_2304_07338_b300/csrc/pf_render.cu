@@ -264,7 +264,8 @@ extern "C" pf_status pf_render_neural(pf_ctx* ctx, const pf_volume* vol, const p
   PF_TRY(pf_check_lights(ctx, lights, n_lights));
   PF_TRY(check_cam(ctx, cam, spp));
   if (!out_rgb_dev) return pf_fail(ctx, PF_ERR_INVALID_ARG, "out_rgb_dev is NULL");
-  if (!(step_vox >= 0.f) || !(g > -1.f && g < 1.f)) return pf_fail(ctx, PF_ERR_INVALID_ARG, "need step_vox >= 0 and |g| < 1");
+  if (!(step_vox == 0.f || (step_vox >= 0.05f && step_vox <= 64.f)) || !(g > -1.f && g < 1.f))
+    return pf_fail(ctx, PF_ERR_INVALID_ARG, "need step_vox = 0 or in [0.05, 64] voxels, and |g| < 1");
   if (field && field->ctx != ctx) return pf_fail(ctx, PF_ERR_INVALID_ARG, "field belongs to another context");
   float maj;
   PF_TRY(pf_majorant_impl(ctx, vol, &maj));

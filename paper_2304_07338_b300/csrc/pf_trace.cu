@@ -246,7 +246,7 @@ extern "C" pf_status pf_build_photon_cache(pf_ctx* ctx, const pf_volume* vol, co
   PF_TRY(pf_majorant_impl(ctx, vol, &maj));
 
   pf_cache* c = new pf_cache();
-  c->ctx = ctx; c->res = res; c->n_lights = n_lights; c->n_g = n_g; c->max_bounces = max_bounces;
+  c->ctx = ctx; c->device = ctx->device; c->res = res; c->n_lights = n_lights; c->n_g = n_g; c->max_bounces = max_bounces;
   c->n_photons = (int64_t)P; c->n_keys = n_keys;
   for (int i = 0; i < n_g; ++i) c->g_set[i] = g_set[i];
   int S = max_bounces - 1;
@@ -365,7 +365,8 @@ extern "C" pf_status pf_cache_export(pf_ctx* ctx, const pf_cache* c, uint32_t* c
 
 extern "C" pf_status pf_cache_free(pf_cache* c) {
   if (!c) return PF_OK;
-  DeviceGuard dg(c->ctx ? c->ctx->device : 0);
+  DeviceGuard dg(c->device);
+  cudaDeviceSynchronize();
   free_cache(c);
   return PF_OK;
 }

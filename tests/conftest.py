@@ -29,4 +29,3 @@ def pf_ctx():
     build.build()
     ctx = api.Context(0)
     yield ctx
-    ctx.close()

@@ -144,9 +144,12 @@ def test_fp8_calibration_and_quantised_forward():
     rng = np.random.default_rng(4)
     q = rng.uniform(0, 1, (256, 6))
     s_a, s_w = F.fp8_calibrate(w, q, desc)
-    assert abs(s_a[0] * 448 - 1.0) < 1e-3                 # encoding amplitude is 1
+    assert s_a[0] == 2.0 ** -8                             # encoding amplitude 1: 1/448 -> 2^-8
     ws = F.unflatten(w, desc)
-    assert np.allclose(s_w * 448, [np.abs(W).max() for W in ws[:-1]])
+    for s, W in zip(s_w, ws[:-1]):
+        a = np.abs(W).max()
+        assert a / s <= 448 and a / (s / 2) > 448 and np.log2(s) == int(np.log2(s))
+    assert F.pow2_scale(448.0) == 1.0 and F.pow2_scale(448.5) == 2.0
     y8, _ = F.forward(w, q, desc, (s_a, s_w))
     y32, _ = F.forward(w, q, F.FieldDesc(12, 32, 2, F.PREC_F32, 5.0, 1))
     assert np.abs(y8 - y32).max() < 0.1 * np.abs(y32).max() + 1e-3
