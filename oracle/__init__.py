@@ -92,11 +92,13 @@ class _Lights:
 
 
 class _Cam:
+    """Camera parameters as the C ABI carries them (float32), widened to FP64."""
+
     def __init__(self, cam):
-        self.eye = np.array(cam.eye, np.float64)
-        self.at = np.array(cam.at, np.float64)
-        self.up = np.array(cam.up, np.float64)
-        self.args = (_p(self.eye), _p(self.at), _p(self.up), float(cam.fovy_deg), int(cam.width), int(cam.height))
+        f32 = lambda v: np.array(v, np.float32).astype(np.float64)
+        self.eye, self.at, self.up = f32(cam.eye), f32(cam.at), f32(cam.up)
+        self.args = (_p(self.eye), _p(self.at), _p(self.up), float(np.float32(cam.fovy_deg)), int(cam.width),
+                     int(cam.height))
 
 
 # ------------------------------------------------------------------ random numbers

@@ -440,7 +440,9 @@ pf_status pf_field_forward_impl(pf_ctx* ctx, const pf_field* f, const float* q, 
 }
 
 extern "C" pf_status pf_field_forward(pf_ctx* ctx, const pf_field* f, const float* q, int64_t B, float* out) {
-  if (!ctx || !f || !q || !out || B < 0) return pf_fail(ctx, PF_ERR_INVALID_ARG, "bad field forward arguments");
+  if (!ctx || !f || B < 0) return pf_fail(ctx, PF_ERR_INVALID_ARG, "bad field forward arguments");
+  if (B == 0) return PF_OK;
+  if (!q || !out) return pf_fail(ctx, PF_ERR_INVALID_ARG, "bad field forward arguments");
   if (f->ctx != ctx) return pf_fail(ctx, PF_ERR_INVALID_ARG, "field belongs to another context");
   DeviceGuard dg(ctx->device);
   return pf_field_forward_impl(ctx, f, q, B, nullptr, out, nullptr, nullptr, nullptr);
@@ -457,7 +459,8 @@ pf_status pf_field_backward_impl(pf_ctx* ctx, const pf_field* f, const float* q,
 
 extern "C" pf_status pf_field_backward(pf_ctx* ctx, const pf_field* f, const float* q, const float* dy, int64_t B,
                                        float* dw) {
-  if (!ctx || !f || !q || !dy || !dw || B < 0) return pf_fail(ctx, PF_ERR_INVALID_ARG, "bad field backward arguments");
+  if (!ctx || !f || !dw || B < 0 || (B > 0 && (!q || !dy)))
+    return pf_fail(ctx, PF_ERR_INVALID_ARG, "bad field backward arguments");
   if (f->ctx != ctx) return pf_fail(ctx, PF_ERR_INVALID_ARG, "field belongs to another context");
   DeviceGuard dg(ctx->device);
   return pf_field_backward_impl(ctx, f, q, dy, nullptr, B, dw, nullptr);

@@ -56,7 +56,9 @@ __global__ void __launch_bounds__(128) k_camera_samples(Vol V, DevLights L, CamF
           for (int i = 0; i < 4; ++i) if (4 * b + i < 16) jl[4 * b + i] = w[i];
         }
         float tau_star = -own_lnf(1.0f - b0[3]);
-        float tau = 0.f;
+        // optical depth accumulated with a compensated (Kahan) sum: its
+        // float32 error stays O(ulp) however many steps the ray takes
+        float tau = 0.f, comp = 0.f;
         int nseg = (int)ceilf((t1 - t0) / h);
         for (int s = 0; s < nseg; ++s) {
           float s0 = t0 + (float)s * h;
@@ -64,12 +66,16 @@ __global__ void __launch_bounds__(128) k_camera_samples(Vol V, DevLights L, CamF
           float len = s1 - s0;
           if (!(len > 0.f)) continue;
           float sg = sigma_at<DT>(V, along(o, d, s0 + b0[2] * len));
-          if (sg > 0.f && tau + sg * len >= tau_star) {
-            th = s0 + (tau_star - tau) / sg;
+          float dtau = sg * len;
+          if (sg > 0.f && (tau - comp) + dtau >= tau_star) {
+            th = s0 + (tau_star - (tau - comp)) / sg;
             hit = true;
             break;
           }
-          tau = tau + sg * len;
+          float y = dtau - comp;
+          float t = tau + y;
+          comp = (t - tau) - y;
+          tau = t;
         }
       } else {
         hit = delta_track<DT>(V, o, d, t0, t1, rng, &th, err);
@@ -85,7 +91,7 @@ __global__ void __launch_bounds__(128) k_camera_samples(Vol V, DevLights L, CamF
           if (box_hit(x, wl, &a0, &a1)) tend = mn(a1, dist);
           float T;
           if (MARCH) {
-            float tau = 0.f;
+            float tau = 0.f, comp = 0.f;
             if (tend > 0.f) {
               int nseg = (int)ceilf(tend / h);
               for (int s = 0; s < nseg; ++s) {
@@ -93,10 +99,13 @@ __global__ void __launch_bounds__(128) k_camera_samples(Vol V, DevLights L, CamF
                 float s1 = mn((float)(s + 1) * h, tend);
                 float len = s1 - s0;
                 if (!(len > 0.f)) continue;
-                tau = tau + sigma_at<DT>(V, along(x, wl, s0 + jl[l] * len)) * len;
+                float y = sigma_at<DT>(V, along(x, wl, s0 + jl[l] * len)) * len - comp;
+                float t = tau + y;
+                comp = (t - tau) - y;
+                tau = t;
               }
             }
-            T = expf(-tau);
+            T = expf(-(tau - comp));
           } else {
             T = ratio_track<DT>(V, x, wl, tend, rng, err);
           }

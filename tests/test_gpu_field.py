@@ -91,7 +91,8 @@ def test_autograd_function(pf_ctx):
     y = api.FieldFunction.apply(fld, q, w)
     (y * y).sum().backward()
     dw = fld.backward(q, (2 * y).detach())
-    assert torch.allclose(w.grad, dw)
+    # float32 atomics make the block-sum order vary between calls
+    assert torch.allclose(w.grad, dw, rtol=1e-4, atol=1e-6)
 
 
 def test_adam_step(pf_ctx):

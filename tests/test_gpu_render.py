@@ -26,7 +26,7 @@ pytestmark = pytest.mark.gpu
 def _rel_err(a, b):
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
-    den = np.maximum(np.abs(b), 1e-3 * np.abs(b).max())
+    den = np.maximum(np.abs(b), max(1e-3 * np.abs(b).max(), 1e-30))
     return np.abs(a - b) / den
 
 
