@@ -1,0 +1,332 @@
+"""Benchmark: neural volumetric path tracing with photon fields on B300.
+
+Workload (the paper's large-render setting, synthetic): 1024^3 float16
+turbulence volume (2 GiB, larger than L2), 256-node RGBA transfer function,
+8 point lights, 1920x1080 at 16 samples per pixel, phase coefficient g drawn
+per frame from U[-0.9, 0.9], photon field 4 x 128 in fp8 (e4m3, per-layer
+power-of-two scales), delta-tracking free flight and ratio-tracking shadow
+rays (Algorithm 2).  One step = one frame of the 60-frame orbit through the
+library's C ABI (pf_render_neural): camera samples, field queries, compose.
+
+Reports frames/s and field queries/s, the dominant stage's roofline from
+live CUDA events, the end-to-end number through the C ABI with the camera
+from host memory and the image read back to pinned host memory, clocks
+sampled during the timed region, and the CPU oracle on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "1080p frames/sec and field queries/sec vs plain GPU path tracer at equal RMSE"
+W_, H_, SPP, N_VOX, N_LIGHTS = 1920, 1080, 16, 1024, 8
+HIDDEN, N_HIDDEN, FREQS = 128, 4, 12
+VOXEL_BYTES = 2                 # float16
+FETCH_BYTES = 8 * VOXEL_BYTES   # one trilinear lookup reads 8 voxels
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d["hbm_gbs"], d["bf16_tflops"], d.get("bf16_tflops_sustained", d["bf16_tflops"]), "measured"
+    except Exception:
+        return 6400.0, 1800.0, 1400.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling in the background while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def setup_scene(device):
+    import torch
+    from paper_2304_07338_b300 import api, inputs as I
+    vol_t, tf, lights, cams = I.large_scene_parts(N_VOX, device=device)
+    return vol_t.contiguous(), torch.from_numpy(tf).to(device), lights, cams
+
+
+def cpu_baseline(vol_host, tf, lights, cams, seed, rows=2, weights=None, desc=None, scales=None):
+    """The oracle (plain C++/numpy) on a bounded sample: `rows` full image rows
+    of one frame at full spp, scaled to a frame."""
+    import oracle
+    from paper_2304_07338_b300 import inputs as I
+    v = I.Volume(vol_host, 20.0, 0.9, tf)
+    cam = cams[0]
+    g = I.frame_g(seed, 0)
+    y0 = H_ // 2
+    t = time.perf_counter()
+    oracle.render_neural(v, lights, g, cam, SPP, 0.0, seed, weights=weights, desc=desc, scales=scales, fp32=True,
+                         rows=(y0, y0 + rows))
+    dt = time.perf_counter() - t
+    frame_s = dt * H_ / rows
+    return {"value": 1.0 / frame_s, "unit": "frames/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "%d of %d rows of frame 0 (%dx%d, %d spp, 8 lights, fp8 field emulated in FP64), "
+                      "scaled to a full frame; %.2f s measured" % (rows, H_, W_, H_, SPP, dt)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-rows", type=int, default=2)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    seed = 20230418
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, dev, seed)
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    from paper_2304_07338_b300 import api, build, inputs as I
+    build.build()
+    ctx = api.Context(local)
+    vol_t, tf_t, lights, cams = setup_scene(dev)
+    vol = api.Volume(vol_t, 20.0, 0.9, tf_t)
+    vol.s.majorant = vol.majorant(ctx)
+    field = api.Field(ctx, FREQS, HIDDEN, N_HIDDEN, "fp8", 5.0, seed=seed)
+    field.calibrate_fp8(calibration_queries().to(dev))
+    out = torch.empty(H_, W_, 3, device=dev)
+
+    def frame(i):
+        f = (rank * 1000 + i) % len(cams)
+        return cams[f], I.frame_g(seed, f)
+
+    for i in range(args.warmup):
+        cam, g = frame(i)
+        api.render_neural(ctx, vol, lights, g, cam, SPP, 0.0, seed + i, field, out)
+    ctx.sync()
+    # work counters (density lookups) from one counted frame outside the timed region
+    counters = torch.zeros(4, dtype=torch.int64, device=dev)
+    ctx.set_counters(counters)
+    cam, g = frame(0)
+    api.render_neural(ctx, vol, lights, g, cam, SPP, 0.0, seed, field, out)
+    ctx.sync()
+    ctx.set_counters(None)
+    fetches_per_frame = int(counters[0].item())
+    qpf = int(counters[1].item())
+
+    # timed region
+    ctx.stage_times()
+    ctx.stage_timing(True)
+    clocks = Clocks(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    s_ev, e_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s_ev.record(ctx.stream)
+    for i in range(args.steps):
+        cam, g = frame(args.warmup + i)
+        api.render_neural(ctx, vol, lights, g, cam, SPP, 0.0, seed + 100 + i, field, out)
+    e_ev.record(ctx.stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms_total = s_ev.elapsed_time(e_ev)
+    clk = clocks.stop()
+    ctx.stage_timing(False)
+    stages = ctx.stage_times()
+    ms = torch.tensor([ms_total], device=dev)
+    if dist:
+        dist.all_reduce(ms, op=dist.ReduceOp.MAX)
+    ms_total = float(ms.item())
+    ms_per_step = ms_total / args.steps
+    fps = world * args.steps / (ms_total / 1e3)
+
+    # end to end through the C ABI: camera from host, image to pinned host memory
+    host_img = torch.empty(H_, W_, 3, dtype=torch.float32, pin_memory=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_steps = max(3, min(args.steps, 10))
+    for i in range(e2e_steps):
+        cam, g = frame(i)
+        api.render_neural(ctx, vol, lights, g, cam, SPP, 0.0, seed + 200 + i, field, out)
+        host_img.copy_(out, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    import ctypes
+    h2d = ctypes.sizeof(api.PfCamera) + N_LIGHTS * ctypes.sizeof(api.PfLight)
+    d2h = H_ * W_ * 3 * 4
+
+    hbm, bf16, bf16s, src = peaks()
+    cam_ms, cam_n = stages["camera"]
+    fld_ms, fld_n = stages["field"]
+    cmp_ms, cmp_n = stages["compose"]
+    dominant = "camera" if cam_ms >= fld_ms else "field"
+    if dominant == "camera":
+        per_launch_s = cam_ms / max(cam_n, 1) / 1e3
+        alg_bytes = fetches_per_frame * FETCH_BYTES
+        achieved = alg_bytes / per_launch_s / 1e9
+        roof = {"kernel": "k_camera_samples (delta + ratio tracking)", "bound": "hbm", "achieved": achieved,
+                "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                "algorithmic": "%d density lookups/frame x %d B" % (fetches_per_frame, FETCH_BYTES),
+                "peak_source": src}
+    else:
+        per_launch_s = fld_ms / max(fld_n, 1) / 1e3
+        flop = qpf * 2 * (12 * FREQS * HIDDEN + (N_HIDDEN - 1) * HIDDEN * HIDDEN + 3 * HIDDEN)
+        achieved = flop / per_launch_s / 1e12
+        peak8 = 2 * bf16s
+        roof = {"kernel": "field forward (fp8)", "bound": "tensor", "achieved": achieved, "peak": peak8,
+                "unit": "TFLOP/s", "frac": achieved / peak8, "traffic": None, "peak_source": src + " bf16 x 2 (fp8)"}
+
+    line = {
+        "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "fp8 field / f32 tracking", "data": "synthetic",
+        "config": {"workload": "large neural render: 1024^3 f16 turbulence, 8 point lights, 1920x1080, 16 spp, "
+                               "fp8 4x128 field, delta/ratio tracking",
+                   "frames": "60-frame orbit", "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (2 GiB volume)"},
+        "queries_per_s": qpf * fps,
+        "queries_per_frame": qpf,
+        "stages_ms_per_frame": {k: v[0] / max(args.steps, 1) for k, v in stages.items() if v[1]},
+        "roofline": roof,
+        "clocks": clk,
+        "e2e": {"value": 1.0 / e2e_s, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps * (cam_n // max(args.steps, 1) + fld_n // max(args.steps, 1) + cmp_n // max(args.steps, 1)),
+    }
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        try:
+            line["cpu_baseline"] = cpu_baseline(vol_t.cpu().numpy(), tf_t.cpu().numpy(), lights, cams, seed,
+                                                rows=args.cpu_rows, **oracle_field(field))
+        except Exception as e:  # reported, not fatal
+            line["cpu_baseline"] = {"error": repr(e)[:200]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def oracle_field(field):
+    from oracle import field as F
+    desc = F.FieldDesc(FREQS, HIDDEN, N_HIDDEN, F.PREC_FP8, field.psi, 0)
+    w = field.get_weights().cpu().numpy().astype(np.float64)
+    s = field_scales(field)
+    return dict(weights=w, desc=desc, scales=s)
+
+
+def calibration_queries():
+    """4096 fp8 calibration queries: uniform positions and angles, g in [-0.9, 0.9]."""
+    import torch
+    g = torch.Generator().manual_seed(0)
+    cal = torch.rand(4096, 6, generator=g)
+    cal[:, 5] = cal[:, 5] * 1.8 - 0.9
+    return cal.contiguous()
+
+
+def field_scales(field):
+    # the oracle computes its own scales from the same calibration queries
+    from oracle import field as F
+    cal = calibration_queries().numpy().astype(np.float64)
+    desc = F.FieldDesc(FREQS, HIDDEN, N_HIDDEN, F.PREC_FP8, field.psi, 0)
+    return F.fp8_calibrate(field.get_weights().cpu().numpy().astype(np.float64), cal, desc)
+
+
+def run_reference(args, dev, seed):
+    """The oracle as the reference arm: each step renders a bounded sample (one
+    image row at full spp) of the same workload on the host cores; frames/s
+    extrapolated from the per-row time."""
+    import torch
+    vol_t, tf_t, lights, cams = setup_scene(dev)
+    vol_h, tf_h = vol_t.cpu().numpy(), tf_t.cpu().numpy()
+    from paper_2304_07338_b300 import api  # noqa: F401  (only for PfCamera sizes)
+    times = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(vol_h, tf_h, lights, cams, seed, rows=1)
+        if i >= args.warmup:
+            times.append(1.0 / r["value"])
+    fps = 1.0 / float(np.mean(times))
+    cb = {"value": fps, "unit": "frames/s", "cores": os.cpu_count(), "kind": "oracle",
+          "sample": "1 of %d rows per step at full spp, scaled to a frame" % H_}
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / fps,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64/f32 oracle",
+                      "data": "synthetic",
+                      "config": {"workload": "large neural render: 1024^3 f16 turbulence, 8 point lights, "
+                                             "1920x1080, 16 spp, fp8 4x128 field, delta/ratio tracking"},
+                      "cpu_baseline": cb,
+                      "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+          flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -56,6 +56,9 @@ SIGNATURES = {
     "pf_destroy": (I, [P]),
     "pf_set_stream": (I, [P, P]),
     "pf_last_error": (C.c_char_p, [P]),
+    "pf_set_counters": (I, [P, P]),
+    "pf_stage_timing": (I, [P, I]),
+    "pf_stage_times": (I, [P, C.POINTER(C.c_double), C.POINTER(C.c_int), I]),
     "pf_sync": (I, [P]),
     "pf_volume_majorant": (I, [P, C.POINTER(PfVolume), C.POINTER(C.c_float)]),
     "pf_build_photon_cache": (I, [P, C.POINTER(PfVolume), C.POINTER(PfLight), I, C.POINTER(C.c_float), I, U64, I, I,

@@ -50,6 +50,23 @@ class Context:
     def sync(self):
         self.check(self.lib.pf_sync(self.h))
 
+    def set_counters(self, counters: Optional[torch.Tensor]):
+        """Count density lookups into counters[0] (int64 CUDA tensor) or stop (None)."""
+        self.check(self.lib.pf_set_counters(self.h, _ptr(counters)))
+
+    STAGES = ("camera", "field", "compose", "path", "train", "photons")
+
+    def stage_timing(self, enable: bool):
+        self.check(self.lib.pf_stage_timing(self.h, int(enable)))
+
+    def stage_times(self):
+        """{stage: (milliseconds, launches)} accumulated since the last call."""
+        n = len(self.STAGES)
+        ms = (C.c_double * n)()
+        cnt = (C.c_int * n)()
+        self.check(self.lib.pf_stage_times(self.h, ms, cnt, n))
+        return {s: (ms[i], cnt[i]) for i, s in enumerate(self.STAGES)}
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.pf_destroy(self.h)

@@ -73,6 +73,8 @@ extern "C" pf_status pf_destroy(pf_ctx* c) {
   DeviceGuard dg(c->device);
   cudaStreamSynchronize(c->stream);
   for (int i = 0; i < WS_COUNT; ++i) cudaFree(c->ws[i]);
+  for (auto& m : c->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
+  for (auto e : c->event_pool) cudaEventDestroy(e);
   cudaFree(c->err_dev);
   cudaFree(c->dbl_dev);
   delete c;
@@ -82,6 +84,53 @@ extern "C" pf_status pf_destroy(pf_ctx* c) {
 extern "C" pf_status pf_set_stream(pf_ctx* c, void* stream) {
   if (!c) return PF_ERR_INVALID_ARG;
   c->stream = (cudaStream_t)stream;
+  return PF_OK;
+}
+
+extern "C" pf_status pf_set_counters(pf_ctx* c, uint64_t* counters_dev) {
+  if (!c) return PF_ERR_INVALID_ARG;
+  c->counters = (unsigned long long*)counters_dev;
+  return PF_OK;
+}
+
+static cudaEvent_t take_event(pf_ctx* c) {
+  if (!c->event_pool.empty()) { cudaEvent_t e = c->event_pool.back(); c->event_pool.pop_back(); return e; }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+StageTimer::StageTimer(pf_ctx* c, int st) : ctx(c), stage(st) {
+  if (!ctx->timing) return;
+  a = take_event(ctx);
+  b = take_event(ctx);
+  cudaEventRecord(a, ctx->stream);
+}
+StageTimer::~StageTimer() {
+  if (!ctx->timing || !a) return;
+  cudaEventRecord(b, ctx->stream);
+  ctx->marks.push_back({stage, a, b});
+}
+
+extern "C" pf_status pf_stage_timing(pf_ctx* c, int enable) {
+  if (!c) return PF_ERR_INVALID_ARG;
+  c->timing = enable ? 1 : 0;
+  return PF_OK;
+}
+
+extern "C" pf_status pf_stage_times(pf_ctx* c, double* ms_host, int* launches_host, int n) {
+  if (!c || !ms_host || n <= 0) return PF_ERR_INVALID_ARG;
+  DeviceGuard dg(c->device);
+  PF_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < n; ++i) { ms_host[i] = 0.0; if (launches_host) launches_host[i] = 0; }
+  for (auto& m : c->marks) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, m.a, m.b);
+    if (m.stage >= 0 && m.stage < n) { ms_host[m.stage] += ms; if (launches_host) launches_host[m.stage] += 1; }
+    c->event_pool.push_back(m.a);
+    c->event_pool.push_back(m.b);
+  }
+  c->marks.clear();
   return PF_OK;
 }
 

@@ -245,15 +245,17 @@ constexpr int kMaxTrackSteps = 1 << 24;
 
 // Delta (Woodcock) tracking in [t, t_end): one Philox block per tentative
 // collision (u0 distance, u1 acceptance).  Returns true on a real collision.
+// `fetches` counts density lookups (the tracers' unit of memory work).
 template <int DT>
 __device__ __forceinline__ bool delta_track(const Vol& V, V3 o, V3 d, float t, float t_end, Rng& rng, float* t_hit,
-                                            uint32_t* err) {
+                                            uint32_t* err, uint32_t& fetches) {
   const float sbar = V.majorant;
   if (!(sbar > 0.0f)) return false;
   for (int it = 0; it < kMaxTrackSteps; ++it) {
     float u[4]; rng.uni4(u);
     t = t + (-own_lnf(1.0f - u[0])) / sbar;
     if (t >= t_end) return false;
+    ++fetches;
     V3 x = along(o, d, t);
     if (u[1] * sbar < sigma_at<DT>(V, x)) { *t_hit = t; return true; }
   }
@@ -263,7 +265,8 @@ __device__ __forceinline__ bool delta_track(const Vol& V, V3 o, V3 d, float t, f
 
 // Ratio-tracking transmittance over [0, t_end).
 template <int DT>
-__device__ __forceinline__ float ratio_track(const Vol& V, V3 o, V3 d, float t_end, Rng& rng, uint32_t* err) {
+__device__ __forceinline__ float ratio_track(const Vol& V, V3 o, V3 d, float t_end, Rng& rng, uint32_t* err,
+                                             uint32_t& fetches) {
   const float sbar = V.majorant;
   if (!(sbar > 0.0f)) return 1.0f;
   float T = 1.0f, t = 0.0f;
@@ -271,6 +274,7 @@ __device__ __forceinline__ float ratio_track(const Vol& V, V3 o, V3 d, float t_e
     float u[4]; rng.uni4(u);
     t = t + (-own_lnf(1.0f - u[0])) / sbar;
     if (t >= t_end) return T;
+    ++fetches;
     float f = 1.0f - sigma_at<DT>(V, along(o, d, t)) / sbar;
     T = T * mx(0.0f, f);
   }

@@ -99,7 +99,7 @@ extern "C" pf_status pf_field_free(pf_field* f) {
   if (!f) return PF_OK;
   DeviceGuard dg(f->device);
   cudaDeviceSynchronize();
-  cudaFree(f->w); cudaFree(f->m); cudaFree(f->v); cudaFree(f->wq); cudaFree(f->scales);
+  cudaFree(f->w); cudaFree(f->m); cudaFree(f->v); cudaFree(f->wq); cudaFree(f->wr); cudaFree(f->scales);
   delete f;
   return PF_OK;
 }
@@ -125,7 +125,8 @@ extern "C" pf_status pf_field_set_weights(pf_ctx* ctx, pf_field* f, const float*
 namespace {
 
 struct FieldView {
-  const float* w;
+  const float* w;     // master weights (output layer read from here)
+  const float* wr;    // hidden layers rounded to the field precision
   int64_t off[10];
   int fan_in[10], fan_out[10];
   int n_layers, n_in, hidden, in_freqs, prec;
@@ -136,6 +137,7 @@ struct FieldView {
 FieldView view_of(const pf_field* f) {
   FieldView v;
   v.w = f->w;
+  v.wr = f->wr ? f->wr : f->w;
   for (int l = 0; l <= f->n_layers && l < 10; ++l) v.off[l] = f->layer_off[l];
   for (int l = 0; l < f->n_layers; ++l) { v.fan_in[l] = f->fan_in[l]; v.fan_out[l] = f->fan_out[l]; }
   v.n_layers = f->n_layers; v.n_in = f->n_in; v.hidden = f->desc.hidden; v.in_freqs = f->desc.in_freqs;
@@ -173,7 +175,7 @@ __device__ void simt_forward(const FieldView& F, const float* q, int tid, float*
   for (int l = 0; l < F.n_layers; ++l) {
     const bool last = (l == F.n_layers - 1);
     const int K = F.fan_in[l], N = F.fan_out[l];
-    const float* W = F.w + F.off[l];
+    const float* W = (last ? F.w : F.wr) + F.off[l];
     if (!last) {
       for (int k = 0; k < K; ++k) {
         float r = rin(in[k * T + tid], F.prec, F.s_a[l]);
@@ -186,11 +188,7 @@ __device__ void simt_forward(const FieldView& F, const float* q, int tid, float*
     for (int n = 0; n < N; ++n) {
       float acc = 0.f;
       const float* wr = W + (size_t)n * K;
-      for (int k = 0; k < K; ++k) {
-        float wv = __ldg(wr + k);
-        if (!last) wv = rin(wv, F.prec, F.s_w[l]);
-        acc = fmaf(in[k * T + tid], wv, acc);
-      }
+      for (int k = 0; k < K; ++k) acc = fmaf(in[k * T + tid], __ldg(wr + k), acc);
       if (last) y[n] = acc;
       else outb[n * T + tid] = fmaxf(acc, 0.f);
     }
@@ -272,7 +270,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_simt_backward(FieldView F, cons
   for (int l = F.n_layers - 1; l >= 0; --l) {
     const bool last = (l == F.n_layers - 1);
     const int K = F.fan_in[l], N = F.fan_out[l];
-    const float* W = F.w + F.off[l];
+    const float* W = (last ? F.w : F.wr) + F.off[l];
     const float* xin = keep + (size_t)koff[l] * T;
     __syncwarp();
     // dW[n][k] += sum over the block's queries of dcur[n] * xin[k]
@@ -288,9 +286,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_simt_backward(FieldView F, cons
     for (int k = 0; k < K; ++k) {
       float acc = 0.f;
       for (int n = 0; n < N; ++n) {
-        float wv = __ldg(W + (size_t)n * K + k);
-        if (!last) wv = rin(wv, F.prec, F.s_w[l]);
-        acc = fmaf(dcur[n * T + tid], wv, acc);
+        acc = fmaf(dcur[n * T + tid], __ldg(W + (size_t)n * K + k), acc);
       }
       float a = xin[k * T + tid];
       float m = rin(a, F.prec, 1.f) > 0.f ? 1.f : 0.f;
@@ -649,6 +645,7 @@ extern "C" pf_status pf_train_field(pf_ctx* ctx, const pf_cache* c, const pf_tra
   PF_CUDA(ctx, cudaMemsetAsync(loss, 0, (size_t)std::max(d->steps, 1) * sizeof(float), ctx->stream));
   CacheView C = cview(c);
   int s0 = (int)std::ceil((double)d->decay_start_frac * d->steps);
+  StageTimer tm(ctx, PF_STAGE_TRAIN);
   for (int s = 0; s < d->steps; ++s) {
     k_batch<<<(unsigned)((B + 255) / 256), 256, 0, ctx->stream>>>(C, B, s, d->seed, f->desc.psi, q, y);
     PF_CUDA(ctx, cudaGetLastError());

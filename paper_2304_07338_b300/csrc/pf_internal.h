@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <string>
+#include <vector>
 #include "../../include/pf.h"
 
 // Device error word codes (bitwise OR of all that happened).
@@ -22,6 +23,11 @@ struct pf_ctx {
   int num_sms = 148;
   uint32_t* err_dev = nullptr;        // device error word
   double* dbl_dev = nullptr;          // small FP64 scratch (reductions)
+  unsigned long long* counters = nullptr;  // optional work counters (caller-owned)
+  int timing = 0;                         // record per-stage CUDA events
+  struct Mark { int stage; cudaEvent_t a, b; };
+  std::vector<Mark> marks;                // recorded (stage, start, end) pairs
+  std::vector<cudaEvent_t> event_pool;
   void* ws[WS_COUNT] = {};
   size_t ws_size[WS_COUNT] = {};
   std::string last_error;
@@ -55,11 +61,19 @@ struct pf_field {
   float* m = nullptr;                 // Adam moments
   float* v = nullptr;
   void* wq = nullptr;                 // packed low-precision weights (tensor-core layout)
+  float* wr = nullptr;                // hidden-layer weights rounded to the field precision (f32 values)
   size_t wq_bytes = 0;
   float* scales = nullptr;            // fp8: s_a[l], s_w[l] (device, 2 x 16)
   float scales_host[32] = {};
   int fp8_ready = 0;
   int step = 0;                       // Adam step counter
+};
+
+// Stage timing (PF_STAGE_* of pf.h): wraps a stage's launches in events.
+struct StageTimer {
+  pf_ctx* ctx; int stage; cudaEvent_t a = nullptr, b = nullptr;
+  StageTimer(pf_ctx* c, int st);
+  ~StageTimer();
 };
 
 // Status helpers.

@@ -25,14 +25,18 @@ using namespace pfd;
 namespace {
 
 // -------------------------------------------------------------- camera samples
+// stats (nullable): stats[0] += density lookups, stats[1] += valid samples
+// (= field queries) of the launch.
 template <int DT, bool MARCH>
 __global__ void __launch_bounds__(128) k_camera_samples(Vol V, DevLights L, CamF cam, float g, int spp, float h,
                                                         uint64_t seed, int64_t n_slots, float* __restrict__ slot_ld,
                                                         float* __restrict__ slot_li, float* __restrict__ cq,
                                                         float* __restrict__ calb, uint32_t* __restrict__ cidx,
-                                                        uint32_t* __restrict__ ccount, uint32_t* err) {
+                                                        uint32_t* __restrict__ ccount, uint32_t* err,
+                                                        unsigned long long* stats) {
   int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool active = slot < n_slots;
+  uint32_t nfetch = 0;
   int valid = 0;
   V3 x = v3(0.f, 0.f, 0.f), wo = x, alb = x, Ld = x;
   if (active) {
@@ -55,9 +59,13 @@ __global__ void __launch_bounds__(128) k_camera_samples(Vol V, DevLights L, CamF
 #pragma unroll
           for (int i = 0; i < 4; ++i) if (4 * b + i < 16) jl[4 * b + i] = w[i];
         }
-        float tau_star = -own_lnf(1.0f - b0[3]);
-        // optical depth accumulated with a compensated (Kahan) sum: its
-        // float32 error stays O(ulp) however many steps the ray takes
+        // Target optical depth tau* = -ln(1-u).  The interaction point is
+        // s0 + (tau* - tau)/sigma: where sigma is small, one float32 ulp of
+        // tau* or tau moves it by ulp/sigma, so tau* (one log per sample) and
+        // that final remainder are evaluated in FP64; the march itself and
+        // its compensated (Kahan) optical-depth sum stay float32.
+        const double tau_star_d = -log1p(-(double)b0[3]);
+        const float tau_star = (float)tau_star_d;
         float tau = 0.f, comp = 0.f;
         int nseg = (int)ceilf((t1 - t0) / h);
         for (int s = 0; s < nseg; ++s) {
@@ -66,9 +74,12 @@ __global__ void __launch_bounds__(128) k_camera_samples(Vol V, DevLights L, CamF
           float len = s1 - s0;
           if (!(len > 0.f)) continue;
           float sg = sigma_at<DT>(V, along(o, d, s0 + b0[2] * len));
+          ++nfetch;
           float dtau = sg * len;
           if (sg > 0.f && (tau - comp) + dtau >= tau_star) {
-            th = s0 + (tau_star - (tau - comp)) / sg;
+            double rem = tau_star_d - ((double)tau - (double)comp);
+            float dl = (float)(rem / (double)sg);
+            th = s0 + mn(mx(dl, 0.f), len);
             hit = true;
             break;
           }
@@ -78,12 +89,13 @@ __global__ void __launch_bounds__(128) k_camera_samples(Vol V, DevLights L, CamF
           tau = t;
         }
       } else {
-        hit = delta_track<DT>(V, o, d, t0, t1, rng, &th, err);
+        hit = delta_track<DT>(V, o, d, t0, t1, rng, &th, err, nfetch);
       }
       if (hit) {
         x = along(o, d, th);
         float sig;
         medium_at<DT>(V, x, &sig, &alb);
+        ++nfetch;
         for (int l = 0; l < L.n; ++l) {
           V3 wl, E; float dist;
           light_geom(L.l[l], x, &wl, &dist, &E);
@@ -100,6 +112,7 @@ __global__ void __launch_bounds__(128) k_camera_samples(Vol V, DevLights L, CamF
                 float len = s1 - s0;
                 if (!(len > 0.f)) continue;
                 float y = sigma_at<DT>(V, along(x, wl, s0 + jl[l] * len)) * len - comp;
+                ++nfetch;
                 float t = tau + y;
                 comp = (t - tau) - y;
                 tau = t;
@@ -107,7 +120,7 @@ __global__ void __launch_bounds__(128) k_camera_samples(Vol V, DevLights L, CamF
             }
             T = expf(-(tau - comp));
           } else {
-            T = ratio_track<DT>(V, x, wl, tend, rng, err);
+            T = ratio_track<DT>(V, x, wl, tend, rng, err, nfetch);
           }
           float ph = hg_eval(g, dot(d, wl));
           Ld = v3(Ld.x + ph * T * E.x, Ld.y + ph * T * E.y, Ld.z + ph * T * E.z);
@@ -121,6 +134,15 @@ __global__ void __launch_bounds__(128) k_camera_samples(Vol V, DevLights L, CamF
     slot_li[3 * slot + 0] = 0.f;
     slot_li[3 * slot + 1] = 0.f;
     slot_li[3 * slot + 2] = 0.f;
+  }
+  if (stats) {
+    unsigned long long v = nfetch;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    unsigned nv = __popc(__ballot_sync(0xffffffffu, valid));
+    if ((threadIdx.x & 31) == 0) {
+      if (v) atomicAdd(stats, v);
+      if (nv) atomicAdd(stats + 1, (unsigned long long)nv);
+    }
   }
   if (cq == nullptr) return;
   // warp-aggregated append of the valid samples' queries
@@ -162,7 +184,8 @@ __global__ void k_compose(const float* __restrict__ slot_ld, const float* __rest
 template <int DT>
 __global__ void __launch_bounds__(128) k_path_samples(Vol V, DevLights L, CamF cam, float g, int spp, int k0, int kc,
                                                       int max_bounces, int use_rr, uint64_t seed, int64_t n_items,
-                                                      float* __restrict__ slot_rad, uint32_t* err) {
+                                                      float* __restrict__ slot_rad, uint32_t* err,
+                                                      unsigned long long* stats) {
   int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (it >= n_items) return;
   int k = k0 + (int)(it % kc);
@@ -173,13 +196,14 @@ __global__ void __launch_bounds__(128) k_path_samples(Vol V, DevLights L, CamF c
   V3 o, d;
   camera_ray(cam, px, py, b0[0], b0[1], &o, &d);
   V3 rad = v3(0.f, 0.f, 0.f);
+  uint32_t nfetch = 0;
   float beta0 = 1.f, beta1 = 1.f, beta2 = 1.f;
   float t0, t1;
   if (box_hit(o, d, &t0, &t1)) {
     float t = t0;
     for (int j = 1; j <= max_bounces; ++j) {
       float th;
-      if (!delta_track<DT>(V, o, d, t, t1, rng, &th, err)) break;
+      if (!delta_track<DT>(V, o, d, t, t1, rng, &th, err, nfetch)) break;
       V3 x = along(o, d, th);
       float sig; V3 alb;
       medium_at<DT>(V, x, &sig, &alb);
@@ -189,7 +213,7 @@ __global__ void __launch_bounds__(128) k_path_samples(Vol V, DevLights L, CamF c
         light_geom(L.l[l], x, &wl, &dist, &E);
         float a0, a1, tend = 0.f;
         if (box_hit(x, wl, &a0, &a1)) tend = mn(a1, dist);
-        float T = ratio_track<DT>(V, x, wl, tend, rng, err);
+        float T = ratio_track<DT>(V, x, wl, tend, rng, err, nfetch);
         float ph = hg_eval(g, dot(d, wl));
         Lr = v3(Lr.x + ph * T * E.x, Lr.y + ph * T * E.y, Lr.z + ph * T * E.z);
       }
@@ -214,6 +238,7 @@ __global__ void __launch_bounds__(128) k_path_samples(Vol V, DevLights L, CamF c
   slot_rad[3 * it + 0] = rad.x;
   slot_rad[3 * it + 1] = rad.y;
   slot_rad[3 * it + 2] = rad.z;
+  if (stats) atomicAdd(stats, (unsigned long long)nfetch);
 }
 
 // acc[p] += r[p][k] for the chunk's samples in order; on the last chunk,
@@ -299,20 +324,27 @@ extern "C" pf_status pf_render_neural(pf_ctx* ctx, const pf_volume* vol, const p
   float h = step_vox > 0.f ? step_vox / (float)nmax : 0.f;
   dim3 blk(128), grd((unsigned)((n_slots + 127) / 128));
   bool march = step_vox > 0.f;
+  {
+  StageTimer tm(ctx, PF_STAGE_CAMERA);
 #define LAUNCH_CS(DT)                                                                                              \
   if (march) k_camera_samples<DT, true><<<grd, blk, 0, ctx->stream>>>(V, L, C, g, spp, h, seed, n_slots, ld, li, cq, \
-                                                                      calb, cidx, ccount, ctx->err_dev);             \
+                                                                      calb, cidx, ccount, ctx->err_dev, ctx->counters); \
   else k_camera_samples<DT, false><<<grd, blk, 0, ctx->stream>>>(V, L, C, g, spp, h, seed, n_slots, ld, li, cq, calb, \
-                                                                 cidx, ccount, ctx->err_dev);
+                                                                 cidx, ccount, ctx->err_dev, ctx->counters);
   if (vol->dtype == PF_F32) { LAUNCH_CS(0) } else if (vol->dtype == PF_F16) { LAUNCH_CS(1) } else { LAUNCH_CS(2) }
 #undef LAUNCH_CS
+  }
   PF_CUDA(ctx, cudaGetLastError());
   if (field) {
+    StageTimer tm(ctx, PF_STAGE_FIELD);
     // The number of valid samples is only known on the device; the field pass
     // reads it from there and covers the worst case n_slots.
     PF_TRY(pf_field_forward_impl(ctx, field, cq, n_slots, ccount, nullptr, cidx, calb, li));
   }
-  k_compose<<<(unsigned)((n_pix + 127) / 128), 128, 0, ctx->stream>>>(ld, li, n_pix, spp, out_rgb_dev);
+  {
+    StageTimer tm(ctx, PF_STAGE_COMPOSE);
+    k_compose<<<(unsigned)((n_pix + 127) / 128), 128, 0, ctx->stream>>>(ld, li, n_pix, spp, out_rgb_dev);
+  }
   PF_CUDA(ctx, cudaGetLastError());
   return PF_OK;
 }
@@ -339,16 +371,17 @@ extern "C" pf_status pf_render_pathtraced(pf_ctx* ctx, const pf_volume* vol, con
   Vol V = pf_make_vol(vol, maj);
   DevLights L = pf_make_lights(lights, n_lights);
   CamF C = make_cam(cam);
+  StageTimer tm(ctx, PF_STAGE_PATH);
   for (int k0 = 0; k0 < spp; k0 += (int)kc) {
     int kn = (int)std::min<int64_t>(kc, spp - k0);
     int64_t n_items = n_pix * kn;
     dim3 grd((unsigned)((n_items + 127) / 128));
     if (vol->dtype == PF_F32)
-      k_path_samples<0><<<grd, 128, 0, ctx->stream>>>(V, L, C, g, spp, k0, kn, max_bounces, use_rr, seed, n_items, rad, ctx->err_dev);
+      k_path_samples<0><<<grd, 128, 0, ctx->stream>>>(V, L, C, g, spp, k0, kn, max_bounces, use_rr, seed, n_items, rad, ctx->err_dev, ctx->counters);
     else if (vol->dtype == PF_F16)
-      k_path_samples<1><<<grd, 128, 0, ctx->stream>>>(V, L, C, g, spp, k0, kn, max_bounces, use_rr, seed, n_items, rad, ctx->err_dev);
+      k_path_samples<1><<<grd, 128, 0, ctx->stream>>>(V, L, C, g, spp, k0, kn, max_bounces, use_rr, seed, n_items, rad, ctx->err_dev, ctx->counters);
     else
-      k_path_samples<2><<<grd, 128, 0, ctx->stream>>>(V, L, C, g, spp, k0, kn, max_bounces, use_rr, seed, n_items, rad, ctx->err_dev);
+      k_path_samples<2><<<grd, 128, 0, ctx->stream>>>(V, L, C, g, spp, k0, kn, max_bounces, use_rr, seed, n_items, rad, ctx->err_dev, ctx->counters);
     PF_CUDA(ctx, cudaGetLastError());
     k_path_accumulate<<<(unsigned)((n_pix + 127) / 128), 128, 0, ctx->stream>>>(rad, n_pix, kn, k0 == 0, k0 + kn >= spp,
                                                                                 spp, acc, out_rgb_dev);

@@ -75,10 +75,11 @@ __global__ void __launch_bounds__(128) k_trace_photons(TraceArgs A, float4* __re
     bool alive = true;
     bool inside = box_hit(o, d, &t0, &t1);
     float t = t0;
+    uint32_t nfetch = 0;
     const uint32_t R = (uint32_t)A.res;
     while (alive && inside) {
       float th;
-      if (!delta_track<DT>(V, o, d, t, t1, rng, &th, err)) break;
+      if (!delta_track<DT>(V, o, d, t, t1, rng, &th, err, nfetch)) break;
       V3 x = along(o, d, th);
       j = j + 1;
       float sig; V3 alb;
@@ -266,6 +267,7 @@ extern "C" pf_status pf_build_photon_cache(pf_ctx* ctx, const pf_volume* vol, co
   CK(cudaMemsetAsync(c->counts, 0, (size_t)n_keys * sizeof(uint32_t), ctx->stream));
   CK(cudaMemsetAsync(tally_dev, 0, 15 * sizeof(double), ctx->stream));
 
+  StageTimer tm(ctx, PF_STAGE_PHOTONS);
   TraceArgs A;
   A.V = pf_make_vol(vol, maj);
   A.L = pf_make_lights(lights, n_lights);
