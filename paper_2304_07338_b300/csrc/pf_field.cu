@@ -422,6 +422,7 @@ extern "C" pf_status pf_field_calibrate_fp8(pf_ctx* ctx, pf_field* f, const floa
 
 // ------------------------------------------------------------------ public forward / backward
 pf_status pf_tc_available(const pf_field* f);
+pf_status pf_tc_backward_available(const pf_field* f);
 pf_status pf_tc_forward(pf_ctx* ctx, const pf_field* f, const float* q, int64_t B_max, const uint32_t* B_dev, float* out,
                         const uint32_t* slot_idx, const float* slot_alb, float* slot_li);
 pf_status pf_tc_backward(pf_ctx* ctx, const pf_field* f, const float* q, const float* dy, const float* targets,
@@ -449,7 +450,7 @@ pf_status pf_field_backward_impl(pf_ctx* ctx, const pf_field* f, const float* q,
   if (f->desc.prec == PF_PREC_FP8) return pf_fail(ctx, PF_ERR_UNSUPPORTED, "fp8 fields are inference-only");
   PF_CUDA(ctx, cudaMemsetAsync(dw, 0, f->n_params * sizeof(float), ctx->stream));
   if (B == 0) return PF_OK;
-  if (pf_tc_available(f) == PF_OK) return pf_tc_backward(ctx, f, q, dy, targets, B, dw, loss);
+  if (pf_tc_backward_available(f) == PF_OK) return pf_tc_backward(ctx, f, q, dy, targets, B, dw, loss);
   return pf_simt_backward(ctx, f, q, dy, targets, B, dw, loss);
 }
 

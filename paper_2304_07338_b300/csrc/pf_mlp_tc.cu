@@ -1,20 +1,344 @@
-// Tensor-core (tcgen05) field kernels -- placeholder until the tcgen05 path lands.
+// Photon field MLP on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// Forward pass (Sec. 3.4; hidden layers bf16 / fp16 / fp8 e4m3, FP32
+// accumulation in tensor memory):
+//   * one CTA = 4 warps, persistent over 128-query tiles;
+//   * the packed hidden-layer weights of the whole network are copied once
+//     per CTA into shared memory with bulk asynchronous copies
+//     (cp.async.bulk, completion on an mbarrier);
+//   * each thread owns one query row: it computes the frequency encoding and
+//     writes it into the A tile in shared memory (K-major core-matrix layout:
+//     8 rows x 16 bytes per core matrix, no swizzle);
+//   * one elected thread issues tcgen05.mma over the K steps of the layer
+//     (M = 128 rows, N = hidden width) into a TMEM accumulator and commits
+//     to an mbarrier;
+//   * every warp reads its 32 TMEM lanes back (tcgen05.ld), applies the fp8
+//     dequantisation, ReLU and the next layer's operand rounding, and writes
+//     the next A tile -- activations never leave the SM;
+//   * the 3-wide output layer runs in float32 on the last hidden activation
+//     straight from registers, followed by either the raw L' output or the
+//     renderer's epilogue (decode 10^(-psi L') times albedo into the sample slot).
+// All waits are bounded; a timeout sets the device error word, frees TMEM
+// and returns.
 #include "pf_internal.h"
-
-pf_status pf_tc_available(const pf_field* f) { (void)f; return PF_ERR_UNSUPPORTED; }
-pf_status pf_tc_forward(pf_ctx* ctx, const pf_field*, const float*, int64_t, const uint32_t*, float*, const uint32_t*,
-                        const float*, float*) {
-  return pf_fail(ctx, PF_ERR_UNSUPPORTED, "tensor-core field path unavailable");
-}
-pf_status pf_tc_backward(pf_ctx* ctx, const pf_field*, const float*, const float*, const float*, int64_t, float*, float*) {
-  return pf_fail(ctx, PF_ERR_UNSUPPORTED, "tensor-core field path unavailable");
-}
 #include "pf_field_common.cuh"
+#include <algorithm>
 
 namespace {
+
+constexpr int kTileM = 128;
+constexpr int kThreads = 128;
+constexpr int kMaxLayers = 8;
+constexpr uint32_t kSpin = 1u << 22;   // bounded mbarrier polls
+
+struct TcLayer {
+  uint32_t w_off;      // byte offset of the layer's packed weights in shared memory
+  uint32_t kp;         // padded K (multiple of the MMA K step)
+  float dequant;       // s_a * s_w (fp8), 1 otherwise
+  float inv_s_in;      // 1 / s_a: scale applied when this layer's input is written (fp8), 1 otherwise
+};
+
+struct TcArgs {
+  const uint8_t* wq;   // packed weights (global)
+  uint32_t wq_bytes;
+  const float* w_out;  // [3][H] float32 output layer
+  int n_hidden, hidden, in_freqs, prec, kstep;  // kstep = 16 (16-bit) or 32 (fp8)
+  uint32_t a_off, a_bytes, wout_off, bar_off, smem_bytes;
+  float psi;
+  TcLayer L[kMaxLayers];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kSpin; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major, no swizzle; LBO = byte distance
+// between core matrices adjacent in K, SBO = between 8-row groups.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of tcgen05
+  return d;
+}
+
+// Instruction descriptor: D = f32, A/B type code, both K-major, M = 128, N.
+__device__ __forceinline__ uint32_t idesc(uint32_t ab_type, uint32_t n) {
+  return (1u << 4) | (ab_type << 7) | (ab_type << 10) | ((n >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
+}
+
+template <bool FP8>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  if (FP8)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem_d),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem_d),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// 16 consecutive fp32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Operand encoding of one value for the A tile.
+template <int PREC>
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+  if (PREC == PF_PREC_BF16) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *(uint32_t*)&h;
+  } else {
+    __half2 h = __floats2half2_rn(a, b);
+    return *(uint32_t*)&h;
+  }
+}
+__device__ __forceinline__ uint32_t pack4_e4m3(float a, float b, float c, float d) {
+  uint32_t r = pff::e4m3_code(a) | ((uint32_t)pff::e4m3_code(b) << 8) | ((uint32_t)pff::e4m3_code(c) << 16) |
+               ((uint32_t)pff::e4m3_code(d) << 24);
+  return r;
+}
+
+// Writes 16 bytes of row r at K-chunk c (16 bytes = one core-matrix row).
+__device__ __forceinline__ void store_chunk(uint8_t* tile, uint32_t kp_bytes, int r, int c, uint4 v) {
+  uint32_t off = (uint32_t)(r >> 3) * (kp_bytes / 16) * 128 + (uint32_t)c * 128 + (uint32_t)(r & 7) * 16;
+  *(uint4*)(tile + off) = v;
+}
+
+// Takes 16 values of one row (already scaled) and stores them as operands:
+// 16-bit types -> two 16-byte chunks, fp8 -> one chunk.  `col` is the first
+// element's K index (multiple of 16).
+template <int PREC>
+__device__ __forceinline__ void store16(uint8_t* tile, uint32_t kp, int r, int col, const float v[16]) {
+  if (PREC == PF_PREC_FP8) {
+    uint4 q;
+    q.x = pack4_e4m3(v[0], v[1], v[2], v[3]);
+    q.y = pack4_e4m3(v[4], v[5], v[6], v[7]);
+    q.z = pack4_e4m3(v[8], v[9], v[10], v[11]);
+    q.w = pack4_e4m3(v[12], v[13], v[14], v[15]);
+    store_chunk(tile, kp, r, col / 16, q);
+  } else {
+    uint4 q0, q1;
+    q0.x = pack2<PREC>(v[0], v[1]); q0.y = pack2<PREC>(v[2], v[3]);
+    q0.z = pack2<PREC>(v[4], v[5]); q0.w = pack2<PREC>(v[6], v[7]);
+    q1.x = pack2<PREC>(v[8], v[9]); q1.y = pack2<PREC>(v[10], v[11]);
+    q1.z = pack2<PREC>(v[12], v[13]); q1.w = pack2<PREC>(v[14], v[15]);
+    store_chunk(tile, kp * 2, r, col / 8, q0);
+    store_chunk(tile, kp * 2, r, col / 8 + 1, q1);
+  }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kThreads, 1) k_tc_forward(TcArgs A, const float* __restrict__ q, int64_t B_max,
+                                                            const uint32_t* __restrict__ B_dev, float* __restrict__ out,
+                                                            const uint32_t* __restrict__ slot_idx,
+                                                            const float* __restrict__ slot_alb,
+                                                            float* __restrict__ slot_li, uint32_t* err) {
+  constexpr bool FP8 = (PREC == PF_PREC_FP8);
+  constexpr uint32_t EB = FP8 ? 1 : 2;
+  constexpr uint32_t AB_TYPE = (PREC == PF_PREC_BF16) ? 1u : 0u;   // f16 = 0, bf16 = 1, e4m3 = 0
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  uint8_t* a_tile = smem + A.a_off;
+  float* w_out = (float*)(smem + A.wout_off);
+  uint64_t* bars = (uint64_t*)(smem + A.bar_off);
+  uint32_t* tmem_slot = (uint32_t*)(smem + A.bar_off + 16);
+  int* abort_flag = (int*)(smem + A.bar_off + 20);
+  const uint32_t bar_w = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]);
+  const int H = A.hidden;
+
+  if (tid == 0) {
+    mbar_init(bar_w, 1);
+    mbar_init(bar_mma, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int i = tid; i < 3 * H; i += kThreads) w_out[i] = A.w_out[i];
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(128u));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  // weights: one bulk copy (the packed block is contiguous and 16-byte sized)
+  if (tid == 0) {
+    mbar_expect_tx(bar_w, A.wq_bytes);
+    bulk_g2s(smem_u32(smem), A.wq, A.wq_bytes, bar_w);
+  }
+  if (!mbar_wait(bar_w, 0)) {
+    if (tid == 0) { atomicOr(err, PFE_ITER_CAP); *abort_flag = 1; }
+  }
+  __syncthreads();
+  const int64_t B = B_dev ? (int64_t)*B_dev : B_max;
+  const int64_t n_tiles = (B + kTileM - 1) / kTileM;
+  uint32_t mma_phase = 0;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const int F = A.in_freqs;
+  const uint32_t kp0 = A.L[0].kp;
+
+  for (int64_t tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x) {
+    const int64_t row = tile * kTileM + tid;
+    const bool valid = row < B;
+    // ---- encoding of this thread's query into the A tile (K = kp0)
+    {
+      float qv[6];
+#pragma unroll
+      for (int d = 0; d < 6; ++d) qv[d] = valid ? __ldg(q + 6 * row + d) : 0.f;
+      const float s = FP8 ? A.L[0].inv_s_in : 1.f;   // input scale of layer 0 (fp8)
+      float buf[16];
+      int nb = 0, col = 0;
+      for (int d = 0; d < 6; ++d) {
+        for (int k = 0; k < F; ++k) {
+          float sn, cs;
+          sincospif(ldexpf(qv[d], k), &sn, &cs);
+          buf[nb++] = sn * s;
+          buf[nb++] = cs * s;
+          if (nb == 16) { store16<PREC>(a_tile, kp0, tid, col, buf); col += 16; nb = 0; }
+        }
+      }
+      while (col < (int)kp0) {      // zero padding up to the MMA K step
+        for (int i = nb; i < 16; ++i) buf[i] = 0.f;
+        store16<PREC>(a_tile, kp0, tid, col, buf);
+        col += 16;
+        nb = 0;
+      }
+    }
+    float y0 = 0.f, y1 = 0.f, y2 = 0.f;
+    for (int l = 0; l < A.n_hidden; ++l) {
+      const TcLayer Ly = A.L[l];
+      fence_proxy_async();
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      if (tid == 0) {
+        const uint32_t a0 = smem_u32(a_tile), b0 = smem_u32(smem + Ly.w_off);
+        const uint32_t sbo = (Ly.kp * EB / 16) * 128;
+        const uint32_t id = idesc(AB_TYPE, (uint32_t)H);
+        const int nk = (int)(Ly.kp / A.kstep);
+        for (int ks = 0; ks < nk; ++ks) {
+          // a K step spans 32 bytes = two core matrices along K, so the start
+          // address advances by 2 * LBO = 256 bytes
+          const uint64_t ad = sdesc(a0 + ks * 256, 128, sbo);
+          const uint64_t bd = sdesc(b0 + ks * 256, 128, sbo);
+          mma<FP8>(tmem, ad, bd, id, ks > 0 ? 1u : 0u);
+        }
+        mma_commit(bar_mma);
+      }
+      if (!mbar_wait(bar_mma, mma_phase)) {
+        atomicOr(err, PFE_ITER_CAP);
+        *abort_flag = 1;
+      }
+      mma_phase ^= 1u;
+      tc_fence_after();
+      if (*abort_flag) break;
+      const bool last = (l == A.n_hidden - 1);
+      const uint32_t kp_next = last ? 0u : A.L[l + 1].kp;
+      const float s_next = (FP8 && !last) ? A.L[l + 1].inv_s_in : 1.f;
+      for (int c0 = 0; c0 < H; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] * Ly.dequant, 0.f);
+        if (last) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            y0 = fmaf(v[i], w_out[c0 + i], y0);
+            y1 = fmaf(v[i], w_out[H + c0 + i], y1);
+            y2 = fmaf(v[i], w_out[2 * H + c0 + i], y2);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] *= s_next;
+          store16<PREC>(a_tile, kp_next, tid, c0, v);
+        }
+      }
+    }
+    if (*abort_flag) break;
+    if (valid) {
+      if (slot_idx) {
+        uint32_t sl = slot_idx[row];
+        slot_li[3 * (size_t)sl + 0] = slot_alb[3 * row + 0] * exp10f(-A.psi * y0);
+        slot_li[3 * (size_t)sl + 1] = slot_alb[3 * row + 1] * exp10f(-A.psi * y1);
+        slot_li[3 * (size_t)sl + 2] = slot_alb[3 * row + 2] * exp10f(-A.psi * y2);
+      } else {
+        out[3 * row + 0] = y0;
+        out[3 * row + 1] = y1;
+        out[3 * row + 2] = y2;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u));
+}
+
+// ---------------------------------------------------------------- weight packing
+// Hidden layer l packed K-major in 8 x 16-byte core matrices:
+//   byte(n, k) = ((n/8) * (kp*eb/16) + (k*eb)/16) * 128 + (n%8) * 16 + (k*eb)%16
+// values = operand rounding of W (fp8: code of W / s_w), zero for k >= fan_in.
+__global__ void k_pack(const float* __restrict__ w, int64_t w_off, int n_out, int fan_in, int kp, int prec, float inv_s,
+                       uint8_t* __restrict__ dst) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n_out * kp) return;
+  int n = (int)(e / kp), k = (int)(e % kp);
+  float x = k < fan_in ? w[w_off + (int64_t)n * fan_in + k] : 0.f;
+  int eb = prec == PF_PREC_FP8 ? 1 : 2;
+  uint32_t off = (uint32_t)((n >> 3) * (kp * eb / 16) + (k * eb) / 16) * 128 + (uint32_t)(n & 7) * 16 + (uint32_t)((k * eb) % 16);
+  if (prec == PF_PREC_FP8) dst[off] = pff::e4m3_code(x * inv_s);
+  else if (prec == PF_PREC_BF16) *(__nv_bfloat16*)(dst + off) = __float2bfloat16_rn(x);
+  else *(__half*)(dst + off) = __float2half_rn(x);
+}
+
 struct Bounds { int64_t b[10]; float s_w[8]; int n; };
 
-// Hidden-layer weights rounded to the field precision (fp8: per-layer scale).
+// Hidden-layer weights rounded to the field precision (fp8: per-layer scale),
+// as float values, for the SIMT path.
 __global__ void k_round_weights(const float* __restrict__ w, float* __restrict__ wr, Bounds B, int prec) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= B.b[B.n]) return;
@@ -22,7 +346,79 @@ __global__ void k_round_weights(const float* __restrict__ w, float* __restrict__
   while (l + 1 < B.n && i >= B.b[l + 1]) ++l;
   wr[i] = pff::round_prec(w[i], prec, B.s_w[l]);
 }
+
+// Shared-memory plan of a field for k_tc_forward.
+bool plan(const pf_field* f, TcArgs* A) {
+  const int prec = f->desc.prec;
+  if (prec == PF_PREC_F32) return false;
+  const int H = f->desc.hidden;
+  if (H != 64 && H != 128) return false;
+  const int nh = f->n_layers - 1;
+  if (nh < 1 || nh > kMaxLayers) return false;
+  const uint32_t eb = prec == PF_PREC_FP8 ? 1 : 2;
+  A->kstep = prec == PF_PREC_FP8 ? 32 : 16;
+  A->n_hidden = nh;
+  A->hidden = H;
+  A->in_freqs = f->desc.in_freqs;
+  A->prec = prec;
+  A->psi = f->desc.psi;
+  uint32_t off = 0, kmax = 0;
+  for (int l = 0; l < nh; ++l) {
+    uint32_t k = (uint32_t)f->fan_in[l];
+    uint32_t kp = (k + A->kstep - 1) / A->kstep * A->kstep;
+    A->L[l].w_off = off;
+    A->L[l].kp = kp;
+    off += (uint32_t)H * kp * eb;
+    kmax = std::max(kmax, kp);
+    float s_a = prec == PF_PREC_FP8 ? f->scales_host[l] : 1.f;
+    float s_w = prec == PF_PREC_FP8 ? f->scales_host[16 + l] : 1.f;
+    A->L[l].dequant = s_a * s_w;
+    A->L[l].inv_s_in = prec == PF_PREC_FP8 ? 1.f / s_a : 1.f;
+  }
+  A->wq_bytes = off;
+  A->a_off = (off + 1023) / 1024 * 1024;
+  A->a_bytes = kTileM * kmax * eb;
+  A->wout_off = A->a_off + A->a_bytes;
+  A->bar_off = A->wout_off + 3 * H * 4;
+  A->bar_off = (A->bar_off + 15) / 16 * 16;
+  A->smem_bytes = A->bar_off + 64;
+  return A->smem_bytes <= 227 * 1024;
+}
+
 }  // namespace
+
+pf_status pf_tc_available(const pf_field* f) {
+  TcArgs A;
+  return plan(f, &A) ? PF_OK : PF_ERR_UNSUPPORTED;
+}
+
+pf_status pf_tc_forward(pf_ctx* ctx, const pf_field* f, const float* q, int64_t B_max, const uint32_t* B_dev, float* out,
+                        const uint32_t* slot_idx, const float* slot_alb, float* slot_li) {
+  if (B_max <= 0) return PF_OK;
+  TcArgs A;
+  if (!plan(f, &A)) return pf_fail(ctx, PF_ERR_UNSUPPORTED, "field shape not supported by the tensor-core path");
+  A.wq = (const uint8_t*)f->wq;
+  A.w_out = f->w + f->layer_off[f->n_layers - 1];
+  int64_t tiles = (B_max + kTileM - 1) / kTileM;
+  int per_sm = A.smem_bytes <= 113 * 1024 ? 2 : 1;
+  int grid = (int)std::min<int64_t>(tiles, (int64_t)ctx->num_sms * per_sm);
+  auto launch = [&](auto kern) -> pf_status {
+    PF_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)A.smem_bytes));
+    kern<<<grid, kThreads, A.smem_bytes, ctx->stream>>>(A, q, B_max, B_dev, out, slot_idx, slot_alb, slot_li,
+                                                         ctx->err_dev);
+    PF_CUDA(ctx, cudaGetLastError());
+    return PF_OK;
+  };
+  if (f->desc.prec == PF_PREC_BF16) return launch(k_tc_forward<PF_PREC_BF16>);
+  if (f->desc.prec == PF_PREC_F16) return launch(k_tc_forward<PF_PREC_F16>);
+  return launch(k_tc_forward<PF_PREC_FP8>);
+}
+
+pf_status pf_tc_backward_available(const pf_field*) { return PF_ERR_UNSUPPORTED; }
+
+pf_status pf_tc_backward(pf_ctx* ctx, const pf_field*, const float*, const float*, const float*, int64_t, float*, float*) {
+  return pf_fail(ctx, PF_ERR_UNSUPPORTED, "tensor-core backward not built");
+}
 
 pf_status pf_field_pack(pf_ctx* ctx, pf_field* f) {
   if (f->desc.prec == PF_PREC_F32) return PF_OK;
@@ -36,6 +432,22 @@ pf_status pf_field_pack(pf_ctx* ctx, pf_field* f) {
   for (int l = 0; l < 8; ++l) B.s_w[l] = f->scales_host[16 + l] > 0.f ? f->scales_host[16 + l] : 1.f;
   int64_t n = B.b[B.n];
   k_round_weights<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(f->w, f->wr, B, f->desc.prec);
+  PF_CUDA(ctx, cudaGetLastError());
+  TcArgs A;
+  if (!plan(f, &A)) return PF_OK;
+  if (!f->wq || f->wq_bytes < A.wq_bytes) {
+    cudaFree(f->wq);
+    f->wq = nullptr;
+    if (cudaMalloc(&f->wq, A.wq_bytes) != cudaSuccess) return pf_fail(ctx, PF_ERR_OOM, "field pack");
+    f->wq_bytes = A.wq_bytes;
+  }
+  for (int l = 0; l < A.n_hidden; ++l) {
+    int64_t ne = (int64_t)A.hidden * A.L[l].kp;
+    float s_w = f->desc.prec == PF_PREC_FP8 && f->scales_host[16 + l] > 0.f ? f->scales_host[16 + l] : 1.f;
+    k_pack<<<(unsigned)((ne + 255) / 256), 256, 0, ctx->stream>>>(f->w, f->layer_off[l], A.hidden, f->fan_in[l],
+                                                                  (int)A.L[l].kp, f->desc.prec, 1.f / s_w,
+                                                                  (uint8_t*)f->wq + A.L[l].w_off);
+  }
   PF_CUDA(ctx, cudaGetLastError());
   return PF_OK;
 }

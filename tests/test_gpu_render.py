@@ -128,3 +128,64 @@ def test_rmse_reduction(pf_ctx):
     r = api.image_rmse(pf_ctx, a, b)
     want = math.sqrt(((a.double() - b.double()) ** 2).mean().item())
     assert abs(r - want) < 1e-12 * want
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_tracking_with_tensor_core_field(pf_ctx, orc, prec):
+    """Tracking renderer with a tensor-core field: the direct part is the
+    oracle's float32 tracking; the field part follows the precision-emulated
+    oracle (L' within 2e-2, i.e. L_i within ~25%; typically ~1e-3)."""
+    from oracle import field as F
+    sc = I.scene_judge(32, 40, 30, 4)
+    vol = api.Volume.from_inputs(sc.volume)
+    hidden = 128 if prec == "fp8" else 64
+    fld = api.Field(pf_ctx, 12, hidden, 4, prec, 5.0, seed=31)
+    desc = F.FieldDesc(12, hidden, 4, {"bf16": F.PREC_BF16, "fp8": F.PREC_FP8}[prec], 5.0, 31)
+    w = F.init_weights(desc).astype(np.float64)
+    # shrink the untrained field's output so decoded radiance stays O(direct)
+    w[-3 * hidden:] *= 0.05
+    wt = torch.from_numpy(w.astype(np.float32)).cuda()
+    fld.set_weights(wt)
+    scales = None
+    if prec == "fp8":
+        cal = np.random.default_rng(2).uniform(0, 1, (4096, 6)).astype(np.float32)
+        fld.calibrate_fp8(torch.from_numpy(cal).cuda())
+        scales = F.fp8_calibrate(w, cal.astype(np.float64), desc)
+    g = 0.3
+    img = api.render_neural(pf_ctx, vol, sc.lights, g, sc.camera, sc.spp, 0.0, seed=8, field=fld)
+    pf_ctx.sync()
+    ref, cs, Li = orc.render_neural(sc.volume, sc.lights, g, sc.camera, sc.spp, 0.0, 8, weights=w, desc=desc,
+                                    scales=scales, fp32=True, return_parts=True)
+    assert Li.max() > 0
+    err = _rel_err(img.cpu().numpy(), ref)
+    assert np.median(err) < 5e-3, np.median(err)
+    assert err.max() < 0.3, err.max()
+
+
+def test_large_render_sampled_rows(pf_ctx, orc):
+    """Full-size large-render workload (1024^3 f16 turbulence, 8 lights,
+    1920x1080, 16 spp, fp8 4x128 field, tracking), in the launch the
+    benchmark times; sampled rows are recomputed by the oracle."""
+    from oracle import field as F
+    vol_t, tf, lights, cams = I.large_scene_parts(1024, device="cuda")
+    tf_t = torch.from_numpy(tf).cuda()
+    vol = api.Volume(vol_t.contiguous(), 20.0, 0.9, tf_t)
+    fld = api.Field(pf_ctx, 12, 128, 4, "fp8", 5.0, seed=5)
+    desc = F.FieldDesc(12, 128, 4, F.PREC_FP8, 5.0, 5)
+    w = F.init_weights(desc).astype(np.float64)
+    w[-3 * 128:] *= 0.05
+    fld.set_weights(torch.from_numpy(w.astype(np.float32)).cuda())
+    cal = np.random.default_rng(3).uniform(0, 1, (4096, 6)).astype(np.float32)
+    fld.calibrate_fp8(torch.from_numpy(cal).cuda())
+    scales = F.fp8_calibrate(w, cal.astype(np.float64), desc)
+    cam, g = cams[7], I.frame_g(11, 7)
+    img = api.render_neural(pf_ctx, vol, lights, g, cam, 16, 0.0, seed=99, field=fld)
+    pf_ctx.sync()
+    vh = I.Volume(vol_t.cpu().numpy(), 20.0, 0.9, tf)
+    for y0 in (500, 700):
+        ref = orc.render_neural(vh, lights, g, cam, 16, 0.0, 99, weights=w, desc=desc, scales=scales, fp32=True,
+                                rows=(y0, y0 + 1))
+        got = img[y0:y0 + 1].cpu().numpy()
+        assert ref.max() > 0
+        err = _rel_err(got, ref)
+        assert np.median(err) < 5e-3 and err.max() < 0.3, (y0, np.median(err), err.max())
