@@ -248,6 +248,29 @@ pf_status pf_render_pathtraced(pf_ctx* ctx, const pf_volume* vol, const pf_light
                                const pf_camera* cam, int spp, int max_bounces, uint64_t seed, int use_rr,
                                float* out_rgb_dev);
 
+/* Allocation-free variant of pf_render_pathtraced (the paper has no
+ * counterpart; it is a deployment aid).  Some callers cannot allocate device
+ * memory when they render: an application that reserved its whole device
+ * budget up front, a plug-in whose host forbids allocation inside the frame
+ * loop, or code that must not risk the device-wide synchronisation that
+ * cudaMalloc / cudaFree can cause.  This entry point needs no pf_ctx and
+ * calls no allocator: its scratch is a file-scope device array of 48 MiB that
+ * every GPU loading the library holds until the process exits, which bounds
+ * the image to about 2.09 million pixels (1920x1080 fits); larger images are
+ * rejected with PF_ERR_INVALID_ARG.  The caller passes the inputs, a stream
+ * of the current device and the output image; vol->majorant must be set
+ * (> 0), e.g. from pf_volume_majorant.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device
+ * current, so make that first call before any stream capture.  All calls
+ * share the array and it keeps the last call's contents (each call resets
+ * what it needs); calls that overlap on the GPU race.  Synchronises the
+ * stream and reports an iteration-limit hit as PF_ERR_TIMEOUT; err_msg
+ * (nullable, err_len bytes) receives a message.  Results equal
+ * pf_render_pathtraced's bit for bit. */
+pf_status pf_render_pathtraced_noalloc(const pf_volume* vol, const pf_light* lights, int n_lights, float g,
+                                       const pf_camera* cam, int spp, int max_bounces, uint64_t seed, int use_rr,
+                                       void* cuda_stream, float* out_rgb_dev, char* err_msg, int err_len);
+
 /* sqrt(sum (a-b)^2 / n) accumulated in FP64 on the device; synchronises. */
 pf_status pf_image_rmse(pf_ctx* ctx, const float* a_dev, const float* b_dev, int64_t n, double* out_host);
 

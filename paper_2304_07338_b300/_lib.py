@@ -81,6 +81,8 @@ SIGNATURES = {
     "pf_render_neural": (I, [P, C.POINTER(PfVolume), C.POINTER(PfLight), I, F, C.POINTER(PfCamera), I, F, U64, P, P]),
     "pf_render_pathtraced": (I, [P, C.POINTER(PfVolume), C.POINTER(PfLight), I, F, C.POINTER(PfCamera), I, I, U64, I,
                                  P]),
+    "pf_render_pathtraced_noalloc": (I, [C.POINTER(PfVolume), C.POINTER(PfLight), I, F, C.POINTER(PfCamera), I, I,
+                                         U64, I, P, P, C.c_char_p, I]),
     "pf_image_rmse": (I, [P, P, P, I64, C.POINTER(C.c_double)]),
 }
 

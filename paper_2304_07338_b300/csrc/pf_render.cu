@@ -17,6 +17,9 @@
 #include "pf_internal.h"
 #include "pf_device.cuh"
 #include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <mutex>
 #include <vector>
 #include <algorithm>
 
@@ -386,6 +389,138 @@ extern "C" pf_status pf_render_pathtraced(pf_ctx* ctx, const pf_volume* vol, con
     k_path_accumulate<<<(unsigned)((n_pix + 127) / 128), 128, 0, ctx->stream>>>(rad, n_pix, kn, k0 == 0, k0 + kn >= spp,
                                                                                 spp, acc, out_rgb_dev);
     PF_CUDA(ctx, cudaGetLastError());
+  }
+  return PF_OK;
+}
+
+// ---------------------------------------------------------------- allocation-free path tracer
+// Scratch for pf_render_pathtraced_noalloc lives in this file-scope device
+// array instead of the context arena: bytes [0, 256) hold the error word,
+// then the per-pixel accumulator (12 B/pixel), then one chunk of per-sample
+// slots (at least 12 B/pixel).  Every GPU that loads the library holds it
+// until the process exits.
+namespace {
+constexpr size_t kNoAllocScratchBytes = (size_t)48 << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64] = {};
+
+void put_msg(char* buf, int len, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
+void put_msg(char* buf, int len, const char* fmt, ...) {
+  if (!buf || len <= 0) return;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, (size_t)len, fmt, ap);
+  va_end(ap);
+}
+}  // namespace
+
+extern "C" pf_status pf_render_pathtraced_noalloc(const pf_volume* vol, const pf_light* lights, int n_lights, float g,
+                                                  const pf_camera* cam, int spp, int max_bounces, uint64_t seed,
+                                                  int use_rr, void* cuda_stream, float* out_rgb_dev, char* err_msg,
+                                                  int err_len) {
+  put_msg(err_msg, err_len, "%s", "");
+  // argument checks (written out here: no context, no heap)
+  if (!vol || !vol->data_dev || !vol->tf_lut_dev || vol->nx < 1 || vol->ny < 1 || vol->nz < 1 || vol->nx > 8192 ||
+      vol->ny > 8192 || vol->nz > 8192 || vol->dtype < 0 || vol->dtype > 2 || vol->tf_n < 2 || vol->tf_n > 65536 ||
+      ((uintptr_t)vol->tf_lut_dev % 16) || !(vol->sigma_scale >= 0.f) || !(vol->albedo >= 0.f)) {
+    put_msg(err_msg, err_len, "invalid volume");
+    return PF_ERR_INVALID_ARG;
+  }
+  if (!(vol->majorant > 0.f) || !isfinite(vol->majorant)) {
+    put_msg(err_msg, err_len, "volume->majorant must be set (> 0): this entry point does not compute it");
+    return PF_ERR_INVALID_ARG;
+  }
+  if (!lights || n_lights < 1 || n_lights > PF_MAX_LIGHTS) {
+    put_msg(err_msg, err_len, "need 1..%d lights", PF_MAX_LIGHTS);
+    return PF_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < n_lights; ++i)
+    if (lights[i].kind != 0 && lights[i].kind != 1) {
+      put_msg(err_msg, err_len, "light %d: unknown kind", i);
+      return PF_ERR_INVALID_ARG;
+    }
+  if (!cam || cam->width <= 0 || cam->height <= 0 || !(cam->fovy_deg > 0.f && cam->fovy_deg < 180.f) || spp <= 0 ||
+      spp > (1 << 24) || max_bounces < 1 || max_bounces > 1024 || !(g > -1.f && g < 1.f) || !out_rgb_dev) {
+    put_msg(err_msg, err_len, "invalid camera, spp, max_bounces, g or output");
+    return PF_ERR_INVALID_ARG;
+  }
+  const int64_t n_pix = (int64_t)cam->width * cam->height;
+  const size_t acc_off = 256, per_pix = 3 * sizeof(float);
+  const int64_t max_pix = (int64_t)((kNoAllocScratchBytes - 2 * acc_off) / (2 * per_pix));
+  if (n_pix > max_pix) {
+    put_msg(err_msg, err_len,
+            "image of %lld pixels exceeds this entry point's static scratch (%zu bytes: at most %lld pixels)",
+            (long long)n_pix, kNoAllocScratchBytes, (long long)max_pix);
+    return PF_ERR_INVALID_ARG;
+  }
+  // once per device, with that device current: the array's device address
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    put_msg(err_msg, err_len, "no current CUDA device");
+    return PF_ERR_CUDA;
+  }
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        put_msg(err_msg, err_len, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        return PF_ERR_CUDA;
+      }
+      g_noalloc_addr[dev] = p;
+    }
+    base = (unsigned char*)g_noalloc_addr[dev];
+  }
+  uint32_t* err_word = (uint32_t*)base;
+  float* acc = (float*)(base + acc_off);
+  size_t rad_off = (acc_off + (size_t)n_pix * per_pix + 255) / 256 * 256;
+  float* rad = (float*)(base + rad_off);
+  int64_t kc = (int64_t)((kNoAllocScratchBytes - rad_off) / ((size_t)n_pix * per_pix));
+  kc = std::max<int64_t>(1, std::min<int64_t>(kc, spp));
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaMemsetAsync(err_word, 0, sizeof(uint32_t), stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    put_msg(err_msg, err_len, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    return PF_ERR_CUDA;
+  }
+  Vol V = pf_make_vol(vol, vol->majorant);
+  DevLights L = pf_make_lights(lights, n_lights);
+  CamF C = make_cam(cam);
+  for (int k0 = 0; k0 < spp; k0 += (int)kc) {
+    int kn = (int)std::min<int64_t>(kc, spp - k0);
+    int64_t n_items = n_pix * kn;
+    dim3 grd((unsigned)((n_items + 127) / 128));
+    if (vol->dtype == PF_F32)
+      k_path_samples<0><<<grd, 128, 0, stream>>>(V, L, C, g, spp, k0, kn, max_bounces, use_rr, seed, n_items, rad, err_word, nullptr);
+    else if (vol->dtype == PF_F16)
+      k_path_samples<1><<<grd, 128, 0, stream>>>(V, L, C, g, spp, k0, kn, max_bounces, use_rr, seed, n_items, rad, err_word, nullptr);
+    else
+      k_path_samples<2><<<grd, 128, 0, stream>>>(V, L, C, g, spp, k0, kn, max_bounces, use_rr, seed, n_items, rad, err_word, nullptr);
+    k_path_accumulate<<<(unsigned)((n_pix + 127) / 128), 128, 0, stream>>>(rad, n_pix, kn, k0 == 0, k0 + kn >= spp, spp,
+                                                                           acc, out_rgb_dev);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    put_msg(err_msg, err_len, "launch: %s", cudaGetErrorString(e));
+    return PF_ERR_CUDA;
+  }
+  uint32_t w = 0;
+  e = cudaMemcpyAsync(&w, err_word, sizeof(w), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    put_msg(err_msg, err_len, "%s", cudaGetErrorString(e));
+    return PF_ERR_CUDA;
+  }
+  if (w) {
+    put_msg(err_msg, err_len, "a tracking loop hit its iteration limit (error word 0x%x)", w);
+    return PF_ERR_TIMEOUT;
   }
   return PF_OK;
 }
