@@ -102,8 +102,9 @@ class Clocks:
 
 def setup_scene(device):
     import torch
-    from paper_2304_07338_b300 import api, inputs as I
+    from paper_2304_07338_b300 import inputs as I
     vol_t, tf, lights, cams = I.large_scene_parts(N_VOX, device=device)
+    cams = [I.Camera(c.eye, c.at, c.up, c.fovy_deg, W_, H_) for c in cams]
     return vol_t.contiguous(), torch.from_numpy(tf).to(device), lights, cams
 
 
@@ -134,7 +135,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=2)
+    ap.add_argument("--res", type=int, default=N_VOX, help="volume resolution (profiling: smaller case)")
+    ap.add_argument("--width", type=int, default=W_)
+    ap.add_argument("--height", type=int, default=H_)
+    ap.add_argument("--spp", type=int, default=SPP)
     args = ap.parse_args()
+    global W_, H_, SPP, N_VOX
+    W_, H_, SPP, N_VOX = args.width, args.height, args.spp, args.res
     args.warmup = max(args.warmup, 3)
 
     rank = int(os.environ.get("RANK", "0"))
@@ -252,8 +259,8 @@ def main():
         "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "fp8 field / f32 tracking", "data": "synthetic",
-        "config": {"workload": "large neural render: 1024^3 f16 turbulence, 8 point lights, 1920x1080, 16 spp, "
-                               "fp8 4x128 field, delta/ratio tracking",
+        "config": {"workload": "large neural render: %d^3 f16 turbulence, 8 point lights, %dx%d, %d spp, "
+                               "fp8 4x128 field, delta/ratio tracking" % (N_VOX, W_, H_, SPP),
                    "frames": "60-frame orbit", "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (2 GiB volume)"},
         "queries_per_s": qpf * fps,
