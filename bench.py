@@ -128,6 +128,7 @@ def cpu_baseline(vol_host, tf, lights, cams, seed, rows=2, weights=None, desc=No
 
 
 def main():
+    global W_, H_, SPP, N_VOX
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -140,7 +141,6 @@ def main():
     ap.add_argument("--height", type=int, default=H_)
     ap.add_argument("--spp", type=int, default=SPP)
     args = ap.parse_args()
-    global W_, H_, SPP, N_VOX
     W_, H_, SPP, N_VOX = args.width, args.height, args.spp, args.res
     args.warmup = max(args.warmup, 3)
 
