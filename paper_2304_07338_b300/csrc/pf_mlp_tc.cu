@@ -22,14 +22,15 @@
 // and returns.
 #include "pf_internal.h"
 #include "pf_field_common.cuh"
+#include "pf_tc_ptx.cuh"
 #include <algorithm>
+
+using namespace pftc;
 
 namespace {
 
-constexpr int kTileM = 128;
 constexpr int kThreads = 128;
 constexpr int kMaxLayers = 8;
-constexpr uint32_t kSpin = 1u << 22;   // bounded mbarrier polls
 
 struct TcLayer {
   uint32_t w_off;      // byte offset of the layer's packed weights in shared memory
@@ -47,84 +48,6 @@ struct TcArgs {
   float psi;
   TcLayer L[kMaxLayers];
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kSpin; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// Shared-memory matrix descriptor: K-major, no swizzle; LBO = byte distance
-// between core matrices adjacent in K, SBO = between 8-row groups.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version of tcgen05
-  return d;
-}
-
-// Instruction descriptor: D = f32, A/B type code, both K-major, M = 128, N.
-__device__ __forceinline__ uint32_t idesc(uint32_t ab_type, uint32_t n) {
-  return (1u << 4) | (ab_type << 7) | (ab_type << 10) | ((n >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
-}
-
-template <bool FP8>
-__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
-  if (FP8)
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-            tmem_d),
-        "l"(a), "l"(b), "r"(id), "r"(acc));
-  else
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-            tmem_d),
-        "l"(a), "l"(b), "r"(id), "r"(acc));
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-// 16 consecutive fp32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 // Operand encoding of one value for the A tile.
 template <int PREC>
@@ -198,11 +121,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_forward(TcArgs A, const floa
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   for (int i = tid; i < 3 * H; i += kThreads) w_out[i] = A.w_out[i];
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(128u));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
+  if (warp == 0) tmem_alloc(tmem_slot, 128u);
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
@@ -315,7 +234,287 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_forward(TcArgs A, const floa
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u));
+  if (warp == 0) tmem_dealloc(tmem, 128u);
+}
+
+// ---------------------------------------------------------------- training step
+// One fused pass per 128-query tile (bf16 / fp16 fields of width 64):
+//   forward  : encoding -> A_0; for each hidden layer l, tcgen05.mma
+//              A_l x W_l^T -> TMEM, ReLU, operand rounding -> A_{l+1}
+//              (every layer's input tile stays in shared memory);
+//   output   : y = W_out h_L in float32 from registers; relative-MSE gradient
+//              dy = 2 (y - t) / (t^2 + 0.01) / (3B) (or a given dy); loss;
+//              dW_out by warp reductions; dZ_{L-1} = (W_out^T dy) * [h_L > 0];
+//   backward : for l = L-1..0, tcgen05.mma dW_l += dZ_l^T x A_l (both operands
+//              MN-major views of the row tiles, M padded to 128 neurons) into
+//              a TMEM accumulator that persists across the CTA's tiles, and
+//              dA_l = dZ_l x W_l (W_l as an MN-major B operand); epilogue
+//              masks with [A_l > 0] and rounds into dZ_{l-1}.
+// At the end each CTA writes its dW (float32) to its own partial row; a
+// second kernel sums the partials in a fixed order.
+struct TrArgs {
+  TcArgs f;                 // forward plan (weights, A-tile K extents)
+  uint32_t a_off[kMaxLayers];   // shared-memory byte offset of A_l
+  uint32_t d_off;           // dZ tile (128 x 128 neurons, padded)
+  uint32_t dwo_off;         // dW_out accumulator (3 x H float32)
+  uint32_t dw_col[kMaxLayers];  // TMEM column of dW_l
+  int64_t layer_off[kMaxLayers + 1];
+  int64_t n_params;
+};
+constexpr uint32_t kTrainCols = 512;
+constexpr uint32_t kDK = 128;       // padded neuron extent of the dZ tile
+
+template <int PREC>
+__global__ void __launch_bounds__(kThreads, 1) k_tc_train(TrArgs T, const float* __restrict__ q,
+                                                          const float* __restrict__ targets,
+                                                          const float* __restrict__ dy_in, int64_t B, float inv_n,
+                                                          float* __restrict__ partial, float* __restrict__ loss,
+                                                          uint32_t* err) {
+  constexpr uint32_t AB_TYPE = (PREC == PF_PREC_BF16) ? 1u : 0u;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const TcArgs& A = T.f;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  float* w_out = (float*)(smem + A.wout_off);
+  float* dwo = (float*)(smem + T.dwo_off);
+  uint8_t* dtile = smem + T.d_off;
+  uint64_t* bars = (uint64_t*)(smem + A.bar_off);
+  uint32_t* tmem_slot = (uint32_t*)(smem + A.bar_off + 16);
+  int* abort_flag = (int*)(smem + A.bar_off + 20);
+  const uint32_t bar_w = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]);
+  const int H = A.hidden, L = A.n_hidden;
+
+  if (tid == 0) {
+    mbar_init(bar_w, 1);
+    mbar_init(bar_mma, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int i = tid; i < 3 * H; i += kThreads) { w_out[i] = A.w_out[i]; dwo[i] = 0.f; }
+  // zero the padded neuron columns of the dZ tile once (never written later)
+  for (int i = tid; i < (int)(kTileM * kDK * 2 / 16); i += kThreads) ((uint4*)dtile)[i] = make_uint4(0, 0, 0, 0);
+  if (warp == 0) tmem_alloc(tmem_slot, kTrainCols);
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  if (tid == 0) {
+    mbar_expect_tx(bar_w, A.wq_bytes);
+    bulk_g2s(smem_u32(smem), A.wq, A.wq_bytes, bar_w);
+  }
+  if (!mbar_wait(bar_w, 0) && tid == 0) { atomicOr(err, PFE_ITER_CAP); *abort_flag = 1; }
+  __syncthreads();
+  const int64_t n_tiles = (B + kTileM - 1) / kTileM;
+  uint32_t phase = 0;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const int F = A.in_freqs;
+  const uint32_t kp0 = A.L[0].kp;
+  const uint32_t d_rg = (kDK * 2 / 16) * 128;       // dZ tile: bytes between 8-row groups
+  bool first_tile = true;
+  float lsum = 0.f;
+
+  auto sync_mma = [&]() -> bool {
+    if (tid == 0) mma_commit(bar_mma);
+    bool ok = mbar_wait(bar_mma, phase);
+    phase ^= 1u;
+    tc_fence_after();
+    if (!ok) { atomicOr(err, PFE_ITER_CAP); *abort_flag = 1; }
+    return ok;
+  };
+  auto pre_mma = [&]() {
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  };
+
+  for (int64_t tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x) {
+    const int64_t row = tile * kTileM + tid;
+    const bool valid = row < B;
+    // ---- encoding -> A_0
+    {
+      uint8_t* a0 = smem + T.a_off[0];
+      float qv[6];
+#pragma unroll
+      for (int d = 0; d < 6; ++d) qv[d] = valid ? __ldg(q + 6 * row + d) : 0.f;
+      float buf[16];
+      int nb = 0, col = 0;
+      for (int d = 0; d < 6; ++d)
+        for (int k = 0; k < F; ++k) {
+          float sn, cs;
+          sincospif(ldexpf(qv[d], k), &sn, &cs);
+          buf[nb++] = sn;
+          buf[nb++] = cs;
+          if (nb == 16) { store16<PREC>(a0, kp0, tid, col, buf); col += 16; nb = 0; }
+        }
+      while (col < (int)kp0) {
+        for (int i = nb; i < 16; ++i) buf[i] = 0.f;
+        store16<PREC>(a0, kp0, tid, col, buf);
+        col += 16;
+        nb = 0;
+      }
+    }
+    // ---- forward through the hidden layers
+    float h[128];
+    for (int l = 0; l < L; ++l) {
+      const TcLayer Ly = A.L[l];
+      pre_mma();
+      if (tid == 0) {
+        const uint32_t a0 = smem_u32(smem + T.a_off[l]), b0 = smem_u32(smem + Ly.w_off);
+        const uint32_t sbo = (Ly.kp * 2 / 16) * 128;
+        const uint32_t id = idesc(AB_TYPE, (uint32_t)H);
+        for (int ks = 0; ks < (int)(Ly.kp / 16); ++ks)
+          mma<false>(tmem, sdesc(a0 + ks * 256, 128, sbo), sdesc(b0 + ks * 256, 128, sbo), id, ks > 0 ? 1u : 0u);
+      }
+      if (!sync_mma()) break;
+      for (int c0 = 0; c0 < H; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
+        if (l == L - 1) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) h[c0 + i] = v[i];
+        } else {
+          store16<PREC>(smem + T.a_off[l + 1], (uint32_t)H, tid, c0, v);
+        }
+      }
+    }
+    if (*abort_flag) break;
+    // ---- output layer, loss, dW_out, dZ_{L-1}
+    float dy[3];
+    {
+      float y[3] = {0.f, 0.f, 0.f};
+      for (int n = 0; n < H; ++n) {
+        y[0] = fmaf(h[n], w_out[n], y[0]);
+        y[1] = fmaf(h[n], w_out[H + n], y[1]);
+        y[2] = fmaf(h[n], w_out[2 * H + n], y[2]);
+      }
+      for (int c = 0; c < 3; ++c) {
+        if (!valid) { dy[c] = 0.f; continue; }
+        if (targets) {
+          float t = targets[3 * row + c];
+          float den = t * t + 0.01f;
+          float diff = y[c] - t;
+          lsum += diff * diff / den;
+          dy[c] = 2.f * diff / den * inv_n;
+        } else {
+          dy[c] = dy_in[3 * row + c];
+        }
+      }
+    }
+    // dW_out[c][n] += sum over rows of dy_c h_n (warp shuffles, then shared atomics)
+    for (int c = 0; c < 3; ++c)
+      for (int n = 0; n < H; ++n) {
+        float v = dy[c] * h[n];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) atomicAdd(&dwo[c * H + n], v);
+      }
+    for (int c0 = 0; c0 < H; c0 += 16) {
+      float v[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int n = c0 + i;
+        float dh = dy[0] * w_out[n] + dy[1] * w_out[H + n] + dy[2] * w_out[2 * H + n];
+        float hr = PREC == PF_PREC_BF16 ? pff::round_bf16(h[n]) : pff::round_f16(h[n]);
+        v[i] = hr > 0.f ? dh : 0.f;
+      }
+      store16<PREC>(dtile, kDK, tid, c0, v);
+    }
+    // ---- backward through the hidden layers
+    for (int l = L - 1; l >= 0; --l) {
+      const TcLayer Ly = A.L[l];
+      pre_mma();
+      if (tid == 0) {
+        // dW_l (+)= dZ_l^T A_l: A = dZ tile viewed MN-major (M = neurons, K = samples),
+        // B = A_l viewed MN-major (N = input features, K = samples); K steps of 16 samples
+        const uint32_t dz0 = smem_u32(dtile), al0 = smem_u32(smem + T.a_off[l]);
+        const uint32_t a_rg = (Ly.kp * 2 / 16) * 128;      // A_l: bytes between 8-row groups
+        const uint32_t idw = idesc(AB_TYPE, Ly.kp, 1u, 1u);
+        for (int ks = 0; ks < kTileM / 16; ++ks) {
+          const uint64_t ad = sdesc(dz0 + ks * 2 * d_rg, d_rg, 128);
+          const uint64_t bd = sdesc(al0 + ks * 2 * a_rg, a_rg, 128);
+          mma<false>(tmem + T.dw_col[l], ad, bd, idw, (first_tile && ks == 0) ? 0u : 1u);
+        }
+        if (l > 0) {
+          // dA_l = dZ_l W_l: A = dZ tile K-major (K = the layer's H output neurons),
+          // B = W_l viewed MN-major (N = input features, K = output neurons)
+          const uint32_t w0 = smem_u32(smem + Ly.w_off);
+          const uint32_t w_rg = (Ly.kp * 2 / 16) * 128;    // W_l: bytes between 8-neuron groups
+          const uint32_t ida = idesc(AB_TYPE, Ly.kp, 0u, 1u);
+          for (int ks = 0; ks < H / 16; ++ks) {
+            const uint64_t ad = sdesc(dz0 + ks * 256, 128, d_rg);
+            const uint64_t bd = sdesc(w0 + ks * 2 * w_rg, w_rg, 128);
+            mma<false>(tmem, ad, bd, ida, ks > 0 ? 1u : 0u);
+          }
+        }
+      }
+      if (!sync_mma()) break;
+      if (l > 0) {
+        // dZ_{l-1} = dA_l * [A_l > 0], rounded; A_l is the layer's (rounded) input tile
+        const uint8_t* al = smem + T.a_off[l];
+        const uint32_t kpl = A.L[l].kp;
+        for (int c0 = 0; c0 < (int)kpl; c0 += 16) {
+          float v[16];
+          tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            const uint32_t off = (uint32_t)(tid >> 3) * ((kpl * 2 / 16) * 128) + (uint32_t)(c0 / 8 + j) * 128 +
+                                 (uint32_t)(tid & 7) * 16;
+            const uint4 raw = *(const uint4*)(al + off);
+            const uint16_t* hv = (const uint16_t*)&raw;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const bool pos = (hv[i] & 0x8000u) == 0 && (hv[i] & 0x7FFFu) != 0;
+              if (!pos) v[8 * j + i] = 0.f;
+            }
+          }
+          store16<PREC>(dtile, kDK, tid, c0, v);
+        }
+      }
+    }
+    first_tile = false;
+  }
+  // ---- per-CTA partial dW: TMEM rows 0..H-1 (warps 0..H/32-1), then dW_out
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  float* part = partial + (size_t)blockIdx.x * (size_t)T.n_params;
+  if (!*abort_flag && warp < H / 32) {
+    const int m = warp * 32 + lane;                  // output neuron of this lane
+    for (int l = 0; l < L; ++l) {
+      const uint32_t kpl = A.L[l].kp;
+      const int fan = l == 0 ? 12 * F : H;
+      for (uint32_t c0 = 0; c0 < kpl; c0 += 16) {
+        float v[16];
+        if (first_tile) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] = 0.f;
+        } else {
+          tmem_ld16(tmem + lane_base + T.dw_col[l] + c0, v);
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          if ((int)c0 + i < fan) part[T.layer_off[l] + (int64_t)m * fan + c0 + i] = v[i];
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < 3 * H; i += kThreads) part[T.layer_off[L] + i] = dwo[i];
+  if (loss) {
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if (lane == 0 && lsum != 0.f) atomicAdd(loss, lsum * inv_n);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kTrainCols);
+}
+
+// dW = sum over CTAs of the partial rows, in CTA order.
+__global__ void k_reduce_partials(const float* __restrict__ partial, int n_parts, int64_t n, float* __restrict__ dw) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float s = 0.f;
+  for (int p = 0; p < n_parts; ++p) s += partial[(size_t)p * n + i];
+  dw[i] = s;
 }
 
 // ---------------------------------------------------------------- weight packing
@@ -414,10 +613,64 @@ pf_status pf_tc_forward(pf_ctx* ctx, const pf_field* f, const float* q, int64_t 
   return launch(k_tc_forward<PF_PREC_FP8>);
 }
 
-pf_status pf_tc_backward_available(const pf_field*) { return PF_ERR_UNSUPPORTED; }
+namespace {
+bool plan_train(const pf_field* f, TrArgs* T) {
+  if (f->desc.prec != PF_PREC_BF16 && f->desc.prec != PF_PREC_F16) return false;
+  if (f->desc.hidden != 64) return false;
+  if (!plan(f, &T->f)) return false;
+  const int L = T->f.n_hidden;
+  const int H = T->f.hidden;
+  uint32_t off = T->f.a_off;                 // weights first, then the activation tiles
+  uint32_t col = 128;
+  for (int l = 0; l < L; ++l) {
+    T->a_off[l] = off;
+    off += kTileM * T->f.L[l].kp * 2;
+    T->dw_col[l] = col;
+    col += T->f.L[l].kp;
+  }
+  if (col > kTrainCols) return false;
+  off = (off + 1023) / 1024 * 1024;
+  T->d_off = off;
+  off += kTileM * kDK * 2;
+  T->f.wout_off = off;
+  off += 3 * H * 4;
+  T->dwo_off = off;
+  off += 3 * H * 4;
+  T->f.bar_off = (off + 15) / 16 * 16;
+  T->f.smem_bytes = T->f.bar_off + 64;
+  for (int l = 0; l <= f->n_layers; ++l) T->layer_off[l] = f->layer_off[l];
+  T->n_params = f->n_params;
+  return T->f.smem_bytes <= 227 * 1024;
+}
+}  // namespace
 
-pf_status pf_tc_backward(pf_ctx* ctx, const pf_field*, const float*, const float*, const float*, int64_t, float*, float*) {
-  return pf_fail(ctx, PF_ERR_UNSUPPORTED, "tensor-core backward not built");
+pf_status pf_tc_backward_available(const pf_field* f) {
+  TrArgs T;
+  return plan_train(f, &T) ? PF_OK : PF_ERR_UNSUPPORTED;
+}
+
+pf_status pf_tc_backward(pf_ctx* ctx, const pf_field* f, const float* q, const float* dy, const float* targets,
+                         int64_t B, float* dw, float* loss) {
+  TrArgs T;
+  if (!plan_train(f, &T)) return pf_fail(ctx, PF_ERR_UNSUPPORTED, "field shape not supported by the tensor-core backward");
+  T.f.wq = (const uint8_t*)f->wq;
+  T.f.w_out = f->w + f->layer_off[f->n_layers - 1];
+  int64_t tiles = (B + kTileM - 1) / kTileM;
+  int grid = (int)std::min<int64_t>(tiles, (int64_t)ctx->num_sms);
+  float* partial;
+  PF_TRY(pf_scratch(ctx, WS_ACT, (size_t)grid * f->n_params * sizeof(float), (void**)&partial));
+  float inv_n = targets ? 1.0f / (float)(3 * B) : 0.f;
+  auto launch = [&](auto kern) -> pf_status {
+    PF_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T.f.smem_bytes));
+    kern<<<grid, kThreads, T.f.smem_bytes, ctx->stream>>>(T, q, targets, dy, B, inv_n, partial, loss, ctx->err_dev);
+    PF_CUDA(ctx, cudaGetLastError());
+    return PF_OK;
+  };
+  if (f->desc.prec == PF_PREC_BF16) { PF_TRY(launch(k_tc_train<PF_PREC_BF16>)); }
+  else { PF_TRY(launch(k_tc_train<PF_PREC_F16>)); }
+  k_reduce_partials<<<(unsigned)((f->n_params + 255) / 256), 256, 0, ctx->stream>>>(partial, grid, f->n_params, dw);
+  PF_CUDA(ctx, cudaGetLastError());
+  return PF_OK;
 }
 
 pf_status pf_field_pack(pf_ctx* ctx, pf_field* f) {
