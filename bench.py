@@ -140,6 +140,13 @@ def main():
     ap.add_argument("--width", type=int, default=W_)
     ap.add_argument("--height", type=int, default=H_)
     ap.add_argument("--spp", type=int, default=SPP)
+    ap.add_argument("--photons", type=int, default=1 << 20, help="photons per light per g for the caches")
+    ap.add_argument("--train-steps", type=int, default=600)
+    ap.add_argument("--train-batch", type=int, default=1 << 16)
+    ap.add_argument("--no-equal-rmse", action="store_true")
+    ap.add_argument("--rmse-width", type=int, default=480)
+    ap.add_argument("--rmse-height", type=int, default=270)
+    ap.add_argument("--ref-spp", type=int, default=4096)
     args = ap.parse_args()
     W_, H_, SPP, N_VOX = args.width, args.height, args.spp, args.res
     args.warmup = max(args.warmup, 3)
@@ -169,7 +176,23 @@ def main():
     vol_t, tf_t, lights, cams = setup_scene(dev)
     vol = api.Volume(vol_t, 20.0, 0.9, tf_t)
     vol.s.majorant = vol.majorant(ctx)
+    setup = {}
+    t0 = time.perf_counter()
+    cache = api.build_photon_cache(ctx, vol, lights, I.G_PAPER, args.photons, 16, 64, seed=seed + 1)
+    ctx.sync()
+    setup["photon_cache_s"] = time.perf_counter() - t0
+    setup["photons"] = int(cache.info.n_photons)
+    setup["records"] = int(cache.n_records)
     field = api.Field(ctx, FREQS, HIDDEN, N_HIDDEN, "fp8", 5.0, seed=seed)
+    if args.train_steps > 0:
+        trainer = api.Field(ctx, FREQS, HIDDEN, N_HIDDEN, "f16", 5.0, seed=seed)
+        t0 = time.perf_counter()
+        loss = trainer.train(cache, steps=args.train_steps, batch=args.train_batch, lr=1e-2, seed=seed + 2)
+        setup["field_training_s"] = time.perf_counter() - t0
+        setup["field_training"] = "%d steps x %d queries, 4x128 f16, loss %.4g -> %.4g" % (
+            args.train_steps, args.train_batch, float(loss[:5].mean()), float(loss[-5:].mean()))
+        field.set_weights(trainer.get_weights())
+        trainer.free()
     field.calibrate_fp8(calibration_queries().to(dev))
     out = torch.empty(H_, W_, 3, device=dev)
 
@@ -271,6 +294,11 @@ def main():
         "e2e": {"value": 1.0 / e2e_s, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps * (cam_n // max(args.steps, 1) + fld_n // max(args.steps, 1) + cmp_n // max(args.steps, 1)),
     }
+    line["setup"] = setup
+    if not args.no_equal_rmse:
+        line["equal_rmse"] = equal_rmse(ctx, vol, lights, frame, field, seed, args, fps)
+        line["vs_path_tracer_equal_rmse"] = line["equal_rmse"].get("speedup")
+    line["training_workload"] = training_workload(ctx, seed)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         try:
             line["cpu_baseline"] = cpu_baseline(vol_t.cpu().numpy(), tf_t.cpu().numpy(), lights, cams, seed,
@@ -289,6 +317,95 @@ def oracle_field(field):
     w = field.get_weights().cpu().numpy().astype(np.float64)
     s = field_scales(field)
     return dict(weights=w, desc=desc, scales=s)
+
+
+def equal_rmse(ctx, vol, lights, frame, field, seed, args, fps_neural):
+    """Equal-RMSE comparison with the plain path tracer (frame 0): the image
+    error of both renderers against a path-traced reference of ref_spp
+    samples per pixel, measured at a reduced resolution (same camera and
+    scene; each renderer's per-pixel error does not depend on the image
+    size), the path tracer's RMSE fitted as a/sqrt(spp) + b, the smallest
+    power-of-two spp reaching the neural render's RMSE, and that path
+    tracer's frames/s at the full resolution."""
+    import torch
+    from paper_2304_07338_b300 import api, inputs as I
+    cam, g = frame(0)
+    small = I.Camera(cam.eye, cam.at, cam.up, cam.fovy_deg, args.rmse_width, args.rmse_height)
+    t0 = time.perf_counter()
+    ref = api.render_pathtraced(ctx, vol, lights, g, small, args.ref_spp, 16, seed=seed + 7)
+    ctx.sync()
+    t_ref = time.perf_counter() - t0
+    neural = api.render_neural(ctx, vol, lights, g, small, SPP, 0.0, seed + 8, field)
+    direct = api.render_neural(ctx, vol, lights, g, small, SPP, 0.0, seed + 8, None)
+    ctx.sync()
+    r_n = api.image_rmse(ctx, neural, ref)
+    r_d = api.image_rmse(ctx, direct, ref)
+    spps, rms = [], []
+    spp = 1
+    while spp <= min(1024, args.ref_spp // 4):
+        img = api.render_pathtraced(ctx, vol, lights, g, small, spp, 16, seed=seed + 9)
+        ctx.sync()
+        spps.append(spp)
+        rms.append(api.image_rmse(ctx, img, ref))
+        spp *= 2
+    # least squares fit of rmse = a / sqrt(spp) + b
+    X = np.stack([1.0 / np.sqrt(spps), np.ones(len(spps))], 1)
+    a, b = np.linalg.lstsq(X, np.array(rms), rcond=None)[0]
+    need = None
+    for sp, r in zip(spps, rms):
+        if r <= r_n:
+            need = sp
+            break
+    if need is None:
+        need = int(2 ** math.ceil(math.log2(max(1.0, (a / max(r_n - b, 1e-12)) ** 2)))) if r_n > b else None
+    out = {"reference": "path tracer, %d spp, %dx%d, frame 0" % (args.ref_spp, args.rmse_width, args.rmse_height),
+           "reference_s": t_ref, "rmse_neural": r_n, "rmse_direct_only": r_d,
+           "pt_rmse_by_spp": dict(zip(map(str, spps), rms)), "pt_fit": {"a": float(a), "b": float(b)},
+           "pt_spp_at_equal_rmse": need}
+    if need is None:
+        out["note"] = "neural RMSE is below the path tracer's fitted floor"
+        return out
+    # path-tracer frames/s at that spp, full resolution
+    img = torch.empty(H_, W_, 3, device=torch.device("cuda", ctx.device))
+    api.render_pathtraced(ctx, vol, lights, g, cam, need, 16, seed=seed + 10, out=img)
+    ctx.sync()
+    n = 3
+    s_ev, e_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s_ev.record(ctx.stream)
+    for i in range(n):
+        api.render_pathtraced(ctx, vol, lights, g, cam, need, 16, seed=seed + 11 + i, out=img)
+    e_ev.record(ctx.stream)
+    torch.cuda.synchronize()
+    pt_fps = n / (s_ev.elapsed_time(e_ev) / 1e3)
+    out["pt_fps_at_equal_rmse"] = pt_fps
+    out["speedup"] = fps_neural / pt_fps
+    return out
+
+
+def training_workload(ctx, seed):
+    """Field-training workload: data-source caches (128^3 fBm, 2 point
+    lights, G = {-0.5, 0, 0.5}, 2^20 photons per light per g, 64^3 caches),
+    4x64 bf16 field, 2^18 queries per step, 2000 steps, lr 1e-2 (tcgen05
+    forward/backward)."""
+    import torch
+    from paper_2304_07338_b300 import api, inputs as I
+    sc = I.scene_judge()
+    vol = api.Volume.from_inputs(sc.volume)
+    t0 = time.perf_counter()
+    cache = api.build_photon_cache(ctx, vol, sc.lights, sc.g_set, 1 << 20, 16, 64, seed=seed + 20)
+    ctx.sync()
+    t_cache = time.perf_counter() - t0
+    fld = api.Field(ctx, 12, 64, 4, "bf16", 5.0, seed=seed + 21)
+    fld.train(cache, steps=5, batch=1 << 18, lr=1e-2, seed=seed + 22)      # warm-up
+    fld2 = api.Field(ctx, 12, 64, 4, "bf16", 5.0, seed=seed + 21)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = fld2.train(cache, steps=2000, batch=1 << 18, lr=1e-2, seed=seed + 22)
+    dt = time.perf_counter() - t0
+    flop = 3 * 2 * (144 * 64 + 3 * 64 * 64 + 3 * 64) * (1 << 18) * 2000
+    return {"steps_per_s": 2000 / dt, "train_s": dt, "loss_first": float(loss[:5].mean()),
+            "loss_last": float(loss[-20:].mean()), "photon_cache_s": t_cache, "photons_per_s": 6 * (1 << 20) / t_cache,
+            "records": int(cache.n_records), "model_tflops": flop / dt / 1e12}
 
 
 def calibration_queries():
