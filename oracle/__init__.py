@@ -47,6 +47,9 @@ def _declare(L):
     L.orc_majorant.argtypes = [i32, i32, i32, i32, P, f64, f64, P, i32, i32]
     L.orc_majorant.restype = f64
     L.orc_free_flight.argtypes = [i32, i32, i32, i32, P, f64, P, i32, P, P, i64, u64, P, P]
+    L.orc_brick_majorants.argtypes = [i32, i32, i32, i32, P, f64, P, i32, i32, P]
+    L.orc_ratio_mean.argtypes = [i32, i32, i32, i32, P, f64, P, i32, P, P, f64, i64, u64, P]
+    L.orc_ratio_mean.restype = f64
     L.orc_trace_photons.argtypes = [i32, i32, i32, i32, P, f64, f64, P, i32,
                                     P, P, P, i32, P, i32, u64, i32, i32, u64, i32, i32, u64, u64,
                                     P, P, P, P, P]
@@ -163,6 +166,26 @@ def density(vol, pts: np.ndarray, fp32: bool = False) -> np.ndarray:
 def majorant(vol, fp32: bool = False) -> float:
     v = _Vol(vol)
     return lib().orc_majorant(*v.args, v.ss, v.alb, *v.tfargs, int(fp32))
+
+
+def brick_majorants(vol, fp32: bool = False) -> np.ndarray:
+    """Majorant per 8^3 brick (x fastest), bounding sigma_t inside each brick."""
+    v = _Vol(vol)
+    nz, ny, nx = vol.data.shape
+    g = [(a + 7) // 8 for a in (nx, ny, nz)]
+    out = np.zeros(g[0] * g[1] * g[2])
+    lib().orc_brick_majorants(*v.args, v.ss, *v.tfargs, int(fp32), _p(out))
+    return out.reshape(g[2], g[1], g[0])
+
+
+def ratio_mean(vol, o, d, t_end: float, n: int, seed: int):
+    """Mean and variance of n ratio-tracking transmittance estimates."""
+    v = _Vol(vol)
+    o = np.ascontiguousarray(o, np.float64)
+    d = np.ascontiguousarray(d, np.float64)
+    var = np.zeros(1)
+    m = lib().orc_ratio_mean(*v.args, v.ss, *v.tfargs, _p(o), _p(d), float(t_end), n, seed, _p(var))
+    return m, float(var[0])
 
 
 def free_flight(vol, o, d, n: int, seed: int):

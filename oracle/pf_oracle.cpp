@@ -313,33 +313,143 @@ template <typename R> V3<R> hg_sample(R g, V3<R> d, R xi1, R xi2) {
     return normalize(nd);
 }
 
-// Delta (Woodcock) tracking from o along d inside [t, t_end).  Returns true
-// and the collision distance on a real collision.  One Philox block per
-// tentative collision: u0 -> free-flight distance, u1 -> accept test.
-template <typename R> bool delta_track(const Volume& V, R sbar, V3<R> o, V3<R> d, R t, R t_end, Rng& rng,
+// Brick majorant grid.  Brick (i,j,k) covers voxels [8i, 8i+8) per axis and
+// the region between the planes x = 8i/nx and min(8i+8, nx)/nx (same for y,
+// z).  Its majorant bounds sigma_t anywhere in that region: sigma_scale times
+// the largest TF alpha over the density range [dmin, dmax] of the voxels
+// trilinear interpolation can reach there (the brick plus a one-voxel apron;
+// bricks on the box boundary also include density 0, the value outside the
+// box), times (1 + 2^-10).
+constexpr int kBrick = 8;
+template <typename R> struct Grid {
+    int gx, gy, gz, nx, ny, nz;
+    std::vector<R> m;
+    R at(int i, int j, int k) const { return m[(size_t)i + (size_t)gx * ((size_t)j + (size_t)gy * k)]; }
+};
+
+template <typename R> R tf_alpha_max(const Volume& V, R dmin, R dmax) {
+    if (dmin < (R)0) dmin = (R)0;
+    if (dmax > (R)1) dmax = (R)1;
+    R a = std::max(tf_at<R>(V, dmin, 3), tf_at<R>(V, dmax, 3));
+    for (int i = 0; i < V.tf_n; ++i) {
+        R nd = (R)i / (R)(V.tf_n - 1);
+        if (nd >= dmin && nd <= dmax && (R)V.tf[4 * i + 3] > a) a = (R)V.tf[4 * i + 3];
+    }
+    return a;
+}
+
+template <typename R> Grid<R> build_grid(const Volume& V) {
+    Grid<R> G;
+    G.nx = V.nx; G.ny = V.ny; G.nz = V.nz;
+    G.gx = (V.nx + kBrick - 1) / kBrick; G.gy = (V.ny + kBrick - 1) / kBrick; G.gz = (V.nz + kBrick - 1) / kBrick;
+    G.m.assign((size_t)G.gx * G.gy * G.gz, (R)0);
+    for (int bz = 0; bz < G.gz; ++bz)
+        for (int by = 0; by < G.gy; ++by)
+            for (int bx = 0; bx < G.gx; ++bx) {
+                R dmin = (R)INFINITY, dmax = (R)-INFINITY;
+                for (int k = std::max(kBrick * bz - 1, 0); k <= std::min(kBrick * bz + kBrick, V.nz - 1); ++k)
+                    for (int j = std::max(kBrick * by - 1, 0); j <= std::min(kBrick * by + kBrick, V.ny - 1); ++j)
+                        for (int i = std::max(kBrick * bx - 1, 0); i <= std::min(kBrick * bx + kBrick, V.nx - 1); ++i) {
+                            R d = voxel<R>(V, i, j, k);
+                            if (d < dmin) dmin = d;
+                            if (d > dmax) dmax = d;
+                        }
+                if (bx == 0 || by == 0 || bz == 0 || bx == G.gx - 1 || by == G.gy - 1 || bz == G.gz - 1)
+                    if ((R)0 < dmin) dmin = (R)0;
+                G.m[(size_t)bx + (size_t)G.gx * ((size_t)by + (size_t)G.gy * bz)] =
+                    (R)V.sigma_scale * tf_alpha_max<R>(V, dmin, dmax) * (R)1.0009765625;
+            }
+    return G;
+}
+
+// Walk over the bricks a ray crosses (Amanatides-Woo stepping).  The brick
+// planes are at min(8i, n)/n; the first brick comes from the start point.
+template <typename R> struct Walk {
+    int c[3], s[3], g[3], n[3];
+    R tn[3];          // ray parameter of the next brick plane per axis
+    R o[3], d[3];
+    R plane_t(int a) const {
+        if (s[a] == 0) return (R)INFINITY;
+        int vi = s[a] > 0 ? std::min((c[a] + 1) * kBrick, n[a]) : c[a] * kBrick;
+        R p = (R)vi / (R)n[a];
+        return (p - o[a]) / d[a];
+    }
+    void init(const Grid<R>& G, V3<R> oo, V3<R> dd, R t) {
+        o[0] = oo.x; o[1] = oo.y; o[2] = oo.z; d[0] = dd.x; d[1] = dd.y; d[2] = dd.z;
+        g[0] = G.gx; g[1] = G.gy; g[2] = G.gz; n[0] = G.nx; n[1] = G.ny; n[2] = G.nz;
+        for (int a = 0; a < 3; ++a) {
+            R p = o[a] + t * d[a];
+            int ci = (int)std::floor(p * ((R)n[a] * (R)0.125));
+            c[a] = std::min(std::max(ci, 0), g[a] - 1);
+            s[a] = d[a] > (R)0 ? 1 : (d[a] < (R)0 ? -1 : 0);
+            tn[a] = plane_t(a);
+        }
+    }
+    R exit_t() const { return std::min(tn[0], std::min(tn[1], tn[2])); }
+    // step into the next brick; false when the ray leaves the grid
+    bool step() {
+        int a = (tn[0] <= tn[1] && tn[0] <= tn[2]) ? 0 : (tn[1] <= tn[2] ? 1 : 2);
+        c[a] += s[a];
+        if (c[a] < 0 || c[a] >= g[a]) return false;
+        tn[a] = plane_t(a);
+        return true;
+    }
+};
+
+// Delta (Woodcock) tracking over the brick majorants from o along d inside
+// [t, t_end): one Philox block per tentative collision (u0 -> optical-depth
+// budget tau = -ln(1-u0) spent brick by brick, u1 -> accept with
+// probability sigma_t / majorant).  Returns true and the distance on a real
+// collision.
+template <typename R> bool delta_track(const Volume& V, const Grid<R>& G, V3<R> o, V3<R> d, R t, R t_end, Rng& rng,
                                        R* t_hit, long* steps) {
-    if (!(sbar > (R)0)) return false;
+    Walk<R> W; W.init(G, o, d, t);
+    R u[4] = {0, 0, 0, 0}, tau = (R)0;
+    bool need = true;
     for (long it = 0; it < (1L << 24); ++it) {
-        R u[4]; rng.uni4<R>(u);
-        t = t + (-M<R>::ln((R)1 - u[0])) / sbar;
+        if (need) { rng.uni4<R>(u); tau = -M<R>::ln((R)1 - u[0]); need = false; }
+        R m = G.at(W.c[0], W.c[1], W.c[2]);
+        R tc = std::min(W.exit_t(), t_end);
+        R seg = tc - t;
+        if (seg < (R)0) seg = (R)0;
+        if (m > (R)0 && tau < m * seg) {
+            t = t + tau / m;
+            if (steps) ++*steps;
+            if (u[1] * m < sigma_at<R>(V, along(o, d, t))) { *t_hit = t; return true; }
+            need = true;
+            continue;
+        }
+        tau = tau - m * seg;
+        t = tc;
         if (t >= t_end) return false;
-        if (steps) ++*steps;
-        V3<R> x = along(o, d, t);
-        if (u[1] * sbar < sigma_at<R>(V, x)) { *t_hit = t; return true; }
+        if (!W.step()) return false;
     }
     return false;
 }
 
-// Ratio-tracking transmittance from o along d over [0, t_end).
-template <typename R> R ratio_track(const Volume& V, R sbar, V3<R> o, V3<R> d, R t_end, Rng& rng) {
-    if (!(sbar > (R)0)) return (R)1;
-    R T = (R)1, t = (R)0;
+// Ratio-tracking transmittance over [0, t_end) with the brick majorants.
+template <typename R> R ratio_track(const Volume& V, const Grid<R>& G, V3<R> o, V3<R> d, R t_end, Rng& rng) {
+    Walk<R> W; W.init(G, o, d, (R)0);
+    R T = (R)1, t = (R)0, tau = (R)0;
+    R u[4] = {0, 0, 0, 0};
+    bool need = true;
     for (long it = 0; it < (1L << 24); ++it) {
-        R u[4]; rng.uni4<R>(u);
-        t = t + (-M<R>::ln((R)1 - u[0])) / sbar;
+        if (need) { rng.uni4<R>(u); tau = -M<R>::ln((R)1 - u[0]); need = false; }
+        R m = G.at(W.c[0], W.c[1], W.c[2]);
+        R tc = std::min(W.exit_t(), t_end);
+        R seg = tc - t;
+        if (seg < (R)0) seg = (R)0;
+        if (m > (R)0 && tau < m * seg) {
+            t = t + tau / m;
+            R f = (R)1 - sigma_at<R>(V, along(o, d, t)) / m;
+            T = T * std::max((R)0, f);
+            need = true;
+            continue;
+        }
+        tau = tau - m * seg;
+        t = tc;
         if (t >= t_end) break;
-        R f = (R)1 - sigma_at<R>(V, along(o, d, t)) / sbar;
-        T = T * std::max((R)0, f);
+        if (!W.step()) break;
     }
     return T;
 }
@@ -403,7 +513,7 @@ template <typename R> void camera_ray(const CamFrame& c, int px, int py, R j1, R
 struct Tally { double emitted[3], escaped[3], absorbed[3], truncated[3], rr[3]; };
 
 template <typename R>
-void trace_photon(const Volume& V, R sbar, const Light* lights, int n_lights, const float* gset, int n_g,
+void trace_photon(const Volume& V, const Grid<R>& G, const Light* lights, int n_lights, const float* gset, int n_g,
                   uint64_t N, int max_bounces, int res, uint64_t seed, int use_rr, uint64_t p,
                   // outputs: per-photon slots (max_bounces-1 of them)
                   uint32_t* keys, float* dirs, float* phis, int* nrec, Tally* T) {
@@ -439,7 +549,7 @@ void trace_photon(const Volume& V, R sbar, const Light* lights, int n_lights, co
     R t = t0;
     while (alive && inside) {
         R th;
-        if (!delta_track<R>(V, sbar, o, d, t, t1, rng, &th, nullptr)) break;
+        if (!delta_track<R>(V, G, o, d, t, t1, rng, &th, nullptr)) break;
         V3<R> x = along(o, d, th);
         j = j + 1;
         Medium<R> m = medium_at<R>(V, x);
@@ -503,7 +613,7 @@ R march_tau(const Volume& V, V3<R> o, V3<R> d, R t0, R t1, R h, R jit) {
 }
 
 template <typename R>
-void camera_sample(const Volume& V, R sbar, const Light* lights, int n_lights, R g, const CamFrame& cf,
+void camera_sample(const Volume& V, const Grid<R>& G, const Light* lights, int n_lights, R g, const CamFrame& cf,
                    int px, int py, int k, R step_vox, uint64_t seed,
                    int* valid, V3<R>* xo, V3<R>* wo, V3<R>* alb, V3<R>* Ld) {
     Rng rng(seed, 1, (uint64_t)py * (uint64_t)cf.W + (uint64_t)px, (uint32_t)k);
@@ -537,7 +647,7 @@ void camera_sample(const Volume& V, R sbar, const Light* lights, int n_lights, R
             tau = tau + sg * len;
         }
     } else {
-        hit = delta_track<R>(V, sbar, o, d, t0, t1, rng, &th, nullptr);
+        hit = delta_track<R>(V, G, o, d, t0, t1, rng, &th, nullptr);
     }
     if (!hit) return;
     V3<R> x = along(o, d, th);
@@ -554,7 +664,7 @@ void camera_sample(const Volume& V, R sbar, const Light* lights, int n_lights, R
             R h = step_vox / (R)nmax;
             T = std::exp(-march_tau<R>(V, x, wl, (R)0, tend, h, jl[l]));
         } else {
-            T = ratio_track<R>(V, sbar, x, wl, tend, rng);
+            T = ratio_track<R>(V, G, x, wl, tend, rng);
         }
         R ph = hg_eval<R>(g, dot(d, wl));
         L = v3(L.x + ph * T * E.x, L.y + ph * T * E.y, L.z + ph * T * E.z);
@@ -568,7 +678,7 @@ void camera_sample(const Volume& V, R sbar, const Light* lights, int n_lights, R
 // albedo; then throughput *= albedo; stop at j == max_bounces; HG continuation
 // and Russian roulette (j >= 3, q = min(1, max_c beta_c)) from one block.
 template <typename R>
-V3<R> path_sample(const Volume& V, R sbar, const Light* lights, int n_lights, R g, const CamFrame& cf,
+V3<R> path_sample(const Volume& V, const Grid<R>& G, const Light* lights, int n_lights, R g, const CamFrame& cf,
                   int px, int py, int k, int max_bounces, uint64_t seed, int use_rr) {
     Rng rng(seed, 1, (uint64_t)py * (uint64_t)cf.W + (uint64_t)px, (uint32_t)k);
     R b0[4]; rng.uni4<R>(b0);
@@ -581,7 +691,7 @@ V3<R> path_sample(const Volume& V, R sbar, const Light* lights, int n_lights, R 
     R t = t0;
     for (int j = 1; j <= max_bounces; ++j) {
         R th;
-        if (!delta_track<R>(V, sbar, o, d, t, t1, rng, &th, nullptr)) break;
+        if (!delta_track<R>(V, G, o, d, t, t1, rng, &th, nullptr)) break;
         V3<R> x = along(o, d, th);
         Medium<R> m = medium_at<R>(V, x);
         V3<R> L = v3((R)0, (R)0, (R)0);
@@ -590,7 +700,7 @@ V3<R> path_sample(const Volume& V, R sbar, const Light* lights, int n_lights, R 
             light_geom<R>(lights[l], x, &wl, &dist, &E);
             R a0, a1, tend = (R)0;
             if (box_hit(x, wl, &a0, &a1)) tend = std::min(a1, dist);
-            R T = ratio_track<R>(V, sbar, x, wl, tend, rng);
+            R T = ratio_track<R>(V, G, x, wl, tend, rng);
             R ph = hg_eval<R>(g, dot(d, wl));
             L = v3(L.x + ph * T * E.x, L.y + ph * T * E.y, L.z + ph * T * E.z);
         }
@@ -678,19 +788,42 @@ double orc_majorant(int nx, int ny, int nz, int dtype, const void* data, double 
     return fp32 ? (double)majorant<float>(V) : majorant<double>(V);
 }
 
+// Brick majorant grid (gx*gy*gz values, x fastest).
+void orc_brick_majorants(int nx, int ny, int nz, int dtype, const void* data, double ss, const float* tf, int tf_n,
+                         int fp32, double* out) {
+    Volume V = mkvol(nx, ny, nz, dtype, data, ss, 1.0, tf, tf_n);
+    if (fp32) { Grid<float> G = build_grid<float>(V); for (size_t i = 0; i < G.m.size(); ++i) out[i] = G.m[i]; }
+    else { Grid<double> G = build_grid<double>(V); for (size_t i = 0; i < G.m.size(); ++i) out[i] = G.m[i]; }
+}
+
+// Mean ratio-tracking transmittance from o along d over [0, t_end) (n walks).
+double orc_ratio_mean(int nx, int ny, int nz, int dtype, const void* data, double ss, const float* tf, int tf_n,
+                      const double* o, const double* d, double t_end, int64_t n, uint64_t seed, double* var) {
+    Volume V = mkvol(nx, ny, nz, dtype, data, ss, 1.0, tf, tf_n);
+    Grid<double> G = build_grid<double>(V);
+    double s = 0, s2 = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        Rng r(seed, 2, (uint64_t)i, 0);
+        double T = ratio_track<double>(V, G, v3(o[0], o[1], o[2]), v3(d[0], d[1], d[2]), t_end, r);
+        s += T; s2 += T * T;
+    }
+    *var = s2 / n - (s / n) * (s / n);
+    return s / n;
+}
+
 // Free-flight distances by delta tracking from o along d (one item per
 // sample, Philox tag PHOTON, item i); -1 where the ray leaves the box.
 void orc_free_flight(int nx, int ny, int nz, int dtype, const void* data, double ss, const float* tf, int tf_n,
                      const double* o, const double* d, int64_t n, uint64_t seed, double* out, int64_t* steps) {
     Volume V = mkvol(nx, ny, nz, dtype, data, ss, 1.0, tf, tf_n);
-    double sbar = majorant<double>(V);
+    Grid<double> G = build_grid<double>(V);
     long st = 0;
     for (int64_t i = 0; i < n; ++i) {
         Rng r(seed, 2, (uint64_t)i, 0);
         V3<double> oo = v3(o[0], o[1], o[2]), dd = v3(d[0], d[1], d[2]);
         double t0, t1, th;
         out[i] = -1.0;
-        if (box_hit(oo, dd, &t0, &t1) && delta_track<double>(V, sbar, oo, dd, t0, t1, r, &th, &st)) out[i] = th - t0;
+        if (box_hit(oo, dd, &t0, &t1) && delta_track<double>(V, G, oo, dd, t0, t1, r, &th, &st)) out[i] = th - t0;
     }
     *steps = st;
 }
@@ -707,8 +840,8 @@ void orc_trace_photons(int nx, int ny, int nz, int dtype, const void* data, doub
     Volume V = mkvol(nx, ny, nz, dtype, data, ss, alb, tf, tf_n);
     std::vector<Light> L = mklights(lkind, lv, lrgb, n_lights);
     int S = max_bounces - 1 > 0 ? max_bounces - 1 : 1;
-    double sb64 = majorant<double>(V);
-    float sb32 = majorant<float>(V);
+    Grid<double> G64 = fp32 ? Grid<double>() : build_grid<double>(V);
+    Grid<float> G32 = fp32 ? build_grid<float>(V) : Grid<float>();
     Tally tot; std::memset(&tot, 0, sizeof(tot));
     #pragma omp parallel
     {
@@ -716,9 +849,9 @@ void orc_trace_photons(int nx, int ny, int nz, int dtype, const void* data, doub
         #pragma omp for schedule(dynamic, 256)
         for (int64_t q = (int64_t)p_begin; q < (int64_t)p_end; ++q) {
             size_t s = (size_t)(q - (int64_t)p_begin);
-            if (fp32) trace_photon<float>(V, sb32, L.data(), n_lights, gset, n_g, N, max_bounces, res, seed, use_rr,
+            if (fp32) trace_photon<float>(V, G32, L.data(), n_lights, gset, n_g, N, max_bounces, res, seed, use_rr,
                                          (uint64_t)q, keys + s * S, dirs + s * S * 3, phis + s * S * 3, nrec + s, &loc);
-            else trace_photon<double>(V, sb64, L.data(), n_lights, gset, n_g, N, max_bounces, res, seed, use_rr,
+            else trace_photon<double>(V, G64, L.data(), n_lights, gset, n_g, N, max_bounces, res, seed, use_rr,
                                       (uint64_t)q, keys + s * S, dirs + s * S * 3, phis + s * S * 3, nrec + s, &loc);
         }
         #pragma omp critical
@@ -746,8 +879,8 @@ void orc_camera_samples(int nx, int ny, int nz, int dtype, const void* data, dou
     Volume V = mkvol(nx, ny, nz, dtype, data, ss, alb, tf, tf_n);
     std::vector<Light> L = mklights(lkind, lv, lrgb, n_lights);
     CamFrame cf = cam_frame(eye, at, up, fovy, W, H);
-    double sb64 = majorant<double>(V);
-    float sb32 = majorant<float>(V);
+    Grid<double> G64 = fp32 ? Grid<double>() : build_grid<double>(V);
+    Grid<float> G32 = fp32 ? build_grid<float>(V) : Grid<float>();
     #pragma omp parallel for schedule(dynamic, 1) collapse(2)
     for (int py = y_begin; py < y_end; ++py)
         for (int px = 0; px < W; ++px)
@@ -756,14 +889,14 @@ void orc_camera_samples(int nx, int ny, int nz, int dtype, const void* data, dou
                 int vld;
                 if (fp32) {
                     V3<float> a, b, c, e;
-                    camera_sample<float>(V, sb32, L.data(), n_lights, (float)g, cf, px, py, k, (float)step_vox, seed, &vld, &a, &b, &c, &e);
+                    camera_sample<float>(V, G32, L.data(), n_lights, (float)g, cf, px, py, k, (float)step_vox, seed, &vld, &a, &b, &c, &e);
                     x[3 * idx] = a.x; x[3 * idx + 1] = a.y; x[3 * idx + 2] = a.z;
                     wo[3 * idx] = b.x; wo[3 * idx + 1] = b.y; wo[3 * idx + 2] = b.z;
                     albedo[3 * idx] = c.x; albedo[3 * idx + 1] = c.y; albedo[3 * idx + 2] = c.z;
                     Ld[3 * idx] = e.x; Ld[3 * idx + 1] = e.y; Ld[3 * idx + 2] = e.z;
                 } else {
                     V3<double> a, b, c, e;
-                    camera_sample<double>(V, sb64, L.data(), n_lights, g, cf, px, py, k, step_vox, seed, &vld, &a, &b, &c, &e);
+                    camera_sample<double>(V, G64, L.data(), n_lights, g, cf, px, py, k, step_vox, seed, &vld, &a, &b, &c, &e);
                     x[3 * idx] = a.x; x[3 * idx + 1] = a.y; x[3 * idx + 2] = a.z;
                     wo[3 * idx] = b.x; wo[3 * idx + 1] = b.y; wo[3 * idx + 2] = b.z;
                     albedo[3 * idx] = c.x; albedo[3 * idx + 1] = c.y; albedo[3 * idx + 2] = c.z;
@@ -785,8 +918,8 @@ void orc_path_trace(int nx, int ny, int nz, int dtype, const void* data, double 
     Volume V = mkvol(nx, ny, nz, dtype, data, ss, alb, tf, tf_n);
     std::vector<Light> L = mklights(lkind, lv, lrgb, n_lights);
     CamFrame cf = cam_frame(eye, at, up, fovy, W, H);
-    double sb64 = majorant<double>(V);
-    float sb32 = majorant<float>(V);
+    Grid<double> G64 = fp32 ? Grid<double>() : build_grid<double>(V);
+    Grid<float> G32 = fp32 ? build_grid<float>(V) : Grid<float>();
     int64_t n_items = px_list ? n_px : (int64_t)(y_end - y_begin) * W;
     #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t it = 0; it < n_items; ++it) {
@@ -796,14 +929,14 @@ void orc_path_trace(int nx, int ny, int nz, int dtype, const void* data, double 
         if (fp32) {
             float acc[3] = {0.f, 0.f, 0.f};
             for (int k = 0; k < spp; ++k) {
-                V3<float> r = path_sample<float>(V, sb32, L.data(), n_lights, (float)g, cf, px, py, k, max_bounces, seed, use_rr);
+                V3<float> r = path_sample<float>(V, G32, L.data(), n_lights, (float)g, cf, px, py, k, max_bounces, seed, use_rr);
                 acc[0] = acc[0] + r.x; acc[1] = acc[1] + r.y; acc[2] = acc[2] + r.z;
             }
             for (int c = 0; c < 3; ++c) out[3 * it + c] = (double)(acc[c] / (float)spp);
         } else {
             double acc[3] = {0, 0, 0};
             for (int k = 0; k < spp; ++k) {
-                V3<double> r = path_sample<double>(V, sb64, L.data(), n_lights, g, cf, px, py, k, max_bounces, seed, use_rr);
+                V3<double> r = path_sample<double>(V, G64, L.data(), n_lights, g, cf, px, py, k, max_bounces, seed, use_rr);
                 acc[0] += r.x; acc[1] += r.y; acc[2] += r.z;
             }
             for (int c = 0; c < 3; ++c) out[3 * it + c] = acc[c] / spp;

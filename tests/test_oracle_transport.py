@@ -2,7 +2,9 @@
 
   * delta tracking samples free-flight distances from Exp(sigma_t) truncated
     at the box (Kolmogorov-Smirnov), with null collisions against a larger
-    majorant;
+    majorant; over the brick-majorant grid in a heterogeneous volume the
+    distances follow 1 - exp(-int sigma) (optical depth by quadrature) and
+    ratio tracking's mean is exp(-int sigma); brick majorants bound sigma_t;
   * directional emission covers the box's projection: the fraction of
     photons entering the unit cube is (|vx|+|vy|+|vz|)/3;
   * point emission is isotropic: the fraction entering the cube is its solid
@@ -42,6 +44,46 @@ def test_delta_tracking_free_flight_distribution(orc):
     cdf = lambda s: (1 - np.exp(-sigma * s)) / (1 - p_esc)
     assert stats.kstest(t, cdf).pvalue > 1e-3
     assert steps / d.size > sigma            # tentative collisions per unit length ~ majorant
+
+
+def _optical_depth(orc, vol, o, d, s_max, n=20001):
+    s = np.linspace(0.0, s_max, n)
+    pts = np.asarray(o)[None, :] + s[:, None] * np.asarray(d)[None, :]
+    sig = vol.sigma_scale * np.interp(orc.density(vol, pts), np.linspace(0, 1, vol.tf.shape[0]), vol.tf[:, 3])
+    tau = np.concatenate([[0.0], np.cumsum(0.5 * (sig[1:] + sig[:-1]) * np.diff(s))])
+    return s, tau
+
+
+def test_brick_majorants_bound_sigma(orc):
+    sc = I.scene_judge(48)
+    vol = sc.volume
+    for fp32 in (False, True):
+        m = orc.brick_majorants(vol, fp32)
+        rng = np.random.default_rng(4)
+        p = rng.uniform(0, 1, (50000, 3))
+        sig = vol.sigma_scale * orc.density(vol, p, fp32)        # alpha = density for this TF
+        b = np.minimum((p * 48 / 8).astype(int), 5)
+        assert np.all(sig <= m[b[:, 2], b[:, 1], b[:, 0]])
+    # tight: the mean brick majorant is well below the global one
+    assert m.mean() < 0.9 * orc.majorant(vol)
+
+
+def test_grid_delta_tracking_in_heterogeneous_volume(orc):
+    sc = I.scene_judge(40)
+    vol = sc.volume
+    o, d = np.array([0.3, 0.62, -0.5]), np.array([0.15, -0.05, 1.0])
+    d = d / np.linalg.norm(d)
+    t0 = (0.0 - o[2]) / d[2]
+    t1 = (1.0 - o[2]) / d[2]
+    s, tau = _optical_depth(orc, vol, o + t0 * d, d, t1 - t0)
+    dist, _ = orc.free_flight(vol, o, d, 60000, seed=21)
+    esc = dist < 0
+    p_esc = math.exp(-tau[-1])
+    assert abs(esc.mean() - p_esc) < 5 * math.sqrt(p_esc * (1 - p_esc) / dist.size) + 2e-3
+    cdf = lambda x: (1 - np.exp(-np.interp(x, s, tau))) / (1 - p_esc)
+    assert stats.kstest(dist[~esc], cdf).pvalue > 1e-3
+    mean, var = orc.ratio_mean(vol, o + t0 * d, d, t1 - t0, 60000, seed=22)
+    assert abs(mean - p_esc) < 5 * math.sqrt(var / 60000) + 2e-3
 
 
 @pytest.mark.parametrize("fp32", [False, True])
