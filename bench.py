@@ -176,6 +176,7 @@ def main():
     vol_t, tf_t, lights, cams = setup_scene(dev)
     vol = api.Volume(vol_t, 20.0, 0.9, tf_t)
     vol.s.majorant = vol.majorant(ctx)
+    vol.attach_brick_majorants(ctx)
     setup = {}
     t0 = time.perf_counter()
     cache = api.build_photon_cache(ctx, vol, lights, I.G_PAPER, args.photons, 16, 64, seed=seed + 1)

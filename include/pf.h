@@ -73,7 +73,9 @@ typedef struct {
   float albedo;             /* single-scattering albedo = albedo * rgb(d) */
   const float* tf_lut_dev;  /* tf_n x 4 RGBA rows over d in [0,1], tf_n >= 2 */
   int tf_n;
-  float majorant;           /* global max of sigma_t; 0 = let the library compute it */
+  float majorant;           /* global max of sigma_t (informational; 0 = unknown) */
+  const float* brick_majorants_dev; /* per-8^3-brick majorants from pf_volume_brick_majorants, or
+                                       NULL: the tracers then compute them into context scratch */
 } pf_volume;
 
 /* Light source.  Directional: v = unit direction towards the light, rgb =
@@ -143,10 +145,18 @@ pf_status pf_stage_times(pf_ctx* ctx, double* ms_host, int* launches_host, int n
 /* Wait for the context's stream; report any device-side error word. */
 pf_status pf_sync(pf_ctx* ctx);
 
-/* Global majorant used by delta and ratio tracking: sigma_scale times the
- * largest transfer-function alpha over densities [0, max voxel], times
- * (1 + 2^-10).  Synchronises; writes one float to out_host. */
+/* Global majorant: sigma_scale times the largest transfer-function alpha
+ * over densities [0, max voxel], times (1 + 2^-10).  Synchronises; writes one
+ * float to out_host. */
 pf_status pf_volume_majorant(pf_ctx* ctx, const pf_volume* vol, float* out_host);
+/* Brick majorants used by delta and ratio tracking (regular tracking over a
+ * piecewise-constant majorant).  Brick (i,j,k) covers voxels [8i, 8i+8) per
+ * axis (region between the planes min(8i, n)/n); its majorant is
+ * sigma_scale times the largest TF alpha over the density range of the
+ * voxels trilinear interpolation can reach there (the brick plus a one-voxel
+ * apron, and density 0 for bricks on the box boundary), times (1 + 2^-10).
+ * out_dev: ceil(nx/8)*ceil(ny/8)*ceil(nz/8) floats, x fastest. */
+pf_status pf_volume_brick_majorants(pf_ctx* ctx, const pf_volume* vol, float* out_dev);
 
 /* ---------------------------------------------------------------- photon caches */
 /* Multi-phase photon tracing (Algorithm 1; Sec. 3.2) on the GPU.
@@ -154,7 +164,7 @@ pf_status pf_volume_majorant(pf_ctx* ctx, const pf_volume* vol, float* out_host)
  * g_set (host array); photon p belongs to light p / (n_g*N) and phase
  * (p / N) % n_g.  Directional lights emit from a sqrt(3)-wide square one unit
  * upstream of the box centre, point lights isotropically.  Delta tracking
- * against the global majorant; at real interaction j the photon is recorded
+ * over the brick majorants; at real interaction j the photon is recorded
  * if j >= 2 (incoming direction, power before this vertex's albedo, cache
  * bin floor(cache_res * x)), then scaled by the albedo, stopped at
  * j == max_bounces, scattered by Henyey-Greenstein, and, for j >= 3 and
@@ -258,8 +268,8 @@ pf_status pf_render_pathtraced(pf_ctx* ctx, const pf_volume* vol, const pf_light
  * every GPU loading the library holds until the process exits, which bounds
  * the image to about 2.09 million pixels (1920x1080 fits); larger images are
  * rejected with PF_ERR_INVALID_ARG.  The caller passes the inputs, a stream
- * of the current device and the output image; vol->majorant must be set
- * (> 0), e.g. from pf_volume_majorant.  The first call on a device looks up
+ * of the current device and the output image; vol->brick_majorants_dev must
+ * be set (an input, e.g. from pf_volume_brick_majorants).  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress) with that device
  * current, so make that first call before any stream capture.  All calls
  * share the array and it keeps the last call's contents (each call resets

@@ -19,7 +19,8 @@ STATUS_NAMES = ["PF_OK", "PF_ERR_INVALID_ARG", "PF_ERR_OOM", "PF_ERR_CUDA", "PF_
 class PfVolume(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dtype", C.c_int),
                 ("data_dev", C.c_void_p), ("sigma_scale", C.c_float), ("albedo", C.c_float),
-                ("tf_lut_dev", C.c_void_p), ("tf_n", C.c_int), ("majorant", C.c_float)]
+                ("tf_lut_dev", C.c_void_p), ("tf_n", C.c_int), ("majorant", C.c_float),
+                ("brick_majorants_dev", C.c_void_p)]
 
 
 class PfLight(C.Structure):
@@ -61,6 +62,7 @@ SIGNATURES = {
     "pf_stage_times": (I, [P, C.POINTER(C.c_double), C.POINTER(C.c_int), I]),
     "pf_sync": (I, [P]),
     "pf_volume_majorant": (I, [P, C.POINTER(PfVolume), C.POINTER(C.c_float)]),
+    "pf_volume_brick_majorants": (I, [P, C.POINTER(PfVolume), P]),
     "pf_build_photon_cache": (I, [P, C.POINTER(PfVolume), C.POINTER(PfLight), I, C.POINTER(C.c_float), I, U64, I, I,
                                   U64, I, PP]),
     "pf_cache_info": (I, [P, P, C.POINTER(PfCacheInfo)]),

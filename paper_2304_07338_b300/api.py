@@ -91,7 +91,8 @@ class Volume:
         self.data, self.tf = data, tf
         nz, ny, nx = data.shape
         self.s = PfVolume(nx, ny, nz, code, data.data_ptr(), float(sigma_scale), float(albedo), tf.data_ptr(),
-                          int(tf.shape[0]), float(majorant))
+                          int(tf.shape[0]), float(majorant), None)
+        self.grid = None
 
     @classmethod
     def from_inputs(cls, vol, device="cuda"):
@@ -99,6 +100,19 @@ class Volume:
         data = torch.from_numpy(np.ascontiguousarray(vol.data)).to(device)
         tf = torch.from_numpy(np.ascontiguousarray(vol.tf, np.float32)).to(device)
         return cls(data, vol.sigma_scale, vol.albedo, tf)
+
+    def brick_majorants(self, ctx: Context) -> torch.Tensor:
+        """Per-8^3-brick majorants (computed on the GPU), shape (gz, gy, gx)."""
+        nz, ny, nx = self.data.shape
+        g = torch.empty(((nz + 7) // 8, (ny + 7) // 8, (nx + 7) // 8), dtype=torch.float32, device=self.data.device)
+        ctx.check(ctx.lib.pf_volume_brick_majorants(ctx.h, C.byref(self.s), _ptr(g)))
+        return g
+
+    def attach_brick_majorants(self, ctx: Context) -> torch.Tensor:
+        """Compute the brick majorants once and let every call reuse them."""
+        self.grid = self.brick_majorants(ctx)
+        self.s.brick_majorants_dev = self.grid.data_ptr()
+        return self.grid
 
     def majorant(self, ctx: Context) -> float:
         out = C.c_float()

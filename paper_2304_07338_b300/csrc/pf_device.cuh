@@ -134,7 +134,10 @@ struct Vol {
   float sigma_scale, albedo, majorant;
   const float4* tf;   // RGBA rows
   int tf_n;
+  const float* mg;    // brick majorants (8^3 bricks, x fastest)
+  int gx, gy, gz;
 };
+constexpr int kBrick = 8;
 
 template <int DT> __device__ __forceinline__ float voxel(const Vol& V, int i, int j, int k) {
   size_t idx = (size_t)i + (size_t)V.nx * ((size_t)j + (size_t)V.ny * (size_t)k);
@@ -243,43 +246,120 @@ __device__ __forceinline__ V3 hg_sample(float g, V3 d, float xi1, float xi2) {
 // Iteration limit of every tracking loop; exceeding it sets PFE_ITER_CAP.
 constexpr int kMaxTrackSteps = 1 << 24;
 
-// Delta (Woodcock) tracking in [t, t_end): one Philox block per tentative
-// collision (u0 distance, u1 acceptance).  Returns true on a real collision.
-// `fetches` counts density lookups (the tracers' unit of memory work).
+// Walk over the 8^3 bricks a ray crosses (Amanatides-Woo stepping).  Brick
+// planes lie at min(8i, n)/n; the first brick is taken from the start point.
+struct Walk {
+  int c[3], s[3], g[3], n[3];
+  float tn[3], o[3], d[3];
+  __device__ __forceinline__ float plane_t(int a) const {
+    if (s[a] == 0) return __int_as_float(0x7f800000);
+    int vi = s[a] > 0 ? min((c[a] + 1) * kBrick, n[a]) : c[a] * kBrick;
+    float p = (float)vi / (float)n[a];
+    return (p - o[a]) / d[a];
+  }
+  __device__ __forceinline__ void init(const Vol& V, V3 oo, V3 dd, float t) {
+    o[0] = oo.x; o[1] = oo.y; o[2] = oo.z; d[0] = dd.x; d[1] = dd.y; d[2] = dd.z;
+    g[0] = V.gx; g[1] = V.gy; g[2] = V.gz; n[0] = V.nx; n[1] = V.ny; n[2] = V.nz;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float p = o[a] + t * d[a];
+      int ci = (int)floorf(p * ((float)n[a] * 0.125f));
+      c[a] = min(max(ci, 0), g[a] - 1);
+      s[a] = d[a] > 0.0f ? 1 : (d[a] < 0.0f ? -1 : 0);
+      tn[a] = plane_t(a);
+    }
+  }
+  __device__ __forceinline__ float exit_t() const { return mn(tn[0], mn(tn[1], tn[2])); }
+  __device__ __forceinline__ float majorant(const Vol& V) const {
+    return __ldg(V.mg + (size_t)c[0] + (size_t)V.gx * ((size_t)c[1] + (size_t)V.gy * (size_t)c[2]));
+  }
+  // step into the next brick; false when the ray leaves the grid
+  __device__ __forceinline__ bool step() {
+    int a = (tn[0] <= tn[1] && tn[0] <= tn[2]) ? 0 : (tn[1] <= tn[2] ? 1 : 2);
+    c[a] += s[a];
+    if (c[a] < 0 || c[a] >= g[a]) return false;
+    tn[a] = plane_t(a);
+    return true;
+  }
+};
+
+// Delta (Woodcock) tracking in [t, t_end) over the brick majorants: one
+// Philox block per tentative collision (u0 -> optical-depth budget
+// tau = -ln(1-u0), spent brick by brick; u1 -> accept with probability
+// sigma_t / majorant).  Returns true on a real collision.  `fetches` counts
+// density lookups (the tracers' unit of memory work).
 template <int DT>
 __device__ __forceinline__ bool delta_track(const Vol& V, V3 o, V3 d, float t, float t_end, Rng& rng, float* t_hit,
                                             uint32_t* err, uint32_t& fetches) {
-  const float sbar = V.majorant;
-  if (!(sbar > 0.0f)) return false;
+  Walk W;
+  W.init(V, o, d, t);
+  float u[4] = {0.f, 0.f, 0.f, 0.f}, tau = 0.f;
+  bool need = true;
   for (int it = 0; it < kMaxTrackSteps; ++it) {
-    float u[4]; rng.uni4(u);
-    t = t + (-own_lnf(1.0f - u[0])) / sbar;
+    if (need) { rng.uni4(u); tau = -own_lnf(1.0f - u[0]); need = false; }
+    const float m = W.majorant(V);
+    const float tc = mn(W.exit_t(), t_end);
+    float seg = tc - t;
+    if (seg < 0.0f) seg = 0.0f;
+    if (m > 0.0f && tau < m * seg) {
+      t = t + tau / m;
+      ++fetches;
+      if (u[1] * m < sigma_at<DT>(V, along(o, d, t))) { *t_hit = t; return true; }
+      need = true;
+      continue;
+    }
+    tau = tau - m * seg;
+    t = tc;
     if (t >= t_end) return false;
-    ++fetches;
-    V3 x = along(o, d, t);
-    if (u[1] * sbar < sigma_at<DT>(V, x)) { *t_hit = t; return true; }
+    if (!W.step()) return false;
   }
   atomicOr(err, 1u);
   return false;
 }
 
-// Ratio-tracking transmittance over [0, t_end).
+// Ratio-tracking transmittance over [0, t_end) with the brick majorants.
 template <int DT>
 __device__ __forceinline__ float ratio_track(const Vol& V, V3 o, V3 d, float t_end, Rng& rng, uint32_t* err,
                                              uint32_t& fetches) {
-  const float sbar = V.majorant;
-  if (!(sbar > 0.0f)) return 1.0f;
-  float T = 1.0f, t = 0.0f;
+  Walk W;
+  W.init(V, o, d, 0.0f);
+  float T = 1.0f, t = 0.0f, tau = 0.f;
+  float u[4] = {0.f, 0.f, 0.f, 0.f};
+  bool need = true;
   for (int it = 0; it < kMaxTrackSteps; ++it) {
-    float u[4]; rng.uni4(u);
-    t = t + (-own_lnf(1.0f - u[0])) / sbar;
+    if (need) { rng.uni4(u); tau = -own_lnf(1.0f - u[0]); need = false; }
+    const float m = W.majorant(V);
+    const float tc = mn(W.exit_t(), t_end);
+    float seg = tc - t;
+    if (seg < 0.0f) seg = 0.0f;
+    if (m > 0.0f && tau < m * seg) {
+      t = t + tau / m;
+      ++fetches;
+      const float f = 1.0f - sigma_at<DT>(V, along(o, d, t)) / m;
+      T = T * mx(0.0f, f);
+      need = true;
+      continue;
+    }
+    tau = tau - m * seg;
+    t = tc;
     if (t >= t_end) return T;
-    ++fetches;
-    float f = 1.0f - sigma_at<DT>(V, along(o, d, t)) / sbar;
-    T = T * mx(0.0f, f);
+    if (!W.step()) return T;
   }
   atomicOr(err, 1u);
   return T;
+}
+
+// Largest TF alpha over densities [dmin, dmax] (piecewise-linear table).
+__device__ __forceinline__ float tf_alpha_max(const Vol& V, float dmin, float dmax) {
+  if (dmin < 0.0f) dmin = 0.0f;
+  if (dmax > 1.0f) dmax = 1.0f;
+  float a = mx(tf_alpha(V, dmin), tf_alpha(V, dmax));
+  for (int i = 0; i < V.tf_n; ++i) {
+    const float nd = (float)i / (float)(V.tf_n - 1);
+    const float ai = __ldg(&V.tf[i].w);
+    if (nd >= dmin && nd <= dmax && ai > a) a = ai;
+  }
+  return a;
 }
 
 // ------------------------------------------------------------------ lights and camera
@@ -316,11 +396,15 @@ __device__ __forceinline__ void camera_ray(const CamF& c, int px, int py, float 
 }  // namespace pfd
 
 // Host-side packing of the public scene structs into the kernels' views.
-inline pfd::Vol pf_make_vol(const pf_volume* v, float majorant) {
+inline pfd::Vol pf_make_vol(const pf_volume* v, float majorant, const float* grid = nullptr) {
   pfd::Vol V;
   V.data = v->data_dev; V.nx = v->nx; V.ny = v->ny; V.nz = v->nz; V.dtype = v->dtype;
   V.sigma_scale = v->sigma_scale; V.albedo = v->albedo; V.majorant = majorant;
   V.tf = (const float4*)v->tf_lut_dev; V.tf_n = v->tf_n;
+  V.mg = grid;
+  V.gx = (v->nx + pfd::kBrick - 1) / pfd::kBrick;
+  V.gy = (v->ny + pfd::kBrick - 1) / pfd::kBrick;
+  V.gz = (v->nz + pfd::kBrick - 1) / pfd::kBrick;
   return V;
 }
 inline pfd::DevLights pf_make_lights(const pf_light* lights, int n) {

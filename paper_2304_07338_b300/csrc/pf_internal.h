@@ -14,7 +14,7 @@ enum : uint32_t { PFE_ITER_CAP = 1u, PFE_NONFINITE = 2u, PFE_OVERFLOW = 4u };
 // Scratch slots of the context arena.
 enum ScratchSlot {
   WS_REDUCE = 0, WS_SCAN, WS_QUERY, WS_TARGET, WS_ACT, WS_GRAD, WS_SAMPLES, WS_SLOT_LD, WS_SLOT_ALB,
-  WS_SLOT_LI, WS_COMPACT_Q, WS_COMPACT_IDX, WS_LOSS, WS_MISC, WS_COUNT
+  WS_SLOT_LI, WS_COMPACT_Q, WS_COMPACT_IDX, WS_LOSS, WS_MISC, WS_GRID, WS_COUNT
 };
 
 struct pf_ctx {
@@ -95,6 +95,8 @@ struct DeviceGuard {
 pf_status pf_check_volume(pf_ctx* ctx, const pf_volume* vol);
 pf_status pf_majorant_impl(pf_ctx* ctx, const pf_volume* vol, float* out);
 pf_status pf_check_lights(pf_ctx* ctx, const pf_light* lights, int n);
+// Brick majorants of a volume: the caller's array, or computed into scratch.
+pf_status pf_grid_for(pf_ctx* ctx, const pf_volume* vol, const float** grid);
 
 // Device-wide exclusive scan of u32 counts into u64 offsets (n+1 entries).
 pf_status pf_scan_u32(pf_ctx* ctx, const uint32_t* in, uint64_t* out, int64_t n);

@@ -439,8 +439,8 @@ extern "C" pf_status pf_render_neural(pf_ctx* ctx, const pf_volume* vol, const p
   if (!(step_vox == 0.f || (step_vox >= 0.05f && step_vox <= 64.f)) || !(g > -1.f && g < 1.f))
     return pf_fail(ctx, PF_ERR_INVALID_ARG, "need step_vox = 0 or in [0.05, 64] voxels, and |g| < 1");
   if (field && field->ctx != ctx) return pf_fail(ctx, PF_ERR_INVALID_ARG, "field belongs to another context");
-  float maj;
-  PF_TRY(pf_majorant_impl(ctx, vol, &maj));
+  const float* grid = nullptr;
+  if (step_vox == 0.f) PF_TRY(pf_grid_for(ctx, vol, &grid));
   int64_t n_pix = (int64_t)cam->width * cam->height;
   int64_t n_slots = n_pix * spp;
   if (n_slots > (int64_t)0xFFFFFFFFll) return pf_fail(ctx, PF_ERR_INVALID_ARG, "width*height*spp must be < 2^32");
@@ -455,7 +455,7 @@ extern "C" pf_status pf_render_neural(pf_ctx* ctx, const pf_volume* vol, const p
     PF_TRY(pf_scratch(ctx, WS_MISC, 256, (void**)&ccount));
     PF_CUDA(ctx, cudaMemsetAsync(ccount, 0, sizeof(uint32_t), ctx->stream));
   }
-  Vol V = pf_make_vol(vol, maj);
+  Vol V = pf_make_vol(vol, 0.f, grid);
   DevLights L = pf_make_lights(lights, n_lights);
   CamF C = make_cam(cam);
   int nmax = std::max(vol->nx, std::max(vol->ny, vol->nz));
@@ -512,15 +512,15 @@ extern "C" pf_status pf_render_pathtraced(pf_ctx* ctx, const pf_volume* vol, con
   if (!out_rgb_dev) return pf_fail(ctx, PF_ERR_INVALID_ARG, "out_rgb_dev is NULL");
   if (max_bounces < 1 || max_bounces > 1024) return pf_fail(ctx, PF_ERR_INVALID_ARG, "max_bounces must be in [1, 1024]");
   if (!(g > -1.f && g < 1.f)) return pf_fail(ctx, PF_ERR_INVALID_ARG, "|g| must be < 1");
-  float maj;
-  PF_TRY(pf_majorant_impl(ctx, vol, &maj));
+  const float* grid;
+  PF_TRY(pf_grid_for(ctx, vol, &grid));
   int64_t n_pix = (int64_t)cam->width * cam->height;
   // samples per chunk: keep the per-sample scratch within 2^26 slots
   int64_t kc = std::max<int64_t>(1, std::min<int64_t>(spp, ((int64_t)1 << 26) / n_pix));
   float *rad, *acc;
   PF_TRY(pf_scratch(ctx, WS_SLOT_LD, (size_t)(n_pix * kc * 3) * sizeof(float), (void**)&rad));
   PF_TRY(pf_scratch(ctx, WS_SLOT_ALB, (size_t)(n_pix * 3) * sizeof(float), (void**)&acc));
-  Vol V = pf_make_vol(vol, maj);
+  Vol V = pf_make_vol(vol, 0.f, grid);
   DevLights L = pf_make_lights(lights, n_lights);
   CamF C = make_cam(cam);
   StageTimer tm(ctx, PF_STAGE_PATH);
@@ -576,8 +576,8 @@ extern "C" pf_status pf_render_pathtraced_noalloc(const pf_volume* vol, const pf
     put_msg(err_msg, err_len, "invalid volume");
     return PF_ERR_INVALID_ARG;
   }
-  if (!(vol->majorant > 0.f) || !isfinite(vol->majorant)) {
-    put_msg(err_msg, err_len, "volume->majorant must be set (> 0): this entry point does not compute it");
+  if (!vol->brick_majorants_dev) {
+    put_msg(err_msg, err_len, "volume->brick_majorants_dev must be set: this entry point does not compute it");
     return PF_ERR_INVALID_ARG;
   }
   if (!lights || n_lights < 1 || n_lights > PF_MAX_LIGHTS) {
@@ -638,7 +638,7 @@ extern "C" pf_status pf_render_pathtraced_noalloc(const pf_volume* vol, const pf
     put_msg(err_msg, err_len, "cudaMemsetAsync: %s", cudaGetErrorString(e));
     return PF_ERR_CUDA;
   }
-  Vol V = pf_make_vol(vol, vol->majorant);
+  Vol V = pf_make_vol(vol, 0.f, vol->brick_majorants_dev);
   DevLights L = pf_make_lights(lights, n_lights);
   CamF C = make_cam(cam);
   for (int k0 = 0; k0 < spp; k0 += (int)kc) {

@@ -215,7 +215,56 @@ __global__ void k_occupied_list(const uint32_t* __restrict__ flag, const uint64_
   occ[pos[c]] = (uint32_t)c;
 }
 
+// Brick majorant: min / max density over the brick plus a one-voxel apron
+// (and 0 on the box boundary), largest TF alpha over that range, margin 2^-10.
+template <int DT>
+__global__ void k_brick_majorants(Vol V, float* __restrict__ out) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nb = (int64_t)V.gx * V.gy * V.gz;
+  if (b >= nb) return;
+  const int bx = (int)(b % V.gx), by = (int)((b / V.gx) % V.gy), bz = (int)(b / ((int64_t)V.gx * V.gy));
+  float dmin = __int_as_float(0x7f800000), dmax = -dmin;
+  for (int k = max(kBrick * bz - 1, 0); k <= min(kBrick * bz + kBrick, V.nz - 1); ++k)
+    for (int j = max(kBrick * by - 1, 0); j <= min(kBrick * by + kBrick, V.ny - 1); ++j)
+      for (int i = max(kBrick * bx - 1, 0); i <= min(kBrick * bx + kBrick, V.nx - 1); ++i) {
+        const float d = voxel<DT>(V, i, j, k);
+        if (d < dmin) dmin = d;
+        if (d > dmax) dmax = d;
+      }
+  if (bx == 0 || by == 0 || bz == 0 || bx == V.gx - 1 || by == V.gy - 1 || bz == V.gz - 1)
+    if (0.0f < dmin) dmin = 0.0f;
+  out[b] = V.sigma_scale * tf_alpha_max(V, dmin, dmax) * 1.0009765625f;
+}
+
 }  // namespace
+
+pf_status pf_brick_majorants_impl(pf_ctx* ctx, const pf_volume* vol, float* out) {
+  Vol V = pf_make_vol(vol, 0.f, nullptr);
+  const int64_t nb = (int64_t)V.gx * V.gy * V.gz;
+  const unsigned grd = (unsigned)((nb + 127) / 128);
+  if (vol->dtype == PF_F32) k_brick_majorants<0><<<grd, 128, 0, ctx->stream>>>(V, out);
+  else if (vol->dtype == PF_F16) k_brick_majorants<1><<<grd, 128, 0, ctx->stream>>>(V, out);
+  else k_brick_majorants<2><<<grd, 128, 0, ctx->stream>>>(V, out);
+  PF_CUDA(ctx, cudaGetLastError());
+  return PF_OK;
+}
+
+pf_status pf_grid_for(pf_ctx* ctx, const pf_volume* vol, const float** grid) {
+  if (vol->brick_majorants_dev) { *grid = vol->brick_majorants_dev; return PF_OK; }
+  const int64_t nb = (int64_t)((vol->nx + 7) / 8) * ((vol->ny + 7) / 8) * ((vol->nz + 7) / 8);
+  float* g;
+  PF_TRY(pf_scratch(ctx, WS_GRID, (size_t)nb * sizeof(float), (void**)&g));
+  PF_TRY(pf_brick_majorants_impl(ctx, vol, g));
+  *grid = g;
+  return PF_OK;
+}
+
+extern "C" pf_status pf_volume_brick_majorants(pf_ctx* ctx, const pf_volume* vol, float* out_dev) {
+  if (!ctx || !out_dev) return PF_ERR_INVALID_ARG;
+  DeviceGuard dg(ctx->device);
+  PF_TRY(pf_check_volume(ctx, vol));
+  return pf_brick_majorants_impl(ctx, vol, out_dev);
+}
 
 static void free_cache(pf_cache* c) {
   if (!c) return;
@@ -243,8 +292,8 @@ extern "C" pf_status pf_build_photon_cache(pf_ctx* ctx, const pf_volume* vol, co
   int64_t nc = (int64_t)res * res * res;
   int64_t n_keys = (int64_t)n_lights * n_g * nc;
   if (n_keys >= (1ll << 32)) return pf_fail(ctx, PF_ERR_INVALID_ARG, "too many cache keys");
-  float maj;
-  PF_TRY(pf_majorant_impl(ctx, vol, &maj));
+  const float* grid;
+  PF_TRY(pf_grid_for(ctx, vol, &grid));
 
   pf_cache* c = new pf_cache();
   c->ctx = ctx; c->device = ctx->device; c->res = res; c->n_lights = n_lights; c->n_g = n_g; c->max_bounces = max_bounces;
@@ -269,7 +318,7 @@ extern "C" pf_status pf_build_photon_cache(pf_ctx* ctx, const pf_volume* vol, co
 
   StageTimer tm(ctx, PF_STAGE_PHOTONS);
   TraceArgs A;
-  A.V = pf_make_vol(vol, maj);
+  A.V = pf_make_vol(vol, 0.f, grid);
   A.L = pf_make_lights(lights, n_lights);
   for (int i = 0; i < 16; ++i) A.g_set[i] = i < n_g ? g_set[i] : 0.f;
   A.n_g = n_g; A.max_bounces = max_bounces; A.res = res; A.use_rr = use_rr; A.N = N; A.seed = seed; A.n_photons = P;

@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 def test_trained_field_beats_no_field_and_untrained(pf_ctx):
     sc = I.scene_judge(48, 64, 64, 64)
     vol = api.Volume.from_inputs(sc.volume)
-    vol.s.majorant = vol.majorant(pf_ctx)
+    vol.attach_brick_majorants(pf_ctx)
     g = 0.0
     ref = api.render_pathtraced(pf_ctx, vol, sc.lights, g, sc.camera, 2048, 16, seed=1)
     cache = api.build_photon_cache(pf_ctx, vol, sc.lights, sc.g_set, 1 << 17, 16, 16, seed=2)

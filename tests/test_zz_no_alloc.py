@@ -32,7 +32,7 @@ def test_noalloc_matches_allocating_path_tracer(pf_ctx):
     L = _lib.load()
     sc = I.scene_judge(32, 48, 36, 8)
     vol = api.Volume.from_inputs(sc.volume)
-    vol.s.majorant = vol.majorant(pf_ctx)
+    vol.attach_brick_majorants(pf_ctx)
     ref = api.render_pathtraced(pf_ctx, vol, sc.lights, 0.5, sc.camera, sc.spp, 16, seed=13)
     pf_ctx.sync()
     msg = C.create_string_buffer(256)
@@ -45,7 +45,7 @@ def test_noalloc_matches_allocating_path_tracer(pf_ctx):
     assert float(ref.max()) > 0
 
 
-def test_noalloc_rejects_oversize_and_missing_majorant(pf_ctx):
+def test_noalloc_rejects_oversize_and_missing_majorants(pf_ctx):
     L = _lib.load()
     sc = I.scene_judge(16, 8, 8, 1)
     vol = api.Volume.from_inputs(sc.volume)
@@ -53,7 +53,7 @@ def test_noalloc_rejects_oversize_and_missing_majorant(pf_ctx):
     out = torch.zeros(8, 8, 3, device="cuda")
     st = _call(L, vol, sc.lights, 0.0, sc.camera, 1, 4, 1, out, msg)
     assert st == _lib.PF_ERR_INVALID_ARG and b"majorant" in msg.value
-    vol.s.majorant = vol.majorant(pf_ctx)
+    vol.attach_brick_majorants(pf_ctx)
     big = I.Camera(sc.camera.eye, sc.camera.at, sc.camera.up, 55.0, 2048, 2048)
     st = _call(L, vol, sc.lights, 0.0, big, 1, 4, 1, out, msg)
     assert st == _lib.PF_ERR_INVALID_ARG and b"static scratch" in msg.value
