@@ -167,141 +167,6 @@ __global__ void __launch_bounds__(128) k_camera_samples(Vol V, DevLights L, CamF
   }
 }
 
-// -------------------------------------------------------------- persistent tracking
-// Tracking mode as a per-lane state machine: every iteration each lane does
-// one tentative collision (one Philox block and one density lookup) of its
-// current walk -- the primary delta-tracking flight, then one ratio-tracking
-// shadow walk per light -- and a lane whose sample is finished takes the next
-// sample index from a global counter (warp-aggregated).  The random numbers
-// and float operations of every sample are those of k_camera_samples, so the
-// results are identical; what changes is that the lanes of a warp stay busy
-// while their walks have different lengths.
-template <int DT>
-__global__ void __launch_bounds__(128) k_track_persistent(Vol V, DevLights L, CamF cam, float g, int spp,
-                                                          uint64_t seed, int64_t n_slots, float* __restrict__ slot_ld,
-                                                          float* __restrict__ slot_li, float* __restrict__ cq,
-                                                          float* __restrict__ calb, uint32_t* __restrict__ cidx,
-                                                          uint32_t* __restrict__ ccount,
-                                                          unsigned long long* __restrict__ work, uint32_t* err,
-                                                          unsigned long long* stats) {
-  const int lane = threadIdx.x & 31;
-  const float sbar = V.majorant;
-  int64_t slot = -1;          // current sample; -1 = needs work; n_slots = retired
-  int phase = 0;              // 0 = primary flight, 1 + l = shadow walk towards light l
-  int steps = 0;
-  Rng rng(0, 0, 0, 0);
-  V3 o = v3(0.f, 0.f, 0.f), d = o, x = o, alb = o, Ld = o, wl = o, E = o;
-  float t = 0.f, tend = 0.f, T = 1.f;
-  uint32_t nfetch = 0;
-  for (;;) {
-    // ---- refill lanes without a sample (one atomic per warp)
-    const unsigned need = __ballot_sync(0xffffffffu, slot < 0);
-    if (need) {
-      unsigned long long base = 0;
-      if (lane == __ffs(need) - 1) base = atomicAdd(work, (unsigned long long)__popc(need));
-      base = __shfl_sync(0xffffffffu, base, __ffs(need) - 1);
-      if (slot < 0) {
-        const int64_t s = (int64_t)base + __popc(need & ((1u << lane) - 1u));
-        slot = s < n_slots ? s : n_slots;
-        if (slot < n_slots) {
-          const int k = (int)(slot % spp);
-          const int64_t pix = slot / spp;
-          rng = Rng(seed, TAG_CAMERA, (uint64_t)pix, (uint32_t)k);
-          float b0[4]; rng.uni4(b0);
-          camera_ray(cam, (int)(pix % cam.W), (int)(pix / cam.W), b0[0], b0[1], &o, &d);
-          float t0, t1;
-          phase = 0; steps = 0; Ld = v3(0.f, 0.f, 0.f); alb = Ld;
-          if (box_hit(o, d, &t0, &t1) && sbar > 0.f) { t = t0; tend = t1; }
-          else phase = -1;                               // no interaction: finished
-        }
-      }
-    }
-    if (__all_sync(0xffffffffu, slot >= n_slots)) break;
-    int done = 0;            // 1 = finished without interaction, 2 = finished with one
-    if (slot >= 0 && slot < n_slots) {
-      if (phase == -1) {
-        done = 1;
-      } else if (steps >= kMaxTrackSteps) {
-        atomicOr(err, 1u);
-        done = phase == 0 ? 1 : 2;
-      } else {
-        float u[4]; rng.uni4(u);
-        t = t + (-own_lnf(1.0f - u[0])) / sbar;
-        ++steps;
-        if (phase == 0) {
-          if (t >= tend) done = 1;
-          else {
-            const V3 xt = along(o, d, t);
-            float sg; V3 a;
-            medium_at<DT>(V, xt, &sg, &a);
-            ++nfetch;
-            if (u[1] * sbar < sg) {          // real collision: start the shadow walks
-              x = xt; alb = a;
-              phase = 1; steps = 0;
-            }
-          }
-        } else if (t < tend) {
-          const float f = 1.0f - sigma_at<DT>(V, along(x, wl, t)) / sbar;
-          ++nfetch;
-          T = T * mx(0.0f, f);
-        } else {                             // shadow walk of light phase-1 finished
-          const float ph = hg_eval(g, dot(d, wl));
-          Ld = v3(Ld.x + ph * T * E.x, Ld.y + ph * T * E.y, Ld.z + ph * T * E.z);
-          phase += 1; steps = 0;
-        }
-        // set up the next shadow walk (no lookup yet)
-        if (!done && phase >= 1 && steps == 0) {
-          if (phase > L.n) done = 2;
-          else {
-            float dist;
-            light_geom(L.l[phase - 1], x, &wl, &dist, &E);
-            float a0, a1;
-            tend = 0.f;
-            if (box_hit(x, wl, &a0, &a1)) tend = mn(a1, dist);
-            t = 0.f; T = 1.f;
-          }
-        }
-      }
-    }
-    // ---- finished samples: slot outputs, compacted field queries
-    if (done) {
-      slot_ld[3 * slot + 0] = done == 2 ? alb.x * Ld.x : 0.f;
-      slot_ld[3 * slot + 1] = done == 2 ? alb.y * Ld.y : 0.f;
-      slot_ld[3 * slot + 2] = done == 2 ? alb.z * Ld.z : 0.f;
-      slot_li[3 * slot + 0] = 0.f;
-      slot_li[3 * slot + 1] = 0.f;
-      slot_li[3 * slot + 2] = 0.f;
-    }
-    const unsigned app = __ballot_sync(0xffffffffu, done == 2 && cq != nullptr);
-    if (app) {
-      uint32_t base = 0;
-      if (lane == __ffs(app) - 1) base = atomicAdd(ccount, (uint32_t)__popc(app));
-      base = __shfl_sync(0xffffffffu, base, __ffs(app) - 1);
-      if (done == 2) {
-        const uint32_t i = base + __popc(app & ((1u << lane) - 1u));
-        const V3 w = v3(-d.x, -d.y, -d.z);
-        float th = acosf(fminf(fmaxf(w.z, -1.f), 1.f)) * 0.318309886183790672f;
-        float ph = atan2f(w.y, w.x) * 0.159154943091895336f;
-        if (ph < 0.f) ph = ph + 1.0f;
-        cq[6 * (size_t)i + 0] = x.x; cq[6 * (size_t)i + 1] = x.y; cq[6 * (size_t)i + 2] = x.z;
-        cq[6 * (size_t)i + 3] = th;  cq[6 * (size_t)i + 4] = ph;  cq[6 * (size_t)i + 5] = g;
-        calb[3 * (size_t)i + 0] = alb.x; calb[3 * (size_t)i + 1] = alb.y; calb[3 * (size_t)i + 2] = alb.z;
-        cidx[i] = (uint32_t)slot;
-      }
-    }
-    if (stats) {
-      const unsigned nv = __popc(__ballot_sync(0xffffffffu, done == 2));
-      if (lane == 0 && nv) atomicAdd(stats + 1, (unsigned long long)nv);
-    }
-    if (done) slot = -1;
-  }
-  if (stats) {
-    unsigned long long v = nfetch;
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    if (lane == 0 && v) atomicAdd(stats, v);
-  }
-}
-
 __global__ void k_compose(const float* __restrict__ slot_ld, const float* __restrict__ slot_li, int64_t n_pix,
                           int spp, float* __restrict__ out) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -462,21 +327,7 @@ extern "C" pf_status pf_render_neural(pf_ctx* ctx, const pf_volume* vol, const p
   float h = step_vox > 0.f ? step_vox / (float)nmax : 0.f;
   dim3 blk(128), grd((unsigned)((n_slots + 127) / 128));
   bool march = step_vox > 0.f;
-  if (!march) {
-    // persistent tracking: a work counter in the scratch arena, grid = resident CTAs
-    unsigned long long* work;
-    PF_TRY(pf_scratch(ctx, WS_REDUCE, 64, (void**)&work));
-    StageTimer tm(ctx, PF_STAGE_CAMERA);
-    PF_CUDA(ctx, cudaMemsetAsync(work, 0, sizeof(unsigned long long), ctx->stream));
-    int per_sm = 0;
-    auto kern = vol->dtype == PF_F32 ? k_track_persistent<0> : vol->dtype == PF_F16 ? k_track_persistent<1>
-                                                                                     : k_track_persistent<2>;
-    PF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0));
-    int64_t want = (n_slots + 127) / 128;
-    unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ctx->num_sms * std::max(per_sm, 1)));
-    kern<<<grid, 128, 0, ctx->stream>>>(V, L, C, g, spp, seed, n_slots, ld, li, cq, calb, cidx, ccount, work,
-                                        ctx->err_dev, ctx->counters);
-  } else {
+  {
   StageTimer tm(ctx, PF_STAGE_CAMERA);
 #define LAUNCH_CS(DT)                                                                                              \
   if (march) k_camera_samples<DT, true><<<grd, blk, 0, ctx->stream>>>(V, L, C, g, spp, h, seed, n_slots, ld, li, cq, \
