@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "1080p frames/sec and field queries/sec vs plain GPU path tracer at equal RMSE"
 W_, H_, SPP, N_VOX, N_LIGHTS = 1920, 1080, 16, 1024, 8
+BRICK = 16                      # majorant brick edge (voxels) for the 1024^3 volume
 HIDDEN, N_HIDDEN, FREQS = 128, 4, 12
 VOXEL_BYTES = 2                 # float16
 FETCH_BYTES = 8 * VOXEL_BYTES   # one trilinear lookup reads 8 voxels
@@ -108,12 +109,12 @@ def setup_scene(device):
     return vol_t.contiguous(), torch.from_numpy(tf).to(device), lights, cams
 
 
-def cpu_baseline(vol_host, tf, lights, cams, seed, rows=2, weights=None, desc=None, scales=None):
+def cpu_baseline(vol_host, tf, lights, cams, seed, rows=2, weights=None, desc=None, scales=None, brick=8):
     """The oracle (plain C++/numpy) on a bounded sample: `rows` full image rows
     of one frame at full spp, scaled to a frame."""
     import oracle
     from paper_2304_07338_b300 import inputs as I
-    v = I.Volume(vol_host, 20.0, 0.9, tf)
+    v = I.Volume(vol_host, 20.0, 0.9, tf, brick=brick)
     cam = cams[0]
     g = I.frame_g(seed, 0)
     y0 = H_ // 2
@@ -147,6 +148,7 @@ def main():
     ap.add_argument("--rmse-width", type=int, default=480)
     ap.add_argument("--rmse-height", type=int, default=270)
     ap.add_argument("--ref-spp", type=int, default=4096)
+    ap.add_argument("--brick", type=int, default=BRICK, help="majorant brick edge in voxels (power of two)")
     args = ap.parse_args()
     W_, H_, SPP, N_VOX = args.width, args.height, args.spp, args.res
     args.warmup = max(args.warmup, 3)
@@ -174,7 +176,7 @@ def main():
     build.build()
     ctx = api.Context(local)
     vol_t, tf_t, lights, cams = setup_scene(dev)
-    vol = api.Volume(vol_t, 20.0, 0.9, tf_t)
+    vol = api.Volume(vol_t, 20.0, 0.9, tf_t, brick=args.brick)
     vol.s.majorant = vol.majorant(ctx)
     vol.attach_brick_majorants(ctx)
     setup = {}
@@ -286,7 +288,7 @@ def main():
         "config": {"workload": "large neural render: %d^3 f16 turbulence, 8 point lights, %dx%d, %d spp, "
                                "fp8 4x128 field, delta/ratio tracking" % (N_VOX, W_, H_, SPP),
                    "frames": "60-frame orbit", "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (2 GiB volume)"},
+                   "l2": "inputs larger than L2 (2 GiB volume)", "majorant_brick": args.brick},
         "queries_per_s": qpf * fps,
         "queries_per_frame": qpf,
         "stages_ms_per_frame": {k: v[0] / max(args.steps, 1) for k, v in stages.items() if v[1]},
@@ -303,7 +305,7 @@ def main():
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         try:
             line["cpu_baseline"] = cpu_baseline(vol_t.cpu().numpy(), tf_t.cpu().numpy(), lights, cams, seed,
-                                                rows=args.cpu_rows, **oracle_field(field))
+                                                rows=args.cpu_rows, brick=args.brick, **oracle_field(field))
         except Exception as e:  # reported, not fatal
             line["cpu_baseline"] = {"error": repr(e)[:200]}
     if rank == 0:
@@ -433,15 +435,21 @@ def run_reference(args, dev, seed):
     import torch
     vol_t, tf_t, lights, cams = setup_scene(dev)
     vol_h, tf_h = vol_t.cpu().numpy(), tf_t.cpu().numpy()
-    from paper_2304_07338_b300 import api  # noqa: F401  (only for PfCamera sizes)
+    from oracle import field as F
+    # a 4x128 fp8 field of the bench's shape (Kaiming init, calibrated scales):
+    # the same per-sample work as the trained field
+    desc = F.FieldDesc(FREQS, HIDDEN, N_HIDDEN, F.PREC_FP8, 5.0, seed + 3)
+    w = F.init_weights(desc).astype(np.float64)
+    fld = dict(weights=w, desc=desc, scales=F.fp8_calibrate(w, calibration_queries().numpy().astype(np.float64),
+                                                            desc))
     times = []
     for i in range(args.warmup + args.steps):
-        r = cpu_baseline(vol_h, tf_h, lights, cams, seed, rows=1)
+        r = cpu_baseline(vol_h, tf_h, lights, cams, seed, rows=1, brick=args.brick, **fld)
         if i >= args.warmup:
             times.append(1.0 / r["value"])
     fps = 1.0 / float(np.mean(times))
     cb = {"value": fps, "unit": "frames/s", "cores": os.cpu_count(), "kind": "oracle",
-          "sample": "1 of %d rows per step at full spp, scaled to a frame" % H_}
+          "sample": "1 of %d rows per step at full spp (4x128 fp8 field, Kaiming init), scaled to a frame" % H_}
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": 1,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / fps,
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64/f32 oracle",

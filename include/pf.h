@@ -74,8 +74,9 @@ typedef struct {
   const float* tf_lut_dev;  /* tf_n x 4 RGBA rows over d in [0,1], tf_n >= 2 */
   int tf_n;
   float majorant;           /* global max of sigma_t (informational; 0 = unknown) */
-  const float* brick_majorants_dev; /* per-8^3-brick majorants from pf_volume_brick_majorants, or
-                                       NULL: the tracers then compute them into context scratch */
+  const float* brick_majorants_dev; /* brick majorants from pf_volume_brick_majorants, or NULL:
+                                       the tracers then compute them into context scratch */
+  int brick;                /* majorant brick edge in voxels: power of two, 0 = 8 */
 } pf_volume;
 
 /* Light source.  Directional: v = unit direction towards the light, rgb =
@@ -150,12 +151,15 @@ pf_status pf_sync(pf_ctx* ctx);
  * float to out_host. */
 pf_status pf_volume_majorant(pf_ctx* ctx, const pf_volume* vol, float* out_host);
 /* Brick majorants used by delta and ratio tracking (regular tracking over a
- * piecewise-constant majorant).  Brick (i,j,k) covers voxels [8i, 8i+8) per
- * axis (region between the planes min(8i, n)/n); its majorant is
+ * piecewise-constant majorant).  With B = vol->brick, brick (i,j,k) covers
+ * voxels [Bi, Bi+B) per axis (region between the planes Bi/n and B(i+1)/n,
+ * the last brick cut by the box); its majorant is
  * sigma_scale times the largest TF alpha over the density range of the
  * voxels trilinear interpolation can reach there (the brick plus a one-voxel
  * apron, and density 0 for bricks on the box boundary), times (1 + 2^-10).
- * out_dev: ceil(nx/8)*ceil(ny/8)*ceil(nz/8) floats, x fastest. */
+ * out_dev: ceil(nx/B)*ceil(ny/B)*ceil(nz/B) floats, x fastest.  Tracing walks
+ * the bricks with an incremental DDA and spends each tentative collision's
+ * optical-depth budget brick by brick. */
 pf_status pf_volume_brick_majorants(pf_ctx* ctx, const pf_volume* vol, float* out_dev);
 
 /* ---------------------------------------------------------------- photon caches */

@@ -46,17 +46,17 @@ def _declare(L):
     L.orc_density.argtypes = [i32, i32, i32, i32, P, P, i64, P, i32]
     L.orc_majorant.argtypes = [i32, i32, i32, i32, P, f64, f64, P, i32, i32]
     L.orc_majorant.restype = f64
-    L.orc_free_flight.argtypes = [i32, i32, i32, i32, P, f64, P, i32, P, P, i64, u64, P, P]
-    L.orc_brick_majorants.argtypes = [i32, i32, i32, i32, P, f64, P, i32, i32, P]
-    L.orc_ratio_mean.argtypes = [i32, i32, i32, i32, P, f64, P, i32, P, P, f64, i64, u64, P]
+    L.orc_free_flight.argtypes = [i32, i32, i32, i32, P, f64, P, i32, i32, P, P, i64, u64, P, P]
+    L.orc_brick_majorants.argtypes = [i32, i32, i32, i32, P, f64, P, i32, i32, i32, P]
+    L.orc_ratio_mean.argtypes = [i32, i32, i32, i32, P, f64, P, i32, i32, P, P, f64, i64, u64, P]
     L.orc_ratio_mean.restype = f64
-    L.orc_trace_photons.argtypes = [i32, i32, i32, i32, P, f64, f64, P, i32,
+    L.orc_trace_photons.argtypes = [i32, i32, i32, i32, P, f64, f64, P, i32, i32,
                                     P, P, P, i32, P, i32, u64, i32, i32, u64, i32, i32, u64, u64,
                                     P, P, P, P, P]
-    L.orc_camera_samples.argtypes = [i32, i32, i32, i32, P, f64, f64, P, i32,
+    L.orc_camera_samples.argtypes = [i32, i32, i32, i32, P, f64, f64, P, i32, i32,
                                      P, P, P, i32, f64, P, P, P, f64, i32, i32,
                                      i32, f64, u64, i32, i32, i32, P, P, P, P, P]
-    L.orc_path_trace.argtypes = [i32, i32, i32, i32, P, f64, f64, P, i32,
+    L.orc_path_trace.argtypes = [i32, i32, i32, i32, P, f64, f64, P, i32, i32,
                                  P, P, P, i32, f64, P, P, P, f64, i32, i32,
                                  i32, i32, u64, i32, i32, i32, i32, P, i64, P]
     L.orc_cell_sigma.argtypes = [i32, i32, i32, i32, P, f64, P, i32, i32, P]
@@ -83,6 +83,7 @@ class _Vol:
         self.ss = float(vol.sigma_scale)
         self.alb = float(vol.albedo)
         self.tfargs = (_p(self.tf), int(self.tf.shape[0]))
+        self.brick = int(getattr(vol, "brick", 8))
 
 
 class _Lights:
@@ -169,12 +170,12 @@ def majorant(vol, fp32: bool = False) -> float:
 
 
 def brick_majorants(vol, fp32: bool = False) -> np.ndarray:
-    """Majorant per 8^3 brick (x fastest), bounding sigma_t inside each brick."""
+    """Majorant per brick (x fastest), bounding sigma_t inside each brick."""
     v = _Vol(vol)
     nz, ny, nx = vol.data.shape
-    g = [(a + 7) // 8 for a in (nx, ny, nz)]
+    g = [(a + v.brick - 1) // v.brick for a in (nx, ny, nz)]
     out = np.zeros(g[0] * g[1] * g[2])
-    lib().orc_brick_majorants(*v.args, v.ss, *v.tfargs, int(fp32), _p(out))
+    lib().orc_brick_majorants(*v.args, v.ss, *v.tfargs, v.brick, int(fp32), _p(out))
     return out.reshape(g[2], g[1], g[0])
 
 
@@ -184,7 +185,7 @@ def ratio_mean(vol, o, d, t_end: float, n: int, seed: int):
     o = np.ascontiguousarray(o, np.float64)
     d = np.ascontiguousarray(d, np.float64)
     var = np.zeros(1)
-    m = lib().orc_ratio_mean(*v.args, v.ss, *v.tfargs, _p(o), _p(d), float(t_end), n, seed, _p(var))
+    m = lib().orc_ratio_mean(*v.args, v.ss, *v.tfargs, v.brick, _p(o), _p(d), float(t_end), n, seed, _p(var))
     return m, float(var[0])
 
 
@@ -195,7 +196,7 @@ def free_flight(vol, o, d, n: int, seed: int):
     d = np.ascontiguousarray(d, np.float64)
     out = np.zeros(n)
     steps = np.zeros(1, np.int64)
-    lib().orc_free_flight(*v.args, v.ss, *v.tfargs, _p(o), _p(d), n, seed, _p(out), _p(steps))
+    lib().orc_free_flight(*v.args, v.ss, *v.tfargs, v.brick, _p(o), _p(d), n, seed, _p(out), _p(steps))
     return out, int(steps[0])
 
 
@@ -215,7 +216,7 @@ def trace_photons(vol, lights, g_set, n_per, max_bounces: int = 16, res: int = 6
     phis = np.zeros((P, S, 3), np.float32)
     nrec = np.zeros(P, np.int32)
     tally = np.zeros(15)
-    lib().orc_trace_photons(*v.args, v.ss, v.alb, *v.tfargs, *L.args, _p(g), len(g), n_per, max_bounces, res,
+    lib().orc_trace_photons(*v.args, v.ss, v.alb, *v.tfargs, v.brick, *L.args, _p(g), len(g), n_per, max_bounces, res,
                             seed, int(use_rr), int(fp32), p_begin, p_end,
                             _p(keys), _p(dirs), _p(phis), _p(nrec), _p(tally))
     return dict(keys=keys, dirs=dirs, phis=phis, nrec=nrec, tally=tally.reshape(5, 3),
@@ -321,7 +322,7 @@ def camera_samples(vol, lights, g: float, cam, spp: int, step_vox: float, seed: 
     n = (y1 - y0) * cam.width * spp
     valid = np.zeros(n, np.uint8)
     x, wo, alb, Ld = (np.zeros((n, 3)) for _ in range(4))
-    lib().orc_camera_samples(*v.args, v.ss, v.alb, *v.tfargs, *L.args, float(g), *cm.args, spp,
+    lib().orc_camera_samples(*v.args, v.ss, v.alb, *v.tfargs, v.brick, *L.args, float(g), *cm.args, spp,
                              float(step_vox), seed, int(fp32), y0, y1,
                              _p(valid), _p(x), _p(wo), _p(alb), _p(Ld))
     shp = (y1 - y0, cam.width, spp)
@@ -356,11 +357,11 @@ def path_trace(vol, lights, g: float, cam, spp: int, max_bounces: int = 16, seed
     if pixels is not None:
         px = np.ascontiguousarray(pixels, np.int32)
         out = np.zeros((px.shape[0], 3))
-        lib().orc_path_trace(*v.args, v.ss, v.alb, *v.tfargs, *L.args, float(g), *cm.args, spp, max_bounces,
+        lib().orc_path_trace(*v.args, v.ss, v.alb, *v.tfargs, v.brick, *L.args, float(g), *cm.args, spp, max_bounces,
                              seed, int(use_rr), int(fp32), 0, 0, _p(px), px.shape[0], _p(out))
         return out
     out = np.zeros(((y1 - y0) * cam.width, 3))
-    lib().orc_path_trace(*v.args, v.ss, v.alb, *v.tfargs, *L.args, float(g), *cm.args, spp, max_bounces,
+    lib().orc_path_trace(*v.args, v.ss, v.alb, *v.tfargs, v.brick, *L.args, float(g), *cm.args, spp, max_bounces,
                          seed, int(use_rr), int(fp32), y0, y1, None, 0, _p(out))
     return out.reshape(y1 - y0, cam.width, 3)
 

@@ -313,16 +313,16 @@ template <typename R> V3<R> hg_sample(R g, V3<R> d, R xi1, R xi2) {
     return normalize(nd);
 }
 
-// Brick majorant grid.  Brick (i,j,k) covers voxels [8i, 8i+8) per axis and
-// the region between the planes x = 8i/nx and min(8i+8, nx)/nx (same for y,
-// z).  Its majorant bounds sigma_t anywhere in that region: sigma_scale times
-// the largest TF alpha over the density range [dmin, dmax] of the voxels
-// trilinear interpolation can reach there (the brick plus a one-voxel apron;
-// bricks on the box boundary also include density 0, the value outside the
-// box), times (1 + 2^-10).
-constexpr int kBrick = 8;
+// Brick majorant grid.  Brick (i,j,k) covers voxels [B i, B i + B) per axis
+// (B = brick edge in voxels, a power of two) and the region between the
+// planes x = B i / nx and B (i+1) / nx (same for y, z; the last brick is cut
+// by the box).  Its majorant bounds sigma_t anywhere in that region, extended
+// by half a voxel: sigma_scale times the largest TF alpha over the density
+// range [dmin, dmax] of the voxels trilinear interpolation can reach there
+// (the brick plus a one-voxel apron; bricks on the box boundary also include
+// density 0, the value outside the box), times (1 + 2^-10).
 template <typename R> struct Grid {
-    int gx, gy, gz, nx, ny, nz;
+    int gx, gy, gz, nx, ny, nz, B;
     std::vector<R> m;
     R at(int i, int j, int k) const { return m[(size_t)i + (size_t)gx * ((size_t)j + (size_t)gy * k)]; }
 };
@@ -338,18 +338,18 @@ template <typename R> R tf_alpha_max(const Volume& V, R dmin, R dmax) {
     return a;
 }
 
-template <typename R> Grid<R> build_grid(const Volume& V) {
+template <typename R> Grid<R> build_grid(const Volume& V, int B) {
     Grid<R> G;
-    G.nx = V.nx; G.ny = V.ny; G.nz = V.nz;
-    G.gx = (V.nx + kBrick - 1) / kBrick; G.gy = (V.ny + kBrick - 1) / kBrick; G.gz = (V.nz + kBrick - 1) / kBrick;
+    G.nx = V.nx; G.ny = V.ny; G.nz = V.nz; G.B = B;
+    G.gx = (V.nx + B - 1) / B; G.gy = (V.ny + B - 1) / B; G.gz = (V.nz + B - 1) / B;
     G.m.assign((size_t)G.gx * G.gy * G.gz, (R)0);
     for (int bz = 0; bz < G.gz; ++bz)
         for (int by = 0; by < G.gy; ++by)
             for (int bx = 0; bx < G.gx; ++bx) {
                 R dmin = (R)INFINITY, dmax = (R)-INFINITY;
-                for (int k = std::max(kBrick * bz - 1, 0); k <= std::min(kBrick * bz + kBrick, V.nz - 1); ++k)
-                    for (int j = std::max(kBrick * by - 1, 0); j <= std::min(kBrick * by + kBrick, V.ny - 1); ++j)
-                        for (int i = std::max(kBrick * bx - 1, 0); i <= std::min(kBrick * bx + kBrick, V.nx - 1); ++i) {
+                for (int k = std::max(B * bz - 1, 0); k <= std::min(B * bz + B, V.nz - 1); ++k)
+                    for (int j = std::max(B * by - 1, 0); j <= std::min(B * by + B, V.ny - 1); ++j)
+                        for (int i = std::max(B * bx - 1, 0); i <= std::min(B * bx + B, V.nx - 1); ++i) {
                             R d = voxel<R>(V, i, j, k);
                             if (d < dmin) dmin = d;
                             if (d > dmax) dmax = d;
@@ -362,27 +362,32 @@ template <typename R> Grid<R> build_grid(const Volume& V) {
     return G;
 }
 
-// Walk over the bricks a ray crosses (Amanatides-Woo stepping).  The brick
-// planes are at min(8i, n)/n; the first brick comes from the start point.
+// Walk over the bricks a ray crosses (Amanatides-Woo).  Per axis: brick
+// width w = B / n, inverse direction inv = 1/d; the first plane parameter is
+// (plane - o) * inv and each further plane adds w * |inv|.  The rounding of
+// the plane parameters stays far below the half-voxel margin of the brick
+// majorants.
 template <typename R> struct Walk {
-    int c[3], s[3], g[3], n[3];
-    R tn[3];          // ray parameter of the next brick plane per axis
-    R o[3], d[3];
-    R plane_t(int a) const {
-        if (s[a] == 0) return (R)INFINITY;
-        int vi = s[a] > 0 ? std::min((c[a] + 1) * kBrick, n[a]) : c[a] * kBrick;
-        R p = (R)vi / (R)n[a];
-        return (p - o[a]) / d[a];
-    }
-    void init(const Grid<R>& G, V3<R> oo, V3<R> dd, R t) {
-        o[0] = oo.x; o[1] = oo.y; o[2] = oo.z; d[0] = dd.x; d[1] = dd.y; d[2] = dd.z;
-        g[0] = G.gx; g[1] = G.gy; g[2] = G.gz; n[0] = G.nx; n[1] = G.ny; n[2] = G.nz;
+    int c[3], s[3], g[3];
+    R tn[3], dt[3];
+    void init(const Grid<R>& G, V3<R> o, V3<R> d, R t) {
+        const R oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
+        const int n[3] = {G.nx, G.ny, G.nz};
+        g[0] = G.gx; g[1] = G.gy; g[2] = G.gz;
         for (int a = 0; a < 3; ++a) {
-            R p = o[a] + t * d[a];
-            int ci = (int)std::floor(p * ((R)n[a] * (R)0.125));
+            R w = (R)G.B / (R)n[a];
+            R p = oo[a] + t * dd[a];
+            int ci = (int)std::floor(p / w);
             c[a] = std::min(std::max(ci, 0), g[a] - 1);
-            s[a] = d[a] > (R)0 ? 1 : (d[a] < (R)0 ? -1 : 0);
-            tn[a] = plane_t(a);
+            if (dd[a] > (R)0) {
+                R inv = (R)1 / dd[a];
+                s[a] = 1; tn[a] = ((R)(c[a] + 1) * w - oo[a]) * inv; dt[a] = w * inv;
+            } else if (dd[a] < (R)0) {
+                R inv = (R)1 / dd[a];
+                s[a] = -1; tn[a] = ((R)c[a] * w - oo[a]) * inv; dt[a] = -(w * inv);
+            } else {
+                s[a] = 0; tn[a] = (R)INFINITY; dt[a] = (R)INFINITY;
+            }
         }
     }
     R exit_t() const { return std::min(tn[0], std::min(tn[1], tn[2])); }
@@ -391,7 +396,7 @@ template <typename R> struct Walk {
         int a = (tn[0] <= tn[1] && tn[0] <= tn[2]) ? 0 : (tn[1] <= tn[2] ? 1 : 2);
         c[a] += s[a];
         if (c[a] < 0 || c[a] >= g[a]) return false;
-        tn[a] = plane_t(a);
+        tn[a] = tn[a] + dt[a];
         return true;
     }
 };
@@ -789,18 +794,18 @@ double orc_majorant(int nx, int ny, int nz, int dtype, const void* data, double 
 }
 
 // Brick majorant grid (gx*gy*gz values, x fastest).
-void orc_brick_majorants(int nx, int ny, int nz, int dtype, const void* data, double ss, const float* tf, int tf_n,
+void orc_brick_majorants(int nx, int ny, int nz, int dtype, const void* data, double ss, const float* tf, int tf_n, int brick,
                          int fp32, double* out) {
     Volume V = mkvol(nx, ny, nz, dtype, data, ss, 1.0, tf, tf_n);
-    if (fp32) { Grid<float> G = build_grid<float>(V); for (size_t i = 0; i < G.m.size(); ++i) out[i] = G.m[i]; }
-    else { Grid<double> G = build_grid<double>(V); for (size_t i = 0; i < G.m.size(); ++i) out[i] = G.m[i]; }
+    if (fp32) { Grid<float> G = build_grid<float>(V, brick); for (size_t i = 0; i < G.m.size(); ++i) out[i] = G.m[i]; }
+    else { Grid<double> G = build_grid<double>(V, brick); for (size_t i = 0; i < G.m.size(); ++i) out[i] = G.m[i]; }
 }
 
 // Mean ratio-tracking transmittance from o along d over [0, t_end) (n walks).
-double orc_ratio_mean(int nx, int ny, int nz, int dtype, const void* data, double ss, const float* tf, int tf_n,
+double orc_ratio_mean(int nx, int ny, int nz, int dtype, const void* data, double ss, const float* tf, int tf_n, int brick,
                       const double* o, const double* d, double t_end, int64_t n, uint64_t seed, double* var) {
     Volume V = mkvol(nx, ny, nz, dtype, data, ss, 1.0, tf, tf_n);
-    Grid<double> G = build_grid<double>(V);
+    Grid<double> G = build_grid<double>(V, brick);
     double s = 0, s2 = 0;
     for (int64_t i = 0; i < n; ++i) {
         Rng r(seed, 2, (uint64_t)i, 0);
@@ -813,10 +818,10 @@ double orc_ratio_mean(int nx, int ny, int nz, int dtype, const void* data, doubl
 
 // Free-flight distances by delta tracking from o along d (one item per
 // sample, Philox tag PHOTON, item i); -1 where the ray leaves the box.
-void orc_free_flight(int nx, int ny, int nz, int dtype, const void* data, double ss, const float* tf, int tf_n,
+void orc_free_flight(int nx, int ny, int nz, int dtype, const void* data, double ss, const float* tf, int tf_n, int brick,
                      const double* o, const double* d, int64_t n, uint64_t seed, double* out, int64_t* steps) {
     Volume V = mkvol(nx, ny, nz, dtype, data, ss, 1.0, tf, tf_n);
-    Grid<double> G = build_grid<double>(V);
+    Grid<double> G = build_grid<double>(V, brick);
     long st = 0;
     for (int64_t i = 0; i < n; ++i) {
         Rng r(seed, 2, (uint64_t)i, 0);
@@ -832,7 +837,7 @@ void orc_free_flight(int nx, int ny, int nz, int dtype, const void* data, double
 // max_bounces - 1; nrec[p] = records of photon p.  tally[15] = emitted,
 // escaped, absorbed, truncated, rr (3 channels each).
 void orc_trace_photons(int nx, int ny, int nz, int dtype, const void* data, double ss, double alb,
-                       const float* tf, int tf_n,
+                       const float* tf, int tf_n, int brick,
                        const int* lkind, const double* lv, const double* lrgb, int n_lights,
                        const float* gset, int n_g, uint64_t N, int max_bounces, int res, uint64_t seed,
                        int use_rr, int fp32, uint64_t p_begin, uint64_t p_end,
@@ -840,8 +845,8 @@ void orc_trace_photons(int nx, int ny, int nz, int dtype, const void* data, doub
     Volume V = mkvol(nx, ny, nz, dtype, data, ss, alb, tf, tf_n);
     std::vector<Light> L = mklights(lkind, lv, lrgb, n_lights);
     int S = max_bounces - 1 > 0 ? max_bounces - 1 : 1;
-    Grid<double> G64 = fp32 ? Grid<double>() : build_grid<double>(V);
-    Grid<float> G32 = fp32 ? build_grid<float>(V) : Grid<float>();
+    Grid<double> G64 = fp32 ? Grid<double>() : build_grid<double>(V, brick);
+    Grid<float> G32 = fp32 ? build_grid<float>(V, brick) : Grid<float>();
     Tally tot; std::memset(&tot, 0, sizeof(tot));
     #pragma omp parallel
     {
@@ -871,7 +876,7 @@ void orc_trace_photons(int nx, int ny, int nz, int dtype, const void* data, doub
 // Camera samples of the neural renderer (Algorithm 2: RayGeneration,
 // VolumeSampling, DirectIllumination).  Arrays are [H][W][spp].
 void orc_camera_samples(int nx, int ny, int nz, int dtype, const void* data, double ss, double alb,
-                        const float* tf, int tf_n,
+                        const float* tf, int tf_n, int brick,
                         const int* lkind, const double* lv, const double* lrgb, int n_lights, double g,
                         const double* eye, const double* at, const double* up, double fovy, int W, int H,
                         int spp, double step_vox, uint64_t seed, int fp32, int y_begin, int y_end,
@@ -879,8 +884,8 @@ void orc_camera_samples(int nx, int ny, int nz, int dtype, const void* data, dou
     Volume V = mkvol(nx, ny, nz, dtype, data, ss, alb, tf, tf_n);
     std::vector<Light> L = mklights(lkind, lv, lrgb, n_lights);
     CamFrame cf = cam_frame(eye, at, up, fovy, W, H);
-    Grid<double> G64 = fp32 ? Grid<double>() : build_grid<double>(V);
-    Grid<float> G32 = fp32 ? build_grid<float>(V) : Grid<float>();
+    Grid<double> G64 = fp32 ? Grid<double>() : build_grid<double>(V, brick);
+    Grid<float> G32 = fp32 ? build_grid<float>(V, brick) : Grid<float>();
     #pragma omp parallel for schedule(dynamic, 1) collapse(2)
     for (int py = y_begin; py < y_end; ++py)
         for (int px = 0; px < W; ++px)
@@ -910,7 +915,7 @@ void orc_camera_samples(int nx, int ny, int nz, int dtype, const void* data, dou
 // per-pixel mean over spp samples accumulated in sample order; or an explicit
 // list of (x, y) pixels.
 void orc_path_trace(int nx, int ny, int nz, int dtype, const void* data, double ss, double alb,
-                    const float* tf, int tf_n,
+                    const float* tf, int tf_n, int brick,
                     const int* lkind, const double* lv, const double* lrgb, int n_lights, double g,
                     const double* eye, const double* at, const double* up, double fovy, int W, int H,
                     int spp, int max_bounces, uint64_t seed, int use_rr, int fp32, int y_begin, int y_end,
@@ -918,8 +923,8 @@ void orc_path_trace(int nx, int ny, int nz, int dtype, const void* data, double 
     Volume V = mkvol(nx, ny, nz, dtype, data, ss, alb, tf, tf_n);
     std::vector<Light> L = mklights(lkind, lv, lrgb, n_lights);
     CamFrame cf = cam_frame(eye, at, up, fovy, W, H);
-    Grid<double> G64 = fp32 ? Grid<double>() : build_grid<double>(V);
-    Grid<float> G32 = fp32 ? build_grid<float>(V) : Grid<float>();
+    Grid<double> G64 = fp32 ? Grid<double>() : build_grid<double>(V, brick);
+    Grid<float> G32 = fp32 ? build_grid<float>(V, brick) : Grid<float>();
     int64_t n_items = px_list ? n_px : (int64_t)(y_end - y_begin) * W;
     #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t it = 0; it < n_items; ++it) {

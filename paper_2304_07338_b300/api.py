@@ -83,7 +83,7 @@ class Volume:
     """Device-resident volume + transfer function (pf_volume)."""
 
     def __init__(self, data: torch.Tensor, sigma_scale: float, albedo: float, tf: torch.Tensor,
-                 majorant: float = 0.0):
+                 majorant: float = 0.0, brick: int = 8):
         code = {torch.float32: 0, torch.float16: 1, torch.uint8: 2}[data.dtype]
         if not data.is_cuda or not data.is_contiguous() or data.dim() != 3:
             raise ValueError("volume data must be a contiguous 3-D CUDA tensor (nz, ny, nx)")
@@ -91,7 +91,7 @@ class Volume:
         self.data, self.tf = data, tf
         nz, ny, nx = data.shape
         self.s = PfVolume(nx, ny, nz, code, data.data_ptr(), float(sigma_scale), float(albedo), tf.data_ptr(),
-                          int(tf.shape[0]), float(majorant), None)
+                          int(tf.shape[0]), float(majorant), None, int(brick))
         self.grid = None
 
     @classmethod
@@ -99,12 +99,14 @@ class Volume:
         """From a paper_2304_07338_b300.inputs.Volume (numpy arrays)."""
         data = torch.from_numpy(np.ascontiguousarray(vol.data)).to(device)
         tf = torch.from_numpy(np.ascontiguousarray(vol.tf, np.float32)).to(device)
-        return cls(data, vol.sigma_scale, vol.albedo, tf)
+        return cls(data, vol.sigma_scale, vol.albedo, tf, brick=getattr(vol, "brick", 8))
 
     def brick_majorants(self, ctx: Context) -> torch.Tensor:
         """Per-8^3-brick majorants (computed on the GPU), shape (gz, gy, gx)."""
         nz, ny, nx = self.data.shape
-        g = torch.empty(((nz + 7) // 8, (ny + 7) // 8, (nx + 7) // 8), dtype=torch.float32, device=self.data.device)
+        B = self.s.brick or 8
+        g = torch.empty(((nz + B - 1) // B, (ny + B - 1) // B, (nx + B - 1) // B), dtype=torch.float32,
+                        device=self.data.device)
         ctx.check(ctx.lib.pf_volume_brick_majorants(ctx.h, C.byref(self.s), _ptr(g)))
         return g
 

@@ -164,6 +164,8 @@ pf_status pf_check_volume(pf_ctx* ctx, const pf_volume* v) {
   if (!(v->sigma_scale >= 0.f) || !std::isfinite(v->sigma_scale) || !(v->albedo >= 0.f))
     return pf_fail(ctx, PF_ERR_INVALID_ARG, "sigma_scale and albedo must be finite and non-negative");
   if (!(v->majorant >= 0.f) || !std::isfinite(v->majorant)) return pf_fail(ctx, PF_ERR_INVALID_ARG, "majorant must be >= 0");
+  if (v->brick != 0 && (v->brick < 2 || v->brick > 256 || (v->brick & (v->brick - 1))))
+    return pf_fail(ctx, PF_ERR_INVALID_ARG, "brick must be 0 (= 8) or a power of two in [2, 256]");
   return PF_OK;
 }
 

@@ -134,10 +134,10 @@ struct Vol {
   float sigma_scale, albedo, majorant;
   const float4* tf;   // RGBA rows
   int tf_n;
-  const float* mg;    // brick majorants (8^3 bricks, x fastest)
-  int gx, gy, gz;
+  const float* mg;    // brick majorants (x fastest)
+  int gx, gy, gz, B;  // brick grid and brick edge (voxels)
+  float wx, wy, wz;   // brick edge in world units, B / n (IEEE division)
 };
-constexpr int kBrick = 8;
 
 template <int DT> __device__ __forceinline__ float voxel(const Vol& V, int i, int j, int k) {
   size_t idx = (size_t)i + (size_t)V.nx * ((size_t)j + (size_t)V.ny * (size_t)k);
@@ -246,39 +246,53 @@ __device__ __forceinline__ V3 hg_sample(float g, V3 d, float xi1, float xi2) {
 // Iteration limit of every tracking loop; exceeding it sets PFE_ITER_CAP.
 constexpr int kMaxTrackSteps = 1 << 24;
 
-// Walk over the 8^3 bricks a ray crosses (Amanatides-Woo stepping).  Brick
-// planes lie at min(8i, n)/n; the first brick is taken from the start point.
+// Walk over the bricks a ray crosses (Amanatides-Woo).  Per axis: brick
+// width w = B / n, inverse direction inv = 1/d; the first plane parameter is
+// (plane - o) * inv and each further plane adds w * |inv| (register-only,
+// no division per crossing).  Plane rounding stays far below the half-voxel
+// margin of the brick majorants.
 struct Walk {
-  int c[3], s[3], g[3], n[3];
-  float tn[3], o[3], d[3];
-  __device__ __forceinline__ float plane_t(int a) const {
-    if (s[a] == 0) return __int_as_float(0x7f800000);
-    int vi = s[a] > 0 ? min((c[a] + 1) * kBrick, n[a]) : c[a] * kBrick;
-    float p = (float)vi / (float)n[a];
-    return (p - o[a]) / d[a];
-  }
-  __device__ __forceinline__ void init(const Vol& V, V3 oo, V3 dd, float t) {
-    o[0] = oo.x; o[1] = oo.y; o[2] = oo.z; d[0] = dd.x; d[1] = dd.y; d[2] = dd.z;
-    g[0] = V.gx; g[1] = V.gy; g[2] = V.gz; n[0] = V.nx; n[1] = V.ny; n[2] = V.nz;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      float p = o[a] + t * d[a];
-      int ci = (int)floorf(p * ((float)n[a] * 0.125f));
-      c[a] = min(max(ci, 0), g[a] - 1);
-      s[a] = d[a] > 0.0f ? 1 : (d[a] < 0.0f ? -1 : 0);
-      tn[a] = plane_t(a);
+  int cx, cy, cz, sx, sy, sz;
+  float tx, ty, tz, dtx, dty, dtz;
+  __device__ __forceinline__ static void axis(float o, float d, float t, float w, int g, int& c, int& s, float& tn,
+                                              float& dt) {
+    const float p = o + t * d;
+    const int ci = (int)floorf(p / w);
+    c = min(max(ci, 0), g - 1);
+    if (d > 0.0f) {
+      const float inv = 1.0f / d;
+      s = 1; tn = ((float)(c + 1) * w - o) * inv; dt = w * inv;
+    } else if (d < 0.0f) {
+      const float inv = 1.0f / d;
+      s = -1; tn = ((float)c * w - o) * inv; dt = -(w * inv);
+    } else {
+      s = 0; tn = __int_as_float(0x7f800000); dt = tn;
     }
   }
-  __device__ __forceinline__ float exit_t() const { return mn(tn[0], mn(tn[1], tn[2])); }
+  __device__ __forceinline__ void init(const Vol& V, V3 o, V3 d, float t) {
+    axis(o.x, d.x, t, V.wx, V.gx, cx, sx, tx, dtx);
+    axis(o.y, d.y, t, V.wy, V.gy, cy, sy, ty, dty);
+    axis(o.z, d.z, t, V.wz, V.gz, cz, sz, tz, dtz);
+  }
+  __device__ __forceinline__ float exit_t() const { return mn(tx, mn(ty, tz)); }
   __device__ __forceinline__ float majorant(const Vol& V) const {
-    return __ldg(V.mg + (size_t)c[0] + (size_t)V.gx * ((size_t)c[1] + (size_t)V.gy * (size_t)c[2]));
+    return __ldg(V.mg + (size_t)cx + (size_t)V.gx * ((size_t)cy + (size_t)V.gy * (size_t)cz));
   }
   // step into the next brick; false when the ray leaves the grid
-  __device__ __forceinline__ bool step() {
-    int a = (tn[0] <= tn[1] && tn[0] <= tn[2]) ? 0 : (tn[1] <= tn[2] ? 1 : 2);
-    c[a] += s[a];
-    if (c[a] < 0 || c[a] >= g[a]) return false;
-    tn[a] = plane_t(a);
+  __device__ __forceinline__ bool step(const Vol& V) {
+    if (tx <= ty && tx <= tz) {
+      cx += sx;
+      if (cx < 0 || cx >= V.gx) return false;
+      tx = tx + dtx;
+    } else if (ty <= tz) {
+      cy += sy;
+      if (cy < 0 || cy >= V.gy) return false;
+      ty = ty + dty;
+    } else {
+      cz += sz;
+      if (cz < 0 || cz >= V.gz) return false;
+      tz = tz + dtz;
+    }
     return true;
   }
 };
@@ -311,7 +325,7 @@ __device__ __forceinline__ bool delta_track(const Vol& V, V3 o, V3 d, float t, f
     tau = tau - m * seg;
     t = tc;
     if (t >= t_end) return false;
-    if (!W.step()) return false;
+    if (!W.step(V)) return false;
   }
   atomicOr(err, 1u);
   return false;
@@ -343,7 +357,7 @@ __device__ __forceinline__ float ratio_track(const Vol& V, V3 o, V3 d, float t_e
     tau = tau - m * seg;
     t = tc;
     if (t >= t_end) return T;
-    if (!W.step()) return T;
+    if (!W.step(V)) return T;
   }
   atomicOr(err, 1u);
   return T;
@@ -397,14 +411,19 @@ __device__ __forceinline__ void camera_ray(const CamF& c, int px, int py, float 
 
 // Host-side packing of the public scene structs into the kernels' views.
 inline pfd::Vol pf_make_vol(const pf_volume* v, float majorant, const float* grid = nullptr) {
+  const int B = v->brick > 0 ? v->brick : 8;
   pfd::Vol V;
   V.data = v->data_dev; V.nx = v->nx; V.ny = v->ny; V.nz = v->nz; V.dtype = v->dtype;
   V.sigma_scale = v->sigma_scale; V.albedo = v->albedo; V.majorant = majorant;
   V.tf = (const float4*)v->tf_lut_dev; V.tf_n = v->tf_n;
   V.mg = grid;
-  V.gx = (v->nx + pfd::kBrick - 1) / pfd::kBrick;
-  V.gy = (v->ny + pfd::kBrick - 1) / pfd::kBrick;
-  V.gz = (v->nz + pfd::kBrick - 1) / pfd::kBrick;
+  V.B = B;
+  V.gx = (v->nx + B - 1) / B;
+  V.gy = (v->ny + B - 1) / B;
+  V.gz = (v->nz + B - 1) / B;
+  V.wx = (float)B / (float)v->nx;
+  V.wy = (float)B / (float)v->ny;
+  V.wz = (float)B / (float)v->nz;
   return V;
 }
 inline pfd::DevLights pf_make_lights(const pf_light* lights, int n) {

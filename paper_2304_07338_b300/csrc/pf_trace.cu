@@ -224,9 +224,10 @@ __global__ void k_brick_majorants(Vol V, float* __restrict__ out) {
   if (b >= nb) return;
   const int bx = (int)(b % V.gx), by = (int)((b / V.gx) % V.gy), bz = (int)(b / ((int64_t)V.gx * V.gy));
   float dmin = __int_as_float(0x7f800000), dmax = -dmin;
-  for (int k = max(kBrick * bz - 1, 0); k <= min(kBrick * bz + kBrick, V.nz - 1); ++k)
-    for (int j = max(kBrick * by - 1, 0); j <= min(kBrick * by + kBrick, V.ny - 1); ++j)
-      for (int i = max(kBrick * bx - 1, 0); i <= min(kBrick * bx + kBrick, V.nx - 1); ++i) {
+  const int B = V.B;
+  for (int k = max(B * bz - 1, 0); k <= min(B * bz + B, V.nz - 1); ++k)
+    for (int j = max(B * by - 1, 0); j <= min(B * by + B, V.ny - 1); ++j)
+      for (int i = max(B * bx - 1, 0); i <= min(B * bx + B, V.nx - 1); ++i) {
         const float d = voxel<DT>(V, i, j, k);
         if (d < dmin) dmin = d;
         if (d > dmax) dmax = d;
@@ -251,7 +252,8 @@ pf_status pf_brick_majorants_impl(pf_ctx* ctx, const pf_volume* vol, float* out)
 
 pf_status pf_grid_for(pf_ctx* ctx, const pf_volume* vol, const float** grid) {
   if (vol->brick_majorants_dev) { *grid = vol->brick_majorants_dev; return PF_OK; }
-  const int64_t nb = (int64_t)((vol->nx + 7) / 8) * ((vol->ny + 7) / 8) * ((vol->nz + 7) / 8);
+  const int B = vol->brick > 0 ? vol->brick : 8;
+  const int64_t nb = (int64_t)((vol->nx + B - 1) / B) * ((vol->ny + B - 1) / B) * ((vol->nz + B - 1) / B);
   float* g;
   PF_TRY(pf_scratch(ctx, WS_GRID, (size_t)nb * sizeof(float), (void**)&g));
   PF_TRY(pf_brick_majorants_impl(ctx, vol, g));

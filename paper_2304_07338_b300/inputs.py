@@ -14,6 +14,8 @@ Conventions shared by every consumer:
   * dtype codes: 0 = float32, 1 = float16, 2 = uint8 (density = value/255);
   * a transfer function is an (n, 4) float32 RGBA table over density [0,1],
     interpolated linearly; sigma_t = sigma_scale * alpha, albedo = A * rgb;
+  * `brick` is the edge (voxels) of the bricks whose majorants drive delta
+    and ratio tracking;
   * a light is (kind, v[3], rgb[3]): kind 0 = directional with v pointing
     towards the light and rgb its irradiance, kind 1 = point light at v with
     rgb its intensity;
@@ -43,6 +45,7 @@ class Volume:
     sigma_scale: float
     albedo: float
     tf: np.ndarray              # (n, 4) float32 RGBA
+    brick: int = 8              # edge of the majorant bricks in voxels (power of two)
 
     @property
     def dtype_code(self) -> int:

@@ -96,14 +96,15 @@ def test_full_size_sampled_photons(pf_ctx, orc):
 
 
 def test_brick_majorants_match_oracle(pf_ctx, orc):
-    for n, tf, dt in ((32, I.tf_white_alpha_ramp(), np.float32), (40, I.tf_piecewise_rgba(64), np.float16),
-                      (27, I.tf_piecewise_rgba(256), np.uint8)):
+    for n, tf, dt, B in ((32, I.tf_white_alpha_ramp(), np.float32, 8), (40, I.tf_piecewise_rgba(64), np.float16, 8),
+                         (27, I.tf_piecewise_rgba(256), np.uint8, 8), (40, I.tf_piecewise_rgba(64), np.float32, 16),
+                         (37, I.tf_white_alpha_ramp(), np.uint8, 4)):
         data = I.fbm_volume(n, seed=n)
         if dt == np.uint8:
             data = np.round(data * 255).astype(np.uint8)
         else:
             data = data.astype(dt)
-        v = I.Volume(data, 17.0, 0.9, tf)
+        v = I.Volume(data, 17.0, 0.9, tf, brick=B)
         g = api.Volume.from_inputs(v).brick_majorants(pf_ctx).cpu().numpy()
         want = orc.brick_majorants(v, fp32=True).astype(np.float32)
         assert g.shape == want.shape and np.array_equal(g.view(np.uint32), want.view(np.uint32))

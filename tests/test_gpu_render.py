@@ -15,6 +15,8 @@ path-tracing baseline), through the C ABI.
 """
 import math
 
+import dataclasses
+
 import numpy as np
 import pytest
 import torch
@@ -73,12 +75,14 @@ def test_tracking_direct_matches_float_oracle(pf_ctx, orc):
         assert err.max() <= 2e-6, (g, err.max())
 
 
-def test_path_tracer_matches_float_oracle(pf_ctx, orc):
-    sc = I.scene_judge(32, 24, 20, 6)
-    vol = api.Volume.from_inputs(sc.volume)
+@pytest.mark.parametrize("brick", [8, 4, 16])
+def test_path_tracer_matches_float_oracle(pf_ctx, orc, brick):
+    sc = I.scene_judge(40 if brick == 16 else 32, 24, 20, 6)
+    v = dataclasses.replace(sc.volume, brick=brick)
+    vol = api.Volume.from_inputs(v)
     img = api.render_pathtraced(pf_ctx, vol, sc.lights, -0.5, sc.camera, sc.spp, 16, seed=11)
     pf_ctx.sync()
-    ref = orc.path_trace(sc.volume, sc.lights, -0.5, sc.camera, sc.spp, 16, seed=11, fp32=True)
+    ref = orc.path_trace(v, sc.lights, -0.5, sc.camera, sc.spp, 16, seed=11, fp32=True)
     a = img.cpu().numpy()
     assert ref.max() > 0
     # same float operations in the same order: identical bits per pixel

@@ -54,23 +54,27 @@ def _optical_depth(orc, vol, o, d, s_max, n=20001):
     return s, tau
 
 
-def test_brick_majorants_bound_sigma(orc):
-    sc = I.scene_judge(48)
-    vol = sc.volume
+@pytest.mark.parametrize("n,B", [(48, 8), (48, 16), (44, 16), (37, 4)])
+def test_brick_majorants_bound_sigma(orc, n, B):
+    import dataclasses
+    vol = dataclasses.replace(I.scene_judge(n).volume, brick=B)
+    nb = -(-n // B)
     for fp32 in (False, True):
         m = orc.brick_majorants(vol, fp32)
+        assert m.shape == (nb, nb, nb)
         rng = np.random.default_rng(4)
         p = rng.uniform(0, 1, (50000, 3))
         sig = vol.sigma_scale * orc.density(vol, p, fp32)        # alpha = density for this TF
-        b = np.minimum((p * 48 / 8).astype(int), 5)
+        b = np.minimum((p * n / B).astype(int), nb - 1)
         assert np.all(sig <= m[b[:, 2], b[:, 1], b[:, 0]])
-    # tight: the mean brick majorant is well below the global one
-    assert m.mean() < 0.9 * orc.majorant(vol)
+    # tight: the mean brick majorant is below the global one (well below for small bricks)
+    assert m.mean() < (0.9 if B <= 8 else 0.99) * orc.majorant(vol)
 
 
-def test_grid_delta_tracking_in_heterogeneous_volume(orc):
-    sc = I.scene_judge(40)
-    vol = sc.volume
+@pytest.mark.parametrize("B", [8, 16, 4])
+def test_grid_delta_tracking_in_heterogeneous_volume(orc, B):
+    import dataclasses
+    vol = dataclasses.replace(I.scene_judge(40).volume, brick=B)
     o, d = np.array([0.3, 0.62, -0.5]), np.array([0.15, -0.05, 1.0])
     d = d / np.linalg.norm(d)
     t0 = (0.0 - o[2]) / d[2]
