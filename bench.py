@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "1080p frames/sec and field queries/sec vs plain GPU path tracer at equal RMSE"
 W_, H_, SPP, N_VOX, N_LIGHTS = 1920, 1080, 16, 1024, 8
-BRICK = 16                      # majorant brick edge (voxels) for the 1024^3 volume
+BRICK = 64                      # majorant brick edge (voxels) for the 1024^3 volume
 HIDDEN, N_HIDDEN, FREQS = 128, 4, 12
 VOXEL_BYTES = 2                 # float16
 FETCH_BYTES = 8 * VOXEL_BYTES   # one trilinear lookup reads 8 voxels
@@ -216,6 +216,7 @@ def main():
     ctx.set_counters(None)
     fetches_per_frame = int(counters[0].item())
     qpf = int(counters[1].item())
+    nee_fetches_per_frame = int(counters[2].item())
 
     # timed region
     ctx.stage_times()
@@ -262,16 +263,20 @@ def main():
 
     hbm, bf16, bf16s, src = peaks()
     cam_ms, cam_n = stages["camera"]
+    nee_ms, nee_n = stages["nee"]
     fld_ms, fld_n = stages["field"]
     cmp_ms, cmp_n = stages["compose"]
-    dominant = "camera" if cam_ms >= fld_ms else "field"
-    if dominant == "camera":
-        per_launch_s = cam_ms / max(cam_n, 1) / 1e3
-        alg_bytes = fetches_per_frame * FETCH_BYTES
+    dominant = max((cam_ms, "camera"), (nee_ms, "nee"), (fld_ms, "field"))[1]
+    if dominant in ("camera", "nee"):
+        st_ms, st_n = stages[dominant]
+        lookups = nee_fetches_per_frame if dominant == "nee" else fetches_per_frame - nee_fetches_per_frame
+        per_launch_s = st_ms / max(st_n, 1) / 1e3
+        alg_bytes = lookups * FETCH_BYTES
         achieved = alg_bytes / per_launch_s / 1e9
-        roof = {"kernel": "k_camera_samples (delta + ratio tracking)", "bound": "hbm", "achieved": achieved,
+        name = "k_nee (ratio-tracked shadow rays)" if dominant == "nee" else "k_camera_samples (delta tracking)"
+        roof = {"kernel": name, "bound": "hbm", "achieved": achieved,
                 "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-                "algorithmic": "%d density lookups/frame x %d B" % (fetches_per_frame, FETCH_BYTES),
+                "algorithmic": "%d density lookups/frame x %d B" % (lookups, FETCH_BYTES),
                 "peak_source": src}
     else:
         per_launch_s = fld_ms / max(fld_n, 1) / 1e3
@@ -291,11 +296,12 @@ def main():
                    "l2": "inputs larger than L2 (2 GiB volume)", "majorant_brick": args.brick},
         "queries_per_s": qpf * fps,
         "queries_per_frame": qpf,
+        "lookups_per_frame": {"camera": fetches_per_frame - nee_fetches_per_frame, "nee": nee_fetches_per_frame},
         "stages_ms_per_frame": {k: v[0] / max(args.steps, 1) for k, v in stages.items() if v[1]},
         "roofline": roof,
         "clocks": clk,
         "e2e": {"value": 1.0 / e2e_s, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": args.steps * (cam_n // max(args.steps, 1) + fld_n // max(args.steps, 1) + cmp_n // max(args.steps, 1)),
+        "gpu_launches": cam_n + nee_n + fld_n + cmp_n,
     }
     line["setup"] = setup
     if not args.no_equal_rmse:

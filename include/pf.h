@@ -131,16 +131,17 @@ pf_status pf_set_stream(pf_ctx* ctx, void* cuda_stream);
 const char* pf_last_error(const pf_ctx* ctx);
 /* Work counters for measurement (not part of the method): while set, the
  * renderers add the number of density lookups they perform to
- * counters_dev[0] and the neural renderer adds its valid samples (= field
- * queries) to counters_dev[1] (u64[2], caller-owned, device memory).  NULL
- * switches them off. */
+ * counters_dev[0], the neural renderer adds its valid samples (= field
+ * queries) to counters_dev[1] and the lookups of its next-event pass (the
+ * shadow rays, tracking mode) to counters_dev[2] (u64[4], caller-owned,
+ * device memory).  NULL switches them off. */
 pf_status pf_set_counters(pf_ctx* ctx, uint64_t* counters_dev);
 /* Per-stage timing for measurement (not part of the method).  While enabled,
  * each stage's kernels are bracketed by CUDA events on the context's stream.
  * pf_stage_times synchronises, returns the accumulated milliseconds and
  * launch counts of the first n stages since the last call, and resets them. */
 enum { PF_STAGE_CAMERA = 0, PF_STAGE_FIELD = 1, PF_STAGE_COMPOSE = 2, PF_STAGE_PATH = 3, PF_STAGE_TRAIN = 4,
-       PF_STAGE_PHOTONS = 5, PF_NUM_STAGES = 6 };
+       PF_STAGE_PHOTONS = 5, PF_STAGE_NEE = 6, PF_NUM_STAGES = 7 };
 pf_status pf_stage_timing(pf_ctx* ctx, int enable);
 pf_status pf_stage_times(pf_ctx* ctx, double* ms_host, int* launches_host, int n);
 /* Wait for the context's stream; report any device-side error word. */

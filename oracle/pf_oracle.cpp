@@ -401,18 +401,31 @@ template <typename R> struct Walk {
     }
 };
 
+// Uniforms of one tracking call, taken one at a time from the caller's
+// stream, four per Philox block in lane order; the rest of the last block is
+// discarded when the call returns.
+template <typename R> struct Uniforms {
+    Rng& rng;
+    R u[4] = {0, 0, 0, 0};
+    int k = 4;
+    explicit Uniforms(Rng& r) : rng(r) {}
+    R next() {
+        if (k == 4) { rng.uni4<R>(u); k = 0; }
+        return u[k++];
+    }
+};
+
 // Delta (Woodcock) tracking over the brick majorants from o along d inside
-// [t, t_end): one Philox block per tentative collision (u0 -> optical-depth
-// budget tau = -ln(1-u0) spent brick by brick, u1 -> accept with
-// probability sigma_t / majorant).  Returns true and the distance on a real
-// collision.
+// [t, t_end).  Uniforms in order: the optical-depth budget tau = -ln(1-u) of
+// the next tentative collision, spent brick by brick; at a tentative
+// collision one uniform accepts it with probability sigma_t / majorant, then
+// the next budget.  Returns true and the distance on a real collision.
 template <typename R> bool delta_track(const Volume& V, const Grid<R>& G, V3<R> o, V3<R> d, R t, R t_end, Rng& rng,
                                        R* t_hit, long* steps) {
     Walk<R> W; W.init(G, o, d, t);
-    R u[4] = {0, 0, 0, 0}, tau = (R)0;
-    bool need = true;
+    Uniforms<R> U(rng);
+    R tau = -M<R>::ln((R)1 - U.next());
     for (long it = 0; it < (1L << 24); ++it) {
-        if (need) { rng.uni4<R>(u); tau = -M<R>::ln((R)1 - u[0]); need = false; }
         R m = G.at(W.c[0], W.c[1], W.c[2]);
         R tc = std::min(W.exit_t(), t_end);
         R seg = tc - t;
@@ -420,8 +433,9 @@ template <typename R> bool delta_track(const Volume& V, const Grid<R>& G, V3<R> 
         if (m > (R)0 && tau < m * seg) {
             t = t + tau / m;
             if (steps) ++*steps;
-            if (u[1] * m < sigma_at<R>(V, along(o, d, t))) { *t_hit = t; return true; }
-            need = true;
+            R ua = U.next();
+            if (ua * m < sigma_at<R>(V, along(o, d, t))) { *t_hit = t; return true; }
+            tau = -M<R>::ln((R)1 - U.next());
             continue;
         }
         tau = tau - m * seg;
@@ -432,14 +446,15 @@ template <typename R> bool delta_track(const Volume& V, const Grid<R>& G, V3<R> 
     return false;
 }
 
-// Ratio-tracking transmittance over [0, t_end) with the brick majorants.
+// Ratio-tracking transmittance over [0, t_end) with the brick majorants: at
+// each tentative collision T *= max(0, 1 - sigma_t / majorant); one uniform
+// per tentative collision (its budget).
 template <typename R> R ratio_track(const Volume& V, const Grid<R>& G, V3<R> o, V3<R> d, R t_end, Rng& rng) {
     Walk<R> W; W.init(G, o, d, (R)0);
-    R T = (R)1, t = (R)0, tau = (R)0;
-    R u[4] = {0, 0, 0, 0};
-    bool need = true;
+    Uniforms<R> U(rng);
+    R T = (R)1, t = (R)0;
+    R tau = -M<R>::ln((R)1 - U.next());
     for (long it = 0; it < (1L << 24); ++it) {
-        if (need) { rng.uni4<R>(u); tau = -M<R>::ln((R)1 - u[0]); need = false; }
         R m = G.at(W.c[0], W.c[1], W.c[2]);
         R tc = std::min(W.exit_t(), t_end);
         R seg = tc - t;
@@ -448,7 +463,7 @@ template <typename R> R ratio_track(const Volume& V, const Grid<R>& G, V3<R> o, 
             t = t + tau / m;
             R f = (R)1 - sigma_at<R>(V, along(o, d, t)) / m;
             T = T * std::max((R)0, f);
-            need = true;
+            tau = -M<R>::ln((R)1 - U.next());
             continue;
         }
         tau = tau - m * seg;
@@ -600,8 +615,16 @@ void trace_photon(const Volume& V, const Grid<R>& G, const Light* lights, int n_
 // seg_start + u*len.  Interaction where the accumulated optical depth reaches
 // tau* = -ln(1-u3).  Philox block 0: (j1, j2, u_march, u_tau); blocks 1..:
 // one jitter per light (light l uses lane l%4 of block 1 + l/4).
-// Delta mode (step == 0): block 0 (j1, j2, -, -); delta tracking for the free
-// flight, ratio tracking towards each light, in light order.
+// Delta mode (step == 0): block 0 (j1, j2, -, -), then delta tracking for the
+// free flight on the same stream; the shadow ray towards light l is ratio
+// tracked on a stream of its own (shadow_item, bounce 1), summed in light
+// order.
+// Stream of the shadow ray towards light l at interaction j of a camera
+// sample: tag 5, sub = sample index, item = pixel + (16 (j-1) + l) 2^32.
+inline uint64_t shadow_item(uint64_t pixel, int j, int l) {
+    return pixel + ((uint64_t)(16 * (j - 1) + l) << 32);
+}
+
 template <typename R>
 R march_tau(const Volume& V, V3<R> o, V3<R> d, R t0, R t1, R h, R jit) {
     R tau = (R)0;
@@ -669,7 +692,8 @@ void camera_sample(const Volume& V, const Grid<R>& G, const Light* lights, int n
             R h = step_vox / (R)nmax;
             T = std::exp(-march_tau<R>(V, x, wl, (R)0, tend, h, jl[l]));
         } else {
-            T = ratio_track<R>(V, G, x, wl, tend, rng);
+            Rng rs(seed, 5, shadow_item((uint64_t)py * (uint64_t)cf.W + (uint64_t)px, 1, l), (uint32_t)k);
+            T = ratio_track<R>(V, G, x, wl, tend, rs);
         }
         R ph = hg_eval<R>(g, dot(d, wl));
         L = v3(L.x + ph * T * E.x, L.y + ph * T * E.y, L.z + ph * T * E.z);
@@ -679,7 +703,8 @@ void camera_sample(const Volume& V, const Grid<R>& G, const Light* lights, int n
 
 // ------------------------------------------------------------------ path tracer
 // Delta tracking; at every real collision j: next-event estimation towards
-// every light with ratio-tracking transmittance, weighted by throughput and
+// every light with ratio-tracking transmittance (each shadow ray on its own
+// stream, shadow_item(pixel, j, l)), weighted by throughput and
 // albedo; then throughput *= albedo; stop at j == max_bounces; HG continuation
 // and Russian roulette (j >= 3, q = min(1, max_c beta_c)) from one block.
 template <typename R>
@@ -705,7 +730,8 @@ V3<R> path_sample(const Volume& V, const Grid<R>& G, const Light* lights, int n_
             light_geom<R>(lights[l], x, &wl, &dist, &E);
             R a0, a1, tend = (R)0;
             if (box_hit(x, wl, &a0, &a1)) tend = std::min(a1, dist);
-            R T = ratio_track<R>(V, G, x, wl, tend, rng);
+            Rng rs(seed, 5, shadow_item((uint64_t)py * (uint64_t)cf.W + (uint64_t)px, j, l), (uint32_t)k);
+            R T = ratio_track<R>(V, G, x, wl, tend, rs);
             R ph = hg_eval<R>(g, dot(d, wl));
             L = v3(L.x + ph * T * E.x, L.y + ph * T * E.y, L.z + ph * T * E.z);
         }

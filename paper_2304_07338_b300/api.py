@@ -54,7 +54,7 @@ class Context:
         """Count density lookups into counters[0] (int64 CUDA tensor) or stop (None)."""
         self.check(self.lib.pf_set_counters(self.h, _ptr(counters)))
 
-    STAGES = ("camera", "field", "compose", "path", "train", "photons")
+    STAGES = ("camera", "field", "compose", "path", "train", "photons", "nee")
 
     def stage_timing(self, enable: bool):
         self.check(self.lib.pf_stage_timing(self.h, int(enable)))

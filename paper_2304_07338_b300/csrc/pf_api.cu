@@ -166,6 +166,11 @@ pf_status pf_check_volume(pf_ctx* ctx, const pf_volume* v) {
   if (!(v->majorant >= 0.f) || !std::isfinite(v->majorant)) return pf_fail(ctx, PF_ERR_INVALID_ARG, "majorant must be >= 0");
   if (v->brick != 0 && (v->brick < 2 || v->brick > 256 || (v->brick & (v->brick - 1))))
     return pf_fail(ctx, PF_ERR_INVALID_ARG, "brick must be 0 (= 8) or a power of two in [2, 256]");
+  {
+    const int64_t B = v->brick ? v->brick : 8;
+    if (((v->nx + B - 1) / B) * ((v->ny + B - 1) / B) * ((v->nz + B - 1) / B) >= ((int64_t)1 << 31))
+      return pf_fail(ctx, PF_ERR_INVALID_ARG, "too many majorant bricks (>= 2^31): use a larger brick");
+  }
   return PF_OK;
 }
 

@@ -48,7 +48,13 @@ struct Rng {
     for (int i = 0; i < 4; ++i) u[i] = (float)(o[i] >> 8) * 5.9604644775390625e-08f;
   }
 };
-enum { TAG_CAMERA = 1, TAG_PHOTON = 2, TAG_QUERY = 3, TAG_INIT = 4 };
+enum { TAG_CAMERA = 1, TAG_PHOTON = 2, TAG_QUERY = 3, TAG_INIT = 4, TAG_SHADOW = 5 };
+// Stream item of the shadow ray towards light l at interaction j of a camera
+// sample (tag TAG_SHADOW, sub = sample index): every shadow ray draws from
+// its own stream, so it can be traced apart from the sample's walk.
+__device__ __forceinline__ uint64_t shadow_item(uint64_t pixel, int j, int l) {
+  return pixel + ((uint64_t)(16 * (j - 1) + l) << 32);
+}
 
 // ------------------------------------------------------------------ own float math
 // ln x: x = 2^e m, m folded into [sqrt(1/2), sqrt(2)); ln m = 2 atanh(s) with
@@ -250,117 +256,160 @@ constexpr int kMaxTrackSteps = 1 << 24;
 // width w = B / n, inverse direction inv = 1/d; the first plane parameter is
 // (plane - o) * inv and each further plane adds w * |inv| (register-only,
 // no division per crossing).  Plane rounding stays far below the half-voxel
-// margin of the brick majorants.
+// margin of the brick majorants.  The walk keeps the linear brick index and
+// the number of crossings left per axis, and loads the majorant of the next
+// brick one crossing ahead so that the load's latency overlaps the work in
+// the current brick.
 struct Walk {
-  int cx, cy, cz, sx, sy, sz;
   float tx, ty, tz, dtx, dty, dtz;
-  __device__ __forceinline__ static void axis(float o, float d, float t, float w, int g, int& c, int& s, float& tn,
-                                              float& dt) {
+  int lx, ly, lz;  // crossings left along each axis before the ray leaves the grid
+  int ox, oy, oz;  // linear-index offset of a crossing along each axis
+  int idx, na;     // current brick, axis of the next crossing
+  float m, m_next; // majorants of the current and the next brick
+  __device__ __forceinline__ static void axis(float o, float d, float t, float w, int g, int stride, int& c, int& l,
+                                              int& off, float& tn, float& dt) {
     const float p = o + t * d;
     const int ci = (int)floorf(p / w);
     c = min(max(ci, 0), g - 1);
     if (d > 0.0f) {
       const float inv = 1.0f / d;
-      s = 1; tn = ((float)(c + 1) * w - o) * inv; dt = w * inv;
+      l = g - 1 - c; off = stride; tn = ((float)(c + 1) * w - o) * inv; dt = w * inv;
     } else if (d < 0.0f) {
       const float inv = 1.0f / d;
-      s = -1; tn = ((float)c * w - o) * inv; dt = -(w * inv);
+      l = c; off = -stride; tn = ((float)c * w - o) * inv; dt = -(w * inv);
     } else {
-      s = 0; tn = __int_as_float(0x7f800000); dt = tn;
+      l = 0; off = 0; tn = __int_as_float(0x7f800000); dt = tn;
     }
+  }
+  __device__ __forceinline__ void plan(const Vol& V) {
+    na = (tx <= ty && tx <= tz) ? 0 : (ty <= tz ? 1 : 2);
+    const int left = na == 0 ? lx : (na == 1 ? ly : lz);
+    const int off = na == 0 ? ox : (na == 1 ? oy : oz);
+    m_next = left > 0 ? __ldg(V.mg + (idx + off)) : 0.0f;
   }
   __device__ __forceinline__ void init(const Vol& V, V3 o, V3 d, float t) {
-    axis(o.x, d.x, t, V.wx, V.gx, cx, sx, tx, dtx);
-    axis(o.y, d.y, t, V.wy, V.gy, cy, sy, ty, dty);
-    axis(o.z, d.z, t, V.wz, V.gz, cz, sz, tz, dtz);
+    int cx, cy, cz;
+    axis(o.x, d.x, t, V.wx, V.gx, 1, cx, lx, ox, tx, dtx);
+    axis(o.y, d.y, t, V.wy, V.gy, V.gx, cy, ly, oy, ty, dty);
+    axis(o.z, d.z, t, V.wz, V.gz, V.gx * V.gy, cz, lz, oz, tz, dtz);
+    idx = cx + V.gx * (cy + V.gy * cz);
+    m = __ldg(V.mg + idx);
+    plan(V);
   }
-  __device__ __forceinline__ float exit_t() const { return mn(tx, mn(ty, tz)); }
-  __device__ __forceinline__ float majorant(const Vol& V) const {
-    return __ldg(V.mg + (size_t)cx + (size_t)V.gx * ((size_t)cy + (size_t)V.gy * (size_t)cz));
-  }
+  __device__ __forceinline__ float exit_t() const { return na == 0 ? tx : (na == 1 ? ty : tz); }
   // step into the next brick; false when the ray leaves the grid
   __device__ __forceinline__ bool step(const Vol& V) {
-    if (tx <= ty && tx <= tz) {
-      cx += sx;
-      if (cx < 0 || cx >= V.gx) return false;
-      tx = tx + dtx;
-    } else if (ty <= tz) {
-      cy += sy;
-      if (cy < 0 || cy >= V.gy) return false;
-      ty = ty + dty;
+    if (na == 0) {
+      if (lx == 0) return false;
+      --lx; idx += ox; tx = tx + dtx;
+    } else if (na == 1) {
+      if (ly == 0) return false;
+      --ly; idx += oy; ty = ty + dty;
     } else {
-      cz += sz;
-      if (cz < 0 || cz >= V.gz) return false;
-      tz = tz + dtz;
+      if (lz == 0) return false;
+      --lz; idx += oz; tz = tz + dtz;
     }
+    m = m_next;
+    plan(V);
     return true;
   }
 };
 
-// Delta (Woodcock) tracking in [t, t_end) over the brick majorants: one
-// Philox block per tentative collision (u0 -> optical-depth budget
-// tau = -ln(1-u0), spent brick by brick; u1 -> accept with probability
-// sigma_t / majorant).  Returns true on a real collision.  `fetches` counts
-// density lookups (the tracers' unit of memory work).
+// Uniforms of one tracking call, taken one at a time from the caller's
+// stream, four per Philox block in lane order; the rest of the last block is
+// discarded when the call returns.
+struct Uniforms {
+  float q0, q1, q2, q3;
+  int n = 0;
+  __device__ __forceinline__ float next(Rng& rng) {
+    if (n == 0) {
+      float u[4]; rng.uni4(u);
+      q0 = u[0]; q1 = u[1]; q2 = u[2]; q3 = u[3]; n = 4;
+    }
+    const float v = q0;
+    q0 = q1; q1 = q2; q2 = q3; --n;
+    return v;
+  }
+};
+
+// Delta (Woodcock) tracking in [t, t_end) over the brick majorants.
+// Uniforms in order: the optical-depth budget tau = -ln(1-u) of the next
+// tentative collision, spent brick by brick; at a tentative collision one
+// uniform accepts it with probability sigma_t / majorant, then the next
+// budget.  Returns true on a real collision.  `fetches` counts density
+// lookups (the tracers' unit of memory work).
+//
+// The loop is nested: the inner loop crosses bricks until the budget runs
+// out inside one, then the lookup follows.  Lanes of a warp thus reach their
+// (expensive) lookups together instead of alternating lookups and
+// (cheap) brick crossings.  Every lane performs the same float operations
+// in the same order as a flat event loop would.
 template <int DT>
 __device__ __forceinline__ bool delta_track(const Vol& V, V3 o, V3 d, float t, float t_end, Rng& rng, float* t_hit,
                                             uint32_t* err, uint32_t& fetches) {
   Walk W;
   W.init(V, o, d, t);
-  float u[4] = {0.f, 0.f, 0.f, 0.f}, tau = 0.f;
-  bool need = true;
-  for (int it = 0; it < kMaxTrackSteps; ++it) {
-    if (need) { rng.uni4(u); tau = -own_lnf(1.0f - u[0]); need = false; }
-    const float m = W.majorant(V);
-    const float tc = mn(W.exit_t(), t_end);
+  Uniforms U;
+  float tau = -own_lnf(1.0f - U.next(rng));
+  float tc = mn(W.exit_t(), t_end);
+  int it = 0;
+  for (;;) {
     float seg = tc - t;
     if (seg < 0.0f) seg = 0.0f;
-    if (m > 0.0f && tau < m * seg) {
-      t = t + tau / m;
-      ++fetches;
-      if (u[1] * m < sigma_at<DT>(V, along(o, d, t))) { *t_hit = t; return true; }
-      need = true;
-      continue;
+    while (!(W.m > 0.0f && tau < W.m * seg)) {
+      tau = tau - W.m * seg;
+      t = tc;
+      if (t >= t_end) return false;
+      if (!W.step(V)) return false;
+      tc = mn(W.exit_t(), t_end);
+      seg = tc - t;
+      if (seg < 0.0f) seg = 0.0f;
+      if (++it >= kMaxTrackSteps) { atomicOr(err, 1u); return false; }
     }
-    tau = tau - m * seg;
-    t = tc;
-    if (t >= t_end) return false;
-    if (!W.step(V)) return false;
+    const float m = W.m;
+    t = t + tau / m;
+    ++fetches;
+    const float ua = U.next(rng);
+    if (ua * m < sigma_at<DT>(V, along(o, d, t))) { *t_hit = t; return true; }
+    tau = -own_lnf(1.0f - U.next(rng));
+    if (++it >= kMaxTrackSteps) { atomicOr(err, 1u); return false; }
   }
-  atomicOr(err, 1u);
-  return false;
 }
 
-// Ratio-tracking transmittance over [0, t_end) with the brick majorants.
+// Ratio-tracking transmittance over [0, t_end) with the brick majorants: at
+// each tentative collision T *= max(0, 1 - sigma_t / majorant); one uniform
+// per tentative collision (its budget).  Same nested loop as delta_track.
 template <int DT>
 __device__ __forceinline__ float ratio_track(const Vol& V, V3 o, V3 d, float t_end, Rng& rng, uint32_t* err,
                                              uint32_t& fetches) {
   Walk W;
   W.init(V, o, d, 0.0f);
-  float T = 1.0f, t = 0.0f, tau = 0.f;
-  float u[4] = {0.f, 0.f, 0.f, 0.f};
-  bool need = true;
-  for (int it = 0; it < kMaxTrackSteps; ++it) {
-    if (need) { rng.uni4(u); tau = -own_lnf(1.0f - u[0]); need = false; }
-    const float m = W.majorant(V);
-    const float tc = mn(W.exit_t(), t_end);
+  Uniforms U;
+  float T = 1.0f, t = 0.0f;
+  float tau = -own_lnf(1.0f - U.next(rng));
+  float tc = mn(W.exit_t(), t_end);
+  int it = 0;
+  for (;;) {
     float seg = tc - t;
     if (seg < 0.0f) seg = 0.0f;
-    if (m > 0.0f && tau < m * seg) {
-      t = t + tau / m;
-      ++fetches;
-      const float f = 1.0f - sigma_at<DT>(V, along(o, d, t)) / m;
-      T = T * mx(0.0f, f);
-      need = true;
-      continue;
+    while (!(W.m > 0.0f && tau < W.m * seg)) {
+      tau = tau - W.m * seg;
+      t = tc;
+      if (t >= t_end) return T;
+      if (!W.step(V)) return T;
+      tc = mn(W.exit_t(), t_end);
+      seg = tc - t;
+      if (seg < 0.0f) seg = 0.0f;
+      if (++it >= kMaxTrackSteps) { atomicOr(err, 1u); return T; }
     }
-    tau = tau - m * seg;
-    t = tc;
-    if (t >= t_end) return T;
-    if (!W.step(V)) return T;
+    const float m = W.m;
+    t = t + tau / m;
+    ++fetches;
+    const float f = 1.0f - sigma_at<DT>(V, along(o, d, t)) / m;
+    T = T * mx(0.0f, f);
+    tau = -own_lnf(1.0f - U.next(rng));
+    if (++it >= kMaxTrackSteps) { atomicOr(err, 1u); return T; }
   }
-  atomicOr(err, 1u);
-  return T;
 }
 
 // Largest TF alpha over densities [dmin, dmax] (piecewise-linear table).

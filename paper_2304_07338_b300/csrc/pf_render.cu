@@ -1,14 +1,24 @@
 // Neural volumetric path tracing (Algorithm 2) and the plain path tracer.
 //
 // Wavefront organisation on B300:
-//   k_camera_samples  one thread per (pixel, sample): RayGeneration, free
-//                     flight (VolumeSampling), next-event estimation
-//                     (DirectIllumination); writes albedo*L_d per sample slot
-//                     and appends the valid samples' field queries to a
-//                     compacted list (one atomic per warp);
-//   field forward     over the compacted list only (the paper's "compact the
-//                     samples buffer, discarding ... holes"), decode, times
-//                     albedo, written back to the sample's slot;
+//   k_camera_samples  one thread per (pixel, sample): RayGeneration and free
+//                     flight (VolumeSampling); appends the samples that
+//                     scatter to a compacted list (one atomic per warp) with
+//                     their field query, direction and albedo.  In marching
+//                     mode it also does the next-event estimation itself;
+//   k_place           (tracking mode) orders the compacted list by a 32^3
+//                     Morton cell of the scattering position (counting sort:
+//                     histogram in k_camera_samples, scan, placement);
+//   k_nee             (tracking mode) DirectIllumination over the ordered
+//                     list: one thread per scattering sample traces its
+//                     ratio-tracked shadow rays, so the ~90% of samples that
+//                     leave the volume do not hold idle lanes while the
+//                     others trace eight shadow rays each, and the lanes of
+//                     a warp start from nearby points: towards one light
+//                     their rays cross the same bricks in step;
+//   field forward     over the compacted list only (the paper's compaction
+//                     of the sample buffer), decode, times albedo, written
+//                     back to the sample's slot;
 //   k_compose         one thread per pixel, sums its samples in order.
 // The path tracer uses the same slot layout and an in-order per-pixel sum,
 // processed in chunks of samples so that any spp fits in bounded scratch.
@@ -27,16 +37,45 @@ using namespace pfd;
 
 namespace {
 
+// Morton index of the 32^3 cell holding x (positions in [0,1]^3).
+constexpr int kCellBits = 5;
+constexpr uint32_t kCells = 1u << (3 * kCellBits);
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+__device__ __forceinline__ uint32_t morton_cell(V3 x) {
+  const float s = (float)(1 << kCellBits);
+  const uint32_t cx = (uint32_t)min(max((int)(x.x * s), 0), (1 << kCellBits) - 1);
+  const uint32_t cy = (uint32_t)min(max((int)(x.y * s), 0), (1 << kCellBits) - 1);
+  const uint32_t cz = (uint32_t)min(max((int)(x.z * s), 0), (1 << kCellBits) - 1);
+  return spread3(cx) | (spread3(cy) << 1) | (spread3(cz) << 2);
+}
+
+// Counting-sort placement: entry i goes to off[key] + (its rank among the
+// entries of that key, in atomic order).
+__global__ void k_place(const uint32_t* __restrict__ ckey, const uint32_t* __restrict__ ccount,
+                        const uint64_t* __restrict__ off, uint32_t* __restrict__ fill, uint32_t* __restrict__ perm) {
+  const uint32_t n = *ccount;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t k = ckey[i];
+    perm[off[k] + atomicAdd(fill + k, 1u)] = i;
+  }
+}
+
 // -------------------------------------------------------------- camera samples
 // stats (nullable): stats[0] += density lookups, stats[1] += valid samples
 // (= field queries) of the launch.
 template <int DT, bool MARCH>
-__global__ void __launch_bounds__(128) k_camera_samples(Vol V, DevLights L, CamF cam, float g, int spp, float h,
+__global__ void __launch_bounds__(128, 5) k_camera_samples(Vol V, DevLights L, CamF cam, float g, int spp, float h,
                                                         uint64_t seed, int64_t n_slots, float* __restrict__ slot_ld,
                                                         float* __restrict__ slot_li, float* __restrict__ cq,
-                                                        float* __restrict__ calb, uint32_t* __restrict__ cidx,
-                                                        uint32_t* __restrict__ ccount, uint32_t* err,
-                                                        unsigned long long* stats) {
+                                                        float* __restrict__ calb, float* __restrict__ cdir,
+                                                        uint32_t* __restrict__ cidx, uint32_t* __restrict__ ccount,
+                                                        uint32_t* __restrict__ ckey, uint32_t* __restrict__ chist,
+                                                        uint32_t* err, unsigned long long* stats) {
   int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool active = slot < n_slots;
   uint32_t nfetch = 0;
@@ -99,13 +138,13 @@ __global__ void __launch_bounds__(128) k_camera_samples(Vol V, DevLights L, CamF
         float sig;
         medium_at<DT>(V, x, &sig, &alb);
         ++nfetch;
-        for (int l = 0; l < L.n; ++l) {
+        for (int l = 0; MARCH && l < L.n; ++l) {
           V3 wl, E; float dist;
           light_geom(L.l[l], x, &wl, &dist, &E);
           float a0, a1, tend = 0.f;
           if (box_hit(x, wl, &a0, &a1)) tend = mn(a1, dist);
           float T;
-          if (MARCH) {
+          {
             float tau = 0.f, comp = 0.f;
             if (tend > 0.f) {
               int nseg = (int)ceilf(tend / h);
@@ -122,8 +161,6 @@ __global__ void __launch_bounds__(128) k_camera_samples(Vol V, DevLights L, CamF
               }
             }
             T = expf(-(tau - comp));
-          } else {
-            T = ratio_track<DT>(V, x, wl, tend, rng, err, nfetch);
           }
           float ph = hg_eval(g, dot(d, wl));
           Ld = v3(Ld.x + ph * T * E.x, Ld.y + ph * T * E.y, Ld.z + ph * T * E.z);
@@ -163,7 +200,58 @@ __global__ void __launch_bounds__(128) k_camera_samples(Vol V, DevLights L, CamF
     cq[6 * (size_t)i + 0] = x.x; cq[6 * (size_t)i + 1] = x.y; cq[6 * (size_t)i + 2] = x.z;
     cq[6 * (size_t)i + 3] = th;  cq[6 * (size_t)i + 4] = ph;  cq[6 * (size_t)i + 5] = g;
     calb[3 * (size_t)i + 0] = alb.x; calb[3 * (size_t)i + 1] = alb.y; calb[3 * (size_t)i + 2] = alb.z;
+    if (!MARCH) {
+      cdir[3 * (size_t)i + 0] = -wo.x; cdir[3 * (size_t)i + 1] = -wo.y; cdir[3 * (size_t)i + 2] = -wo.z;
+      const uint32_t key = morton_cell(x);
+      ckey[i] = key;
+      atomicAdd(chist + key, 1u);
+    }
     cidx[i] = (uint32_t)slot;
+  }
+}
+
+// Next-event estimation of the scattering samples (tracking mode), grid-stride
+// over the compacted list: L_d = sum over lights, in order, of
+// p(d . w_l) T_l E_l with T_l ratio tracked on the shadow ray's own stream;
+// slot_ld[slot] = albedo * L_d.  stats[0] and stats[2] += its lookups.
+template <int DT>
+__global__ void __launch_bounds__(128, 6) k_nee(Vol V, DevLights L, float g, int spp, uint64_t seed,
+                                             const float* __restrict__ cq, const float* __restrict__ cdir,
+                                             const float* __restrict__ calb, const uint32_t* __restrict__ cidx,
+                                             const uint32_t* __restrict__ ccount, const uint32_t* __restrict__ perm,
+                                             float* __restrict__ slot_ld, uint32_t* err, unsigned long long* stats) {
+  const uint32_t n = *ccount;
+  uint32_t nfetch = 0;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+    const uint32_t i = perm[j];
+    const V3 x = v3(cq[6 * (size_t)i + 0], cq[6 * (size_t)i + 1], cq[6 * (size_t)i + 2]);
+    const V3 d = v3(cdir[3 * (size_t)i + 0], cdir[3 * (size_t)i + 1], cdir[3 * (size_t)i + 2]);
+    const uint32_t slot = cidx[i];
+    const uint64_t pix = slot / (uint32_t)spp;
+    const uint32_t k = slot % (uint32_t)spp;
+    V3 Ld = v3(0.f, 0.f, 0.f);
+    for (int l = 0; l < L.n; ++l) {
+      V3 wl, E; float dist;
+      light_geom(L.l[l], x, &wl, &dist, &E);
+      float a0, a1, tend = 0.f;
+      if (box_hit(x, wl, &a0, &a1)) tend = mn(a1, dist);
+      Rng rs(seed, TAG_SHADOW, shadow_item(pix, 1, l), k);
+      float T = ratio_track<DT>(V, x, wl, tend, rs, err, nfetch);
+      float ph = hg_eval(g, dot(d, wl));
+      Ld = v3(Ld.x + ph * T * E.x, Ld.y + ph * T * E.y, Ld.z + ph * T * E.z);
+    }
+    slot_ld[3 * (size_t)slot + 0] = calb[3 * (size_t)i + 0] * Ld.x;
+    slot_ld[3 * (size_t)slot + 1] = calb[3 * (size_t)i + 1] * Ld.y;
+    slot_ld[3 * (size_t)slot + 2] = calb[3 * (size_t)i + 2] * Ld.z;
+  }
+  if (stats) {
+    unsigned long long v = nfetch;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0 && v) {
+      atomicAdd(stats, v);
+      atomicAdd(stats + 2, v);
+    }
   }
 }
 
@@ -216,7 +304,8 @@ __global__ void __launch_bounds__(128) k_path_samples(Vol V, DevLights L, CamF c
         light_geom(L.l[l], x, &wl, &dist, &E);
         float a0, a1, tend = 0.f;
         if (box_hit(x, wl, &a0, &a1)) tend = mn(a1, dist);
-        float T = ratio_track<DT>(V, x, wl, tend, rng, err, nfetch);
+        Rng rs(seed, TAG_SHADOW, shadow_item((uint64_t)pix, j, l), (uint32_t)k);
+        float T = ratio_track<DT>(V, x, wl, tend, rs, err, nfetch);
         float ph = hg_eval(g, dot(d, wl));
         Lr = v3(Lr.x + ph * T * E.x, Lr.y + ph * T * E.y, Lr.z + ph * T * E.z);
       }
@@ -282,6 +371,19 @@ CamF make_cam(const pf_camera* c) {
   return o;
 }
 
+// Resident 128-thread blocks per SM of k_nee (grid of its grid-stride loop).
+int nee_blocks_per_sm(int dtype) {
+  static int cached[3] = {0, 0, 0};
+  if (!cached[dtype]) {
+    int b = 0;
+    if (dtype == PF_F32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_nee<0>, 128, 0);
+    else if (dtype == PF_F16) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_nee<1>, 128, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_nee<2>, 128, 0);
+    cached[dtype] = std::max(b, 1);
+  }
+  return cached[dtype];
+}
+
 }  // namespace
 
 static pf_status check_cam(pf_ctx* ctx, const pf_camera* cam, int spp) {
@@ -309,16 +411,28 @@ extern "C" pf_status pf_render_neural(pf_ctx* ctx, const pf_volume* vol, const p
   int64_t n_pix = (int64_t)cam->width * cam->height;
   int64_t n_slots = n_pix * spp;
   if (n_slots > (int64_t)0xFFFFFFFFll) return pf_fail(ctx, PF_ERR_INVALID_ARG, "width*height*spp must be < 2^32");
-  float *ld, *li, *cq = nullptr, *calb = nullptr;
+  bool march = step_vox > 0.f;
+  float *ld, *li, *cq = nullptr, *calb = nullptr, *cdir = nullptr;
   uint32_t *cidx = nullptr, *ccount = nullptr;
   PF_TRY(pf_scratch(ctx, WS_SLOT_LD, n_slots * 3 * sizeof(float), (void**)&ld));
   PF_TRY(pf_scratch(ctx, WS_SLOT_LI, n_slots * 3 * sizeof(float), (void**)&li));
-  if (field) {
+  if (field || !march) {
     PF_TRY(pf_scratch(ctx, WS_COMPACT_Q, n_slots * 6 * sizeof(float), (void**)&cq));
     PF_TRY(pf_scratch(ctx, WS_SLOT_ALB, n_slots * 3 * sizeof(float), (void**)&calb));
     PF_TRY(pf_scratch(ctx, WS_COMPACT_IDX, n_slots * sizeof(uint32_t), (void**)&cidx));
     PF_TRY(pf_scratch(ctx, WS_MISC, 256, (void**)&ccount));
     PF_CUDA(ctx, cudaMemsetAsync(ccount, 0, sizeof(uint32_t), ctx->stream));
+  }
+  uint32_t *ckey = nullptr, *chist = nullptr, *cfill = nullptr, *perm = nullptr;
+  uint64_t* coff = nullptr;
+  if (!march) {
+    PF_TRY(pf_scratch(ctx, WS_COMPACT_DIR, n_slots * 3 * sizeof(float), (void**)&cdir));
+    PF_TRY(pf_scratch(ctx, WS_CELL_KEY, n_slots * sizeof(uint32_t), (void**)&ckey));
+    PF_TRY(pf_scratch(ctx, WS_CELL_PERM, n_slots * sizeof(uint32_t), (void**)&perm));
+    PF_TRY(pf_scratch(ctx, WS_CELL_HIST, 2 * kCells * sizeof(uint32_t), (void**)&chist));
+    PF_TRY(pf_scratch(ctx, WS_CELL_OFF, (kCells + 1) * sizeof(uint64_t), (void**)&coff));
+    cfill = chist + kCells;
+    PF_CUDA(ctx, cudaMemsetAsync(chist, 0, 2 * kCells * sizeof(uint32_t), ctx->stream));
   }
   Vol V = pf_make_vol(vol, 0.f, grid);
   DevLights L = pf_make_lights(lights, n_lights);
@@ -326,18 +440,34 @@ extern "C" pf_status pf_render_neural(pf_ctx* ctx, const pf_volume* vol, const p
   int nmax = std::max(vol->nx, std::max(vol->ny, vol->nz));
   float h = step_vox > 0.f ? step_vox / (float)nmax : 0.f;
   dim3 blk(128), grd((unsigned)((n_slots + 127) / 128));
-  bool march = step_vox > 0.f;
   {
   StageTimer tm(ctx, PF_STAGE_CAMERA);
 #define LAUNCH_CS(DT)                                                                                              \
   if (march) k_camera_samples<DT, true><<<grd, blk, 0, ctx->stream>>>(V, L, C, g, spp, h, seed, n_slots, ld, li, cq, \
-                                                                      calb, cidx, ccount, ctx->err_dev, ctx->counters); \
+                                                                      calb, cdir, cidx, ccount, ckey, chist,        \
+                                                                      ctx->err_dev, ctx->counters);                 \
   else k_camera_samples<DT, false><<<grd, blk, 0, ctx->stream>>>(V, L, C, g, spp, h, seed, n_slots, ld, li, cq, calb, \
-                                                                 cidx, ccount, ctx->err_dev, ctx->counters);
+                                                                 cdir, cidx, ccount, ckey, chist, ctx->err_dev,     \
+                                                                 ctx->counters);
   if (vol->dtype == PF_F32) { LAUNCH_CS(0) } else if (vol->dtype == PF_F16) { LAUNCH_CS(1) } else { LAUNCH_CS(2) }
 #undef LAUNCH_CS
   }
   PF_CUDA(ctx, cudaGetLastError());
+  if (!march) {
+    StageTimer tm(ctx, PF_STAGE_NEE);
+    PF_TRY(pf_scan_u32(ctx, chist, coff, kCells));
+    k_place<<<(unsigned)std::min<int64_t>((n_slots + 255) / 256, (int64_t)ctx->num_sms * 8), 256, 0, ctx->stream>>>(
+        ckey, ccount, coff, cfill, perm);
+    PF_CUDA(ctx, cudaGetLastError());
+    unsigned nb = (unsigned)std::min<int64_t>((n_slots + 127) / 128, (int64_t)ctx->num_sms * nee_blocks_per_sm(vol->dtype));
+    if (vol->dtype == PF_F32)
+      k_nee<0><<<nb, 128, 0, ctx->stream>>>(V, L, g, spp, seed, cq, cdir, calb, cidx, ccount, perm, ld, ctx->err_dev, ctx->counters);
+    else if (vol->dtype == PF_F16)
+      k_nee<1><<<nb, 128, 0, ctx->stream>>>(V, L, g, spp, seed, cq, cdir, calb, cidx, ccount, perm, ld, ctx->err_dev, ctx->counters);
+    else
+      k_nee<2><<<nb, 128, 0, ctx->stream>>>(V, L, g, spp, seed, cq, cdir, calb, cidx, ccount, perm, ld, ctx->err_dev, ctx->counters);
+    PF_CUDA(ctx, cudaGetLastError());
+  }
   if (field) {
     StageTimer tm(ctx, PF_STAGE_FIELD);
     // The number of valid samples is only known on the device; the field pass
