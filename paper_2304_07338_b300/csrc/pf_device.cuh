@@ -259,13 +259,22 @@ constexpr int kMaxTrackSteps = 1 << 24;
 // margin of the brick majorants.  The walk keeps the linear brick index and
 // the number of crossings left per axis, and loads the majorant of the next
 // brick one crossing ahead so that the load's latency overlaps the work in
-// the current brick.
+// the current brick.  S: the majorants are read from a copy at the start of
+// the block's dynamic shared memory instead of global memory.
+template <bool S>
 struct Walk {
   float tx, ty, tz, dtx, dty, dtz;
   int lx, ly, lz;  // crossings left along each axis before the ray leaves the grid
   int ox, oy, oz;  // linear-index offset of a crossing along each axis
   int idx, na;     // current brick, axis of the next crossing
   float m, m_next; // majorants of the current and the next brick
+  __device__ __forceinline__ static float load(const Vol& V, int i) {
+    if (S) {
+      extern __shared__ float pf_walk_smem[];
+      return pf_walk_smem[i];
+    }
+    return __ldg(V.mg + i);
+  }
   __device__ __forceinline__ static void axis(float o, float d, float t, float w, int g, int stride, int& c, int& l,
                                               int& off, float& tn, float& dt) {
     const float p = o + t * d;
@@ -285,7 +294,7 @@ struct Walk {
     na = (tx <= ty && tx <= tz) ? 0 : (ty <= tz ? 1 : 2);
     const int left = na == 0 ? lx : (na == 1 ? ly : lz);
     const int off = na == 0 ? ox : (na == 1 ? oy : oz);
-    m_next = left > 0 ? __ldg(V.mg + (idx + off)) : 0.0f;
+    m_next = left > 0 ? load(V, idx + off) : 0.0f;
   }
   __device__ __forceinline__ void init(const Vol& V, V3 o, V3 d, float t) {
     int cx, cy, cz;
@@ -293,22 +302,20 @@ struct Walk {
     axis(o.y, d.y, t, V.wy, V.gy, V.gx, cy, ly, oy, ty, dty);
     axis(o.z, d.z, t, V.wz, V.gz, V.gx * V.gy, cz, lz, oz, tz, dtz);
     idx = cx + V.gx * (cy + V.gy * cz);
-    m = __ldg(V.mg + idx);
+    m = load(V, idx);
     plan(V);
   }
   __device__ __forceinline__ float exit_t() const { return na == 0 ? tx : (na == 1 ? ty : tz); }
-  // step into the next brick; false when the ray leaves the grid
+  // step into the next brick (branch-free selects); false when the ray
+  // leaves the grid
   __device__ __forceinline__ bool step(const Vol& V) {
-    if (na == 0) {
-      if (lx == 0) return false;
-      --lx; idx += ox; tx = tx + dtx;
-    } else if (na == 1) {
-      if (ly == 0) return false;
-      --ly; idx += oy; ty = ty + dty;
-    } else {
-      if (lz == 0) return false;
-      --lz; idx += oz; tz = tz + dtz;
-    }
+    const bool ax = na == 0, ay = na == 1, az = na == 2;
+    const int left = ax ? lx : (ay ? ly : lz);
+    if (left == 0) return false;
+    lx -= (int)ax; ly -= (int)ay; lz -= (int)az;
+    idx += ax ? ox : (ay ? oy : oz);
+    const float sx = tx + dtx, sy = ty + dty, sz = tz + dtz;
+    tx = ax ? sx : tx; ty = ay ? sy : ty; tz = az ? sz : tz;
     m = m_next;
     plan(V);
     return true;
@@ -344,10 +351,10 @@ struct Uniforms {
 // (expensive) lookups together instead of alternating lookups and
 // (cheap) brick crossings.  Every lane performs the same float operations
 // in the same order as a flat event loop would.
-template <int DT>
+template <int DT, bool S = false>
 __device__ __forceinline__ bool delta_track(const Vol& V, V3 o, V3 d, float t, float t_end, Rng& rng, float* t_hit,
                                             uint32_t* err, uint32_t& fetches) {
-  Walk W;
+  Walk<S> W;
   W.init(V, o, d, t);
   Uniforms U;
   float tau = -own_lnf(1.0f - U.next(rng));
@@ -379,10 +386,10 @@ __device__ __forceinline__ bool delta_track(const Vol& V, V3 o, V3 d, float t, f
 // Ratio-tracking transmittance over [0, t_end) with the brick majorants: at
 // each tentative collision T *= max(0, 1 - sigma_t / majorant); one uniform
 // per tentative collision (its budget).  Same nested loop as delta_track.
-template <int DT>
+template <int DT, bool S = false>
 __device__ __forceinline__ float ratio_track(const Vol& V, V3 o, V3 d, float t_end, Rng& rng, uint32_t* err,
                                              uint32_t& fetches) {
-  Walk W;
+  Walk<S> W;
   W.init(V, o, d, 0.0f);
   Uniforms U;
   float T = 1.0f, t = 0.0f;

@@ -214,12 +214,18 @@ __global__ void __launch_bounds__(128, 5) k_camera_samples(Vol V, DevLights L, C
 // over the compacted list: L_d = sum over lights, in order, of
 // p(d . w_l) T_l E_l with T_l ratio tracked on the shadow ray's own stream;
 // slot_ld[slot] = albedo * L_d.  stats[0] and stats[2] += its lookups.
-template <int DT>
+template <int DT, bool S>
 __global__ void __launch_bounds__(128, 6) k_nee(Vol V, DevLights L, float g, int spp, uint64_t seed,
                                              const float* __restrict__ cq, const float* __restrict__ cdir,
                                              const float* __restrict__ calb, const uint32_t* __restrict__ cidx,
                                              const uint32_t* __restrict__ ccount, const uint32_t* __restrict__ perm,
                                              float* __restrict__ slot_ld, uint32_t* err, unsigned long long* stats) {
+  if (S) {  // the brick majorants, staged once per block
+    extern __shared__ float pf_walk_smem[];
+    const int nb = V.gx * V.gy * V.gz;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) pf_walk_smem[b] = __ldg(V.mg + b);
+    __syncthreads();
+  }
   const uint32_t n = *ccount;
   uint32_t nfetch = 0;
   const uint32_t stride = gridDim.x * blockDim.x;
@@ -237,7 +243,7 @@ __global__ void __launch_bounds__(128, 6) k_nee(Vol V, DevLights L, float g, int
       float a0, a1, tend = 0.f;
       if (box_hit(x, wl, &a0, &a1)) tend = mn(a1, dist);
       Rng rs(seed, TAG_SHADOW, shadow_item(pix, 1, l), k);
-      float T = ratio_track<DT>(V, x, wl, tend, rs, err, nfetch);
+      float T = ratio_track<DT, S>(V, x, wl, tend, rs, err, nfetch);
       float ph = hg_eval(g, dot(d, wl));
       Ld = v3(Ld.x + ph * T * E.x, Ld.y + ph * T * E.y, Ld.z + ph * T * E.z);
     }
@@ -371,17 +377,29 @@ CamF make_cam(const pf_camera* c) {
   return o;
 }
 
-// Resident 128-thread blocks per SM of k_nee (grid of its grid-stride loop).
-int nee_blocks_per_sm(int dtype) {
-  static int cached[3] = {0, 0, 0};
-  if (!cached[dtype]) {
-    int b = 0;
-    if (dtype == PF_F32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_nee<0>, 128, 0);
-    else if (dtype == PF_F16) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_nee<1>, 128, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_nee<2>, 128, 0);
-    cached[dtype] = std::max(b, 1);
-  }
-  return cached[dtype];
+// Brick grids up to this size are staged in shared memory by k_nee.
+constexpr size_t kNeeSmemGridBytes = 48 << 10;
+
+// Launches k_nee as a grid-stride loop over the compacted list with as many
+// blocks as fit on the device at once.
+template <int DT>
+pf_status launch_nee(pf_ctx* ctx, const Vol& V, const DevLights& L, float g, int spp, uint64_t seed, int64_t n_max,
+                     const float* cq, const float* cdir, const float* calb, const uint32_t* cidx,
+                     const uint32_t* ccount, const uint32_t* perm, float* ld) {
+  const size_t grid_bytes = (size_t)V.gx * V.gy * V.gz * sizeof(float);
+  const bool smem = grid_bytes <= kNeeSmemGridBytes;
+  int o = 0;  // resident blocks per SM
+  if (smem) PF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_nee<DT, true>, 128, grid_bytes));
+  else PF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_nee<DT, false>, 128, 0));
+  unsigned nb = (unsigned)std::min<int64_t>((n_max + 127) / 128, (int64_t)ctx->num_sms * std::max(o, 1));
+  if (smem)
+    k_nee<DT, true><<<nb, 128, grid_bytes, ctx->stream>>>(V, L, g, spp, seed, cq, cdir, calb, cidx, ccount, perm, ld,
+                                                          ctx->err_dev, ctx->counters);
+  else
+    k_nee<DT, false><<<nb, 128, 0, ctx->stream>>>(V, L, g, spp, seed, cq, cdir, calb, cidx, ccount, perm, ld,
+                                                  ctx->err_dev, ctx->counters);
+  PF_CUDA(ctx, cudaGetLastError());
+  return PF_OK;
 }
 
 }  // namespace
@@ -459,14 +477,12 @@ extern "C" pf_status pf_render_neural(pf_ctx* ctx, const pf_volume* vol, const p
     k_place<<<(unsigned)std::min<int64_t>((n_slots + 255) / 256, (int64_t)ctx->num_sms * 8), 256, 0, ctx->stream>>>(
         ckey, ccount, coff, cfill, perm);
     PF_CUDA(ctx, cudaGetLastError());
-    unsigned nb = (unsigned)std::min<int64_t>((n_slots + 127) / 128, (int64_t)ctx->num_sms * nee_blocks_per_sm(vol->dtype));
     if (vol->dtype == PF_F32)
-      k_nee<0><<<nb, 128, 0, ctx->stream>>>(V, L, g, spp, seed, cq, cdir, calb, cidx, ccount, perm, ld, ctx->err_dev, ctx->counters);
+      PF_TRY(launch_nee<0>(ctx, V, L, g, spp, seed, n_slots, cq, cdir, calb, cidx, ccount, perm, ld));
     else if (vol->dtype == PF_F16)
-      k_nee<1><<<nb, 128, 0, ctx->stream>>>(V, L, g, spp, seed, cq, cdir, calb, cidx, ccount, perm, ld, ctx->err_dev, ctx->counters);
+      PF_TRY(launch_nee<1>(ctx, V, L, g, spp, seed, n_slots, cq, cdir, calb, cidx, ccount, perm, ld));
     else
-      k_nee<2><<<nb, 128, 0, ctx->stream>>>(V, L, g, spp, seed, cq, cdir, calb, cidx, ccount, perm, ld, ctx->err_dev, ctx->counters);
-    PF_CUDA(ctx, cudaGetLastError());
+      PF_TRY(launch_nee<2>(ctx, V, L, g, spp, seed, n_slots, cq, cdir, calb, cidx, ccount, perm, ld));
   }
   if (field) {
     StageTimer tm(ctx, PF_STAGE_FIELD);
