@@ -36,6 +36,11 @@ W_, H_, SPP, N_VOX, N_LIGHTS = 1920, 1080, 16, 1024, 8
 BRICK = 64                      # majorant brick edge (voxels) for the 1024^3 volume
 HIDDEN, N_HIDDEN, FREQS = 128, 4, 12
 VOXEL_BYTES = 2                 # float16
+# DRAM bytes (read + write) per density lookup of k_nee, from one ncu capture
+# of the small case (profiles/k_nee__large_render_512cube_960x540.md:
+# 2.852 GB + 0.054 GB for 43.354 M lookups); a full launch is scaled by its
+# lookups.  Set to None whenever k_nee changes until it is captured again.
+NEE_DRAM_BYTES_PER_LOOKUP = (2.852484e9 + 0.053576e9) / 43354446
 FETCH_BYTES = 8 * VOXEL_BYTES   # one trilinear lookup reads 8 voxels
 
 
@@ -207,16 +212,18 @@ def main():
         cam, g = frame(i)
         api.render_neural(ctx, vol, lights, g, cam, SPP, 0.0, seed + i, field, out)
     ctx.sync()
-    # work counters (density lookups) from one counted frame outside the timed region
+    # work counters (density lookups, queries): the timed frames rendered once
+    # more outside the timed region with counting on, averaged per frame
     counters = torch.zeros(4, dtype=torch.int64, device=dev)
     ctx.set_counters(counters)
-    cam, g = frame(0)
-    api.render_neural(ctx, vol, lights, g, cam, SPP, 0.0, seed, field, out)
+    for i in range(args.steps):
+        cam, g = frame(args.warmup + i)
+        api.render_neural(ctx, vol, lights, g, cam, SPP, 0.0, seed + 100 + i, field, out)
     ctx.sync()
     ctx.set_counters(None)
-    fetches_per_frame = int(counters[0].item())
-    qpf = int(counters[1].item())
-    nee_fetches_per_frame = int(counters[2].item())
+    fetches_per_frame = int(counters[0].item()) // args.steps
+    qpf = int(counters[1].item()) // args.steps
+    nee_fetches_per_frame = int(counters[2].item()) // args.steps
 
     # timed region
     ctx.stage_times()
@@ -274,8 +281,13 @@ def main():
         alg_bytes = lookups * FETCH_BYTES
         achieved = alg_bytes / per_launch_s / 1e9
         name = "k_nee (ratio-tracked shadow rays)" if dominant == "nee" else "k_camera_samples (delta tracking)"
+        traffic = None
+        if dominant == "nee" and NEE_DRAM_BYTES_PER_LOOKUP is not None:
+            traffic = lookups * NEE_DRAM_BYTES_PER_LOOKUP
         roof = {"kernel": name, "bound": "hbm", "achieved": achieved,
-                "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+                "traffic_note": "DRAM bytes per launch, scaled from the small-case ncu capture by lookups"
+                if traffic else None,
                 "algorithmic": "%d density lookups/frame x %d B" % (lookups, FETCH_BYTES),
                 "peak_source": src}
     else:
@@ -301,7 +313,8 @@ def main():
         "roofline": roof,
         "clocks": clk,
         "e2e": {"value": 1.0 / e2e_s, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": cam_n + nee_n + fld_n + cmp_n,
+        # kernels per frame: camera samples; scan (3) + placement + k_nee; field; compose
+        "gpu_launches": cam_n + 5 * nee_n + fld_n + cmp_n,
     }
     line["setup"] = setup
     if not args.no_equal_rmse:

@@ -173,7 +173,8 @@ def test_large_render_sampled_rows(pf_ctx, orc):
     from oracle import field as F
     vol_t, tf, lights, cams = I.large_scene_parts(1024, device="cuda")
     tf_t = torch.from_numpy(tf).cuda()
-    vol = api.Volume(vol_t.contiguous(), 20.0, 0.9, tf_t)
+    vol = api.Volume(vol_t.contiguous(), 20.0, 0.9, tf_t, brick=64)     # the benchmark's brick size
+    vol.attach_brick_majorants(pf_ctx)
     fld = api.Field(pf_ctx, 12, 128, 4, "fp8", 5.0, seed=5)
     desc = F.FieldDesc(12, 128, 4, F.PREC_FP8, 5.0, 5)
     w = F.init_weights(desc).astype(np.float64)
@@ -185,10 +186,43 @@ def test_large_render_sampled_rows(pf_ctx, orc):
     cam, g = cams[7], I.frame_g(11, 7)
     img = api.render_neural(pf_ctx, vol, lights, g, cam, 16, 0.0, seed=99, field=fld)
     pf_ctx.sync()
-    vh = I.Volume(vol_t.cpu().numpy(), 20.0, 0.9, tf)
+    vh = I.Volume(vol_t.cpu().numpy(), 20.0, 0.9, tf, brick=64)
     for y0 in (500, 700):
         ref = orc.render_neural(vh, lights, g, cam, 16, 0.0, 99, weights=w, desc=desc, scales=scales, fp32=True,
                                 rows=(y0, y0 + 1))
+        got = img[y0:y0 + 1].cpu().numpy()
+        assert ref.max() > 0
+        err = _rel_err(got, ref)
+        assert np.median(err) < 5e-3 and err.max() < 0.3, (y0, np.median(err), err.max())
+
+
+@pytest.mark.parametrize("prec", ["f16", "fp8"])
+def test_mid_render_sampled_rows(pf_ctx, orc, prec):
+    """Full-size mid-render workload (512^3 u8 blurred noise, 256-node RGBA
+    table, 4 point lights, 1024^2 x 4 spp, 4x128 field in f16 or fp8,
+    tracking); sampled rows recomputed by the oracle."""
+    from oracle import field as F
+    sc = I.scene_mid(device="cuda")
+    data = np.ascontiguousarray(sc.volume.data)
+    vol = api.Volume(torch.from_numpy(data).cuda(), sc.volume.sigma_scale, sc.volume.albedo,
+                     torch.from_numpy(sc.volume.tf).cuda())
+    pcode = {"f16": F.PREC_F16, "fp8": F.PREC_FP8}[prec]
+    fld = api.Field(pf_ctx, 12, 128, 4, prec, 5.0, seed=8)
+    desc = F.FieldDesc(12, 128, 4, pcode, 5.0, 8)
+    w = F.init_weights(desc).astype(np.float64)
+    w[-3 * 128:] *= 0.05
+    fld.set_weights(torch.from_numpy(w.astype(np.float32)).cuda())
+    scales = None
+    if prec == "fp8":
+        cal = np.random.default_rng(4).uniform(0, 1, (4096, 6)).astype(np.float32)
+        fld.calibrate_fp8(torch.from_numpy(cal).cuda())
+        scales = F.fp8_calibrate(w, cal.astype(np.float64), desc)
+    img = api.render_neural(pf_ctx, vol, sc.lights, sc.g, sc.camera, sc.spp, 0.0, seed=41, field=fld)
+    pf_ctx.sync()
+    vh = I.Volume(data, sc.volume.sigma_scale, sc.volume.albedo, sc.volume.tf)
+    for y0 in (300, 512, 811):
+        ref = orc.render_neural(vh, sc.lights, sc.g, sc.camera, sc.spp, 0.0, 41, weights=w, desc=desc,
+                                scales=scales, fp32=True, rows=(y0, y0 + 1))
         got = img[y0:y0 + 1].cpu().numpy()
         assert ref.max() > 0
         err = _rel_err(got, ref)
