@@ -33,14 +33,14 @@ sys.path.insert(0, ROOT)
 
 METRIC = "1080p frames/sec and field queries/sec vs plain GPU path tracer at equal RMSE"
 W_, H_, SPP, N_VOX, N_LIGHTS = 1920, 1080, 16, 1024, 8
-BRICK = 64                      # majorant brick edge (voxels) for the 1024^3 volume
+BRICK = 32                      # majorant brick edge (voxels) for the 1024^3 volume
 HIDDEN, N_HIDDEN, FREQS = 128, 4, 12
 VOXEL_BYTES = 2                 # float16
 # DRAM bytes (read + write) per density lookup of k_nee, from one ncu capture
-# of the small case (profiles/k_nee__large_render_512cube_960x540.md:
-# 2.852 GB + 0.054 GB for 43.354 M lookups); a full launch is scaled by its
-# lookups.  Set to None whenever k_nee changes until it is captured again.
-NEE_DRAM_BYTES_PER_LOOKUP = (2.852484e9 + 0.053576e9) / 43354446
+# of the small case (profiles/k_nee__large_render_512cube_960x540.md); a full
+# launch is scaled by its lookups.  None whenever k_nee changed since the
+# capture.
+NEE_DRAM_BYTES_PER_LOOKUP = (1.845204e9 + 0.063788e9) / 26857378
 FETCH_BYTES = 8 * VOXEL_BYTES   # one trilinear lookup reads 8 voxels
 
 
@@ -401,6 +401,11 @@ def equal_rmse(ctx, vol, lights, frame, field, seed, args, fps_neural):
     pt_fps = n / (s_ev.elapsed_time(e_ev) / 1e3)
     out["pt_fps_at_equal_rmse"] = pt_fps
     out["speedup"] = fps_neural / pt_fps
+    # the same from the fit's continuous spp (path-tracer time scales with spp)
+    if r_n > b:
+        spp_fit = (a / (r_n - b)) ** 2
+        out["pt_spp_fit"] = float(spp_fit)
+        out["speedup_fit"] = float(fps_neural / (pt_fps * need / spp_fit))
     return out
 
 

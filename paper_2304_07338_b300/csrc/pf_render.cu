@@ -211,29 +211,53 @@ __global__ void __launch_bounds__(128, 5) k_camera_samples(Vol V, DevLights L, C
 }
 
 // Next-event estimation of the scattering samples (tracking mode), grid-stride
-// over the compacted list: L_d = sum over lights, in order, of
+// over the cell-ordered compacted list: L_d = sum over lights, in order, of
 // p(d . w_l) T_l E_l with T_l ratio tracked on the shadow ray's own stream;
 // slot_ld[slot] = albedo * L_d.  stats[0] and stats[2] += its lookups.
-template <int DT, bool S>
+//
+// Ratio tracking's tentative collisions do not depend on the density, only
+// the weights 1 - sigma_t/majorant do.  A warp therefore traces its 32 shadow
+// rays (one light at a time) in passes: each lane walks its ray, recording
+// up to kNeePool collisions (distance, majorant) in the warp's shared-memory
+// pool; then all 32 lanes evaluate the pooled density lookups together,
+// whatever ray they belong to; then each lane multiplies its own factors in
+// collision order.  The floats are those of a walk with the lookups inline
+// (same operations, same order per ray); only the lane doing each lookup
+// changes, so the lanes stay busy while the rays' collision counts differ.
+// The pool lives in shared memory, which the SM carves out of the same
+// storage as the L1 cache that serves the density gathers; it is kept small.
+constexpr int kNeePool = 16;                                               // collisions per lane per pass
+constexpr int kNeeWarpFloats = 32 * kNeePool * 2 + 32 * kNeePool / 2 + 32 * 6;  // t/factor, majorant, u16 map; x, w_l
+constexpr int kNeeWarps = 4;
+
+template <int DT>
 __global__ void __launch_bounds__(128, 6) k_nee(Vol V, DevLights L, float g, int spp, uint64_t seed,
                                              const float* __restrict__ cq, const float* __restrict__ cdir,
                                              const float* __restrict__ calb, const uint32_t* __restrict__ cidx,
                                              const uint32_t* __restrict__ ccount, const uint32_t* __restrict__ perm,
                                              float* __restrict__ slot_ld, uint32_t* err, unsigned long long* stats) {
-  if (S) {  // the brick majorants, staged once per block
-    extern __shared__ float pf_walk_smem[];
-    const int nb = V.gx * V.gy * V.gz;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) pf_walk_smem[b] = __ldg(V.mg + b);
-    __syncthreads();
-  }
+  extern __shared__ float pf_nee_smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* pool = pf_nee_smem + warp * kNeeWarpFloats;
+  float* pt = pool;                                        // collision distance, then its factor
+  float* pm = pool + 32 * kNeePool;                        // majorant at the collision
+  uint16_t* pmap = (uint16_t*)(pool + 64 * kNeePool);      // pooled entry -> lane * kNeePool + index
+  float* pxw = pool + 64 * kNeePool + 16 * kNeePool;       // per lane: origin x (3), direction w_l (3)
   const uint32_t n = *ccount;
   uint32_t nfetch = 0;
   const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
-    const uint32_t i = perm[j];
-    const V3 x = v3(cq[6 * (size_t)i + 0], cq[6 * (size_t)i + 1], cq[6 * (size_t)i + 2]);
-    const V3 d = v3(cdir[3 * (size_t)i + 0], cdir[3 * (size_t)i + 1], cdir[3 * (size_t)i + 2]);
-    const uint32_t slot = cidx[i];
+  // warp-uniform loop: lane j = base + lane, idle when j >= n
+  for (uint32_t base = blockIdx.x * blockDim.x + warp * 32; base < n; base += stride) {
+    const uint32_t j = base + lane;
+    const bool act = j < n;
+    V3 x = v3(0.5f, 0.5f, 0.5f), d = v3(0.f, 0.f, 1.f);
+    uint32_t i = 0, slot = 0;
+    if (act) {
+      i = perm[j];
+      x = v3(cq[6 * (size_t)i + 0], cq[6 * (size_t)i + 1], cq[6 * (size_t)i + 2]);
+      d = v3(cdir[3 * (size_t)i + 0], cdir[3 * (size_t)i + 1], cdir[3 * (size_t)i + 2]);
+      slot = cidx[i];
+    }
     const uint64_t pix = slot / (uint32_t)spp;
     const uint32_t k = slot % (uint32_t)spp;
     V3 Ld = v3(0.f, 0.f, 0.f);
@@ -243,18 +267,73 @@ __global__ void __launch_bounds__(128, 6) k_nee(Vol V, DevLights L, float g, int
       float a0, a1, tend = 0.f;
       if (box_hit(x, wl, &a0, &a1)) tend = mn(a1, dist);
       Rng rs(seed, TAG_SHADOW, shadow_item(pix, 1, l), k);
-      float T = ratio_track<DT, S>(V, x, wl, tend, rs, err, nfetch);
+      Walk<false> W;
+      W.init(V, x, wl, 0.0f);
+      Uniforms U;
+      float T = 1.0f, t = 0.0f;
+      float tau = -own_lnf(1.0f - U.next(rs));
+      float tc = mn(W.exit_t(), tend);
+      bool done = !act;
+      int it = 0;
+      pxw[6 * lane + 0] = x.x; pxw[6 * lane + 1] = x.y; pxw[6 * lane + 2] = x.z;
+      pxw[6 * lane + 3] = wl.x; pxw[6 * lane + 4] = wl.y; pxw[6 * lane + 5] = wl.z;
+      for (;;) {
+        // walk: record up to kNeePool tentative collisions of this lane's ray
+        int cnt = 0;
+        while (!done && cnt < kNeePool) {
+          float seg = tc - t;
+          if (seg < 0.0f) seg = 0.0f;
+          if (W.m > 0.0f && tau < W.m * seg) {
+            const float m = W.m;
+            t = t + tau / m;
+            pt[lane * kNeePool + cnt] = t;
+            pm[lane * kNeePool + cnt] = m;
+            ++cnt;
+            tau = -own_lnf(1.0f - U.next(rs));
+          } else {
+            tau = tau - W.m * seg;
+            t = tc;
+            if (t >= tend || !W.step(V)) done = true;
+            else tc = mn(W.exit_t(), tend);
+          }
+          if (++it >= kMaxTrackSteps) { atomicOr(err, 1u); done = true; }
+        }
+        // pool the warp's collisions
+        int incl = cnt;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, incl, off);
+          if (lane >= off) incl += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        for (int c = 0; c < cnt; ++c) pmap[incl - cnt + c] = (uint16_t)(lane * kNeePool + c);
+        __syncwarp();
+        for (int e = lane; e < total; e += 32) {
+          const int si = pmap[e];
+          const int o = si / kNeePool;
+          const V3 xo = v3(pxw[6 * o + 0], pxw[6 * o + 1], pxw[6 * o + 2]);
+          const V3 wo = v3(pxw[6 * o + 3], pxw[6 * o + 4], pxw[6 * o + 5]);
+          pt[si] = 1.0f - sigma_at<DT>(V, along(xo, wo, pt[si])) / pm[si];
+          ++nfetch;
+        }
+        __syncwarp();
+        for (int c = 0; c < cnt; ++c) T = T * mx(0.0f, pt[lane * kNeePool + c]);
+        __syncwarp();
+        if (__all_sync(0xffffffffu, done)) break;
+      }
       float ph = hg_eval(g, dot(d, wl));
       Ld = v3(Ld.x + ph * T * E.x, Ld.y + ph * T * E.y, Ld.z + ph * T * E.z);
     }
-    slot_ld[3 * (size_t)slot + 0] = calb[3 * (size_t)i + 0] * Ld.x;
-    slot_ld[3 * (size_t)slot + 1] = calb[3 * (size_t)i + 1] * Ld.y;
-    slot_ld[3 * (size_t)slot + 2] = calb[3 * (size_t)i + 2] * Ld.z;
+    if (act) {
+      slot_ld[3 * (size_t)slot + 0] = calb[3 * (size_t)i + 0] * Ld.x;
+      slot_ld[3 * (size_t)slot + 1] = calb[3 * (size_t)i + 1] * Ld.y;
+      slot_ld[3 * (size_t)slot + 2] = calb[3 * (size_t)i + 2] * Ld.z;
+    }
   }
   if (stats) {
     unsigned long long v = nfetch;
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    if ((threadIdx.x & 31) == 0 && v) {
+    if (lane == 0 && v) {
       atomicAdd(stats, v);
       atomicAdd(stats + 2, v);
     }
@@ -377,27 +456,18 @@ CamF make_cam(const pf_camera* c) {
   return o;
 }
 
-// Brick grids up to this size are staged in shared memory by k_nee.
-constexpr size_t kNeeSmemGridBytes = 48 << 10;
-
 // Launches k_nee as a grid-stride loop over the compacted list with as many
 // blocks as fit on the device at once.
 template <int DT>
 pf_status launch_nee(pf_ctx* ctx, const Vol& V, const DevLights& L, float g, int spp, uint64_t seed, int64_t n_max,
                      const float* cq, const float* cdir, const float* calb, const uint32_t* cidx,
                      const uint32_t* ccount, const uint32_t* perm, float* ld) {
-  const size_t grid_bytes = (size_t)V.gx * V.gy * V.gz * sizeof(float);
-  const bool smem = grid_bytes <= kNeeSmemGridBytes;
+  const size_t bytes = (size_t)kNeeWarps * kNeeWarpFloats * sizeof(float);
   int o = 0;  // resident blocks per SM
-  if (smem) PF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_nee<DT, true>, 128, grid_bytes));
-  else PF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_nee<DT, false>, 128, 0));
+  PF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_nee<DT>, 32 * kNeeWarps, bytes));
   unsigned nb = (unsigned)std::min<int64_t>((n_max + 127) / 128, (int64_t)ctx->num_sms * std::max(o, 1));
-  if (smem)
-    k_nee<DT, true><<<nb, 128, grid_bytes, ctx->stream>>>(V, L, g, spp, seed, cq, cdir, calb, cidx, ccount, perm, ld,
-                                                          ctx->err_dev, ctx->counters);
-  else
-    k_nee<DT, false><<<nb, 128, 0, ctx->stream>>>(V, L, g, spp, seed, cq, cdir, calb, cidx, ccount, perm, ld,
-                                                  ctx->err_dev, ctx->counters);
+  k_nee<DT><<<nb, 32 * kNeeWarps, bytes, ctx->stream>>>(V, L, g, spp, seed, cq, cdir, calb, cidx, ccount, perm, ld,
+                                                        ctx->err_dev, ctx->counters);
   PF_CUDA(ctx, cudaGetLastError());
   return PF_OK;
 }

@@ -173,7 +173,7 @@ def test_large_render_sampled_rows(pf_ctx, orc):
     from oracle import field as F
     vol_t, tf, lights, cams = I.large_scene_parts(1024, device="cuda")
     tf_t = torch.from_numpy(tf).cuda()
-    vol = api.Volume(vol_t.contiguous(), 20.0, 0.9, tf_t, brick=64)     # the benchmark's brick size
+    vol = api.Volume(vol_t.contiguous(), 20.0, 0.9, tf_t, brick=32)     # the benchmark's brick size
     vol.attach_brick_majorants(pf_ctx)
     fld = api.Field(pf_ctx, 12, 128, 4, "fp8", 5.0, seed=5)
     desc = F.FieldDesc(12, 128, 4, F.PREC_FP8, 5.0, 5)
@@ -186,7 +186,7 @@ def test_large_render_sampled_rows(pf_ctx, orc):
     cam, g = cams[7], I.frame_g(11, 7)
     img = api.render_neural(pf_ctx, vol, lights, g, cam, 16, 0.0, seed=99, field=fld)
     pf_ctx.sync()
-    vh = I.Volume(vol_t.cpu().numpy(), 20.0, 0.9, tf, brick=64)
+    vh = I.Volume(vol_t.cpu().numpy(), 20.0, 0.9, tf, brick=32)
     for y0 in (500, 700):
         ref = orc.render_neural(vh, lights, g, cam, 16, 0.0, 99, weights=w, desc=desc, scales=scales, fp32=True,
                                 rows=(y0, y0 + 1))
