@@ -257,11 +257,14 @@ struct TrArgs {
   uint32_t a_off[kMaxLayers];   // shared-memory byte offset of A_l
   uint32_t d_off;           // dZ tile (128 x 128 neurons, padded)
   uint32_t dwo_off;         // dW_out accumulator (3 x H float32)
+  uint32_t hs_off;          // last hidden activations of the tile (128 x H float32, rows rotated)
+  uint32_t dys_off;         // output-layer gradients of the tile (128 x 4 float32)
   uint32_t dw_col[kMaxLayers];  // TMEM column of dW_l
   int64_t layer_off[kMaxLayers + 1];
   int64_t n_params;
 };
 constexpr uint32_t kTrainCols = 512;
+constexpr int kTrainHidden = 64;
 constexpr uint32_t kDK = 128;       // padded neuron extent of the dZ tile
 
 template <int PREC>
@@ -281,7 +284,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_train(TrArgs T, const float*
   uint32_t* tmem_slot = (uint32_t*)(smem + A.bar_off + 16);
   int* abort_flag = (int*)(smem + A.bar_off + 20);
   const uint32_t bar_w = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]);
-  const int H = A.hidden, L = A.n_hidden;
+  constexpr int H = kTrainHidden;   // the only width planned for this kernel
+  const int L = A.n_hidden;
+  float* hs = (float*)(smem + T.hs_off);
+  float* dys = (float*)(smem + T.dys_off);
 
   if (tid == 0) {
     mbar_init(bar_w, 1);
@@ -353,7 +359,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_train(TrArgs T, const float*
       }
     }
     // ---- forward through the hidden layers
-    float h[128];
+    float h[H];
     for (int l = 0; l < L; ++l) {
       const TcLayer Ly = A.L[l];
       pre_mma();
@@ -365,6 +371,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_train(TrArgs T, const float*
           mma<false>(tmem, sdesc(a0 + ks * 256, 128, sbo), sdesc(b0 + ks * 256, 128, sbo), id, ks > 0 ? 1u : 0u);
       }
       if (!sync_mma()) break;
+#pragma unroll
       for (int c0 = 0; c0 < H; c0 += 16) {
         float v[16];
         tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
@@ -383,6 +390,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_train(TrArgs T, const float*
     float dy[3];
     {
       float y[3] = {0.f, 0.f, 0.f};
+#pragma unroll
       for (int n = 0; n < H; ++n) {
         y[0] = fmaf(h[n], w_out[n], y[0]);
         y[1] = fmaf(h[n], w_out[H + n], y[1]);
@@ -401,13 +409,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_train(TrArgs T, const float*
         }
       }
     }
-    // dW_out[c][n] += sum over rows of dy_c h_n (warp shuffles, then shared atomics)
-    for (int c = 0; c < 3; ++c)
-      for (int n = 0; n < H; ++n) {
-        float v = dy[c] * h[n];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) atomicAdd(&dwo[c * H + n], v);
-      }
+    // dW_out[c][n] += sum over the tile's rows of dy_c h_n: the rows are staged
+    // in shared memory (row r rotated by r, so that neither the row writes nor
+    // the column reads conflict on banks) and each (c, n) has one owner thread
+    // that sums the 128 rows in order.
+#pragma unroll
+    for (int n = 0; n < H; ++n) hs[tid * H + ((n + tid) & (H - 1))] = h[n];
+    dys[4 * tid + 0] = dy[0]; dys[4 * tid + 1] = dy[1]; dys[4 * tid + 2] = dy[2];
+    __syncthreads();
+    for (int o = tid; o < 3 * H; o += kThreads) {
+      const int c = o / H, n = o % H;
+      float acc = 0.f;
+#pragma unroll 8
+      for (int r = 0; r < kTileM; ++r) acc = fmaf(dys[4 * r + c], hs[r * H + ((n + r) & (H - 1))], acc);
+      dwo[o] += acc;
+    }
+#pragma unroll
     for (int c0 = 0; c0 < H; c0 += 16) {
       float v[16];
 #pragma unroll
@@ -616,7 +633,7 @@ pf_status pf_tc_forward(pf_ctx* ctx, const pf_field* f, const float* q, int64_t 
 namespace {
 bool plan_train(const pf_field* f, TrArgs* T) {
   if (f->desc.prec != PF_PREC_BF16 && f->desc.prec != PF_PREC_F16) return false;
-  if (f->desc.hidden != 64) return false;
+  if (f->desc.hidden != kTrainHidden) return false;
   if (!plan(f, &T->f)) return false;
   const int L = T->f.n_hidden;
   const int H = T->f.hidden;
@@ -636,6 +653,11 @@ bool plan_train(const pf_field* f, TrArgs* T) {
   off += 3 * H * 4;
   T->dwo_off = off;
   off += 3 * H * 4;
+  off = (off + 15) / 16 * 16;
+  T->hs_off = off;
+  off += kTileM * H * 4;
+  T->dys_off = off;
+  off += kTileM * 4 * 4;
   T->f.bar_off = (off + 15) / 16 * 16;
   T->f.smem_bytes = T->f.bar_off + 64;
   for (int l = 0; l <= f->n_layers; ++l) T->layer_off[l] = f->layer_off[l];
