@@ -95,6 +95,54 @@ __device__ __forceinline__ void store16(uint8_t* tile, uint32_t kp, int r, int c
   }
 }
 
+// Frequency encoding of one query (6 inputs x F frequencies, features ordered
+// [input][k][sin, cos], each times s) into row r of an A tile with K extent
+// kp, zero-padded to kp; features sin/cos(2^k pi v), the argument scaled
+// exactly by ldexpf.  F = 12 (the usual width) is unrolled so that the
+// 16-feature staging buffer stays in registers.
+template <int PREC>
+__device__ __forceinline__ void encode_query(uint8_t* tile, uint32_t kp, int r, const float qv[6], int F, float s) {
+  if (F == 12) {
+    float buf[16];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        float sn, cs;
+        sincospif(ldexpf(qv[d], k), &sn, &cs);
+        const int f = 24 * d + 2 * k;       // feature index; 16 features per store
+        buf[f % 16] = sn * s;
+        buf[(f + 1) % 16] = cs * s;
+        if ((f + 2) % 16 == 0) store16<PREC>(tile, kp, r, f + 2 - 16, buf);
+      }
+    }
+    // features 144..kp-1: zero padding (144 = 9 x 16)
+    for (int col = 144; col < (int)kp; col += 16) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) buf[i] = 0.f;
+      store16<PREC>(tile, kp, r, col, buf);
+    }
+    return;
+  }
+  float buf[16];
+  int nb = 0, col = 0;
+  for (int d = 0; d < 6; ++d) {
+    for (int k = 0; k < F; ++k) {
+      float sn, cs;
+      sincospif(ldexpf(qv[d], k), &sn, &cs);
+      buf[nb++] = sn * s;
+      buf[nb++] = cs * s;
+      if (nb == 16) { store16<PREC>(tile, kp, r, col, buf); col += 16; nb = 0; }
+    }
+  }
+  while (col < (int)kp) {      // zero padding up to the MMA K step
+    for (int i = nb; i < 16; ++i) buf[i] = 0.f;
+    store16<PREC>(tile, kp, r, col, buf);
+    col += 16;
+    nb = 0;
+  }
+}
+
 template <int PREC>
 __global__ void __launch_bounds__(kThreads, 1) k_tc_forward(TcArgs A, const float* __restrict__ q, int64_t B_max,
                                                             const uint32_t* __restrict__ B_dev, float* __restrict__ out,
@@ -150,23 +198,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_forward(TcArgs A, const floa
 #pragma unroll
       for (int d = 0; d < 6; ++d) qv[d] = valid ? __ldg(q + 6 * row + d) : 0.f;
       const float s = FP8 ? A.L[0].inv_s_in : 1.f;   // input scale of layer 0 (fp8)
-      float buf[16];
-      int nb = 0, col = 0;
-      for (int d = 0; d < 6; ++d) {
-        for (int k = 0; k < F; ++k) {
-          float sn, cs;
-          sincospif(ldexpf(qv[d], k), &sn, &cs);
-          buf[nb++] = sn * s;
-          buf[nb++] = cs * s;
-          if (nb == 16) { store16<PREC>(a_tile, kp0, tid, col, buf); col += 16; nb = 0; }
-        }
-      }
-      while (col < (int)kp0) {      // zero padding up to the MMA K step
-        for (int i = nb; i < 16; ++i) buf[i] = 0.f;
-        store16<PREC>(a_tile, kp0, tid, col, buf);
-        col += 16;
-        nb = 0;
-      }
+      encode_query<PREC>(a_tile, kp0, tid, qv, F, s);
     }
     float y0 = 0.f, y1 = 0.f, y2 = 0.f;
     for (int l = 0; l < A.n_hidden; ++l) {
@@ -341,22 +373,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_train(TrArgs T, const float*
       float qv[6];
 #pragma unroll
       for (int d = 0; d < 6; ++d) qv[d] = valid ? __ldg(q + 6 * row + d) : 0.f;
-      float buf[16];
-      int nb = 0, col = 0;
-      for (int d = 0; d < 6; ++d)
-        for (int k = 0; k < F; ++k) {
-          float sn, cs;
-          sincospif(ldexpf(qv[d], k), &sn, &cs);
-          buf[nb++] = sn;
-          buf[nb++] = cs;
-          if (nb == 16) { store16<PREC>(a0, kp0, tid, col, buf); col += 16; nb = 0; }
-        }
-      while (col < (int)kp0) {
-        for (int i = nb; i < 16; ++i) buf[i] = 0.f;
-        store16<PREC>(a0, kp0, tid, col, buf);
-        col += 16;
-        nb = 0;
-      }
+      encode_query<PREC>(a0, kp0, tid, qv, F, 1.f);
     }
     // ---- forward through the hidden layers
     float h[H];
