@@ -297,18 +297,37 @@ struct TrArgs {
 };
 constexpr uint32_t kTrainCols = 512;
 constexpr int kTrainHidden = 64;
+constexpr int kTrainThreads = 256;
 constexpr uint32_t kDK = 128;       // padded neuron extent of the dZ tile
 
+// Writes 8 values of row r as one 16-byte chunk (16-bit operand types);
+// `chunk` is the K index / 8.
 template <int PREC>
-__global__ void __launch_bounds__(kThreads, 1) k_tc_train(TrArgs T, const float* __restrict__ q,
-                                                          const float* __restrict__ targets,
-                                                          const float* __restrict__ dy_in, int64_t B, float inv_n,
-                                                          float* __restrict__ partial, float* __restrict__ loss,
-                                                          uint32_t* err) {
+__device__ __forceinline__ void store8(uint8_t* tile, uint32_t kp, int r, int chunk, const float v[8]) {
+  uint4 q;
+  q.x = pack2<PREC>(v[0], v[1]); q.y = pack2<PREC>(v[2], v[3]);
+  q.z = pack2<PREC>(v[4], v[5]); q.w = pack2<PREC>(v[6], v[7]);
+  store_chunk(tile, kp * 2, r, chunk, q);
+}
+
+// Fused forward + loss + backward for a 128-query tile, two warpgroups: the
+// thread pair (r, r + 128) owns tile row r, and the two threads split the
+// row's columns (encoding inputs 0-2 / 3-5; neurons 0-31 / 32-63), so that
+// each SM sub-partition has two warps to switch between while the other
+// waits.  TMEM lane quarter of warp w: w mod 4.
+template <int PREC>
+__global__ void __launch_bounds__(kTrainThreads, 1) k_tc_train(TrArgs T, const float* __restrict__ q,
+                                                               const float* __restrict__ targets,
+                                                               const float* __restrict__ dy_in, int64_t B, float inv_n,
+                                                               float* __restrict__ partial, float* __restrict__ loss,
+                                                               uint32_t* err) {
   constexpr uint32_t AB_TYPE = (PREC == PF_PREC_BF16) ? 1u : 0u;
+  constexpr int H = kTrainHidden;   // the only width planned for this kernel
+  constexpr int HH = H / 2;         // columns per thread of a row pair
   extern __shared__ __align__(1024) uint8_t smem[];
   const TcArgs& A = T.f;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int r = tid & (kTileM - 1), hf = tid >> 7;
   float* w_out = (float*)(smem + A.wout_off);
   float* dwo = (float*)(smem + T.dwo_off);
   uint8_t* dtile = smem + T.d_off;
@@ -316,10 +335,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_train(TrArgs T, const float*
   uint32_t* tmem_slot = (uint32_t*)(smem + A.bar_off + 16);
   int* abort_flag = (int*)(smem + A.bar_off + 20);
   const uint32_t bar_w = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]);
-  constexpr int H = kTrainHidden;   // the only width planned for this kernel
   const int L = A.n_hidden;
   float* hs = (float*)(smem + T.hs_off);
-  float* dys = (float*)(smem + T.dys_off);
+  float* dys = (float*)(smem + T.dys_off);      // [128][4]: dy of the row
+  float* ys = dys + 4 * kTileM;                  // [128][4]: second half's partial output
 
   if (tid == 0) {
     mbar_init(bar_w, 1);
@@ -327,9 +346,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_train(TrArgs T, const float*
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int i = tid; i < 3 * H; i += kThreads) { w_out[i] = A.w_out[i]; dwo[i] = 0.f; }
+  for (int i = tid; i < 3 * H; i += kTrainThreads) { w_out[i] = A.w_out[i]; dwo[i] = 0.f; }
   // zero the padded neuron columns of the dZ tile once (never written later)
-  for (int i = tid; i < (int)(kTileM * kDK * 2 / 16); i += kThreads) ((uint4*)dtile)[i] = make_uint4(0, 0, 0, 0);
+  for (int i = tid; i < (int)(kTileM * kDK * 2 / 16); i += kTrainThreads) ((uint4*)dtile)[i] = make_uint4(0, 0, 0, 0);
   if (warp == 0) tmem_alloc(tmem_slot, kTrainCols);
   __syncthreads();
   tc_fence_after();
@@ -342,7 +361,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_train(TrArgs T, const float*
   __syncthreads();
   const int64_t n_tiles = (B + kTileM - 1) / kTileM;
   uint32_t phase = 0;
-  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
   const int F = A.in_freqs;
   const uint32_t kp0 = A.L[0].kp;
   const uint32_t d_rg = (kDK * 2 / 16) * 128;       // dZ tile: bytes between 8-row groups
@@ -365,18 +384,40 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_train(TrArgs T, const float*
   };
 
   for (int64_t tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x) {
-    const int64_t row = tile * kTileM + tid;
+    const int64_t row = tile * kTileM + r;
     const bool valid = row < B;
     // ---- encoding -> A_0
     {
       uint8_t* a0 = smem + T.a_off[0];
-      float qv[6];
+      if (F == 12) {
+        // this thread: inputs 3 hf .. 3 hf + 2 = features 72 hf .. 72 hf + 71
+        float buf[8];
 #pragma unroll
-      for (int d = 0; d < 6; ++d) qv[d] = valid ? __ldg(q + 6 * row + d) : 0.f;
-      encode_query<PREC>(a0, kp0, tid, qv, F, 1.f);
+        for (int dd = 0; dd < 3; ++dd) {
+          const float v = valid ? __ldg(q + 6 * row + 3 * hf + dd) : 0.f;
+#pragma unroll
+          for (int k = 0; k < 12; ++k) {
+            float sn, cs;
+            sincospif(ldexpf(v, k), &sn, &cs);
+            const int lf = 24 * dd + 2 * k;
+            buf[lf % 8] = sn;
+            buf[(lf + 1) % 8] = cs;
+            if ((lf + 2) % 8 == 0) store8<PREC>(a0, kp0, r, (72 * hf + lf + 2 - 8) / 8, buf);
+          }
+        }
+        // zero padding of K = 144 .. kp0 - 1, chunks split between the pair
+#pragma unroll
+        for (int i = 0; i < 8; ++i) buf[i] = 0.f;
+        for (int c = 18 + hf; c < (int)(kp0 / 8); c += 2) store8<PREC>(a0, kp0, r, c, buf);
+      } else if (hf == 0) {
+        float qv[6];
+#pragma unroll
+        for (int d = 0; d < 6; ++d) qv[d] = valid ? __ldg(q + 6 * row + d) : 0.f;
+        encode_query<PREC>(a0, kp0, r, qv, F, 1.f);
+      }
     }
     // ---- forward through the hidden layers
-    float h[H];
+    float h[HH];
     for (int l = 0; l < L; ++l) {
       const TcLayer Ly = A.L[l];
       pre_mma();
@@ -389,69 +430,80 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_train(TrArgs T, const float*
       }
       if (!sync_mma()) break;
 #pragma unroll
-      for (int c0 = 0; c0 < H; c0 += 16) {
+      for (int g = 0; g < HH / 16; ++g) {
+        const int c0 = HH * hf + 16 * g;
         float v[16];
         tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
         if (l == L - 1) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) h[c0 + i] = v[i];
+          for (int i = 0; i < 16; ++i) h[16 * g + i] = v[i];
         } else {
-          store16<PREC>(smem + T.a_off[l + 1], (uint32_t)H, tid, c0, v);
+          store16<PREC>(smem + T.a_off[l + 1], (uint32_t)H, r, c0, v);
         }
       }
     }
     if (*abort_flag) break;
-    // ---- output layer, loss, dW_out, dZ_{L-1}
-    float dy[3];
+    // ---- output layer (float32 on the unrounded last activation), loss, dy
     {
-      float y[3] = {0.f, 0.f, 0.f};
+      float y0 = 0.f, y1 = 0.f, y2 = 0.f;
 #pragma unroll
-      for (int n = 0; n < H; ++n) {
-        y[0] = fmaf(h[n], w_out[n], y[0]);
-        y[1] = fmaf(h[n], w_out[H + n], y[1]);
-        y[2] = fmaf(h[n], w_out[2 * H + n], y[2]);
+      for (int j = 0; j < HH; ++j) {
+        const int n = HH * hf + j;
+        y0 = fmaf(h[j], w_out[n], y0);
+        y1 = fmaf(h[j], w_out[H + n], y1);
+        y2 = fmaf(h[j], w_out[2 * H + n], y2);
       }
-      for (int c = 0; c < 3; ++c) {
-        if (!valid) { dy[c] = 0.f; continue; }
-        if (targets) {
-          float t = targets[3 * row + c];
-          float den = t * t + 0.01f;
-          float diff = y[c] - t;
-          lsum += diff * diff / den;
-          dy[c] = 2.f * diff / den * inv_n;
-        } else {
-          dy[c] = dy_in[3 * row + c];
+      if (hf == 1) { ys[4 * r + 0] = y0; ys[4 * r + 1] = y1; ys[4 * r + 2] = y2; }
+      __syncthreads();
+      if (hf == 0) {
+        const float y[3] = {y0 + ys[4 * r + 0], y1 + ys[4 * r + 1], y2 + ys[4 * r + 2]};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          float g = 0.f;
+          if (valid) {
+            if (targets) {
+              const float t = targets[3 * row + c];
+              const float den = t * t + 0.01f;
+              const float diff = y[c] - t;
+              lsum += diff * diff / den;
+              g = 2.f * diff / den * inv_n;
+            } else {
+              g = dy_in[3 * row + c];
+            }
+          }
+          dys[4 * r + c] = g;
         }
       }
-    }
-    // dW_out[c][n] += sum over the tile's rows of dy_c h_n: the rows are staged
-    // in shared memory (row r rotated by r, so that neither the row writes nor
-    // the column reads conflict on banks) and each (c, n) has one owner thread
-    // that sums the 128 rows in order.
+      // this thread's columns of the last activation, for dW_out (row r
+      // rotated by r: conflict-free writes and column reads)
 #pragma unroll
-    for (int n = 0; n < H; ++n) hs[tid * H + ((n + tid) & (H - 1))] = h[n];
-    dys[4 * tid + 0] = dy[0]; dys[4 * tid + 1] = dy[1]; dys[4 * tid + 2] = dy[2];
-    __syncthreads();
-    for (int o = tid; o < 3 * H; o += kThreads) {
+      for (int j = 0; j < HH; ++j) hs[r * H + ((HH * hf + j + r) & (H - 1))] = h[j];
+      __syncthreads();
+    }
+    const float dy0 = dys[4 * r + 0], dy1 = dys[4 * r + 1], dy2 = dys[4 * r + 2];
+    // dW_out[c][n] += sum over the tile's rows of dy_c h_n: one owner thread
+    // per (c, n), rows summed in order
+    for (int o = tid; o < 3 * H; o += kTrainThreads) {
       const int c = o / H, n = o % H;
       float acc = 0.f;
 #pragma unroll 8
-      for (int r = 0; r < kTileM; ++r) acc = fmaf(dys[4 * r + c], hs[r * H + ((n + r) & (H - 1))], acc);
+      for (int rr = 0; rr < kTileM; ++rr) acc = fmaf(dys[4 * rr + c], hs[rr * H + ((n + rr) & (H - 1))], acc);
       dwo[o] += acc;
     }
+    // dZ_{L-1} = (dy W_out) * [rounded h > 0], this thread's columns
 #pragma unroll
-    for (int c0 = 0; c0 < H; c0 += 16) {
+    for (int g = 0; g < HH / 16; ++g) {
       float v[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
-        const int n = c0 + i;
-        float dh = dy[0] * w_out[n] + dy[1] * w_out[H + n] + dy[2] * w_out[2 * H + n];
-        float hr = PREC == PF_PREC_BF16 ? pff::round_bf16(h[n]) : pff::round_f16(h[n]);
+        const int j = 16 * g + i, n = HH * hf + j;
+        const float dh = dy0 * w_out[n] + dy1 * w_out[H + n] + dy2 * w_out[2 * H + n];
+        const float hr = PREC == PF_PREC_BF16 ? pff::round_bf16(h[j]) : pff::round_f16(h[j]);
         v[i] = hr > 0.f ? dh : 0.f;
       }
-      store16<PREC>(dtile, kDK, tid, c0, v);
+      store16<PREC>(dtile, kDK, r, HH * hf + 16 * g, v);
     }
     // ---- backward through the hidden layers
     for (int l = L - 1; l >= 0; --l) {
@@ -483,16 +535,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_train(TrArgs T, const float*
       }
       if (!sync_mma()) break;
       if (l > 0) {
-        // dZ_{l-1} = dA_l * [A_l > 0], rounded; A_l is the layer's (rounded) input tile
+        // dZ_{l-1} = dA_l * [A_l > 0], rounded; A_l is the layer's (rounded)
+        // input tile (H wide for l > 0); the pair splits its column groups
         const uint8_t* al = smem + T.a_off[l];
         const uint32_t kpl = A.L[l].kp;
-        for (int c0 = 0; c0 < (int)kpl; c0 += 16) {
+        for (int c0 = 16 * hf; c0 < (int)kpl; c0 += 32) {
           float v[16];
           tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
 #pragma unroll
           for (int j = 0; j < 2; ++j) {
-            const uint32_t off = (uint32_t)(tid >> 3) * ((kpl * 2 / 16) * 128) + (uint32_t)(c0 / 8 + j) * 128 +
-                                 (uint32_t)(tid & 7) * 16;
+            const uint32_t off = (uint32_t)(r >> 3) * ((kpl * 2 / 16) * 128) + (uint32_t)(c0 / 8 + j) * 128 +
+                                 (uint32_t)(r & 7) * 16;
             const uint4 raw = *(const uint4*)(al + off);
             const uint16_t* hv = (const uint16_t*)&raw;
 #pragma unroll
@@ -501,23 +554,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_train(TrArgs T, const float*
               if (!pos) v[8 * j + i] = 0.f;
             }
           }
-          store16<PREC>(dtile, kDK, tid, c0, v);
+          store16<PREC>(dtile, kDK, r, c0, v);
         }
       }
     }
     first_tile = false;
   }
-  // ---- per-CTA partial dW: TMEM rows 0..H-1 (warps 0..H/32-1), then dW_out
+  // ---- per-CTA partial dW: TMEM rows 0..H-1 (lane quarters 0..H/32-1), then dW_out
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   float* part = partial + (size_t)blockIdx.x * (size_t)T.n_params;
-  if (!*abort_flag && warp < H / 32) {
-    const int m = warp * 32 + lane;                  // output neuron of this lane
+  if (!*abort_flag && (warp & 3) < H / 32) {
+    const int m = (warp & 3) * 32 + lane;            // output neuron of this lane
     for (int l = 0; l < L; ++l) {
       const uint32_t kpl = A.L[l].kp;
       const int fan = l == 0 ? 12 * F : H;
-      for (uint32_t c0 = 0; c0 < kpl; c0 += 16) {
+      for (uint32_t c0 = 16 * hf; c0 < kpl; c0 += 32) {
         float v[16];
         if (first_tile) {
 #pragma unroll
@@ -532,7 +585,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_train(TrArgs T, const float*
     }
   }
   __syncthreads();
-  for (int i = tid; i < 3 * H; i += kThreads) part[T.layer_off[L] + i] = dwo[i];
+  for (int i = tid; i < 3 * H; i += kTrainThreads) part[T.layer_off[L] + i] = dwo[i];
   if (loss) {
     for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
     if (lane == 0 && lsum != 0.f) atomicAdd(loss, lsum * inv_n);
@@ -674,7 +727,7 @@ bool plan_train(const pf_field* f, TrArgs* T) {
   T->hs_off = off;
   off += kTileM * H * 4;
   T->dys_off = off;
-  off += kTileM * 4 * 4;
+  off += 2 * kTileM * 4 * 4;                 // dy and the pair's partial outputs
   T->f.bar_off = (off + 15) / 16 * 16;
   T->f.smem_bytes = T->f.bar_off + 64;
   for (int l = 0; l <= f->n_layers; ++l) T->layer_off[l] = f->layer_off[l];
@@ -701,7 +754,8 @@ pf_status pf_tc_backward(pf_ctx* ctx, const pf_field* f, const float* q, const f
   float inv_n = targets ? 1.0f / (float)(3 * B) : 0.f;
   auto launch = [&](auto kern) -> pf_status {
     PF_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T.f.smem_bytes));
-    kern<<<grid, kThreads, T.f.smem_bytes, ctx->stream>>>(T, q, targets, dy, B, inv_n, partial, loss, ctx->err_dev);
+    kern<<<grid, kTrainThreads, T.f.smem_bytes, ctx->stream>>>(T, q, targets, dy, B, inv_n, partial, loss,
+                                                               ctx->err_dev);
     PF_CUDA(ctx, cudaGetLastError());
     return PF_OK;
   };
