@@ -270,13 +270,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_forward(TcArgs A, const floa
 }
 
 // ---------------------------------------------------------------- training step
-// One fused pass per 128-query tile (bf16 / fp16 fields of width 64):
+// One fused pass per 128-query tile (bf16 / fp16 fields of width 64), two
+// warpgroups splitting each row's columns:
 //   forward  : encoding -> A_0; for each hidden layer l, tcgen05.mma
 //              A_l x W_l^T -> TMEM, ReLU, operand rounding -> A_{l+1}
 //              (every layer's input tile stays in shared memory);
 //   output   : y = W_out h_L in float32 from registers; relative-MSE gradient
 //              dy = 2 (y - t) / (t^2 + 0.01) / (3B) (or a given dy); loss;
-//              dW_out by warp reductions; dZ_{L-1} = (W_out^T dy) * [h_L > 0];
+//              dW_out by one owner thread per weight over the tile's rows
+//              staged in shared memory; dZ_{L-1} = (W_out^T dy) * [h_L > 0];
 //   backward : for l = L-1..0, tcgen05.mma dW_l += dZ_l^T x A_l (both operands
 //              MN-major views of the row tiles, M padded to 128 neurons) into
 //              a TMEM accumulator that persists across the CTA's tiles, and
@@ -595,13 +597,24 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_tc_train(TrArgs T, const f
   if (warp == 0) tmem_dealloc(tmem, kTrainCols);
 }
 
-// dW = sum over CTAs of the partial rows, in CTA order.
+// dW = sum over CTAs of the partial rows: four running sums over the CTAs
+// p = 0, 4, 8, ... / 1, 5, 9, ... / ..., each in CTA order, then
+// (s0 + s1) + (s2 + s3) -- a fixed order, with four independent load chains.
 __global__ void k_reduce_partials(const float* __restrict__ partial, int n_parts, int64_t n, float* __restrict__ dw) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  float s = 0.f;
-  for (int p = 0; p < n_parts; ++p) s += partial[(size_t)p * n + i];
-  dw[i] = s;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  int p = 0;
+  for (; p + 4 <= n_parts; p += 4) {
+    s0 += partial[(size_t)p * n + i];
+    s1 += partial[(size_t)(p + 1) * n + i];
+    s2 += partial[(size_t)(p + 2) * n + i];
+    s3 += partial[(size_t)(p + 3) * n + i];
+  }
+  if (p < n_parts) s0 += partial[(size_t)p * n + i];
+  if (p + 1 < n_parts) s1 += partial[(size_t)(p + 1) * n + i];
+  if (p + 2 < n_parts) s2 += partial[(size_t)(p + 2) * n + i];
+  dw[i] = (s0 + s1) + (s2 + s3);
 }
 
 // ---------------------------------------------------------------- weight packing
@@ -761,7 +774,7 @@ pf_status pf_tc_backward(pf_ctx* ctx, const pf_field* f, const float* q, const f
   };
   if (f->desc.prec == PF_PREC_BF16) { PF_TRY(launch(k_tc_train<PF_PREC_BF16>)); }
   else { PF_TRY(launch(k_tc_train<PF_PREC_F16>)); }
-  k_reduce_partials<<<(unsigned)((f->n_params + 255) / 256), 256, 0, ctx->stream>>>(partial, grid, f->n_params, dw);
+  k_reduce_partials<<<(unsigned)((f->n_params + 127) / 128), 128, 0, ctx->stream>>>(partial, grid, f->n_params, dw);
   PF_CUDA(ctx, cudaGetLastError());
   return PF_OK;
 }
