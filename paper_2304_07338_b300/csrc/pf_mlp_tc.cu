@@ -60,10 +60,12 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
     return *(uint32_t*)&h;
   }
 }
+// Four e4m3 codes (round to nearest even, saturating), a in the low byte;
+// two paired conversions, each the same rounding as pff::e4m3_code.
 __device__ __forceinline__ uint32_t pack4_e4m3(float a, float b, float c, float d) {
-  uint32_t r = pff::e4m3_code(a) | ((uint32_t)pff::e4m3_code(b) << 8) | ((uint32_t)pff::e4m3_code(c) << 16) |
-               ((uint32_t)pff::e4m3_code(d) << 24);
-  return r;
+  const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+  const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+  return (lo & 0xFFFFu) | (hi << 16);
 }
 
 // Writes 16 bytes of row r at K-chunk c (16 bytes = one core-matrix row).
@@ -230,22 +232,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_forward(TcArgs A, const floa
       if (*abort_flag) break;
       const bool last = (l == A.n_hidden - 1);
       const uint32_t kp_next = last ? 0u : A.L[l + 1].kp;
+      // dequantisation and the next layer's input scale are powers of two
+      // (fp8; 1 otherwise), so one product by their product is exact too
       const float s_next = (FP8 && !last) ? A.L[l + 1].inv_s_in : 1.f;
+      const float sc = last ? Ly.dequant : Ly.dequant * s_next;
       for (int c0 = 0; c0 < H; c0 += 16) {
         float v[16];
         tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] * Ly.dequant, 0.f);
+        for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] * sc, 0.f);
         if (last) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            y0 = fmaf(v[i], w_out[c0 + i], y0);
-            y1 = fmaf(v[i], w_out[H + c0 + i], y1);
-            y2 = fmaf(v[i], w_out[2 * H + c0 + i], y2);
+          for (int i = 0; i < 16; i += 4) {
+            const float4 w0 = *(const float4*)(w_out + c0 + i);
+            const float4 w1 = *(const float4*)(w_out + H + c0 + i);
+            const float4 w2 = *(const float4*)(w_out + 2 * H + c0 + i);
+            y0 = fmaf(v[i], w0.x, y0); y0 = fmaf(v[i + 1], w0.y, y0);
+            y0 = fmaf(v[i + 2], w0.z, y0); y0 = fmaf(v[i + 3], w0.w, y0);
+            y1 = fmaf(v[i], w1.x, y1); y1 = fmaf(v[i + 1], w1.y, y1);
+            y1 = fmaf(v[i + 2], w1.z, y1); y1 = fmaf(v[i + 3], w1.w, y1);
+            y2 = fmaf(v[i], w2.x, y2); y2 = fmaf(v[i + 1], w2.y, y2);
+            y2 = fmaf(v[i + 2], w2.z, y2); y2 = fmaf(v[i + 3], w2.w, y2);
           }
         } else {
-#pragma unroll
-          for (int i = 0; i < 16; ++i) v[i] *= s_next;
           store16<PREC>(a_tile, kp_next, tid, c0, v);
         }
       }
