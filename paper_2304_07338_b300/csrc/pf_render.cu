@@ -75,7 +75,8 @@ __global__ void __launch_bounds__(128, 5) k_camera_samples(Vol V, DevLights L, C
                                                         float* __restrict__ calb, float* __restrict__ cdir,
                                                         uint32_t* __restrict__ cidx, uint32_t* __restrict__ ccount,
                                                         uint32_t* __restrict__ ckey, uint32_t* __restrict__ chist,
-                                                        uint32_t* err, unsigned long long* stats) {
+                                                        uint32_t* __restrict__ vmask, uint32_t* err,
+                                                        unsigned long long* stats) {
   int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool active = slot < n_slots;
   uint32_t nfetch = 0;
@@ -168,13 +169,16 @@ __global__ void __launch_bounds__(128, 5) k_camera_samples(Vol V, DevLights L, C
         valid = 1;
       }
     }
-    slot_ld[3 * slot + 0] = alb.x * Ld.x;
-    slot_ld[3 * slot + 1] = alb.y * Ld.y;
-    slot_ld[3 * slot + 2] = alb.z * Ld.z;
-    slot_li[3 * slot + 0] = 0.f;
-    slot_li[3 * slot + 1] = 0.f;
-    slot_li[3 * slot + 2] = 0.f;
+    if (MARCH && valid) {  // tracking mode: k_nee writes L_d of the valid slots
+      slot_ld[3 * slot + 0] = alb.x * Ld.x;
+      slot_ld[3 * slot + 1] = alb.y * Ld.y;
+      slot_ld[3 * slot + 2] = alb.z * Ld.z;
+    }
   }
+  // one validity bit per slot (the warp's 32 slots are one aligned word);
+  // compose reads only the valid slots, so no slot is zero-filled
+  const unsigned ball = __ballot_sync(0xffffffffu, valid);
+  if ((threadIdx.x & 31) == 0 && slot < n_slots) vmask[slot >> 5] = ball;
   if (stats) {
     unsigned long long v = nfetch;
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
@@ -186,7 +190,6 @@ __global__ void __launch_bounds__(128, 5) k_camera_samples(Vol V, DevLights L, C
   }
   if (cq == nullptr) return;
   // warp-aggregated append of the valid samples' queries
-  unsigned ball = __ballot_sync(0xffffffffu, valid);
   if (ball == 0) return;
   int lane = threadIdx.x & 31;
   uint32_t base = 0;
@@ -340,16 +343,24 @@ __global__ void __launch_bounds__(128, 6) k_nee(Vol V, DevLights L, float g, int
   }
 }
 
-__global__ void k_compose(const float* __restrict__ slot_ld, const float* __restrict__ slot_li, int64_t n_pix,
-                          int spp, float* __restrict__ out) {
+// Pixel = (1/spp) sum over its samples, in order, of albedo (L_d + L_i).  A
+// sample that did not scatter contributes exactly zero and is skipped (the
+// running sums are non-negative, so adding +0 would not change a bit);
+// slot_li is NULL when no field was queried.
+__global__ void k_compose(const float* __restrict__ slot_ld, const float* __restrict__ slot_li,
+                          const uint32_t* __restrict__ vmask, int64_t n_pix, int spp, float* __restrict__ out) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n_pix) return;
   float a0 = 0.f, a1 = 0.f, a2 = 0.f;
   for (int k = 0; k < spp; ++k) {
-    size_t s = 3 * ((size_t)p * spp + k);
-    a0 = a0 + (slot_ld[s + 0] + slot_li[s + 0]);
-    a1 = a1 + (slot_ld[s + 1] + slot_li[s + 1]);
-    a2 = a2 + (slot_ld[s + 2] + slot_li[s + 2]);
+    const size_t sl = (size_t)p * spp + k;
+    if (!((__ldg(vmask + (sl >> 5)) >> (sl & 31)) & 1u)) continue;
+    const size_t s = 3 * sl;
+    float l0 = slot_ld[s + 0], l1 = slot_ld[s + 1], l2 = slot_ld[s + 2];
+    if (slot_li) { l0 = l0 + slot_li[s + 0]; l1 = l1 + slot_li[s + 1]; l2 = l2 + slot_li[s + 2]; }
+    a0 = a0 + l0;
+    a1 = a1 + l1;
+    a2 = a2 + l2;
   }
   out[3 * p + 0] = a0 / (float)spp;
   out[3 * p + 1] = a1 / (float)spp;
@@ -511,7 +522,8 @@ extern "C" pf_status pf_render_neural(pf_ctx* ctx, const pf_volume* vol, const p
     PF_TRY(pf_scratch(ctx, WS_MISC, 256, (void**)&ccount));
     PF_CUDA(ctx, cudaMemsetAsync(ccount, 0, sizeof(uint32_t), ctx->stream));
   }
-  uint32_t *ckey = nullptr, *chist = nullptr, *cfill = nullptr, *perm = nullptr;
+  uint32_t *ckey = nullptr, *chist = nullptr, *cfill = nullptr, *perm = nullptr, *vmask = nullptr;
+  PF_TRY(pf_scratch(ctx, WS_VMASK, (size_t)((n_slots + 31) / 32) * sizeof(uint32_t), (void**)&vmask));
   uint64_t* coff = nullptr;
   if (!march) {
     PF_TRY(pf_scratch(ctx, WS_COMPACT_DIR, n_slots * 3 * sizeof(float), (void**)&cdir));
@@ -532,11 +544,11 @@ extern "C" pf_status pf_render_neural(pf_ctx* ctx, const pf_volume* vol, const p
   StageTimer tm(ctx, PF_STAGE_CAMERA);
 #define LAUNCH_CS(DT)                                                                                              \
   if (march) k_camera_samples<DT, true><<<grd, blk, 0, ctx->stream>>>(V, L, C, g, spp, h, seed, n_slots, ld, li, cq, \
-                                                                      calb, cdir, cidx, ccount, ckey, chist,        \
+                                                                      calb, cdir, cidx, ccount, ckey, chist, vmask, \
                                                                       ctx->err_dev, ctx->counters);                 \
   else k_camera_samples<DT, false><<<grd, blk, 0, ctx->stream>>>(V, L, C, g, spp, h, seed, n_slots, ld, li, cq, calb, \
-                                                                 cdir, cidx, ccount, ckey, chist, ctx->err_dev,     \
-                                                                 ctx->counters);
+                                                                 cdir, cidx, ccount, ckey, chist, vmask,            \
+                                                                 ctx->err_dev, ctx->counters);
   if (vol->dtype == PF_F32) { LAUNCH_CS(0) } else if (vol->dtype == PF_F16) { LAUNCH_CS(1) } else { LAUNCH_CS(2) }
 #undef LAUNCH_CS
   }
@@ -562,7 +574,8 @@ extern "C" pf_status pf_render_neural(pf_ctx* ctx, const pf_volume* vol, const p
   }
   {
     StageTimer tm(ctx, PF_STAGE_COMPOSE);
-    k_compose<<<(unsigned)((n_pix + 127) / 128), 128, 0, ctx->stream>>>(ld, li, n_pix, spp, out_rgb_dev);
+    k_compose<<<(unsigned)((n_pix + 127) / 128), 128, 0, ctx->stream>>>(ld, field ? li : nullptr, vmask, n_pix, spp,
+                                                                        out_rgb_dev);
   }
   PF_CUDA(ctx, cudaGetLastError());
   return PF_OK;
