@@ -34,6 +34,7 @@ sys.path.insert(0, ROOT)
 METRIC = "1080p frames/sec and field queries/sec vs plain GPU path tracer at equal RMSE"
 W_, H_, SPP, N_VOX, N_LIGHTS = 1920, 1080, 16, 1024, 8
 BRICK = 32                      # majorant brick edge (voxels) for the 1024^3 volume
+BRICK_PRIMARY = 64              # brick edge of the camera rays' (pooled) majorant grid
 HIDDEN, N_HIDDEN, FREQS = 128, 4, 12
 VOXEL_BYTES = 2                 # float16
 # DRAM bytes (read + write) per density lookup of k_nee, from one ncu capture
@@ -135,12 +136,13 @@ def setup_scene(device):
     return vol_t.contiguous(), torch.from_numpy(tf).to(device), lights, cams
 
 
-def cpu_baseline(vol_host, tf, lights, cams, seed, rows=2, weights=None, desc=None, scales=None, brick=8):
+def cpu_baseline(vol_host, tf, lights, cams, seed, rows=2, weights=None, desc=None, scales=None, brick=8,
+                 brick_primary=0):
     """The oracle (plain C++/numpy) on a bounded sample: `rows` full image rows
     of one frame at full spp, scaled to a frame."""
     import oracle
     from paper_2304_07338_b300 import inputs as I
-    v = I.Volume(vol_host, 20.0, 0.9, tf, brick=brick)
+    v = I.Volume(vol_host, 20.0, 0.9, tf, brick=brick, brick_primary=brick_primary)
     cam = cams[0]
     g = I.frame_g(seed, 0)
     y0 = H_ // 2
@@ -175,6 +177,8 @@ def main():
     ap.add_argument("--rmse-height", type=int, default=270)
     ap.add_argument("--ref-spp", type=int, default=4096)
     ap.add_argument("--brick", type=int, default=BRICK, help="majorant brick edge in voxels (power of two)")
+    ap.add_argument("--brick-primary", type=int, default=BRICK_PRIMARY,
+                    help="brick edge of the camera rays' pooled majorant grid (multiple of --brick)")
     args = ap.parse_args()
     W_, H_, SPP, N_VOX = args.width, args.height, args.spp, args.res
     args.warmup = max(args.warmup, 3)
@@ -202,7 +206,7 @@ def main():
     build.build()
     ctx = api.Context(local)
     vol_t, tf_t, lights, cams = setup_scene(dev)
-    vol = api.Volume(vol_t, 20.0, 0.9, tf_t, brick=args.brick)
+    vol = api.Volume(vol_t, 20.0, 0.9, tf_t, brick=args.brick, brick_primary=args.brick_primary)
     vol.s.majorant = vol.majorant(ctx)
     vol.attach_brick_majorants(ctx)
     setup = {}
@@ -324,7 +328,8 @@ def main():
         "config": {"workload": "large neural render: %d^3 f16 turbulence, 8 point lights, %dx%d, %d spp, "
                                "fp8 4x128 field, delta/ratio tracking" % (N_VOX, W_, H_, SPP),
                    "frames": "60-frame orbit", "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (2 GiB volume)", "majorant_brick": args.brick},
+                   "l2": "inputs larger than L2 (2 GiB volume)", "majorant_brick": args.brick,
+                   "majorant_brick_primary": args.brick_primary},
         "queries_per_s": qpf * fps,
         "queries_per_frame": qpf,
         "lookups_per_frame": {"camera": fetches_per_frame - nee_fetches_per_frame, "nee": nee_fetches_per_frame},
@@ -343,7 +348,8 @@ def main():
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         try:
             line["cpu_baseline"] = cpu_baseline(vol_t.cpu().numpy(), tf_t.cpu().numpy(), lights, cams, seed,
-                                                rows=args.cpu_rows, brick=args.brick, **oracle_field(field))
+                                                rows=args.cpu_rows, brick=args.brick,
+                                                brick_primary=args.brick_primary, **oracle_field(field))
         except Exception as e:  # reported, not fatal
             line["cpu_baseline"] = {"error": repr(e)[:200]}
     if rank == 0:
@@ -487,7 +493,8 @@ def run_reference(args, dev, seed):
                                                             desc))
     times = []
     for i in range(args.warmup + args.steps):
-        r = cpu_baseline(vol_h, tf_h, lights, cams, seed, rows=1, brick=args.brick, **fld)
+        r = cpu_baseline(vol_h, tf_h, lights, cams, seed, rows=1, brick=args.brick,
+                         brick_primary=args.brick_primary, **fld)
         if i >= args.warmup:
             times.append(1.0 / r["value"])
     fps = 1.0 / float(np.mean(times))

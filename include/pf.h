@@ -77,6 +77,11 @@ typedef struct {
   const float* brick_majorants_dev; /* brick majorants from pf_volume_brick_majorants, or NULL:
                                        the tracers then compute them into context scratch */
   int brick;                /* majorant brick edge in voxels: power of two, 0 = 8 */
+  int brick_primary;        /* brick edge for the free flight of the neural renderer's camera
+                               rays: 0 = brick, else a power-of-two multiple of brick; that
+                               grid is the brick grid max-pooled over groups of bricks (camera
+                               rays cross the whole volume and rarely collide, so fewer, looser
+                               bricks cost less; shadow rays keep the tight grid) */
 } pf_volume;
 
 /* Light source.  Directional: v = unit direction towards the light, rgb =

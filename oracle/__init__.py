@@ -53,7 +53,7 @@ def _declare(L):
     L.orc_trace_photons.argtypes = [i32, i32, i32, i32, P, f64, f64, P, i32, i32,
                                     P, P, P, i32, P, i32, u64, i32, i32, u64, i32, i32, u64, u64,
                                     P, P, P, P, P]
-    L.orc_camera_samples.argtypes = [i32, i32, i32, i32, P, f64, f64, P, i32, i32,
+    L.orc_camera_samples.argtypes = [i32, i32, i32, i32, P, f64, f64, P, i32, i32, i32,
                                      P, P, P, i32, f64, P, P, P, f64, i32, i32,
                                      i32, f64, u64, i32, i32, i32, P, P, P, P, P]
     L.orc_path_trace.argtypes = [i32, i32, i32, i32, P, f64, f64, P, i32, i32,
@@ -84,6 +84,7 @@ class _Vol:
         self.alb = float(vol.albedo)
         self.tfargs = (_p(self.tf), int(self.tf.shape[0]))
         self.brick = int(getattr(vol, "brick", 8))
+        self.brick_primary = int(getattr(vol, "brick_primary", 0))
 
 
 class _Lights:
@@ -322,7 +323,7 @@ def camera_samples(vol, lights, g: float, cam, spp: int, step_vox: float, seed: 
     n = (y1 - y0) * cam.width * spp
     valid = np.zeros(n, np.uint8)
     x, wo, alb, Ld = (np.zeros((n, 3)) for _ in range(4))
-    lib().orc_camera_samples(*v.args, v.ss, v.alb, *v.tfargs, v.brick, *L.args, float(g), *cm.args, spp,
+    lib().orc_camera_samples(*v.args, v.ss, v.alb, *v.tfargs, v.brick, v.brick_primary, *L.args, float(g), *cm.args, spp,
                              float(step_vox), seed, int(fp32), y0, y1,
                              _p(valid), _p(x), _p(wo), _p(alb), _p(Ld))
     shp = (y1 - y0, cam.width, spp)

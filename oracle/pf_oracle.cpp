@@ -362,6 +362,24 @@ template <typename R> Grid<R> build_grid(const Volume& V, int B) {
     return G;
 }
 
+// Coarser majorant grid for f x f x f groups of bricks (brick edge f B):
+// the largest of the group's brick majorants (exact; it bounds sigma_t over
+// the group because each brick majorant bounds it over its brick).
+template <typename R> Grid<R> pool_grid(const Grid<R>& G, int f) {
+    if (f <= 1) return G;
+    Grid<R> P;
+    P.nx = G.nx; P.ny = G.ny; P.nz = G.nz; P.B = G.B * f;
+    P.gx = (G.gx + f - 1) / f; P.gy = (G.gy + f - 1) / f; P.gz = (G.gz + f - 1) / f;
+    P.m.assign((size_t)P.gx * P.gy * P.gz, (R)0);
+    for (int k = 0; k < G.gz; ++k)
+        for (int j = 0; j < G.gy; ++j)
+            for (int i = 0; i < G.gx; ++i) {
+                R& c = P.m[(size_t)(i / f) + (size_t)P.gx * ((size_t)(j / f) + (size_t)P.gy * (k / f))];
+                c = std::max(c, G.at(i, j, k));
+            }
+    return P;
+}
+
 // Walk over the bricks a ray crosses (Amanatides-Woo).  Per axis: brick
 // width w = B / n, inverse direction inv = 1/d; the first plane parameter is
 // (plane - o) * inv and each further plane adds w * |inv|.  The rounding of
@@ -641,7 +659,8 @@ R march_tau(const Volume& V, V3<R> o, V3<R> d, R t0, R t1, R h, R jit) {
 }
 
 template <typename R>
-void camera_sample(const Volume& V, const Grid<R>& G, const Light* lights, int n_lights, R g, const CamFrame& cf,
+void camera_sample(const Volume& V, const Grid<R>& G, const Grid<R>& Gp, const Light* lights, int n_lights, R g,
+                   const CamFrame& cf,
                    int px, int py, int k, R step_vox, uint64_t seed,
                    int* valid, V3<R>* xo, V3<R>* wo, V3<R>* alb, V3<R>* Ld) {
     Rng rng(seed, 1, (uint64_t)py * (uint64_t)cf.W + (uint64_t)px, (uint32_t)k);
@@ -675,7 +694,7 @@ void camera_sample(const Volume& V, const Grid<R>& G, const Light* lights, int n
             tau = tau + sg * len;
         }
     } else {
-        hit = delta_track<R>(V, G, o, d, t0, t1, rng, &th, nullptr);
+        hit = delta_track<R>(V, Gp, o, d, t0, t1, rng, &th, nullptr);
     }
     if (!hit) return;
     V3<R> x = along(o, d, th);
@@ -900,9 +919,11 @@ void orc_trace_photons(int nx, int ny, int nz, int dtype, const void* data, doub
 }
 
 // Camera samples of the neural renderer (Algorithm 2: RayGeneration,
-// VolumeSampling, DirectIllumination).  Arrays are [H][W][spp].
+// VolumeSampling, DirectIllumination).  Arrays are [H][W][spp].  The free
+// flight of the camera rays uses the brick grid pooled to bricks of edge
+// brick_primary (0: brick); shadow rays use the brick grid.
 void orc_camera_samples(int nx, int ny, int nz, int dtype, const void* data, double ss, double alb,
-                        const float* tf, int tf_n, int brick,
+                        const float* tf, int tf_n, int brick, int brick_primary,
                         const int* lkind, const double* lv, const double* lrgb, int n_lights, double g,
                         const double* eye, const double* at, const double* up, double fovy, int W, int H,
                         int spp, double step_vox, uint64_t seed, int fp32, int y_begin, int y_end,
@@ -912,6 +933,9 @@ void orc_camera_samples(int nx, int ny, int nz, int dtype, const void* data, dou
     CamFrame cf = cam_frame(eye, at, up, fovy, W, H);
     Grid<double> G64 = fp32 ? Grid<double>() : build_grid<double>(V, brick);
     Grid<float> G32 = fp32 ? build_grid<float>(V, brick) : Grid<float>();
+    const int f = brick_primary > brick ? brick_primary / brick : 1;
+    Grid<double> P64 = pool_grid(G64, f);
+    Grid<float> P32 = pool_grid(G32, f);
     #pragma omp parallel for schedule(dynamic, 1) collapse(2)
     for (int py = y_begin; py < y_end; ++py)
         for (int px = 0; px < W; ++px)
@@ -920,14 +944,14 @@ void orc_camera_samples(int nx, int ny, int nz, int dtype, const void* data, dou
                 int vld;
                 if (fp32) {
                     V3<float> a, b, c, e;
-                    camera_sample<float>(V, G32, L.data(), n_lights, (float)g, cf, px, py, k, (float)step_vox, seed, &vld, &a, &b, &c, &e);
+                    camera_sample<float>(V, G32, P32, L.data(), n_lights, (float)g, cf, px, py, k, (float)step_vox, seed, &vld, &a, &b, &c, &e);
                     x[3 * idx] = a.x; x[3 * idx + 1] = a.y; x[3 * idx + 2] = a.z;
                     wo[3 * idx] = b.x; wo[3 * idx + 1] = b.y; wo[3 * idx + 2] = b.z;
                     albedo[3 * idx] = c.x; albedo[3 * idx + 1] = c.y; albedo[3 * idx + 2] = c.z;
                     Ld[3 * idx] = e.x; Ld[3 * idx + 1] = e.y; Ld[3 * idx + 2] = e.z;
                 } else {
                     V3<double> a, b, c, e;
-                    camera_sample<double>(V, G64, L.data(), n_lights, g, cf, px, py, k, step_vox, seed, &vld, &a, &b, &c, &e);
+                    camera_sample<double>(V, G64, P64, L.data(), n_lights, g, cf, px, py, k, step_vox, seed, &vld, &a, &b, &c, &e);
                     x[3 * idx] = a.x; x[3 * idx + 1] = a.y; x[3 * idx + 2] = a.z;
                     wo[3 * idx] = b.x; wo[3 * idx + 1] = b.y; wo[3 * idx + 2] = b.z;
                     albedo[3 * idx] = c.x; albedo[3 * idx + 1] = c.y; albedo[3 * idx + 2] = c.z;

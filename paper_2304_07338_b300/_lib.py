@@ -20,7 +20,8 @@ class PfVolume(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dtype", C.c_int),
                 ("data_dev", C.c_void_p), ("sigma_scale", C.c_float), ("albedo", C.c_float),
                 ("tf_lut_dev", C.c_void_p), ("tf_n", C.c_int), ("majorant", C.c_float),
-                ("brick_majorants_dev", C.c_void_p), ("brick", C.c_int)]
+                ("brick_majorants_dev", C.c_void_p), ("brick", C.c_int),
+                ("brick_primary", C.c_int)]
 
 
 class PfLight(C.Structure):

@@ -167,6 +167,12 @@ pf_status pf_check_volume(pf_ctx* ctx, const pf_volume* v) {
   if (v->brick != 0 && (v->brick < 2 || v->brick > 256 || (v->brick & (v->brick - 1))))
     return pf_fail(ctx, PF_ERR_INVALID_ARG, "brick must be 0 (= 8) or a power of two in [2, 256]");
   {
+    const int Bb = v->brick ? v->brick : 8;
+    if (v->brick_primary != 0 && (v->brick_primary < Bb || v->brick_primary > 1024 ||
+                                  (v->brick_primary & (v->brick_primary - 1))))
+      return pf_fail(ctx, PF_ERR_INVALID_ARG, "brick_primary must be 0 or a power-of-two multiple of brick, <= 1024");
+  }
+  {
     const int64_t B = v->brick ? v->brick : 8;
     if (((v->nx + B - 1) / B) * ((v->ny + B - 1) / B) * ((v->nz + B - 1) / B) >= ((int64_t)1 << 31))
       return pf_fail(ctx, PF_ERR_INVALID_ARG, "too many majorant bricks (>= 2^31): use a larger brick");

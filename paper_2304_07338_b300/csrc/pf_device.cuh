@@ -466,8 +466,9 @@ __device__ __forceinline__ void camera_ray(const CamF& c, int px, int py, float 
 }  // namespace pfd
 
 // Host-side packing of the public scene structs into the kernels' views.
-inline pfd::Vol pf_make_vol(const pf_volume* v, float majorant, const float* grid = nullptr) {
-  const int B = v->brick > 0 ? v->brick : 8;
+// brick_edge: edge of the bricks of `grid` (0: the volume's brick).
+inline pfd::Vol pf_make_vol(const pf_volume* v, float majorant, const float* grid = nullptr, int brick_edge = 0) {
+  const int B = brick_edge > 0 ? brick_edge : (v->brick > 0 ? v->brick : 8);
   pfd::Vol V;
   V.data = v->data_dev; V.nx = v->nx; V.ny = v->ny; V.nz = v->nz; V.dtype = v->dtype;
   V.sigma_scale = v->sigma_scale; V.albedo = v->albedo; V.majorant = majorant;

@@ -54,6 +54,20 @@ __device__ __forceinline__ uint32_t morton_cell(V3 x) {
   return spread3(cx) | (spread3(cy) << 1) | (spread3(cz) << 2);
 }
 
+// Coarser majorant grid: each cell the largest majorant of its f x f x f
+// group of bricks (exact; it bounds sigma_t over the group).
+__global__ void k_pool_majorants(const float* __restrict__ fine, int gx, int gy, int gz, int f, int px, int py,
+                                 int pz, float* __restrict__ coarse) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= (int64_t)px * py * pz) return;
+  const int I = (int)(c % px), J = (int)((c / px) % py), K = (int)(c / ((int64_t)px * py));
+  float m = 0.0f;
+  for (int k = K * f; k < min(K * f + f, gz); ++k)
+    for (int j = J * f; j < min(J * f + f, gy); ++j)
+      for (int i = I * f; i < min(I * f + f, gx); ++i) m = fmaxf(m, fine[i + (int64_t)gx * (j + (int64_t)gy * k)]);
+  coarse[c] = m;
+}
+
 // Counting-sort placement: entry i goes to off[key] + (its rank among the
 // entries of that key, in atomic order).
 __global__ void k_place(const uint32_t* __restrict__ ckey, const uint32_t* __restrict__ ccount,
@@ -535,6 +549,18 @@ extern "C" pf_status pf_render_neural(pf_ctx* ctx, const pf_volume* vol, const p
     PF_CUDA(ctx, cudaMemsetAsync(chist, 0, 2 * kCells * sizeof(uint32_t), ctx->stream));
   }
   Vol V = pf_make_vol(vol, 0.f, grid);
+  Vol Vp = V;  // camera rays' free flight: the grid pooled to brick_primary
+  if (!march && vol->brick_primary > V.B) {
+    const int f = vol->brick_primary / V.B;
+    const int px = (V.gx + f - 1) / f, py = (V.gy + f - 1) / f, pz = (V.gz + f - 1) / f;
+    const int64_t np = (int64_t)px * py * pz;
+    float* pooled;
+    PF_TRY(pf_scratch(ctx, WS_GRID_PRIMARY, (size_t)np * sizeof(float), (void**)&pooled));
+    k_pool_majorants<<<(unsigned)((np + 127) / 128), 128, 0, ctx->stream>>>(grid, V.gx, V.gy, V.gz, f, px, py, pz,
+                                                                           pooled);
+    PF_CUDA(ctx, cudaGetLastError());
+    Vp = pf_make_vol(vol, 0.f, pooled, vol->brick_primary);
+  }
   DevLights L = pf_make_lights(lights, n_lights);
   CamF C = make_cam(cam);
   int nmax = std::max(vol->nx, std::max(vol->ny, vol->nz));
@@ -543,10 +569,10 @@ extern "C" pf_status pf_render_neural(pf_ctx* ctx, const pf_volume* vol, const p
   {
   StageTimer tm(ctx, PF_STAGE_CAMERA);
 #define LAUNCH_CS(DT)                                                                                              \
-  if (march) k_camera_samples<DT, true><<<grd, blk, 0, ctx->stream>>>(V, L, C, g, spp, h, seed, n_slots, ld, li, cq, \
+  if (march) k_camera_samples<DT, true><<<grd, blk, 0, ctx->stream>>>(Vp, L, C, g, spp, h, seed, n_slots, ld, li, cq, \
                                                                       calb, cdir, cidx, ccount, ckey, chist, vmask, \
                                                                       ctx->err_dev, ctx->counters);                 \
-  else k_camera_samples<DT, false><<<grd, blk, 0, ctx->stream>>>(V, L, C, g, spp, h, seed, n_slots, ld, li, cq, calb, \
+  else k_camera_samples<DT, false><<<grd, blk, 0, ctx->stream>>>(Vp, L, C, g, spp, h, seed, n_slots, ld, li, cq, calb, \
                                                                  cdir, cidx, ccount, ckey, chist, vmask,            \
                                                                  ctx->err_dev, ctx->counters);
   if (vol->dtype == PF_F32) { LAUNCH_CS(0) } else if (vol->dtype == PF_F16) { LAUNCH_CS(1) } else { LAUNCH_CS(2) }

@@ -64,13 +64,15 @@ def test_march_with_f32_field(pf_ctx, orc):
     assert err.max() <= 5e-3, err.max()
 
 
-def test_tracking_direct_matches_float_oracle(pf_ctx, orc):
+@pytest.mark.parametrize("brick,primary", [(8, 0), (4, 16), (8, 32)])
+def test_tracking_direct_matches_float_oracle(pf_ctx, orc, brick, primary):
     sc = I.scene_judge(32, 32, 24, 8)
-    vol = api.Volume.from_inputs(sc.volume)
+    v = dataclasses.replace(sc.volume, brick=brick, brick_primary=primary)
+    vol = api.Volume.from_inputs(v)
     for g in (0.0, 0.5):
         img = api.render_neural(pf_ctx, vol, sc.lights, g, sc.camera, sc.spp, 0.0, seed=3)
         pf_ctx.sync()
-        ref = orc.render_neural(sc.volume, sc.lights, g, sc.camera, sc.spp, 0.0, 3, fp32=True)
+        ref = orc.render_neural(v, sc.lights, g, sc.camera, sc.spp, 0.0, 3, fp32=True)
         err = _rel_err(img.cpu().numpy(), ref)
         assert err.max() <= 2e-6, (g, err.max())
 
@@ -173,7 +175,7 @@ def test_large_render_sampled_rows(pf_ctx, orc):
     from oracle import field as F
     vol_t, tf, lights, cams = I.large_scene_parts(1024, device="cuda")
     tf_t = torch.from_numpy(tf).cuda()
-    vol = api.Volume(vol_t.contiguous(), 20.0, 0.9, tf_t, brick=32)     # the benchmark's brick size
+    vol = api.Volume(vol_t.contiguous(), 20.0, 0.9, tf_t, brick=32, brick_primary=64)   # the benchmark's bricks
     vol.attach_brick_majorants(pf_ctx)
     fld = api.Field(pf_ctx, 12, 128, 4, "fp8", 5.0, seed=5)
     desc = F.FieldDesc(12, 128, 4, F.PREC_FP8, 5.0, 5)
@@ -186,7 +188,7 @@ def test_large_render_sampled_rows(pf_ctx, orc):
     cam, g = cams[7], I.frame_g(11, 7)
     img = api.render_neural(pf_ctx, vol, lights, g, cam, 16, 0.0, seed=99, field=fld)
     pf_ctx.sync()
-    vh = I.Volume(vol_t.cpu().numpy(), 20.0, 0.9, tf, brick=32)
+    vh = I.Volume(vol_t.cpu().numpy(), 20.0, 0.9, tf, brick=32, brick_primary=64)
     for y0 in (500, 700):
         ref = orc.render_neural(vh, lights, g, cam, 16, 0.0, 99, weights=w, desc=desc, scales=scales, fp32=True,
                                 rows=(y0, y0 + 1))

@@ -125,3 +125,29 @@ def test_photon_map_indirect_matches_path_tracer(orc):
     # the field target stands for the in-scattered radiance itself: dropping
     # the 1/sigma normalisation or the phase function would miss by far more
     assert abs(neural.mean() - pt.mean()) < 0.04 * pt.mean()
+
+
+def test_pooled_primary_grid_samples_the_same_free_flight(orc):
+    """Camera rays tracked over the brick grid max-pooled to 16-voxel bricks
+    (brick_primary) sample the same free-flight distribution as over the
+    4-voxel brick grid: per-pixel scatter fractions and mean scatter depths
+    agree within their sampling error, on a heterogeneous volume."""
+    import dataclasses
+    sc = I.scene_judge(40, 3, 3, 1)
+    base = dataclasses.replace(sc.volume, brick=4)
+    pooled = dataclasses.replace(sc.volume, brick=4, brick_primary=16)
+    spp = 6000
+    a = orc.camera_samples(base, sc.lights, 0.0, sc.camera, spp, 0.0, seed=31)
+    b = orc.camera_samples(pooled, sc.lights, 0.0, sc.camera, spp, 0.0, seed=32)
+    pa, pb = a["valid"].mean(axis=2), b["valid"].mean(axis=2)
+    se = np.sqrt(pa * (1 - pa) / spp + pb * (1 - pb) / spp) + 1e-12
+    assert np.all(np.abs(pa - pb) < 5 * se), (pa, pb)
+    eye = np.array(sc.camera.eye)
+    for y in range(3):
+        for x in range(3):
+            da = np.linalg.norm(a["x"][y, x][a["valid"][y, x]] - eye, axis=1)
+            db = np.linalg.norm(b["x"][y, x][b["valid"][y, x]] - eye, axis=1)
+            if da.size > 50 and db.size > 50:
+                s = np.sqrt(da.var() / da.size + db.var() / db.size)
+                assert abs(da.mean() - db.mean()) < 5 * s + 1e-9
+    assert pa.mean() > 0.05
