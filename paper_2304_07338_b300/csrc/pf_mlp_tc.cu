@@ -2,10 +2,13 @@
 //
 // Forward pass (Sec. 3.4; hidden layers bf16 / fp16 / fp8 e4m3, FP32
 // accumulation in tensor memory):
-//   * one CTA = 4 warps, persistent over 128-query tiles;
+//   * one CTA per SM, persistent over 128-query tiles, with up to four
+//     warpgroups that each carry their own tile through the layers (own A
+//     tile, TMEM columns, MMA barrier and named barrier), so that one
+//     group's MMAs overlap the others' CUDA-core work;
 //   * the packed hidden-layer weights of the whole network are copied once
-//     per CTA into shared memory with bulk asynchronous copies
-//     (cp.async.bulk, completion on an mbarrier);
+//     per CTA into shared memory, shared by the groups, with a bulk
+//     asynchronous copy (cp.async.bulk, completion on an mbarrier);
 //   * each thread owns one query row: it computes the frequency encoding and
 //     writes it into the A tile in shared memory (K-major core-matrix layout:
 //     8 rows x 16 bytes per core matrix, no swizzle);
@@ -30,6 +33,7 @@ using namespace pftc;
 namespace {
 
 constexpr int kThreads = 128;
+constexpr int kFwdMaxThreads = 512;   // forward: up to four warpgroups
 constexpr int kMaxLayers = 8;
 
 struct TcLayer {
@@ -44,6 +48,7 @@ struct TcArgs {
   uint32_t wq_bytes;
   const float* w_out;  // [3][H] float32 output layer
   int n_hidden, hidden, in_freqs, prec, kstep;  // kstep = 16 (16-bit) or 32 (fp8)
+  int n_groups;        // forward: warpgroups (tiles in flight) per CTA
   uint32_t a_off, a_bytes, wout_off, bar_off, smem_bytes;
   float psi;
   TcLayer L[kMaxLayers];
@@ -146,7 +151,7 @@ __device__ __forceinline__ void encode_query(uint8_t* tile, uint32_t kp, int r, 
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(kThreads, 1) k_tc_forward(TcArgs A, const float* __restrict__ q, int64_t B_max,
+__global__ void __launch_bounds__(kFwdMaxThreads, 1) k_tc_forward(TcArgs A, const float* __restrict__ q, int64_t B_max,
                                                             const uint32_t* __restrict__ B_dev, float* __restrict__ out,
                                                             const uint32_t* __restrict__ slot_idx,
                                                             const float* __restrict__ slot_alb,
@@ -156,25 +161,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_forward(TcArgs A, const floa
   constexpr uint32_t AB_TYPE = (PREC == PF_PREC_BF16) ? 1u : 0u;   // f16 = 0, bf16 = 1, e4m3 = 0
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5;
-  uint8_t* a_tile = smem + A.a_off;
+  const int wg = tid >> 7, ltid = tid & 127;     // warpgroup; its thread = row of its tile
+  const int NG = A.n_groups;
+  uint8_t* a_tile = smem + A.a_off + (uint32_t)wg * A.a_bytes;
   float* w_out = (float*)(smem + A.wout_off);
-  uint64_t* bars = (uint64_t*)(smem + A.bar_off);
-  uint32_t* tmem_slot = (uint32_t*)(smem + A.bar_off + 16);
-  int* abort_flag = (int*)(smem + A.bar_off + 20);
-  const uint32_t bar_w = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]);
+  uint64_t* bars = (uint64_t*)(smem + A.bar_off);          // [0] weights, [1 + g] MMAs of group g
+  uint32_t* tmem_slot = (uint32_t*)(smem + A.bar_off + 48);
+  int* abort_flag = (int*)(smem + A.bar_off + 52);
+  const uint32_t bar_w = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1 + wg]);
   const int H = A.hidden;
+  const uint32_t tmem_cols = (uint32_t)(NG * H);        // 128, 256 or 512
 
   if (tid == 0) {
     mbar_init(bar_w, 1);
-    mbar_init(bar_mma, 1);
+    for (int g = 0; g < NG; ++g) mbar_init(smem_u32(&bars[1 + g]), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int i = tid; i < 3 * H; i += kThreads) w_out[i] = A.w_out[i];
-  if (warp == 0) tmem_alloc(tmem_slot, 128u);
+  for (int i = tid; i < 3 * H; i += blockDim.x) w_out[i] = A.w_out[i];
+  if (warp == 0) tmem_alloc(tmem_slot, tmem_cols);
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
+  const uint32_t tmem = *tmem_slot + (uint32_t)(wg * H);   // this group's accumulator columns
   // weights: one bulk copy (the packed block is contiguous and 16-byte sized)
   if (tid == 0) {
     mbar_expect_tx(bar_w, A.wq_bytes);
@@ -187,12 +195,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_forward(TcArgs A, const floa
   const int64_t B = B_dev ? (int64_t)*B_dev : B_max;
   const int64_t n_tiles = (B + kTileM - 1) / kTileM;
   uint32_t mma_phase = 0;
-  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
   const int F = A.in_freqs;
   const uint32_t kp0 = A.L[0].kp;
 
-  for (int64_t tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x) {
-    const int64_t row = tile * kTileM + tid;
+  for (int64_t tile = (int64_t)blockIdx.x * NG + wg; tile < n_tiles && !*abort_flag;
+       tile += (int64_t)gridDim.x * NG) {
+    const int64_t row = tile * kTileM + ltid;
     const bool valid = row < B;
     // ---- encoding of this thread's query into the A tile (K = kp0)
     {
@@ -200,16 +209,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_forward(TcArgs A, const floa
 #pragma unroll
       for (int d = 0; d < 6; ++d) qv[d] = valid ? __ldg(q + 6 * row + d) : 0.f;
       const float s = FP8 ? A.L[0].inv_s_in : 1.f;   // input scale of layer 0 (fp8)
-      encode_query<PREC>(a_tile, kp0, tid, qv, F, s);
+      encode_query<PREC>(a_tile, kp0, ltid, qv, F, s);
     }
     float y0 = 0.f, y1 = 0.f, y2 = 0.f;
     for (int l = 0; l < A.n_hidden; ++l) {
       const TcLayer Ly = A.L[l];
       fence_proxy_async();
       tc_fence_before();
-      __syncthreads();
+      named_barrier(1 + wg, 128);
       tc_fence_after();
-      if (tid == 0) {
+      if (ltid == 0) {
         const uint32_t a0 = smem_u32(a_tile), b0 = smem_u32(smem + Ly.w_off);
         const uint32_t sbo = (Ly.kp * EB / 16) * 128;
         const uint32_t id = idesc(AB_TYPE, (uint32_t)H);
@@ -255,7 +264,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_forward(TcArgs A, const floa
             y2 = fmaf(v[i + 2], w2.z, y2); y2 = fmaf(v[i + 3], w2.w, y2);
           }
         } else {
-          store16<PREC>(a_tile, kp_next, tid, c0, v);
+          store16<PREC>(a_tile, kp_next, ltid, c0, v);
         }
       }
     }
@@ -275,7 +284,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_forward(TcArgs A, const floa
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, 128u);
+  if (warp == 0) tmem_dealloc(*tmem_slot, tmem_cols);
 }
 
 // ---------------------------------------------------------------- training step
@@ -686,11 +695,14 @@ bool plan(const pf_field* f, TcArgs* A) {
   A->wq_bytes = off;
   A->a_off = (off + 1023) / 1024 * 1024;
   A->a_bytes = kTileM * kmax * eb;
-  A->wout_off = A->a_off + A->a_bytes;
-  A->bar_off = A->wout_off + 3 * H * 4;
-  A->bar_off = (A->bar_off + 15) / 16 * 16;
-  A->smem_bytes = A->bar_off + 64;
-  return A->smem_bytes <= 227 * 1024;
+  // as many groups (tiles in flight) as TMEM (512 columns) and shared memory allow
+  for (A->n_groups = 4; A->n_groups >= 1; A->n_groups /= 2) {
+    A->wout_off = A->a_off + (uint32_t)A->n_groups * A->a_bytes;
+    A->bar_off = (A->wout_off + 3 * H * 4 + 15) / 16 * 16;
+    A->smem_bytes = A->bar_off + 64;
+    if (A->n_groups * H <= 512 && A->smem_bytes <= 227 * 1024) break;
+  }
+  return A->n_groups >= 1;
 }
 
 }  // namespace
@@ -708,12 +720,11 @@ pf_status pf_tc_forward(pf_ctx* ctx, const pf_field* f, const float* q, int64_t 
   A.wq = (const uint8_t*)f->wq;
   A.w_out = f->w + f->layer_off[f->n_layers - 1];
   int64_t tiles = (B_max + kTileM - 1) / kTileM;
-  int per_sm = A.smem_bytes <= 113 * 1024 ? 2 : 1;
-  int grid = (int)std::min<int64_t>(tiles, (int64_t)ctx->num_sms * per_sm);
+  int grid = (int)std::min<int64_t>((tiles + A.n_groups - 1) / A.n_groups, (int64_t)ctx->num_sms);
   auto launch = [&](auto kern) -> pf_status {
     PF_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)A.smem_bytes));
-    kern<<<grid, kThreads, A.smem_bytes, ctx->stream>>>(A, q, B_max, B_dev, out, slot_idx, slot_alb, slot_li,
-                                                         ctx->err_dev);
+    kern<<<grid, kThreads * A.n_groups, A.smem_bytes, ctx->stream>>>(A, q, B_max, B_dev, out, slot_idx, slot_alb,
+                                                                      slot_li, ctx->err_dev);
     PF_CUDA(ctx, cudaGetLastError());
     return PF_OK;
   };
