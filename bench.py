@@ -177,6 +177,9 @@ def main():
     ap.add_argument("--rmse-height", type=int, default=270)
     ap.add_argument("--ref-spp", type=int, default=4096)
     ap.add_argument("--brick", type=int, default=BRICK, help="majorant brick edge in voxels (power of two)")
+    ap.add_argument("--training-only", action="store_true",
+                    help="run only the field-training workload and print its JSON (profiling)")
+    ap.add_argument("--training-steps", type=int, default=2000)
     ap.add_argument("--brick-primary", type=int, default=BRICK_PRIMARY,
                     help="brick edge of the camera rays' pooled majorant grid (multiple of --brick)")
     args = ap.parse_args()
@@ -205,6 +208,12 @@ def main():
     from paper_2304_07338_b300 import api, build, inputs as I
     build.build()
     ctx = api.Context(local)
+    if args.training_only:
+        if rank == 0:
+            print(json.dumps({"training_workload": training_workload(ctx, seed, args.training_steps)}), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return
     vol_t, tf_t, lights, cams = setup_scene(dev)
     vol = api.Volume(vol_t, 20.0, 0.9, tf_t, brick=args.brick, brick_primary=args.brick_primary)
     vol.s.majorant = vol.majorant(ctx)
@@ -434,7 +443,7 @@ def equal_rmse(ctx, vol, lights, frame, field, seed, args, fps_neural):
     return out
 
 
-def training_workload(ctx, seed):
+def training_workload(ctx, seed, steps=2000):
     """Field-training workload: data-source caches (128^3 fBm, 2 point
     lights, G = {-0.5, 0, 0.5}, 2^20 photons per light per g, 64^3 caches),
     4x64 bf16 field, 2^18 queries per step, 2000 steps, lr 1e-2 (tcgen05
@@ -452,10 +461,10 @@ def training_workload(ctx, seed):
     fld2 = api.Field(ctx, 12, 64, 4, "bf16", 5.0, seed=seed + 21)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    loss = fld2.train(cache, steps=2000, batch=1 << 18, lr=1e-2, seed=seed + 22)
+    loss = fld2.train(cache, steps=steps, batch=1 << 18, lr=1e-2, seed=seed + 22)
     dt = time.perf_counter() - t0
-    flop = 3 * 2 * (144 * 64 + 3 * 64 * 64 + 3 * 64) * (1 << 18) * 2000
-    return {"steps_per_s": 2000 / dt, "train_s": dt, "loss_first": float(loss[:5].mean()),
+    flop = 3 * 2 * (144 * 64 + 3 * 64 * 64 + 3 * 64) * (1 << 18) * steps
+    return {"steps_per_s": steps / dt, "train_s": dt, "loss_first": float(loss[:5].mean()),
             "loss_last": float(loss[-20:].mean()), "photon_cache_s": t_cache, "photons_per_s": 6 * (1 << 20) / t_cache,
             "records": int(cache.n_records), "model_tflops": flop / dt / 1e12}
 
