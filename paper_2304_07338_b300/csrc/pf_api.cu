@@ -75,6 +75,11 @@ extern "C" pf_status pf_destroy(pf_ctx* c) {
   for (int i = 0; i < WS_COUNT; ++i) cudaFree(c->ws[i]);
   for (auto& m : c->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
   for (auto e : c->event_pool) cudaEventDestroy(e);
+  if (c->aux) {
+    cudaStreamSynchronize(c->aux);
+    for (auto e : c->aux_ev) if (e) cudaEventDestroy(e);
+    cudaStreamDestroy(c->aux);
+  }
   cudaFree(c->err_dev);
   cudaFree(c->dbl_dev);
   delete c;

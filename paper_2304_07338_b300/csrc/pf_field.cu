@@ -448,9 +448,10 @@ extern "C" pf_status pf_field_forward(pf_ctx* ctx, const pf_field* f, const floa
 pf_status pf_field_backward_impl(pf_ctx* ctx, const pf_field* f, const float* q, const float* dy, const float* targets,
                                  int64_t B, float* dw, float* loss) {
   if (f->desc.prec == PF_PREC_FP8) return pf_fail(ctx, PF_ERR_UNSUPPORTED, "fp8 fields are inference-only");
+  // the tensor-core backward writes every element of dw
+  if (B > 0 && pf_tc_backward_available(f) == PF_OK) return pf_tc_backward(ctx, f, q, dy, targets, B, dw, loss);
   PF_CUDA(ctx, cudaMemsetAsync(dw, 0, f->n_params * sizeof(float), ctx->stream));
   if (B == 0) return PF_OK;
-  if (pf_tc_backward_available(f) == PF_OK) return pf_tc_backward(ctx, f, q, dy, targets, B, dw, loss);
   return pf_simt_backward(ctx, f, q, dy, targets, B, dw, loss);
 }
 
@@ -639,22 +640,49 @@ extern "C" pf_status pf_train_field(pf_ctx* ctx, const pf_cache* c, const pf_tra
   if (f->desc.prec == PF_PREC_FP8) return pf_fail(ctx, PF_ERR_UNSUPPORTED, "fp8 fields are inference-only; train bf16/fp16");
   int64_t B = d->batch;
   float *q, *y, *g, *loss;
-  PF_TRY(pf_scratch(ctx, WS_QUERY, B * 6 * sizeof(float), (void**)&q));
-  PF_TRY(pf_scratch(ctx, WS_TARGET, B * 3 * sizeof(float), (void**)&y));
+  // two batch buffers: the batch of step s + 1 (queries and targets, which do
+  // not depend on the weights) is drawn on a second stream while step s
+  // trains on the context's stream
+  PF_TRY(pf_scratch(ctx, WS_QUERY, 2 * B * 6 * sizeof(float), (void**)&q));
+  PF_TRY(pf_scratch(ctx, WS_TARGET, 2 * B * 3 * sizeof(float), (void**)&y));
   PF_TRY(pf_scratch(ctx, WS_GRAD, f->n_params * sizeof(float), (void**)&g));
   PF_TRY(pf_scratch(ctx, WS_LOSS, (size_t)std::max(d->steps, 1) * sizeof(float), (void**)&loss));
   PF_CUDA(ctx, cudaMemsetAsync(loss, 0, (size_t)std::max(d->steps, 1) * sizeof(float), ctx->stream));
+  if (!ctx->aux) {
+    PF_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
+    for (auto& e : ctx->aux_ev) PF_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  cudaEvent_t* ready = ctx->aux_ev;          // [b]: batch buffer b written
+  cudaEvent_t* consumed = ctx->aux_ev + 2;   // [b]: last training step reading buffer b done
+  cudaEvent_t fork = ctx->aux_ev[4];
+  float* qb[2] = {q, q + 6 * B};
+  float* yb[2] = {y, y + 3 * B};
   CacheView C = cview(c);
   int s0 = (int)std::ceil((double)d->decay_start_frac * d->steps);
   StageTimer tm(ctx, PF_STAGE_TRAIN);
-  for (int s = 0; s < d->steps; ++s) {
-    k_batch<<<(unsigned)((B + 255) / 256), 256, 0, ctx->stream>>>(C, B, s, d->seed, f->desc.psi, q, y);
+  auto draw = [&](int s) -> pf_status {      // batch of step s on the second stream
+    k_batch<<<(unsigned)((B + 255) / 256), 256, 0, ctx->aux>>>(C, B, s, d->seed, f->desc.psi, qb[s & 1], yb[s & 1]);
     PF_CUDA(ctx, cudaGetLastError());
-    PF_TRY(pf_field_backward_impl(ctx, f, q, nullptr, y, B, g, loss + s));
+    PF_CUDA(ctx, cudaEventRecord(ready[s & 1], ctx->aux));
+    return PF_OK;
+  };
+  PF_CUDA(ctx, cudaEventRecord(fork, ctx->stream));     // the caches were built on the context's stream
+  PF_CUDA(ctx, cudaStreamWaitEvent(ctx->aux, fork, 0));
+  if (d->steps > 0) PF_TRY(draw(0));
+  for (int s = 0; s < d->steps; ++s) {
+    if (s + 1 < d->steps) {
+      if (s >= 1) PF_CUDA(ctx, cudaStreamWaitEvent(ctx->aux, consumed[(s + 1) & 1], 0));  // step s - 1's buffer
+      PF_TRY(draw(s + 1));
+    }
+    PF_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ready[s & 1], 0));
+    PF_TRY(pf_field_backward_impl(ctx, f, qb[s & 1], nullptr, yb[s & 1], B, g, loss + s));
+    PF_CUDA(ctx, cudaEventRecord(consumed[s & 1], ctx->stream));
     int k = s < s0 ? 0 : (s - s0) / d->decay_every + 1;
     float lr = (float)((double)d->lr * std::pow((double)d->decay, k));
     PF_TRY(pf_adam_impl(ctx, f, g, lr, d->beta1, d->beta2, d->eps));
   }
+  PF_CUDA(ctx, cudaEventRecord(fork, ctx->aux));        // join: nothing of the second stream outlives the call
+  PF_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, fork, 0));
   if (loss_host && d->steps > 0)
     PF_CUDA(ctx, cudaMemcpyAsync(loss_host, loss, d->steps * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
   PF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));

@@ -28,6 +28,8 @@ struct pf_ctx {
   struct Mark { int stage; cudaEvent_t a, b; };
   std::vector<Mark> marks;                // recorded (stage, start, end) pairs
   std::vector<cudaEvent_t> event_pool;
+  cudaStream_t aux = nullptr;             // second stream (training-batch prefetch), created on first use
+  cudaEvent_t aux_ev[5] = {};             // its events: batch ready x2, batch consumed x2, fork
   void* ws[WS_COUNT] = {};
   size_t ws_size[WS_COUNT] = {};
   std::string last_error;

@@ -639,20 +639,36 @@ __global__ void k_reduce_partials(const float* __restrict__ partial, int n_parts
 // Hidden layer l packed K-major in 8 x 16-byte core matrices:
 //   byte(n, k) = ((n/8) * (kp*eb/16) + (k*eb)/16) * 128 + (n%8) * 16 + (k*eb)%16
 // values = operand rounding of W (fp8: code of W / s_w), zero for k >= fan_in.
-__global__ void k_pack(const float* __restrict__ w, int64_t w_off, int n_out, int fan_in, int kp, int prec, float inv_s,
-                       uint8_t* __restrict__ dst) {
-  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int64_t)n_out * kp) return;
-  int n = (int)(e / kp), k = (int)(e % kp);
-  float x = k < fan_in ? w[w_off + (int64_t)n * fan_in + k] : 0.f;
-  int eb = prec == PF_PREC_FP8 ? 1 : 2;
-  uint32_t off = (uint32_t)((n >> 3) * (kp * eb / 16) + (k * eb) / 16) * 128 + (uint32_t)(n & 7) * 16 + (uint32_t)((k * eb) % 16);
-  if (prec == PF_PREC_FP8) dst[off] = pff::e4m3_code(x * inv_s);
-  else if (prec == PF_PREC_BF16) *(__nv_bfloat16*)(dst + off) = __float2bfloat16_rn(x);
-  else *(__half*)(dst + off) = __float2half_rn(x);
-}
-
 struct Bounds { int64_t b[10]; float s_w[8]; int n; };
+
+// All hidden layers packed in one launch (layout above): element e of the
+// packed block belongs to layer l with first[l] <= e < first[l + 1] (H x kp_l elements
+// each, in the order of k_pack).
+struct PackAll {
+  int64_t first[kMaxLayers + 1];
+  int64_t w_off[kMaxLayers];
+  uint32_t dst_off[kMaxLayers];
+  int kp[kMaxLayers], fan_in[kMaxLayers];
+  float inv_s[kMaxLayers];
+  int n, prec;
+};
+__global__ void k_pack_all(const float* __restrict__ w, PackAll P, uint8_t* __restrict__ dst) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= P.first[P.n]) return;
+  int l = 0;
+  while (l + 1 < P.n && e >= P.first[l + 1]) ++l;
+  const int64_t le = e - P.first[l];
+  const int kp = P.kp[l];
+  const int n = (int)(le / kp), k = (int)(le % kp);
+  const float x = k < P.fan_in[l] ? w[P.w_off[l] + (int64_t)n * P.fan_in[l] + k] : 0.f;
+  const int eb = P.prec == PF_PREC_FP8 ? 1 : 2;
+  uint8_t* d = dst + P.dst_off[l];
+  const uint32_t off = (uint32_t)((n >> 3) * (kp * eb / 16) + (k * eb) / 16) * 128 + (uint32_t)(n & 7) * 16 +
+                       (uint32_t)((k * eb) % 16);
+  if (P.prec == PF_PREC_FP8) d[off] = pff::e4m3_code(x * P.inv_s[l]);
+  else if (P.prec == PF_PREC_BF16) *(__nv_bfloat16*)(d + off) = __float2bfloat16_rn(x);
+  else *(__half*)(d + off) = __float2half_rn(x);
+}
 
 // Hidden-layer weights rounded to the field precision (fp8: per-layer scale),
 // as float values, for the SIMT path.
@@ -801,32 +817,47 @@ pf_status pf_tc_backward(pf_ctx* ctx, const pf_field* f, const float* q, const f
 
 pf_status pf_field_pack(pf_ctx* ctx, pf_field* f) {
   if (f->desc.prec == PF_PREC_F32) return PF_OK;
-  if (!f->wr) {
-    if (cudaMalloc(&f->wr, f->n_params * sizeof(float)) != cudaSuccess) return pf_fail(ctx, PF_ERR_OOM, "field pack");
-    PF_CUDA(ctx, cudaMemsetAsync(f->wr, 0, f->n_params * sizeof(float), ctx->stream));
-  }
-  Bounds B;
-  B.n = f->n_layers - 1;
-  for (int l = 0; l <= B.n; ++l) B.b[l] = f->layer_off[l];
-  for (int l = 0; l < 8; ++l) B.s_w[l] = f->scales_host[16 + l] > 0.f ? f->scales_host[16 + l] : 1.f;
-  int64_t n = B.b[B.n];
-  k_round_weights<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(f->w, f->wr, B, f->desc.prec);
-  PF_CUDA(ctx, cudaGetLastError());
   TcArgs A;
-  if (!plan(f, &A)) return PF_OK;
+  const bool tc_fwd = plan(f, &A);
+  TrArgs T;
+  const bool tc_bwd = f->desc.prec != PF_PREC_FP8 && plan_train(f, &T);
+  // the float copy rounded to the field precision serves only the SIMT
+  // kernels: needed unless every pass of this field runs on tcgen05
+  const bool need_wr = !tc_fwd || (f->desc.prec != PF_PREC_FP8 && !tc_bwd);
+  if (need_wr) {
+    if (!f->wr) {
+      if (cudaMalloc(&f->wr, f->n_params * sizeof(float)) != cudaSuccess) return pf_fail(ctx, PF_ERR_OOM, "field pack");
+      PF_CUDA(ctx, cudaMemsetAsync(f->wr, 0, f->n_params * sizeof(float), ctx->stream));
+    }
+    Bounds B;
+    B.n = f->n_layers - 1;
+    for (int l = 0; l <= B.n; ++l) B.b[l] = f->layer_off[l];
+    for (int l = 0; l < 8; ++l) B.s_w[l] = f->scales_host[16 + l] > 0.f ? f->scales_host[16 + l] : 1.f;
+    int64_t n = B.b[B.n];
+    k_round_weights<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(f->w, f->wr, B, f->desc.prec);
+    PF_CUDA(ctx, cudaGetLastError());
+  }
+  if (!tc_fwd) return PF_OK;
   if (!f->wq || f->wq_bytes < A.wq_bytes) {
     cudaFree(f->wq);
     f->wq = nullptr;
     if (cudaMalloc(&f->wq, A.wq_bytes) != cudaSuccess) return pf_fail(ctx, PF_ERR_OOM, "field pack");
     f->wq_bytes = A.wq_bytes;
   }
+  PackAll P;
+  P.n = A.n_hidden;
+  P.prec = f->desc.prec;
+  P.first[0] = 0;
   for (int l = 0; l < A.n_hidden; ++l) {
-    int64_t ne = (int64_t)A.hidden * A.L[l].kp;
-    float s_w = f->desc.prec == PF_PREC_FP8 && f->scales_host[16 + l] > 0.f ? f->scales_host[16 + l] : 1.f;
-    k_pack<<<(unsigned)((ne + 255) / 256), 256, 0, ctx->stream>>>(f->w, f->layer_off[l], A.hidden, f->fan_in[l],
-                                                                  (int)A.L[l].kp, f->desc.prec, 1.f / s_w,
-                                                                  (uint8_t*)f->wq + A.L[l].w_off);
+    P.first[l + 1] = P.first[l] + (int64_t)A.hidden * A.L[l].kp;
+    P.w_off[l] = f->layer_off[l];
+    P.dst_off[l] = A.L[l].w_off;
+    P.kp[l] = (int)A.L[l].kp;
+    P.fan_in[l] = f->fan_in[l];
+    const float s_w = f->desc.prec == PF_PREC_FP8 && f->scales_host[16 + l] > 0.f ? f->scales_host[16 + l] : 1.f;
+    P.inv_s[l] = 1.f / s_w;
   }
+  k_pack_all<<<(unsigned)((P.first[P.n] + 255) / 256), 256, 0, ctx->stream>>>(f->w, P, (uint8_t*)f->wq);
   PF_CUDA(ctx, cudaGetLastError());
   return PF_OK;
 }
