@@ -137,9 +137,10 @@ def setup_scene(device):
 
 
 def cpu_baseline(vol_host, tf, lights, cams, seed, rows=2, weights=None, desc=None, scales=None, brick=8,
-                 brick_primary=0):
-    """The oracle (plain C++/numpy) on a bounded sample: `rows` full image rows
-    of one frame at full spp, scaled to a frame."""
+                 brick_primary=0, cols=None):
+    """The oracle (plain C++/numpy) on a bounded sample: `rows` image rows of
+    one frame (all columns, or the columns [x0, x1)) at full spp, scaled to
+    a frame."""
     import oracle
     from paper_2304_07338_b300 import inputs as I
     v = I.Volume(vol_host, 20.0, 0.9, tf, brick=brick, brick_primary=brick_primary)
@@ -147,13 +148,15 @@ def cpu_baseline(vol_host, tf, lights, cams, seed, rows=2, weights=None, desc=No
     g = I.frame_g(seed, 0)
     y0 = H_ // 2
     t = time.perf_counter()
+    x0, x1 = cols if cols is not None else (0, W_)
     oracle.render_neural(v, lights, g, cam, SPP, 0.0, seed, weights=weights, desc=desc, scales=scales, fp32=True,
-                         rows=(y0, y0 + rows))
+                         rows=(y0, y0 + rows), cols=(x0, x1))
     dt = time.perf_counter() - t
-    frame_s = dt * H_ / rows
+    frame_s = dt * (H_ / rows) * (W_ / (x1 - x0))
     return {"value": 1.0 / frame_s, "unit": "frames/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "%d of %d rows of frame 0 (%dx%d, %d spp, 8 lights, fp8 field emulated in FP64), "
-                      "scaled to a full frame; %.2f s measured" % (rows, H_, W_, H_, SPP, dt)}
+            "sample": "%d pixels (%d row(s) x columns %d-%d) of frame 0 (%dx%d, %d spp, 8 lights, fp8 field "
+                      "emulated in FP64), scaled to a full frame; %.2f s measured"
+                      % (rows * (x1 - x0), rows, x0, x1, W_, H_, SPP, dt)}
 
 
 def main():
@@ -487,9 +490,9 @@ def field_scales(field):
 
 
 def run_reference(args, dev, seed):
-    """The oracle as the reference arm: each step renders a bounded sample (one
-    image row at full spp) of the same workload on the host cores; frames/s
-    extrapolated from the per-row time."""
+    """The oracle as the reference arm: each step renders a bounded sample (240
+    pixels of the middle row at full spp) of the same workload on the host
+    cores; frames/s extrapolated from the per-pixel time."""
     import torch
     vol_t, tf_t, lights, cams = setup_scene(dev)
     vol_h, tf_h = vol_t.cpu().numpy(), tf_t.cpu().numpy()
@@ -503,12 +506,13 @@ def run_reference(args, dev, seed):
     times = []
     for i in range(args.warmup + args.steps):
         r = cpu_baseline(vol_h, tf_h, lights, cams, seed, rows=1, brick=args.brick,
-                         brick_primary=args.brick_primary, **fld)
+                         brick_primary=args.brick_primary, cols=(W_ // 2 - 120, W_ // 2 + 120), **fld)
         if i >= args.warmup:
             times.append(1.0 / r["value"])
     fps = 1.0 / float(np.mean(times))
     cb = {"value": fps, "unit": "frames/s", "cores": os.cpu_count(), "kind": "oracle",
-          "sample": "1 of %d rows per step at full spp (4x128 fp8 field, Kaiming init), scaled to a frame" % H_}
+          "sample": "240 pixels of the middle row per step at full spp (4x128 fp8 field, Kaiming init), scaled "
+                    "to a frame"}
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": 1,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / fps,
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64/f32 oracle",

@@ -55,7 +55,7 @@ def _declare(L):
                                     P, P, P, P, P]
     L.orc_camera_samples.argtypes = [i32, i32, i32, i32, P, f64, f64, P, i32, i32, i32,
                                      P, P, P, i32, f64, P, P, P, f64, i32, i32,
-                                     i32, f64, u64, i32, i32, i32, P, P, P, P, P]
+                                     i32, f64, u64, i32, i32, i32, i32, i32, P, P, P, P, P]
     L.orc_path_trace.argtypes = [i32, i32, i32, i32, P, f64, f64, P, i32, i32,
                                  P, P, P, i32, f64, P, P, P, f64, i32, i32,
                                  i32, i32, u64, i32, i32, i32, i32, P, i64, P]
@@ -316,27 +316,30 @@ def estimate_targets(q: np.ndarray, g_set, cache: Dict, csig: np.ndarray) -> np.
 
 # ------------------------------------------------------------------ rendering (Algorithm 2)
 def camera_samples(vol, lights, g: float, cam, spp: int, step_vox: float, seed: int,
-                   fp32: bool = False, rows=None) -> Dict:
-    """RayGeneration + VolumeSampling + DirectIllumination per camera sample."""
+                   fp32: bool = False, rows=None, cols=None) -> Dict:
+    """RayGeneration + VolumeSampling + DirectIllumination per camera sample
+    (pixels in rows [y0, y1) and columns [x0, x1))."""
     v, L, cm = _Vol(vol), _Lights(lights), _Cam(cam)
     y0, y1 = rows if rows is not None else (0, cam.height)
-    n = (y1 - y0) * cam.width * spp
+    x0, x1 = cols if cols is not None else (0, cam.width)
+    n = (y1 - y0) * (x1 - x0) * spp
     valid = np.zeros(n, np.uint8)
     x, wo, alb, Ld = (np.zeros((n, 3)) for _ in range(4))
     lib().orc_camera_samples(*v.args, v.ss, v.alb, *v.tfargs, v.brick, v.brick_primary, *L.args, float(g), *cm.args, spp,
-                             float(step_vox), seed, int(fp32), y0, y1,
+                             float(step_vox), seed, int(fp32), y0, y1, x0, x1,
                              _p(valid), _p(x), _p(wo), _p(alb), _p(Ld))
-    shp = (y1 - y0, cam.width, spp)
+    shp = (y1 - y0, x1 - x0, spp)
     return dict(valid=valid.reshape(shp).astype(bool), x=x.reshape(shp + (3,)), wo=wo.reshape(shp + (3,)),
                 albedo=alb.reshape(shp + (3,)), Ld=Ld.reshape(shp + (3,)))
 
 
 def render_neural(vol, lights, g: float, cam, spp: int, step_vox: float, seed: int,
-                  weights=None, desc=None, scales=None, fp32: bool = False, rows=None, return_parts: bool = False):
+                  weights=None, desc=None, scales=None, fp32: bool = False, rows=None, cols=None,
+                  return_parts: bool = False):
     """Neural path tracing (Algorithm 2): camera samples, field prediction and
     exponential decode at the valid samples, then Compose
     L = 1/spp sum_k albedo_k (L_d,k + L_i,k) with unit MIS weights."""
-    cs = camera_samples(vol, lights, g, cam, spp, step_vox, seed, fp32, rows)
+    cs = camera_samples(vol, lights, g, cam, spp, step_vox, seed, fp32, rows, cols)
     Li = np.zeros_like(cs["Ld"])
     if weights is not None:
         vm = cs["valid"]

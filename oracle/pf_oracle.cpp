@@ -919,7 +919,8 @@ void orc_trace_photons(int nx, int ny, int nz, int dtype, const void* data, doub
 }
 
 // Camera samples of the neural renderer (Algorithm 2: RayGeneration,
-// VolumeSampling, DirectIllumination).  Arrays are [H][W][spp].  The free
+// VolumeSampling, DirectIllumination) of the pixels in rows [y_begin, y_end)
+// and columns [x_begin, x_end).  Arrays are [rows][columns][spp].  The free
 // flight of the camera rays uses the brick grid pooled to bricks of edge
 // brick_primary (0: brick); shadow rays use the brick grid.
 void orc_camera_samples(int nx, int ny, int nz, int dtype, const void* data, double ss, double alb,
@@ -927,8 +928,10 @@ void orc_camera_samples(int nx, int ny, int nz, int dtype, const void* data, dou
                         const int* lkind, const double* lv, const double* lrgb, int n_lights, double g,
                         const double* eye, const double* at, const double* up, double fovy, int W, int H,
                         int spp, double step_vox, uint64_t seed, int fp32, int y_begin, int y_end,
+                        int x_begin, int x_end,
                         uint8_t* valid, double* x, double* wo, double* albedo, double* Ld) {
     Volume V = mkvol(nx, ny, nz, dtype, data, ss, alb, tf, tf_n);
+    const int NW = x_end - x_begin;
     std::vector<Light> L = mklights(lkind, lv, lrgb, n_lights);
     CamFrame cf = cam_frame(eye, at, up, fovy, W, H);
     Grid<double> G64 = fp32 ? Grid<double>() : build_grid<double>(V, brick);
@@ -938,9 +941,9 @@ void orc_camera_samples(int nx, int ny, int nz, int dtype, const void* data, dou
     Grid<float> P32 = pool_grid(G32, f);
     #pragma omp parallel for schedule(dynamic, 1) collapse(2)
     for (int py = y_begin; py < y_end; ++py)
-        for (int px = 0; px < W; ++px)
+        for (int px = x_begin; px < x_end; ++px)
             for (int k = 0; k < spp; ++k) {
-                size_t idx = (((size_t)(py - y_begin) * W + px) * spp + k);
+                size_t idx = (((size_t)(py - y_begin) * NW + (px - x_begin)) * spp + k);
                 int vld;
                 if (fp32) {
                     V3<float> a, b, c, e;
