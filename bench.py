@@ -35,6 +35,7 @@ METRIC = "1080p frames/sec and field queries/sec vs plain GPU path tracer at equ
 W_, H_, SPP, N_VOX, N_LIGHTS = 1920, 1080, 16, 1024, 8
 BRICK = 32                      # majorant brick edge (voxels) for the 1024^3 volume
 BRICK_PRIMARY = 64              # brick edge of the camera rays' (pooled) majorant grid
+BRICK_SHADOW = 0                # brick edge walked by shadow rays, thinned to BRICK (0: BRICK)
 HIDDEN, N_HIDDEN, FREQS = 128, 4, 12
 VOXEL_BYTES = 2                 # float16
 # DRAM bytes (read + write) per density lookup of k_nee, from one ncu capture
@@ -137,13 +138,13 @@ def setup_scene(device):
 
 
 def cpu_baseline(vol_host, tf, lights, cams, seed, rows=2, weights=None, desc=None, scales=None, brick=8,
-                 brick_primary=0, cols=None):
+                 brick_primary=0, cols=None, brick_shadow=0):
     """The oracle (plain C++/numpy) on a bounded sample: `rows` image rows of
     one frame (all columns, or the columns [x0, x1)) at full spp, scaled to
     a frame."""
     import oracle
     from paper_2304_07338_b300 import inputs as I
-    v = I.Volume(vol_host, 20.0, 0.9, tf, brick=brick, brick_primary=brick_primary)
+    v = I.Volume(vol_host, 20.0, 0.9, tf, brick=brick, brick_primary=brick_primary, brick_shadow=brick_shadow)
     cam = cams[0]
     g = I.frame_g(seed, 0)
     y0 = H_ // 2
@@ -183,6 +184,8 @@ def main():
     ap.add_argument("--training-only", action="store_true",
                     help="run only the field-training workload and print its JSON (profiling)")
     ap.add_argument("--training-steps", type=int, default=2000)
+    ap.add_argument("--brick-shadow", type=int, default=BRICK_SHADOW,
+                    help="brick edge walked by shadow rays, thinned to --brick (0: --brick)")
     ap.add_argument("--brick-primary", type=int, default=BRICK_PRIMARY,
                     help="brick edge of the camera rays' pooled majorant grid (multiple of --brick)")
     args = ap.parse_args()
@@ -218,7 +221,8 @@ def main():
             dist.destroy_process_group()
         return
     vol_t, tf_t, lights, cams = setup_scene(dev)
-    vol = api.Volume(vol_t, 20.0, 0.9, tf_t, brick=args.brick, brick_primary=args.brick_primary)
+    vol = api.Volume(vol_t, 20.0, 0.9, tf_t, brick=args.brick, brick_primary=args.brick_primary,
+                     brick_shadow=args.brick_shadow)
     vol.s.majorant = vol.majorant(ctx)
     vol.attach_brick_majorants(ctx)
     setup = {}
@@ -341,7 +345,7 @@ def main():
                                "fp8 4x128 field, delta/ratio tracking" % (N_VOX, W_, H_, SPP),
                    "frames": "60-frame orbit", "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (2 GiB volume)", "majorant_brick": args.brick,
-                   "majorant_brick_primary": args.brick_primary},
+                   "majorant_brick_primary": args.brick_primary, "majorant_brick_shadow": args.brick_shadow},
         "queries_per_s": qpf * fps,
         "queries_per_frame": qpf,
         "lookups_per_frame": {"camera": fetches_per_frame - nee_fetches_per_frame, "nee": nee_fetches_per_frame},
@@ -361,7 +365,8 @@ def main():
         try:
             line["cpu_baseline"] = cpu_baseline(vol_t.cpu().numpy(), tf_t.cpu().numpy(), lights, cams, seed,
                                                 rows=args.cpu_rows, brick=args.brick,
-                                                brick_primary=args.brick_primary, **oracle_field(field))
+                                                brick_primary=args.brick_primary, brick_shadow=args.brick_shadow,
+                                                **oracle_field(field))
         except Exception as e:  # reported, not fatal
             line["cpu_baseline"] = {"error": repr(e)[:200]}
     if rank == 0:
@@ -506,7 +511,8 @@ def run_reference(args, dev, seed):
     times = []
     for i in range(args.warmup + args.steps):
         r = cpu_baseline(vol_h, tf_h, lights, cams, seed, rows=1, brick=args.brick,
-                         brick_primary=args.brick_primary, cols=(W_ // 2 - 120, W_ // 2 + 120), **fld)
+                         brick_primary=args.brick_primary, brick_shadow=args.brick_shadow,
+                         cols=(W_ // 2 - 120, W_ // 2 + 120), **fld)
         if i >= args.warmup:
             times.append(1.0 / r["value"])
     fps = 1.0 / float(np.mean(times))

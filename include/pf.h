@@ -82,6 +82,11 @@ typedef struct {
                                grid is the brick grid max-pooled over groups of bricks (camera
                                rays cross the whole volume and rarely collide, so fewer, looser
                                bricks cost less; shadow rays keep the tight grid) */
+  int brick_shadow;         /* brick edge walked by the neural renderer's shadow rays: 0 = brick,
+                               else a power-of-two multiple of brick; the rays cross that
+                               max-pooled grid and thin its tentative collisions (one more
+                               uniform each) to the brick grid's majorants, so the ratio-tracking
+                               estimate is that of the brick grid at the cost of a coarser walk */
 } pf_volume;
 
 /* Light source.  Directional: v = unit direction towards the light, rgb =

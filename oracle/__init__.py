@@ -48,12 +48,12 @@ def _declare(L):
     L.orc_majorant.restype = f64
     L.orc_free_flight.argtypes = [i32, i32, i32, i32, P, f64, P, i32, i32, P, P, i64, u64, P, P]
     L.orc_brick_majorants.argtypes = [i32, i32, i32, i32, P, f64, P, i32, i32, i32, P]
-    L.orc_ratio_mean.argtypes = [i32, i32, i32, i32, P, f64, P, i32, i32, P, P, f64, i64, u64, P]
+    L.orc_ratio_mean.argtypes = [i32, i32, i32, i32, P, f64, P, i32, i32, i32, P, P, f64, i64, u64, P]
     L.orc_ratio_mean.restype = f64
     L.orc_trace_photons.argtypes = [i32, i32, i32, i32, P, f64, f64, P, i32, i32,
                                     P, P, P, i32, P, i32, u64, i32, i32, u64, i32, i32, u64, u64,
                                     P, P, P, P, P]
-    L.orc_camera_samples.argtypes = [i32, i32, i32, i32, P, f64, f64, P, i32, i32, i32,
+    L.orc_camera_samples.argtypes = [i32, i32, i32, i32, P, f64, f64, P, i32, i32, i32, i32,
                                      P, P, P, i32, f64, P, P, P, f64, i32, i32,
                                      i32, f64, u64, i32, i32, i32, i32, i32, P, P, P, P, P]
     L.orc_path_trace.argtypes = [i32, i32, i32, i32, P, f64, f64, P, i32, i32,
@@ -85,6 +85,7 @@ class _Vol:
         self.tfargs = (_p(self.tf), int(self.tf.shape[0]))
         self.brick = int(getattr(vol, "brick", 8))
         self.brick_primary = int(getattr(vol, "brick_primary", 0))
+        self.brick_shadow = int(getattr(vol, "brick_shadow", 0))
 
 
 class _Lights:
@@ -181,12 +182,14 @@ def brick_majorants(vol, fp32: bool = False) -> np.ndarray:
 
 
 def ratio_mean(vol, o, d, t_end: float, n: int, seed: int):
-    """Mean and variance of n ratio-tracking transmittance estimates."""
+    """Mean and variance of n ratio-tracking transmittance estimates (walking
+    the grid pooled to vol.brick_shadow and thinned to vol.brick, if set)."""
     v = _Vol(vol)
     o = np.ascontiguousarray(o, np.float64)
     d = np.ascontiguousarray(d, np.float64)
     var = np.zeros(1)
-    m = lib().orc_ratio_mean(*v.args, v.ss, *v.tfargs, v.brick, _p(o), _p(d), float(t_end), n, seed, _p(var))
+    m = lib().orc_ratio_mean(*v.args, v.ss, *v.tfargs, v.brick, v.brick_shadow, _p(o), _p(d), float(t_end), n, seed,
+                             _p(var))
     return m, float(var[0])
 
 
@@ -325,7 +328,7 @@ def camera_samples(vol, lights, g: float, cam, spp: int, step_vox: float, seed: 
     n = (y1 - y0) * (x1 - x0) * spp
     valid = np.zeros(n, np.uint8)
     x, wo, alb, Ld = (np.zeros((n, 3)) for _ in range(4))
-    lib().orc_camera_samples(*v.args, v.ss, v.alb, *v.tfargs, v.brick, v.brick_primary, *L.args, float(g), *cm.args, spp,
+    lib().orc_camera_samples(*v.args, v.ss, v.alb, *v.tfargs, v.brick, v.brick_primary, v.brick_shadow, *L.args, float(g), *cm.args, spp,
                              float(step_vox), seed, int(fp32), y0, y1, x0, x1,
                              _p(valid), _p(x), _p(wo), _p(alb), _p(Ld))
     shp = (y1 - y0, x1 - x0, spp)

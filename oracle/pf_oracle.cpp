@@ -492,6 +492,57 @@ template <typename R> R ratio_track(const Volume& V, const Grid<R>& G, V3<R> o, 
     return T;
 }
 
+// Ratio tracking as above whose tentative collisions come from a coarser
+// walk: the rays cross the bricks of Gw (edge f B, each the largest of its
+// f^3 bricks of G) and a tentative collision of that process at x is kept
+// with probability m_G(x) / m_Gw (one more uniform, after the collision's
+// budget), which thins it to a Poisson process of rate m_G: the estimator is
+// ratio tracking with the tight majorant of G, T *= max(0, 1 - sigma_t /
+// m_G(x)) at kept collisions, at the cost of a walk over the coarse bricks.
+// m_G(x) is the majorant of the brick of G holding x, its index clamped into
+// the current brick of Gw.  Gw = G is plain ratio tracking.
+template <typename R> R ratio_track_thinned(const Volume& V, const Grid<R>& G, const Grid<R>& Gw, V3<R> o, V3<R> d,
+                                            R t_end, Rng& rng) {
+    if (Gw.B == G.B) return ratio_track<R>(V, G, o, d, t_end, rng);
+    const int f = Gw.B / G.B;
+    Walk<R> W; W.init(Gw, o, d, (R)0);
+    Uniforms<R> U(rng);
+    R T = (R)1, t = (R)0;
+    R tau = -M<R>::ln((R)1 - U.next());
+    for (long it = 0; it < (1L << 24); ++it) {
+        R m = Gw.at(W.c[0], W.c[1], W.c[2]);
+        R tc = std::min(W.exit_t(), t_end);
+        R seg = tc - t;
+        if (seg < (R)0) seg = (R)0;
+        if (m > (R)0 && tau < m * seg) {
+            t = t + tau / m;
+            R ut = U.next();
+            V3<R> x = along(o, d, t);
+            const R p[3] = {x.x, x.y, x.z};
+            const int n[3] = {G.nx, G.ny, G.nz}, g[3] = {G.gx, G.gy, G.gz};
+            int c[3];
+            for (int a = 0; a < 3; ++a) {
+                R w = (R)G.B / (R)n[a];
+                int ci = (int)std::floor(p[a] / w);
+                int lo = W.c[a] * f, hi = std::min(W.c[a] * f + f, g[a]) - 1;
+                c[a] = std::min(std::max(ci, lo), hi);
+            }
+            R mf = G.at(c[0], c[1], c[2]);
+            if (ut * m < mf) {
+                R fr = (R)1 - sigma_at<R>(V, x) / mf;
+                T = T * std::max((R)0, fr);
+            }
+            tau = -M<R>::ln((R)1 - U.next());
+            continue;
+        }
+        tau = tau - m * seg;
+        t = tc;
+        if (t >= t_end) break;
+        if (!W.step()) break;
+    }
+    return T;
+}
+
 // Direction to light l from x, distance limit and irradiance at x.
 template <typename R> void light_geom(const Light& L, V3<R> x, V3<R>* wl, R* dist, V3<R>* E) {
     if (L.kind == 0) {
@@ -659,8 +710,8 @@ R march_tau(const Volume& V, V3<R> o, V3<R> d, R t0, R t1, R h, R jit) {
 }
 
 template <typename R>
-void camera_sample(const Volume& V, const Grid<R>& G, const Grid<R>& Gp, const Light* lights, int n_lights, R g,
-                   const CamFrame& cf,
+void camera_sample(const Volume& V, const Grid<R>& G, const Grid<R>& Gp, const Grid<R>& Gs, const Light* lights,
+                   int n_lights, R g, const CamFrame& cf,
                    int px, int py, int k, R step_vox, uint64_t seed,
                    int* valid, V3<R>* xo, V3<R>* wo, V3<R>* alb, V3<R>* Ld) {
     Rng rng(seed, 1, (uint64_t)py * (uint64_t)cf.W + (uint64_t)px, (uint32_t)k);
@@ -712,7 +763,7 @@ void camera_sample(const Volume& V, const Grid<R>& G, const Grid<R>& Gp, const L
             T = std::exp(-march_tau<R>(V, x, wl, (R)0, tend, h, jl[l]));
         } else {
             Rng rs(seed, 5, shadow_item((uint64_t)py * (uint64_t)cf.W + (uint64_t)px, 1, l), (uint32_t)k);
-            T = ratio_track<R>(V, G, x, wl, tend, rs);
+            T = ratio_track_thinned<R>(V, G, Gs, x, wl, tend, rs);
         }
         R ph = hg_eval<R>(g, dot(d, wl));
         L = v3(L.x + ph * T * E.x, L.y + ph * T * E.y, L.z + ph * T * E.z);
@@ -848,13 +899,15 @@ void orc_brick_majorants(int nx, int ny, int nz, int dtype, const void* data, do
 
 // Mean ratio-tracking transmittance from o along d over [0, t_end) (n walks).
 double orc_ratio_mean(int nx, int ny, int nz, int dtype, const void* data, double ss, const float* tf, int tf_n, int brick,
-                      const double* o, const double* d, double t_end, int64_t n, uint64_t seed, double* var) {
+                      int brick_shadow, const double* o, const double* d, double t_end, int64_t n, uint64_t seed,
+                      double* var) {
     Volume V = mkvol(nx, ny, nz, dtype, data, ss, 1.0, tf, tf_n);
     Grid<double> G = build_grid<double>(V, brick);
+    Grid<double> Gw = pool_grid(G, brick_shadow > brick ? brick_shadow / brick : 1);
     double s = 0, s2 = 0;
     for (int64_t i = 0; i < n; ++i) {
         Rng r(seed, 2, (uint64_t)i, 0);
-        double T = ratio_track<double>(V, G, v3(o[0], o[1], o[2]), v3(d[0], d[1], d[2]), t_end, r);
+        double T = ratio_track_thinned<double>(V, G, Gw, v3(o[0], o[1], o[2]), v3(d[0], d[1], d[2]), t_end, r);
         s += T; s2 += T * T;
     }
     *var = s2 / n - (s / n) * (s / n);
@@ -922,9 +975,10 @@ void orc_trace_photons(int nx, int ny, int nz, int dtype, const void* data, doub
 // VolumeSampling, DirectIllumination) of the pixels in rows [y_begin, y_end)
 // and columns [x_begin, x_end).  Arrays are [rows][columns][spp].  The free
 // flight of the camera rays uses the brick grid pooled to bricks of edge
-// brick_primary (0: brick); shadow rays use the brick grid.
+// brick_primary (0: brick); shadow rays walk the grid pooled to brick_shadow
+// (0: brick) thinned to the brick grid.
 void orc_camera_samples(int nx, int ny, int nz, int dtype, const void* data, double ss, double alb,
-                        const float* tf, int tf_n, int brick, int brick_primary,
+                        const float* tf, int tf_n, int brick, int brick_primary, int brick_shadow,
                         const int* lkind, const double* lv, const double* lrgb, int n_lights, double g,
                         const double* eye, const double* at, const double* up, double fovy, int W, int H,
                         int spp, double step_vox, uint64_t seed, int fp32, int y_begin, int y_end,
@@ -939,6 +993,9 @@ void orc_camera_samples(int nx, int ny, int nz, int dtype, const void* data, dou
     const int f = brick_primary > brick ? brick_primary / brick : 1;
     Grid<double> P64 = pool_grid(G64, f);
     Grid<float> P32 = pool_grid(G32, f);
+    const int fs = brick_shadow > brick ? brick_shadow / brick : 1;
+    Grid<double> S64 = pool_grid(G64, fs);
+    Grid<float> S32 = pool_grid(G32, fs);
     #pragma omp parallel for schedule(dynamic, 1) collapse(2)
     for (int py = y_begin; py < y_end; ++py)
         for (int px = x_begin; px < x_end; ++px)
@@ -947,14 +1004,14 @@ void orc_camera_samples(int nx, int ny, int nz, int dtype, const void* data, dou
                 int vld;
                 if (fp32) {
                     V3<float> a, b, c, e;
-                    camera_sample<float>(V, G32, P32, L.data(), n_lights, (float)g, cf, px, py, k, (float)step_vox, seed, &vld, &a, &b, &c, &e);
+                    camera_sample<float>(V, G32, P32, S32, L.data(), n_lights, (float)g, cf, px, py, k, (float)step_vox, seed, &vld, &a, &b, &c, &e);
                     x[3 * idx] = a.x; x[3 * idx + 1] = a.y; x[3 * idx + 2] = a.z;
                     wo[3 * idx] = b.x; wo[3 * idx + 1] = b.y; wo[3 * idx + 2] = b.z;
                     albedo[3 * idx] = c.x; albedo[3 * idx + 1] = c.y; albedo[3 * idx + 2] = c.z;
                     Ld[3 * idx] = e.x; Ld[3 * idx + 1] = e.y; Ld[3 * idx + 2] = e.z;
                 } else {
                     V3<double> a, b, c, e;
-                    camera_sample<double>(V, G64, P64, L.data(), n_lights, g, cf, px, py, k, step_vox, seed, &vld, &a, &b, &c, &e);
+                    camera_sample<double>(V, G64, P64, S64, L.data(), n_lights, g, cf, px, py, k, step_vox, seed, &vld, &a, &b, &c, &e);
                     x[3 * idx] = a.x; x[3 * idx + 1] = a.y; x[3 * idx + 2] = a.z;
                     wo[3 * idx] = b.x; wo[3 * idx + 1] = b.y; wo[3 * idx + 2] = b.z;
                     albedo[3 * idx] = c.x; albedo[3 * idx + 1] = c.y; albedo[3 * idx + 2] = c.z;

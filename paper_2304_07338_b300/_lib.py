@@ -21,7 +21,7 @@ class PfVolume(C.Structure):
                 ("data_dev", C.c_void_p), ("sigma_scale", C.c_float), ("albedo", C.c_float),
                 ("tf_lut_dev", C.c_void_p), ("tf_n", C.c_int), ("majorant", C.c_float),
                 ("brick_majorants_dev", C.c_void_p), ("brick", C.c_int),
-                ("brick_primary", C.c_int)]
+                ("brick_primary", C.c_int), ("brick_shadow", C.c_int)]
 
 
 class PfLight(C.Structure):

@@ -83,7 +83,7 @@ class Volume:
     """Device-resident volume + transfer function (pf_volume)."""
 
     def __init__(self, data: torch.Tensor, sigma_scale: float, albedo: float, tf: torch.Tensor,
-                 majorant: float = 0.0, brick: int = 8, brick_primary: int = 0):
+                 majorant: float = 0.0, brick: int = 8, brick_primary: int = 0, brick_shadow: int = 0):
         code = {torch.float32: 0, torch.float16: 1, torch.uint8: 2}[data.dtype]
         if not data.is_cuda or not data.is_contiguous() or data.dim() != 3:
             raise ValueError("volume data must be a contiguous 3-D CUDA tensor (nz, ny, nx)")
@@ -91,7 +91,8 @@ class Volume:
         self.data, self.tf = data, tf
         nz, ny, nx = data.shape
         self.s = PfVolume(nx, ny, nz, code, data.data_ptr(), float(sigma_scale), float(albedo), tf.data_ptr(),
-                          int(tf.shape[0]), float(majorant), None, int(brick), int(brick_primary))
+                          int(tf.shape[0]), float(majorant), None, int(brick), int(brick_primary),
+                          int(brick_shadow))
         self.grid = None
 
     @classmethod
@@ -100,7 +101,7 @@ class Volume:
         data = torch.from_numpy(np.ascontiguousarray(vol.data)).to(device)
         tf = torch.from_numpy(np.ascontiguousarray(vol.tf, np.float32)).to(device)
         return cls(data, vol.sigma_scale, vol.albedo, tf, brick=getattr(vol, "brick", 8),
-                   brick_primary=getattr(vol, "brick_primary", 0))
+                   brick_primary=getattr(vol, "brick_primary", 0), brick_shadow=getattr(vol, "brick_shadow", 0))
 
     def brick_majorants(self, ctx: Context) -> torch.Tensor:
         """Per-8^3-brick majorants (computed on the GPU), shape (gz, gy, gx)."""

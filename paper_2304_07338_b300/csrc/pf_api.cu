@@ -176,6 +176,9 @@ pf_status pf_check_volume(pf_ctx* ctx, const pf_volume* v) {
     if (v->brick_primary != 0 && (v->brick_primary < Bb || v->brick_primary > 1024 ||
                                   (v->brick_primary & (v->brick_primary - 1))))
       return pf_fail(ctx, PF_ERR_INVALID_ARG, "brick_primary must be 0 or a power-of-two multiple of brick, <= 1024");
+    if (v->brick_shadow != 0 && (v->brick_shadow < Bb || v->brick_shadow > 1024 ||
+                                 (v->brick_shadow & (v->brick_shadow - 1))))
+      return pf_fail(ctx, PF_ERR_INVALID_ARG, "brick_shadow must be 0 or a power-of-two multiple of brick, <= 1024");
   }
   {
     const int64_t B = v->brick ? v->brick : 8;

@@ -227,6 +227,17 @@ __global__ void __launch_bounds__(128, 5) k_camera_samples(Vol V, DevLights L, C
   }
 }
 
+// Majorant of the brick of V holding x, its index clamped into brick `widx`
+// of the coarser grid Vw (so that it never exceeds Vw's majorant there).
+__device__ __forceinline__ float thin_majorant(const Vol& V, const Vol& Vw, int widx, V3 x) {
+  const int f = Vw.B / V.B;
+  const int wx = widx % Vw.gx, wy = (widx / Vw.gx) % Vw.gy, wz = widx / (Vw.gx * Vw.gy);
+  const int cx = min(max((int)floorf(x.x / V.wx), wx * f), min(wx * f + f, V.gx) - 1);
+  const int cy = min(max((int)floorf(x.y / V.wy), wy * f), min(wy * f + f, V.gy) - 1);
+  const int cz = min(max((int)floorf(x.z / V.wz), wz * f), min(wz * f + f, V.gz) - 1);
+  return __ldg(V.mg + (cx + V.gx * (cy + V.gy * cz)));
+}
+
 // Next-event estimation of the scattering samples (tracking mode), grid-stride
 // over the cell-ordered compacted list: L_d = sum over lights, in order, of
 // p(d . w_l) T_l E_l with T_l ratio tracked on the shadow ray's own stream;
@@ -247,8 +258,13 @@ constexpr int kNeePool = 16;                                               // co
 constexpr int kNeeWarpFloats = 32 * kNeePool * 2 + 32 * kNeePool / 2 + 32 * 6;  // t/factor, majorant, u16 map; x, w_l
 constexpr int kNeeWarps = 4;
 
-template <int DT>
-__global__ void __launch_bounds__(128, 6) k_nee(Vol V, DevLights L, float g, int spp, uint64_t seed,
+// THIN: the rays walk Vw (the brick grid max-pooled by f = Vw.B / V.B) and a
+// tentative collision of that walk at x is kept with probability
+// m_V(x) / m_Vw (one more uniform after its budget), m_V(x) the majorant of
+// the brick of V holding x, clamped into the current brick of Vw: the kept
+// collisions are those of ratio tracking over V's bricks.
+template <int DT, bool THIN>
+__global__ void __launch_bounds__(128, 6) k_nee(Vol V, Vol Vw, DevLights L, float g, int spp, uint64_t seed,
                                              const float* __restrict__ cq, const float* __restrict__ cdir,
                                              const float* __restrict__ calb, const uint32_t* __restrict__ cidx,
                                              const uint32_t* __restrict__ ccount, const uint32_t* __restrict__ perm,
@@ -285,7 +301,7 @@ __global__ void __launch_bounds__(128, 6) k_nee(Vol V, DevLights L, float g, int
       if (box_hit(x, wl, &a0, &a1)) tend = mn(a1, dist);
       Rng rs(seed, TAG_SHADOW, shadow_item(pix, 1, l), k);
       Walk<false> W;
-      W.init(V, x, wl, 0.0f);
+      W.init(THIN ? Vw : V, x, wl, 0.0f);
       Uniforms U;
       float T = 1.0f, t = 0.0f;
       float tau = -own_lnf(1.0f - U.next(rs));
@@ -303,14 +319,24 @@ __global__ void __launch_bounds__(128, 6) k_nee(Vol V, DevLights L, float g, int
           if (W.m > 0.0f && tau < W.m * seg) {
             const float m = W.m;
             t = t + tau / m;
-            pt[lane * kNeePool + cnt] = t;
-            pm[lane * kNeePool + cnt] = m;
-            ++cnt;
+            if (THIN) {
+              const float ut = U.next(rs);
+              const float mf = thin_majorant(V, Vw, W.idx, along(x, wl, t));
+              if (ut * m < mf) {
+                pt[lane * kNeePool + cnt] = t;
+                pm[lane * kNeePool + cnt] = mf;
+                ++cnt;
+              }
+            } else {
+              pt[lane * kNeePool + cnt] = t;
+              pm[lane * kNeePool + cnt] = m;
+              ++cnt;
+            }
             tau = -own_lnf(1.0f - U.next(rs));
           } else {
             tau = tau - W.m * seg;
             t = tc;
-            if (t >= tend || !W.step(V)) done = true;
+            if (t >= tend || !W.step(THIN ? Vw : V)) done = true;
             else tc = mn(W.exit_t(), tend);
           }
           if (++it >= kMaxTrackSteps) { atomicOr(err, 1u); done = true; }
@@ -484,15 +510,21 @@ CamF make_cam(const pf_camera* c) {
 // Launches k_nee as a grid-stride loop over the compacted list with as many
 // blocks as fit on the device at once.
 template <int DT>
-pf_status launch_nee(pf_ctx* ctx, const Vol& V, const DevLights& L, float g, int spp, uint64_t seed, int64_t n_max,
-                     const float* cq, const float* cdir, const float* calb, const uint32_t* cidx,
+pf_status launch_nee(pf_ctx* ctx, const Vol& V, const Vol& Vw, const DevLights& L, float g, int spp, uint64_t seed,
+                     int64_t n_max, const float* cq, const float* cdir, const float* calb, const uint32_t* cidx,
                      const uint32_t* ccount, const uint32_t* perm, float* ld) {
   const size_t bytes = (size_t)kNeeWarps * kNeeWarpFloats * sizeof(float);
+  const bool thin = Vw.B > V.B;
   int o = 0;  // resident blocks per SM
-  PF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_nee<DT>, 32 * kNeeWarps, bytes));
+  if (thin) PF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_nee<DT, true>, 32 * kNeeWarps, bytes));
+  else PF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_nee<DT, false>, 32 * kNeeWarps, bytes));
   unsigned nb = (unsigned)std::min<int64_t>((n_max + 127) / 128, (int64_t)ctx->num_sms * std::max(o, 1));
-  k_nee<DT><<<nb, 32 * kNeeWarps, bytes, ctx->stream>>>(V, L, g, spp, seed, cq, cdir, calb, cidx, ccount, perm, ld,
-                                                        ctx->err_dev, ctx->counters);
+  if (thin)
+    k_nee<DT, true><<<nb, 32 * kNeeWarps, bytes, ctx->stream>>>(V, Vw, L, g, spp, seed, cq, cdir, calb, cidx, ccount,
+                                                                perm, ld, ctx->err_dev, ctx->counters);
+  else
+    k_nee<DT, false><<<nb, 32 * kNeeWarps, bytes, ctx->stream>>>(V, Vw, L, g, spp, seed, cq, cdir, calb, cidx, ccount,
+                                                                 perm, ld, ctx->err_dev, ctx->counters);
   PF_CUDA(ctx, cudaGetLastError());
   return PF_OK;
 }
@@ -549,18 +581,25 @@ extern "C" pf_status pf_render_neural(pf_ctx* ctx, const pf_volume* vol, const p
     PF_CUDA(ctx, cudaMemsetAsync(chist, 0, 2 * kCells * sizeof(uint32_t), ctx->stream));
   }
   Vol V = pf_make_vol(vol, 0.f, grid);
-  Vol Vp = V;  // camera rays' free flight: the grid pooled to brick_primary
-  if (!march && vol->brick_primary > V.B) {
-    const int f = vol->brick_primary / V.B;
+  // coarser grids, max-pooled from the brick grid: the camera rays' free
+  // flight (brick_primary) and the shadow rays' walk (brick_shadow)
+  auto pooled_vol = [&](int edge, int slot, Vol* out) -> pf_status {
+    *out = V;
+    if (march || edge <= V.B) return PF_OK;
+    const int f = edge / V.B;
     const int px = (V.gx + f - 1) / f, py = (V.gy + f - 1) / f, pz = (V.gz + f - 1) / f;
     const int64_t np = (int64_t)px * py * pz;
     float* pooled;
-    PF_TRY(pf_scratch(ctx, WS_GRID_PRIMARY, (size_t)np * sizeof(float), (void**)&pooled));
+    PF_TRY(pf_scratch(ctx, slot, (size_t)np * sizeof(float), (void**)&pooled));
     k_pool_majorants<<<(unsigned)((np + 127) / 128), 128, 0, ctx->stream>>>(grid, V.gx, V.gy, V.gz, f, px, py, pz,
                                                                            pooled);
     PF_CUDA(ctx, cudaGetLastError());
-    Vp = pf_make_vol(vol, 0.f, pooled, vol->brick_primary);
-  }
+    *out = pf_make_vol(vol, 0.f, pooled, edge);
+    return PF_OK;
+  };
+  Vol Vp, Vs;
+  PF_TRY(pooled_vol(vol->brick_primary, WS_GRID_PRIMARY, &Vp));
+  PF_TRY(pooled_vol(vol->brick_shadow, WS_GRID_SHADOW, &Vs));
   DevLights L = pf_make_lights(lights, n_lights);
   CamF C = make_cam(cam);
   int nmax = std::max(vol->nx, std::max(vol->ny, vol->nz));
@@ -586,11 +625,11 @@ extern "C" pf_status pf_render_neural(pf_ctx* ctx, const pf_volume* vol, const p
         ckey, ccount, coff, cfill, perm);
     PF_CUDA(ctx, cudaGetLastError());
     if (vol->dtype == PF_F32)
-      PF_TRY(launch_nee<0>(ctx, V, L, g, spp, seed, n_slots, cq, cdir, calb, cidx, ccount, perm, ld));
+      PF_TRY(launch_nee<0>(ctx, V, Vs, L, g, spp, seed, n_slots, cq, cdir, calb, cidx, ccount, perm, ld));
     else if (vol->dtype == PF_F16)
-      PF_TRY(launch_nee<1>(ctx, V, L, g, spp, seed, n_slots, cq, cdir, calb, cidx, ccount, perm, ld));
+      PF_TRY(launch_nee<1>(ctx, V, Vs, L, g, spp, seed, n_slots, cq, cdir, calb, cidx, ccount, perm, ld));
     else
-      PF_TRY(launch_nee<2>(ctx, V, L, g, spp, seed, n_slots, cq, cdir, calb, cidx, ccount, perm, ld));
+      PF_TRY(launch_nee<2>(ctx, V, Vs, L, g, spp, seed, n_slots, cq, cdir, calb, cidx, ccount, perm, ld));
   }
   if (field) {
     StageTimer tm(ctx, PF_STAGE_FIELD);

@@ -47,6 +47,7 @@ class Volume:
     tf: np.ndarray              # (n, 4) float32 RGBA
     brick: int = 8              # edge of the majorant bricks in voxels (power of two)
     brick_primary: int = 0      # brick edge for the camera rays' free flight (0: brick)
+    brick_shadow: int = 0       # brick edge walked by shadow rays, thinned to brick (0: brick)
 
     @property
     def dtype_code(self) -> int:

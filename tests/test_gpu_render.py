@@ -64,10 +64,10 @@ def test_march_with_f32_field(pf_ctx, orc):
     assert err.max() <= 5e-3, err.max()
 
 
-@pytest.mark.parametrize("brick,primary", [(8, 0), (4, 16), (8, 32)])
-def test_tracking_direct_matches_float_oracle(pf_ctx, orc, brick, primary):
+@pytest.mark.parametrize("brick,primary,shadow", [(8, 0, 0), (4, 16, 0), (8, 32, 0), (4, 16, 16), (4, 0, 32)])
+def test_tracking_direct_matches_float_oracle(pf_ctx, orc, brick, primary, shadow):
     sc = I.scene_judge(32, 32, 24, 8)
-    v = dataclasses.replace(sc.volume, brick=brick, brick_primary=primary)
+    v = dataclasses.replace(sc.volume, brick=brick, brick_primary=primary, brick_shadow=shadow)
     vol = api.Volume.from_inputs(v)
     for g in (0.0, 0.5):
         img = api.render_neural(pf_ctx, vol, sc.lights, g, sc.camera, sc.spp, 0.0, seed=3)

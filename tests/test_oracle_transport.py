@@ -194,3 +194,27 @@ def test_fp32_and_fp64_tracers_agree_statistically(orc):
     na, nb = a["nrec"].sum(), b["nrec"].sum()
     assert abs(na - nb) < 5 * math.sqrt(na + nb) + 0.02 * na
     assert abs(a["tally"][1, 0] - b["tally"][1, 0]) / a["tally"][0, 0] < 0.02
+
+
+@pytest.mark.parametrize("B,Bs", [(4, 16), (8, 32), (4, 64)])
+def test_thinned_ratio_tracking(orc, B, Bs):
+    """Shadow rays walking the grid pooled to Bs-voxel bricks and thinning
+    its tentative collisions to the B-voxel brick majorants: the mean is
+    exp(-tau) by quadrature, and the variance is that of plain ratio
+    tracking with the B-voxel majorants (it is the same estimator).  An
+    optically moderate ray (tau ~ 1.5) keeps the variance estimates sharp."""
+    import dataclasses
+    vol = dataclasses.replace(I.scene_judge(40).volume, brick=B, sigma_scale=3.0)
+    thin = dataclasses.replace(vol, brick_shadow=Bs)
+    o, d = np.array([0.3, 0.62, -0.5]), np.array([0.15, -0.05, 1.0])
+    d = d / np.linalg.norm(d)
+    t0, t1 = (0.0 - o[2]) / d[2], (1.0 - o[2]) / d[2]
+    s, tau = _optical_depth(orc, vol, o + t0 * d, d, t1 - t0)
+    assert 0.5 < tau[-1] < 3.0
+    n = 100000
+    m_t, v_t = orc.ratio_mean(thin, o + t0 * d, d, t1 - t0, n, seed=41)
+    m_p, v_p = orc.ratio_mean(vol, o + t0 * d, d, t1 - t0, n, seed=42)
+    want = math.exp(-tau[-1])
+    assert abs(m_t - want) < 5 * math.sqrt(v_t / n) + 1e-4 * want
+    assert abs(m_p - want) < 5 * math.sqrt(v_p / n) + 1e-4 * want
+    assert 0.9 < v_t / v_p < 1.1
