@@ -181,6 +181,9 @@ def main():
     ap.add_argument("--rmse-height", type=int, default=270)
     ap.add_argument("--ref-spp", type=int, default=4096)
     ap.add_argument("--brick", type=int, default=BRICK, help="majorant brick edge in voxels (power of two)")
+    ap.add_argument("--no-march", action="store_true", help="skip the ray-marched renderer's measurement")
+    ap.add_argument("--march-width", type=int, default=480)
+    ap.add_argument("--march-height", type=int, default=270)
     ap.add_argument("--training-only", action="store_true",
                     help="run only the field-training workload and print its JSON (profiling)")
     ap.add_argument("--training-steps", type=int, default=2000)
@@ -360,6 +363,8 @@ def main():
     if not args.no_equal_rmse:
         line["equal_rmse"] = equal_rmse(ctx, vol, lights, frame, field, seed, args, fps)
         line["vs_path_tracer_equal_rmse"] = line["equal_rmse"].get("speedup")
+    if not args.no_march:
+        line["march_workload"] = march_workload(ctx, vol, lights, frame, field, seed, args)
     line["training_workload"] = training_workload(ctx, seed)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         try:
@@ -381,6 +386,49 @@ def oracle_field(field):
     w = field.get_weights().cpu().numpy().astype(np.float64)
     s = field_scales(field)
     return dict(weights=w, desc=desc, scales=s)
+
+
+def march_workload(ctx, vol, lights, frame, field, seed, args):
+    """The ray-marched variant of the neural renderer (step h = 0.5 voxel,
+    inverse-CDF free flight, marched Beer-Lambert shadow rays, one fused
+    camera-sample kernel) on the same scene, camera and field at a reduced
+    resolution (a full 1080p frame takes seconds): frames/s at that
+    resolution, samples/s, density lookups/s and the kernel's algorithmic
+    bandwidth."""
+    import torch
+    from paper_2304_07338_b300 import api, inputs as I
+    cam, g = frame(0)
+    small = I.Camera(cam.eye, cam.at, cam.up, cam.fovy_deg, args.march_width, args.march_height)
+    out = torch.empty(small.height, small.width, 3, device=torch.device("cuda", ctx.device))
+    api.render_neural(ctx, vol, lights, g, small, SPP, 0.5, seed + 30, field, out)     # warm-up
+    counters = torch.zeros(4, dtype=torch.int64, device=out.device)
+    ctx.set_counters(counters)
+    api.render_neural(ctx, vol, lights, g, small, SPP, 0.5, seed + 31, field, out)
+    ctx.sync()
+    ctx.set_counters(None)
+    lookups = int(counters[0].item())
+    n = 3
+    ctx.stage_times()
+    ctx.stage_timing(True)
+    s_ev, e_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s_ev.record(ctx.stream)
+    for i in range(n):
+        api.render_neural(ctx, vol, lights, g, small, SPP, 0.5, seed + 31, field, out)
+    e_ev.record(ctx.stream)
+    torch.cuda.synchronize()
+    ctx.stage_timing(False)
+    st = ctx.stage_times()
+    ms = s_ev.elapsed_time(e_ev) / n
+    cam_ms = st["camera"][0] / max(st["camera"][1], 1)
+    samples = small.width * small.height * SPP
+    hbm = peaks()[0]
+    bw = lookups * FETCH_BYTES / (cam_ms / 1e3) / 1e9
+    return {"resolution": "%dx%d x %d spp, h = 0.5 voxel" % (small.width, small.height, SPP),
+            "frames_per_s": 1e3 / ms, "ms_per_frame": ms, "samples_per_s": samples / (ms / 1e3),
+            "lookups_per_frame": lookups, "stages_ms_per_frame": {k: v[0] / n for k, v in st.items() if v[1]},
+            "roofline": {"kernel": "k_camera_samples (marched free flight and shadow rays)", "bound": "hbm",
+                         "achieved": bw, "peak": hbm, "unit": "GB/s", "frac": bw / hbm,
+                         "algorithmic": "%d lookups x %d B" % (lookups, FETCH_BYTES)}}
 
 
 def equal_rmse(ctx, vol, lights, frame, field, seed, args, fps_neural):
