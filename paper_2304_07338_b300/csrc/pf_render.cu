@@ -6,7 +6,7 @@
 //                     scatter to a compacted list (one atomic per warp) with
 //                     their field query, direction and albedo.  In marching
 //                     mode it also does the next-event estimation itself;
-//   k_place           (tracking mode) orders the compacted list by a 32^3
+//   k_place           (tracking mode) orders the compacted list by a 64^3
 //                     Morton cell of the scattering position (counting sort:
 //                     histogram in k_camera_samples, scan, placement);
 //   k_nee             (tracking mode) DirectIllumination over the ordered
@@ -37,8 +37,8 @@ using namespace pfd;
 
 namespace {
 
-// Morton index of the 32^3 cell holding x (positions in [0,1]^3).
-constexpr int kCellBits = 5;
+// Morton index of the 64^3 cell holding x (positions in [0,1]^3).
+constexpr int kCellBits = 6;
 constexpr uint32_t kCells = 1u << (3 * kCellBits);
 __device__ __forceinline__ uint32_t spread3(uint32_t v) {
   v = (v | (v << 8)) & 0x0300F00Fu;
