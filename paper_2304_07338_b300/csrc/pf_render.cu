@@ -83,7 +83,7 @@ __global__ void k_place(const uint32_t* __restrict__ ckey, const uint32_t* __res
 // stats (nullable): stats[0] += density lookups, stats[1] += valid samples
 // (= field queries) of the launch.
 template <int DT, bool MARCH>
-__global__ void __launch_bounds__(128, 5) k_camera_samples(Vol V, DevLights L, CamF cam, float g, int spp, float h,
+__global__ void __launch_bounds__(128, 8) k_camera_samples(Vol V, DevLights L, CamF cam, float g, int spp, float h,
                                                         uint64_t seed, int64_t n_slots, float* __restrict__ slot_ld,
                                                         float* __restrict__ slot_li, float* __restrict__ cq,
                                                         float* __restrict__ calb, float* __restrict__ cdir,
