@@ -409,7 +409,7 @@ __global__ void k_compose(const float* __restrict__ slot_ld, const float* __rest
 
 // -------------------------------------------------------------- path tracer
 template <int DT>
-__global__ void __launch_bounds__(128) k_path_samples(Vol V, DevLights L, CamF cam, float g, int spp, int k0, int kc,
+__global__ void __launch_bounds__(128, 8) k_path_samples(Vol V, DevLights L, CamF cam, float g, int spp, int k0, int kc,
                                                       int max_bounces, int use_rr, uint64_t seed, int64_t n_items,
                                                       float* __restrict__ slot_rad, uint32_t* err,
                                                       unsigned long long* stats) {
