@@ -31,7 +31,7 @@ struct TraceArgs {
 };
 
 template <int DT>
-__global__ void __launch_bounds__(128) k_trace_photons(TraceArgs A, float4* __restrict__ slots,
+__global__ void __launch_bounds__(128, 8) k_trace_photons(TraceArgs A, float4* __restrict__ slots,
                                                        uint8_t* __restrict__ nrec, uint32_t* __restrict__ counts,
                                                        double* __restrict__ tally, uint32_t* err) {
   __shared__ double s_tally[15];
