@@ -83,14 +83,14 @@ __global__ void k_place(const uint32_t* __restrict__ ckey, const uint32_t* __res
 // stats (nullable): stats[0] += density lookups, stats[1] += valid samples
 // (= field queries) of the launch.
 template <int DT, bool MARCH>
-__global__ void __launch_bounds__(128, 8) k_camera_samples(Vol V, DevLights L, CamF cam, float g, int spp, float h,
-                                                        uint64_t seed, int64_t n_slots, float* __restrict__ slot_ld,
-                                                        float* __restrict__ slot_li, float* __restrict__ cq,
-                                                        float* __restrict__ calb, float* __restrict__ cdir,
-                                                        uint32_t* __restrict__ cidx, uint32_t* __restrict__ ccount,
-                                                        uint32_t* __restrict__ ckey, uint32_t* __restrict__ chist,
-                                                        uint32_t* __restrict__ vmask, uint32_t* err,
-                                                        unsigned long long* stats) {
+__device__ __forceinline__ void camera_samples(Vol V, DevLights L, CamF cam, float g, int spp, float h,
+                                               uint64_t seed, int64_t n_slots, float* __restrict__ slot_ld,
+                                               float* __restrict__ slot_li, float* __restrict__ cq,
+                                               float* __restrict__ calb, float* __restrict__ cdir,
+                                               uint32_t* __restrict__ cidx, uint32_t* __restrict__ ccount,
+                                               uint32_t* __restrict__ ckey, uint32_t* __restrict__ chist,
+                                               uint32_t* __restrict__ vmask, uint32_t* err,
+                                               unsigned long long* stats) {
   int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool active = slot < n_slots;
   uint32_t nfetch = 0;
@@ -226,6 +226,25 @@ __global__ void __launch_bounds__(128, 8) k_camera_samples(Vol V, DevLights L, C
     cidx[i] = (uint32_t)slot;
   }
 }
+
+// The two modes as separate kernels: the tracking body is lean and gains from
+// 8 resident blocks per SM (64 registers), the marched body (shadow rays
+// marched in the same kernel) needs its registers.
+#define PF_CAMERA_ARGS                                                                                              \
+  Vol V, DevLights L, CamF cam, float g, int spp, float h, uint64_t seed, int64_t n_slots, float* __restrict__ slot_ld, \
+      float* __restrict__ slot_li, float* __restrict__ cq, float* __restrict__ calb, float* __restrict__ cdir,       \
+      uint32_t* __restrict__ cidx, uint32_t* __restrict__ ccount, uint32_t* __restrict__ ckey,                      \
+      uint32_t* __restrict__ chist, uint32_t* __restrict__ vmask, uint32_t* err, unsigned long long* stats
+#define PF_CAMERA_PASS \
+  V, L, cam, g, spp, h, seed, n_slots, slot_ld, slot_li, cq, calb, cdir, cidx, ccount, ckey, chist, vmask, err, stats
+template <int DT>
+__global__ void __launch_bounds__(128, 8) k_camera_samples(PF_CAMERA_ARGS) { camera_samples<DT, false>(PF_CAMERA_PASS); }
+template <int DT>
+__global__ void __launch_bounds__(128, 5) k_camera_samples_march(PF_CAMERA_ARGS) {
+  camera_samples<DT, true>(PF_CAMERA_PASS);
+}
+#undef PF_CAMERA_ARGS
+#undef PF_CAMERA_PASS
 
 // Majorant of the brick of V holding x, its index clamped into brick `widx`
 // of the coarser grid Vw (so that it never exceeds Vw's majorant there).
@@ -608,10 +627,10 @@ extern "C" pf_status pf_render_neural(pf_ctx* ctx, const pf_volume* vol, const p
   {
   StageTimer tm(ctx, PF_STAGE_CAMERA);
 #define LAUNCH_CS(DT)                                                                                              \
-  if (march) k_camera_samples<DT, true><<<grd, blk, 0, ctx->stream>>>(Vp, L, C, g, spp, h, seed, n_slots, ld, li, cq, \
+  if (march) k_camera_samples_march<DT><<<grd, blk, 0, ctx->stream>>>(Vp, L, C, g, spp, h, seed, n_slots, ld, li, cq, \
                                                                       calb, cdir, cidx, ccount, ckey, chist, vmask, \
                                                                       ctx->err_dev, ctx->counters);                 \
-  else k_camera_samples<DT, false><<<grd, blk, 0, ctx->stream>>>(Vp, L, C, g, spp, h, seed, n_slots, ld, li, cq, calb, \
+  else k_camera_samples<DT><<<grd, blk, 0, ctx->stream>>>(Vp, L, C, g, spp, h, seed, n_slots, ld, li, cq, calb, \
                                                                  cdir, cidx, ccount, ckey, chist, vmask,            \
                                                                  ctx->err_dev, ctx->counters);
   if (vol->dtype == PF_F32) { LAUNCH_CS(0) } else if (vol->dtype == PF_F16) { LAUNCH_CS(1) } else { LAUNCH_CS(2) }
