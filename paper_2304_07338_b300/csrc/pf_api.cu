@@ -98,6 +98,13 @@ extern "C" pf_status pf_set_counters(pf_ctx* c, uint64_t* counters_dev) {
   return PF_OK;
 }
 
+pf_status pf_aux_stream(pf_ctx* ctx) {
+  if (ctx->aux) return PF_OK;
+  PF_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
+  for (auto& e : ctx->aux_ev) PF_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  return PF_OK;
+}
+
 static cudaEvent_t take_event(pf_ctx* c) {
   if (!c->event_pool.empty()) { cudaEvent_t e = c->event_pool.back(); c->event_pool.pop_back(); return e; }
   cudaEvent_t e = nullptr;

@@ -648,10 +648,7 @@ extern "C" pf_status pf_train_field(pf_ctx* ctx, const pf_cache* c, const pf_tra
   PF_TRY(pf_scratch(ctx, WS_GRAD, f->n_params * sizeof(float), (void**)&g));
   PF_TRY(pf_scratch(ctx, WS_LOSS, (size_t)std::max(d->steps, 1) * sizeof(float), (void**)&loss));
   PF_CUDA(ctx, cudaMemsetAsync(loss, 0, (size_t)std::max(d->steps, 1) * sizeof(float), ctx->stream));
-  if (!ctx->aux) {
-    PF_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
-    for (auto& e : ctx->aux_ev) PF_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-  }
+  PF_TRY(pf_aux_stream(ctx));
   cudaEvent_t* ready = ctx->aux_ev;          // [b]: batch buffer b written
   cudaEvent_t* consumed = ctx->aux_ev + 2;   // [b]: last training step reading buffer b done
   cudaEvent_t fork = ctx->aux_ev[4];

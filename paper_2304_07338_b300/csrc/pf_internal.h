@@ -84,6 +84,9 @@ pf_status pf_cuda_check(pf_ctx* ctx, cudaError_t e, const char* what);
 #define PF_CUDA(ctx, call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) return pf_cuda_check(ctx, e_, #call); } while (0)
 #define PF_TRY(expr) do { pf_status s_ = (expr); if (s_ != PF_OK) return s_; } while (0)
 
+// The context's second stream and its events, created on first use.
+pf_status pf_aux_stream(pf_ctx* ctx);
+
 // Scratch arena: returns a device buffer of at least `bytes` for `slot`.
 pf_status pf_scratch(pf_ctx* ctx, int slot, size_t bytes, void** out);
 // Enter the context's device for the duration of a call.
