@@ -182,6 +182,8 @@ def main():
     ap.add_argument("--ref-spp", type=int, default=4096)
     ap.add_argument("--brick", type=int, default=BRICK, help="majorant brick edge in voxels (power of two)")
     ap.add_argument("--no-march", action="store_true", help="skip the ray-marched renderer's measurement")
+    ap.add_argument("--linear-voxels", action="store_true",
+                    help="gather from the caller's x-fastest volume instead of the 4x4x4-tiled copy")
     ap.add_argument("--march-width", type=int, default=480)
     ap.add_argument("--march-height", type=int, default=270)
     ap.add_argument("--training-only", action="store_true",
@@ -228,6 +230,8 @@ def main():
                      brick_shadow=args.brick_shadow)
     vol.s.majorant = vol.majorant(ctx)
     vol.attach_brick_majorants(ctx)
+    if not args.linear_voxels:
+        vol.attach_tiled(ctx)
     setup = {}
     t0 = time.perf_counter()
     cache = api.build_photon_cache(ctx, vol, lights, I.G_PAPER, args.photons, 16, 64, seed=seed + 1)
@@ -348,7 +352,8 @@ def main():
                                "fp8 4x128 field, delta/ratio tracking" % (N_VOX, W_, H_, SPP),
                    "frames": "60-frame orbit", "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (2 GiB volume)", "majorant_brick": args.brick,
-                   "majorant_brick_primary": args.brick_primary, "majorant_brick_shadow": args.brick_shadow},
+                   "majorant_brick_primary": args.brick_primary, "majorant_brick_shadow": args.brick_shadow,
+                   "voxel_layout": "linear" if args.linear_voxels else "4x4x4 tiles"},
         "queries_per_s": qpf * fps,
         "queries_per_frame": qpf,
         "lookups_per_frame": {"camera": fetches_per_frame - nee_fetches_per_frame, "nee": nee_fetches_per_frame},

@@ -21,7 +21,7 @@ class PfVolume(C.Structure):
                 ("data_dev", C.c_void_p), ("sigma_scale", C.c_float), ("albedo", C.c_float),
                 ("tf_lut_dev", C.c_void_p), ("tf_n", C.c_int), ("majorant", C.c_float),
                 ("brick_majorants_dev", C.c_void_p), ("brick", C.c_int),
-                ("brick_primary", C.c_int), ("brick_shadow", C.c_int)]
+                ("brick_primary", C.c_int), ("brick_shadow", C.c_int), ("tiled_dev", C.c_void_p)]
 
 
 class PfLight(C.Structure):
@@ -64,6 +64,7 @@ SIGNATURES = {
     "pf_sync": (I, [P]),
     "pf_volume_majorant": (I, [P, C.POINTER(PfVolume), C.POINTER(C.c_float)]),
     "pf_volume_brick_majorants": (I, [P, C.POINTER(PfVolume), P]),
+    "pf_volume_tile": (I, [P, C.POINTER(PfVolume), P]),
     "pf_build_photon_cache": (I, [P, C.POINTER(PfVolume), C.POINTER(PfLight), I, C.POINTER(C.c_float), I, U64, I, I,
                                   U64, I, PP]),
     "pf_cache_info": (I, [P, P, C.POINTER(PfCacheInfo)]),

@@ -103,8 +103,18 @@ class Volume:
         return cls(data, vol.sigma_scale, vol.albedo, tf, brick=getattr(vol, "brick", 8),
                    brick_primary=getattr(vol, "brick_primary", 0), brick_shadow=getattr(vol, "brick_shadow", 0))
 
+    def attach_tiled(self, ctx: Context) -> torch.Tensor:
+        """Copy the voxels into 4x4x4 tiles once (same values) and let the
+        tracers gather from the copy."""
+        nz, ny, nx = self.data.shape
+        n = ((nx + 3) // 4) * ((ny + 3) // 4) * ((nz + 3) // 4) * 64
+        self.tiled = torch.empty(n, dtype=self.data.dtype, device=self.data.device)
+        ctx.check(ctx.lib.pf_volume_tile(ctx.h, C.byref(self.s), _ptr(self.tiled)))
+        self.s.tiled_dev = self.tiled.data_ptr()
+        return self.tiled
+
     def brick_majorants(self, ctx: Context) -> torch.Tensor:
-        """Per-8^3-brick majorants (computed on the GPU), shape (gz, gy, gx)."""
+        """Brick majorants (computed on the GPU), shape (gz, gy, gx)."""
         nz, ny, nx = self.data.shape
         B = self.s.brick or 8
         g = torch.empty(((nz + B - 1) // B, (ny + B - 1) // B, (nx + B - 1) // B), dtype=torch.float32,

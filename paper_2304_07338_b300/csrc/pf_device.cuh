@@ -143,13 +143,31 @@ struct Vol {
   const float* mg;    // brick majorants (x fastest)
   int gx, gy, gz, B;  // brick grid and brick edge (voxels)
   float wx, wy, wz;   // brick edge in world units, B / n (IEEE division)
+  const void* tiled;  // voxels in 4x4x4 tiles (same values), or null
+  int tnx, tny;       // tiles along x and y
 };
 
+// Element offset of voxel (i, j, k) = X(i) + Y(j) + Z(k) in either layout:
+// x-fastest (X = i, Y = nx j, Z = nx ny k) or 4x4x4 tiles with z-slices of
+// 16 consecutive elements (X = 64 (i>>2) + (i&3), Y = 64 tnx (j>>2) + 4 (j&3),
+// Z = 64 tnx tny (k>>2) + 16 (k&3)).
+__device__ __forceinline__ size_t offx(const Vol& V, int i) {
+  return V.tiled ? (size_t)(i >> 2) * 64 + (size_t)(i & 3) : (size_t)i;
+}
+__device__ __forceinline__ size_t offy(const Vol& V, int j) {
+  return V.tiled ? (size_t)(j >> 2) * (size_t)V.tnx * 64 + (size_t)((j & 3) * 4) : (size_t)j * (size_t)V.nx;
+}
+__device__ __forceinline__ size_t offz(const Vol& V, int k) {
+  return V.tiled ? (size_t)(k >> 2) * (size_t)V.tnx * (size_t)V.tny * 64 + (size_t)((k & 3) * 16)
+                 : (size_t)k * (size_t)V.nx * (size_t)V.ny;
+}
+template <int DT> __device__ __forceinline__ float voxel_at(const void* base, size_t idx) {
+  if (DT == 0) return __ldg((const float*)base + idx);
+  if (DT == 1) return __half2float(__ldg((const __half*)base + idx));
+  return (float)__ldg((const uint8_t*)base + idx) / 255.0f;
+}
 template <int DT> __device__ __forceinline__ float voxel(const Vol& V, int i, int j, int k) {
-  size_t idx = (size_t)i + (size_t)V.nx * ((size_t)j + (size_t)V.ny * (size_t)k);
-  if (DT == 0) return __ldg((const float*)V.data + idx);
-  if (DT == 1) return __half2float(__ldg((const __half*)V.data + idx));
-  return (float)__ldg((const uint8_t*)V.data + idx) / 255.0f;
+  return voxel_at<DT>(V.tiled ? V.tiled : V.data, offx(V, i) + offy(V, j) + offz(V, k));
 }
 
 // Trilinear density; x, then y, then z lerps, each a + t*(b - a).
@@ -161,10 +179,14 @@ template <int DT> __device__ __forceinline__ float density(const Vol& V, V3 p) {
   int x0 = (int)ix, y0 = (int)iy, z0 = (int)iz;
   int x1 = min(x0 + 1, V.nx - 1), y1 = min(y0 + 1, V.ny - 1), z1 = min(z0 + 1, V.nz - 1);
   x0 = max(x0, 0); y0 = max(y0, 0); z0 = max(z0, 0);
-  float v000 = voxel<DT>(V, x0, y0, z0), v100 = voxel<DT>(V, x1, y0, z0);
-  float v010 = voxel<DT>(V, x0, y1, z0), v110 = voxel<DT>(V, x1, y1, z0);
-  float v001 = voxel<DT>(V, x0, y0, z1), v101 = voxel<DT>(V, x1, y0, z1);
-  float v011 = voxel<DT>(V, x0, y1, z1), v111 = voxel<DT>(V, x1, y1, z1);
+  // the layout decided once per lookup; the eight loads then issue together
+  const void* base = V.tiled ? V.tiled : V.data;
+  const size_t ax0 = offx(V, x0), ax1 = offx(V, x1), ay0 = offy(V, y0), ay1 = offy(V, y1);
+  const size_t az0 = offz(V, z0), az1 = offz(V, z1);
+  float v000 = voxel_at<DT>(base, ax0 + ay0 + az0), v100 = voxel_at<DT>(base, ax1 + ay0 + az0);
+  float v010 = voxel_at<DT>(base, ax0 + ay1 + az0), v110 = voxel_at<DT>(base, ax1 + ay1 + az0);
+  float v001 = voxel_at<DT>(base, ax0 + ay0 + az1), v101 = voxel_at<DT>(base, ax1 + ay0 + az1);
+  float v011 = voxel_at<DT>(base, ax0 + ay1 + az1), v111 = voxel_at<DT>(base, ax1 + ay1 + az1);
   float c00 = v000 + tx * (v100 - v000);
   float c10 = v010 + tx * (v110 - v010);
   float c01 = v001 + tx * (v101 - v001);
@@ -481,6 +503,9 @@ inline pfd::Vol pf_make_vol(const pf_volume* v, float majorant, const float* gri
   V.wx = (float)B / (float)v->nx;
   V.wy = (float)B / (float)v->ny;
   V.wz = (float)B / (float)v->nz;
+  V.tiled = v->tiled_dev;
+  V.tnx = (v->nx + 3) / 4;
+  V.tny = (v->ny + 3) / 4;
   return V;
 }
 inline pfd::DevLights pf_make_lights(const pf_light* lights, int n) {

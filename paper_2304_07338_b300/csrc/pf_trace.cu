@@ -261,6 +261,42 @@ pf_status pf_grid_for(pf_ctx* ctx, const pf_volume* vol, const float** grid) {
   return PF_OK;
 }
 
+namespace {
+// Tiled copy: one thread per destination element (tile-major, 64 per tile).
+template <typename T>
+__global__ void k_tile_volume(const T* __restrict__ src, int nx, int ny, int nz, int tnx, int tny, int64_t n,
+                              T* __restrict__ dst) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int64_t tile = e >> 6;
+  const int w = (int)(e & 63);
+  const int i = (int)(tile % tnx) * 4 + (w & 3);
+  const int j = (int)((tile / tnx) % tny) * 4 + ((w >> 2) & 3);
+  const int k = (int)(tile / ((int64_t)tnx * tny)) * 4 + (w >> 4);
+  dst[e] = (i < nx && j < ny && k < nz) ? src[(size_t)i + (size_t)nx * ((size_t)j + (size_t)ny * (size_t)k)] : T(0);
+}
+}  // namespace
+
+extern "C" pf_status pf_volume_tile(pf_ctx* ctx, const pf_volume* vol, void* out_dev) {
+  if (!ctx || !out_dev) return PF_ERR_INVALID_ARG;
+  DeviceGuard dg(ctx->device);
+  PF_TRY(pf_check_volume(ctx, vol));
+  const int tnx = (vol->nx + 3) / 4, tny = (vol->ny + 3) / 4, tnz = (vol->nz + 3) / 4;
+  const int64_t n = (int64_t)tnx * tny * tnz * 64;
+  const unsigned grid = (unsigned)((n + 255) / 256);
+  if (vol->dtype == PF_F32)
+    k_tile_volume<float><<<grid, 256, 0, ctx->stream>>>((const float*)vol->data_dev, vol->nx, vol->ny, vol->nz, tnx,
+                                                         tny, n, (float*)out_dev);
+  else if (vol->dtype == PF_F16)
+    k_tile_volume<uint16_t><<<grid, 256, 0, ctx->stream>>>((const uint16_t*)vol->data_dev, vol->nx, vol->ny, vol->nz,
+                                                            tnx, tny, n, (uint16_t*)out_dev);
+  else
+    k_tile_volume<uint8_t><<<grid, 256, 0, ctx->stream>>>((const uint8_t*)vol->data_dev, vol->nx, vol->ny, vol->nz,
+                                                           tnx, tny, n, (uint8_t*)out_dev);
+  PF_CUDA(ctx, cudaGetLastError());
+  return PF_OK;
+}
+
 extern "C" pf_status pf_volume_brick_majorants(pf_ctx* ctx, const pf_volume* vol, float* out_dev) {
   if (!ctx || !out_dev) return PF_ERR_INVALID_ARG;
   DeviceGuard dg(ctx->device);

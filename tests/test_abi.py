@@ -23,7 +23,7 @@ def test_library_builds_and_exports_header():
 
 def test_struct_layouts_match_header():
     import ctypes as C
-    assert C.sizeof(_lib.PfVolume) == 72   # sizes as laid out by a C compiler for pf.h
+    assert C.sizeof(_lib.PfVolume) == 80   # sizes as laid out by a C compiler for pf.h
     assert C.sizeof(_lib.PfLight) == 28
     assert C.sizeof(_lib.PfCamera) == 48
     assert C.sizeof(_lib.PfFieldDesc) == 32

@@ -75,6 +75,8 @@ def test_tracking_direct_matches_float_oracle(pf_ctx, orc, brick, primary, shado
     sc = I.scene_judge(32, 32, 24, 8)
     v = dataclasses.replace(sc.volume, brick=brick, brick_primary=primary, brick_shadow=shadow)
     vol = api.Volume.from_inputs(v)
+    if primary:
+        vol.attach_tiled(pf_ctx)      # the tiled voxel copy holds the same values
     for g in (0.0, 0.5):
         img = api.render_neural(pf_ctx, vol, sc.lights, g, sc.camera, sc.spp, 0.0, seed=3)
         pf_ctx.sync()
@@ -88,6 +90,8 @@ def test_path_tracer_matches_float_oracle(pf_ctx, orc, brick):
     sc = I.scene_judge(40 if brick == 16 else 32, 24, 20, 6)
     v = dataclasses.replace(sc.volume, brick=brick)
     vol = api.Volume.from_inputs(v)
+    if brick == 16:
+        vol.attach_tiled(pf_ctx)      # the tiled voxel copy holds the same values
     img = api.render_pathtraced(pf_ctx, vol, sc.lights, -0.5, sc.camera, sc.spp, 16, seed=11)
     pf_ctx.sync()
     ref = orc.path_trace(v, sc.lights, -0.5, sc.camera, sc.spp, 16, seed=11, fp32=True)
@@ -104,6 +108,7 @@ def test_path_tracer_u8_and_f16_volumes(pf_ctx, orc):
         data = (np.round(data * 255).astype(np.uint8) if dt == np.uint8 else data.astype(np.float16))
         v = I.Volume(data, 20.0, 0.95, I.tf_piecewise_rgba(16))
         vol = api.Volume.from_inputs(v)
+        vol.attach_tiled(pf_ctx)          # the tiled voxel copy holds the same values
         img = api.render_pathtraced(pf_ctx, vol, sc.lights, 0.3, sc.camera, sc.spp, 16, seed=2)
         pf_ctx.sync()
         ref = orc.path_trace(v, sc.lights, 0.3, sc.camera, sc.spp, 16, seed=2, fp32=True)
@@ -235,3 +240,21 @@ def test_mid_render_sampled_rows(pf_ctx, orc, prec):
         assert ref.max() > 0
         err = _rel_err(got, ref)
         assert np.median(err) < 5e-3 and err.max() < 0.3, (y0, np.median(err), err.max())
+
+
+def test_tiled_volume_with_ragged_tiles(pf_ctx, orc):
+    """A 27 x 22 x 19 volume (tiles cut at every far face): the path tracer and
+    the tracking renderer read the tiled copy and still match the oracle."""
+    data = I.fbm_volume(27, seed=8)[:19, :22, :].copy()
+    v = I.Volume(data.astype(np.float32), 18.0, 0.9, I.tf_piecewise_rgba(64), brick=4)
+    sc = I.scene_judge(16, 20, 14, 4)
+    vol = api.Volume.from_inputs(v)
+    vol.attach_tiled(pf_ctx)
+    img = api.render_pathtraced(pf_ctx, vol, sc.lights, 0.2, sc.camera, sc.spp, 16, seed=5)
+    trk = api.render_neural(pf_ctx, vol, sc.lights, 0.2, sc.camera, sc.spp, 0.0, seed=6)
+    pf_ctx.sync()
+    ref = orc.path_trace(v, sc.lights, 0.2, sc.camera, sc.spp, 16, seed=5, fp32=True)
+    assert ref.max() > 0
+    assert np.array_equal(img.cpu().numpy().astype(np.float32), ref.astype(np.float32))
+    ref2 = orc.render_neural(v, sc.lights, 0.2, sc.camera, sc.spp, 0.0, 6, fp32=True)
+    assert _rel_err(trk.cpu().numpy(), ref2).max() <= 2e-6
