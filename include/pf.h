@@ -23,6 +23,10 @@
  *   Streams.  Every call is ordered on the context's stream.  Calls return
  *     after enqueueing their kernels unless they write host memory (those
  *     synchronise the stream first).  pf_sync waits for the stream.
+ *     pf_train_field also uses a second stream of the context internally and
+ *     joins it back before returning.
+ *   Threads.  A context (and the caches and fields made with it) is used by
+ *     one host thread at a time; separate contexts may run concurrently.
  *   Errors.  Every call returns a pf_status and never aborts.  pf_last_error
  *     gives a message.  Device loops carry iteration limits; a kernel that
  *     hits one records it in a device error word, which the next synchronising
