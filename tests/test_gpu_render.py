@@ -27,7 +27,7 @@ import numpy as np
 import pytest
 import torch
 
-from paper_2304_07338_b300 import api, inputs as I
+from paper_2304_07338_b300 import _lib, api, inputs as I
 
 pytestmark = pytest.mark.gpu
 
@@ -258,3 +258,27 @@ def test_tiled_volume_with_ragged_tiles(pf_ctx, orc):
     assert np.array_equal(img.cpu().numpy().astype(np.float32), ref.astype(np.float32))
     ref2 = orc.render_neural(v, sc.lights, 0.2, sc.camera, sc.spp, 0.0, 6, fp32=True)
     assert _rel_err(trk.cpu().numpy(), ref2).max() <= 2e-6
+
+
+def test_iteration_limit_reports_timeout_and_context_survives(pf_ctx):
+    """A tracking loop that cannot finish within its iteration limit (2^24
+    tentative collisions) ends, records the limit in the device error word,
+    and the next synchronising call reports PF_ERR_TIMEOUT; the context keeps
+    working.  The medium: density 0.5 everywhere with alpha(0.5) = 1e-7 but
+    alpha(0) = 1, so the box-boundary brick majorant is ~1e7 times sigma_t
+    and a unit ray meets ~1e8 null collisions."""
+    data = np.full((8, 8, 8), 0.5, np.float32)
+    tf = np.array([[1, 1, 1, 1.0], [1, 1, 1, 1e-7], [1, 1, 1, 1e-7]], np.float32)
+    v = I.Volume(data, 1e8, 0.9, tf, brick=8)
+    vol = api.Volume.from_inputs(v)
+    lights = [I.Light(I.DIRECTIONAL, (0.0, 0.0, 1.0), (1.0, 1.0, 1.0))]
+    cam = I.Camera((0.5, 0.5, -1.5), (0.5, 0.5, 0.5), (0, 1, 0), 5.0, 1, 1)
+    api.render_pathtraced(pf_ctx, vol, lights, 0.0, cam, 1, 1, seed=3)
+    with pytest.raises(api.PfError) as e:
+        pf_ctx.sync()
+    assert e.value.status == _lib.PF_ERR_TIMEOUT
+    # the error word was cleared and the context still renders
+    sc = I.scene_small(16, 4, 4, 1)
+    img = api.render_pathtraced(pf_ctx, api.Volume.from_inputs(sc.volume), sc.lights, 0.0, sc.camera, 1, 4, seed=1)
+    pf_ctx.sync()
+    assert torch.isfinite(img).all()
