@@ -298,16 +298,32 @@ def main():
     ms_per_step = ms_total / args.steps
     fps = whole_job_rate(args.steps, world, ms_total / 1e3)
 
-    # end to end through the C ABI: camera from host, image to pinned host memory
-    host_img = torch.empty(H_, W_, 3, dtype=torch.float32, pin_memory=True)
+    # end to end through the C ABI, over the same frames as the timed region:
+    # camera and lights from host memory, each frame's image copied into
+    # pinned host memory and waited for by the host; the copy of frame i
+    # (second stream) overlaps the rendering of frame i + 1 (two buffers)
+    host_img = [torch.empty(H_, W_, 3, dtype=torch.float32, pin_memory=True) for _ in range(2)]
+    outs = [out, torch.empty_like(out)]
+    copy_stream = torch.cuda.Stream(device=dev)
+    rendered = [torch.cuda.Event() for _ in range(2)]
+    copied = [torch.cuda.Event() for _ in range(2)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    e2e_steps = max(3, min(args.steps, 10))
+    e2e_steps = args.steps
     for i in range(e2e_steps):
-        cam, g = frame(i)
-        api.render_neural(ctx, vol, lights, g, cam, SPP, 0.0, seed + 200 + i, field, out)
-        host_img.copy_(out, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+        b = i & 1
+        cam, g = frame(args.warmup + i)
+        if i >= 2:
+            ctx.stream.wait_event(copied[b])              # buffer b's previous copy is done
+        api.render_neural(ctx, vol, lights, g, cam, SPP, 0.0, seed + 100 + i, field, outs[b])
+        rendered[b].record(ctx.stream)
+        copy_stream.wait_event(rendered[b])
+        with torch.cuda.stream(copy_stream):
+            host_img[b].copy_(outs[b], non_blocking=True)
+            copied[b].record(copy_stream)
+        if i >= 1:
+            copied[b ^ 1].synchronize()                   # the host has frame i - 1
+    copied[(e2e_steps - 1) & 1].synchronize()
     e2e_total = reduce_max(time.perf_counter() - t0, dist, dev)
     e2e_fps = whole_job_rate(e2e_steps, world, e2e_total)
     import ctypes
