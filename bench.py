@@ -168,7 +168,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-rows", type=int, default=2)
+    ap.add_argument("--cpu-rows", type=int, default=3)   # ~10-15 s of host time
     ap.add_argument("--res", type=int, default=N_VOX, help="volume resolution (profiling: smaller case)")
     ap.add_argument("--width", type=int, default=W_)
     ap.add_argument("--height", type=int, default=H_)
