@@ -52,7 +52,7 @@ def _declare(L):
     L.orc_ratio_mean.restype = f64
     L.orc_trace_photons.argtypes = [i32, i32, i32, i32, P, f64, f64, P, i32, i32,
                                     P, P, P, i32, P, i32, u64, i32, i32, u64, i32, i32, u64, u64,
-                                    P, P, P, P, P]
+                                    P, P, P, P, P, P]
     L.orc_camera_samples.argtypes = [i32, i32, i32, i32, P, f64, f64, P, i32, i32, i32, i32,
                                      P, P, P, i32, f64, P, P, P, f64, i32, i32,
                                      i32, f64, u64, i32, i32, i32, i32, i32, P, P, P, P, P]
@@ -61,6 +61,7 @@ def _declare(L):
                                  i32, i32, u64, i32, i32, i32, i32, P, i64, P]
     L.orc_cell_sigma.argtypes = [i32, i32, i32, i32, P, f64, P, i32, i32, P]
     L.orc_estimate.argtypes = [P, P, P, i64, P, P, P, P, P, i32, i32, i32, P]
+    L.orc_estimate_knn.argtypes = [P, P, P, i64, P, P, P, P, P, i64, i32, C.c_float, P, P, i32, P, P, P]
 
 
 def _p(a: np.ndarray):
@@ -218,23 +219,25 @@ def trace_photons(vol, lights, g_set, n_per, max_bounces: int = 16, res: int = 6
     keys = np.full((P, S), 0xFFFFFFFF, np.uint32)
     dirs = np.zeros((P, S, 3), np.float32)
     phis = np.zeros((P, S, 3), np.float32)
+    poss = np.zeros((P, S, 3), np.float32)
     nrec = np.zeros(P, np.int32)
     tally = np.zeros(15)
     lib().orc_trace_photons(*v.args, v.ss, v.alb, *v.tfargs, v.brick, *L.args, _p(g), len(g), n_per, max_bounces, res,
                             seed, int(use_rr), int(fp32), p_begin, p_end,
-                            _p(keys), _p(dirs), _p(phis), _p(nrec), _p(tally))
-    return dict(keys=keys, dirs=dirs, phis=phis, nrec=nrec, tally=tally.reshape(5, 3),
+                            _p(keys), _p(dirs), _p(phis), _p(poss), _p(nrec), _p(tally))
+    return dict(keys=keys, dirs=dirs, phis=phis, poss=poss, nrec=nrec, tally=tally.reshape(5, 3),
                 n_keys=L.n * len(g) * res ** 3, res=res, n_lights=L.n, n_g=len(g), p_begin=p_begin)
 
 
 def flatten_records(tr: Dict):
-    """Records in (photon id, bounce) order: key, photon id, slot, dir, power."""
+    """Records in (photon id, bounce) order: key, photon id, slot, dir, power,
+    position."""
     S = tr["keys"].shape[1]
     mask = np.arange(S)[None, :] < tr["nrec"][:, None]
     pid = np.broadcast_to((np.arange(tr["keys"].shape[0]) + tr["p_begin"])[:, None], mask.shape)[mask]
     slot = np.broadcast_to(np.arange(S)[None, :], mask.shape)[mask]
     return dict(key=tr["keys"][mask], pid=pid.astype(np.int64), slot=slot.astype(np.int64),
-                dir=tr["dirs"][mask], phi=tr["phis"][mask])
+                dir=tr["dirs"][mask], phi=tr["phis"][mask], pos=tr["poss"][mask])
 
 
 def build_cache(tr: Dict) -> Dict:
@@ -249,8 +252,10 @@ def build_cache(tr: Dict) -> Dict:
     order = np.argsort(rec["key"], kind="stable")
     cache64 = np.zeros((n_keys, 3))
     np.add.at(cache64, rec["key"].astype(np.int64), rec["phi"].astype(np.float64))
+    rid = ((rec["pid"] << 4) | rec["slot"]).astype(np.uint32)
     return dict(counts=counts, offsets=offsets, dir=rec["dir"][order], phi=rec["phi"][order],
-                key=rec["key"][order], cache=cache64.astype(np.float32), cache64=cache64,
+                key=rec["key"][order], pos=rec["pos"][order], rid=rid[order],
+                phase=((rec["key"][order].astype(np.int64) // tr["res"] ** 3) % tr["n_g"]).astype(np.int32), cache=cache64.astype(np.float32), cache64=cache64,
                 res=tr["res"], n_lights=tr["n_lights"], n_g=tr["n_g"])
 
 
@@ -315,6 +320,34 @@ def estimate_targets(q: np.ndarray, g_set, cache: Dict, csig: np.ndarray) -> np.
     lib().orc_estimate(_p(x), _p(w), _p(gi), q.shape[0], _p(off), _p(rdir), _p(rphi), _p(cs), _p(gs),
                        len(gs), cache["n_lights"], cache["res"], _p(out))
     return out
+
+
+def estimate_targets_knn(q: np.ndarray, g_set, cache: Dict, csig: np.ndarray, K: int, r_max: float):
+    """Phase-selective KNN radiance estimate per query (Sec. 3.3.1, the
+    adaptive-radius estimator over the K nearest photons of the query's phase,
+    search radius capped at r_max; box units).  `cache` needs the records'
+    pos, rid, phase, dir and phi (build_cache, or any dict with those
+    arrays).  Returns (L_s (B,3) float64, k used (B,), radius r (B,) float32)."""
+    q = np.ascontiguousarray(q, np.float64)
+    gs = np.asarray(g_set, np.float32)
+    gi = np.array([int(np.nonzero(gs == np.float32(v))[0][0]) for v in q[:, 5]], np.int32)
+    x = np.ascontiguousarray(q[:, :3], np.float32)
+    w = np.ascontiguousarray(query_direction(q))
+    pos = np.ascontiguousarray(cache["pos"], np.float32)
+    rid = np.ascontiguousarray(cache["rid"], np.uint32)
+    ph = np.ascontiguousarray(cache["phase"], np.int32)
+    rdir = np.ascontiguousarray(cache["dir"], np.float32)
+    rphi = np.ascontiguousarray(cache["phi"], np.float32)
+    cs = np.ascontiguousarray(csig, np.float64)
+    res = round(cs.size ** (1.0 / 3.0))
+    assert res ** 3 == cs.size
+    B = q.shape[0]
+    out = np.zeros((B, 3))
+    k = np.zeros(B, np.int32)
+    r = np.zeros(B, np.float32)
+    lib().orc_estimate_knn(_p(x), _p(w), _p(gi), B, _p(pos), _p(rid), _p(ph), _p(rdir), _p(rphi), pos.shape[0],
+                           int(K), float(np.float32(r_max)), _p(cs), _p(gs), res, _p(out), _p(k), _p(r))
+    return out, k, r
 
 
 # ------------------------------------------------------------------ rendering (Algorithm 2)

@@ -605,7 +605,7 @@ template <typename R>
 void trace_photon(const Volume& V, const Grid<R>& G, const Light* lights, int n_lights, const float* gset, int n_g,
                   uint64_t N, int max_bounces, int res, uint64_t seed, int use_rr, uint64_t p,
                   // outputs: per-photon slots (max_bounces-1 of them)
-                  uint32_t* keys, float* dirs, float* phis, int* nrec, Tally* T) {
+                  uint32_t* keys, float* dirs, float* phis, float* poss, int* nrec, Tally* T) {
     int l = (int)(p / ((uint64_t)n_g * N));
     int gi = (int)((p / N) % (uint64_t)n_g);
     const Light& L = lights[l];
@@ -650,6 +650,7 @@ void trace_photon(const Volume& V, const Grid<R>& G, const Light* lights, int n_
             keys[n] = key;
             dirs[3 * n + 0] = (float)d.x; dirs[3 * n + 1] = (float)d.y; dirs[3 * n + 2] = (float)d.z;
             phis[3 * n + 0] = (float)P[0]; phis[3 * n + 1] = (float)P[1]; phis[3 * n + 2] = (float)P[2];
+            poss[3 * n + 0] = (float)x.x; poss[3 * n + 1] = (float)x.y; poss[3 * n + 2] = (float)x.z;
             n = n + 1;
         }
         R Pa[3] = {P[0] * m.albedo.x, P[1] * m.albedo.y, P[2] * m.albedo.z};
@@ -932,14 +933,15 @@ void orc_free_flight(int nx, int ny, int nz, int dtype, const void* data, double
 }
 
 // Photon tracing into per-photon slots.  keys[p*S + n] etc. with S =
-// max_bounces - 1; nrec[p] = records of photon p.  tally[15] = emitted,
+// max_bounces - 1 (dirs, phis, poss: three floats per slot; poss = the
+// interaction position); nrec[p] = records of photon p.  tally[15] = emitted,
 // escaped, absorbed, truncated, rr (3 channels each).
 void orc_trace_photons(int nx, int ny, int nz, int dtype, const void* data, double ss, double alb,
                        const float* tf, int tf_n, int brick,
                        const int* lkind, const double* lv, const double* lrgb, int n_lights,
                        const float* gset, int n_g, uint64_t N, int max_bounces, int res, uint64_t seed,
                        int use_rr, int fp32, uint64_t p_begin, uint64_t p_end,
-                       uint32_t* keys, float* dirs, float* phis, int* nrec, double* tally) {
+                       uint32_t* keys, float* dirs, float* phis, float* poss, int* nrec, double* tally) {
     Volume V = mkvol(nx, ny, nz, dtype, data, ss, alb, tf, tf_n);
     std::vector<Light> L = mklights(lkind, lv, lrgb, n_lights);
     int S = max_bounces - 1 > 0 ? max_bounces - 1 : 1;
@@ -953,9 +955,11 @@ void orc_trace_photons(int nx, int ny, int nz, int dtype, const void* data, doub
         for (int64_t q = (int64_t)p_begin; q < (int64_t)p_end; ++q) {
             size_t s = (size_t)(q - (int64_t)p_begin);
             if (fp32) trace_photon<float>(V, G32, L.data(), n_lights, gset, n_g, N, max_bounces, res, seed, use_rr,
-                                         (uint64_t)q, keys + s * S, dirs + s * S * 3, phis + s * S * 3, nrec + s, &loc);
+                                         (uint64_t)q, keys + s * S, dirs + s * S * 3, phis + s * S * 3, poss + s * S * 3,
+                                         nrec + s, &loc);
             else trace_photon<double>(V, G64, L.data(), n_lights, gset, n_g, N, max_bounces, res, seed, use_rr,
-                                      (uint64_t)q, keys + s * S, dirs + s * S * 3, phis + s * S * 3, nrec + s, &loc);
+                                      (uint64_t)q, keys + s * S, dirs + s * S * 3, phis + s * S * 3, poss + s * S * 3,
+                                         nrec + s, &loc);
         }
         #pragma omp critical
         {
@@ -1116,6 +1120,64 @@ void orc_estimate(const double* x, const double* w, const int* gi, int64_t B,
         }
         double s = cell_sigma[cell];
         for (int c = 0; c < 3; ++c) out[3 * b + c] = s > 0 ? acc[c] / (vcell * s) : 0.0;
+    }
+}
+
+
+// Phase-selective k-nearest-neighbour radiance estimate (Sec. 3.3.1: the
+// adaptive-radius estimator of Jensen and Christensen over the photons of the
+// query's phase only, K nearest, search radius capped at r_max).
+// For query b at float32 position x, outgoing direction w and phase index gi:
+//   candidates: every record n of phase gi (any light) with
+//     d2_n = ((x_n - x)^2 + (y_n - y)^2) + (z_n - z)^2 <= r_max^2,
+//     each difference, square and sum a float32 operation;
+//   ordered by (d2_n, record id); the first k = min(K, #candidates) are used;
+//   r = sqrt(d2) of the K-th if #candidates >= K (the K nearest lie inside
+//     the cap), else r_max (fewer than K photons: the estimate covers the
+//     whole ball searched);
+//   L_s = sum_{used n} p_g(dir_n . w) Phi_n / ((4/3) pi r^3 sigma_cell(x)),
+//     sigma_cell(x) = mean sigma_t of the cache cell holding x (the same
+//     normaliser as the cache-cell estimate), and L_s = 0 if r or sigma is 0.
+// Brute force over all records: no spatial index.  k_out, r_out nullable.
+void orc_estimate_knn(const float* xq, const double* w, const int* gi, int64_t B,
+                      const float* rpos, const uint32_t* rid, const int* rphase, const float* rdir,
+                      const float* rphi, int64_t n_rec, int K, float r_max, const double* cell_sigma,
+                      const float* gset, int res, double* out, int* k_out, float* r_out) {
+    const double pi = 3.14159265358979323846;
+    float r2max = r_max * r_max;
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t b = 0; b < B; ++b) {
+        float qx = xq[3 * b], qy = xq[3 * b + 1], qz = xq[3 * b + 2];
+        struct Cand { float d2; uint32_t id; int64_t n; };
+        std::vector<Cand> cand;
+        for (int64_t n = 0; n < n_rec; ++n) {
+            if (rphase[n] != gi[b]) continue;
+            float dx = rpos[3 * n] - qx, dy = rpos[3 * n + 1] - qy, dz = rpos[3 * n + 2] - qz;
+            float d2 = dx * dx + dy * dy + dz * dz;
+            if (d2 <= r2max) cand.push_back(Cand{d2, rid[n], n});
+        }
+        std::sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& c) {
+            return a.d2 < c.d2 || (a.d2 == c.d2 && a.id < c.id);
+        });
+        int64_t k = std::min<int64_t>((int64_t)K, (int64_t)cand.size());
+        float r = (int64_t)cand.size() >= (int64_t)K && K > 0 ? std::sqrt(cand[(size_t)K - 1].d2) : r_max;
+        double g = gset[gi[b]];
+        double acc[3] = {0, 0, 0};
+        for (int64_t i = 0; i < k; ++i) {
+            int64_t n = cand[(size_t)i].n;
+            double mu = (double)rdir[3 * n] * w[3 * b] + (double)rdir[3 * n + 1] * w[3 * b + 1] +
+                        (double)rdir[3 * n + 2] * w[3 * b + 2];
+            double p = hg_eval<double>(g, mu);
+            for (int c = 0; c < 3; ++c) acc[c] += p * (double)rphi[3 * n + c];
+        }
+        int bx = std::min(std::max((int)std::floor(qx * (float)res), 0), res - 1);
+        int by = std::min(std::max((int)std::floor(qy * (float)res), 0), res - 1);
+        int bz = std::min(std::max((int)std::floor(qz * (float)res), 0), res - 1);
+        double s = cell_sigma[bx + (int64_t)res * (by + (int64_t)res * bz)];
+        double vol = 4.0 / 3.0 * pi * (double)r * (double)r * (double)r;
+        for (int c = 0; c < 3; ++c) out[3 * b + c] = (s > 0 && r > 0) ? acc[c] / (vol * s) : 0.0;
+        if (k_out) k_out[b] = (int)k;
+        if (r_out) r_out[b] = r;
     }
 }
 
