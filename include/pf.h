@@ -121,7 +121,17 @@ typedef struct {
 } pf_field_desc;
 
 /* Training (Sec. 3.5.1): Adam(beta1, beta2, eps), learning rate lr decayed by
- * `decay` every `decay_every` steps from step ceil(decay_start_frac*steps). */
+ * `decay` every `decay_every` steps from step ceil(decay_start_frac*steps).
+ * Targets (Sec. 3.3.1): PF_TARGET_CELL, the estimate over the query's cache
+ * cell (pf_estimate_targets), or PF_TARGET_KNN, the phase-selective K-nearest
+ * estimate (pf_estimate_targets_knn) with K = knn_k and the staggered radius
+ * schedule of Sec. 3.5.2: stage i (of knn_stages, 1..8) starts at step
+ * ceil(knn_stage_begin[i] * steps) and caps the search radius at
+ * knn_radius[i] (box units, in (0, 2]); knn_stage_begin[0] = 0 and the
+ * starts do not decrease.  A zero-initialised tail (target 0) keeps the cell
+ * estimate. */
+enum { PF_TARGET_CELL = 0, PF_TARGET_KNN = 1 };
+#define PF_MAX_KNN_STAGES 8
 typedef struct {
   int steps;
   int batch;
@@ -129,6 +139,11 @@ typedef struct {
   float decay, decay_start_frac;
   int decay_every;
   uint64_t seed;
+  int target;               /* PF_TARGET_CELL or PF_TARGET_KNN */
+  int knn_k;                /* K, in [1, 2^20] */
+  int knn_stages;
+  float knn_stage_begin[PF_MAX_KNN_STAGES];
+  float knn_radius[PF_MAX_KNN_STAGES];
 } pf_train_desc;
 
 /* Totals of a photon cache.  tally = emitted, escaped, absorbed, truncated
@@ -214,13 +229,14 @@ pf_status pf_cache_info(pf_ctx* ctx, const pf_cache* cache, pf_cache_info_t* out
  *   flux_dev     [n_keys*3] f32 per-key power sums (FP64 accumulation)
  *   rec_key_dev  [n_records] u32, rec_id_dev [n_records] u32 (photon id << 4 | slot,
  *                slot = interaction index - 2), rec_dir_dev [n_records*3] f32,
- *                rec_phi_dev [n_records*3] f32 -- the records grouped by key
- *                (CSR order; order inside a key is unspecified)
+ *                rec_phi_dev [n_records*3] f32, rec_pos_dev [n_records*3] f32
+ *                (interaction position) -- the records grouped by key (CSR
+ *                order; order inside a key is unspecified)
  *   occupied_dev [n_occupied] u32 cells with records and sigma > 0, ascending
  *   cell_sigma_dev [res^3] f32   mean sigma_t of the voxel centres in each cell */
 pf_status pf_cache_export(pf_ctx* ctx, const pf_cache* cache, uint32_t* counts_dev, float* flux_dev,
                           uint32_t* rec_key_dev, uint32_t* rec_id_dev, float* rec_dir_dev, float* rec_phi_dev,
-                          uint32_t* occupied_dev, float* cell_sigma_dev);
+                          float* rec_pos_dev, uint32_t* occupied_dev, float* cell_sigma_dev);
 pf_status pf_cache_free(pf_cache* cache);
 
 /* ---------------------------------------------------------------- training samples */
@@ -234,6 +250,22 @@ pf_status pf_sample_queries(pf_ctx* ctx, const pf_cache* cache, int64_t B, int s
  * L_s > 10^-psi else 1 (Sec. 3.3.2).  ls_dev, lp_dev [B*3] f32, nullable. */
 pf_status pf_estimate_targets(pf_ctx* ctx, const pf_cache* cache, const float* q_dev, int64_t B, float psi,
                               float* ls_dev, float* lp_dev);
+/* Phase-selective k-nearest-neighbour radiance estimate per query (Sec. 3.3.1:
+ * the adaptive-radius estimator over the photons of the query's phase g only,
+ * from every light, K nearest, search radius capped at r_max):
+ *   L_s = sum_{K nearest} p_g(dir_n . w) Phi_n / ((4/3) pi r^3 sigma_cell(x)),
+ * "nearest" ordering records by (d2, record id) with the float32 squared
+ * distance d2 = ((x_n - x)^2 + (y_n - y)^2) + (z_n - z)^2, each operation
+ * rounded; records with d2 > r_max^2 (float32 product) are never used.
+ * r = sqrt(d2) of the K-th record when at least K lie within r_max, else r_max.
+ * sigma_cell(x) = mean sigma_t of the query's cache cell (the normaliser of
+ * the cell estimate); L_s = 0 when sigma_cell or r is 0.  Then the log
+ * encoding of pf_estimate_targets.  K in [1, 2^20], r_max in (0, 2] (box
+ * units).  ls_dev, lp_dev [B*3] f32; k_dev [B] i32 (records used) and r_dev
+ * [B] f32 (radius); all nullable. */
+pf_status pf_estimate_targets_knn(pf_ctx* ctx, const pf_cache* cache, const float* q_dev, int64_t B, int K,
+                                  float r_max, float psi, float* ls_dev, float* lp_dev, int32_t* k_dev,
+                                  float* r_dev);
 
 /* ---------------------------------------------------------------- photon field */
 /* Create a field with seeded Kaiming-uniform weights (layer l, element e:
@@ -260,7 +292,8 @@ pf_status pf_field_backward(pf_ctx* ctx, const pf_field* field, const float* q_d
 pf_status pf_field_adam(pf_ctx* ctx, pf_field* field, const float* grad_dev, float lr, float beta1, float beta2,
                         float eps);
 /* Field training (Sec. 3.3-3.5): per step, fresh queries (step index as the
- * Philox sub-stream), targets from the cache, forward, relative MSE
+ * Philox sub-stream), targets from the cache (cell or KNN estimate, with the
+ * step's radius), forward, relative MSE
  * (yhat-y)^2/(y^2+0.01) averaged over batch and channels, backward, Adam.
  * loss_host [steps] (nullable) receives the loss of every step; synchronises
  * at the end. */

@@ -41,7 +41,8 @@ class PfFieldDesc(C.Structure):
 class PfTrainDesc(C.Structure):
     _fields_ = [("steps", C.c_int), ("batch", C.c_int), ("lr", C.c_float), ("beta1", C.c_float),
                 ("beta2", C.c_float), ("eps", C.c_float), ("decay", C.c_float), ("decay_start_frac", C.c_float),
-                ("decay_every", C.c_int), ("seed", C.c_uint64)]
+                ("decay_every", C.c_int), ("seed", C.c_uint64), ("target", C.c_int), ("knn_k", C.c_int),
+                ("knn_stages", C.c_int), ("knn_stage_begin", C.c_float * 8), ("knn_radius", C.c_float * 8)]
 
 
 class PfCacheInfo(C.Structure):
@@ -68,10 +69,11 @@ SIGNATURES = {
     "pf_build_photon_cache": (I, [P, C.POINTER(PfVolume), C.POINTER(PfLight), I, C.POINTER(C.c_float), I, U64, I, I,
                                   U64, I, PP]),
     "pf_cache_info": (I, [P, P, C.POINTER(PfCacheInfo)]),
-    "pf_cache_export": (I, [P, P, P, P, P, P, P, P, P, P]),
+    "pf_cache_export": (I, [P, P, P, P, P, P, P, P, P, P, P]),
     "pf_cache_free": (I, [P]),
     "pf_sample_queries": (I, [P, P, I64, I, U64, P]),
     "pf_estimate_targets": (I, [P, P, P, I64, F, P, P]),
+    "pf_estimate_targets_knn": (I, [P, P, P, I64, I, F, F, P, P, P, P]),
     "pf_field_create": (I, [P, C.POINTER(PfFieldDesc), PP]),
     "pf_field_free": (I, [P]),
     "pf_field_num_params": (I64, [P]),

@@ -7,7 +7,7 @@ torch current stream of its device unless one is given.
 from __future__ import annotations
 
 import ctypes as C
-from typing import Optional, Sequence
+from typing import Optional, Sequence, Tuple
 
 import numpy as np
 import torch
@@ -178,14 +178,15 @@ class Cache:
         rid = torch.empty(nr, dtype=torch.int32, device=dev)
         rdir = torch.empty(nr * 3, dtype=torch.float32, device=dev)
         rphi = torch.empty(nr * 3, dtype=torch.float32, device=dev)
+        rpos = torch.empty(nr * 3, dtype=torch.float32, device=dev)
         occ = torch.empty(max(i.n_occupied, 1), dtype=torch.int32, device=dev)
         csig = torch.empty(i.res ** 3, dtype=torch.float32, device=dev)
         self.ctx.check(self.ctx.lib.pf_cache_export(self.ctx.h, self.h, *map(_ptr, (counts, flux, key, rid, rdir, rphi,
-                                                                                     occ, csig))))
+                                                                                     rpos, occ, csig))))
         torch.cuda.synchronize(dev)
         n = i.n_records
         return dict(counts=counts, flux=flux.view(-1, 3), key=key[:n], id=rid[:n], dir=rdir[:3 * n].view(-1, 3),
-                    phi=rphi[:3 * n].view(-1, 3), occupied=occ[:i.n_occupied], cell_sigma=csig)
+                    phi=rphi[:3 * n].view(-1, 3), pos=rpos[:3 * n].view(-1, 3), occupied=occ[:i.n_occupied], cell_sigma=csig)
 
     def sample_queries(self, B: int, step: int, seed: int) -> torch.Tensor:
         q = torch.empty(B * 6, dtype=torch.float32, device=torch.device("cuda", self.ctx.device))
@@ -199,6 +200,18 @@ class Cache:
         lp = torch.empty(B * 3, dtype=torch.float32, device=q.device)
         self.ctx.check(self.ctx.lib.pf_estimate_targets(self.ctx.h, self.h, _ptr(q), B, psi, _ptr(ls), _ptr(lp)))
         return ls.view(B, 3), lp.view(B, 3)
+
+    def estimate_targets_knn(self, q: torch.Tensor, K: int, r_max: float, psi: float = 5.0):
+        """Phase-selective K-nearest estimate: (L_s, L', records used, radius)."""
+        _need(q, torch.float32, name="q")
+        B = q.numel() // 6
+        ls = torch.empty(B * 3, dtype=torch.float32, device=q.device)
+        lp = torch.empty(B * 3, dtype=torch.float32, device=q.device)
+        k = torch.empty(B, dtype=torch.int32, device=q.device)
+        r = torch.empty(B, dtype=torch.float32, device=q.device)
+        self.ctx.check(self.ctx.lib.pf_estimate_targets_knn(self.ctx.h, self.h, _ptr(q), B, K, r_max, psi, _ptr(ls),
+                                                            _ptr(lp), _ptr(k), _ptr(r)))
+        return ls.view(B, 3), lp.view(B, 3), k, r
 
     def free(self):
         if self.h:
@@ -273,8 +286,18 @@ class Field:
         self.ctx.check(self.ctx.lib.pf_field_adam(self.ctx.h, self.h, _ptr(grad), lr, beta1, beta2, eps))
 
     def train(self, cache: Cache, steps: int, batch: int, lr=1e-2, beta1=0.9, beta2=0.99, eps=1e-8, decay=0.92,
-              decay_start_frac=0.7, decay_every=25, seed=1) -> np.ndarray:
+              decay_start_frac=0.7, decay_every=25, seed=1, knn_k: int = 0,
+              knn_schedule: Sequence[Tuple[float, float]] = ()) -> np.ndarray:
+        """Train on the cache's targets: the cell estimate, or with knn_k > 0
+        the K-nearest estimate under the staggered schedule knn_schedule =
+        [(start fraction of the steps, radius cap in box units), ...]."""
         d = PfTrainDesc(steps, batch, lr, beta1, beta2, eps, decay, decay_start_frac, decay_every, seed)
+        if knn_k > 0:
+            if not 1 <= len(knn_schedule) <= 8:
+                raise ValueError("knn_schedule needs 1..8 (start, radius) stages")
+            d.target, d.knn_k, d.knn_stages = 1, knn_k, len(knn_schedule)
+            for i, (b, r) in enumerate(knn_schedule):
+                d.knn_stage_begin[i], d.knn_radius[i] = b, r
         loss = np.zeros(max(steps, 1), np.float32)
         self.ctx.check(self.ctx.lib.pf_train_field(self.ctx.h, cache.h, C.byref(d), self.h,
                                                    loss.ctypes.data_as(C.c_void_p)))

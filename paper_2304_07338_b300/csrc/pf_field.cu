@@ -638,6 +638,20 @@ extern "C" pf_status pf_train_field(pf_ctx* ctx, const pf_cache* c, const pf_tra
     return pf_fail(ctx, PF_ERR_INVALID_ARG, "bad training description");
   if (c->n_occupied == 0) return pf_fail(ctx, PF_ERR_INVALID_ARG, "cache has no occupied cells");
   if (f->desc.prec == PF_PREC_FP8) return pf_fail(ctx, PF_ERR_UNSUPPORTED, "fp8 fields are inference-only; train bf16/fp16");
+  const bool knn = d->target == PF_TARGET_KNN;
+  if (d->target != PF_TARGET_CELL && !knn) return pf_fail(ctx, PF_ERR_INVALID_ARG, "unknown target estimate");
+  if (knn) {
+    if (d->knn_k < 1 || d->knn_k > (1 << 20)) return pf_fail(ctx, PF_ERR_INVALID_ARG, "knn_k must be in [1, 2^20]");
+    if (d->knn_stages < 1 || d->knn_stages > PF_MAX_KNN_STAGES || d->knn_stage_begin[0] != 0.f)
+      return pf_fail(ctx, PF_ERR_INVALID_ARG, "the KNN schedule needs 1..8 stages, the first starting at 0");
+    for (int i = 0; i < d->knn_stages; ++i) {
+      if (!(d->knn_radius[i] > 0.f && d->knn_radius[i] <= 2.f))
+        return pf_fail(ctx, PF_ERR_INVALID_ARG, "KNN radii must lie in (0, 2]");
+      if (!(d->knn_stage_begin[i] >= 0.f && d->knn_stage_begin[i] <= 1.f) ||
+          (i > 0 && d->knn_stage_begin[i] < d->knn_stage_begin[i - 1]))
+        return pf_fail(ctx, PF_ERR_INVALID_ARG, "KNN stage starts must not decrease and lie in [0, 1]");
+    }
+  }
   int64_t B = d->batch;
   float *q, *y, *g, *loss;
   // two batch buffers: the batch of step s + 1 (queries and targets, which do
@@ -657,8 +671,21 @@ extern "C" pf_status pf_train_field(pf_ctx* ctx, const pf_cache* c, const pf_tra
   CacheView C = cview(c);
   int s0 = (int)std::ceil((double)d->decay_start_frac * d->steps);
   StageTimer tm(ctx, PF_STAGE_TRAIN);
+  auto radius = [&](int s) {                 // the staggered schedule's cap at step s
+    float r = d->knn_radius[0];
+    for (int i = 1; i < d->knn_stages; ++i)
+      if ((double)s >= std::ceil((double)d->knn_stage_begin[i] * d->steps)) r = d->knn_radius[i];
+    return r;
+  };
   auto draw = [&](int s) -> pf_status {      // batch of step s on the second stream
-    k_batch<<<(unsigned)((B + 255) / 256), 256, 0, ctx->aux>>>(C, B, s, d->seed, f->desc.psi, qb[s & 1], yb[s & 1]);
+    if (knn) {
+      k_sample_queries<<<(unsigned)((B + 255) / 256), 256, 0, ctx->aux>>>(C, B, s, d->seed, qb[s & 1]);
+      PF_CUDA(ctx, cudaGetLastError());
+      PF_TRY(pf_knn_targets_impl(ctx, c, qb[s & 1], B, d->knn_k, radius(s), f->desc.psi, nullptr, yb[s & 1], nullptr,
+                                 nullptr, ctx->aux));
+    } else {
+      k_batch<<<(unsigned)((B + 255) / 256), 256, 0, ctx->aux>>>(C, B, s, d->seed, f->desc.psi, qb[s & 1], yb[s & 1]);
+    }
     PF_CUDA(ctx, cudaGetLastError());
     PF_CUDA(ctx, cudaEventRecord(ready[s & 1], ctx->aux));
     return PF_OK;

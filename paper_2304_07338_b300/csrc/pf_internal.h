@@ -45,6 +45,7 @@ struct pf_cache {
   uint32_t* counts = nullptr;         // [n_keys]
   uint64_t* offsets = nullptr;        // [n_keys + 1]
   float4* recs = nullptr;             // CSR records, 2 x float4 each
+  float4* pos = nullptr;              // CSR record positions (x, y, z, record id bits)
   float* flux = nullptr;              // [n_keys * 3]
   uint32_t* occupied = nullptr;       // [n_occupied]
   float* cell_sigma = nullptr;        // [res^3]
@@ -116,3 +117,7 @@ pf_status pf_field_forward_impl(pf_ctx* ctx, const pf_field* f, const float* q, 
                                 const uint32_t* B_dev, float* out, const uint32_t* slot_idx,
                                 const float* slot_alb, float* slot_li);
 pf_status pf_field_pack(pf_ctx* ctx, pf_field* f);
+// KNN radiance estimate (see pf_estimate_targets_knn) on `stream`; ls, lp,
+// k_out, r_out nullable.
+pf_status pf_knn_targets_impl(pf_ctx* ctx, const pf_cache* c, const float* q, int64_t B, int K, float r_max, float psi,
+                              float* ls, float* lp, int32_t* k_out, float* r_out, cudaStream_t stream);

@@ -5,10 +5,12 @@
 //   k_trace_photons  one thread per photon; emission, delta tracking, HG
 //                    scattering, Russian roulette; record j (j >= 2) goes to
 //                    the photon's own slot p*(max_bounces-1) + j-2 -- so no
-//                    global append counter -- and bumps counts[key];
+//                    global append counter -- and bumps counts[key]; the
+//                    interaction position goes to a parallel slot array;
 //   scan(counts)     -> CSR offsets;
 //   k_scatter        slot records -> CSR order (position within a key taken
-//                    by an atomic cursor);
+//                    by an atomic cursor), positions with them (x, y, z, id)
+//                    for the KNN estimate;
 //   k_key_flux       per-key power sums in FP64 -> float;
 //   k_cell_sigma     mean sigma_t over the voxel centres of every cache cell;
 //   k_occupancy + scan + k_occupied_list -> ascending occupied cells.
@@ -32,7 +34,7 @@ struct TraceArgs {
 
 template <int DT>
 __global__ void __launch_bounds__(128, 8) k_trace_photons(TraceArgs A, float4* __restrict__ slots,
-                                                       uint8_t* __restrict__ nrec, uint32_t* __restrict__ counts,
+                                                       float4* __restrict__ slot_pos, uint8_t* __restrict__ nrec, uint32_t* __restrict__ counts,
                                                        double* __restrict__ tally, uint32_t* err) {
   __shared__ double s_tally[15];
   if (threadIdx.x < 15) s_tally[threadIdx.x] = 0.0;
@@ -47,6 +49,7 @@ __global__ void __launch_bounds__(128, 8) k_trace_photons(TraceArgs A, float4* _
     float g = A.g_set[gi];
     int S = A.max_bounces - 1 > 0 ? A.max_bounces - 1 : 1;
     float4* my = slots + 2 * (size_t)p * S;
+    float4* my_pos = slot_pos + (size_t)p * S;
     Rng rng(A.seed, TAG_PHOTON, p, 0);
     float u[4]; rng.uni4(u);
     V3 o, d;
@@ -91,6 +94,7 @@ __global__ void __launch_bounds__(128, 8) k_trace_photons(TraceArgs A, float4* _
         uint32_t key = (uint32_t)(l * A.n_g + gi) * (R * R * R) + bin;
         my[2 * n + 0] = make_float4(__uint_as_float(key), __uint_as_float((uint32_t)(p << 4) | (uint32_t)n), d.x, d.y);
         my[2 * n + 1] = make_float4(d.z, P0, P1, P2);
+        my_pos[n] = make_float4(x.x, x.y, x.z, 0.0f);
         atomicAdd(&counts[key], 1u);
         n = n + 1;
       }
@@ -139,8 +143,10 @@ __global__ void __launch_bounds__(128, 8) k_trace_photons(TraceArgs A, float4* _
 }
 
 // Move slot records into CSR order.
-__global__ void k_scatter(const float4* __restrict__ slots, const uint8_t* __restrict__ nrec, uint64_t n_photons, int S,
-                          const uint64_t* __restrict__ offsets, uint32_t* __restrict__ cursor, float4* __restrict__ recs) {
+__global__ void k_scatter(const float4* __restrict__ slots, const float4* __restrict__ slot_pos,
+                          const uint8_t* __restrict__ nrec, uint64_t n_photons, int S,
+                          const uint64_t* __restrict__ offsets, uint32_t* __restrict__ cursor, float4* __restrict__ recs,
+                          float4* __restrict__ rpos) {
   uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   uint64_t p = i / (uint64_t)S;
   int s = (int)(i % (uint64_t)S);
@@ -150,6 +156,9 @@ __global__ void k_scatter(const float4* __restrict__ slots, const uint8_t* __res
   uint64_t pos = offsets[key] + atomicAdd(&cursor[key], 1u);
   recs[2 * pos] = a;
   recs[2 * pos + 1] = b;
+  float4 x = slot_pos[i];
+  x.w = a.y;                                   // record id: the KNN tie-break
+  rpos[pos] = x;
 }
 
 // Per-key power sums: one warp per key, FP64 lanes, rounded once.
@@ -306,7 +315,7 @@ extern "C" pf_status pf_volume_brick_majorants(pf_ctx* ctx, const pf_volume* vol
 
 static void free_cache(pf_cache* c) {
   if (!c) return;
-  cudaFree(c->counts); cudaFree(c->offsets); cudaFree(c->recs); cudaFree(c->flux);
+  cudaFree(c->counts); cudaFree(c->offsets); cudaFree(c->recs); cudaFree(c->pos); cudaFree(c->flux);
   cudaFree(c->occupied); cudaFree(c->cell_sigma);
   delete c;
 }
@@ -340,12 +349,14 @@ extern "C" pf_status pf_build_photon_cache(pf_ctx* ctx, const pf_volume* vol, co
   int S = max_bounces - 1;
   auto fail = [&](pf_status s) { free_cache(c); return s; };
   float4* slots = nullptr;
+  float4* slot_pos = nullptr;
   uint8_t* nrec = nullptr;
   uint32_t* cursor = nullptr;
   double* tally_dev = nullptr;
-#define CK(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { cudaFree(slots); cudaFree(nrec); cudaFree(cursor); cudaFree(tally_dev); \
+#define CK(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { cudaFree(slots); cudaFree(slot_pos); cudaFree(nrec); cudaFree(cursor); cudaFree(tally_dev); \
   return fail(pf_cuda_check(ctx, e_, #call)); } } while (0)
   CK(cudaMalloc(&slots, (size_t)P * S * 2 * sizeof(float4)));
+  CK(cudaMalloc(&slot_pos, (size_t)P * S * sizeof(float4)));
   CK(cudaMalloc(&nrec, (size_t)P));
   CK(cudaMalloc(&c->counts, (size_t)n_keys * sizeof(uint32_t)));
   CK(cudaMalloc(&cursor, (size_t)std::max<int64_t>(n_keys, nc) * sizeof(uint32_t)));
@@ -361,21 +372,23 @@ extern "C" pf_status pf_build_photon_cache(pf_ctx* ctx, const pf_volume* vol, co
   for (int i = 0; i < 16; ++i) A.g_set[i] = i < n_g ? g_set[i] : 0.f;
   A.n_g = n_g; A.max_bounces = max_bounces; A.res = res; A.use_rr = use_rr; A.N = N; A.seed = seed; A.n_photons = P;
   unsigned grd = (unsigned)((P + 127) / 128);
-  if (vol->dtype == PF_F32) k_trace_photons<0><<<grd, 128, 0, ctx->stream>>>(A, slots, nrec, c->counts, tally_dev, ctx->err_dev);
-  else if (vol->dtype == PF_F16) k_trace_photons<1><<<grd, 128, 0, ctx->stream>>>(A, slots, nrec, c->counts, tally_dev, ctx->err_dev);
-  else k_trace_photons<2><<<grd, 128, 0, ctx->stream>>>(A, slots, nrec, c->counts, tally_dev, ctx->err_dev);
+  if (vol->dtype == PF_F32) k_trace_photons<0><<<grd, 128, 0, ctx->stream>>>(A, slots, slot_pos, nrec, c->counts, tally_dev, ctx->err_dev);
+  else if (vol->dtype == PF_F16) k_trace_photons<1><<<grd, 128, 0, ctx->stream>>>(A, slots, slot_pos, nrec, c->counts, tally_dev, ctx->err_dev);
+  else k_trace_photons<2><<<grd, 128, 0, ctx->stream>>>(A, slots, slot_pos, nrec, c->counts, tally_dev, ctx->err_dev);
   CK(cudaGetLastError());
   pf_status st = pf_scan_u32(ctx, c->counts, c->offsets, n_keys);
-  if (st != PF_OK) { cudaFree(slots); cudaFree(nrec); cudaFree(cursor); cudaFree(tally_dev); return fail(st); }
+  if (st != PF_OK) { cudaFree(slots); cudaFree(slot_pos); cudaFree(nrec); cudaFree(cursor); cudaFree(tally_dev); return fail(st); }
   uint64_t n_rec = 0;
   CK(cudaMemcpyAsync(&n_rec, c->offsets + n_keys, sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(c->tally, tally_dev, 15 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   c->n_records = (int64_t)n_rec;
   CK(cudaMalloc(&c->recs, (size_t)std::max<uint64_t>(n_rec, 1) * 2 * sizeof(float4)));
+  CK(cudaMalloc(&c->pos, (size_t)std::max<uint64_t>(n_rec, 1) * sizeof(float4)));
   CK(cudaMemsetAsync(cursor, 0, (size_t)n_keys * sizeof(uint32_t), ctx->stream));
   uint64_t n_slots = P * (uint64_t)S;
-  k_scatter<<<(unsigned)((n_slots + 255) / 256), 256, 0, ctx->stream>>>(slots, nrec, P, S, c->offsets, cursor, c->recs);
+  k_scatter<<<(unsigned)((n_slots + 255) / 256), 256, 0, ctx->stream>>>(slots, slot_pos, nrec, P, S, c->offsets, cursor,
+                                                                        c->recs, c->pos);
   CK(cudaGetLastError());
   CK(cudaMalloc(&c->flux, (size_t)n_keys * 3 * sizeof(float)));
   k_key_flux<<<(unsigned)((n_keys * 32 + 255) / 256), 256, 0, ctx->stream>>>(c->recs, c->offsets, n_keys, c->flux);
@@ -391,6 +404,8 @@ extern "C" pf_status pf_build_photon_cache(pf_ctx* ctx, const pf_volume* vol, co
   CK(cudaMalloc(&opos, (size_t)(nc + 1) * sizeof(uint64_t)));
   cudaFree(slots);
   slots = (float4*)opos;     // freed with the other temporaries below
+  cudaFree(slot_pos);
+  slot_pos = nullptr;
   k_occupancy<<<gc, 128, 0, ctx->stream>>>(c->counts, c->cell_sigma, nc, n_lights * n_g, cursor);
   CK(cudaGetLastError());
   st = pf_scan_u32(ctx, cursor, opos, nc);
@@ -421,10 +436,12 @@ extern "C" pf_status pf_cache_info(pf_ctx* ctx, const pf_cache* c, pf_cache_info
 }
 
 namespace {
-__global__ void k_export_recs(const float4* __restrict__ recs, int64_t n, uint32_t* key, uint32_t* id, float* dir, float* phi) {
+__global__ void k_export_recs(const float4* __restrict__ recs, const float4* __restrict__ rpos, int64_t n, uint32_t* key,
+                              uint32_t* id, float* dir, float* phi, float* pos) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float4 a = recs[2 * i], b = recs[2 * i + 1];
+  if (pos) { float4 x = rpos[i]; pos[3 * i] = x.x; pos[3 * i + 1] = x.y; pos[3 * i + 2] = x.z; }
   if (key) key[i] = __float_as_uint(a.x);
   if (id) id[i] = __float_as_uint(a.y);
   if (dir) { dir[3 * i] = a.z; dir[3 * i + 1] = a.w; dir[3 * i + 2] = b.x; }
@@ -434,7 +451,8 @@ __global__ void k_export_recs(const float4* __restrict__ recs, int64_t n, uint32
 
 extern "C" pf_status pf_cache_export(pf_ctx* ctx, const pf_cache* c, uint32_t* counts_dev, float* flux_dev,
                                      uint32_t* rec_key_dev, uint32_t* rec_id_dev, float* rec_dir_dev,
-                                     float* rec_phi_dev, uint32_t* occupied_dev, float* cell_sigma_dev) {
+                                     float* rec_phi_dev, float* rec_pos_dev, uint32_t* occupied_dev,
+                                     float* cell_sigma_dev) {
   if (!ctx || !c) return PF_ERR_INVALID_ARG;
   DeviceGuard dg(ctx->device);
   cudaStream_t s = ctx->stream;
@@ -444,9 +462,10 @@ extern "C" pf_status pf_cache_export(pf_ctx* ctx, const pf_cache* c, uint32_t* c
     PF_CUDA(ctx, cudaMemcpyAsync(occupied_dev, c->occupied, c->n_occupied * 4, cudaMemcpyDeviceToDevice, s));
   if (cell_sigma_dev)
     PF_CUDA(ctx, cudaMemcpyAsync(cell_sigma_dev, c->cell_sigma, (size_t)c->res * c->res * c->res * 4, cudaMemcpyDeviceToDevice, s));
-  if ((rec_key_dev || rec_id_dev || rec_dir_dev || rec_phi_dev) && c->n_records) {
-    k_export_recs<<<(unsigned)((c->n_records + 255) / 256), 256, 0, s>>>(c->recs, c->n_records, rec_key_dev, rec_id_dev,
-                                                                           rec_dir_dev, rec_phi_dev);
+  if ((rec_key_dev || rec_id_dev || rec_dir_dev || rec_phi_dev || rec_pos_dev) && c->n_records) {
+    k_export_recs<<<(unsigned)((c->n_records + 255) / 256), 256, 0, s>>>(c->recs, c->pos, c->n_records, rec_key_dev,
+                                                                           rec_id_dev, rec_dir_dev, rec_phi_dev,
+                                                                           rec_pos_dev);
     PF_CUDA(ctx, cudaGetLastError());
   }
   return PF_OK;

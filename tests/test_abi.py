@@ -27,7 +27,7 @@ def test_struct_layouts_match_header():
     assert C.sizeof(_lib.PfLight) == 28
     assert C.sizeof(_lib.PfCamera) == 48
     assert C.sizeof(_lib.PfFieldDesc) == 32
-    assert C.sizeof(_lib.PfTrainDesc) == 48
+    assert C.sizeof(_lib.PfTrainDesc) == 128
     assert _lib.PfCacheInfo.tally.offset == 48
 
 
