@@ -68,9 +68,10 @@ __device__ __forceinline__ void axis_range(float c, float rr, int R, int* lo, in
   *hi = min(h, R - 1);
 }
 
-// Squared distance from c to the cell interval [i/R, (i+1)/R].
-__device__ __forceinline__ float gap2(float c, int i, int R) {
-  const float lo = (float)i / (float)R, hi = (float)(i + 1) / (float)R;
+// Squared distance from c to the cell interval [i/R, (i+1)/R] (R a power of
+// two: the products by 1/R are exact).
+__device__ __forceinline__ float gap2(float c, int i, float inv_r) {
+  const float lo = (float)i * inv_r, hi = (float)(i + 1) * inv_r;
   const float d = fmaxf(0.f, fmaxf(lo - c, c - hi));
   return d * d;
 }
@@ -85,7 +86,8 @@ __device__ __forceinline__ void row_range(const KnnArgs& A, const Query& Q, int 
   const int cz = Q.zlo + rem / ny, cy = Q.ylo + rem % ny;
   *s = 0;
   *len = 0;
-  const float gyz = (gap2(Q.z, cz, R) + gap2(Q.y, cy, R)) * (1.f - 1e-5f);
+  const float inv_r = 1.0f / (float)R;
+  const float gyz = (gap2(Q.z, cz, inv_r) + gap2(Q.y, cy, inv_r)) * (1.f - 1e-5f);
   if (gyz > Q.r2) return;
   const float rx = sqrtf(Q.r2 - gyz) * (1.f + 1e-5f) + 1e-7f;
   int xlo, xhi;
@@ -97,44 +99,62 @@ __device__ __forceinline__ void row_range(const KnnArgs& A, const Query& Q, int 
   *len = (uint32_t)(b - a);
 }
 
+// Rows r0 .. r0+31 of the cover, one per lane: the lane's record range
+// [s, s + len) and the running total inc over lanes 0..lane.
+struct Chunk {
+  uint64_t s;
+  uint32_t len, inc, total;
+};
+
+__device__ __forceinline__ Chunk chunk_at(const KnnArgs& A, const Query& Q, int lane, int r0, int n_rows, int ny,
+                                          int nz) {
+  Chunk c;
+  c.s = 0;
+  c.len = 0;
+  if (r0 + lane < n_rows) row_range(A, Q, r0 + lane, ny, nz, &c.s, &c.len);
+  c.inc = c.len;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, c.inc, o);
+    if (lane >= o) c.inc += v;
+  }
+  c.total = __shfl_sync(0xffffffffu, c.inc, 31);
+  return c;
+}
+
+// Calls f(n, d2, id) for the records of a chunk with d2 <= r_max^2.  The
+// lanes walk the concatenation of the chunk's record ranges, each lane
+// finding its row by a binary search over the lanes' running totals, so short
+// rows leave no lane idle.
+template <typename F>
+__device__ __forceinline__ void walk_chunk(const KnnArgs& A, const Query& Q, int lane, const Chunk& c, F&& f) {
+  for (uint32_t t0 = 0; t0 < c.total; t0 += 32) {
+    const uint32_t t = t0 + lane;
+    int j = 0;                                    // first lane whose running total exceeds t
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1)
+      if (__shfl_sync(0xffffffffu, c.inc, j + step - 1) <= t) j += step;
+    const uint32_t inc_j = __shfl_sync(0xffffffffu, c.inc, j), len_j = __shfl_sync(0xffffffffu, c.len, j);
+    const uint64_t s_j = __shfl_sync(0xffffffffu, c.s, j);
+    if (t < c.total) {
+      const uint64_t n = s_j + (t - (inc_j - len_j));
+      const float4 p = __ldg(&A.pos[n]);
+      const float dx = __fsub_rn(p.x, Q.x), dy = __fsub_rn(p.y, Q.y), dz = __fsub_rn(p.z, Q.z);
+      const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+      if (d2 <= Q.r2) f(n, d2, __float_as_uint(p.w));
+    }
+  }
+}
+
 // Calls f(n, d2, id) for every record n of the query's phase (all lights)
-// with d2 <= r_max^2.  Rows are taken 32 at a time, one per lane (their
-// offsets load in parallel); the lanes then walk the concatenation of those
-// rows' record ranges, each lane finding its row by a binary search over the
-// lanes' running totals, so short rows leave no lane idle.
+// with d2 <= r_max^2, the cover's rows taken 32 at a time (their offsets
+// load in parallel).
 template <typename F>
 __device__ __forceinline__ void for_candidates(const KnnArgs& A, const Query& Q, int lane, F&& f) {
   const int ny = Q.yhi - Q.ylo + 1, nz = Q.zhi - Q.zlo + 1;
   if (ny <= 0 || nz <= 0) return;
   const int n_rows = A.n_lights * ny * nz;
-  for (int r0 = 0; r0 < n_rows; r0 += 32) {
-    uint64_t s = 0;
-    uint32_t len = 0;
-    if (r0 + lane < n_rows) row_range(A, Q, r0 + lane, ny, nz, &s, &len);
-    uint32_t inc = len;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += v;
-    }
-    const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
-    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
-      const uint32_t t = t0 + lane;
-      int j = 0;                                  // first lane whose running total exceeds t
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1)
-        if (__shfl_sync(0xffffffffu, inc, j + step - 1) <= t) j += step;
-      const uint32_t inc_j = __shfl_sync(0xffffffffu, inc, j), len_j = __shfl_sync(0xffffffffu, len, j);
-      const uint64_t s_j = __shfl_sync(0xffffffffu, s, j);
-      if (t < total) {
-        const uint64_t n = s_j + (t - (inc_j - len_j));
-        const float4 p = __ldg(&A.pos[n]);
-        const float dx = __fsub_rn(p.x, Q.x), dy = __fsub_rn(p.y, Q.y), dz = __fsub_rn(p.z, Q.z);
-        const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-        if (d2 <= Q.r2) f(n, d2, __float_as_uint(p.w));
-      }
-    }
-  }
+  for (int r0 = 0; r0 < n_rows; r0 += 32) walk_chunk(A, Q, lane, chunk_at(A, Q, lane, r0, n_rows, ny, nz), f);
 }
 
 // Records in the rows covering the ball (offsets only).
@@ -240,7 +260,25 @@ __global__ void __launch_bounds__(32 * kWarps, 5) k_knn(KnnArgs A) {
   };
   float r = r_max;
   const uint32_t K = (uint32_t)A.K;
-  bool all = row_total(A, Q, lane) <= (uint64_t)K;
+  const float sig = A.cell_sigma[min(max((int)floorf(Q.x * (float)R), 0), R - 1) +
+                                 (int64_t)R * (min(max((int)floorf(Q.y * (float)R), 0), R - 1) +
+                                               (int64_t)R * min(max((int)floorf(Q.z * (float)R), 0), R - 1))];
+  // a cover of at most 32 rows is one chunk: its ranges stay in registers,
+  // and if it holds at most K records they are all used at once
+  const int ny = Q.yhi - Q.ylo + 1, nz = Q.zhi - Q.zlo + 1;
+  const int n_rows = (ny > 0 && nz > 0) ? A.n_lights * ny * nz : 0;
+  bool all, done = false;
+  float dmax = 0.f;            // all-records path: largest d2 used (the K-th when exactly K)
+  if (n_rows <= 32) {
+    const Chunk c0 = chunk_at(A, Q, lane, 0, n_rows, ny, nz);
+    all = c0.total <= K;
+    if (all) {
+      walk_chunk(A, Q, lane, c0, [&](uint64_t n, float d2, uint32_t) { add(n); dmax = fmaxf(dmax, d2); });
+      done = true;
+    }
+  } else {
+    all = row_total(A, Q, lane) <= (uint64_t)K;
+  }
   int bstar = 0;
   uint32_t need = 0;
   if (!all) {
@@ -259,9 +297,9 @@ __global__ void __launch_bounds__(32 * kWarps, 5) k_knn(KnnArgs A) {
       need = K - below;
     }
   }
-  float dmax = 0.f;            // all-records path: largest d2 used (the K-th when exactly K)
   if (all) {
-    for_candidates(A, Q, lane, [&](uint64_t n, float d2, uint32_t) { add(n); dmax = fmaxf(dmax, d2); });
+    if (!done)
+      for_candidates(A, Q, lane, [&](uint64_t n, float d2, uint32_t) { add(n); dmax = fmaxf(dmax, d2); });
   } else {
     // narrow bin b* by radix rounds on the key until its share fits the list
     uint32_t inF = hist[bstar];
@@ -336,10 +374,6 @@ __global__ void __launch_bounds__(32 * kWarps, 5) k_knn(KnnArgs A) {
   }
   if (all && kc >= K) r = __fsqrt_rn(dmax);
   if (lane == 0) {
-    const int bx = min(max((int)floorf(Q.x * (float)R), 0), R - 1);
-    const int by = min(max((int)floorf(Q.y * (float)R), 0), R - 1);
-    const int bz = min(max((int)floorf(Q.z * (float)R), 0), R - 1);
-    const float sig = A.cell_sigma[bx + (int64_t)R * (by + (int64_t)R * bz)];
     const float vol = 4.18879032f * r * r * r;
     const float norm = (sig > 0.f && vol > 0.f) ? 1.0f / (vol * sig) : 0.f;
     const float L[3] = {a0 * norm, a1 * norm, a2 * norm};
