@@ -9,7 +9,7 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
     k = 0..F-1, for all six inputs, ordered [input][frequency][sin, cos].
   * Network: ReLU MLP without bias (Sec. 3.4, "no output activation"),
     Kaiming-uniform initialisation W ~ U(-sqrt(6/fan_in), sqrt(6/fan_in)).
-  * Decode: exponential decode of Eq. 8, L = 10^(-psi L').
+  * Decode: exponential decode of Eq. 7, L = 10^(-psi L').
   * Loss: relative MSE (Sec. 3.5.1), (yhat - y)^2 / (y^2 + 0.01), averaged
     over the batch and the three outputs.
   * Optimiser: Adam (Sec. 3.5.1), beta1 0.9, beta2 0.99, exponential decay of
@@ -138,7 +138,7 @@ def log_encode(L: np.ndarray, psi: float) -> np.ndarray:
 
 
 def log_decode(Lp: np.ndarray, psi: float) -> np.ndarray:
-    """Exponential decode (Eq. 8): L = 10^(-psi L')."""
+    """Exponential decode (Eq. 7): L = 10^(-psi L')."""
     return np.power(10.0, -psi * np.asarray(Lp, np.float64))
 
 

@@ -1,7 +1,7 @@
 """Pins of the oracle's field numerics (Sec. 3.3.2, 3.4, 3.5).
 
   * frequency encoding: known values and the [input][k][sin, cos] order;
-  * log target codec (Sec. 3.3.2 / Eq. 8): exact round trip above 10^-psi and
+  * log target codec (Sec. 3.3.2, Eq. 6 and Eq. 7): exact round trip above 10^-psi and
     the clamp branch below it;
   * forward pass against a brute-force loop evaluation of a tiny network;
   * backward pass against central finite differences (FP64);
