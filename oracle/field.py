@@ -6,7 +6,10 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
     view direction in normalised spherical coordinates (Sec. 3.1).
   * Encoding: NeRF-style frequency encoding (Sec. 3.4 names it as the
     alternative to the hashgrid): gamma(v) = [sin(2^k pi v), cos(2^k pi v)],
-    k = 0..F-1, for all six inputs, ordered [input][frequency][sin, cos].
+    k = 0..F-1, for all six inputs, ordered [input][frequency][sin, cos];
+    or the paper's own multiresolution hash-grid encoding (Sec. 3.4, after
+    Mueller et al. 2022), one 3-D grid for the position and one 2-D grid for
+    the direction, g passed through raw (see hash_encode).
   * Network: ReLU MLP without bias (Sec. 3.4, "no output activation"),
     Kaiming-uniform initialisation W ~ U(-sqrt(6/fan_in), sqrt(6/fan_in)).
   * Decode: exponential decode of Eq. 7, L = 10^(-psi L').
@@ -35,7 +38,42 @@ from typing import List, Sequence, Tuple
 import numpy as np
 
 PREC_F32, PREC_BF16, PREC_F16, PREC_FP8 = 0, 1, 2, 3
+ENC_FREQUENCY, ENC_HASHGRID = 0, 1
 E4M3_MAX = 448.0
+HASH_PRIMES = (1, 2654435761, 805459861)
+HASH_INIT = 1e-4
+
+
+@dataclasses.dataclass
+class HashGrid:
+    """One multiresolution hash grid over [0,1]^dim: level l has resolution
+    N_l = floor(base_res * scale^l) cells per axis, (N_l + 1)^dim vertices,
+    and a table of min((N_l + 1)^dim, 2^log2_size) entries of `features`
+    floats; a level whose vertices fit is indexed densely (x fastest), the
+    others by the spatial hash (xor of v_k * pi_k, pi = 1, 2654435761,
+    805459861, in 32-bit arithmetic) modulo the table size."""
+    dim: int
+    levels: int
+    features: int
+    log2_size: int
+    base_res: int
+    scale: float
+
+    def res(self, l: int) -> int:
+        return int(math.floor(self.base_res * self.scale ** l))
+
+    def dense(self, l: int) -> bool:
+        return (self.res(l) + 1) ** self.dim <= 2 ** self.log2_size
+
+    def entries(self, l: int) -> int:
+        return (self.res(l) + 1) ** self.dim if self.dense(l) else 2 ** self.log2_size
+
+    def level_floats(self, l: int) -> int:
+        # tables start on 8-float boundaries
+        return (self.entries(l) * self.features + 7) // 8 * 8
+
+    def n_params(self) -> int:
+        return sum(self.level_floats(l) for l in range(self.levels))
 
 
 @dataclasses.dataclass
@@ -46,9 +84,21 @@ class FieldDesc:
     prec: int = PREC_F32
     psi: float = 5.0
     seed: int = 0
+    encoding: int = ENC_FREQUENCY
+    hash_levels: int = 16
+    hash_features: int = 8
+    hash_log2_size: int = 19
+    hash_base_res: int = 16
+    hash_scale: float = 2.0
+
+    def grids(self) -> List[HashGrid]:
+        a = (self.hash_levels, self.hash_features, self.hash_log2_size, self.hash_base_res, self.hash_scale)
+        return [HashGrid(3, *a), HashGrid(2, *a)]
 
     @property
     def n_in(self) -> int:
+        if self.encoding == ENC_HASHGRID:
+            return 2 * self.hash_levels * self.hash_features + 1
         return 12 * self.in_freqs
 
     def shapes(self) -> List[Tuple[int, int]]:
@@ -57,11 +107,32 @@ class FieldDesc:
         s += [(3, self.hidden)]
         return s
 
-    def n_params(self) -> int:
+    def n_mlp(self) -> int:
         return sum(o * i for o, i in self.shapes())
+
+    def n_params(self) -> int:
+        n = self.n_mlp()
+        if self.encoding == ENC_HASHGRID:
+            n = (n + 7) // 8 * 8 + sum(g.n_params() for g in self.grids())
+        return n
+
+    def table_offsets(self) -> List[List[int]]:
+        """Float offset of every level's table in the flat parameter vector:
+        after the MLP layers (rounded up to 8 floats), position grid levels,
+        then direction grid levels."""
+        o = (self.n_mlp() + 7) // 8 * 8
+        out = []
+        for g in self.grids():
+            offs = []
+            for l in range(g.levels):
+                offs.append(o)
+                o += g.level_floats(l)
+            out.append(offs)
+        return out
 
 
 def unflatten(flat: np.ndarray, desc: FieldDesc) -> List[np.ndarray]:
+    """The MLP layers' weight matrices (hash tables, if any, are not part of it)."""
     out, o = [], 0
     for (a, b) in desc.shapes():
         out.append(np.asarray(flat[o:o + a * b], np.float64).reshape(a, b))
@@ -76,7 +147,9 @@ def flatten(ws: Sequence[np.ndarray]) -> np.ndarray:
 def init_weights(desc: FieldDesc) -> np.ndarray:
     """Seeded Kaiming-uniform weights as float32 master copies: element e of
     layer l draws u from Philox (tag INIT, item l, block e/4, lane e%4);
-    w = (2u - 1) sqrt(6/fan_in) evaluated in FP64, then rounded once."""
+    w = (2u - 1) sqrt(6/fan_in) evaluated in FP64, then rounded once.  Hash
+    tables: element e of level l of grid j (0 position, 1 direction) draws u
+    from item 64 + 16 j + l: w = (2u - 1) 1e-4; padding floats are 0."""
     from . import philox_stream, uniform, TAG_INIT
     flat = []
     for l, (o, i) in enumerate(desc.shapes()):
@@ -86,7 +159,20 @@ def init_weights(desc: FieldDesc) -> np.ndarray:
         u = uniform(words.reshape(-1)[:n])
         bound = math.sqrt(6.0 / i)
         flat.append(((2.0 * u - 1.0) * bound).astype(np.float32))
-    return np.concatenate(flat)
+    w = np.concatenate(flat)
+    if desc.encoding != ENC_HASHGRID:
+        return w
+    out = np.zeros(desc.n_params(), np.float32)
+    out[:w.size] = w
+    for j, (g, offs) in enumerate(zip(desc.grids(), desc.table_offsets())):
+        for l in range(g.levels):
+            n = g.entries(l) * g.features
+            nb = (n + 3) // 4
+            item = 64 + 16 * j + l
+            words = philox_stream(desc.seed, TAG_INIT, 0, item + 1, nb)[item]
+            u = uniform(words.reshape(-1)[:n])
+            out[offs[l]:offs[l] + n] = ((2.0 * u - 1.0) * HASH_INIT).astype(np.float32)
+    return out
 
 
 # ------------------------------------------------------------------ rounding
@@ -126,6 +212,57 @@ def encode(q: np.ndarray, n_freq: int) -> np.ndarray:
     arg = math.pi * q[:, :, None] * k[None, None, :]
     f = np.stack([np.sin(arg), np.cos(arg)], axis=-1)
     return f.reshape(q.shape[0], -1)
+
+
+def hash_corners(grid: HashGrid, l: int, x: np.ndarray):
+    """Table indices (B, 2^dim) and interpolation weights (B, 2^dim) of level
+    l at points x (B, dim).  The cell is decided in float32, as the kernel
+    does: p = float32(clamp(x, 0, 1)) * N_l, i = min(floor(p), N_l - 1),
+    fraction p - i (exact in float32); corner c takes vertex i + c with weight
+    prod_k (c_k ? f_k : 1 - f_k) (multilinear interpolation)."""
+    N = grid.res(l)
+    xc = np.clip(np.asarray(x, np.float32), np.float32(0), np.float32(1))
+    p = xc * np.float32(N)
+    i = np.minimum(np.floor(p), np.float32(N - 1)).astype(np.int64)
+    f = (p - i.astype(np.float32)).astype(np.float64)
+    B, d = xc.shape
+    idx = np.zeros((B, 2 ** d), np.int64)
+    wgt = np.ones((B, 2 ** d))
+    for c in range(2 ** d):
+        v = [i[:, k] + ((c >> k) & 1) for k in range(d)]
+        for k in range(d):
+            wgt[:, c] *= np.where((c >> k) & 1, f[:, k], 1.0 - f[:, k])
+        if grid.dense(l):
+            lin = np.zeros(B, np.int64)
+            for k in range(d - 1, -1, -1):
+                lin = lin * (N + 1) + v[k]
+            idx[:, c] = lin
+        else:
+            h = np.zeros(B, np.uint64)
+            for k in range(d):
+                h ^= (v[k].astype(np.uint64) * np.uint64(HASH_PRIMES[k])) & np.uint64(0xFFFFFFFF)
+            idx[:, c] = (h & np.uint64(2 ** grid.log2_size - 1)).astype(np.int64)
+    return idx, wgt
+
+
+def hash_encode(weights: np.ndarray, q: np.ndarray, desc: FieldDesc):
+    """Hash-grid input of the MLP: [position levels' features, direction
+    levels' features, g], level-major, F features per level.  Returns the
+    (B, n_in) inputs and the corner lists for the backward pass."""
+    q = np.asarray(q, np.float64)
+    w = np.asarray(weights, np.float64)
+    B = q.shape[0]
+    cols, corners = [], []
+    for j, (g, offs) in enumerate(zip(desc.grids(), desc.table_offsets())):
+        x = q[:, 0:3] if j == 0 else q[:, 3:5]
+        for l in range(g.levels):
+            idx, wgt = hash_corners(g, l, x)
+            F = g.features
+            tab = w[offs[l]:offs[l] + g.entries(l) * F].reshape(-1, F)
+            cols.append(np.einsum("bc,bcf->bf", wgt, tab[idx]))
+            corners.append((offs[l], F, idx, wgt))
+    cols.append(q[:, 5:6])
+    return np.concatenate(cols, 1).reshape(B, -1), corners
 
 
 def log_encode(L: np.ndarray, psi: float) -> np.ndarray:
@@ -176,7 +313,11 @@ def fp8_calibrate(weights: np.ndarray, q_cal: np.ndarray, desc: FieldDesc):
 def forward(weights: np.ndarray, q: np.ndarray, desc: FieldDesc, scales=None):
     """Field forward pass; returns (L' prediction (B,3), cache for backward)."""
     ws = unflatten(weights, desc)
-    h = encode(q, desc.in_freqs)
+    corners = None
+    if desc.encoding == ENC_HASHGRID:
+        h, corners = hash_encode(weights, q, desc)
+    else:
+        h = encode(q, desc.in_freqs)
     ins, zs = [], []
     L = len(ws)
     for l, W in enumerate(ws):
@@ -191,19 +332,36 @@ def forward(weights: np.ndarray, q: np.ndarray, desc: FieldDesc, scales=None):
         ins.append(hin)
         zs.append(z)
         h = z if l == L - 1 else np.maximum(z, 0.0)
-    return h, (ins, zs)
+    return h, (ins, zs, corners)
 
 
 def backward(weights: np.ndarray, cache, dy: np.ndarray, desc: FieldDesc) -> np.ndarray:
-    """dW = sum_b (d yhat_b / dW)^T dy_b for every layer, flattened."""
+    """dW = sum_b (d yhat_b / dW)^T dy_b for every layer, flattened; for a
+    hash-grid field also the tables' gradient: the MLP input's gradient
+    d_in = d_0 W_0 (W_0 as the forward used it, the input's rounding taken as
+    the identity) spread over each level's corners with their interpolation
+    weights."""
     ws = unflatten(weights, desc)
-    ins, zs = cache
+    ins, zs, corners = cache
     L = len(ws)
     grads = [None] * L
     d = np.asarray(dy, np.float64)
     for l in range(L - 1, -1, -1):
         grads[l] = d.T @ ins[l]
         if l == 0:
+            if corners is not None:
+                W0 = ws[0] if L == 1 else rnd(ws[0], desc.prec)
+                d_in = d @ W0
+                out = np.zeros(desc.n_params())
+                mlp = flatten(grads)
+                out[:mlp.size] = mlp
+                col = 0
+                for off, F, idx, wgt in corners:
+                    contrib = wgt[:, :, None] * d_in[:, None, col:col + F]
+                    tgt = off + idx[:, :, None] * F + np.arange(F)[None, None, :]
+                    np.add.at(out, tgt.reshape(-1), contrib.reshape(-1))
+                    col += F
+                return out
             break
         Wq = ws[l] if l == L - 1 else rnd(ws[l], desc.prec)
         dh = d @ Wq
