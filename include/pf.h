@@ -106,11 +106,33 @@ typedef struct { int kind; float v[3]; float rgb[3]; } pf_light;
 typedef struct { float eye[3], at[3], up[3]; float fovy_deg; int width, height; } pf_camera;
 
 /* Photon field (Sec. 3.4): 6-D query (x, y, z, theta', phi', g) with theta',
- * phi' the outgoing direction in normalised spherical coordinates, frequency
- * encoding with in_freqs frequencies per input (12 * in_freqs features),
- * n_hidden ReLU layers of width `hidden` (64 or 128) without bias, a linear
- * 3-wide output predicting L' (the log-encoded radiance, Sec. 3.3.2), and
- * decode L = 10^(-psi L').  prec selects the hidden layers' arithmetic. */
+ * phi' the outgoing direction in normalised spherical coordinates, an input
+ * encoding, n_hidden ReLU layers of width `hidden` (32, 64 or 128) without
+ * bias, a linear 3-wide output predicting L' (the log-encoded radiance,
+ * Sec. 3.3.2), and decode L = 10^(-psi L').  prec selects the hidden layers'
+ * arithmetic.
+ * Encodings:
+ *   PF_ENC_FREQUENCY  sin / cos of 2^k pi v, k < in_freqs, for all six inputs
+ *                     (12 * in_freqs features);
+ *   PF_ENC_HASHGRID   the paper's multiresolution hash grids (Sec. 3.4, after
+ *                     Mueller et al. 2022): a 3-D grid over the position and
+ *                     a 2-D grid over (theta', phi'), each with hash_levels
+ *                     levels of hash_features features; level l has
+ *                     N_l = floor(hash_base_res * hash_scale^l) cells per axis
+ *                     (hash_scale^l as repeated FP64 products) and a table of
+ *                     min((N_l + 1)^d, 2^hash_log2_size) entries, indexed
+ *                     densely (x fastest) when the vertices fit and else by
+ *                     (xor of v_k pi_k, pi = 1, 2654435761, 805459861, 32-bit)
+ *                     mod 2^hash_log2_size; the cell is i = min(floor(p),
+ *                     N_l - 1) with p = clamp(v, 0, 1) * N_l in float32, and
+ *                     the features are multilinear in the corners; g enters
+ *                     raw.  MLP input: [position levels, direction levels, g]
+ *                     (2 L F + 1).  The tables follow the MLP weights in the
+ *                     flat parameter vector (see pf_field_num_params), each
+ *                     level on an 8-float boundary, initialised to
+ *                     (2u - 1) 1e-4 (Philox tag 4, item 64 + 16 grid + level).
+ *                     f32 / bf16 / f16 fields; SIMT kernels. */
+enum { PF_ENC_FREQUENCY = 0, PF_ENC_HASHGRID = 1 };
 typedef struct {
   int in_freqs;
   int hidden;
@@ -118,6 +140,12 @@ typedef struct {
   int prec;                 /* pf_prec */
   float psi;
   uint64_t seed;            /* Kaiming-uniform initialisation */
+  int encoding;             /* PF_ENC_FREQUENCY (0) or PF_ENC_HASHGRID */
+  int hash_levels;          /* [1, 16] */
+  int hash_features;        /* 1, 2, 4 or 8 */
+  int hash_log2_size;       /* [4, 24] */
+  int hash_base_res;        /* [1, 65536] */
+  float hash_scale;         /* [1, 4]; N_l must stay <= 2^22 */
 } pf_field_desc;
 
 /* Training (Sec. 3.5.1): Adam(beta1, beta2, eps), learning rate lr decayed by
@@ -272,8 +300,11 @@ pf_status pf_estimate_targets_knn(pf_ctx* ctx, const pf_cache* cache, const floa
  * u from Philox tag 4, item l, block e/4, lane e%4; w = (2u-1) sqrt(6/fan_in)). */
 pf_status pf_field_create(pf_ctx* ctx, const pf_field_desc* desc, pf_field** out);
 pf_status pf_field_free(pf_field* field);
-/* Number of float weights: layers [hidden x 12*in_freqs], (n_hidden-1) x
- * [hidden x hidden], [3 x hidden], each row-major [out][in], concatenated. */
+/* Number of float parameters: layers [hidden x n_in], (n_hidden-1) x
+ * [hidden x hidden], [3 x hidden], each row-major [out][in], concatenated
+ * (n_in = 12*in_freqs, or 2*L*F + 1 for hash grids); for hash grids then,
+ * from the next multiple of 8, the position grid's level tables and the
+ * direction grid's, each [entries][F] rounded up to 8 floats. */
 int64_t pf_field_num_params(const pf_field* field);
 pf_status pf_field_get_weights(pf_ctx* ctx, const pf_field* field, float* dst_dev);
 pf_status pf_field_set_weights(pf_ctx* ctx, pf_field* field, const float* src_dev);

@@ -38,6 +38,7 @@ def _declare(L):
     i32, i64, u32, u64, f64 = C.c_int, C.c_int64, C.c_uint32, C.c_uint64, C.c_double
     L.orc_philox.argtypes = [u64, P, P]
     L.orc_philox_stream.argtypes = [u64, u32, u32, i64, i32, P]
+    L.orc_philox_item.argtypes = [u64, u32, u32, u64, i64, P]
     L.orc_lnf.argtypes = [P, P, i64]
     L.orc_sincos2pif.argtypes = [P, P, P, i64]
     L.orc_hg_eval.argtypes = [f64, f64]
@@ -121,6 +122,13 @@ def philox_stream(seed: int, tag: int, sub: int, n_items: int, n_blocks: int) ->
     """Raw words [item][block][4] of the stream (seed, tag, sub)."""
     out = np.zeros((n_items, n_blocks, 4), np.uint32)
     lib().orc_philox_stream(seed, tag, sub, n_items, n_blocks, _p(out))
+    return out
+
+
+def philox_item(seed: int, tag: int, sub: int, item: int, n_blocks: int) -> np.ndarray:
+    """Raw words [block][4] of one item of the stream (seed, tag, sub)."""
+    out = np.zeros((n_blocks, 4), np.uint32)
+    lib().orc_philox_item(seed, tag, sub, item, n_blocks, _p(out))
     return out
 
 

@@ -60,7 +60,11 @@ class HashGrid:
     scale: float
 
     def res(self, l: int) -> int:
-        return int(math.floor(self.base_res * self.scale ** l))
+        # scale^l by repeated FP64 products of the float32 scale, as the library does
+        s = 1.0
+        for _ in range(l):
+            s *= float(np.float32(self.scale))
+        return int(math.floor(self.base_res * s))
 
     def dense(self, l: int) -> bool:
         return (self.res(l) + 1) ** self.dim <= 2 ** self.log2_size
@@ -150,7 +154,7 @@ def init_weights(desc: FieldDesc) -> np.ndarray:
     w = (2u - 1) sqrt(6/fan_in) evaluated in FP64, then rounded once.  Hash
     tables: element e of level l of grid j (0 position, 1 direction) draws u
     from item 64 + 16 j + l: w = (2u - 1) 1e-4; padding floats are 0."""
-    from . import philox_stream, uniform, TAG_INIT
+    from . import philox_item, philox_stream, uniform, TAG_INIT
     flat = []
     for l, (o, i) in enumerate(desc.shapes()):
         n = o * i
@@ -168,8 +172,7 @@ def init_weights(desc: FieldDesc) -> np.ndarray:
         for l in range(g.levels):
             n = g.entries(l) * g.features
             nb = (n + 3) // 4
-            item = 64 + 16 * j + l
-            words = philox_stream(desc.seed, TAG_INIT, 0, item + 1, nb)[item]
+            words = philox_item(desc.seed, TAG_INIT, 0, 64 + 16 * j + l, nb)
             u = uniform(words.reshape(-1)[:n])
             out[offs[l]:offs[l] + n] = ((2.0 * u - 1.0) * HASH_INIT).astype(np.float32)
     return out

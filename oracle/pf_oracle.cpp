@@ -858,6 +858,12 @@ void orc_philox_stream(uint64_t seed, uint32_t tag, uint32_t sub, int64_t n_item
     }
 }
 
+// Raw words [block][4] of one item of the stream (seed, tag, sub).
+void orc_philox_item(uint64_t seed, uint32_t tag, uint32_t sub, uint64_t item, int64_t n_blocks, uint32_t* out) {
+    Rng r(seed, tag, item, sub);
+    for (int64_t b = 0; b < n_blocks; ++b) r.raw4(out + (size_t)b * 4);
+}
+
 void orc_lnf(const float* x, float* y, int64_t n) { for (int64_t i = 0; i < n; ++i) y[i] = own_lnf(x[i]); }
 void orc_sincos2pif(const float* u, float* s, float* c, int64_t n) {
     for (int64_t i = 0; i < n; ++i) own_sincos2pif(u[i], s + i, c + i);

@@ -35,7 +35,9 @@ class PfCamera(C.Structure):
 
 class PfFieldDesc(C.Structure):
     _fields_ = [("in_freqs", C.c_int), ("hidden", C.c_int), ("n_hidden", C.c_int), ("prec", C.c_int),
-                ("psi", C.c_float), ("seed", C.c_uint64)]
+                ("psi", C.c_float), ("seed", C.c_uint64), ("encoding", C.c_int), ("hash_levels", C.c_int),
+                ("hash_features", C.c_int), ("hash_log2_size", C.c_int), ("hash_base_res", C.c_int),
+                ("hash_scale", C.c_float)]
 
 
 class PfTrainDesc(C.Structure):

@@ -238,11 +238,17 @@ def build_photon_cache(ctx: Context, vol: Volume, lights, g_set: Sequence[float]
 class Field:
     """pf_field: photon field network with library-owned weights."""
 
-    def __init__(self, ctx: Context, in_freqs=12, hidden=64, n_hidden=3, prec="f32", psi=5.0, seed=0):
+    def __init__(self, ctx: Context, in_freqs=12, hidden=64, n_hidden=3, prec="f32", psi=5.0, seed=0,
+                 encoding: str = "frequency", hash_levels=16, hash_features=8, hash_log2_size=19, hash_base_res=16,
+                 hash_scale=2.0):
+        """encoding "frequency" (in_freqs per input) or "hashgrid" (the
+        hash_* parameters; see pf_field_desc)."""
         self.ctx = ctx
         self.prec = prec
+        enc = {"frequency": 0, "hashgrid": 1}[encoding]
         self.desc = PfFieldDesc(int(in_freqs), int(hidden), int(n_hidden), PREC[prec] if isinstance(prec, str) else int(prec),
-                                float(psi), int(seed))
+                                float(psi), int(seed), enc, int(hash_levels), int(hash_features), int(hash_log2_size),
+                                int(hash_base_res), float(hash_scale))
         h = C.c_void_p()
         ctx.check(ctx.lib.pf_field_create(ctx.h, C.byref(self.desc), C.byref(h)))
         self.h = h

@@ -3,7 +3,8 @@
 //
 // This file holds the parts that are not tensor-core contractions:
 //   * seeded Kaiming-uniform initialisation;
-//   * the frequency encoding of the 6-D query;
+//   * the frequency encoding of the 6-D query, and the multiresolution
+//     hash-grid encoding (forward, and its tables' gradient);
 //   * a SIMT forward / backward (one thread per query, activations staged in
 //     shared memory column-per-thread) that serves float32 fields and rounds
 //     operands exactly as the tensor-core path specifies for the others;
@@ -45,6 +46,16 @@ __global__ void k_init(float* w, int64_t off, int64_t n, int layer, int fan_in, 
   double bound = sqrt(6.0 / (double)fan_in);
   w[off + e] = (float)((2.0 * u - 1.0) * bound);
 }
+
+// Hash-grid tables: w = (2u - 1) 1e-4 (Philox tag 4, item 64 + 16 grid + level).
+__global__ void k_init_table(float* w, int64_t off, int64_t n, int item, uint64_t seed) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  uint32_t o[4];
+  philox_block(seed, 4, (uint64_t)item, 0, (uint32_t)(e / 4), o);
+  double u = (double)(o[e % 4] >> 8) * (1.0 / 16777216.0);
+  w[off + e] = (float)((2.0 * u - 1.0) * 1e-4);
+}
 }  // namespace
 
 extern "C" pf_status pf_field_create(pf_ctx* ctx, const pf_field_desc* d, pf_field** out) {
@@ -57,11 +68,29 @@ extern "C" pf_status pf_field_create(pf_ctx* ctx, const pf_field_desc* d, pf_fie
   if (d->n_hidden < 1 || d->n_hidden > 8) return pf_fail(ctx, PF_ERR_INVALID_ARG, "n_hidden must be in [1, 8]");
   if (d->prec < 0 || d->prec > 3) return pf_fail(ctx, PF_ERR_INVALID_ARG, "unknown precision %d", d->prec);
   if (!(d->psi > 0.f)) return pf_fail(ctx, PF_ERR_INVALID_ARG, "psi must be > 0");
+  const bool hash = d->encoding == PF_ENC_HASHGRID;
+  if (d->encoding != PF_ENC_FREQUENCY && !hash) return pf_fail(ctx, PF_ERR_INVALID_ARG, "unknown encoding");
+  int hres[2][16] = {};
+  if (hash) {
+    const int F = d->hash_features;
+    if (d->hash_levels < 1 || d->hash_levels > 16 || (F != 1 && F != 2 && F != 4 && F != 8) ||
+        d->hash_log2_size < 4 || d->hash_log2_size > 24 || d->hash_base_res < 1 || d->hash_base_res > 65536 ||
+        !(d->hash_scale >= 1.f && d->hash_scale <= 4.f))
+      return pf_fail(ctx, PF_ERR_INVALID_ARG, "bad hash-grid parameters");
+    if (d->prec == PF_PREC_FP8) return pf_fail(ctx, PF_ERR_UNSUPPORTED, "hash-grid fields are f32, bf16 or f16");
+    double s = 1.0;
+    for (int l = 0; l < d->hash_levels; ++l) {
+      const double n = std::floor((double)d->hash_base_res * s);
+      if (n > (double)(1 << 22)) return pf_fail(ctx, PF_ERR_INVALID_ARG, "hash-grid level finer than 2^22 cells");
+      hres[0][l] = hres[1][l] = (int)n;
+      s *= (double)d->hash_scale;
+    }
+  }
   pf_field* f = new pf_field();
   f->ctx = ctx;
   f->device = ctx->device;
   f->desc = *d;
-  f->n_in = 12 * d->in_freqs;
+  f->n_in = hash ? 2 * d->hash_levels * d->hash_features + 1 : 12 * d->in_freqs;
   f->n_layers = d->n_hidden + 1;
   int64_t off = 0;
   for (int l = 0; l < f->n_layers; ++l) {
@@ -71,6 +100,23 @@ extern "C" pf_status pf_field_create(pf_ctx* ctx, const pf_field_desc* d, pf_fie
     off += (int64_t)f->fan_in[l] * f->fan_out[l];
   }
   f->layer_off[f->n_layers] = off;
+  if (hash) {
+    off = (off + 7) / 8 * 8;
+    const double T = std::ldexp(1.0, d->hash_log2_size);
+    for (int gi = 0; gi < 2; ++gi) {
+      const int D = gi == 0 ? 3 : 2;
+      for (int l = 0; l < d->hash_levels; ++l) {
+        const int N = hres[gi][l];
+        const double verts = std::pow((double)N + 1.0, D);
+        const bool dense = verts <= T;
+        f->hash_res[gi][l] = N;
+        f->hash_entries[gi][l] = (uint32_t)(dense ? verts : T);
+        if (dense) f->hash_dense[gi] |= 1u << l;
+        f->hash_off[gi][l] = off;
+        off += ((int64_t)f->hash_entries[gi][l] * d->hash_features + 7) / 8 * 8;
+      }
+    }
+  }
   f->n_params = off;
   size_t bytes = (size_t)off * sizeof(float);
   if (cudaMalloc(&f->w, bytes) != cudaSuccess || cudaMalloc(&f->m, bytes) != cudaSuccess ||
@@ -80,6 +126,7 @@ extern "C" pf_status pf_field_create(pf_ctx* ctx, const pf_field_desc* d, pf_fie
     delete f;
     return pf_fail(ctx, PF_ERR_OOM, "field allocation failed");
   }
+  cudaMemsetAsync(f->w, 0, bytes, ctx->stream);
   cudaMemsetAsync(f->m, 0, bytes, ctx->stream);
   cudaMemsetAsync(f->v, 0, bytes, ctx->stream);
   cudaMemsetAsync(f->scales, 0, 64 * sizeof(float), ctx->stream);
@@ -87,6 +134,13 @@ extern "C" pf_status pf_field_create(pf_ctx* ctx, const pf_field_desc* d, pf_fie
     int64_t n = (int64_t)f->fan_in[l] * f->fan_out[l];
     k_init<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(f->w, f->layer_off[l], n, l, f->fan_in[l], d->seed);
   }
+  if (hash)
+    for (int gi = 0; gi < 2; ++gi)
+      for (int l = 0; l < d->hash_levels; ++l) {
+        const int64_t n = (int64_t)f->hash_entries[gi][l] * d->hash_features;
+        k_init_table<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(f->w, f->hash_off[gi][l], n,
+                                                                           64 + 16 * gi + l, d->seed);
+      }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { pf_field_free(f); return pf_cuda_check(ctx, e, "field init"); }
   pf_status st = pf_field_pack(ctx, f);
@@ -132,6 +186,12 @@ struct FieldView {
   int n_layers, n_in, hidden, in_freqs, prec;
   float psi;
   float s_a[8], s_w[8];
+  // hash-grid encoding (enc == PF_ENC_HASHGRID)
+  int enc, hl, hf;
+  int hres[2][16];
+  uint32_t hent[2][16];
+  uint32_t hdense[2];
+  int64_t hoff[2][16];
 };
 
 FieldView view_of(const pf_field* f) {
@@ -143,12 +203,122 @@ FieldView view_of(const pf_field* f) {
   v.n_layers = f->n_layers; v.n_in = f->n_in; v.hidden = f->desc.hidden; v.in_freqs = f->desc.in_freqs;
   v.prec = f->desc.prec; v.psi = f->desc.psi;
   for (int l = 0; l < 8; ++l) { v.s_a[l] = f->scales_host[l]; v.s_w[l] = f->scales_host[16 + l]; }
+  v.enc = f->desc.encoding;
+  v.hl = f->desc.hash_levels;
+  v.hf = f->desc.hash_features;
+  for (int gi = 0; gi < 2; ++gi) {
+    v.hdense[gi] = f->hash_dense[gi];
+    for (int l = 0; l < 16; ++l) {
+      v.hres[gi][l] = f->hash_res[gi][l];
+      v.hent[gi][l] = f->hash_entries[gi][l];
+      v.hoff[gi][l] = f->hash_off[gi][l];
+    }
+  }
   return v;
+}
+
+// ---- multiresolution hash grids (Sec. 3.4): grid gi (0: x, y, z; 1: theta',
+// phi'), level l.  The cell holding x: p = clamp(x, 0, 1) * N_l in float32,
+// i = min(floor(p), N_l - 1), fraction p - i (exact).
+template <int D>
+__device__ __forceinline__ void hash_cell(const FieldView& F, int gi, int l, const float* x, uint32_t i0[D],
+                                          float fr[D]) {
+  const int N = F.hres[gi][l];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const float p = __fmul_rn(fminf(fmaxf(x[k], 0.f), 1.f), (float)N);
+    const int i = min((int)floorf(p), N - 1);
+    i0[k] = (uint32_t)i;
+    fr[k] = __fsub_rn(p, (float)i);
+  }
+}
+
+// Table entry of corner c (bit k: +1 along axis k): dense x-fastest index, or
+// the spatial hash xor_k v_k pi_k (pi = 1, 2654435761, 805459861) modulo the
+// table size (a power of two).
+template <int D>
+__device__ __forceinline__ uint32_t hash_index(const FieldView& F, int gi, int l, const uint32_t i0[D], int c) {
+  uint32_t v[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) v[k] = i0[k] + ((c >> k) & 1);
+  if ((F.hdense[gi] >> l) & 1u) {
+    const uint32_t n1 = (uint32_t)F.hres[gi][l] + 1u;
+    uint32_t idx = v[D - 1];
+#pragma unroll
+    for (int k = D - 2; k >= 0; --k) idx = idx * n1 + v[k];
+    return idx;
+  }
+  uint32_t h = v[0] ^ (v[1] * 2654435761u);
+  if (D == 3) h ^= v[D - 1] * 805459861u;
+  return h & (F.hent[gi][l] - 1u);
+}
+
+// Multilinear weight of corner c: prod_k (bit k ? f_k : 1 - f_k).
+template <int D>
+__device__ __forceinline__ float corner_weight(const float fr[D], int c) {
+  float w = 1.f;
+#pragma unroll
+  for (int k = 0; k < D; ++k) w *= ((c >> k) & 1) ? fr[k] : 1.f - fr[k];
+  return w;
+}
+
+// The F features of level l of grid gi at x.
+template <int D>
+__device__ __forceinline__ void hash_features(const FieldView& F, int gi, int l, const float* x, float acc[8]) {
+  uint32_t i0[D];
+  float fr[D];
+  hash_cell<D>(F, gi, l, x, i0, fr);
+  const float* tab = F.w + F.hoff[gi][l];
+#pragma unroll
+  for (int f = 0; f < 8; ++f) acc[f] = 0.f;
+#pragma unroll
+  for (int c = 0; c < (1 << D); ++c) {
+    const float* e = tab + (size_t)hash_index<D>(F, gi, l, i0, c) * F.hf;
+    const float w = corner_weight<D>(fr, c);
+#pragma unroll
+    for (int f = 0; f < 8; ++f)
+      if (f < F.hf) acc[f] = fmaf(w, __ldg(e + f), acc[f]);
+  }
+}
+
+// Spreads the gradient dx of level l's features over its corners' entries.
+template <int D>
+__device__ __forceinline__ void hash_scatter(const FieldView& F, int gi, int l, const float* x, const float dx[8],
+                                             float* dw) {
+  uint32_t i0[D];
+  float fr[D];
+  hash_cell<D>(F, gi, l, x, i0, fr);
+  float* tab = dw + F.hoff[gi][l];
+#pragma unroll
+  for (int c = 0; c < (1 << D); ++c) {
+    float* e = tab + (size_t)hash_index<D>(F, gi, l, i0, c) * F.hf;
+    const float w = corner_weight<D>(fr, c);
+#pragma unroll
+    for (int f = 0; f < 8; ++f)
+      if (f < F.hf) atomicAdd(e + f, w * dx[f]);
+  }
+}
+
+// MLP input of a hash-grid field: [position levels, direction levels, g],
+// F features per level; column k of the thread's query goes to buf[k * T + tid].
+template <int T>
+__device__ __forceinline__ void hash_encode(const FieldView& F, const float* q, int tid, float* buf) {
+  const int LF = F.hl * F.hf;
+  for (int gi = 0; gi < 2; ++gi)
+    for (int l = 0; l < F.hl; ++l) {
+      float acc[8];
+      if (gi == 0) hash_features<3>(F, 0, l, q, acc);
+      else hash_features<2>(F, 1, l, q + 3, acc);
+#pragma unroll
+      for (int f = 0; f < 8; ++f)
+        if (f < F.hf) buf[(gi * LF + l * F.hf + f) * T + tid] = acc[f];
+    }
+  buf[(2 * LF) * T + tid] = q[5];
 }
 
 constexpr int kSimtThreads = 64;   // forward: queries per block
 constexpr int kBwdThreads = 32;    // backward: queries per block (one warp)
-constexpr int kMaxK = 192;         // 12 * 16 frequencies
+constexpr int kMaxK = 272;         // MLP inputs: 12 * 16 frequencies, or 2 * 16 * 8 + 1 hash-grid features
 
 // Operand rounding of the hidden layers (see pf_field_common.cuh).
 __device__ __forceinline__ float rin(float x, int prec, float s) { return round_prec(x, prec, s); }
@@ -160,7 +330,8 @@ template <int T>
 __device__ void simt_forward(const FieldView& F, const float* q, int tid, float* bufA, float* bufB, float* keep,
                              const int* koff, float y[3]) {
   // encoding -> bufA (rounded to the first layer's input precision)
-  for (int d = 0; d < 6; ++d) {
+  if (F.enc == PF_ENC_HASHGRID) hash_encode<T>(F, q, tid, bufA);
+  else for (int d = 0; d < 6; ++d) {
     float v = q[d];
     for (int k = 0; k < F.in_freqs; ++k) {
       float s, c;
@@ -280,7 +451,28 @@ __global__ void __launch_bounds__(kBwdThreads) k_simt_backward(FieldView F, cons
       for (int t = 0; t < T; ++t) s = fmaf(dcur[n * T + t], xin[k * T + t], s);
       atomicAdd(&dw[F.off[l] + e], s);
     }
-    if (l == 0) break;
+    if (l == 0) {
+      if (F.enc == PF_ENC_HASHGRID && act) {
+        // input gradient W_0^T dcur, level by level, spread over the corners
+        const float* W0 = F.wr + F.off[0];
+        const int LF = F.hl * F.hf;
+        for (int gi = 0; gi < 2; ++gi)
+          for (int lv = 0; lv < F.hl; ++lv) {
+            const int col = gi * LF + lv * F.hf;
+            float dx[8];
+#pragma unroll
+            for (int f = 0; f < 8; ++f) {
+              float a = 0.f;
+              if (f < F.hf)
+                for (int n = 0; n < N; ++n) a = fmaf(dcur[n * T + tid], __ldg(W0 + (size_t)n * K + col + f), a);
+              dx[f] = a;
+            }
+            if (gi == 0) hash_scatter<3>(F, 0, lv, qq, dx, dw);
+            else hash_scatter<2>(F, 1, lv, qq + 3, dx, dw);
+          }
+      }
+      break;
+    }
     // gradient w.r.t. the input of layer l: W^T dcur, masked by the ReLU of
     // layer l-1 (taken from the rounded activation) and rounded
     for (int k = 0; k < K; ++k) {
@@ -426,7 +618,52 @@ pf_status pf_tc_backward_available(const pf_field* f);
 pf_status pf_tc_forward(pf_ctx* ctx, const pf_field* f, const float* q, int64_t B_max, const uint32_t* B_dev, float* out,
                         const uint32_t* slot_idx, const float* slot_alb, float* slot_li);
 pf_status pf_tc_backward(pf_ctx* ctx, const pf_field* f, const float* q, const float* dy, const float* targets,
-                         int64_t B, float* dw, float* loss);
+                         int64_t B, float* dw, float* loss, const uint16_t* x_in, float* dx_out);
+
+namespace {
+// Hash-grid features of the tensor-core training step: one thread per
+// (query, grid, level); the level's F features rounded to the field
+// precision at x[b][(grid * L + level) * F ...] (x: [B][2 L F] 16-bit).
+template <int PREC>
+__global__ void k_hash_features(FieldView F, const float* __restrict__ q, int64_t B, uint16_t* __restrict__ x) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int per = 2 * F.hl;
+  if (t >= B * per) return;
+  const int64_t b = t / per;
+  const int j = (int)(t % per), gi = j / F.hl, l = j % F.hl;
+  float v[3];
+  for (int k = 0; k < 3; ++k) v[k] = q[6 * b + (gi == 0 ? k : 3 + (k < 2 ? k : 1))];
+  float acc[8];
+  if (gi == 0) hash_features<3>(F, 0, l, v, acc);
+  else hash_features<2>(F, 1, l, v, acc);
+  uint16_t* dst = x + (size_t)b * (2 * F.hl * F.hf) + (size_t)j * F.hf;
+#pragma unroll
+  for (int f = 0; f < 8; ++f) {
+    if (f >= F.hf) break;
+    dst[f] = PREC == PF_PREC_BF16 ? __bfloat16_as_ushort(__float2bfloat16_rn(acc[f]))
+                                  : __half_as_ushort(__float2half_rn(acc[f]));
+  }
+}
+
+// Spreads the features' gradient dx [B][2 L F] over the level tables' corners
+// (one thread per (query, grid, level)).
+__global__ void k_hash_scatter(FieldView F, const float* __restrict__ q, const float* __restrict__ dx, int64_t B,
+                               float* __restrict__ dw) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int per = 2 * F.hl;
+  if (t >= B * per) return;
+  const int64_t b = t / per;
+  const int j = (int)(t % per), gi = j / F.hl, l = j % F.hl;
+  float v[3];
+  for (int k = 0; k < 3; ++k) v[k] = q[6 * b + (gi == 0 ? k : 3 + (k < 2 ? k : 1))];
+  const float* src = dx + (size_t)b * (2 * F.hl * F.hf) + (size_t)j * F.hf;
+  float d[8];
+#pragma unroll
+  for (int f = 0; f < 8; ++f) d[f] = f < F.hf ? src[f] : 0.f;
+  if (gi == 0) hash_scatter<3>(F, 0, l, v, d, dw);
+  else hash_scatter<2>(F, 1, l, v, d, dw);
+}
+}  // namespace
 
 pf_status pf_field_forward_impl(pf_ctx* ctx, const pf_field* f, const float* q, int64_t B_max, const uint32_t* B_dev,
                                 float* out, const uint32_t* slot_idx, const float* slot_alb, float* slot_li) {
@@ -448,8 +685,29 @@ extern "C" pf_status pf_field_forward(pf_ctx* ctx, const pf_field* f, const floa
 pf_status pf_field_backward_impl(pf_ctx* ctx, const pf_field* f, const float* q, const float* dy, const float* targets,
                                  int64_t B, float* dw, float* loss) {
   if (f->desc.prec == PF_PREC_FP8) return pf_fail(ctx, PF_ERR_UNSUPPORTED, "fp8 fields are inference-only");
-  // the tensor-core backward writes every element of dw
-  if (B > 0 && pf_tc_backward_available(f) == PF_OK) return pf_tc_backward(ctx, f, q, dy, targets, B, dw, loss);
+  if (B > 0 && pf_tc_backward_available(f) == PF_OK) {
+    if (f->desc.encoding != PF_ENC_HASHGRID)   // the tensor-core backward writes every element of dw
+      return pf_tc_backward(ctx, f, q, dy, targets, B, dw, loss, nullptr, nullptr);
+    // hash grids: table features (gather), the MLP on tcgen05 (which writes
+    // the MLP's dW and the features' gradient), then the table scatter
+    const FieldView F = view_of(f);
+    const int nf = 2 * F.hl * F.hf;
+    uint16_t* x;
+    float* dx;
+    PF_TRY(pf_scratch(ctx, WS_HASH_X, (size_t)B * nf * sizeof(uint16_t), (void**)&x));
+    PF_TRY(pf_scratch(ctx, WS_HASH_DX, (size_t)B * nf * sizeof(float), (void**)&dx));
+    const int64_t n_thr = B * 2 * F.hl;
+    const unsigned grid = (unsigned)((n_thr + 255) / 256);
+    if (f->desc.prec == PF_PREC_BF16) k_hash_features<PF_PREC_BF16><<<grid, 256, 0, ctx->stream>>>(F, q, B, x);
+    else k_hash_features<PF_PREC_F16><<<grid, 256, 0, ctx->stream>>>(F, q, B, x);
+    PF_CUDA(ctx, cudaGetLastError());
+    const int64_t n_mlp = f->layer_off[f->n_layers];
+    PF_CUDA(ctx, cudaMemsetAsync(dw + n_mlp, 0, (size_t)(f->n_params - n_mlp) * sizeof(float), ctx->stream));
+    PF_TRY(pf_tc_backward(ctx, f, q, dy, targets, B, dw, loss, x, dx));
+    k_hash_scatter<<<grid, 256, 0, ctx->stream>>>(F, q, dx, B, dw);
+    PF_CUDA(ctx, cudaGetLastError());
+    return PF_OK;
+  }
   PF_CUDA(ctx, cudaMemsetAsync(dw, 0, f->n_params * sizeof(float), ctx->stream));
   if (B == 0) return PF_OK;
   return pf_simt_backward(ctx, f, q, dy, targets, B, dw, loss);

@@ -14,7 +14,7 @@ enum : uint32_t { PFE_ITER_CAP = 1u, PFE_NONFINITE = 2u, PFE_OVERFLOW = 4u };
 // Scratch slots of the context arena.
 enum ScratchSlot {
   WS_REDUCE = 0, WS_SCAN, WS_QUERY, WS_TARGET, WS_ACT, WS_GRAD, WS_SAMPLES, WS_SLOT_LD, WS_SLOT_ALB,
-  WS_SLOT_LI, WS_COMPACT_Q, WS_COMPACT_IDX, WS_LOSS, WS_MISC, WS_GRID, WS_COMPACT_DIR, WS_CELL_HIST, WS_CELL_OFF, WS_CELL_KEY, WS_CELL_PERM, WS_VMASK, WS_GRID_PRIMARY, WS_GRID_SHADOW, WS_COUNT
+  WS_SLOT_LI, WS_COMPACT_Q, WS_COMPACT_IDX, WS_LOSS, WS_MISC, WS_GRID, WS_COMPACT_DIR, WS_CELL_HIST, WS_CELL_OFF, WS_CELL_KEY, WS_CELL_PERM, WS_VMASK, WS_GRID_PRIMARY, WS_GRID_SHADOW, WS_HASH_X, WS_HASH_DX, WS_COUNT
 };
 
 struct pf_ctx {
@@ -70,6 +70,13 @@ struct pf_field {
   float scales_host[32] = {};
   int fp8_ready = 0;
   int step = 0;                       // Adam step counter
+  // hash-grid encoding: per grid (0 position, 1 direction) and level the
+  // cells per axis, table entries, dense flag (bit l) and the float offset of
+  // the level's table in the flat parameters
+  int hash_res[2][16] = {};
+  uint32_t hash_entries[2][16] = {};
+  uint32_t hash_dense[2] = {};
+  int64_t hash_off[2][16] = {};
 };
 
 // Stage timing (PF_STAGE_* of pf.h): wraps a stage's launches in events.

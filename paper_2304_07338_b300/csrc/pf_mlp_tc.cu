@@ -312,8 +312,16 @@ struct TrArgs {
   uint32_t hs_off;          // last hidden activations of the tile (128 x H float32, rows rotated)
   uint32_t dys_off;         // output-layer gradients of the tile (128 x 4 float32)
   uint32_t dw_col[kMaxLayers];  // TMEM column of dW_l
+  uint32_t g_off;           // hash grids: [H] g weights, [H] dW of the g column, [128] g of the rows
   int64_t layer_off[kMaxLayers + 1];
-  int64_t n_params;
+  int64_t n_params;         // MLP weights (the partial rows' stride)
+  // hash-grid fields: layer 0's operand is the nf = 2 L F table features
+  // (x_in, [B][nf] in the field precision); g (fan0 = nf + 1 inputs) enters
+  // on the CUDA cores; dx_out [B][nf] receives the features' gradient
+  int hash, fan0, nf;
+  const uint16_t* x_in;
+  float* dx_out;
+  const float* w0;          // layer 0 master weights [H][fan0]
 };
 constexpr uint32_t kTrainCols = 512;
 constexpr int kTrainHidden = 64;
@@ -330,12 +338,24 @@ __device__ __forceinline__ void store8(uint8_t* tile, uint32_t kp, int r, int ch
   store_chunk(tile, kp * 2, r, chunk, q);
 }
 
+// One 16-bit operand (bf16 or f16 bits) as a float.
+template <int PREC>
+__device__ __forceinline__ float op_value(uint16_t h) {
+  if (PREC == PF_PREC_BF16) return __bfloat162float(__ushort_as_bfloat16(h));
+  return __half2float(__ushort_as_half(h));
+}
+
 // Fused forward + loss + backward for a 128-query tile, two warpgroups: the
 // thread pair (r, r + 128) owns tile row r, and the two threads split the
-// row's columns (encoding inputs 0-2 / 3-5; neurons 0-31 / 32-63), so that
-// each SM sub-partition has two warps to switch between while the other
-// waits.  TMEM lane quarter of warp w: w mod 4.
-template <int PREC>
+// row's columns (encoding inputs 0-2 / 3-5, or the position / direction
+// halves of the hash-grid features; neurons 0-31 / 32-63), so that each SM
+// sub-partition has two warps to switch between while the other waits.
+// TMEM lane quarter of warp w: w mod 4.
+// HASH: layer 0's operand is the table features from x_in; g's term
+// W_0[:, nf] g is added on the CUDA cores before the ReLU, its weight
+// gradient summed on them too, and the features' gradient dZ_0 W_0 is
+// written to dx_out for the table scatter.
+template <int PREC, bool HASH>
 __global__ void __launch_bounds__(kTrainThreads, 1) k_tc_train(TrArgs T, const float* __restrict__ q,
                                                                const float* __restrict__ targets,
                                                                const float* __restrict__ dy_in, int64_t B, float inv_n,
@@ -359,6 +379,9 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_tc_train(TrArgs T, const f
   float* hs = (float*)(smem + T.hs_off);
   float* dys = (float*)(smem + T.dys_off);      // [128][4]: dy of the row
   float* ys = dys + 4 * kTileM;                  // [128][4]: second half's partial output
+  float* wg = (float*)(smem + T.g_off);          // hash grids: [H] rounded g weights of layer 0
+  float* dwg = wg + H;                           // [H] dW of layer 0's g column
+  float* gs = dwg + H;                           // [128] rounded g of the tile's rows
 
   if (tid == 0) {
     mbar_init(bar_w, 1);
@@ -367,6 +390,12 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_tc_train(TrArgs T, const f
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   for (int i = tid; i < 3 * H; i += kTrainThreads) { w_out[i] = A.w_out[i]; dwo[i] = 0.f; }
+  if (HASH)
+    for (int i = tid; i < H; i += kTrainThreads) {
+      const float wv = T.w0[(size_t)i * T.fan0 + T.nf];
+      wg[i] = PREC == PF_PREC_BF16 ? pff::round_bf16(wv) : pff::round_f16(wv);
+      dwg[i] = 0.f;
+    }
   // zero the padded neuron columns of the dZ tile once (never written later)
   for (int i = tid; i < (int)(kTileM * kDK * 2 / 16); i += kTrainThreads) ((uint4*)dtile)[i] = make_uint4(0, 0, 0, 0);
   if (warp == 0) tmem_alloc(tmem_slot, kTrainCols);
@@ -409,7 +438,17 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_tc_train(TrArgs T, const f
     // ---- encoding -> A_0
     {
       uint8_t* a0 = smem + T.a_off[0];
-      if (F == 12) {
+      if (HASH) {
+        // this thread: half hf of the row's table features, as 16-byte chunks
+        const int nc = T.nf / 16;
+        const uint4* src = (const uint4*)(T.x_in + (size_t)(valid ? row : 0) * T.nf);
+        for (int c = hf * nc; c < (hf + 1) * nc; ++c)
+          store_chunk(a0, kp0 * 2, r, c, valid ? __ldg(src + c) : make_uint4(0, 0, 0, 0));
+        if (hf == 0) {
+          const float gv = valid ? __ldg(q + 6 * row + 5) : 0.f;
+          gs[r] = PREC == PF_PREC_BF16 ? pff::round_bf16(gv) : pff::round_f16(gv);
+        }
+      } else if (F == 12) {
         // this thread: inputs 3 hf .. 3 hf + 2 = features 72 hf .. 72 hf + 71
         float buf[8];
 #pragma unroll
@@ -454,6 +493,11 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_tc_train(TrArgs T, const f
         const int c0 = HH * hf + 16 * g;
         float v[16];
         tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
+        if (HASH && l == 0) {
+          const float gr = gs[r];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] = fmaf(wg[c0 + i], gr, v[i]);
+        }
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
         if (l == L - 1) {
@@ -511,6 +555,13 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_tc_train(TrArgs T, const f
 #pragma unroll 8
       for (int rr = 0; rr < kTileM; ++rr) acc = fmaf(dys[4 * rr + c], hs[rr * H + ((n + rr) & (H - 1))], acc);
       dwo[o] += acc;
+    }
+    // hs shares the dZ tile's bytes: from here on it is dead; restore the
+    // tile's zero padding (neurons H .. kDK - 1) before dZ_{L-1} goes in
+    __syncthreads();
+    for (int i = tid; i < kTileM * (int)(kDK - H) / 8; i += kTrainThreads) {
+      const int per = (int)(kDK - H) / 8;
+      store_chunk(dtile, kDK * 2, i / per, H / 8 + i % per, make_uint4(0, 0, 0, 0));
     }
     // dZ_{L-1} = (dy W_out) * [rounded h > 0], this thread's columns
 #pragma unroll
@@ -577,6 +628,49 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_tc_train(TrArgs T, const f
           store16<PREC>(dtile, kDK, r, c0, v);
         }
       }
+      if (HASH && l == 0) {
+        // dW of the g column: one owner thread per neuron over the tile's rows
+        for (int n = tid; n < H; n += kTrainThreads) {
+          float acc = 0.f;
+          for (int rr = 0; rr < kTileM; ++rr) {
+            const uint32_t off = (uint32_t)(rr >> 3) * d_rg + (uint32_t)(n >> 3) * 128 + (uint32_t)(rr & 7) * 16 +
+                                 (uint32_t)(n & 7) * 2;
+            acc = fmaf(op_value<PREC>(*(const uint16_t*)(dtile + off)), gs[rr], acc);
+          }
+          dwg[n] += acc;
+        }
+        // the features' gradient dZ_0 W_0 (W_0 rounded, as packed): this
+        // thread's half of the row
+        if (valid) {
+          float dz[H];
+#pragma unroll
+          for (int c = 0; c < H / 8; ++c) {
+            const uint4 raw = *(const uint4*)(dtile + (uint32_t)(r >> 3) * d_rg + (uint32_t)c * 128 +
+                                              (uint32_t)(r & 7) * 16);
+            const uint16_t* hv = (const uint16_t*)&raw;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) dz[8 * c + i] = op_value<PREC>(hv[i]);
+          }
+          const uint8_t* w0p = smem + A.L[0].w_off;
+          const int nc = T.nf / 16;
+          float* dst = T.dx_out + (size_t)row * T.nf;
+          for (int c = hf * nc; c < (hf + 1) * nc; ++c) {
+            float acc[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) acc[i] = 0.f;
+#pragma unroll 8
+            for (int n = 0; n < H; ++n) {
+              const uint4 raw = *(const uint4*)(w0p + ((uint32_t)(n >> 3) * (kp0 / 8) + (uint32_t)c) * 128 +
+                                                (uint32_t)(n & 7) * 16);
+              const uint16_t* hv = (const uint16_t*)&raw;
+#pragma unroll
+              for (int i = 0; i < 8; ++i) acc[i] = fmaf(dz[n], op_value<PREC>(hv[i]), acc[i]);
+            }
+            ((float4*)(dst + 8 * c))[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+            ((float4*)(dst + 8 * c))[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+          }
+        }
+      }
     }
     first_tile = false;
   }
@@ -589,7 +683,8 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_tc_train(TrArgs T, const f
     const int m = (warp & 3) * 32 + lane;            // output neuron of this lane
     for (int l = 0; l < L; ++l) {
       const uint32_t kpl = A.L[l].kp;
-      const int fan = l == 0 ? 12 * F : H;
+      const int fan = l == 0 ? T.fan0 : H;           // row stride of W_l
+      const int ncol = l == 0 ? T.nf : H;            // columns accumulated in TMEM
       for (uint32_t c0 = 16 * hf; c0 < kpl; c0 += 32) {
         float v[16];
         if (first_tile) {
@@ -600,11 +695,13 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_tc_train(TrArgs T, const f
         }
 #pragma unroll
         for (int i = 0; i < 16; ++i)
-          if ((int)c0 + i < fan) part[T.layer_off[l] + (int64_t)m * fan + c0 + i] = v[i];
+          if ((int)c0 + i < ncol) part[T.layer_off[l] + (int64_t)m * fan + c0 + i] = v[i];
       }
     }
   }
   __syncthreads();
+  if (HASH)
+    for (int n = tid; n < H; n += kTrainThreads) part[T.layer_off[0] + (int64_t)n * T.fan0 + T.nf] = dwg[n];
   for (int i = tid; i < 3 * H; i += kTrainThreads) part[T.layer_off[L] + i] = dwo[i];
   if (loss) {
     for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
@@ -680,10 +777,14 @@ __global__ void k_round_weights(const float* __restrict__ w, float* __restrict__
   wr[i] = pff::round_prec(w[i], prec, B.s_w[l]);
 }
 
-// Shared-memory plan of a field for k_tc_forward.
-bool plan(const pf_field* f, TcArgs* A) {
+// Shared-memory plan of a field for k_tc_forward (hash-grid fields: only as
+// the first part of the training plan; their layer-0 operand is the 2 L F
+// table features, g is added on the CUDA cores).
+bool plan(const pf_field* f, TcArgs* A, bool for_train = false) {
   const int prec = f->desc.prec;
   if (prec == PF_PREC_F32) return false;
+  const bool hash = f->desc.encoding == PF_ENC_HASHGRID;
+  if (hash && (!for_train || (f->n_in - 1) % 16 != 0 || f->n_in - 1 > 256)) return false;
   const int H = f->desc.hidden;
   if (H != 64 && H != 128) return false;
   const int nh = f->n_layers - 1;
@@ -698,6 +799,7 @@ bool plan(const pf_field* f, TcArgs* A) {
   uint32_t off = 0, kmax = 0;
   for (int l = 0; l < nh; ++l) {
     uint32_t k = (uint32_t)f->fan_in[l];
+    if (hash && l == 0) k -= 1;              // the g column is not an MMA operand
     uint32_t kp = (k + A->kstep - 1) / A->kstep * A->kstep;
     A->L[l].w_off = off;
     A->L[l].kp = kp;
@@ -753,11 +855,14 @@ namespace {
 bool plan_train(const pf_field* f, TrArgs* T) {
   if (f->desc.prec != PF_PREC_BF16 && f->desc.prec != PF_PREC_F16) return false;
   if (f->desc.hidden != kTrainHidden) return false;
-  if (!plan(f, &T->f)) return false;
+  if (!plan(f, &T->f, true)) return false;
   const int L = T->f.n_hidden;
   const int H = T->f.hidden;
+  T->hash = f->desc.encoding == PF_ENC_HASHGRID ? 1 : 0;
+  T->fan0 = f->fan_in[0];
+  T->nf = T->hash ? f->fan_in[0] - 1 : f->fan_in[0];
   uint32_t off = T->f.a_off;                 // weights first, then the activation tiles
-  uint32_t col = 128;
+  uint32_t col = (uint32_t)H;                // columns [0, H): forward and dA accumulators
   for (int l = 0; l < L; ++l) {
     T->a_off[l] = off;
     off += kTileM * T->f.L[l].kp * 2;
@@ -768,19 +873,23 @@ bool plan_train(const pf_field* f, TrArgs* T) {
   off = (off + 1023) / 1024 * 1024;
   T->d_off = off;
   off += kTileM * kDK * 2;
+  // the last activations (float32, for dW_out) share the dZ tile's bytes:
+  // they are dead before dZ_{L-1} is written
+  T->hs_off = T->d_off;
+  static_assert(kTileM * kDK * 2 == kTileM * kTrainHidden * 4, "hs must fit the dZ tile");
   T->f.wout_off = off;
   off += 3 * H * 4;
   T->dwo_off = off;
   off += 3 * H * 4;
+  T->g_off = off;                            // hash grids: g weights, g per row, dW of the g column
+  off += (2 * H + kTileM) * 4;
   off = (off + 15) / 16 * 16;
-  T->hs_off = off;
-  off += kTileM * H * 4;
   T->dys_off = off;
   off += 2 * kTileM * 4 * 4;                 // dy and the pair's partial outputs
   T->f.bar_off = (off + 15) / 16 * 16;
   T->f.smem_bytes = T->f.bar_off + 64;
   for (int l = 0; l <= f->n_layers; ++l) T->layer_off[l] = f->layer_off[l];
-  T->n_params = f->n_params;
+  T->n_params = f->layer_off[f->n_layers];   // the MLP's weights (hash tables are scattered separately)
   return T->f.smem_bytes <= 227 * 1024;
 }
 }  // namespace
@@ -791,15 +900,19 @@ pf_status pf_tc_backward_available(const pf_field* f) {
 }
 
 pf_status pf_tc_backward(pf_ctx* ctx, const pf_field* f, const float* q, const float* dy, const float* targets,
-                         int64_t B, float* dw, float* loss) {
+                         int64_t B, float* dw, float* loss, const uint16_t* x_in, float* dx_out) {
   TrArgs T;
   if (!plan_train(f, &T)) return pf_fail(ctx, PF_ERR_UNSUPPORTED, "field shape not supported by the tensor-core backward");
+  if (T.hash && (!x_in || !dx_out)) return pf_fail(ctx, PF_ERR_INVALID_ARG, "hash-grid backward needs its features");
   T.f.wq = (const uint8_t*)f->wq;
   T.f.w_out = f->w + f->layer_off[f->n_layers - 1];
+  T.x_in = x_in;
+  T.dx_out = dx_out;
+  T.w0 = f->w + f->layer_off[0];
   int64_t tiles = (B + kTileM - 1) / kTileM;
   int grid = (int)std::min<int64_t>(tiles, (int64_t)ctx->num_sms);
   float* partial;
-  PF_TRY(pf_scratch(ctx, WS_ACT, (size_t)grid * f->n_params * sizeof(float), (void**)&partial));
+  PF_TRY(pf_scratch(ctx, WS_ACT, (size_t)grid * T.n_params * sizeof(float), (void**)&partial));
   float inv_n = targets ? 1.0f / (float)(3 * B) : 0.f;
   auto launch = [&](auto kern) -> pf_status {
     PF_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T.f.smem_bytes));
@@ -808,9 +921,14 @@ pf_status pf_tc_backward(pf_ctx* ctx, const pf_field* f, const float* q, const f
     PF_CUDA(ctx, cudaGetLastError());
     return PF_OK;
   };
-  if (f->desc.prec == PF_PREC_BF16) { PF_TRY(launch(k_tc_train<PF_PREC_BF16>)); }
-  else { PF_TRY(launch(k_tc_train<PF_PREC_F16>)); }
-  k_reduce_partials<<<(unsigned)((f->n_params + 127) / 128), 128, 0, ctx->stream>>>(partial, grid, f->n_params, dw);
+  if (T.hash) {
+    if (f->desc.prec == PF_PREC_BF16) { PF_TRY(launch(k_tc_train<PF_PREC_BF16, true>)); }
+    else { PF_TRY(launch(k_tc_train<PF_PREC_F16, true>)); }
+  } else {
+    if (f->desc.prec == PF_PREC_BF16) { PF_TRY(launch(k_tc_train<PF_PREC_BF16, false>)); }
+    else { PF_TRY(launch(k_tc_train<PF_PREC_F16, false>)); }
+  }
+  k_reduce_partials<<<(unsigned)((T.n_params + 127) / 128), 128, 0, ctx->stream>>>(partial, grid, T.n_params, dw);
   PF_CUDA(ctx, cudaGetLastError());
   return PF_OK;
 }
@@ -826,8 +944,10 @@ pf_status pf_field_pack(pf_ctx* ctx, pf_field* f) {
   const bool need_wr = !tc_fwd || (f->desc.prec != PF_PREC_FP8 && !tc_bwd);
   if (need_wr) {
     if (!f->wr) {
-      if (cudaMalloc(&f->wr, f->n_params * sizeof(float)) != cudaSuccess) return pf_fail(ctx, PF_ERR_OOM, "field pack");
-      PF_CUDA(ctx, cudaMemsetAsync(f->wr, 0, f->n_params * sizeof(float), ctx->stream));
+      // the MLP layers only (hash-grid tables are read from the master copy)
+      const size_t nb = (size_t)f->layer_off[f->n_layers] * sizeof(float);
+      if (cudaMalloc(&f->wr, nb) != cudaSuccess) return pf_fail(ctx, PF_ERR_OOM, "field pack");
+      PF_CUDA(ctx, cudaMemsetAsync(f->wr, 0, nb, ctx->stream));
     }
     Bounds B;
     B.n = f->n_layers - 1;
@@ -837,7 +957,8 @@ pf_status pf_field_pack(pf_ctx* ctx, pf_field* f) {
     k_round_weights<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(f->w, f->wr, B, f->desc.prec);
     PF_CUDA(ctx, cudaGetLastError());
   }
-  if (!tc_fwd) return PF_OK;
+  if (!tc_fwd && !tc_bwd) return PF_OK;
+  if (!tc_fwd) A = T.f;                      // hash grids: packed for the training kernel only
   if (!f->wq || f->wq_bytes < A.wq_bytes) {
     cudaFree(f->wq);
     f->wq = nullptr;

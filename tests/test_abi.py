@@ -26,7 +26,7 @@ def test_struct_layouts_match_header():
     assert C.sizeof(_lib.PfVolume) == 80   # sizes as laid out by a C compiler for pf.h
     assert C.sizeof(_lib.PfLight) == 28
     assert C.sizeof(_lib.PfCamera) == 48
-    assert C.sizeof(_lib.PfFieldDesc) == 32
+    assert C.sizeof(_lib.PfFieldDesc) == 56
     assert C.sizeof(_lib.PfTrainDesc) == 128
     assert _lib.PfCacheInfo.tally.offset == 48
 
