@@ -547,7 +547,54 @@ def training_workload(ctx, seed, steps=2000):
            "loss_last": float(loss[-20:].mean()), "photon_cache_s": t_cache, "photons_per_s": 6 * (1 << 20) / t_cache,
            "records": int(cache.n_records), "model_tflops": flop / dt / 1e12}
     out["knn"] = knn_training(ctx, cache, seed, steps, vol_res=sc.volume.data.shape[0])
+    out["hashgrid"] = hashgrid_training(ctx, cache, seed, steps)
     return out
+
+
+# The paper's encoding (Sec. 3.4): 16 levels of 8 features, x2 per level,
+# 2^19 table entries; base resolution 16 cells.
+HASH = dict(encoding="hashgrid", hash_levels=16, hash_features=8, hash_log2_size=19, hash_base_res=16,
+            hash_scale=2.0)
+
+
+def hashgrid_training(ctx, cache, seed, steps, batch=1 << 16):
+    """Convergence of the hash-grid field against the frequency encoding on
+    the same caches and cell targets: 4x64 bf16 MLPs, 2^16 queries per step
+    (the paper's batch), `steps` steps each.  The training loss of every step
+    is taken on a fresh batch, so its running mean is a held-out estimate;
+    reported at a few steps, with the step (and time) at which the hash-grid
+    field first matches the frequency field's final loss, and both fields'
+    loss on one held-out batch."""
+    import torch
+    from paper_2304_07338_b300 import api
+    qv = cache.sample_queries(1 << 16, step=0, seed=seed + 41)
+    _, yv = cache.estimate_targets(qv)
+    res = {"batch": batch, "steps": steps, "config": dict(HASH, mlp="4x64 bf16")}
+    curves = {}
+    for name, kw in (("frequency", {}), ("hashgrid", HASH)):
+        w = api.Field(ctx, 12, 64, 4, "bf16", 5.0, seed=seed + 21, **kw)
+        w.train(cache, steps=3, batch=batch, lr=1e-2, seed=seed + 42)            # warm-up
+        del w
+        fld = api.Field(ctx, 12, 64, 4, "bf16", 5.0, seed=seed + 21, **kw)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss = fld.train(cache, steps=steps, batch=batch, lr=1e-2, seed=seed + 42)
+        dt = time.perf_counter() - t0
+        yh = fld.forward(qv)
+        val = float(torch.mean((yh - yv) ** 2 / (yv ** 2 + 0.01)))
+        run = np.convolve(loss, np.ones(20) / 20, mode="valid")         # mean of steps s-19 .. s
+        curves[name] = run
+        res[name] = {"steps_per_s": steps / dt, "train_s": dt, "params": int(fld.n_params), "val_loss": val,
+                     "loss_at": {str(s_): float(run[s_ - 20]) for s_ in (100, 250, 500, 1000, steps) if s_ <= steps}}
+        del fld
+    target = curves["frequency"][-1]
+    hit = np.nonzero(curves["hashgrid"] <= target)[0]
+    if hit.size:
+        s_hit = int(hit[0]) + 20
+        res["hashgrid_steps_to_frequency_final_loss"] = s_hit
+        res["hashgrid_time_to_frequency_final_loss_s"] = s_hit / res["hashgrid"]["steps_per_s"]
+    res["frequency_time_s"] = res["frequency"]["train_s"]
+    return res
 
 
 # Staggered KNN schedule (Sec. 3.5.2, Table 1, the 6M-photon row: this

@@ -186,8 +186,9 @@ struct FieldView {
   int n_layers, n_in, hidden, in_freqs, prec;
   float psi;
   float s_a[8], s_w[8];
-  // hash-grid encoding (enc == PF_ENC_HASHGRID)
-  int enc, hl, hf;
+  // hash-grid encoding (enc == PF_ENC_HASHGRID); vec: the gradient buffer is
+  // 16-byte aligned, so entries of 4 or 8 features take vector atomics
+  int enc, hl, hf, vec;
   int hres[2][16];
   uint32_t hent[2][16];
   uint32_t hdense[2];
@@ -204,6 +205,7 @@ FieldView view_of(const pf_field* f) {
   v.prec = f->desc.prec; v.psi = f->desc.psi;
   for (int l = 0; l < 8; ++l) { v.s_a[l] = f->scales_host[l]; v.s_w[l] = f->scales_host[16 + l]; }
   v.enc = f->desc.encoding;
+  v.vec = 0;
   v.hl = f->desc.hash_levels;
   v.hf = f->desc.hash_features;
   for (int gi = 0; gi < 2; ++gi) {
@@ -293,9 +295,16 @@ __device__ __forceinline__ void hash_scatter(const FieldView& F, int gi, int l, 
   for (int c = 0; c < (1 << D); ++c) {
     float* e = tab + (size_t)hash_index<D>(F, gi, l, i0, c) * F.hf;
     const float w = corner_weight<D>(fr, c);
+    if (F.vec && F.hf >= 4) {
+      // entries of 4 or 8 features start on 16-byte boundaries (level tables
+      // on 8-float boundaries): vector atomics
+      atomicAdd((float4*)e, make_float4(w * dx[0], w * dx[1], w * dx[2], w * dx[3]));
+      if (F.hf == 8) atomicAdd((float4*)e + 1, make_float4(w * dx[4], w * dx[5], w * dx[6], w * dx[7]));
+    } else {
 #pragma unroll
-    for (int f = 0; f < 8; ++f)
-      if (f < F.hf) atomicAdd(e + f, w * dx[f]);
+      for (int f = 0; f < 4; ++f)
+        if (f < F.hf) atomicAdd(e + f, w * dx[f]);
+    }
   }
 }
 
@@ -517,6 +526,7 @@ pf_status pf_simt_forward(pf_ctx* ctx, const pf_field* f, const float* q, int64_
 pf_status pf_simt_backward(pf_ctx* ctx, const pf_field* f, const float* q, const float* dy, const float* targets,
                            int64_t B, float* dw, float* loss) {
   FieldView F = view_of(f);
+  F.vec = ((uintptr_t)dw & 15) == 0;
   size_t sm = simt_bwd_smem(f);
   if (sm > 227 * 1024) return pf_fail(ctx, PF_ERR_UNSUPPORTED, "SIMT backward: network too deep for shared memory");
   cudaFuncSetAttribute(k_simt_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -690,7 +700,8 @@ pf_status pf_field_backward_impl(pf_ctx* ctx, const pf_field* f, const float* q,
       return pf_tc_backward(ctx, f, q, dy, targets, B, dw, loss, nullptr, nullptr);
     // hash grids: table features (gather), the MLP on tcgen05 (which writes
     // the MLP's dW and the features' gradient), then the table scatter
-    const FieldView F = view_of(f);
+    FieldView F = view_of(f);
+    F.vec = ((uintptr_t)dw & 15) == 0;
     const int nf = 2 * F.hl * F.hf;
     uint16_t* x;
     float* dx;
@@ -724,18 +735,38 @@ extern "C" pf_status pf_field_backward(pf_ctx* ctx, const pf_field* f, const flo
 
 // ------------------------------------------------------------------ Adam
 namespace {
+__device__ __forceinline__ void adam1(float& w, float& m, float& v, float g, float lr, float b1, float b2, float eps,
+                                      float c1, float c2) {
+  m = b1 * m + (1.f - b1) * g;
+  v = b2 * v + (1.f - b2) * g * g;
+  const float mh = m / c1, vh = v / c2;
+  w = w - lr * mh / (sqrtf(vh) + eps);
+}
+
+// One Adam update per parameter; four per thread (16-byte accesses) when the
+// arrays allow it (hash-grid fields carry ~10^8 parameters).
 __global__ void k_adam(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v, const float* __restrict__ g,
                        int64_t n, float lr, float b1, float b2, float eps, float c1, float c2, uint32_t* err) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float gi = g[i];
   if (!isfinite(gi)) { atomicOr(err, 2u); return; }
-  float mi = b1 * m[i] + (1.f - b1) * gi;
-  float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-  m[i] = mi;
-  v[i] = vi;
-  float mh = mi / c1, vh = vi / c2;
-  w[i] = w[i] - lr * mh / (sqrtf(vh) + eps);
+  adam1(w[i], m[i], v[i], gi, lr, b1, b2, eps, c1, c2);
+}
+
+__global__ void k_adam4(float4* __restrict__ w, float4* __restrict__ m, float4* __restrict__ v,
+                        const float4* __restrict__ g, int64_t n4, float lr, float b1, float b2, float eps, float c1,
+                        float c2, uint32_t* err) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n4) return;
+  const float4 gi = g[i];
+  if (!isfinite(gi.x) || !isfinite(gi.y) || !isfinite(gi.z) || !isfinite(gi.w)) { atomicOr(err, 2u); return; }
+  float4 wi = w[i], mi = m[i], vi = v[i];
+  adam1(wi.x, mi.x, vi.x, gi.x, lr, b1, b2, eps, c1, c2);
+  adam1(wi.y, mi.y, vi.y, gi.y, lr, b1, b2, eps, c1, c2);
+  adam1(wi.z, mi.z, vi.z, gi.z, lr, b1, b2, eps, c1, c2);
+  adam1(wi.w, mi.w, vi.w, gi.w, lr, b1, b2, eps, c1, c2);
+  w[i] = wi; m[i] = mi; v[i] = vi;
 }
 }  // namespace
 
@@ -743,8 +774,14 @@ pf_status pf_adam_impl(pf_ctx* ctx, pf_field* f, const float* g, float lr, float
   f->step += 1;
   float c1 = (float)(1.0 - std::pow((double)b1, f->step));
   float c2 = (float)(1.0 - std::pow((double)b2, f->step));
-  k_adam<<<(unsigned)((f->n_params + 255) / 256), 256, 0, ctx->stream>>>(f->w, f->m, f->v, g, f->n_params, lr, b1, b2,
-                                                                         eps, c1, c2, ctx->err_dev);
+  const bool vec = f->n_params % 4 == 0 && ((uintptr_t)g & 15) == 0;
+  if (vec)
+    k_adam4<<<(unsigned)((f->n_params / 4 + 255) / 256), 256, 0, ctx->stream>>>(
+        (float4*)f->w, (float4*)f->m, (float4*)f->v, (const float4*)g, f->n_params / 4, lr, b1, b2, eps, c1, c2,
+        ctx->err_dev);
+  else
+    k_adam<<<(unsigned)((f->n_params + 255) / 256), 256, 0, ctx->stream>>>(f->w, f->m, f->v, g, f->n_params, lr, b1,
+                                                                           b2, eps, c1, c2, ctx->err_dev);
   PF_CUDA(ctx, cudaGetLastError());
   return pf_field_pack(ctx, f);
 }
