@@ -62,6 +62,8 @@ def _declare(L):
                                  i32, i32, u64, i32, i32, i32, i32, P, i64, P]
     L.orc_cell_sigma.argtypes = [i32, i32, i32, i32, P, f64, P, i32, i32, P]
     L.orc_estimate.argtypes = [P, P, P, i64, P, P, P, P, P, i32, i32, i32, P]
+    L.orc_raymarch.argtypes = [i32, i32, i32, i32, P, f64, f64, P, i32, P, P, P, i32, f64, P, P, P, f64, i32, i32,
+                               i32, f64, u64, i32, i32, P, P, P, P, P]
     L.orc_estimate_knn.argtypes = [P, P, P, i64, P, P, P, P, P, i64, i32, C.c_float, P, P, i32, P, P, P]
 
 
@@ -393,6 +395,41 @@ def render_neural(vol, lights, g: float, cam, spp: int, step_vox: float, seed: i
     img = (cs["albedo"] * (cs["Ld"] + Li)).sum(axis=2) / spp
     if return_parts:
         return img, cs, Li
+    return img
+
+
+def render_raymarched(vol, lights, g: float, cam, spp: int, step_vox: float, seed: int,
+                      weights=None, desc=None, scales=None, rows=None, return_parts: bool = False):
+    """Ray marching with the photon field at every step (Sec. 3.6): per
+    camera sample the sum over the march segments of a_s albedo_s (L_d + L_i)
+    (see orc_raymarch), averaged over the samples of a pixel; L_i from the
+    field (weights, desc, scales as for render_neural), or 0 without one.
+    Returns the image of rows [y0, y1) (and the per-ray direct part, query
+    counts, queries and weights with return_parts)."""
+    v, L, cm = _Vol(vol), _Lights(lights), _Cam(cam)
+    y0, y1 = rows if rows is not None else (0, cam.height)
+    n = (y1 - y0) * cam.width * spp
+    D = np.zeros((n, 3))
+    cnt = np.zeros(n, np.int64)
+    args = (*v.args, v.ss, v.alb, *v.tfargs, *L.args, float(g), *cm.args, spp, float(step_vox), seed, y0, y1)
+    lib().orc_raymarch(*args, _p(D), _p(cnt), None, None, None)
+    rad = D.copy()
+    q = w = None
+    if weights is not None:
+        off = np.zeros(n + 1, np.int64)
+        np.cumsum(cnt, out=off[1:])
+        q = np.zeros((int(off[-1]), 6))
+        w = np.zeros((int(off[-1]), 3))
+        D2 = np.zeros((n, 3))
+        cnt2 = np.zeros(n, np.int64)
+        lib().orc_raymarch(*args, _p(D2), _p(cnt2), _p(off), _p(q), _p(w))
+        ray = np.repeat(np.arange(n), cnt)
+        for a in range(0, q.shape[0], 1 << 18):
+            y, _ = field.forward(weights, q[a:a + (1 << 18)], desc, scales)
+            np.add.at(rad, ray[a:a + (1 << 18)], field.log_decode(y, desc.psi) * w[a:a + (1 << 18)])
+    img = rad.reshape(y1 - y0, cam.width, spp, 3).mean(2)
+    if return_parts:
+        return img, dict(direct=D, count=cnt, q=q, w=w)
     return img
 
 

@@ -772,6 +772,76 @@ void camera_sample(const Volume& V, const Grid<R>& G, const Grid<R>& Gp, const G
     *valid = 1; *xo = x; *alb = m.albedo; *Ld = L;
 }
 
+// ------------------------------------------------------------------ ray marching with the field at every step
+// Sec. 3.6: the field replaces the multiple-scattering term in ray marching
+// as well as in path tracing.  Camera sample k of pixel p: the ray from Philox
+// block 0 of (seed, tag 1, p, k) (lanes 0, 1: pixel jitter; lane 2: march
+// offset u).  Segment s covers [t0 + s h, min(t0 + (s+1) h, t1)) with its
+// sample point at fraction u of it and sigma_s = sigma_t there; tau_s is the
+// optical depth of the segments before it.  Weight
+//   a_s = exp(-tau_s) (1 - exp(-sigma_s len_s))
+// (the segment's exact share of the ray's extinction for constant sigma, so
+// the weights of a ray add up to 1 - exp(-tau) of the whole ray), and
+//   L = sum_s a_s albedo(x_s) (L_d(x_s) + L_i(x_s, -d, g)),
+// L_d towards every light by a marched shadow ray (march_tau) whose jitter is
+// lane l % 4 of block 4 s + l / 4 of the stream (seed, tag 6, p, k).  A
+// segment with sigma_s = 0 adds nothing and asks no field query.
+// D: the ray's direct part; returns the number of field queries; q, w (each
+// nullable) receive the queries (x, theta', phi', g) and weights a_s albedo_s.
+long raymarch_ray(const Volume& V, const Light* lights, int n_lights, double g, const CamFrame& cf, int px, int py,
+                  int k, double h, uint64_t seed, double D[3], double* q, double* w) {
+    const uint64_t pix = (uint64_t)py * (uint64_t)cf.W + (uint64_t)px;
+    Rng rng(seed, 1, pix, (uint32_t)k);
+    double b0[4]; rng.uni4<double>(b0);
+    V3<double> o, d;
+    camera_ray<double>(cf, px, py, b0[0], b0[1], &o, &d);
+    D[0] = D[1] = D[2] = 0.0;
+    long n = 0;
+    double t0, t1;
+    if (!box_hit(o, d, &t0, &t1)) return 0;
+    const double th = std::acos(std::min(1.0, std::max(-1.0, -d.z))) / M_PI;
+    double ph = std::atan2(-d.y, -d.x) / (2.0 * M_PI);
+    if (ph < 0.0) ph += 1.0;
+    const long nseg = (long)std::ceil((t1 - t0) / h);
+    double tau = 0.0;
+    for (long s = 0; s < nseg; ++s) {
+        const double s0 = t0 + (double)s * h;
+        const double s1 = std::min(t0 + (double)(s + 1) * h, t1);
+        const double len = s1 - s0;
+        if (!(len > 0.0)) continue;
+        const V3<double> x = along(o, d, s0 + b0[2] * len);
+        const Medium<double> m = medium_at<double>(V, x);
+        if (m.sigma > 0.0) {
+            const double a = std::exp(-tau) * -std::expm1(-m.sigma * len);
+            double Ld[3] = {0.0, 0.0, 0.0};
+            Rng rs(seed, 6, pix, (uint32_t)k);
+            for (int gq = 0; 4 * gq < n_lights; ++gq) {
+                rs.ctr[3] = (uint32_t)(4 * s + gq);
+                double jit[4]; rs.uni4<double>(jit);
+                for (int i = 0; i < 4 && 4 * gq + i < n_lights; ++i) {
+                    V3<double> wl, E; double dist;
+                    light_geom<double>(lights[4 * gq + i], x, &wl, &dist, &E);
+                    double a0, a1, tend = 0.0;
+                    if (box_hit(x, wl, &a0, &a1)) tend = std::min(a1, dist);
+                    const double T = std::exp(-march_tau<double>(V, x, wl, 0.0, tend, h, jit[i]));
+                    const double p = hg_eval<double>(g, dot(d, wl));
+                    Ld[0] += p * T * E.x; Ld[1] += p * T * E.y; Ld[2] += p * T * E.z;
+                }
+            }
+            const double wr[3] = {a * m.albedo.x, a * m.albedo.y, a * m.albedo.z};
+            for (int c = 0; c < 3; ++c) D[c] += wr[c] * Ld[c];
+            if (q) {
+                q[6 * n + 0] = x.x; q[6 * n + 1] = x.y; q[6 * n + 2] = x.z;
+                q[6 * n + 3] = th; q[6 * n + 4] = ph; q[6 * n + 5] = g;
+            }
+            if (w) for (int c = 0; c < 3; ++c) w[3 * n + c] = wr[c];
+            ++n;
+        }
+        tau += m.sigma * len;
+    }
+    return n;
+}
+
 // ------------------------------------------------------------------ path tracer
 // Delta tracking; at every real collision j: next-event estimation towards
 // every light with ratio-tracking transmittance (each shadow ray on its own
@@ -1187,4 +1257,28 @@ void orc_estimate_knn(const float* xq, const double* w, const int* gi, int64_t B
     }
 }
 
+
+// Ray-marched render of rows [y_begin, y_end): per camera sample (ray r =
+// ((py - y_begin) W + px) spp + k) the direct part D[r] and the number of
+// field queries count[r]; with offsets (exclusive sums of count, nullable)
+// also the queries q [..][6] and weights w [..][3] at offsets[r].
+void orc_raymarch(int nx, int ny, int nz, int dtype, const void* data, double ss, double alb,
+                  const float* tf, int tf_n, const int* lkind, const double* lv, const double* lrgb, int n_lights,
+                  double g, const double* eye, const double* at, const double* up, double fovy, int W, int H,
+                  int spp, double step_vox, uint64_t seed, int y_begin, int y_end,
+                  double* D, int64_t* count, const int64_t* offsets, double* q, double* w) {
+    Volume V = mkvol(nx, ny, nz, dtype, data, ss, alb, tf, tf_n);
+    std::vector<Light> L = mklights(lkind, lv, lrgb, n_lights);
+    CamFrame cf = cam_frame(eye, at, up, fovy, W, H);
+    const double h = step_vox / (double)std::max(nx, std::max(ny, nz));
+    #pragma omp parallel for schedule(dynamic, 1) collapse(2)
+    for (int py = y_begin; py < y_end; ++py)
+        for (int px = 0; px < W; ++px)
+            for (int k = 0; k < spp; ++k) {
+                const size_t r = ((size_t)(py - y_begin) * W + px) * spp + k;
+                double* qq = offsets ? q + 6 * offsets[r] : nullptr;
+                double* ww = offsets ? w + 3 * offsets[r] : nullptr;
+                count[r] = raymarch_ray(V, L.data(), n_lights, g, cf, px, py, k, h, seed, D + 3 * r, qq, ww);
+            }
+}
 }  // extern "C"
