@@ -386,6 +386,7 @@ def main():
     if not args.no_equal_rmse:
         line["equal_rmse"] = equal_rmse(ctx, vol, lights, frame, field, seed, args, fps)
         line["vs_path_tracer_equal_rmse"] = line["equal_rmse"].get("speedup")
+        line["phase_sweep"] = phase_sweep(ctx, vol, lights, frame, field, seed, args)
     if not args.no_march:
         line["march_workload"] = march_workload(ctx, vol, lights, frame, field, seed, args)
     line["training_workload"] = training_workload(ctx, seed)
@@ -452,6 +453,31 @@ def march_workload(ctx, vol, lights, frame, field, seed, args):
             "roofline": {"kernel": "k_camera_samples (marched free flight and shadow rays)", "bound": "hbm",
                          "achieved": bw, "peak": hbm, "unit": "GB/s", "frac": bw / hbm,
                          "algorithmic": "%d lookups x %d B" % (lookups, FETCH_BYTES)}}
+
+
+def phase_sweep(ctx, vol, lights, frame, field, seed, args, ref_spp=1024):
+    """Phase-function awareness (Sec. 4.3.4): the field, trained on caches
+    traced at G = {-0.75, 0, 0.75}, rendered at g inside and between the
+    traced phases.  For every g, the image error (frame 0's camera, the
+    equal-RMSE resolution) of the neural render, of the same render with
+    the field off (direct light only) and of the path tracer at the neural
+    render's spp, against a ref_spp path-traced reference at that g."""
+    from paper_2304_07338_b300 import api, inputs as I
+    cam, _ = frame(0)
+    small = I.Camera(cam.eye, cam.at, cam.up, cam.fovy_deg, args.rmse_width, args.rmse_height)
+    rows = []
+    for i, g in enumerate((-0.9, -0.75, -0.5, -0.25, 0.0, 0.25, 0.5, 0.75, 0.9)):
+        ref = api.render_pathtraced(ctx, vol, lights, g, small, ref_spp, 16, seed=seed + 60 + i)
+        neural = api.render_neural(ctx, vol, lights, g, small, SPP, 0.0, seed + 8, field)
+        direct = api.render_neural(ctx, vol, lights, g, small, SPP, 0.0, seed + 8, None)
+        pt = api.render_pathtraced(ctx, vol, lights, g, small, SPP, 16, seed=seed + 9)
+        ctx.sync()
+        r_n, r_d, r_p = (api.image_rmse(ctx, x, ref) for x in (neural, direct, pt))
+        rows.append({"g": g, "in_G": g in I.G_PAPER, "rmse_neural": r_n, "rmse_direct_only": r_d,
+                     "rmse_pt_same_spp": r_p, "error_removed": 1.0 - r_n / r_d})
+    return {"reference": "path tracer, %d spp per g, %dx%d, frame 0 camera" % (ref_spp, args.rmse_width,
+                                                                            args.rmse_height),
+            "spp": SPP, "by_g": rows}
 
 
 def equal_rmse(ctx, vol, lights, frame, field, seed, args, fps_neural):

@@ -344,6 +344,23 @@ pf_status pf_train_field(pf_ctx* ctx, const pf_cache* cache, const pf_train_desc
 pf_status pf_render_neural(pf_ctx* ctx, const pf_volume* vol, const pf_light* lights, int n_lights, float g,
                            const pf_camera* cam, int spp, float step_vox, uint64_t seed, const pf_field* field,
                            float* out_rgb_dev);
+/* Ray marching with the photon field at every step (Sec. 3.6: the field
+ * replaces the multiple-scattering term in ray marching as in path tracing).
+ * Per pixel and sample: a jittered pinhole ray (Philox tag 1, block 0: pixel
+ * jitter, march offset u); segments of step_vox voxels ([t0 + s h,
+ * min(t0 + (s+1) h, t1))) sampled at fraction u; weight a_s = exp(-tau_s)
+ * (1 - exp(-sigma_s len_s)) with tau_s the optical depth before the segment;
+ * L = sum_s a_s albedo_s (L_d + L_i) with L_d towards every light by a marched
+ * shadow ray (jitter: lane l % 4 of block 4 s + l / 4 of Philox tag 6, item
+ * pixel, sub sample) and L_i = 10^(-psi L') from the field at (x_s, -d, g)
+ * (no field: L_i = 0); the pixel is the mean over its samples.  Every
+ * segment with sigma > 0 asks one field query: the call counts them first,
+ * then renders in chunks of whole pixels whose queries fit a buffer of 2^23
+ * (or one pixel's worth); synchronises once.  step_vox in [0.05, 64].
+ * out_rgb_dev [H*W*3] f32. */
+pf_status pf_render_raymarched(pf_ctx* ctx, const pf_volume* vol, const pf_light* lights, int n_lights, float g,
+                               const pf_camera* cam, int spp, float step_vox, uint64_t seed, const pf_field* field,
+                               float* out_rgb_dev);
 /* Plain multi-bounce path tracer (the paper's baseline): delta tracking,
  * next-event estimation with ratio tracking at every real interaction,
  * Henyey-Greenstein continuation, at most max_bounces interactions, Russian

@@ -87,6 +87,8 @@ SIGNATURES = {
     "pf_field_adam": (I, [P, P, P, F, F, F, F]),
     "pf_train_field": (I, [P, P, C.POINTER(PfTrainDesc), P, P]),
     "pf_render_neural": (I, [P, C.POINTER(PfVolume), C.POINTER(PfLight), I, F, C.POINTER(PfCamera), I, F, U64, P, P]),
+    "pf_render_raymarched": (I, [P, C.POINTER(PfVolume), C.POINTER(PfLight), I, F, C.POINTER(PfCamera), I, F, U64, P,
+                                 P]),
     "pf_render_pathtraced": (I, [P, C.POINTER(PfVolume), C.POINTER(PfLight), I, F, C.POINTER(PfCamera), I, I, U64, I,
                                  P]),
     "pf_render_pathtraced_noalloc": (I, [C.POINTER(PfVolume), C.POINTER(PfLight), I, F, C.POINTER(PfCamera), I, I,

@@ -332,6 +332,19 @@ def render_neural(ctx: Context, vol: Volume, lights, g: float, cam, spp: int, st
     return out
 
 
+def render_raymarched(ctx: Context, vol: Volume, lights, g: float, cam, spp: int, step_vox: float, seed: int,
+                      field: Optional[Field] = None, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Ray marching with the field at every step (pf_render_raymarched)."""
+    la, n = _lights(lights)
+    c = _camera(cam)
+    if out is None:
+        out = torch.empty(cam.height, cam.width, 3, dtype=torch.float32, device=torch.device("cuda", ctx.device))
+    ctx.check(ctx.lib.pf_render_raymarched(ctx.h, C.byref(vol.s), la, n, float(g), C.byref(c), int(spp),
+                                           float(step_vox), int(seed), field.h if field is not None else None,
+                                           _ptr(out)))
+    return out
+
+
 def render_pathtraced(ctx: Context, vol: Volume, lights, g: float, cam, spp: int, max_bounces: int = 16, seed: int = 1,
                       use_rr: bool = True, out: Optional[torch.Tensor] = None) -> torch.Tensor:
     la, n = _lights(lights)

@@ -526,6 +526,142 @@ CamF make_cam(const pf_camera* c) {
   return o;
 }
 
+// ---- ray marching with the field at every step (Sec. 3.6) -----------------
+// Camera sample k of pixel p: the ray from block 0 of (seed, tag 1, p, k)
+// (pixel jitter, march offset u in lane 2).  Segment s covers
+// [t0 + s h, min(t0 + (s+1) h, t1)); its sample point sits at fraction u,
+// with sigma_s and albedo_s there; weight a_s = exp(-tau_s) (1 - exp(-sigma_s
+// len_s)), tau_s the (compensated) optical depth before the segment.  L_d
+// towards every light by a marched shadow ray whose jitter is lane l % 4 of
+// Philox block 4 s + l / 4 of (seed, tag 6, p, k).  A segment with sigma_s > 0
+// asks one field query (x_s, -d, g) with weight a_s albedo_s.
+constexpr uint32_t kTagMarch = 6;
+
+// EMIT = false: count the queries of each ray; EMIT = true: write them (at
+// off[ray] - base, when q is given) and each ray's direct part.
+template <int DT, bool EMIT>
+__global__ void __launch_bounds__(128) k_raymarch(Vol V, DevLights L, CamF cam, float g, int spp, float h,
+                                                  uint64_t seed, int64_t r0, int64_t n_rays,
+                                                  uint32_t* __restrict__ counts, const uint64_t* __restrict__ off,
+                                                  uint64_t base, float* __restrict__ q, float* __restrict__ wgt,
+                                                  float* __restrict__ direct) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_rays) return;
+  const int64_t ray = r0 + i;
+  const int k = (int)(ray % spp);
+  const int64_t pix = ray / spp;
+  const int px = (int)(pix % cam.W), py = (int)(pix / cam.W);
+  Rng rng(seed, TAG_CAMERA, (uint64_t)pix, (uint32_t)k);
+  float b0[4];
+  rng.uni4(b0);
+  V3 o, d;
+  camera_ray(cam, px, py, b0[0], b0[1], &o, &d);
+  uint32_t n = 0;
+  V3 D = v3(0.f, 0.f, 0.f);
+  uint64_t j = (EMIT && q) ? off[ray] - base : 0;
+  const uint64_t j_end = (EMIT && q) ? off[ray + 1] - base : 0;   // the ray's range (the count pass's)
+  float t0, t1;
+  if (box_hit(o, d, &t0, &t1)) {
+    const float qth = acosf(fminf(fmaxf(-d.z, -1.f), 1.f)) * 0.318309886183790672f;
+    float qph = atan2f(-d.y, -d.x) * 0.159154943091895336f;
+    if (qph < 0.f) qph = qph + 1.0f;
+    float tau = 0.f, comp = 0.f;
+    const int nseg = (int)ceilf((t1 - t0) / h);
+    for (int s = 0; s < nseg; ++s) {
+      const float s0 = t0 + (float)s * h;
+      const float s1 = mn(t0 + (float)(s + 1) * h, t1);
+      const float len = s1 - s0;
+      if (!(len > 0.f)) continue;
+      const V3 x = along(o, d, s0 + b0[2] * len);
+      float sg;
+      V3 alb;
+      medium_at<DT>(V, x, &sg, &alb);
+      if (sg > 0.f) {
+        ++n;
+        if (EMIT) {
+          const float a = expf(-(tau - comp)) * -expm1f(-sg * len);
+          V3 Ld = v3(0.f, 0.f, 0.f);
+          Rng rs(seed, kTagMarch, (uint64_t)pix, (uint32_t)k);
+          for (int gq = 0; 4 * gq < L.n; ++gq) {
+            rs.c3 = (uint32_t)(4 * s + gq);
+            float jit[4];
+            rs.uni4(jit);
+            for (int ii = 0; ii < 4 && 4 * gq + ii < L.n; ++ii) {
+              V3 wl, E;
+              float dist;
+              light_geom(L.l[4 * gq + ii], x, &wl, &dist, &E);
+              float a0, a1, tend = 0.f;
+              if (box_hit(x, wl, &a0, &a1)) tend = mn(a1, dist);
+              float st = 0.f, sc = 0.f;
+              if (tend > 0.f) {
+                const int ns = (int)ceilf(tend / h);
+                for (int m = 0; m < ns; ++m) {
+                  const float m0 = (float)m * h;
+                  const float m1 = mn((float)(m + 1) * h, tend);
+                  const float ml = m1 - m0;
+                  if (!(ml > 0.f)) continue;
+                  const float y = sigma_at<DT>(V, along(x, wl, m0 + jit[ii] * ml)) * ml - sc;
+                  const float t = st + y;
+                  sc = (t - st) - y;
+                  st = t;
+                }
+              }
+              const float T = expf(-(st - sc));
+              const float ph = hg_eval(g, dot(d, wl));
+              Ld = v3(Ld.x + ph * T * E.x, Ld.y + ph * T * E.y, Ld.z + ph * T * E.z);
+            }
+          }
+          const V3 w = v3(a * alb.x, a * alb.y, a * alb.z);
+          D = v3(D.x + w.x * Ld.x, D.y + w.y * Ld.y, D.z + w.z * Ld.z);
+          if (q && j < j_end) {
+            q[6 * j + 0] = x.x; q[6 * j + 1] = x.y; q[6 * j + 2] = x.z;
+            q[6 * j + 3] = qth; q[6 * j + 4] = qph; q[6 * j + 5] = g;
+            wgt[3 * j + 0] = w.x; wgt[3 * j + 1] = w.y; wgt[3 * j + 2] = w.z;
+            ++j;
+          }
+        }
+      }
+      const float y = sg * len - comp;
+      const float t = tau + y;
+      comp = (t - tau) - y;
+      tau = t;
+    }
+  }
+  if (!EMIT) {
+    counts[i] = n;
+  } else {
+    direct[3 * i + 0] = D.x; direct[3 * i + 1] = D.y; direct[3 * i + 2] = D.z;
+  }
+}
+
+__global__ void k_iota(uint32_t* __restrict__ v, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = (uint32_t)i;
+}
+
+// Pixel p0 + i: the mean over its samples of the direct part plus the
+// weighted field values of the sample's queries (li, nullable).
+__global__ void k_raymarch_compose(const float* __restrict__ direct, const float* __restrict__ li,
+                                   const uint64_t* __restrict__ off, uint64_t base, int64_t p0, int64_t n_pix,
+                                   int spp, float* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_pix) return;
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+  for (int k = 0; k < spp; ++k) {
+    const int64_t rl = i * spp + k;                  // ray within the chunk
+    a0 += direct[3 * rl]; a1 += direct[3 * rl + 1]; a2 += direct[3 * rl + 2];
+    if (li) {
+      const int64_t ray = p0 * spp + rl;
+      for (uint64_t jj = off[ray] - base; jj < off[ray + 1] - base; ++jj) {
+        a0 += li[3 * jj]; a1 += li[3 * jj + 1]; a2 += li[3 * jj + 2];
+      }
+    }
+  }
+  const float inv = 1.0f / (float)spp;
+  const int64_t p = p0 + i;
+  out[3 * p] = a0 * inv; out[3 * p + 1] = a1 * inv; out[3 * p + 2] = a2 * inv;
+}
+
 // Launches k_nee as a grid-stride loop over the compacted list with as many
 // blocks as fit on the device at once.
 template <int DT>
@@ -662,6 +798,107 @@ extern "C" pf_status pf_render_neural(pf_ctx* ctx, const pf_volume* vol, const p
                                                                         out_rgb_dev);
   }
   PF_CUDA(ctx, cudaGetLastError());
+  return PF_OK;
+}
+
+// Ray marching with the field at every step: count the field queries of every
+// camera sample, then render in chunks of whole pixels whose queries fit the
+// query buffer (queries + weights, the field forward with the render
+// epilogue, compose).
+extern "C" pf_status pf_render_raymarched(pf_ctx* ctx, const pf_volume* vol, const pf_light* lights, int n_lights,
+                                          float g, const pf_camera* cam, int spp, float step_vox, uint64_t seed,
+                                          const pf_field* field, float* out_rgb_dev) {
+  if (!ctx) return PF_ERR_INVALID_ARG;
+  DeviceGuard dg(ctx->device);
+  PF_TRY(pf_check_volume(ctx, vol));
+  PF_TRY(pf_check_lights(ctx, lights, n_lights));
+  PF_TRY(check_cam(ctx, cam, spp));
+  if (!out_rgb_dev) return pf_fail(ctx, PF_ERR_INVALID_ARG, "out_rgb_dev is NULL");
+  if (!(step_vox >= 0.05f && step_vox <= 64.f) || !(g > -1.f && g < 1.f))
+    return pf_fail(ctx, PF_ERR_INVALID_ARG, "need step_vox in [0.05, 64] voxels and |g| < 1");
+  if (field && field->ctx != ctx) return pf_fail(ctx, PF_ERR_INVALID_ARG, "field belongs to another context");
+  const int64_t n_pix = (int64_t)cam->width * cam->height;
+  const int64_t n_rays = n_pix * spp;
+  if (n_rays > (int64_t)0xFFFFFFFFll) return pf_fail(ctx, PF_ERR_INVALID_ARG, "width*height*spp must be < 2^32");
+  const Vol V = pf_make_vol(vol, 0.f, nullptr);
+  const DevLights L = pf_make_lights(lights, n_lights);
+  const CamF C = make_cam(cam);
+  const int nmax = std::max(vol->nx, std::max(vol->ny, vol->nz));
+  const float h = step_vox / (float)nmax;
+  float* direct;
+  PF_TRY(pf_scratch(ctx, WS_SLOT_LD, (size_t)n_rays * 3 * sizeof(float), (void**)&direct));
+#define RM_LAUNCH(EMIT, r0_, n_, ...)                                                                              \
+  do {                                                                                                             \
+    const unsigned gr_ = (unsigned)(((n_) + 127) / 128);                                                           \
+    if (vol->dtype == PF_F32) k_raymarch<0, EMIT><<<gr_, 128, 0, ctx->stream>>>(V, L, C, g, spp, h, seed, r0_, n_, \
+                                                                               __VA_ARGS__);                       \
+    else if (vol->dtype == PF_F16) k_raymarch<1, EMIT><<<gr_, 128, 0, ctx->stream>>>(V, L, C, g, spp, h, seed, r0_, \
+                                                                                    n_, __VA_ARGS__);              \
+    else k_raymarch<2, EMIT><<<gr_, 128, 0, ctx->stream>>>(V, L, C, g, spp, h, seed, r0_, n_, __VA_ARGS__);        \
+    PF_CUDA(ctx, cudaGetLastError());                                                                              \
+  } while (0)
+  if (!field) {
+    StageTimer tm(ctx, PF_STAGE_CAMERA);
+    RM_LAUNCH(true, (int64_t)0, n_rays, nullptr, nullptr, (uint64_t)0, nullptr, nullptr, direct);
+    k_raymarch_compose<<<(unsigned)((n_pix + 127) / 128), 128, 0, ctx->stream>>>(direct, nullptr, nullptr, 0, 0, n_pix,
+                                                                                spp, out_rgb_dev);
+    PF_CUDA(ctx, cudaGetLastError());
+    return PF_OK;
+  }
+  uint32_t* counts;
+  uint64_t* off;
+  PF_TRY(pf_scratch(ctx, WS_COMPACT_IDX, (size_t)n_rays * sizeof(uint32_t), (void**)&counts));
+  PF_TRY(pf_scratch(ctx, WS_CELL_OFF, (size_t)(n_rays + 1) * sizeof(uint64_t), (void**)&off));
+  {
+    StageTimer tm(ctx, PF_STAGE_CAMERA);
+    RM_LAUNCH(false, (int64_t)0, n_rays, counts, nullptr, (uint64_t)0, nullptr, nullptr, nullptr);
+  }
+  PF_TRY(pf_scan_u32(ctx, counts, off, n_rays));
+  std::vector<uint64_t> hoff((size_t)n_rays + 1);
+  PF_CUDA(ctx, cudaMemcpyAsync(hoff.data(), off, hoff.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
+  PF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  // query buffer: 2^23 queries, or one pixel's worth if that is more
+  uint64_t cap = 1ull << 23, most = 0;
+  for (int64_t p = 0; p < n_pix; ++p) most = std::max(most, hoff[(size_t)(p + 1) * spp] - hoff[(size_t)p * spp]);
+  cap = std::max(cap, most);
+  cap = std::min<uint64_t>(cap, std::max<uint64_t>(hoff[(size_t)n_rays], 1));
+  float *q, *wgt, *li;
+  uint32_t* iota;
+  PF_TRY(pf_scratch(ctx, WS_COMPACT_Q, (size_t)cap * 6 * sizeof(float), (void**)&q));
+  PF_TRY(pf_scratch(ctx, WS_SLOT_ALB, (size_t)cap * 3 * sizeof(float), (void**)&wgt));
+  PF_TRY(pf_scratch(ctx, WS_SLOT_LI, (size_t)cap * 3 * sizeof(float), (void**)&li));
+  PF_TRY(pf_scratch(ctx, WS_CELL_PERM, (size_t)cap * sizeof(uint32_t), (void**)&iota));
+  k_iota<<<(unsigned)((cap + 255) / 256), 256, 0, ctx->stream>>>(iota, (int64_t)cap);
+  PF_CUDA(ctx, cudaGetLastError());
+  for (int64_t p0 = 0; p0 < n_pix;) {
+    // the most whole pixels from p0 whose queries fit the buffer
+    int64_t lo = p0 + 1, hi = n_pix;
+    const uint64_t base = hoff[(size_t)p0 * spp];
+    while (lo < hi) {
+      const int64_t mid = (lo + hi + 1) / 2;
+      if (hoff[(size_t)mid * spp] - base <= cap) lo = mid;
+      else hi = mid - 1;
+    }
+    const int64_t p1 = lo;
+    const int64_t nq = (int64_t)(hoff[(size_t)p1 * spp] - base);
+    {
+      StageTimer tm(ctx, PF_STAGE_CAMERA);
+      RM_LAUNCH(true, p0 * spp, (p1 - p0) * spp, nullptr, off, base, q, wgt, direct);
+    }
+    if (nq > 0) {
+      StageTimer tm(ctx, PF_STAGE_FIELD);
+      PF_TRY(pf_field_forward_impl(ctx, field, q, nq, nullptr, nullptr, iota, wgt, li));
+    }
+    {
+      StageTimer tm(ctx, PF_STAGE_COMPOSE);
+      k_raymarch_compose<<<(unsigned)((p1 - p0 + 127) / 128), 128, 0, ctx->stream>>>(direct, nq > 0 ? li : nullptr,
+                                                                                    off, base, p0, p1 - p0, spp,
+                                                                                    out_rgb_dev);
+      PF_CUDA(ctx, cudaGetLastError());
+    }
+    p0 = p1;
+  }
+#undef RM_LAUNCH
   return PF_OK;
 }
 
