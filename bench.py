@@ -569,9 +569,11 @@ def training_workload(ctx, seed, steps=2000):
     loss = fld2.train(cache, steps=steps, batch=1 << 18, lr=1e-2, seed=seed + 22)
     dt = time.perf_counter() - t0
     flop = 3 * 2 * (144 * 64 + 3 * 64 * 64 + 3 * 64) * (1 << 18) * steps
+    renders = judge_renders(ctx, sc, vol, fld2, seed)
     out = {"steps_per_s": steps / dt, "train_s": dt, "loss_first": float(loss[:5].mean()),
            "loss_last": float(loss[-20:].mean()), "photon_cache_s": t_cache, "photons_per_s": 6 * (1 << 20) / t_cache,
            "records": int(cache.n_records), "model_tflops": flop / dt / 1e12}
+    out["renders"] = renders
     out["knn"] = knn_training(ctx, cache, seed, steps, vol_res=sc.volume.data.shape[0])
     out["hashgrid"] = hashgrid_training(ctx, cache, seed, steps)
     return out
@@ -621,6 +623,43 @@ def hashgrid_training(ctx, cache, seed, steps, batch=1 << 16):
         res["hashgrid_time_to_frequency_final_loss_s"] = s_hit / res["hashgrid"]["steps_per_s"]
     res["frequency_time_s"] = res["frequency"]["train_s"]
     return res
+
+
+def judge_renders(ctx, sc, vol, fld, seed, ref_spp=1024):
+    """The data-source scene (256^2, g = 0) with the field just trained:
+    error against a ref_spp path-traced reference and frames/s of the
+    ray-marching renderer with the field at every step (Sec. 3.6; 1 spp,
+    0.5-voxel steps), the neural path tracer (16 spp, tracking), both without
+    the field, and the path tracer at 16 spp."""
+    import torch
+    from paper_2304_07338_b300 import api
+    cam, g = sc.camera, 0.0
+    ref = api.render_pathtraced(ctx, vol, sc.lights, g, cam, ref_spp, 16, seed=seed + 50)
+    ctx.sync()
+
+    def timed(fn, n=5):
+        img = fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        for _ in range(n):
+            fn()
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        return img, n / (e0.elapsed_time(e1) / 1e3)
+
+    runs = {
+        "raymarch_field": lambda: api.render_raymarched(ctx, vol, sc.lights, g, cam, 1, 0.5, seed + 51, fld),
+        "raymarch_direct_only": lambda: api.render_raymarched(ctx, vol, sc.lights, g, cam, 1, 0.5, seed + 51),
+        "neural_pt_16spp": lambda: api.render_neural(ctx, vol, sc.lights, g, cam, 16, 0.0, seed + 52, fld),
+        "neural_pt_direct_only_16spp": lambda: api.render_neural(ctx, vol, sc.lights, g, cam, 16, 0.0, seed + 52),
+        "path_tracer_16spp": lambda: api.render_pathtraced(ctx, vol, sc.lights, g, cam, 16, 16, seed=seed + 53),
+    }
+    out = {"reference": "path tracer, %d spp, %dx%d, g = 0" % (ref_spp, cam.width, cam.height)}
+    for name, fn in runs.items():
+        img, fps = timed(fn)
+        out[name] = {"rmse": api.image_rmse(ctx, img, ref), "frames_per_s": fps}
+    return out
 
 
 # Staggered KNN schedule (Sec. 3.5.2, Table 1, the 6M-photon row: this
