@@ -395,7 +395,7 @@ def main():
             line["cpu_baseline"] = cpu_baseline(vol_t.cpu().numpy(), tf_t.cpu().numpy(), lights, cams, seed,
                                                 rows=args.cpu_rows, brick=args.brick,
                                                 brick_primary=args.brick_primary, brick_shadow=args.brick_shadow,
-                                                **oracle_field(field))
+                                                **oracle_field(seed))
         except Exception as e:  # reported, not fatal
             line["cpu_baseline"] = {"error": repr(e)[:200]}
     if rank == 0:
@@ -404,12 +404,15 @@ def main():
         dist.destroy_process_group()
 
 
-def oracle_field(field):
+def oracle_field(seed):
+    """The CPU baseline's field: a Kaiming-initialised 4x128 fp8 field of the
+    bench's shape with scales calibrated by the oracle (the same per-sample
+    work as the trained field; nothing taken from the GPU path)."""
     from oracle import field as F
-    desc = F.FieldDesc(FREQS, HIDDEN, N_HIDDEN, F.PREC_FP8, field.psi, 0)
-    w = field.get_weights().cpu().numpy().astype(np.float64)
-    s = field_scales(field)
-    return dict(weights=w, desc=desc, scales=s)
+    desc = F.FieldDesc(FREQS, HIDDEN, N_HIDDEN, F.PREC_FP8, 5.0, seed + 3)
+    w = F.init_weights(desc).astype(np.float64)
+    return dict(weights=w, desc=desc,
+                scales=F.fp8_calibrate(w, calibration_queries().numpy().astype(np.float64), desc))
 
 
 def march_workload(ctx, vol, lights, frame, field, seed, args):
@@ -730,14 +733,6 @@ def calibration_queries():
     return cal.contiguous()
 
 
-def field_scales(field):
-    # the oracle computes its own scales from the same calibration queries
-    from oracle import field as F
-    cal = calibration_queries().numpy().astype(np.float64)
-    desc = F.FieldDesc(FREQS, HIDDEN, N_HIDDEN, F.PREC_FP8, field.psi, 0)
-    return F.fp8_calibrate(field.get_weights().cpu().numpy().astype(np.float64), cal, desc)
-
-
 def run_reference(args, dev, seed):
     """The oracle as the reference arm: each step renders a bounded sample (240
     pixels of the middle row at full spp) of the same workload on the host
@@ -745,13 +740,9 @@ def run_reference(args, dev, seed):
     import torch
     vol_t, tf_t, lights, cams = setup_scene(dev)
     vol_h, tf_h = vol_t.cpu().numpy(), tf_t.cpu().numpy()
-    from oracle import field as F
     # a 4x128 fp8 field of the bench's shape (Kaiming init, calibrated scales):
     # the same per-sample work as the trained field
-    desc = F.FieldDesc(FREQS, HIDDEN, N_HIDDEN, F.PREC_FP8, 5.0, seed + 3)
-    w = F.init_weights(desc).astype(np.float64)
-    fld = dict(weights=w, desc=desc, scales=F.fp8_calibrate(w, calibration_queries().numpy().astype(np.float64),
-                                                            desc))
+    fld = oracle_field(seed)
     times = []
     for i in range(args.warmup + args.steps):
         r = cpu_baseline(vol_h, tf_h, lights, cams, seed, rows=1, brick=args.brick,

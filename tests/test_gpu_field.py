@@ -63,8 +63,8 @@ def test_forward_empty_and_single(pf_ctx):
     assert y.shape == (0, 3)
     q = _queries(1)
     y1 = fld.forward(torch.from_numpy(q).cuda()).cpu().numpy()
-    ref, _ = F.forward(fld.get_weights().cpu().numpy().astype(np.float64), q.astype(np.float64),
-                       F.FieldDesc(12, 64, 3, 0, 5.0, 1))
+    desc = F.FieldDesc(12, 64, 3, 0, 5.0, 1)
+    ref, _ = F.forward(F.init_weights(desc).astype(np.float64), q.astype(np.float64), desc)
     assert np.abs(y1 - ref).max() < 1e-5
 
 
@@ -97,7 +97,7 @@ def test_autograd_function(pf_ctx):
 
 def test_adam_step(pf_ctx):
     fld = api.Field(pf_ctx, 12, 64, 3, "f32", 5.0, seed=2)
-    w0 = fld.get_weights().cpu().numpy().astype(np.float64)
+    w0 = F.init_weights(F.FieldDesc(12, 64, 3, F.PREC_F32, 5.0, 2)).astype(np.float64)   # the field's seeded init
     g = np.random.default_rng(1).normal(size=w0.size).astype(np.float32)
     fld.adam(torch.from_numpy(g).cuda(), 1e-2, 0.9, 0.99, 1e-8)
     w1 = fld.get_weights().cpu().numpy()

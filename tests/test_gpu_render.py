@@ -59,9 +59,9 @@ def test_march_with_f32_field(pf_ctx, orc):
     sc = I.scene_small(64, 64, 64, 4)
     vol = api.Volume.from_inputs(sc.volume)
     fld = api.Field(pf_ctx, 12, 64, 3, "f32", 5.0, seed=3)
-    w = fld.get_weights().cpu().numpy()
     desc = F.FieldDesc(12, 64, 3, F.PREC_F32, 5.0, 3)
-    assert np.array_equal(w, F.init_weights(desc))           # seeded init is bit-identical
+    w = F.init_weights(desc)
+    assert np.array_equal(fld.get_weights().cpu().numpy(), w)   # seeded init is bit-identical
     img = api.render_neural(pf_ctx, vol, sc.lights, sc.g, sc.camera, sc.spp, 0.5, seed=5, field=fld)
     pf_ctx.sync()
     ref = orc.render_neural(sc.volume, sc.lights, sc.g, sc.camera, sc.spp, 0.5, 5, weights=w.astype(np.float64), desc=desc)
