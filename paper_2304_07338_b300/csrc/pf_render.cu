@@ -634,6 +634,12 @@ __global__ void __launch_bounds__(128) k_raymarch(Vol V, DevLights L, CamF cam, 
   }
 }
 
+// out[p] = off[p * spp], p <= n_pix: the query offsets at pixel boundaries.
+__global__ void k_pixel_offsets(const uint64_t* __restrict__ off, int spp, int64_t n_pix, uint64_t* __restrict__ out) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p <= n_pix) out[p] = off[p * spp];
+}
+
 __global__ void k_iota(uint32_t* __restrict__ v, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) v[i] = (uint32_t)i;
@@ -854,14 +860,19 @@ extern "C" pf_status pf_render_raymarched(pf_ctx* ctx, const pf_volume* vol, con
     RM_LAUNCH(false, (int64_t)0, n_rays, counts, nullptr, (uint64_t)0, nullptr, nullptr, nullptr);
   }
   PF_TRY(pf_scan_u32(ctx, counts, off, n_rays));
-  std::vector<uint64_t> hoff((size_t)n_rays + 1);
-  PF_CUDA(ctx, cudaMemcpyAsync(hoff.data(), off, hoff.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
+  // the offsets at pixel boundaries plan the chunks on the host
+  uint64_t* poff;
+  PF_TRY(pf_scratch(ctx, WS_CELL_KEY, (size_t)(n_pix + 1) * sizeof(uint64_t), (void**)&poff));
+  k_pixel_offsets<<<(unsigned)((n_pix + 1 + 255) / 256), 256, 0, ctx->stream>>>(off, spp, n_pix, poff);
+  PF_CUDA(ctx, cudaGetLastError());
+  std::vector<uint64_t> hoff((size_t)n_pix + 1);
+  PF_CUDA(ctx, cudaMemcpyAsync(hoff.data(), poff, hoff.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
   PF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   // query buffer: 2^23 queries, or one pixel's worth if that is more
   uint64_t cap = 1ull << 23, most = 0;
-  for (int64_t p = 0; p < n_pix; ++p) most = std::max(most, hoff[(size_t)(p + 1) * spp] - hoff[(size_t)p * spp]);
+  for (int64_t p = 0; p < n_pix; ++p) most = std::max(most, hoff[(size_t)p + 1] - hoff[(size_t)p]);
   cap = std::max(cap, most);
-  cap = std::min<uint64_t>(cap, std::max<uint64_t>(hoff[(size_t)n_rays], 1));
+  cap = std::min<uint64_t>(cap, std::max<uint64_t>(hoff[(size_t)n_pix], 1));
   float *q, *wgt, *li;
   uint32_t* iota;
   PF_TRY(pf_scratch(ctx, WS_COMPACT_Q, (size_t)cap * 6 * sizeof(float), (void**)&q));
@@ -873,14 +884,14 @@ extern "C" pf_status pf_render_raymarched(pf_ctx* ctx, const pf_volume* vol, con
   for (int64_t p0 = 0; p0 < n_pix;) {
     // the most whole pixels from p0 whose queries fit the buffer
     int64_t lo = p0 + 1, hi = n_pix;
-    const uint64_t base = hoff[(size_t)p0 * spp];
+    const uint64_t base = hoff[(size_t)p0];
     while (lo < hi) {
       const int64_t mid = (lo + hi + 1) / 2;
-      if (hoff[(size_t)mid * spp] - base <= cap) lo = mid;
+      if (hoff[(size_t)mid] - base <= cap) lo = mid;
       else hi = mid - 1;
     }
     const int64_t p1 = lo;
-    const int64_t nq = (int64_t)(hoff[(size_t)p1 * spp] - base);
+    const int64_t nq = (int64_t)(hoff[(size_t)p1] - base);
     {
       StageTimer tm(ctx, PF_STAGE_CAMERA);
       RM_LAUNCH(true, p0 * spp, (p1 - p0) * spp, nullptr, off, base, q, wgt, direct);
