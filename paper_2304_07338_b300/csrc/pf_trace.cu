@@ -11,7 +11,7 @@
 //   k_scatter        slot records -> CSR order (position within a key taken
 //                    by an atomic cursor), positions with them (x, y, z, id)
 //                    for the KNN estimate;
-//   k_key_flux       per-key power sums in FP64 -> float;
+//   k_key_flux       per-key power sums in FP64 -> float (thread per key);
 //   k_cell_sigma     mean sigma_t over the voxel centres of every cache cell;
 //   k_occupancy + scan + k_occupied_list -> ascending occupied cells.
 // Compiled with -fmad=false: see pf_device.cuh.
@@ -32,13 +32,15 @@ struct TraceArgs {
   uint64_t N, seed, n_photons;
 };
 
+// One warp per block: a photon path's length varies a lot, and a one-warp
+// block leaves the SM as soon as its own 32 photons are done (no block-wide
+// barrier, no waiting for other warps); each block writes its FP64 tallies to
+// its own row of tally_part, summed by k_tally_reduce.
+constexpr int kTraceThreads = 32;
 template <int DT>
-__global__ void __launch_bounds__(128, 8) k_trace_photons(TraceArgs A, float4* __restrict__ slots,
+__global__ void __launch_bounds__(kTraceThreads, 32) k_trace_photons(TraceArgs A, float4* __restrict__ slots,
                                                        float4* __restrict__ slot_pos, uint8_t* __restrict__ nrec, uint32_t* __restrict__ counts,
-                                                       double* __restrict__ tally, uint32_t* err) {
-  __shared__ double s_tally[15];
-  if (threadIdx.x < 15) s_tally[threadIdx.x] = 0.0;
-  __syncthreads();
+                                                       double* __restrict__ tally_part, uint32_t* err) {
   uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double t_em[3] = {0, 0, 0}, t_es[3] = {0, 0, 0}, t_ab[3] = {0, 0, 0}, t_tr[3] = {0, 0, 0}, t_rr[3] = {0, 0, 0};
   if (p < A.n_photons) {
@@ -128,7 +130,7 @@ __global__ void __launch_bounds__(128, 8) k_trace_photons(TraceArgs A, float4* _
     if (alive) { t_es[0] += P0; t_es[1] += P1; t_es[2] += P2; }
     nrec[p] = (uint8_t)n;
   }
-  // block reduction of the FP64 tallies (warp shuffles, then shared atomics)
+  // the block's (warp's) FP64 tallies: shuffles, then one row of tally_part
   double* parts[5] = {t_em, t_es, t_ab, t_tr, t_rr};
 #pragma unroll
   for (int a = 0; a < 5; ++a)
@@ -136,10 +138,27 @@ __global__ void __launch_bounds__(128, 8) k_trace_photons(TraceArgs A, float4* _
     for (int c = 0; c < 3; ++c) {
       double v = parts[a][c];
       for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-      if ((threadIdx.x & 31) == 0) atomicAdd(&s_tally[3 * a + c], v);
+      if (threadIdx.x == 0) tally_part[(size_t)blockIdx.x * 15 + 3 * a + c] = v;
     }
+}
+
+// tally[i] += sum over the rows of tally_part (FP64; tally zeroed first).
+// The rows are read as one contiguous array; with 240 threads per block and a
+// grid stride that is a multiple of 15, every thread always meets the same
+// tally index.
+constexpr int kTallyThreads = 240;
+__global__ void __launch_bounds__(kTallyThreads) k_tally_reduce(const double* __restrict__ part, int64_t rows,
+                                                              double* __restrict__ tally) {
+  __shared__ double s[15];
+  if (threadIdx.x < 15) s[threadIdx.x] = 0.0;
   __syncthreads();
-  if (threadIdx.x < 15) atomicAdd(&tally[threadIdx.x], s_tally[threadIdx.x]);
+  const int64_t n = rows * 15;
+  const int64_t stride = (int64_t)gridDim.x * kTallyThreads;
+  double v = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * kTallyThreads + threadIdx.x; e < n; e += stride) v += part[e];
+  atomicAdd(&s[threadIdx.x % 15], v);
+  __syncthreads();
+  if (threadIdx.x < 15) atomicAdd(&tally[threadIdx.x], s[threadIdx.x]);
 }
 
 // Move slot records into CSR order.
@@ -161,23 +180,18 @@ __global__ void k_scatter(const float4* __restrict__ slots, const float4* __rest
   rpos[pos] = x;
 }
 
-// Per-key power sums: one warp per key, FP64 lanes, rounded once.
+// Per-key power sums: one thread per key (keys hold few records on average),
+// FP64, rounded once.
 __global__ void k_key_flux(const float4* __restrict__ recs, const uint64_t* __restrict__ offsets, int64_t n_keys,
                            float* __restrict__ flux) {
-  int64_t key = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
+  const int64_t key = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (key >= n_keys) return;
   double s0 = 0, s1 = 0, s2 = 0;
-  for (uint64_t n = offsets[key] + lane; n < offsets[key + 1]; n += 32) {
-    float4 b = recs[2 * n + 1];
+  for (uint64_t n = offsets[key]; n < offsets[key + 1]; ++n) {
+    const float4 b = recs[2 * n + 1];
     s0 += b.y; s1 += b.z; s2 += b.w;
   }
-  for (int off = 16; off > 0; off >>= 1) {
-    s0 += __shfl_down_sync(0xffffffffu, s0, off);
-    s1 += __shfl_down_sync(0xffffffffu, s1, off);
-    s2 += __shfl_down_sync(0xffffffffu, s2, off);
-  }
-  if (lane == 0) { flux[3 * key] = (float)s0; flux[3 * key + 1] = (float)s1; flux[3 * key + 2] = (float)s2; }
+  flux[3 * key] = (float)s0; flux[3 * key + 1] = (float)s1; flux[3 * key + 2] = (float)s2;
 }
 
 // First voxel index whose centre lies in cache cell c (axis of n voxels, res cells).
@@ -361,9 +375,10 @@ extern "C" pf_status pf_build_photon_cache(pf_ctx* ctx, const pf_volume* vol, co
   CK(cudaMalloc(&c->counts, (size_t)n_keys * sizeof(uint32_t)));
   CK(cudaMalloc(&cursor, (size_t)std::max<int64_t>(n_keys, nc) * sizeof(uint32_t)));
   CK(cudaMalloc(&c->offsets, (size_t)(n_keys + 1) * sizeof(uint64_t)));
-  CK(cudaMalloc(&tally_dev, 15 * sizeof(double)));
+  const int64_t trace_blocks = (int64_t)((P + kTraceThreads - 1) / kTraceThreads);
+  CK(cudaMalloc(&tally_dev, (size_t)(trace_blocks + 1) * 15 * sizeof(double)));   // per-block rows + the sums
   CK(cudaMemsetAsync(c->counts, 0, (size_t)n_keys * sizeof(uint32_t), ctx->stream));
-  CK(cudaMemsetAsync(tally_dev, 0, 15 * sizeof(double), ctx->stream));
+
 
   StageTimer tm(ctx, PF_STAGE_PHOTONS);
   TraceArgs A;
@@ -371,16 +386,25 @@ extern "C" pf_status pf_build_photon_cache(pf_ctx* ctx, const pf_volume* vol, co
   A.L = pf_make_lights(lights, n_lights);
   for (int i = 0; i < 16; ++i) A.g_set[i] = i < n_g ? g_set[i] : 0.f;
   A.n_g = n_g; A.max_bounces = max_bounces; A.res = res; A.use_rr = use_rr; A.N = N; A.seed = seed; A.n_photons = P;
-  unsigned grd = (unsigned)((P + 127) / 128);
-  if (vol->dtype == PF_F32) k_trace_photons<0><<<grd, 128, 0, ctx->stream>>>(A, slots, slot_pos, nrec, c->counts, tally_dev, ctx->err_dev);
-  else if (vol->dtype == PF_F16) k_trace_photons<1><<<grd, 128, 0, ctx->stream>>>(A, slots, slot_pos, nrec, c->counts, tally_dev, ctx->err_dev);
-  else k_trace_photons<2><<<grd, 128, 0, ctx->stream>>>(A, slots, slot_pos, nrec, c->counts, tally_dev, ctx->err_dev);
+  const unsigned grd = (unsigned)trace_blocks;
+  double* tally_sum = tally_dev + (size_t)trace_blocks * 15;
+  if (vol->dtype == PF_F32)
+    k_trace_photons<0><<<grd, kTraceThreads, 0, ctx->stream>>>(A, slots, slot_pos, nrec, c->counts, tally_dev, ctx->err_dev);
+  else if (vol->dtype == PF_F16)
+    k_trace_photons<1><<<grd, kTraceThreads, 0, ctx->stream>>>(A, slots, slot_pos, nrec, c->counts, tally_dev, ctx->err_dev);
+  else
+    k_trace_photons<2><<<grd, kTraceThreads, 0, ctx->stream>>>(A, slots, slot_pos, nrec, c->counts, tally_dev, ctx->err_dev);
+  CK(cudaGetLastError());
+  CK(cudaMemsetAsync(tally_sum, 0, 15 * sizeof(double), ctx->stream));
+  k_tally_reduce<<<(unsigned)std::min<int64_t>((trace_blocks * 15 + kTallyThreads - 1) / kTallyThreads,
+                                               (int64_t)ctx->num_sms * 8),
+                   kTallyThreads, 0, ctx->stream>>>(tally_dev, trace_blocks, tally_sum);
   CK(cudaGetLastError());
   pf_status st = pf_scan_u32(ctx, c->counts, c->offsets, n_keys);
   if (st != PF_OK) { cudaFree(slots); cudaFree(slot_pos); cudaFree(nrec); cudaFree(cursor); cudaFree(tally_dev); return fail(st); }
   uint64_t n_rec = 0;
   CK(cudaMemcpyAsync(&n_rec, c->offsets + n_keys, sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaMemcpyAsync(c->tally, tally_dev, 15 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(c->tally, tally_sum, 15 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   c->n_records = (int64_t)n_rec;
   CK(cudaMalloc(&c->recs, (size_t)std::max<uint64_t>(n_rec, 1) * 2 * sizeof(float4)));
@@ -391,7 +415,7 @@ extern "C" pf_status pf_build_photon_cache(pf_ctx* ctx, const pf_volume* vol, co
                                                                         c->recs, c->pos);
   CK(cudaGetLastError());
   CK(cudaMalloc(&c->flux, (size_t)n_keys * 3 * sizeof(float)));
-  k_key_flux<<<(unsigned)((n_keys * 32 + 255) / 256), 256, 0, ctx->stream>>>(c->recs, c->offsets, n_keys, c->flux);
+  k_key_flux<<<(unsigned)((n_keys + 255) / 256), 256, 0, ctx->stream>>>(c->recs, c->offsets, n_keys, c->flux);
   CK(cudaGetLastError());
   CK(cudaMalloc(&c->cell_sigma, (size_t)nc * sizeof(float)));
   unsigned gc = (unsigned)((nc + 127) / 128);
