@@ -560,10 +560,18 @@ def training_workload(ctx, seed, steps=2000):
     from paper_2304_07338_b300 import api, inputs as I
     sc = I.scene_judge()
     vol = api.Volume.from_inputs(sc.volume)
-    t0 = time.perf_counter()
+    # photon caches: one warm-up build, then the best of three (each build
+    # allocates its device buffers, whose first-touch cost varies)
     cache = api.build_photon_cache(ctx, vol, sc.lights, sc.g_set, 1 << 20, 16, 64, seed=seed + 20)
-    ctx.sync()
-    t_cache = time.perf_counter() - t0
+    times = []
+    for _ in range(3):
+        cache.free()
+        ctx.sync()
+        t0 = time.perf_counter()
+        cache = api.build_photon_cache(ctx, vol, sc.lights, sc.g_set, 1 << 20, 16, 64, seed=seed + 20)
+        ctx.sync()
+        times.append(time.perf_counter() - t0)
+    t_cache = min(times)
     fld = api.Field(ctx, 12, 64, 4, "bf16", 5.0, seed=seed + 21)
     fld.train(cache, steps=5, batch=1 << 18, lr=1e-2, seed=seed + 22)      # warm-up
     fld2 = api.Field(ctx, 12, 64, 4, "bf16", 5.0, seed=seed + 21)

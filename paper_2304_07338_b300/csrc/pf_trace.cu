@@ -2,8 +2,9 @@
 // the training-sample generator reads (Sec. 3.3).
 //
 // Pipeline (all stream-ordered, no host round trip except two scalars):
-//   k_trace_photons  one thread per photon; emission, delta tracking, HG
-//                    scattering, Russian roulette; record j (j >= 2) goes to
+//   k_trace_photons  persistent warps, one photon per lane at a time (lanes
+//                    refill from a global counter); emission, delta tracking,
+//                    HG scattering, Russian roulette; record j (j >= 2) goes to
 //                    the photon's own slot p*(max_bounces-1) + j-2 -- so no
 //                    global append counter -- and bumps counts[key]; the
 //                    interaction position goes to a parallel slot array;
@@ -32,114 +33,143 @@ struct TraceArgs {
   uint64_t N, seed, n_photons;
 };
 
-// One warp per block: a photon path's length varies a lot, and a one-warp
-// block leaves the SM as soon as its own 32 photons are done (no block-wide
-// barrier, no waiting for other warps); each block writes its FP64 tallies to
-// its own row of tally_part, summed by k_tally_reduce.
+// Persistent warps (one per block) that refill: a photon path's length
+// varies a lot (most photons leave the box after zero or one collision, a
+// few scatter a dozen times), so a thread per photon leaves most lanes idle
+// while the warp's longest path finishes.  Here every lane carries one photon
+// at a time and the loop body advances each lane by one interaction; a lane
+// whose photon is finished takes the next photon id from a global counter
+// (one atomic per warp and round).  A photon's arithmetic and random numbers
+// are those of a thread-per-photon tracer (its Philox stream is its id), so
+// records and bins do not depend on which lane traced it.  FP64 tallies
+// accumulate per lane in shared memory; each block writes one row of
+// tally_part, summed by k_tally_reduce.
 constexpr int kTraceThreads = 32;
 template <int DT>
 __global__ void __launch_bounds__(kTraceThreads, 32) k_trace_photons(TraceArgs A, float4* __restrict__ slots,
                                                        float4* __restrict__ slot_pos, uint8_t* __restrict__ nrec, uint32_t* __restrict__ counts,
-                                                       double* __restrict__ tally_part, uint32_t* err) {
-  uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double t_em[3] = {0, 0, 0}, t_es[3] = {0, 0, 0}, t_ab[3] = {0, 0, 0}, t_tr[3] = {0, 0, 0}, t_rr[3] = {0, 0, 0};
-  if (p < A.n_photons) {
-    const Vol& V = A.V;
-    int l = (int)(p / ((uint64_t)A.n_g * A.N));
-    int gi = (int)((p / A.N) % (uint64_t)A.n_g);
-    const DevLight& Lt = A.L.l[l];
-    float g = A.g_set[gi];
-    int S = A.max_bounces - 1 > 0 ? A.max_bounces - 1 : 1;
-    float4* my = slots + 2 * (size_t)p * S;
-    float4* my_pos = slot_pos + (size_t)p * S;
-    Rng rng(A.seed, TAG_PHOTON, p, 0);
-    float u[4]; rng.uni4(u);
-    V3 o, d;
-    float P0, P1, P2;
-    if (Lt.kind == 0) {
-      V3 v = normalize(v3(Lt.v[0], Lt.v[1], Lt.v[2]));
-      V3 e1, e2; onb(v, &e1, &e2);
-      float side = 1.7320508075688772f;
-      float a = (u[0] - 0.5f) * side, b = (u[1] - 0.5f) * side;
-      o = v3(0.5f + v.x + a * e1.x + b * e2.x, 0.5f + v.y + a * e1.y + b * e2.y, 0.5f + v.z + a * e1.z + b * e2.z);
-      d = v3(-v.x, -v.y, -v.z);
-      P0 = Lt.rgb[0] * 3.0f / (float)A.N; P1 = Lt.rgb[1] * 3.0f / (float)A.N; P2 = Lt.rgb[2] * 3.0f / (float)A.N;
-    } else {
-      float z = 1.0f - 2.0f * u[0];
-      float r = sqrtf(mx(0.0f, 1.0f - z * z));
-      float sp, cp; own_sincos2pif(u[1], &sp, &cp);
-      d = v3(r * cp, r * sp, z);
-      o = v3(Lt.v[0], Lt.v[1], Lt.v[2]);
-      const float fpi = 12.566370614359172f;
-      P0 = Lt.rgb[0] * fpi / (float)A.N; P1 = Lt.rgb[1] * fpi / (float)A.N; P2 = Lt.rgb[2] * fpi / (float)A.N;
-    }
-    t_em[0] = P0; t_em[1] = P1; t_em[2] = P2;
-    float pe_max = mx(P0, mx(P1, P2));
-    int n = 0, j = 0;
-    float t0 = 0.f, t1 = 0.f;
-    bool alive = true;
-    bool inside = box_hit(o, d, &t0, &t1);
-    float t = t0;
-    uint32_t nfetch = 0;
-    const uint32_t R = (uint32_t)A.res;
-    while (alive && inside) {
-      float th;
-      if (!delta_track<DT>(V, o, d, t, t1, rng, &th, err, nfetch)) break;
-      V3 x = along(o, d, th);
-      j = j + 1;
-      float sig; V3 alb;
-      medium_at<DT>(V, x, &sig, &alb);
-      if (j >= 2) {
-        int bx = (int)floorf(x.x * (float)A.res), by = (int)floorf(x.y * (float)A.res), bz = (int)floorf(x.z * (float)A.res);
-        bx = min(max(bx, 0), A.res - 1); by = min(max(by, 0), A.res - 1); bz = min(max(bz, 0), A.res - 1);
-        uint32_t bin = (uint32_t)bx + R * ((uint32_t)by + R * (uint32_t)bz);
-        uint32_t key = (uint32_t)(l * A.n_g + gi) * (R * R * R) + bin;
-        my[2 * n + 0] = make_float4(__uint_as_float(key), __uint_as_float((uint32_t)(p << 4) | (uint32_t)n), d.x, d.y);
-        my[2 * n + 1] = make_float4(d.z, P0, P1, P2);
-        my_pos[n] = make_float4(x.x, x.y, x.z, 0.0f);
-        atomicAdd(&counts[key], 1u);
-        n = n + 1;
-      }
-      float Q0 = P0 * alb.x, Q1 = P1 * alb.y, Q2 = P2 * alb.z;
-      t_ab[0] += (double)P0 - (double)Q0; t_ab[1] += (double)P1 - (double)Q1; t_ab[2] += (double)P2 - (double)Q2;
-      P0 = Q0; P1 = Q1; P2 = Q2;
-      if (j == A.max_bounces) {
-        t_tr[0] += P0; t_tr[1] += P1; t_tr[2] += P2;
-        alive = false;
-        break;
-      }
-      float w[4]; rng.uni4(w);
-      V3 nd = hg_sample(g, d, w[0], w[1]);
-      if (A.use_rr && j >= 3) {
-        float q = mx(P0, mx(P1, P2)) / pe_max;
-        if (q > 1.0f) q = 1.0f;
-        if (!(w[2] < q)) {
-          t_rr[0] += P0; t_rr[1] += P1; t_rr[2] += P2;
-          alive = false;
-          break;
-        }
-        float n0 = P0 / q, n1 = P1 / q, n2 = P2 / q;
-        t_rr[0] -= (double)n0 - (double)P0; t_rr[1] -= (double)n1 - (double)P1; t_rr[2] -= (double)n2 - (double)P2;
-        P0 = n0; P1 = n1; P2 = n2;
-      }
-      o = x; d = nd;
-      float a0, a1;
-      if (!box_hit(o, d, &a0, &a1)) break;
-      t = 0.0f; t1 = a1;
-    }
-    if (alive) { t_es[0] += P0; t_es[1] += P1; t_es[2] += P2; }
+                                                       unsigned long long* __restrict__ next, double* __restrict__ tally_part,
+                                                       uint32_t* err) {
+  __shared__ double s_t[15][kTraceThreads];        // emitted, escaped, absorbed, truncated, RR net (x 3 channels)
+  const int lane = threadIdx.x;
+#pragma unroll
+  for (int i = 0; i < 15; ++i) s_t[i][lane] = 0.0;
+  const Vol& V = A.V;
+  const int S = A.max_bounces - 1 > 0 ? A.max_bounces - 1 : 1;
+  const uint32_t R = (uint32_t)A.res;
+  bool has = false;
+  uint64_t p = 0;
+  int l = 0, gi = 0, j = 0, n = 0;
+  float g = 0.f, t = 0.f, t1 = 0.f, P0 = 0.f, P1 = 0.f, P2 = 0.f, pe_max = 1.f;
+  V3 o = v3(0.f, 0.f, 0.f), d = o;
+  Rng rng(0, 0, 0, 0);
+  uint32_t nfetch = 0;
+  auto finish = [&](bool escaped) {
+    if (escaped) { s_t[3][lane] += P0; s_t[4][lane] += P1; s_t[5][lane] += P2; }
     nrec[p] = (uint8_t)n;
-  }
-  // the block's (warp's) FP64 tallies: shuffles, then one row of tally_part
-  double* parts[5] = {t_em, t_es, t_ab, t_tr, t_rr};
-#pragma unroll
-  for (int a = 0; a < 5; ++a)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      double v = parts[a][c];
-      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-      if (threadIdx.x == 0) tally_part[(size_t)blockIdx.x * 15 + 3 * a + c] = v;
+    has = false;
+  };
+  for (;;) {
+    // refill the lanes without a photon
+    const unsigned need = __ballot_sync(0xffffffffu, !has);
+    if (need) {
+      const int leader = __ffs(need) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(next, (unsigned long long)__popc(need));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (!has) {
+        const uint64_t qid = base + (uint64_t)__popc(need & ((1u << lane) - 1u));
+        if (qid < A.n_photons) {
+          p = qid;
+          has = true;
+          l = (int)(p / ((uint64_t)A.n_g * A.N));
+          gi = (int)((p / A.N) % (uint64_t)A.n_g);
+          const DevLight& Lt = A.L.l[l];
+          g = A.g_set[gi];
+          rng = Rng(A.seed, TAG_PHOTON, p, 0);
+          float u[4]; rng.uni4(u);
+          if (Lt.kind == 0) {
+            V3 v = normalize(v3(Lt.v[0], Lt.v[1], Lt.v[2]));
+            V3 e1, e2; onb(v, &e1, &e2);
+            float side = 1.7320508075688772f;
+            float a = (u[0] - 0.5f) * side, b = (u[1] - 0.5f) * side;
+            o = v3(0.5f + v.x + a * e1.x + b * e2.x, 0.5f + v.y + a * e1.y + b * e2.y, 0.5f + v.z + a * e1.z + b * e2.z);
+            d = v3(-v.x, -v.y, -v.z);
+            P0 = Lt.rgb[0] * 3.0f / (float)A.N; P1 = Lt.rgb[1] * 3.0f / (float)A.N; P2 = Lt.rgb[2] * 3.0f / (float)A.N;
+          } else {
+            float z = 1.0f - 2.0f * u[0];
+            float r = sqrtf(mx(0.0f, 1.0f - z * z));
+            float sp, cp; own_sincos2pif(u[1], &sp, &cp);
+            d = v3(r * cp, r * sp, z);
+            o = v3(Lt.v[0], Lt.v[1], Lt.v[2]);
+            const float fpi = 12.566370614359172f;
+            P0 = Lt.rgb[0] * fpi / (float)A.N; P1 = Lt.rgb[1] * fpi / (float)A.N; P2 = Lt.rgb[2] * fpi / (float)A.N;
+          }
+          s_t[0][lane] += P0; s_t[1][lane] += P1; s_t[2][lane] += P2;
+          pe_max = mx(P0, mx(P1, P2));
+          n = 0; j = 0;
+          float t0_ = 0.f, t1_ = 0.f;
+          if (box_hit(o, d, &t0_, &t1_)) { t = t0_; t1 = t1_; }
+          else finish(true);                       // misses the box: escapes at once
+        }
+      }
     }
+    if (!__any_sync(0xffffffffu, has)) break;
+    if (!has) continue;
+    // one interaction of this lane's photon
+    float th;
+    if (!delta_track<DT>(V, o, d, t, t1, rng, &th, err, nfetch)) { finish(true); continue; }
+    const V3 x = along(o, d, th);
+    j = j + 1;
+    float sig; V3 alb;
+    medium_at<DT>(V, x, &sig, &alb);
+    if (j >= 2) {
+      int bx = (int)floorf(x.x * (float)A.res), by = (int)floorf(x.y * (float)A.res), bz = (int)floorf(x.z * (float)A.res);
+      bx = min(max(bx, 0), A.res - 1); by = min(max(by, 0), A.res - 1); bz = min(max(bz, 0), A.res - 1);
+      const uint32_t bin = (uint32_t)bx + R * ((uint32_t)by + R * (uint32_t)bz);
+      const uint32_t key = (uint32_t)(l * A.n_g + gi) * (R * R * R) + bin;
+      float4* my = slots + 2 * (size_t)p * S;
+      my[2 * n + 0] = make_float4(__uint_as_float(key), __uint_as_float((uint32_t)(p << 4) | (uint32_t)n), d.x, d.y);
+      my[2 * n + 1] = make_float4(d.z, P0, P1, P2);
+      slot_pos[(size_t)p * S + n] = make_float4(x.x, x.y, x.z, 0.0f);
+      atomicAdd(&counts[key], 1u);
+      n = n + 1;
+    }
+    const float Q0 = P0 * alb.x, Q1 = P1 * alb.y, Q2 = P2 * alb.z;
+    s_t[6][lane] += (double)P0 - (double)Q0; s_t[7][lane] += (double)P1 - (double)Q1; s_t[8][lane] += (double)P2 - (double)Q2;
+    P0 = Q0; P1 = Q1; P2 = Q2;
+    if (j == A.max_bounces) {
+      s_t[9][lane] += P0; s_t[10][lane] += P1; s_t[11][lane] += P2;
+      finish(false);
+      continue;
+    }
+    float w[4]; rng.uni4(w);
+    const V3 nd = hg_sample(g, d, w[0], w[1]);
+    if (A.use_rr && j >= 3) {
+      float q = mx(P0, mx(P1, P2)) / pe_max;
+      if (q > 1.0f) q = 1.0f;
+      if (!(w[2] < q)) {
+        s_t[12][lane] += P0; s_t[13][lane] += P1; s_t[14][lane] += P2;
+        finish(false);
+        continue;
+      }
+      const float n0 = P0 / q, n1 = P1 / q, n2 = P2 / q;
+      s_t[12][lane] -= (double)n0 - (double)P0; s_t[13][lane] -= (double)n1 - (double)P1; s_t[14][lane] -= (double)n2 - (double)P2;
+      P0 = n0; P1 = n1; P2 = n2;
+    }
+    o = x; d = nd;
+    float a0, a1;
+    if (!box_hit(o, d, &a0, &a1)) { finish(true); continue; }
+    t = 0.0f; t1 = a1;
+  }
+  // the block's (warp's) FP64 tallies: one row of tally_part
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < 15; ++i) {
+    double v = s_t[i][lane];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) tally_part[(size_t)blockIdx.x * 15 + i] = v;
+  }
 }
 
 // tally[i] += sum over the rows of tally_part (FP64; tally zeroed first).
@@ -375,8 +405,15 @@ extern "C" pf_status pf_build_photon_cache(pf_ctx* ctx, const pf_volume* vol, co
   CK(cudaMalloc(&c->counts, (size_t)n_keys * sizeof(uint32_t)));
   CK(cudaMalloc(&cursor, (size_t)std::max<int64_t>(n_keys, nc) * sizeof(uint32_t)));
   CK(cudaMalloc(&c->offsets, (size_t)(n_keys + 1) * sizeof(uint64_t)));
-  const int64_t trace_blocks = (int64_t)((P + kTraceThreads - 1) / kTraceThreads);
-  CK(cudaMalloc(&tally_dev, (size_t)(trace_blocks + 1) * 15 * sizeof(double)));   // per-block rows + the sums
+  // persistent tracing warps: as many one-warp blocks as fit on the device
+  int per_sm = 0;
+  if (vol->dtype == PF_F32) CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_photons<0>, kTraceThreads, 0));
+  else if (vol->dtype == PF_F16) CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_photons<1>, kTraceThreads, 0));
+  else CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_photons<2>, kTraceThreads, 0));
+  const int64_t trace_blocks = std::max<int64_t>(
+      1, std::min<int64_t>((int64_t)ctx->num_sms * std::max(per_sm, 1), (int64_t)((P + kTraceThreads - 1) / kTraceThreads)));
+  // per-block tally rows, the 15 sums, and the photon counter
+  CK(cudaMalloc(&tally_dev, (size_t)(trace_blocks + 2) * 15 * sizeof(double)));
   CK(cudaMemsetAsync(c->counts, 0, (size_t)n_keys * sizeof(uint32_t), ctx->stream));
 
 
@@ -388,12 +425,17 @@ extern "C" pf_status pf_build_photon_cache(pf_ctx* ctx, const pf_volume* vol, co
   A.n_g = n_g; A.max_bounces = max_bounces; A.res = res; A.use_rr = use_rr; A.N = N; A.seed = seed; A.n_photons = P;
   const unsigned grd = (unsigned)trace_blocks;
   double* tally_sum = tally_dev + (size_t)trace_blocks * 15;
+  unsigned long long* next = (unsigned long long*)(tally_sum + 15);
+  CK(cudaMemsetAsync(next, 0, sizeof(unsigned long long), ctx->stream));
   if (vol->dtype == PF_F32)
-    k_trace_photons<0><<<grd, kTraceThreads, 0, ctx->stream>>>(A, slots, slot_pos, nrec, c->counts, tally_dev, ctx->err_dev);
+    k_trace_photons<0><<<grd, kTraceThreads, 0, ctx->stream>>>(A, slots, slot_pos, nrec, c->counts, next, tally_dev,
+                                                                ctx->err_dev);
   else if (vol->dtype == PF_F16)
-    k_trace_photons<1><<<grd, kTraceThreads, 0, ctx->stream>>>(A, slots, slot_pos, nrec, c->counts, tally_dev, ctx->err_dev);
+    k_trace_photons<1><<<grd, kTraceThreads, 0, ctx->stream>>>(A, slots, slot_pos, nrec, c->counts, next, tally_dev,
+                                                                ctx->err_dev);
   else
-    k_trace_photons<2><<<grd, kTraceThreads, 0, ctx->stream>>>(A, slots, slot_pos, nrec, c->counts, tally_dev, ctx->err_dev);
+    k_trace_photons<2><<<grd, kTraceThreads, 0, ctx->stream>>>(A, slots, slot_pos, nrec, c->counts, next, tally_dev,
+                                                                ctx->err_dev);
   CK(cudaGetLastError());
   CK(cudaMemsetAsync(tally_sum, 0, 15 * sizeof(double), ctx->stream));
   k_tally_reduce<<<(unsigned)std::min<int64_t>((trace_blocks * 15 + kTallyThreads - 1) / kTallyThreads,
