@@ -397,13 +397,15 @@ extern "C" pf_status pf_build_photon_cache(pf_ctx* ctx, const pf_volume* vol, co
   uint8_t* nrec = nullptr;
   uint32_t* cursor = nullptr;
   double* tally_dev = nullptr;
-#define CK(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { cudaFree(slots); cudaFree(slot_pos); cudaFree(nrec); cudaFree(cursor); cudaFree(tally_dev); \
-  return fail(pf_cuda_check(ctx, e_, #call)); } } while (0)
-  CK(cudaMalloc(&slots, (size_t)P * S * 2 * sizeof(float4)));
-  CK(cudaMalloc(&slot_pos, (size_t)P * S * sizeof(float4)));
-  CK(cudaMalloc(&nrec, (size_t)P));
+  // the temporaries live in the context's scratch arena (reused by the next
+  // build); the cache's own arrays are allocated for it
+#define CK(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) return fail(pf_cuda_check(ctx, e_, #call)); } while (0)
+#define ST(call) do { pf_status s_ = (call); if (s_ != PF_OK) return fail(s_); } while (0)
+  ST(pf_scratch(ctx, WS_TRACE_SLOTS, (size_t)P * S * 2 * sizeof(float4), (void**)&slots));
+  ST(pf_scratch(ctx, WS_TRACE_POS, (size_t)P * S * sizeof(float4), (void**)&slot_pos));
+  ST(pf_scratch(ctx, WS_TRACE_NREC, (size_t)P, (void**)&nrec));
   CK(cudaMalloc(&c->counts, (size_t)n_keys * sizeof(uint32_t)));
-  CK(cudaMalloc(&cursor, (size_t)std::max<int64_t>(n_keys, nc) * sizeof(uint32_t)));
+  ST(pf_scratch(ctx, WS_TRACE_CURSOR, (size_t)std::max<int64_t>(n_keys, nc) * sizeof(uint32_t), (void**)&cursor));
   CK(cudaMalloc(&c->offsets, (size_t)(n_keys + 1) * sizeof(uint64_t)));
   // persistent tracing warps: as many one-warp blocks as fit on the device
   int per_sm = 0;
@@ -413,7 +415,7 @@ extern "C" pf_status pf_build_photon_cache(pf_ctx* ctx, const pf_volume* vol, co
   const int64_t trace_blocks = std::max<int64_t>(
       1, std::min<int64_t>((int64_t)ctx->num_sms * std::max(per_sm, 1), (int64_t)((P + kTraceThreads - 1) / kTraceThreads)));
   // per-block tally rows, the 15 sums, and the photon counter
-  CK(cudaMalloc(&tally_dev, (size_t)(trace_blocks + 2) * 15 * sizeof(double)));
+  ST(pf_scratch(ctx, WS_TRACE_TALLY, (size_t)(trace_blocks + 2) * 15 * sizeof(double), (void**)&tally_dev));
   CK(cudaMemsetAsync(c->counts, 0, (size_t)n_keys * sizeof(uint32_t), ctx->stream));
 
 
@@ -442,8 +444,7 @@ extern "C" pf_status pf_build_photon_cache(pf_ctx* ctx, const pf_volume* vol, co
                                                (int64_t)ctx->num_sms * 8),
                    kTallyThreads, 0, ctx->stream>>>(tally_dev, trace_blocks, tally_sum);
   CK(cudaGetLastError());
-  pf_status st = pf_scan_u32(ctx, c->counts, c->offsets, n_keys);
-  if (st != PF_OK) { cudaFree(slots); cudaFree(slot_pos); cudaFree(nrec); cudaFree(cursor); cudaFree(tally_dev); return fail(st); }
+  ST(pf_scan_u32(ctx, c->counts, c->offsets, n_keys));
   uint64_t n_rec = 0;
   CK(cudaMemcpyAsync(&n_rec, c->offsets + n_keys, sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(c->tally, tally_sum, 15 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -467,15 +468,10 @@ extern "C" pf_status pf_build_photon_cache(pf_ctx* ctx, const pf_volume* vol, co
   CK(cudaGetLastError());
   // occupancy flags reuse `cursor`; their exclusive scan gets its own buffer
   uint64_t* opos = nullptr;
-  CK(cudaMalloc(&opos, (size_t)(nc + 1) * sizeof(uint64_t)));
-  cudaFree(slots);
-  slots = (float4*)opos;     // freed with the other temporaries below
-  cudaFree(slot_pos);
-  slot_pos = nullptr;
+  ST(pf_scratch(ctx, WS_TRACE_OPOS, (size_t)(nc + 1) * sizeof(uint64_t), (void**)&opos));
   k_occupancy<<<gc, 128, 0, ctx->stream>>>(c->counts, c->cell_sigma, nc, n_lights * n_g, cursor);
   CK(cudaGetLastError());
-  st = pf_scan_u32(ctx, cursor, opos, nc);
-  if (st != PF_OK) { cudaFree(slots); cudaFree(nrec); cudaFree(cursor); cudaFree(tally_dev); return fail(st); }
+  ST(pf_scan_u32(ctx, cursor, opos, nc));
   uint64_t n_occ = 0;
   CK(cudaMemcpyAsync(&n_occ, opos + nc, sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -485,7 +481,7 @@ extern "C" pf_status pf_build_photon_cache(pf_ctx* ctx, const pf_volume* vol, co
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(ctx->stream));
 #undef CK
-  cudaFree(slots); cudaFree(nrec); cudaFree(cursor); cudaFree(tally_dev);
+#undef ST
   pf_status es = pf_check_error_word(ctx);
   if (es != PF_OK) { free_cache(c); return es; }
   *out = c;
