@@ -72,11 +72,13 @@ __global__ void __launch_bounds__(kTraceThreads, 32) k_trace_photons(TraceArgs A
   for (;;) {
     // refill the lanes without a photon
     const unsigned need = __ballot_sync(0xffffffffu, !has);
+    bool exhausted = false;
     if (need) {
       const int leader = __ffs(need) - 1;
       unsigned long long base = 0;
       if (lane == leader) base = atomicAdd(next, (unsigned long long)__popc(need));
       base = __shfl_sync(0xffffffffu, base, leader);
+      exhausted = base + (unsigned long long)__popc(need) >= A.n_photons;
       if (!has) {
         const uint64_t qid = base + (uint64_t)__popc(need & ((1u << lane) - 1u));
         if (qid < A.n_photons) {
@@ -114,7 +116,12 @@ __global__ void __launch_bounds__(kTraceThreads, 32) k_trace_photons(TraceArgs A
         }
       }
     }
-    if (!__any_sync(0xffffffffu, has)) break;
+    // a warp leaves only when it is idle and the counter has run out (its
+    // new photons may all have missed the box and finished at once)
+    if (!__any_sync(0xffffffffu, has)) {
+      if (exhausted) break;
+      continue;
+    }
     if (!has) continue;
     // one interaction of this lane's photon
     float th;
