@@ -490,6 +490,102 @@ __global__ void __launch_bounds__(128, 8) k_path_samples(Vol V, DevLights L, Cam
 
 // acc[p] += r[p][k] for the chunk's samples in order; on the last chunk,
 // out = acc / spp.
+// The path tracer proper: persistent warps (a block's four warps refill
+// independently) in which each lane carries one camera sample's path at a
+// time and the loop body advances every lane by one interaction (free flight
+// to the next real collision, next-event estimation towards every light,
+// Henyey-Greenstein continuation, Russian roulette); a lane whose path ended
+// takes the next sample from a global counter.  Paths differ widely in
+// length, so a thread per sample leaves most lanes idle while the warp's
+// longest path finishes.  A sample's arithmetic and random streams are those
+// of k_path_samples (its streams are keyed by pixel and sample), so the
+// per-sample radiance is the same bit for bit.
+template <int DT>
+__global__ void __launch_bounds__(128, 8) k_path_persistent(Vol V, DevLights L, CamF cam, float g, int spp, int k0, int kc,
+                                                      int max_bounces, int use_rr, uint64_t seed, int64_t n_items,
+                                                      float* __restrict__ slot_rad, unsigned long long* __restrict__ next,
+                                                      uint32_t* err) {
+  const int lane = threadIdx.x & 31;
+  bool has = false;
+  int64_t it = 0;
+  int64_t pix = 0;
+  int k = 0, j = 0;
+  V3 o = v3(0.f, 0.f, 0.f), d = o, rad = o;
+  float beta0 = 1.f, beta1 = 1.f, beta2 = 1.f, t = 0.f, t1 = 0.f;
+  Rng rng(0, 0, 0, 0);
+  uint32_t nfetch = 0;
+  auto finish = [&]() {
+    slot_rad[3 * it + 0] = rad.x; slot_rad[3 * it + 1] = rad.y; slot_rad[3 * it + 2] = rad.z;
+    has = false;
+  };
+  for (;;) {
+    const unsigned need = __ballot_sync(0xffffffffu, !has);
+    bool exhausted = false;
+    if (need) {
+      const int leader = __ffs(need) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(next, (unsigned long long)__popc(need));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      exhausted = (int64_t)(base + (unsigned long long)__popc(need)) >= n_items;
+      if (!has) {
+        const int64_t q = (int64_t)(base + (unsigned long long)__popc(need & ((1u << lane) - 1u)));
+        if (q < n_items) {
+          it = q; has = true;
+          k = k0 + (int)(it % kc);
+          pix = it / kc;
+          const int px = (int)(pix % cam.W), py = (int)(pix / cam.W);
+          rng = Rng(seed, TAG_CAMERA, (uint64_t)pix, (uint32_t)k);
+          float b0[4]; rng.uni4(b0);
+          camera_ray(cam, px, py, b0[0], b0[1], &o, &d);
+          rad = v3(0.f, 0.f, 0.f);
+          beta0 = beta1 = beta2 = 1.f;
+          j = 0;
+          float t0_, t1_;
+          if (box_hit(o, d, &t0_, &t1_)) { t = t0_; t1 = t1_; } else finish();
+        }
+      }
+    }
+    if (!__any_sync(0xffffffffu, has)) {
+      if (exhausted) break;
+      continue;
+    }
+    if (!has) continue;
+    j = j + 1;
+    float th;
+    if (!delta_track<DT>(V, o, d, t, t1, rng, &th, err, nfetch)) { finish(); continue; }
+    const V3 x = along(o, d, th);
+    float sig; V3 alb;
+    medium_at<DT>(V, x, &sig, &alb);
+    V3 Lr = v3(0.f, 0.f, 0.f);
+    for (int l = 0; l < L.n; ++l) {
+      V3 wl, E; float dist;
+      light_geom(L.l[l], x, &wl, &dist, &E);
+      float a0, a1, tend = 0.f;
+      if (box_hit(x, wl, &a0, &a1)) tend = mn(a1, dist);
+      Rng rs(seed, TAG_SHADOW, shadow_item((uint64_t)pix, j, l), (uint32_t)k);
+      float T = ratio_track<DT>(V, x, wl, tend, rs, err, nfetch);
+      float ph = hg_eval(g, dot(d, wl));
+      Lr = v3(Lr.x + ph * T * E.x, Lr.y + ph * T * E.y, Lr.z + ph * T * E.z);
+    }
+    const float c0 = beta0 * alb.x, c1 = beta1 * alb.y, c2 = beta2 * alb.z;
+    rad = v3(rad.x + c0 * Lr.x, rad.y + c1 * Lr.y, rad.z + c2 * Lr.z);
+    beta0 = c0; beta1 = c1; beta2 = c2;
+    if (j == max_bounces) { finish(); continue; }
+    float w[4]; rng.uni4(w);
+    const V3 nd = hg_sample(g, d, w[0], w[1]);
+    if (use_rr && j >= 3) {
+      float q = mx(beta0, mx(beta1, beta2));
+      if (q > 1.f) q = 1.f;
+      if (!(w[2] < q)) { finish(); continue; }
+      beta0 = beta0 / q; beta1 = beta1 / q; beta2 = beta2 / q;
+    }
+    o = x; d = nd;
+    float a0, a1;
+    if (!box_hit(o, d, &a0, &a1)) { finish(); continue; }
+    t = 0.f; t1 = a1;
+  }
+}
+
 __global__ void k_path_accumulate(const float* __restrict__ slot_rad, int64_t n_pix, int kc, int first, int last,
                                   int spp, float* __restrict__ acc, float* __restrict__ out) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -932,6 +1028,8 @@ extern "C" pf_status pf_render_pathtraced(pf_ctx* ctx, const pf_volume* vol, con
   float *rad, *acc;
   PF_TRY(pf_scratch(ctx, WS_SLOT_LD, (size_t)(n_pix * kc * 3) * sizeof(float), (void**)&rad));
   PF_TRY(pf_scratch(ctx, WS_SLOT_ALB, (size_t)(n_pix * 3) * sizeof(float), (void**)&acc));
+  unsigned long long* next;   // the persistent kernel's sample counter
+  PF_TRY(pf_scratch(ctx, WS_MISC, 256, (void**)&next));
   Vol V = pf_make_vol(vol, 0.f, grid);
   DevLights L = pf_make_lights(lights, n_lights);
   CamF C = make_cam(cam);
@@ -939,13 +1037,17 @@ extern "C" pf_status pf_render_pathtraced(pf_ctx* ctx, const pf_volume* vol, con
   for (int k0 = 0; k0 < spp; k0 += (int)kc) {
     int kn = (int)std::min<int64_t>(kc, spp - k0);
     int64_t n_items = n_pix * kn;
-    dim3 grd((unsigned)((n_items + 127) / 128));
+    PF_CUDA(ctx, cudaMemsetAsync(next, 0, sizeof(unsigned long long), ctx->stream));
+    const dim3 pg((unsigned)std::min<int64_t>((int64_t)ctx->num_sms * 8, (n_items + 127) / 128));
     if (vol->dtype == PF_F32)
-      k_path_samples<0><<<grd, 128, 0, ctx->stream>>>(V, L, C, g, spp, k0, kn, max_bounces, use_rr, seed, n_items, rad, ctx->err_dev, ctx->counters);
+      k_path_persistent<0><<<pg, 128, 0, ctx->stream>>>(V, L, C, g, spp, k0, kn, max_bounces, use_rr, seed, n_items, rad,
+                                                        next, ctx->err_dev);
     else if (vol->dtype == PF_F16)
-      k_path_samples<1><<<grd, 128, 0, ctx->stream>>>(V, L, C, g, spp, k0, kn, max_bounces, use_rr, seed, n_items, rad, ctx->err_dev, ctx->counters);
+      k_path_persistent<1><<<pg, 128, 0, ctx->stream>>>(V, L, C, g, spp, k0, kn, max_bounces, use_rr, seed, n_items, rad,
+                                                        next, ctx->err_dev);
     else
-      k_path_samples<2><<<grd, 128, 0, ctx->stream>>>(V, L, C, g, spp, k0, kn, max_bounces, use_rr, seed, n_items, rad, ctx->err_dev, ctx->counters);
+      k_path_persistent<2><<<pg, 128, 0, ctx->stream>>>(V, L, C, g, spp, k0, kn, max_bounces, use_rr, seed, n_items, rad,
+                                                        next, ctx->err_dev);
     PF_CUDA(ctx, cudaGetLastError());
     k_path_accumulate<<<(unsigned)((n_pix + 127) / 128), 128, 0, ctx->stream>>>(rad, n_pix, kn, k0 == 0, k0 + kn >= spp,
                                                                                 spp, acc, out_rgb_dev);
