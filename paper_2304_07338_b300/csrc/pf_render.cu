@@ -257,22 +257,28 @@ __device__ __forceinline__ float thin_majorant(const Vol& V, const Vol& Vw, int 
   return __ldg(V.mg + (cx + V.gx * (cy + V.gy * cz)));
 }
 
-// Next-event estimation of the scattering samples (tracking mode), grid-stride
-// over the cell-ordered compacted list: L_d = sum over lights, in order, of
-// p(d . w_l) T_l E_l with T_l ratio tracked on the shadow ray's own stream;
-// slot_ld[slot] = albedo * L_d.  stats[0] and stats[2] += its lookups.
+// Next-event estimation of the scattering samples (tracking mode): one shadow
+// ray per (light, scattering sample), ratio tracked on the ray's own stream;
+// k_nee_sum then forms L_d = sum over lights, in order, of p(d . w_l) T_l E_l
+// and slot_ld[slot] = albedo * L_d.  stats[0] and stats[2] += its lookups.
+//
+// Work items are the shadow rays in light-major order over the cell-sorted
+// samples (item = l * n + j), so a warp's rays share a light and start close
+// together.  Warps are persistent and refill: a lane whose ray is done takes
+// the next item from a global counter (one atomic per warp and pass), so a
+// warp no longer idles while its longest ray finishes.
 //
 // Ratio tracking's tentative collisions do not depend on the density, only
-// the weights 1 - sigma_t/majorant do.  A warp therefore traces its 32 shadow
-// rays (one light at a time) in passes: each lane walks its ray, recording
-// up to kNeePool collisions (distance, majorant) in the warp's shared-memory
-// pool; then all 32 lanes evaluate the pooled density lookups together,
-// whatever ray they belong to; then each lane multiplies its own factors in
-// collision order.  The floats are those of a walk with the lookups inline
-// (same operations, same order per ray); only the lane doing each lookup
-// changes, so the lanes stay busy while the rays' collision counts differ.
-// The pool lives in shared memory, which the SM carves out of the same
-// storage as the L1 cache that serves the density gathers; it is kept small.
+// the weights 1 - sigma_t/majorant do.  A warp therefore traces its rays in
+// passes: each lane walks its ray, recording up to kNeePool collisions
+// (distance, majorant) in the warp's shared-memory pool; then all 32 lanes
+// evaluate the pooled density lookups together, whatever ray they belong to;
+// then each lane multiplies its own factors in collision order.  The floats
+// are those of a walk with the lookups inline (same operations, same order per
+// ray); only the lane doing each lookup changes, so the lanes stay busy while
+// the rays' collision counts differ.  The pool lives in shared memory, which
+// the SM carves out of the same storage as the L1 cache that serves the
+// density gathers; it is kept small.
 constexpr int kNeePool = 16;                                               // collisions per lane per pass
 constexpr int kNeeWarpFloats = 32 * kNeePool * 2 + 32 * kNeePool / 2 + 32 * 6;  // t/factor, majorant, u16 map; x, w_l
 constexpr int kNeeWarps = 4;
@@ -282,12 +288,13 @@ constexpr int kNeeWarps = 4;
 // m_V(x) / m_Vw (one more uniform after its budget), m_V(x) the majorant of
 // the brick of V holding x, clamped into the current brick of Vw: the kept
 // collisions are those of ratio tracking over V's bricks.
+// contrib [n_lights][n][3]: p(d . w_l) T_l E_l of sorted sample j for light l.
 template <int DT, bool THIN>
 __global__ void __launch_bounds__(128, 6) k_nee(Vol V, Vol Vw, DevLights L, float g, int spp, uint64_t seed,
                                              const float* __restrict__ cq, const float* __restrict__ cdir,
-                                             const float* __restrict__ calb, const uint32_t* __restrict__ cidx,
-                                             const uint32_t* __restrict__ ccount, const uint32_t* __restrict__ perm,
-                                             float* __restrict__ slot_ld, uint32_t* err, unsigned long long* stats) {
+                                             const uint32_t* __restrict__ cidx, const uint32_t* __restrict__ ccount,
+                                             const uint32_t* __restrict__ perm, unsigned long long* __restrict__ next,
+                                             float* __restrict__ contrib, uint32_t* err, unsigned long long* stats) {
   extern __shared__ float pf_nee_smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* pool = pf_nee_smem + warp * kNeeWarpFloats;
@@ -295,101 +302,120 @@ __global__ void __launch_bounds__(128, 6) k_nee(Vol V, Vol Vw, DevLights L, floa
   float* pm = pool + 32 * kNeePool;                        // majorant at the collision
   uint16_t* pmap = (uint16_t*)(pool + 64 * kNeePool);      // pooled entry -> lane * kNeePool + index
   float* pxw = pool + 64 * kNeePool + 16 * kNeePool;       // per lane: origin x (3), direction w_l (3)
-  const uint32_t n = *ccount;
+  const uint64_t n = *ccount;
+  const uint64_t n_items = n * (uint64_t)L.n;
   uint32_t nfetch = 0;
-  const uint32_t stride = gridDim.x * blockDim.x;
-  // warp-uniform loop: lane j = base + lane, idle when j >= n
-  for (uint32_t base = blockIdx.x * blockDim.x + warp * 32; base < n; base += stride) {
-    const uint32_t j = base + lane;
-    const bool act = j < n;
-    V3 x = v3(0.5f, 0.5f, 0.5f), d = v3(0.f, 0.f, 1.f);
-    uint32_t i = 0, slot = 0;
-    if (act) {
-      i = perm[j];
-      x = v3(cq[6 * (size_t)i + 0], cq[6 * (size_t)i + 1], cq[6 * (size_t)i + 2]);
-      d = v3(cdir[3 * (size_t)i + 0], cdir[3 * (size_t)i + 1], cdir[3 * (size_t)i + 2]);
-      slot = cidx[i];
-    }
-    const uint64_t pix = slot / (uint32_t)spp;
-    const uint32_t k = slot % (uint32_t)spp;
-    V3 Ld = v3(0.f, 0.f, 0.f);
-    for (int l = 0; l < L.n; ++l) {
-      V3 wl, E; float dist;
-      light_geom(L.l[l], x, &wl, &dist, &E);
-      float a0, a1, tend = 0.f;
-      if (box_hit(x, wl, &a0, &a1)) tend = mn(a1, dist);
-      Rng rs(seed, TAG_SHADOW, shadow_item(pix, 1, l), k);
-      Walk<false> W;
-      W.init(THIN ? Vw : V, x, wl, 0.0f);
-      Uniforms U;
-      float T = 1.0f, t = 0.0f;
-      float tau = -own_lnf(1.0f - U.next(rs));
-      float tc = mn(W.exit_t(), tend);
-      bool done = !act;
-      int it = 0;
-      pxw[6 * lane + 0] = x.x; pxw[6 * lane + 1] = x.y; pxw[6 * lane + 2] = x.z;
-      pxw[6 * lane + 3] = wl.x; pxw[6 * lane + 4] = wl.y; pxw[6 * lane + 5] = wl.z;
-      for (;;) {
-        // walk: record up to kNeePool tentative collisions of this lane's ray
-        int cnt = 0;
-        while (!done && cnt < kNeePool) {
-          float seg = tc - t;
-          if (seg < 0.0f) seg = 0.0f;
-          if (W.m > 0.0f && tau < W.m * seg) {
-            const float m = W.m;
-            t = t + tau / m;
-            if (THIN) {
-              const float ut = U.next(rs);
-              const float mf = thin_majorant(V, Vw, W.idx, along(x, wl, t));
-              if (ut * m < mf) {
-                pt[lane * kNeePool + cnt] = t;
-                pm[lane * kNeePool + cnt] = mf;
-                ++cnt;
-              }
-            } else {
-              pt[lane * kNeePool + cnt] = t;
-              pm[lane * kNeePool + cnt] = m;
-              ++cnt;
-            }
-            tau = -own_lnf(1.0f - U.next(rs));
-          } else {
-            tau = tau - W.m * seg;
-            t = tc;
-            if (t >= tend || !W.step(THIN ? Vw : V)) done = true;
-            else tc = mn(W.exit_t(), tend);
-          }
-          if (++it >= kMaxTrackSteps) { atomicOr(err, 1u); done = true; }
+  // the lane's shadow ray
+  bool has = false, done = true;
+  uint64_t item = 0;
+  V3 x = v3(0.5f, 0.5f, 0.5f), wl = v3(0.f, 0.f, 1.f), E = v3(0.f, 0.f, 0.f);
+  float ph = 0.f, T = 1.0f, t = 0.0f, tau = 0.0f, tc = 0.0f, tend = 0.0f;
+  int it = 0;
+  Walk<false> W;
+  Uniforms U;
+  Rng rs(0, 0, 0, 0);
+  for (;;) {
+    // refill: lanes whose ray is done take the next items
+    const unsigned need = __ballot_sync(0xffffffffu, !has);
+    bool exhausted = false;
+    if (need) {
+      const int leader = __ffs(need) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(next, (unsigned long long)__popc(need));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      exhausted = base + (unsigned long long)__popc(need) >= n_items;
+      if (!has) {
+        const uint64_t q = base + (uint64_t)__popc(need & ((1u << lane) - 1u));
+        if (q < n_items) {
+          has = true;
+          item = q;
+          const int l = (int)(q / n);
+          const uint32_t i = perm[q % n];
+          x = v3(cq[6 * (size_t)i + 0], cq[6 * (size_t)i + 1], cq[6 * (size_t)i + 2]);
+          const V3 d = v3(cdir[3 * (size_t)i + 0], cdir[3 * (size_t)i + 1], cdir[3 * (size_t)i + 2]);
+          const uint32_t slot = cidx[i];
+          const uint64_t pix = slot / (uint32_t)spp;
+          const uint32_t k = slot % (uint32_t)spp;
+          float dist;
+          light_geom(L.l[l], x, &wl, &dist, &E);
+          float a0, a1;
+          tend = 0.f;
+          if (box_hit(x, wl, &a0, &a1)) tend = mn(a1, dist);
+          ph = hg_eval(g, dot(d, wl));
+          rs = Rng(seed, TAG_SHADOW, shadow_item(pix, 1, l), k);
+          W.init(THIN ? Vw : V, x, wl, 0.0f);
+          U = Uniforms();
+          T = 1.0f;
+          t = 0.0f;
+          tau = -own_lnf(1.0f - U.next(rs));
+          tc = mn(W.exit_t(), tend);
+          done = false;
+          it = 0;
+          pxw[6 * lane + 0] = x.x; pxw[6 * lane + 1] = x.y; pxw[6 * lane + 2] = x.z;
+          pxw[6 * lane + 3] = wl.x; pxw[6 * lane + 4] = wl.y; pxw[6 * lane + 5] = wl.z;
         }
-        // pool the warp's collisions
-        int incl = cnt;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-          const int y = __shfl_up_sync(0xffffffffu, incl, off);
-          if (lane >= off) incl += y;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        for (int c = 0; c < cnt; ++c) pmap[incl - cnt + c] = (uint16_t)(lane * kNeePool + c);
-        __syncwarp();
-        for (int e = lane; e < total; e += 32) {
-          const int si = pmap[e];
-          const int o = si / kNeePool;
-          const V3 xo = v3(pxw[6 * o + 0], pxw[6 * o + 1], pxw[6 * o + 2]);
-          const V3 wo = v3(pxw[6 * o + 3], pxw[6 * o + 4], pxw[6 * o + 5]);
-          pt[si] = 1.0f - sigma_at<DT>(V, along(xo, wo, pt[si])) / pm[si];
-          ++nfetch;
-        }
-        __syncwarp();
-        for (int c = 0; c < cnt; ++c) T = T * mx(0.0f, pt[lane * kNeePool + c]);
-        __syncwarp();
-        if (__all_sync(0xffffffffu, done)) break;
       }
-      float ph = hg_eval(g, dot(d, wl));
-      Ld = v3(Ld.x + ph * T * E.x, Ld.y + ph * T * E.y, Ld.z + ph * T * E.z);
     }
-    if (act) {
-      slot_ld[3 * (size_t)slot + 0] = calb[3 * (size_t)i + 0] * Ld.x;
-      slot_ld[3 * (size_t)slot + 1] = calb[3 * (size_t)i + 1] * Ld.y;
-      slot_ld[3 * (size_t)slot + 2] = calb[3 * (size_t)i + 2] * Ld.z;
+    if (!__any_sync(0xffffffffu, has)) {
+      if (exhausted) break;
+      continue;
+    }
+    // walk: record up to kNeePool tentative collisions of this lane's ray
+    int cnt = 0;
+    while (has && !done && cnt < kNeePool) {
+      float seg = tc - t;
+      if (seg < 0.0f) seg = 0.0f;
+      if (W.m > 0.0f && tau < W.m * seg) {
+        const float m = W.m;
+        t = t + tau / m;
+        if (THIN) {
+          const float ut = U.next(rs);
+          const float mf = thin_majorant(V, Vw, W.idx, along(x, wl, t));
+          if (ut * m < mf) {
+            pt[lane * kNeePool + cnt] = t;
+            pm[lane * kNeePool + cnt] = mf;
+            ++cnt;
+          }
+        } else {
+          pt[lane * kNeePool + cnt] = t;
+          pm[lane * kNeePool + cnt] = m;
+          ++cnt;
+        }
+        tau = -own_lnf(1.0f - U.next(rs));
+      } else {
+        tau = tau - W.m * seg;
+        t = tc;
+        if (t >= tend || !W.step(THIN ? Vw : V)) done = true;
+        else tc = mn(W.exit_t(), tend);
+      }
+      if (++it >= kMaxTrackSteps) { atomicOr(err, 1u); done = true; }
+    }
+    // pool the warp's collisions
+    int incl = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int c = 0; c < cnt; ++c) pmap[incl - cnt + c] = (uint16_t)(lane * kNeePool + c);
+    __syncwarp();
+    for (int e = lane; e < total; e += 32) {
+      const int si = pmap[e];
+      const int o = si / kNeePool;
+      const V3 xo = v3(pxw[6 * o + 0], pxw[6 * o + 1], pxw[6 * o + 2]);
+      const V3 wo = v3(pxw[6 * o + 3], pxw[6 * o + 4], pxw[6 * o + 5]);
+      pt[si] = 1.0f - sigma_at<DT>(V, along(xo, wo, pt[si])) / pm[si];
+      ++nfetch;
+    }
+    __syncwarp();
+    for (int c = 0; c < cnt; ++c) T = T * mx(0.0f, pt[lane * kNeePool + c]);
+    __syncwarp();
+    if (has && done) {
+      float* dst = contrib + 3 * (size_t)item;
+      const float w = ph * T;
+      dst[0] = w * E.x; dst[1] = w * E.y; dst[2] = w * E.z;
+      has = false;
     }
   }
   if (stats) {
@@ -399,6 +425,26 @@ __global__ void __launch_bounds__(128, 6) k_nee(Vol V, Vol Vw, DevLights L, floa
       atomicAdd(stats, v);
       atomicAdd(stats + 2, v);
     }
+  }
+}
+
+// L_d of sorted sample j: the lights' contributions summed in light order;
+// slot_ld[slot] = albedo * L_d.
+__global__ void k_nee_sum(const float* __restrict__ contrib, int n_lights, const float* __restrict__ calb,
+                          const uint32_t* __restrict__ cidx, const uint32_t* __restrict__ ccount,
+                          const uint32_t* __restrict__ perm, float* __restrict__ slot_ld) {
+  const uint64_t n = *ccount;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (uint64_t)gridDim.x * blockDim.x) {
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    for (int l = 0; l < n_lights; ++l) {
+      const float* c = contrib + 3 * ((size_t)l * n + j);
+      a0 = a0 + c[0]; a1 = a1 + c[1]; a2 = a2 + c[2];
+    }
+    const uint32_t i = perm[j];
+    const uint32_t slot = cidx[i];
+    slot_ld[3 * (size_t)slot + 0] = calb[3 * (size_t)i + 0] * a0;
+    slot_ld[3 * (size_t)slot + 1] = calb[3 * (size_t)i + 1] * a1;
+    slot_ld[3 * (size_t)slot + 2] = calb[3 * (size_t)i + 2] * a2;
   }
 }
 
@@ -772,16 +818,26 @@ pf_status launch_nee(pf_ctx* ctx, const Vol& V, const Vol& Vw, const DevLights& 
                      const uint32_t* ccount, const uint32_t* perm, float* ld) {
   const size_t bytes = (size_t)kNeeWarps * kNeeWarpFloats * sizeof(float);
   const bool thin = Vw.B > V.B;
+  // per-(light, sample) contributions, sized for the worst case (every slot
+  // scatters), and the work counter (in the bytes after the sample count)
+  float* contrib;
+  PF_TRY(pf_scratch(ctx, WS_NEE_CONTRIB, (size_t)L.n * (size_t)n_max * 3 * sizeof(float), (void**)&contrib));
+  unsigned long long* next = (unsigned long long*)((char*)ccount + 64);
+  PF_CUDA(ctx, cudaMemsetAsync(next, 0, sizeof(unsigned long long), ctx->stream));
   int o = 0;  // resident blocks per SM
   if (thin) PF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_nee<DT, true>, 32 * kNeeWarps, bytes));
   else PF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_nee<DT, false>, 32 * kNeeWarps, bytes));
-  unsigned nb = (unsigned)std::min<int64_t>((n_max + 127) / 128, (int64_t)ctx->num_sms * std::max(o, 1));
+  const unsigned nb = (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>((n_max * L.n + 127) / 128, (int64_t)ctx->num_sms * std::max(o, 1)));
   if (thin)
-    k_nee<DT, true><<<nb, 32 * kNeeWarps, bytes, ctx->stream>>>(V, Vw, L, g, spp, seed, cq, cdir, calb, cidx, ccount,
-                                                                perm, ld, ctx->err_dev, ctx->counters);
+    k_nee<DT, true><<<nb, 32 * kNeeWarps, bytes, ctx->stream>>>(V, Vw, L, g, spp, seed, cq, cdir, cidx, ccount, perm,
+                                                                next, contrib, ctx->err_dev, ctx->counters);
   else
-    k_nee<DT, false><<<nb, 32 * kNeeWarps, bytes, ctx->stream>>>(V, Vw, L, g, spp, seed, cq, cdir, calb, cidx, ccount,
-                                                                 perm, ld, ctx->err_dev, ctx->counters);
+    k_nee<DT, false><<<nb, 32 * kNeeWarps, bytes, ctx->stream>>>(V, Vw, L, g, spp, seed, cq, cdir, cidx, ccount, perm,
+                                                                 next, contrib, ctx->err_dev, ctx->counters);
+  PF_CUDA(ctx, cudaGetLastError());
+  k_nee_sum<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((n_max + 255) / 256, (int64_t)ctx->num_sms * 8)), 256, 0,
+              ctx->stream>>>(contrib, L.n, calb, cidx, ccount, perm, ld);
   PF_CUDA(ctx, cudaGetLastError());
   return PF_OK;
 }
