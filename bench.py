@@ -379,8 +379,8 @@ def main():
         "roofline": roof,
         "clocks": clk,
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        # kernels per frame: camera samples; scan (3) + placement + k_nee; field; compose
-        "gpu_launches": cam_n + 5 * nee_n + fld_n + cmp_n,
+        # kernels per frame: camera samples; scan (3) + placement + k_nee + k_nee_sum; field; compose
+        "gpu_launches": cam_n + 6 * nee_n + fld_n + cmp_n,
     }
     line["setup"] = setup
     if not args.no_equal_rmse:
