@@ -262,9 +262,10 @@ __device__ __forceinline__ float thin_majorant(const Vol& V, const Vol& Vw, int 
 // k_nee_sum then forms L_d = sum over lights, in order, of p(d . w_l) T_l E_l
 // and slot_ld[slot] = albedo * L_d.  stats[0] and stats[2] += its lookups.
 //
-// Work items are the shadow rays in light-major order over the cell-sorted
-// samples (item = l * n + j), so a warp's rays share a light and start close
-// together.  Warps are persistent and refill: a lane whose ray is done takes
+// Work items are the shadow rays, in windows of kNeeWindow cell-sorted
+// samples and light-major inside a window, so a warp's rays share a light and
+// start close together, and a window's voxels serve all lights while they are
+// in L2.  Warps are persistent and refill: a lane whose ray is done takes
 // the next item from a global counter (one atomic per warp and pass), so a
 // warp no longer idles while its longest ray finishes.
 //
@@ -282,6 +283,7 @@ __device__ __forceinline__ float thin_majorant(const Vol& V, const Vol& Vw, int 
 constexpr int kNeePool = 16;                                               // collisions per lane per pass
 constexpr int kNeeWarpFloats = 32 * kNeePool * 2 + 32 * kNeePool / 2 + 32 * 6;  // t/factor, majorant, u16 map; x, w_l
 constexpr int kNeeWarps = 4;
+constexpr uint64_t kNeeWindow = 4096;   // sorted samples whose shadow rays (all lights) run together
 
 // THIN: the rays walk Vw (the brick grid max-pooled by f = Vw.B / V.B) and a
 // tentative collision of that walk at x is kept with probability
@@ -328,9 +330,23 @@ __global__ void __launch_bounds__(128, 6) k_nee(Vol V, Vol Vw, DevLights L, floa
         const uint64_t q = base + (uint64_t)__popc(need & ((1u << lane) - 1u));
         if (q < n_items) {
           has = true;
-          item = q;
-          const int l = (int)(q / n);
-          const uint32_t i = perm[q % n];
+          // windows of kNeeWindow sorted samples, light-major inside a window:
+          // the rays of all lights of a window run while its voxels are in L2
+          const uint64_t per_w = (uint64_t)kNeeWindow * (uint64_t)L.n;
+          const uint64_t full = n / kNeeWindow;
+          uint64_t j;
+          int l;
+          if (q < full * per_w) {
+            const uint64_t r = q % per_w;
+            l = (int)(r / kNeeWindow);
+            j = (q / per_w) * kNeeWindow + r % kNeeWindow;
+          } else {
+            const uint64_t r = q - full * per_w, rem = n - full * kNeeWindow;
+            l = (int)(r / rem);
+            j = full * kNeeWindow + r % rem;
+          }
+          item = (uint64_t)l * n + j;                    // contrib index (light-major)
+          const uint32_t i = perm[j];
           x = v3(cq[6 * (size_t)i + 0], cq[6 * (size_t)i + 1], cq[6 * (size_t)i + 2]);
           const V3 d = v3(cdir[3 * (size_t)i + 0], cdir[3 * (size_t)i + 1], cdir[3 * (size_t)i + 2]);
           const uint32_t slot = cidx[i];
