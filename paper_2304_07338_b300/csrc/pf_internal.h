@@ -15,7 +15,7 @@ enum : uint32_t { PFE_ITER_CAP = 1u, PFE_NONFINITE = 2u, PFE_OVERFLOW = 4u };
 enum ScratchSlot {
   WS_REDUCE = 0, WS_SCAN, WS_QUERY, WS_TARGET, WS_ACT, WS_GRAD, WS_SAMPLES, WS_SLOT_LD, WS_SLOT_ALB,
   WS_SLOT_LI, WS_COMPACT_Q, WS_COMPACT_IDX, WS_LOSS, WS_MISC, WS_GRID, WS_COMPACT_DIR, WS_CELL_HIST, WS_CELL_OFF, WS_CELL_KEY, WS_CELL_PERM, WS_VMASK, WS_GRID_PRIMARY, WS_GRID_SHADOW, WS_HASH_X, WS_HASH_DX, WS_TRACE_SLOTS, WS_TRACE_POS, WS_TRACE_NREC, WS_TRACE_CURSOR, WS_TRACE_TALLY,
-  WS_TRACE_OPOS, WS_NEE_CONTRIB, WS_COUNT
+  WS_TRACE_OPOS, WS_NEE_CONTRIB, WS_KNN_LIST, WS_COUNT
 };
 
 struct pf_ctx {

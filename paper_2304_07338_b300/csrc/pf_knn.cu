@@ -28,6 +28,7 @@
 // float32, each operation rounded: the selection is a pure function of the
 // records, and the record id (photon << 4 | interaction slot) breaks ties.
 #include "pf_internal.h"
+#include <algorithm>
 #include <cstdint>
 
 namespace {
@@ -50,6 +51,8 @@ struct KnnArgs {
   float* lp;
   int32_t* k_out;
   float* r_out;
+  const uint32_t* list;        // warp kernel: the queries to do (nullptr: all B, one warp each)
+  const uint32_t* list_count;
 };
 
 struct Query {
@@ -213,18 +216,9 @@ __device__ __forceinline__ int find_bucket(const uint32_t* h, int per, uint32_t 
   return bucket;
 }
 
-__global__ void __launch_bounds__(32 * kWarps, 5) k_knn(KnnArgs A) {
-  __shared__ uint32_t s_hist[kWarps][kBins];
-  __shared__ unsigned long long s_key[kWarps][kList];
-  __shared__ uint32_t s_idx[kWarps][kList];
-  __shared__ uint32_t s_cnt[kWarps];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t b = (int64_t)blockIdx.x * kWarps + warp;
-  if (b >= A.B) return;
-  uint32_t* hist = s_hist[warp];
-  unsigned long long* lkey = s_key[warp];
-  uint32_t* lidx = s_idx[warp];
-
+// The query's parameters: position, outgoing direction, phase, HG
+// constants, r_max^2, histogram scale and the cover's cell ranges.
+__device__ __forceinline__ Query make_query(const KnnArgs& A, int64_t b) {
   Query Q;
   const float* qb = A.q + 6 * b;
   Q.x = qb[0]; Q.y = qb[1]; Q.z = qb[2];
@@ -243,10 +237,42 @@ __global__ void __launch_bounds__(32 * kWarps, 5) k_knn(KnnArgs A) {
   Q.r2 = __fmul_rn(r_max, r_max);
   Q.hs = (float)kBins / (Q.r2 * sqrtf(Q.r2));
   const int R = A.res;
-  int xlo, xhi;
-  axis_range(Q.x, r_max, R, &xlo, &xhi);
   axis_range(Q.y, r_max, R, &Q.ylo, &Q.yhi);
   axis_range(Q.z, r_max, R, &Q.zlo, &Q.zhi);
+  return Q;
+}
+
+// Mean sigma_t of the query's cache cell.
+__device__ __forceinline__ float query_sigma(const KnnArgs& A, const Query& Q) {
+  const int R = A.res;
+  return A.cell_sigma[min(max((int)floorf(Q.x * (float)R), 0), R - 1) +
+                      (int64_t)R * (min(max((int)floorf(Q.y * (float)R), 0), R - 1) +
+                                    (int64_t)R * min(max((int)floorf(Q.z * (float)R), 0), R - 1))];
+}
+
+// L_s (and L') of query b from its sums, records used and radius.
+__device__ __forceinline__ void write_query(const KnnArgs& A, int64_t b, float sig, float r, float a0, float a1,
+                                            float a2, uint32_t kc) {
+  const float vol = 4.18879032f * r * r * r;
+  const float norm = (sig > 0.f && vol > 0.f) ? 1.0f / (vol * sig) : 0.f;
+  const float L[3] = {a0 * norm, a1 * norm, a2 * norm};
+  const float thr = exp10f(-A.psi);
+  for (int c = 0; c < 3; ++c) {
+    if (A.ls) A.ls[3 * b + c] = L[c];
+    if (A.lp) A.lp[3 * b + c] = L[c] > thr ? -log10f(L[c]) / A.psi : 1.0f;
+  }
+  if (A.k_out) A.k_out[b] = (int32_t)kc;
+  if (A.r_out) A.r_out[b] = r;
+}
+
+// One query on one warp (the histogram / selection passes of the file's
+// header).
+__device__ __forceinline__ void knn_warp(const KnnArgs& A, int64_t b, int lane, uint32_t* hist,
+                                         unsigned long long* lkey, uint32_t* lidx, uint32_t* cnt_slot) {
+  __syncwarp();                            // the previous query's shared-memory reads are done
+  const Query Q = make_query(A, b);
+  const float r_max = A.r_max;
+  const int R = A.res;
 
   float a0 = 0.f, a1 = 0.f, a2 = 0.f;
   uint32_t kc = 0;
@@ -260,9 +286,8 @@ __global__ void __launch_bounds__(32 * kWarps, 5) k_knn(KnnArgs A) {
   };
   float r = r_max;
   const uint32_t K = (uint32_t)A.K;
-  const float sig = A.cell_sigma[min(max((int)floorf(Q.x * (float)R), 0), R - 1) +
-                                 (int64_t)R * (min(max((int)floorf(Q.y * (float)R), 0), R - 1) +
-                                               (int64_t)R * min(max((int)floorf(Q.z * (float)R), 0), R - 1))];
+  const float sig = query_sigma(A, Q);
+  (void)R;
   // a cover of at most 32 rows is one chunk: its ranges stay in registers,
   // and if it holds at most K records they are all used at once
   const int ny = Q.yhi - Q.ylo + 1, nz = Q.zhi - Q.zlo + 1;
@@ -325,7 +350,7 @@ __global__ void __launch_bounds__(32 * kWarps, 5) k_knn(KnnArgs A) {
       shift = sh;
       __syncwarp();
     }
-    if (lane == 0) s_cnt[warp] = 0;
+    if (lane == 0) *cnt_slot = 0;
     __syncwarp();
     for_candidates(A, Q, lane, [&](uint64_t n, float d2, uint32_t id) {
       const int bn = bin_of(Q, d2);
@@ -335,11 +360,11 @@ __global__ void __launch_bounds__(32 * kWarps, 5) k_knn(KnnArgs A) {
       const uint64_t kp = shift < 64 ? (key >> shift) : 0;
       if (kp < prefix) { add(n); return; }
       if (kp > prefix) return;
-      const uint32_t slot = atomicAdd(&s_cnt[warp], 1u);
+      const uint32_t slot = atomicAdd(cnt_slot, 1u);
       if (slot < (uint32_t)kList) { lkey[slot] = key; lidx[slot] = (uint32_t)n; }
     });
     __syncwarp();
-    const uint32_t cnt = min(s_cnt[warp], (uint32_t)kList);
+    const uint32_t cnt = min(*cnt_slot, (uint32_t)kList);
     int P2 = 32;
     while (P2 < (int)cnt) P2 <<= 1;
     for (int i = (int)cnt + lane; i < P2; i += 32) { lkey[i] = ~0ull; lidx[i] = 0; }
@@ -373,18 +398,76 @@ __global__ void __launch_bounds__(32 * kWarps, 5) k_knn(KnnArgs A) {
     dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
   }
   if (all && kc >= K) r = __fsqrt_rn(dmax);
-  if (lane == 0) {
-    const float vol = 4.18879032f * r * r * r;
-    const float norm = (sig > 0.f && vol > 0.f) ? 1.0f / (vol * sig) : 0.f;
-    const float L[3] = {a0 * norm, a1 * norm, a2 * norm};
-    const float thr = exp10f(-A.psi);
-    for (int c = 0; c < 3; ++c) {
-      if (A.ls) A.ls[3 * b + c] = L[c];
-      if (A.lp) A.lp[3 * b + c] = L[c] > thr ? -log10f(L[c]) / A.psi : 1.0f;
-    }
-    if (A.k_out) A.k_out[b] = (int32_t)kc;
-    if (A.r_out) A.r_out[b] = r;
+  if (lane == 0) write_query(A, b, sig, r, a0, a1, a2, kc);
+}
+
+// One warp per query.
+__global__ void __launch_bounds__(32 * kWarps, 5) k_knn(KnnArgs A) {
+  __shared__ uint32_t s_hist[kWarps][kBins];
+  __shared__ unsigned long long s_key[kWarps][kList];
+  __shared__ uint32_t s_idx[kWarps][kList];
+  __shared__ uint32_t s_cnt[kWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t b = (int64_t)blockIdx.x * kWarps + warp;
+  if (b < A.B) knn_warp(A, b, lane, s_hist[warp], s_key[warp], s_idx[warp], &s_cnt[warp]);
+}
+
+// Persistent warps over the listed queries (those k_knn_thread passed on).
+__global__ void __launch_bounds__(32 * kWarps, 5) k_knn_list(KnnArgs A) {
+  __shared__ uint32_t s_hist[kWarps][kBins];
+  __shared__ unsigned long long s_key[kWarps][kList];
+  __shared__ uint32_t s_idx[kWarps][kList];
+  __shared__ uint32_t s_cnt[kWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t n = *A.list_count;
+  for (uint32_t i = blockIdx.x * kWarps + warp; i < n; i += gridDim.x * kWarps)
+    knn_warp(A, (int64_t)A.list[i], lane, s_hist[warp], s_key[warp], s_idx[warp], &s_cnt[warp]);
+}
+
+// One thread per query: a query whose cover rows hold at most K records
+// (offsets alone) uses every record within r_max, summed in row and record
+// order; the others are listed for the warp kernel.  Most queries of the
+// staggered schedule's small radii take this path.
+__global__ void __launch_bounds__(128) k_knn_thread(KnnArgs A, uint32_t* __restrict__ list,
+                                                   uint32_t* __restrict__ list_count) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= A.B) return;
+  const Query Q = make_query(A, b);
+  const int ny = Q.yhi - Q.ylo + 1, nz = Q.zhi - Q.zlo + 1;
+  const int n_rows = (ny > 0 && nz > 0) ? A.n_lights * ny * nz : 0;
+  uint64_t T = 0;
+  for (int ri = 0; ri < n_rows; ++ri) {
+    uint64_t s0;
+    uint32_t len;
+    row_range(A, Q, ri, ny, nz, &s0, &len);
+    T += len;
   }
+  if (T > (uint64_t)A.K) {
+    list[atomicAdd(list_count, 1u)] = (uint32_t)b;
+    return;
+  }
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, dmax = 0.f;
+  uint32_t kc = 0;
+  for (int ri = 0; ri < n_rows; ++ri) {
+    uint64_t s0;
+    uint32_t len;
+    row_range(A, Q, ri, ny, nz, &s0, &len);
+    for (uint64_t n = s0; n < s0 + len; ++n) {
+      const float4 p = __ldg(&A.pos[n]);
+      const float dx = __fsub_rn(p.x, Q.x), dy = __fsub_rn(p.y, Q.y), dz = __fsub_rn(p.z, Q.z);
+      const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+      if (!(d2 <= Q.r2)) continue;
+      const float4 r0 = __ldg(&A.recs[2 * n]), r1 = __ldg(&A.recs[2 * n + 1]);
+      const float mu = r0.z * Q.wx + r0.w * Q.wy + r1.x * Q.wz;
+      const float den = Q.c1 - Q.c2 * mu;
+      const float ph = Q.c0 / (den * sqrtf(den));
+      a0 = fmaf(ph, r1.y, a0); a1 = fmaf(ph, r1.z, a1); a2 = fmaf(ph, r1.w, a2);
+      dmax = fmaxf(dmax, d2);
+      ++kc;
+    }
+  }
+  const float r = kc >= (uint32_t)A.K ? __fsqrt_rn(dmax) : A.r_max;
+  write_query(A, b, query_sigma(A, Q), r, a0, a1, a2, kc);
 }
 
 }  // namespace
@@ -398,7 +481,24 @@ pf_status pf_knn_targets_impl(pf_ctx* ctx, const pf_cache* c, const float* q, in
   A.r_max = r_max; A.psi = psi;
   for (int i = 0; i < 16; ++i) A.g_set[i] = c->g_set[i];
   A.ls = ls; A.lp = lp; A.k_out = k_out; A.r_out = r_out;
-  k_knn<<<(unsigned)((B + kWarps - 1) / kWarps), 32 * kWarps, 0, stream>>>(A);
+  A.list = nullptr; A.list_count = nullptr;
+  if (r_max * (float)c->res > 1.0f) {
+    // covers wider than a cell in every direction: one warp per query
+    k_knn<<<(unsigned)((B + kWarps - 1) / kWarps), 32 * kWarps, 0, stream>>>(A);
+    PF_CUDA(ctx, cudaGetLastError());
+    return PF_OK;
+  }
+  // small covers: one thread per query first; the queries with more than K
+  // records in their cover go to the warp kernel through a list
+  uint32_t* list;
+  PF_TRY(pf_scratch(ctx, WS_KNN_LIST, ((size_t)B + 64) * sizeof(uint32_t), (void**)&list));
+  uint32_t* count = list + B + 32;
+  PF_CUDA(ctx, cudaMemsetAsync(count, 0, sizeof(uint32_t), stream));
+  k_knn_thread<<<(unsigned)((B + 127) / 128), 128, 0, stream>>>(A, list, count);
+  PF_CUDA(ctx, cudaGetLastError());
+  A.list = list; A.list_count = count;
+  const int64_t blocks = std::min<int64_t>((B + kWarps - 1) / kWarps, (int64_t)ctx->num_sms * 5);
+  k_knn_list<<<(unsigned)blocks, 32 * kWarps, 0, stream>>>(A);
   PF_CUDA(ctx, cudaGetLastError());
   return PF_OK;
 }

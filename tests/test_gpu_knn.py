@@ -7,7 +7,9 @@ distances with the record id breaking ties, so the records used and the
 radius agree bit for bit; the radiance sums agree to float32 rounding.
 Cases cover the radius-limited estimate (r = r_max), the saturated one
 (r = K-th distance), the histogram bin holding the K-th neighbour overflowing
-the selection list (radix refinement), and the degenerate K = 1.
+the selection list (radix refinement), the degenerate K = 1, and a radius
+cap within one cache cell (the thread-per-query route with its hand-over of
+crowded queries to the warp kernel).
 """
 import numpy as np
 import pytest
@@ -46,6 +48,8 @@ def test_positions_bit_exact(knn_cache):
     (16, 0.15),       # saturated: the K-th distance
     (64, 0.3),
     (1, 0.2),         # nearest record only
+    (4, 0.0625),      # cover within one cell: thread per query, the queries with more than K
+                      # records in their cover passed to the warp kernel
     (300, 2.0),       # the first histogram bin spans d < 0.31: it overflows the list, radix refinement
 ])
 def test_knn_targets_match_oracle(pf_ctx, orc, knn_cache, K, r_max):
