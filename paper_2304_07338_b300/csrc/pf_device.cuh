@@ -145,6 +145,7 @@ struct Vol {
   float wx, wy, wz;   // brick edge in world units, B / n (IEEE division)
   const void* tiled;  // voxels in 4x4x4 tiles (same values), or null
   int tnx, tny;       // tiles along x and y
+  int off32;          // element offsets of the layout in use fit 32 bits
 };
 
 // Element offset of voxel (i, j, k) = X(i) + Y(j) + Z(k) in either layout:
@@ -160,6 +161,16 @@ __device__ __forceinline__ size_t offy(const Vol& V, int j) {
 __device__ __forceinline__ size_t offz(const Vol& V, int k) {
   return V.tiled ? (size_t)(k >> 2) * (size_t)V.tnx * (size_t)V.tny * 64 + (size_t)((k & 3) * 16)
                  : (size_t)k * (size_t)V.nx * (size_t)V.ny;
+}
+__device__ __forceinline__ uint32_t offx32(const Vol& V, int i) {
+  return V.tiled ? ((uint32_t)(i >> 2) << 6) + (uint32_t)(i & 3) : (uint32_t)i;
+}
+__device__ __forceinline__ uint32_t offy32(const Vol& V, int j) {
+  return V.tiled ? (uint32_t)(j >> 2) * ((uint32_t)V.tnx << 6) + (uint32_t)((j & 3) * 4) : (uint32_t)j * (uint32_t)V.nx;
+}
+__device__ __forceinline__ uint32_t offz32(const Vol& V, int k) {
+  return V.tiled ? (uint32_t)(k >> 2) * ((uint32_t)V.tnx * (uint32_t)V.tny << 6) + (uint32_t)((k & 3) * 16)
+                 : (uint32_t)k * ((uint32_t)V.nx * (uint32_t)V.ny);
 }
 template <int DT> __device__ __forceinline__ float voxel_at(const void* base, size_t idx) {
   if (DT == 0) return __ldg((const float*)base + idx);
@@ -181,12 +192,22 @@ template <int DT> __device__ __forceinline__ float density(const Vol& V, V3 p) {
   x0 = max(x0, 0); y0 = max(y0, 0); z0 = max(z0, 0);
   // the layout decided once per lookup; the eight loads then issue together
   const void* base = V.tiled ? V.tiled : V.data;
-  const size_t ax0 = offx(V, x0), ax1 = offx(V, x1), ay0 = offy(V, y0), ay1 = offy(V, y1);
-  const size_t az0 = offz(V, z0), az1 = offz(V, z1);
-  float v000 = voxel_at<DT>(base, ax0 + ay0 + az0), v100 = voxel_at<DT>(base, ax1 + ay0 + az0);
-  float v010 = voxel_at<DT>(base, ax0 + ay1 + az0), v110 = voxel_at<DT>(base, ax1 + ay1 + az0);
-  float v001 = voxel_at<DT>(base, ax0 + ay0 + az1), v101 = voxel_at<DT>(base, ax1 + ay0 + az1);
-  float v011 = voxel_at<DT>(base, ax0 + ay1 + az1), v111 = voxel_at<DT>(base, ax1 + ay1 + az1);
+  float v000, v100, v010, v110, v001, v101, v011, v111;
+  if (V.off32) {  // 32-bit offset arithmetic (volumes below 2^32 elements)
+    const uint32_t ax0 = offx32(V, x0), ax1 = offx32(V, x1), ay0 = offy32(V, y0), ay1 = offy32(V, y1);
+    const uint32_t az0 = offz32(V, z0), az1 = offz32(V, z1);
+    v000 = voxel_at<DT>(base, ax0 + ay0 + az0); v100 = voxel_at<DT>(base, ax1 + ay0 + az0);
+    v010 = voxel_at<DT>(base, ax0 + ay1 + az0); v110 = voxel_at<DT>(base, ax1 + ay1 + az0);
+    v001 = voxel_at<DT>(base, ax0 + ay0 + az1); v101 = voxel_at<DT>(base, ax1 + ay0 + az1);
+    v011 = voxel_at<DT>(base, ax0 + ay1 + az1); v111 = voxel_at<DT>(base, ax1 + ay1 + az1);
+  } else {
+    const size_t ax0 = offx(V, x0), ax1 = offx(V, x1), ay0 = offy(V, y0), ay1 = offy(V, y1);
+    const size_t az0 = offz(V, z0), az1 = offz(V, z1);
+    v000 = voxel_at<DT>(base, ax0 + ay0 + az0); v100 = voxel_at<DT>(base, ax1 + ay0 + az0);
+    v010 = voxel_at<DT>(base, ax0 + ay1 + az0); v110 = voxel_at<DT>(base, ax1 + ay1 + az0);
+    v001 = voxel_at<DT>(base, ax0 + ay0 + az1); v101 = voxel_at<DT>(base, ax1 + ay0 + az1);
+    v011 = voxel_at<DT>(base, ax0 + ay1 + az1); v111 = voxel_at<DT>(base, ax1 + ay1 + az1);
+  }
   float c00 = v000 + tx * (v100 - v000);
   float c10 = v010 + tx * (v110 - v010);
   float c01 = v001 + tx * (v101 - v001);
@@ -506,6 +527,9 @@ inline pfd::Vol pf_make_vol(const pf_volume* v, float majorant, const float* gri
   V.tiled = v->tiled_dev;
   V.tnx = (v->nx + 3) / 4;
   V.tny = (v->ny + 3) / 4;
+  const uint64_t elems = v->tiled_dev ? (uint64_t)V.tnx * (uint64_t)V.tny * (uint64_t)((v->nz + 3) / 4) * 64u
+                                      : (uint64_t)v->nx * (uint64_t)v->ny * (uint64_t)v->nz;
+  V.off32 = elems <= 0xffffffffull ? 1 : 0;
   return V;
 }
 inline pfd::DevLights pf_make_lights(const pf_light* lights, int n) {

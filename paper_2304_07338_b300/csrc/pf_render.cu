@@ -336,7 +336,19 @@ __global__ void __launch_bounds__(128, 6) k_nee(Vol V, Vol Vw, DevLights L, floa
           const uint64_t full = n / kNeeWindow;
           uint64_t j;
           int l;
-          if (q < full * per_w) {
+          if (n_items <= 0xffffffffull) {  // the same split in 32-bit arithmetic
+            const uint32_t q32 = (uint32_t)q, pw = (uint32_t)per_w, f32 = (uint32_t)full;
+            if (q32 < f32 * pw) {
+              const uint32_t w = q32 / pw, r = q32 - w * pw;
+              l = (int)(r / (uint32_t)kNeeWindow);
+              j = (uint64_t)w * kNeeWindow + r % (uint32_t)kNeeWindow;
+            } else {
+              const uint32_t r = q32 - f32 * pw, rem = (uint32_t)(n - full * kNeeWindow);
+              const uint32_t lq = r / rem;
+              l = (int)lq;
+              j = full * kNeeWindow + (r - lq * rem);
+            }
+          } else if (q < full * per_w) {
             const uint64_t r = q % per_w;
             l = (int)(r / kNeeWindow);
             j = (q / per_w) * kNeeWindow + r % kNeeWindow;
