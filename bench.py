@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 METRIC = "1080p frames/sec and field queries/sec vs plain GPU path tracer at equal RMSE"
 W_, H_, SPP, N_VOX, N_LIGHTS = 1920, 1080, 16, 1024, 8
 BRICK = 32                      # majorant brick edge (voxels) for the 1024^3 volume
-BRICK_PRIMARY = 64              # brick edge of the camera rays' (pooled) majorant grid
+BRICK_PRIMARY = 128             # brick edge of the camera rays' (pooled) majorant grid
 BRICK_SHADOW = 0                # brick edge walked by shadow rays, thinned to BRICK (0: BRICK)
 HIDDEN, N_HIDDEN, FREQS = 128, 4, 12
 VOXEL_BYTES = 2                 # float16
