@@ -350,8 +350,8 @@ def main():
                 "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
                 "traffic_note": "DRAM bytes per launch, scaled from the small-case ncu capture by lookups"
                 if traffic else None,
-                "limiter": "issue-bound divergent control flow, not bandwidth (ncu, small case: issue active 74 %, "
-                           "17.5 of 32 lanes per instruction, DRAM 5.5 % of peak)" if dominant == "nee" else None,
+                "limiter": "issue-bound divergent control flow, not bandwidth (ncu, small case: issue active 73.5 %, "
+                           "17.4 of 32 lanes per instruction, DRAM 5.5 % of peak)" if dominant == "nee" else None,
                 "algorithmic": "%d density lookups/frame x %d B" % (lookups, FETCH_BYTES),
                 "peak_source": src}
     else:
