@@ -36,6 +36,7 @@ W_, H_, SPP, N_VOX, N_LIGHTS = 1920, 1080, 16, 1024, 8
 BRICK = 32                      # majorant brick edge (voxels) for the 1024^3 volume
 BRICK_PRIMARY = 128             # brick edge of the camera rays' (pooled) majorant grid
 BRICK_SHADOW = 0                # brick edge walked by shadow rays, thinned to BRICK (0: BRICK)
+BRICK_PT = 64                   # majorant brick edge of the path-tracer baseline (its own best, tuned apart)
 HIDDEN, N_HIDDEN, FREQS = 128, 4, 12
 VOXEL_BYTES = 2                 # float16
 # DRAM bytes (read + write) per density lookup of k_nee, from one ncu capture
@@ -189,6 +190,8 @@ def main():
     ap.add_argument("--training-only", action="store_true",
                     help="run only the field-training workload and print its JSON (profiling)")
     ap.add_argument("--training-steps", type=int, default=2000)
+    ap.add_argument("--brick-pt", type=int, default=BRICK_PT,
+                    help="majorant brick edge of the path-tracer baseline (power of two)")
     ap.add_argument("--brick-shadow", type=int, default=BRICK_SHADOW,
                     help="brick edge walked by shadow rays, thinned to --brick (0: --brick)")
     ap.add_argument("--brick-primary", type=int, default=BRICK_PRIMARY,
@@ -232,6 +235,15 @@ def main():
     vol.attach_brick_majorants(ctx)
     if not args.linear_voxels:
         vol.attach_tiled(ctx)
+    # the path-tracer baseline walks its own majorant grid (same voxels)
+    vol_pt = vol
+    if args.brick_pt != args.brick:
+        vol_pt = api.Volume(vol_t, 20.0, 0.9, tf_t, brick=args.brick_pt)
+        vol_pt.s.majorant = vol.s.majorant
+        vol_pt.attach_brick_majorants(ctx)
+        if not args.linear_voxels:
+            vol_pt.tiled = vol.tiled
+            vol_pt.s.tiled_dev = vol.s.tiled_dev
     setup = {}
     t0 = time.perf_counter()
     cache = api.build_photon_cache(ctx, vol, lights, I.G_PAPER, args.photons, 16, 64, seed=seed + 1)
@@ -371,6 +383,7 @@ def main():
                    "frames": "60-frame orbit", "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (2 GiB volume)", "majorant_brick": args.brick,
                    "majorant_brick_primary": args.brick_primary, "majorant_brick_shadow": args.brick_shadow,
+                   "majorant_brick_path_tracer": args.brick_pt,
                    "voxel_layout": "linear" if args.linear_voxels else "4x4x4 tiles"},
         "queries_per_s": qpf * fps,
         "queries_per_frame": qpf,
@@ -384,7 +397,7 @@ def main():
     }
     line["setup"] = setup
     if not args.no_equal_rmse:
-        line["equal_rmse"] = equal_rmse(ctx, vol, lights, frame, field, seed, args, fps)
+        line["equal_rmse"] = equal_rmse(ctx, vol, vol_pt, lights, frame, field, seed, args, fps)
         line["vs_path_tracer_equal_rmse"] = line["equal_rmse"].get("speedup")
         line["phase_sweep"] = phase_sweep(ctx, vol, lights, frame, field, seed, args)
     if not args.no_march:
@@ -483,8 +496,9 @@ def phase_sweep(ctx, vol, lights, frame, field, seed, args, ref_spp=1024):
             "spp": SPP, "by_g": rows}
 
 
-def equal_rmse(ctx, vol, lights, frame, field, seed, args, fps_neural):
-    """Equal-RMSE comparison with the plain path tracer (frame 0): the image
+def equal_rmse(ctx, vol, vol_pt, lights, frame, field, seed, args, fps_neural):
+    """Equal-RMSE comparison with the plain path tracer (frame 0; the path
+    tracer on vol_pt, the same voxels over its own majorant bricks): the image
     error of both renderers against a path-traced reference of ref_spp
     samples per pixel, measured at a reduced resolution (same camera and
     scene; each renderer's per-pixel error does not depend on the image
@@ -496,7 +510,7 @@ def equal_rmse(ctx, vol, lights, frame, field, seed, args, fps_neural):
     cam, g = frame(0)
     small = I.Camera(cam.eye, cam.at, cam.up, cam.fovy_deg, args.rmse_width, args.rmse_height)
     t0 = time.perf_counter()
-    ref = api.render_pathtraced(ctx, vol, lights, g, small, args.ref_spp, 16, seed=seed + 7)
+    ref = api.render_pathtraced(ctx, vol_pt, lights, g, small, args.ref_spp, 16, seed=seed + 7)
     ctx.sync()
     t_ref = time.perf_counter() - t0
     neural = api.render_neural(ctx, vol, lights, g, small, SPP, 0.0, seed + 8, field)
@@ -507,7 +521,7 @@ def equal_rmse(ctx, vol, lights, frame, field, seed, args, fps_neural):
     spps, rms = [], []
     spp = 1
     while spp <= min(1024, args.ref_spp // 4):
-        img = api.render_pathtraced(ctx, vol, lights, g, small, spp, 16, seed=seed + 9)
+        img = api.render_pathtraced(ctx, vol_pt, lights, g, small, spp, 16, seed=seed + 9)
         ctx.sync()
         spps.append(spp)
         rms.append(api.image_rmse(ctx, img, ref))
@@ -531,13 +545,13 @@ def equal_rmse(ctx, vol, lights, frame, field, seed, args, fps_neural):
         return out
     # path-tracer frames/s at that spp, full resolution
     img = torch.empty(H_, W_, 3, device=torch.device("cuda", ctx.device))
-    api.render_pathtraced(ctx, vol, lights, g, cam, need, 16, seed=seed + 10, out=img)
+    api.render_pathtraced(ctx, vol_pt, lights, g, cam, need, 16, seed=seed + 10, out=img)
     ctx.sync()
     n = 3
     s_ev, e_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     s_ev.record(ctx.stream)
     for i in range(n):
-        api.render_pathtraced(ctx, vol, lights, g, cam, need, 16, seed=seed + 11 + i, out=img)
+        api.render_pathtraced(ctx, vol_pt, lights, g, cam, need, 16, seed=seed + 11 + i, out=img)
     e_ev.record(ctx.stream)
     torch.cuda.synchronize()
     pt_fps = n / (s_ev.elapsed_time(e_ev) / 1e3)
