@@ -281,7 +281,9 @@ __device__ __forceinline__ float thin_majorant(const Vol& V, const Vol& Vw, int 
 // the SM carves out of the same storage as the L1 cache that serves the
 // density gathers; it is kept small.
 constexpr int kNeePool = 16;                                               // collisions per lane per pass
-constexpr int kNeeWarpFloats = 32 * kNeePool * 2 + 32 * kNeePool / 2 + 32 * 6;  // t/factor, majorant, u16 map; x, w_l
+constexpr int kNeeTau = 8;                                                 // buffered budgets per lane (ring)
+constexpr int kNeeWarpFloats =
+    32 * kNeePool * 2 + 32 * kNeePool / 2 + 32 * 6 + 32 * kNeeTau;  // t/factor, majorant, u16 map; x, w_l; budgets
 constexpr int kNeeWarps = 4;
 constexpr uint64_t kNeeWindow = 4096;   // sorted samples whose shadow rays (all lights) run together
 
@@ -304,6 +306,7 @@ __global__ void __launch_bounds__(128, 6) k_nee(Vol V, Vol Vw, DevLights L, floa
   float* pm = pool + 32 * kNeePool;                        // majorant at the collision
   uint16_t* pmap = (uint16_t*)(pool + 64 * kNeePool);      // pooled entry -> lane * kNeePool + index
   float* pxw = pool + 64 * kNeePool + 16 * kNeePool;       // per lane: origin x (3), direction w_l (3)
+  float* ptau = pxw + 32 * 6 + lane * kNeeTau;             // this lane's ring of budgets -ln(1 - u)
   const uint64_t n = *ccount;
   const uint64_t n_items = n * (uint64_t)L.n;
   uint32_t nfetch = 0;
@@ -314,7 +317,9 @@ __global__ void __launch_bounds__(128, 6) k_nee(Vol V, Vol Vw, DevLights L, floa
   float ph = 0.f, T = 1.0f, t = 0.0f, tau = 0.0f, tc = 0.0f, tend = 0.0f;
   int it = 0;
   Walk<false> W;
-  Uniforms U;
+  Uniforms U;                   // THIN: uniforms drawn in the walk
+  int un = 0, ur = 0;           // !THIN: budgets buffered in ptau, read position
+  bool need_tau = false;        // !THIN: the next budget is still to be taken
   Rng rs(0, 0, 0, 0);
   for (;;) {
     // refill: lanes whose ray is done take the next items
@@ -375,7 +380,8 @@ __global__ void __launch_bounds__(128, 6) k_nee(Vol V, Vol Vw, DevLights L, floa
           U = Uniforms();
           T = 1.0f;
           t = 0.0f;
-          tau = -own_lnf(1.0f - U.next(rs));
+          if (THIN) tau = -own_lnf(1.0f - U.next(rs));
+          else { un = 0; ur = 0; need_tau = true; }   // the first budget comes with the pass's draws
           tc = mn(W.exit_t(), tend);
           done = false;
           it = 0;
@@ -388,9 +394,31 @@ __global__ void __launch_bounds__(128, 6) k_nee(Vol V, Vol Vw, DevLights L, floa
       if (exhausted) break;
       continue;
     }
+    // !THIN: every uniform of a shadow ray is a budget.  The lanes draw the
+    // Philox blocks of the budgets this pass may need here, together (two
+    // blocks at most, keeping at least five budgets in the ring), instead of
+    // one lane at a time inside the divergent walk; the budgets and their
+    // order are those of drawing them one by one.  A lane whose ring runs dry
+    // within a pass waits for the next one.
+    if (!THIN && has && !done) {
+#pragma unroll 1
+      for (int b = 0; b < 2 && un <= 4; ++b) {
+        float u[4];
+        rs.uni4(u);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) ptau[(ur + un + i) & (kNeeTau - 1)] = -own_lnf(1.0f - u[i]);
+        un += 4;
+      }
+      if (need_tau) {
+        tau = ptau[ur];
+        ur = (ur + 1) & (kNeeTau - 1);
+        --un;
+        need_tau = false;
+      }
+    }
     // walk: record up to kNeePool tentative collisions of this lane's ray
     int cnt = 0;
-    while (has && !done && cnt < kNeePool) {
+    while (has && !done && !need_tau && cnt < kNeePool) {
       float seg = tc - t;
       if (seg < 0.0f) seg = 0.0f;
       if (W.m > 0.0f && tau < W.m * seg) {
@@ -409,7 +437,15 @@ __global__ void __launch_bounds__(128, 6) k_nee(Vol V, Vol Vw, DevLights L, floa
           pm[lane * kNeePool + cnt] = m;
           ++cnt;
         }
-        tau = -own_lnf(1.0f - U.next(rs));
+        if (THIN) {
+          tau = -own_lnf(1.0f - U.next(rs));
+        } else if (un > 0) {
+          tau = ptau[ur];
+          ur = (ur + 1) & (kNeeTau - 1);
+          --un;
+        } else {
+          need_tau = true;
+        }
       } else {
         tau = tau - W.m * seg;
         t = tc;
