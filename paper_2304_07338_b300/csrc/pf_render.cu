@@ -280,7 +280,7 @@ __device__ __forceinline__ float thin_majorant(const Vol& V, const Vol& Vw, int 
 // the rays' collision counts differ.  The pool lives in shared memory, which
 // the SM carves out of the same storage as the L1 cache that serves the
 // density gathers; it is kept small.
-constexpr int kNeePool = 16;                                               // collisions per lane per pass
+constexpr int kNeePool = 8;                                                // collisions per lane per pass (the budget ring bounds them too)
 constexpr int kNeeTau = 8;                                                 // buffered budgets per lane (ring)
 constexpr int kNeeWarpFloats =
     32 * kNeePool * 2 + 32 * kNeePool / 2 + 32 * 6 + 32 * kNeeTau;  // t/factor, majorant, u16 map; x, w_l; budgets
