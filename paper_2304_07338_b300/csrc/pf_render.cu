@@ -294,7 +294,7 @@ constexpr uint64_t kNeeWindow = 4096;   // sorted samples whose shadow rays (all
 // collisions are those of ratio tracking over V's bricks.
 // contrib [n_lights][n][3]: p(d . w_l) T_l E_l of sorted sample j for light l.
 template <int DT, bool THIN>
-__global__ void __launch_bounds__(128, 6) k_nee(Vol V, Vol Vw, DevLights L, float g, int spp, uint64_t seed,
+__global__ void __launch_bounds__(128, 8) k_nee(Vol V, Vol Vw, DevLights L, float g, int spp, uint64_t seed,
                                              const float* __restrict__ cq, const float* __restrict__ cdir,
                                              const uint32_t* __restrict__ cidx, const uint32_t* __restrict__ ccount,
                                              const uint32_t* __restrict__ perm, unsigned long long* __restrict__ next,
