@@ -297,15 +297,63 @@ __global__ void k_brick_majorants(Vol V, float* __restrict__ out) {
   out[b] = V.sigma_scale * tf_alpha_max(V, dmin, dmax) * 1.0009765625f;
 }
 
+// The same majorant with one block per brick (large bricks): warps take the
+// (y, z) rows of the brick plus apron, lanes the voxels along x; min and max
+// are combined by comparisons, so the order does not change the result.
+template <int DT>
+__global__ void __launch_bounds__(256) k_brick_majorants_block(Vol V, float* __restrict__ out) {
+  __shared__ float s_min[8], s_max[8];
+  const int64_t b = blockIdx.x;
+  const int bx = (int)(b % V.gx), by = (int)((b / V.gx) % V.gy), bz = (int)(b / ((int64_t)V.gx * V.gy));
+  const int B = V.B;
+  const int i0 = max(B * bx - 1, 0), i1 = min(B * bx + B, V.nx - 1);
+  const int j0 = max(B * by - 1, 0), j1 = min(B * by + B, V.ny - 1);
+  const int k0 = max(B * bz - 1, 0), k1 = min(B * bz + B, V.nz - 1);
+  const int nj = j1 - j0 + 1, rows = nj * (k1 - k0 + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  float dmin = __int_as_float(0x7f800000), dmax = -dmin;
+  for (int r = warp; r < rows; r += nw) {
+    const int j = j0 + r % nj, k = k0 + r / nj;
+    for (int i = i0 + lane; i <= i1; i += 32) {
+      const float d = voxel<DT>(V, i, j, k);
+      if (d < dmin) dmin = d;
+      if (d > dmax) dmax = d;
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const float a = __shfl_xor_sync(0xffffffffu, dmin, off), c = __shfl_xor_sync(0xffffffffu, dmax, off);
+    if (a < dmin) dmin = a;
+    if (c > dmax) dmax = c;
+  }
+  if (lane == 0) { s_min[warp] = dmin; s_max[warp] = dmax; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < nw; ++w) {
+      if (s_min[w] < dmin) dmin = s_min[w];
+      if (s_max[w] > dmax) dmax = s_max[w];
+    }
+    if (bx == 0 || by == 0 || bz == 0 || bx == V.gx - 1 || by == V.gy - 1 || bz == V.gz - 1)
+      if (0.0f < dmin) dmin = 0.0f;
+    out[b] = V.sigma_scale * tf_alpha_max(V, dmin, dmax) * 1.0009765625f;
+  }
+}
+
 }  // namespace
 
 pf_status pf_brick_majorants_impl(pf_ctx* ctx, const pf_volume* vol, float* out) {
   Vol V = pf_make_vol(vol, 0.f, nullptr);
   const int64_t nb = (int64_t)V.gx * V.gy * V.gz;
-  const unsigned grd = (unsigned)((nb + 127) / 128);
-  if (vol->dtype == PF_F32) k_brick_majorants<0><<<grd, 128, 0, ctx->stream>>>(V, out);
-  else if (vol->dtype == PF_F16) k_brick_majorants<1><<<grd, 128, 0, ctx->stream>>>(V, out);
-  else k_brick_majorants<2><<<grd, 128, 0, ctx->stream>>>(V, out);
+  if (V.B >= 64) {   // (B + 2)^3 voxels per brick: a block each (measured faster from B = 64)
+    const unsigned grd = (unsigned)nb;
+    if (vol->dtype == PF_F32) k_brick_majorants_block<0><<<grd, 256, 0, ctx->stream>>>(V, out);
+    else if (vol->dtype == PF_F16) k_brick_majorants_block<1><<<grd, 256, 0, ctx->stream>>>(V, out);
+    else k_brick_majorants_block<2><<<grd, 256, 0, ctx->stream>>>(V, out);
+  } else {
+    const unsigned grd = (unsigned)((nb + 127) / 128);
+    if (vol->dtype == PF_F32) k_brick_majorants<0><<<grd, 128, 0, ctx->stream>>>(V, out);
+    else if (vol->dtype == PF_F16) k_brick_majorants<1><<<grd, 128, 0, ctx->stream>>>(V, out);
+    else k_brick_majorants<2><<<grd, 128, 0, ctx->stream>>>(V, out);
+  }
   PF_CUDA(ctx, cudaGetLastError());
   return PF_OK;
 }

@@ -98,7 +98,8 @@ def test_full_size_sampled_photons(pf_ctx, orc):
 def test_brick_majorants_match_oracle(pf_ctx, orc):
     for n, tf, dt, B in ((32, I.tf_white_alpha_ramp(), np.float32, 8), (40, I.tf_piecewise_rgba(64), np.float16, 8),
                          (27, I.tf_piecewise_rgba(256), np.uint8, 8), (40, I.tf_piecewise_rgba(64), np.float32, 16),
-                         (37, I.tf_white_alpha_ramp(), np.uint8, 4)):
+                         (37, I.tf_white_alpha_ramp(), np.uint8, 4), (70, I.tf_piecewise_rgba(64), np.float16, 32),
+                         (150, I.tf_white_alpha_ramp(), np.uint8, 64)):
         data = I.fbm_volume(n, seed=n)
         if dt == np.uint8:
             data = np.round(data * 255).astype(np.uint8)
