@@ -43,7 +43,7 @@ VOXEL_BYTES = 2                 # float16
 # of the small case (profiles/k_nee__large_render_512cube_960x540.md); a full
 # launch is scaled by its lookups.  None whenever k_nee changed since the
 # capture.
-NEE_DRAM_BYTES_PER_LOOKUP = (0.863514e9 + 0.104858e9) / 26852954
+NEE_DRAM_BYTES_PER_LOOKUP = None  # k_nee changed since the last capture
 FETCH_BYTES = 8 * VOXEL_BYTES   # one trilinear lookup reads 8 voxels
 
 

@@ -292,7 +292,8 @@ constexpr uint64_t kNeeWindow = 4096;   // sorted samples whose shadow rays (all
 // m_V(x) / m_Vw (one more uniform after its budget), m_V(x) the majorant of
 // the brick of V holding x, clamped into the current brick of Vw: the kept
 // collisions are those of ratio tracking over V's bricks.
-// contrib [n_lights][n][3]: p(d . w_l) T_l E_l of sorted sample j for light l.
+// contrib [n_lights][n][2]: (p(d . w_l) T_l, |p_l - x|^2) of sorted sample j for
+// light l; k_nee_sum forms E_l from the second (point lights) and multiplies.
 template <int DT, bool THIN>
 __global__ void __launch_bounds__(128, 8) k_nee(Vol V, Vol Vw, DevLights L, float g, int spp, uint64_t seed,
                                              const float* __restrict__ cq, const float* __restrict__ cdir,
@@ -314,7 +315,7 @@ __global__ void __launch_bounds__(128, 8) k_nee(Vol V, Vol Vw, DevLights L, floa
   bool has = false, done = true;
   uint64_t item = 0;
   V3 x = v3(0.5f, 0.5f, 0.5f), wl = v3(0.f, 0.f, 1.f), E = v3(0.f, 0.f, 0.f);
-  float ph = 0.f, T = 1.0f, t = 0.0f, tau = 0.0f, tc = 0.0f, tend = 0.0f;
+  float ph = 0.f, T = 1.0f, t = 0.0f, tau = 0.0f, tc = 0.0f, tend = 0.0f, d2l = 0.0f;
   int it = 0;
   Walk<false> W;
   Uniforms U;                   // THIN: uniforms drawn in the walk
@@ -371,6 +372,11 @@ __global__ void __launch_bounds__(128, 8) k_nee(Vol V, Vol Vw, DevLights L, floa
           const uint32_t k = slot % (uint32_t)spp;
           float dist;
           light_geom(L.l[l], x, &wl, &dist, &E);
+          if (L.l[l].kind == 0) d2l = 0.0f;
+          else {
+            const V3 dv = v3(L.l[l].v[0] - x.x, L.l[l].v[1] - x.y, L.l[l].v[2] - x.z);
+            d2l = dot(dv, dv);                             // as light_geom forms it
+          }
           float a0, a1;
           tend = 0.f;
           if (box_hit(x, wl, &a0, &a1)) tend = mn(a1, dist);
@@ -476,9 +482,7 @@ __global__ void __launch_bounds__(128, 8) k_nee(Vol V, Vol Vw, DevLights L, floa
     for (int c = 0; c < cnt; ++c) T = T * mx(0.0f, pt[lane * kNeePool + c]);
     __syncwarp();
     if (has && done) {
-      float* dst = contrib + 3 * (size_t)item;
-      const float w = ph * T;
-      dst[0] = w * E.x; dst[1] = w * E.y; dst[2] = w * E.z;
+      reinterpret_cast<float2*>(contrib)[item] = make_float2(ph * T, d2l);
       has = false;
     }
   }
@@ -494,15 +498,21 @@ __global__ void __launch_bounds__(128, 8) k_nee(Vol V, Vol Vw, DevLights L, floa
 
 // L_d of sorted sample j: the lights' contributions summed in light order;
 // slot_ld[slot] = albedo * L_d.
-__global__ void k_nee_sum(const float* __restrict__ contrib, int n_lights, const float* __restrict__ calb,
+// Per light, E_l = rgb (directional) or rgb / d^2 (point) as light_geom forms
+// it, and the term w E_l is rounded before it is added, as when k_nee wrote
+// the three products itself.
+__global__ void k_nee_sum(const float* __restrict__ contrib, DevLights L, const float* __restrict__ calb,
                           const uint32_t* __restrict__ cidx, const uint32_t* __restrict__ ccount,
                           const uint32_t* __restrict__ perm, float* __restrict__ slot_ld) {
   const uint64_t n = *ccount;
   for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (uint64_t)gridDim.x * blockDim.x) {
     float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-    for (int l = 0; l < n_lights; ++l) {
-      const float* c = contrib + 3 * ((size_t)l * n + j);
-      a0 = a0 + c[0]; a1 = a1 + c[1]; a2 = a2 + c[2];
+    for (int l = 0; l < L.n; ++l) {
+      const float2 c = reinterpret_cast<const float2*>(contrib)[(size_t)l * n + j];
+      const DevLight& ll = L.l[l];
+      float e0 = ll.rgb[0], e1 = ll.rgb[1], e2 = ll.rgb[2];
+      if (ll.kind != 0) { e0 = e0 / c.y; e1 = e1 / c.y; e2 = e2 / c.y; }
+      a0 = a0 + c.x * e0; a1 = a1 + c.x * e1; a2 = a2 + c.x * e2;
     }
     const uint32_t i = perm[j];
     const uint32_t slot = cidx[i];
@@ -885,7 +895,7 @@ pf_status launch_nee(pf_ctx* ctx, const Vol& V, const Vol& Vw, const DevLights& 
   // per-(light, sample) contributions, sized for the worst case (every slot
   // scatters), and the work counter (in the bytes after the sample count)
   float* contrib;
-  PF_TRY(pf_scratch(ctx, WS_NEE_CONTRIB, (size_t)L.n * (size_t)n_max * 3 * sizeof(float), (void**)&contrib));
+  PF_TRY(pf_scratch(ctx, WS_NEE_CONTRIB, (size_t)L.n * (size_t)n_max * 2 * sizeof(float), (void**)&contrib));
   unsigned long long* next = (unsigned long long*)((char*)ccount + 64);
   PF_CUDA(ctx, cudaMemsetAsync(next, 0, sizeof(unsigned long long), ctx->stream));
   int o = 0;  // resident blocks per SM
@@ -901,7 +911,7 @@ pf_status launch_nee(pf_ctx* ctx, const Vol& V, const Vol& Vw, const DevLights& 
                                                                  next, contrib, ctx->err_dev, ctx->counters);
   PF_CUDA(ctx, cudaGetLastError());
   k_nee_sum<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((n_max + 255) / 256, (int64_t)ctx->num_sms * 8)), 256, 0,
-              ctx->stream>>>(contrib, L.n, calb, cidx, ccount, perm, ld);
+              ctx->stream>>>(contrib, L, calb, cidx, ccount, perm, ld);
   PF_CUDA(ctx, cudaGetLastError());
   return PF_OK;
 }
