@@ -43,7 +43,7 @@ VOXEL_BYTES = 2                 # float16
 # of the small case (profiles/k_nee__large_render_512cube_960x540.md); a full
 # launch is scaled by its lookups.  None whenever k_nee changed since the
 # capture.
-NEE_DRAM_BYTES_PER_LOOKUP = None  # k_nee changed since the last capture
+NEE_DRAM_BYTES_PER_LOOKUP = (0.842871e9 + 0.069161e9) / 26852954
 FETCH_BYTES = 8 * VOXEL_BYTES   # one trilinear lookup reads 8 voxels
 
 
@@ -362,8 +362,8 @@ def main():
                 "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
                 "traffic_note": "DRAM bytes per launch, scaled from the small-case ncu capture by lookups"
                 if traffic else None,
-                "limiter": "issue-bound divergent control flow, not bandwidth (ncu, small case: issue active 81 %, "
-                           "20.6 of 32 lanes per instruction, DRAM 6.6 % of peak)" if dominant == "nee" else None,
+                "limiter": "issue-bound divergent control flow, not bandwidth (ncu, small case: issue active 81.5 %, "
+                           "20.5 of 32 lanes per instruction, DRAM 6.3 % of peak)" if dominant == "nee" else None,
                 "algorithmic": "%d density lookups/frame x %d B" % (lookups, FETCH_BYTES),
                 "peak_source": src}
     else:
