@@ -214,7 +214,7 @@ def encode(q: np.ndarray, n_freq: int) -> np.ndarray:
     k = 2.0 ** np.arange(n_freq)
     arg = math.pi * q[:, :, None] * k[None, None, :]
     f = np.stack([np.sin(arg), np.cos(arg)], axis=-1)
-    return f.reshape(q.shape[0], -1)
+    return f.reshape(q.shape[0], q.shape[1] * n_freq * 2)      # also for an empty batch
 
 
 def hash_corners(grid: HashGrid, l: int, x: np.ndarray):
