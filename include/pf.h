@@ -380,9 +380,13 @@ pf_status pf_render_pathtraced(pf_ctx* ctx, const pf_volume* vol, const pf_light
  * the image to about 2.09 million pixels (1920x1080 fits); larger images are
  * rejected with PF_ERR_INVALID_ARG.  The caller passes the inputs, a stream
  * of the current device and the output image; vol->brick_majorants_dev must
- * be set (an input, e.g. from pf_volume_brick_majorants).  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress) with that device
- * current, so make that first call before any stream capture.  All calls
+ * be set (an input, e.g. from pf_volume_brick_majorants).  It accepts exactly the
+ * volumes and lights pf_render_pathtraced accepts (the same checks).  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current and keeps it for the
+ * process, so make that first call before any stream capture, and do not
+ * call this entry point on a device after cudaDeviceReset there (the module
+ * may then be loaded at another address).  All calls
  * share the array and it keeps the last call's contents (each call resets
  * what it needs); calls that overlap on the GPU race.  Synchronises the
  * stream and reports an iteration-limit hit as PF_ERR_TIMEOUT; err_msg

@@ -41,6 +41,8 @@ def _declare(L):
     L.orc_philox_item.argtypes = [u64, u32, u32, u64, i64, P]
     L.orc_lnf.argtypes = [P, P, i64]
     L.orc_sincos2pif.argtypes = [P, P, P, i64]
+    L.orc_atan2f.argtypes = [P, P, P, i64]
+    L.orc_query_f32.argtypes = [P, P, C.c_float, i64, P]
     L.orc_hg_eval.argtypes = [f64, f64]
     L.orc_hg_eval.restype = f64
     L.orc_hg_sample.argtypes = [f64, P, P, i64, P, i32]
@@ -151,6 +153,27 @@ def sincos2pif(u: np.ndarray):
     s, c = np.zeros_like(u), np.zeros_like(u)
     lib().orc_sincos2pif(_p(u), _p(s), _p(c), u.size)
     return s, c
+
+
+def atan2f(y: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """The project's own float32 atan2 (half-angle step + Taylor series)."""
+    y = np.ascontiguousarray(y, np.float32)
+    x = np.ascontiguousarray(x, np.float32)
+    out = np.zeros_like(y)
+    lib().orc_atan2f(_p(y), _p(x), _p(out), y.size)
+    return out
+
+
+def query_f32(x: np.ndarray, wo: np.ndarray, g: float) -> np.ndarray:
+    """Field queries (x, theta', phi', g) formed in float32 from float32
+    interaction points and outgoing directions, as the renderer forms them
+    (Sec. 3.1's normalised spherical coordinates with the own atan2);
+    returned as float64 (exact)."""
+    x = np.ascontiguousarray(np.asarray(x).reshape(-1, 3), np.float32)
+    wo = np.ascontiguousarray(np.asarray(wo).reshape(-1, 3), np.float32)
+    q = np.zeros((x.shape[0], 6), np.float32)
+    lib().orc_query_f32(_p(x), _p(wo), float(np.float32(g)), x.shape[0], _p(q))
+    return q.astype(np.float64)
 
 
 # ------------------------------------------------------------------ phase function
@@ -389,7 +412,9 @@ def render_neural(vol, lights, g: float, cam, spp: int, step_vox: float, seed: i
     Li = np.zeros_like(cs["Ld"])
     if weights is not None:
         vm = cs["valid"]
-        qv = field.query_from_sample(cs["x"][vm], cs["wo"][vm], g)
+        # float32 instantiation: the queries as the renderer forms them in
+        # float32; FP64: the exact spherical coordinates
+        qv = query_f32(cs["x"][vm], cs["wo"][vm], g) if fp32 else field.query_from_sample(cs["x"][vm], cs["wo"][vm], g)
         y, _ = field.forward(weights, qv, desc, scales)
         Li[vm] = field.log_decode(y, desc.psi)
     img = (cs["albedo"] * (cs["Ld"] + Li)).sum(axis=2) / spp

@@ -35,6 +35,7 @@
 #include <cstdio>
 #include <vector>
 #include <algorithm>
+#include <type_traits>
 
 namespace {
 
@@ -133,6 +134,44 @@ void own_sincos2pif(float u, float* s_out, float* c_out) {
         default: s = -cphi; c = sphi; break;
     }
     *s_out = s; *c_out = c;
+}
+
+// atan2(y, x) in float32, from the textbook reductions: t = min/max of |x|,
+// |y| in [0, 1]; above tan(pi/8) use atan t = pi/4 + atan((t-1)/(t+1)); one
+// half-angle step atan t = 2 atan(t / (1 + sqrt(1 + t^2))); the odd Taylor
+// series of atan up to u^11; octant and quadrant fix-ups.  atan2(0, 0) = 0.
+float own_atan2f(float y, float x) {
+    const float ax = std::fabs(x), ay = std::fabs(y);
+    const float hi = (ax < ay) ? ay : ax;
+    const float lo = (ax < ay) ? ax : ay;
+    if (!(hi > 0.0f)) return 0.0f;
+    float t = lo / hi;
+    const bool big = t > 0.414213562f;
+    if (big) t = (t - 1.0f) / (t + 1.0f);
+    const float u = t / (1.0f + std::sqrt(1.0f + t * t));
+    const float u2 = u * u;
+    float p = -0.0909090909f;         // -1/11
+    p = p * u2 + 0.111111111f;        // 1/9
+    p = p * u2 + -0.142857143f;       // -1/7
+    p = p * u2 + 0.2f;                // 1/5
+    p = p * u2 + -0.333333333f;       // -1/3
+    float r = u + u * (u2 * p);
+    r = r + r;
+    if (big) r = r + 0.785398163f;
+    if (ax < ay) r = 1.57079633f - r;
+    if (x < 0.0f) r = 3.14159265f - r;
+    return (y < 0.0f) ? -r : r;
+}
+
+// The field's direction inputs in float32 (the renderer's precision):
+// theta' = acos(w_z)/pi with acos z = atan2(sqrt((1-z)(1+z)), z), and
+// phi' = atan2(w_y, w_x)/(2 pi), wrapped into [0, 1).
+void query_angles_f32(float wx, float wy, float wz, float* th, float* ph) {
+    const float z = (wz < -1.0f) ? -1.0f : ((wz > 1.0f) ? 1.0f : wz);
+    *th = own_atan2f(std::sqrt((1.0f - z) * (1.0f + z)), z) * 0.318309886f;
+    float p = own_atan2f(wy, wx) * 0.159154943f;
+    if (p < 0.0f) p = p + 1.0f;
+    *ph = p;
 }
 
 template <typename R> struct M;
@@ -710,6 +749,57 @@ R march_tau(const Volume& V, V3<R> o, V3<R> d, R t0, R t1, R h, R jit) {
     return tau;
 }
 
+// Marched free flight and shadow-ray optical depth in the kernel's float32
+// precision contract.  The segments, their sample points and sigma are the
+// float32 steps above; the running optical depth is a compensated (Kahan)
+// float32 sum; the target tau* = -ln(1 - u) and the remainder at the
+// interaction, (tau* - tau) / sigma, are evaluated in FP64 (where sigma is
+// small one float ulp of tau* or tau would move the interaction by ulp/sigma).
+// Real arithmetic gives the plain sums of march_tau and camera_sample.
+bool march_flight_f32(const Volume& V, V3<float> o, V3<float> d, float t0, float t1, float h, float u_seg, float u_tau,
+                      float* th) {
+    const double tau_star_d = -std::log1p(-(double)u_tau);
+    const float tau_star = (float)tau_star_d;
+    float tau = 0.0f, comp = 0.0f;
+    const int nseg = (int)std::ceil((t1 - t0) / h);
+    for (int s = 0; s < nseg; ++s) {
+        const float s0 = t0 + (float)s * h;
+        const float s1 = std::min(t0 + (float)(s + 1) * h, t1);
+        const float len = s1 - s0;
+        if (!(len > 0.0f)) continue;
+        const float sg = sigma_at<float>(V, along(o, d, s0 + u_seg * len));
+        const float dtau = sg * len;
+        if (sg > 0.0f && (tau - comp) + dtau >= tau_star) {
+            const double rem = tau_star_d - ((double)tau - (double)comp);
+            const float dl = (float)(rem / (double)sg);
+            *th = s0 + std::min(std::max(dl, 0.0f), len);
+            return true;
+        }
+        const float y = dtau - comp;
+        const float t = tau + y;
+        comp = (t - tau) - y;
+        tau = t;
+    }
+    return false;
+}
+
+float march_tau_f32(const Volume& V, V3<float> o, V3<float> d, float tend, float h, float jit) {
+    float tau = 0.0f, comp = 0.0f;
+    if (!(tend > 0.0f)) return 0.0f;
+    const int nseg = (int)std::ceil(tend / h);
+    for (int s = 0; s < nseg; ++s) {
+        const float s0 = (float)s * h;
+        const float s1 = std::min((float)(s + 1) * h, tend);
+        const float len = s1 - s0;
+        if (!(len > 0.0f)) continue;
+        const float y = sigma_at<float>(V, along(o, d, s0 + jit * len)) * len - comp;
+        const float t = tau + y;
+        comp = (t - tau) - y;
+        tau = t;
+    }
+    return tau - comp;
+}
+
 template <typename R>
 void camera_sample(const Volume& V, const Grid<R>& G, const Grid<R>& Gp, const Grid<R>& Gs, const Light* lights,
                    int n_lights, R g, const CamFrame& cf,
@@ -730,20 +820,24 @@ void camera_sample(const Volume& V, const Grid<R>& G, const Grid<R>& Gp, const G
     if (step_vox > (R)0) {
         R h = step_vox / (R)nmax;
         for (int b = 0; b < (n_lights + 3) / 4; ++b) { R w[4]; rng.uni4<R>(w); for (int i = 0; i < 4; ++i) if (4 * b + i < 16) jl[4 * b + i] = w[i]; }
-        R tau_star = -M<R>::ln((R)1 - b0[3]);
-        R tau = (R)0;
-        long nseg = (long)std::ceil((double)((t1 - t0) / h));
-        for (long s = 0; s < nseg; ++s) {
-            R s0 = t0 + (R)s * h;
-            R s1 = std::min(t0 + (R)(s + 1) * h, t1);
-            R len = s1 - s0;
-            if (!(len > (R)0)) continue;
-            R sg = sigma_at<R>(V, along(o, d, s0 + b0[2] * len));
-            if (sg > (R)0 && tau + sg * len >= tau_star) {
-                th = s0 + (tau_star - tau) / sg;
-                hit = true; break;
+        if constexpr (std::is_same<R, float>::value) {
+            hit = march_flight_f32(V, o, d, t0, t1, h, b0[2], b0[3], &th);
+        } else {
+            R tau_star = -M<R>::ln((R)1 - b0[3]);
+            R tau = (R)0;
+            long nseg = (long)std::ceil((double)((t1 - t0) / h));
+            for (long s = 0; s < nseg; ++s) {
+                R s0 = t0 + (R)s * h;
+                R s1 = std::min(t0 + (R)(s + 1) * h, t1);
+                R len = s1 - s0;
+                if (!(len > (R)0)) continue;
+                R sg = sigma_at<R>(V, along(o, d, s0 + b0[2] * len));
+                if (sg > (R)0 && tau + sg * len >= tau_star) {
+                    th = s0 + (tau_star - tau) / sg;
+                    hit = true; break;
+                }
+                tau = tau + sg * len;
             }
-            tau = tau + sg * len;
         }
     } else {
         hit = delta_track<R>(V, Gp, o, d, t0, t1, rng, &th, nullptr);
@@ -761,7 +855,10 @@ void camera_sample(const Volume& V, const Grid<R>& G, const Grid<R>& Gp, const G
         R T;
         if (step_vox > (R)0) {
             R h = step_vox / (R)nmax;
-            T = std::exp(-march_tau<R>(V, x, wl, (R)0, tend, h, jl[l]));
+            if constexpr (std::is_same<R, float>::value)
+                T = (float)std::exp(-(double)march_tau_f32(V, x, wl, tend, h, jl[l]));
+            else
+                T = std::exp(-march_tau<R>(V, x, wl, (R)0, tend, h, jl[l]));
         } else {
             Rng rs(seed, 5, shadow_item((uint64_t)py * (uint64_t)cf.W + (uint64_t)px, 1, l), (uint32_t)k);
             T = ratio_track_thinned<R>(V, G, Gs, x, wl, tend, rs);
@@ -937,6 +1034,21 @@ void orc_philox_item(uint64_t seed, uint32_t tag, uint32_t sub, uint64_t item, i
 void orc_lnf(const float* x, float* y, int64_t n) { for (int64_t i = 0; i < n; ++i) y[i] = own_lnf(x[i]); }
 void orc_sincos2pif(const float* u, float* s, float* c, int64_t n) {
     for (int64_t i = 0; i < n; ++i) own_sincos2pif(u[i], s + i, c + i);
+}
+
+void orc_atan2f(const float* y, const float* x, float* out, int64_t n) {
+    for (int64_t i = 0; i < n; ++i) out[i] = own_atan2f(y[i], x[i]);
+}
+
+// Field queries (x, theta', phi', g) of camera samples in float32, as the
+// renderer forms them from its float32 interaction point and direction.
+void orc_query_f32(const float* x, const float* wo, float g, int64_t n, float* q) {
+    for (int64_t i = 0; i < n; ++i) {
+        float th, ph;
+        query_angles_f32(wo[3 * i], wo[3 * i + 1], wo[3 * i + 2], &th, &ph);
+        q[6 * i + 0] = x[3 * i]; q[6 * i + 1] = x[3 * i + 1]; q[6 * i + 2] = x[3 * i + 2];
+        q[6 * i + 3] = th; q[6 * i + 4] = ph; q[6 * i + 5] = g;
+    }
 }
 
 double orc_hg_eval(double g, double mu) { return hg_eval<double>(g, mu); }

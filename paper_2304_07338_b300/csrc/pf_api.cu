@@ -165,46 +165,65 @@ extern "C" pf_status pf_sync(pf_ctx* c) {
   return pf_check_error_word(c);
 }
 
-pf_status pf_check_volume(pf_ctx* ctx, const pf_volume* v) {
-  if (!v) return pf_fail(ctx, PF_ERR_INVALID_ARG, "volume is NULL");
+// Argument checks that need no context: on a problem they write a message
+// into buf (len bytes) and return true.  Both the context entry points and
+// the allocation-free path tracer use them, so they accept the same inputs.
+bool pf_volume_problem(const pf_volume* v, char* buf, size_t len) {
+  auto bad = [&](const char* fmt, auto... a) {
+    if (buf && len) snprintf(buf, len, fmt, a...);
+    return true;
+  };
+  if (!v) return bad("%s", "volume is NULL");
   if (v->nx < 1 || v->ny < 1 || v->nz < 1 || v->nx > 8192 || v->ny > 8192 || v->nz > 8192)
-    return pf_fail(ctx, PF_ERR_INVALID_ARG, "volume extents must be in [1, 8192]");
-  if (v->dtype < 0 || v->dtype > 2) return pf_fail(ctx, PF_ERR_INVALID_ARG, "unknown volume dtype %d", v->dtype);
-  if (!v->data_dev || !v->tf_lut_dev) return pf_fail(ctx, PF_ERR_INVALID_ARG, "volume data or transfer function is NULL");
-  if (v->tf_n < 2 || v->tf_n > 65536) return pf_fail(ctx, PF_ERR_INVALID_ARG, "tf_n must be in [2, 65536]");
-  if ((uintptr_t)v->tf_lut_dev % 16) return pf_fail(ctx, PF_ERR_INVALID_ARG, "transfer function must be 16-byte aligned");
-  if (!(v->sigma_scale >= 0.f) || !std::isfinite(v->sigma_scale) || !(v->albedo >= 0.f))
-    return pf_fail(ctx, PF_ERR_INVALID_ARG, "sigma_scale and albedo must be finite and non-negative");
-  if (!(v->majorant >= 0.f) || !std::isfinite(v->majorant)) return pf_fail(ctx, PF_ERR_INVALID_ARG, "majorant must be >= 0");
+    return bad("%s", "volume extents must be in [1, 8192]");
+  if (v->dtype < 0 || v->dtype > 2) return bad("unknown volume dtype %d", (int)v->dtype);
+  if (!v->data_dev || !v->tf_lut_dev) return bad("%s", "volume data or transfer function is NULL");
+  if (v->tf_n < 2 || v->tf_n > 65536) return bad("%s", "tf_n must be in [2, 65536]");
+  if ((uintptr_t)v->tf_lut_dev % 16) return bad("%s", "transfer function must be 16-byte aligned");
+  if (!(v->sigma_scale >= 0.f) || !std::isfinite(v->sigma_scale) || !(v->albedo >= 0.f) || !std::isfinite(v->albedo))
+    return bad("%s", "sigma_scale and albedo must be finite and non-negative");
+  if (!(v->majorant >= 0.f) || !std::isfinite(v->majorant)) return bad("%s", "majorant must be finite and >= 0");
   if (v->brick != 0 && (v->brick < 2 || v->brick > 256 || (v->brick & (v->brick - 1))))
-    return pf_fail(ctx, PF_ERR_INVALID_ARG, "brick must be 0 (= 8) or a power of two in [2, 256]");
-  {
-    const int Bb = v->brick ? v->brick : 8;
-    if (v->brick_primary != 0 && (v->brick_primary < Bb || v->brick_primary > 1024 ||
-                                  (v->brick_primary & (v->brick_primary - 1))))
-      return pf_fail(ctx, PF_ERR_INVALID_ARG, "brick_primary must be 0 or a power-of-two multiple of brick, <= 1024");
-    if (v->brick_shadow != 0 && (v->brick_shadow < Bb || v->brick_shadow > 1024 ||
-                                 (v->brick_shadow & (v->brick_shadow - 1))))
-      return pf_fail(ctx, PF_ERR_INVALID_ARG, "brick_shadow must be 0 or a power-of-two multiple of brick, <= 1024");
+    return bad("%s", "brick must be 0 (= 8) or a power of two in [2, 256]");
+  const int Bb = v->brick ? v->brick : 8;
+  if (v->brick_primary != 0 &&
+      (v->brick_primary < Bb || v->brick_primary > 1024 || (v->brick_primary & (v->brick_primary - 1))))
+    return bad("%s", "brick_primary must be 0 or a power-of-two multiple of brick, <= 1024");
+  if (v->brick_shadow != 0 &&
+      (v->brick_shadow < Bb || v->brick_shadow > 1024 || (v->brick_shadow & (v->brick_shadow - 1))))
+    return bad("%s", "brick_shadow must be 0 or a power-of-two multiple of brick, <= 1024");
+  const int64_t B = Bb;
+  if (((v->nx + B - 1) / B) * ((v->ny + B - 1) / B) * ((v->nz + B - 1) / B) >= ((int64_t)1 << 31))
+    return bad("%s", "too many majorant bricks (>= 2^31): use a larger brick");
+  return false;
+}
+
+bool pf_lights_problem(const pf_light* l, int n, char* buf, size_t len) {
+  auto bad = [&](const char* fmt, auto... a) {
+    if (buf && len) snprintf(buf, len, fmt, a...);
+    return true;
+  };
+  if (n < 1 || n > PF_MAX_LIGHTS || !l) return bad("need 1..%d lights (host array)", PF_MAX_LIGHTS);
+  for (int i = 0; i < n; ++i) {
+    if (l[i].kind != 0 && l[i].kind != 1) return bad("light %d: unknown kind", i);
+    const float n2 = l[i].v[0] * l[i].v[0] + l[i].v[1] * l[i].v[1] + l[i].v[2] * l[i].v[2];
+    if (l[i].kind == 0 && !(n2 > 0.f && std::isfinite(n2))) return bad("light %d: zero or non-finite direction", i);
+    if (l[i].kind == 1 && l[i].v[0] >= 0.f && l[i].v[0] <= 1.f && l[i].v[1] >= 0.f && l[i].v[1] <= 1.f &&
+        l[i].v[2] >= 0.f && l[i].v[2] <= 1.f)
+      return bad("light %d: point lights must lie outside the unit box", i);
   }
-  {
-    const int64_t B = v->brick ? v->brick : 8;
-    if (((v->nx + B - 1) / B) * ((v->ny + B - 1) / B) * ((v->nz + B - 1) / B) >= ((int64_t)1 << 31))
-      return pf_fail(ctx, PF_ERR_INVALID_ARG, "too many majorant bricks (>= 2^31): use a larger brick");
-  }
+  return false;
+}
+
+pf_status pf_check_volume(pf_ctx* ctx, const pf_volume* v) {
+  char msg[256];
+  if (pf_volume_problem(v, msg, sizeof(msg))) return pf_fail(ctx, PF_ERR_INVALID_ARG, "%s", msg);
   return PF_OK;
 }
 
 pf_status pf_check_lights(pf_ctx* ctx, const pf_light* l, int n) {
-  if (n < 1 || n > PF_MAX_LIGHTS || !l) return pf_fail(ctx, PF_ERR_INVALID_ARG, "need 1..%d lights (host array)", PF_MAX_LIGHTS);
-  for (int i = 0; i < n; ++i) {
-    if (l[i].kind != 0 && l[i].kind != 1) return pf_fail(ctx, PF_ERR_INVALID_ARG, "light %d: unknown kind", i);
-    float n2 = l[i].v[0] * l[i].v[0] + l[i].v[1] * l[i].v[1] + l[i].v[2] * l[i].v[2];
-    if (l[i].kind == 0 && !(n2 > 0.f)) return pf_fail(ctx, PF_ERR_INVALID_ARG, "light %d: zero direction", i);
-    if (l[i].kind == 1 && l[i].v[0] >= 0.f && l[i].v[0] <= 1.f && l[i].v[1] >= 0.f && l[i].v[1] <= 1.f &&
-        l[i].v[2] >= 0.f && l[i].v[2] <= 1.f)
-      return pf_fail(ctx, PF_ERR_INVALID_ARG, "light %d: point lights must lie outside the unit box", i);
-  }
+  char msg[256];
+  if (pf_lights_problem(l, n, msg, sizeof(msg))) return pf_fail(ctx, PF_ERR_INVALID_ARG, "%s", msg);
   return PF_OK;
 }
 

@@ -109,6 +109,45 @@ __device__ __forceinline__ void own_sincos2pif(float u, float* s_out, float* c_o
   *s_out = s; *c_out = c;
 }
 
+// atan2(y, x) in float32: the quotient t = min(|x|,|y|) / max(|x|,|y|) in
+// [0, 1]; for t > tan(pi/8) the identity atan t = pi/4 + atan((t-1)/(t+1));
+// one half-angle step atan t = 2 atan(t / (1 + sqrt(1 + t^2))) brings the
+// argument below tan(pi/16); the odd Taylor series of atan to u^11
+// (truncation < 1e-10); then the octant and quadrant fix-ups.  atan2(0, 0) = 0.
+__device__ __forceinline__ float own_atan2f(float y, float x) {
+  const float ax = fabsf(x), ay = fabsf(y);
+  const float hi = (ax < ay) ? ay : ax;
+  const float lo = (ax < ay) ? ax : ay;
+  if (!(hi > 0.0f)) return 0.0f;
+  float t = lo / hi;
+  const bool big = t > 0.414213562f;
+  if (big) t = (t - 1.0f) / (t + 1.0f);
+  const float u = t / (1.0f + sqrtf(1.0f + t * t));
+  const float u2 = u * u;
+  float p = -0.0909090909f;         // -1/11
+  p = p * u2 + 0.111111111f;        // 1/9
+  p = p * u2 + -0.142857143f;       // -1/7
+  p = p * u2 + 0.2f;                // 1/5
+  p = p * u2 + -0.333333333f;       // -1/3
+  float r = u + u * (u2 * p);
+  r = r + r;
+  if (big) r = r + 0.785398163f;
+  if (ax < ay) r = 1.57079633f - r;
+  if (x < 0.0f) r = 3.14159265f - r;
+  return (y < 0.0f) ? -r : r;
+}
+
+// The field's direction inputs (Sec. 3.1, normalised spherical coordinates)
+// of an outgoing direction w: theta' = acos(w_z) / pi (acos as
+// atan2(sqrt((1 - z)(1 + z)), z)), phi' = atan2(w_y, w_x) / 2pi mod 1.
+__device__ __forceinline__ void query_angles(float wx, float wy, float wz, float* th, float* ph) {
+  const float z = (wz < -1.0f) ? -1.0f : ((wz > 1.0f) ? 1.0f : wz);
+  *th = own_atan2f(sqrtf((1.0f - z) * (1.0f + z)), z) * 0.318309886f;
+  float p = own_atan2f(wy, wx) * 0.159154943f;
+  if (p < 0.0f) p = p + 1.0f;
+  *ph = p;
+}
+
 // min / max with the semantics of std::min / std::max (first argument on ties)
 __device__ __forceinline__ float mn(float a, float b) { return (b < a) ? b : a; }
 __device__ __forceinline__ float mx(float a, float b) { return (a < b) ? b : a; }

@@ -105,7 +105,10 @@ struct DeviceGuard {
   ~DeviceGuard() { int cur; cudaGetDevice(&cur); if (prev >= 0 && cur != prev) cudaSetDevice(prev); }
 };
 
-// Volume validation and majorant.
+// Volume validation and majorant.  The *_problem forms need no context: on a
+// problem they write a message into buf and return true.
+bool pf_volume_problem(const pf_volume* vol, char* buf, size_t len);
+bool pf_lights_problem(const pf_light* lights, int n, char* buf, size_t len);
 pf_status pf_check_volume(pf_ctx* ctx, const pf_volume* vol);
 pf_status pf_majorant_impl(pf_ctx* ctx, const pf_volume* vol, float* out);
 pf_status pf_check_lights(pf_ctx* ctx, const pf_light* lights, int n);

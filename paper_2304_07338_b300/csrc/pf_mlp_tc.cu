@@ -732,6 +732,375 @@ __global__ void k_reduce_partials(const float* __restrict__ partial, int n_parts
   dw[i] = (s0 + s1) + (s2 + s3);
 }
 
+// ---------------------------------------------------------------- training step, width 128
+// Fields of width 128 (the render workloads' 4 x 128) do not fit the
+// query-per-lane plan above: four resident weight matrices (132 KB) plus
+// every layer's 128-query input tile exceed shared memory, and dW of all
+// layers (144 + 3 x 128 columns) plus an accumulator exceed TMEM.  This
+// kernel transposes the problem so that every MMA has M = 128 neurons (or
+// input features) on the TMEM lanes and the tile's Q = 64 queries on the
+// columns:
+//   forward  : Z_l^T [n][q] = W_l [n][k] X_l^T [k][q]  (A = W_l K-major,
+//              B = X_l; X_0 is stored query rows (K-major), X_{l>0} feature
+//              rows with the queries contiguous (MN-major));
+//              X_{l+1} = rnd(ReLU(Z_l)) written by the thread that owns
+//              neuron n (one TMEM lane) as feature row n;
+//   output   : y = W_out h on the CUDA cores from the unrounded last
+//              activation, summed over the 128 neurons by a warp butterfly
+//              per channel and over the four warps in shared memory;
+//   backward : dW_l [n][k] += dZ_l [n][q] X_l [q][k]  (both K-major over q
+//              for l > 0; X_0 MN-major), accumulated in TMEM across the
+//              CTA's tiles for l > 0; dA_l^T [k][q] = W_l^T [k][n] dZ_l^T
+//              [n][q] (A = W_l viewed MN-major, B = dZ_l MN-major), masked
+//              by [X_l > 0] and rounded into dZ_{l-1};
+//   dW_0     : 144 columns do not fit beside dW_1..3 (384) and the
+//              accumulator (64), so each tile's dW_0 goes through the free
+//              128 columns in two MMAs (features 0..127, then the rest) and
+//              is summed in registers (72 per thread).
+// TMEM: [0, 384) dW_1..3, [384, 448) accumulator, [448, 512) spare.
+// Two warpgroups: warp w reads TMEM lanes 32 (w mod 4) .. + 31 (its neuron
+// rows); warpgroup hf takes the query columns [32 hf, 32 hf + 32).
+constexpr int kT128Threads = 256;
+constexpr int kT128Q = 64;                         // queries per tile (MMA N)
+constexpr uint32_t kT128RowGroup = kT128Q * 2 / 16 * 128;   // bytes between 8-row groups of a [row][q] tile
+constexpr uint32_t kT128Acc = 384;                 // TMEM column of the forward / dA accumulator
+
+struct T128Args {
+  const uint8_t* wq;        // packed hidden-layer weights (k_pack_all layout)
+  uint32_t wq_bytes;
+  const float* w_out;       // [3][128] float32 output layer
+  int n_hidden, in_freqs;
+  uint32_t w_off[4], kp[4]; // packed layer offsets (bytes) and K extents
+  uint32_t x_off[4];        // X_l tiles
+  uint32_t dz_off, wout_off, dys_off, red_off, bar_off, smem_bytes;
+  int64_t layer_off[6];
+  int64_t n_params;
+};
+
+// 16 bytes (8 operands) of row r, query chunk c of a [row][q] tile (rows in
+// groups of 8, the Q queries of a row contiguous in 16-byte chunks).
+__device__ __forceinline__ uint32_t qrow_off(int r, int c) {
+  return (uint32_t)(r >> 3) * kT128RowGroup + (uint32_t)c * 128 + (uint32_t)(r & 7) * 16;
+}
+
+template <int PREC>
+__device__ __forceinline__ uint4 pack8(const float* v) {
+  uint4 q;
+  q.x = pack2<PREC>(v[0], v[1]); q.y = pack2<PREC>(v[2], v[3]);
+  q.z = pack2<PREC>(v[4], v[5]); q.w = pack2<PREC>(v[6], v[7]);
+  return q;
+}
+
+__device__ __forceinline__ bool op_positive(uint16_t h) { return (h & 0x8000u) == 0 && (h & 0x7FFFu) != 0; }
+
+template <int PREC>
+__global__ void __launch_bounds__(kT128Threads, 1) k_tc_train128(T128Args T, const float* __restrict__ q,
+                                                                  const float* __restrict__ targets,
+                                                                  const float* __restrict__ dy_in, int64_t B,
+                                                                  float inv_n, float* __restrict__ partial,
+                                                                  float* __restrict__ loss, uint32_t* err) {
+  constexpr uint32_t AB = (PREC == PF_PREC_BF16) ? 1u : 0u;
+  constexpr int H = 128;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int hf = warp >> 2, lq = warp & 3;
+  const int n = lq * 32 + lane;                        // this thread's TMEM lane (neuron / feature row)
+  const int L = T.n_hidden;
+  float* w_out = (float*)(smem + T.wout_off);
+  float* dys = (float*)(smem + T.dys_off);             // [Q][4] dy of the tile's queries
+  float* red = (float*)(smem + T.red_off);             // [2][4][32][3] output-layer warp sums
+  uint64_t* bars = (uint64_t*)(smem + T.bar_off);
+  uint32_t* tmem_slot = (uint32_t*)(smem + T.bar_off + 16);
+  int* abort_flag = (int*)(smem + T.bar_off + 20);
+  const uint32_t bar_w = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]);
+  uint8_t* dz = smem + T.dz_off;
+
+  if (tid == 0) {
+    mbar_init(bar_w, 1);
+    mbar_init(bar_mma, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int i = tid; i < 3 * H; i += kT128Threads) w_out[i] = T.w_out[i];
+  if (warp == 0) tmem_alloc(tmem_slot, 512);
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  if (tid == 0) {
+    mbar_expect_tx(bar_w, T.wq_bytes);
+    bulk_g2s(smem_u32(smem), T.wq, T.wq_bytes, bar_w);
+  }
+  if (!mbar_wait(bar_w, 0) && tid == 0) { atomicOr(err, PFE_ITER_CAP); *abort_flag = 1; }
+  __syncthreads();
+
+  const uint32_t lane_addr = tmem + ((uint32_t)(lq * 32) << 16);
+  const float wo0 = w_out[n], wo1 = w_out[H + n], wo2 = w_out[2 * H + n];
+  constexpr int F = 12;                                // frequencies (the plan admits only 12)
+  constexpr uint32_t kp0 = 12 * F;                     // 144 input features
+  const uint32_t x0_rg = kp0 * 2 / 16 * 128;           // X_0: bytes between 8-query groups
+  float dw0a[64], dw0b[8];
+#pragma unroll
+  for (int i = 0; i < 64; ++i) dw0a[i] = 0.f;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) dw0b[i] = 0.f;
+  float dwo0 = 0.f, dwo1 = 0.f, dwo2 = 0.f, lsum = 0.f;
+  uint32_t phase = 0;
+  bool first_tile = true;
+  const int64_t n_tiles = (B + kT128Q - 1) / kT128Q;
+
+  auto pre_mma = [&]() {
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  };
+  auto commit_wait = [&]() -> bool {
+    if (tid == 0) mma_commit(bar_mma);
+    const bool ok = mbar_wait(bar_mma, phase);
+    phase ^= 1u;
+    tc_fence_after();
+    if (!ok) { atomicOr(err, PFE_ITER_CAP); *abort_flag = 1; }
+    return ok;
+  };
+
+  for (int64_t tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x) {
+    const int64_t row0 = tile * kT128Q;
+    // ---- frequency encoding -> X_0 [q][k]: one (query, input) pair per item
+    {
+      uint8_t* x0 = smem + T.x_off[0];
+      for (int it = tid; it < kT128Q * 6; it += kT128Threads) {
+        const int qq = it & (kT128Q - 1), d = it / kT128Q;
+        const int64_t row = row0 + qq;
+        const float v = row < B ? __ldg(q + 6 * row + d) : 0.f;
+        float buf[8];
+#pragma unroll
+        for (int k = 0; k < F; ++k) {
+          float sn, cs;
+          sincospif(ldexpf(v, k), &sn, &cs);
+          buf[(2 * k) & 7] = sn;
+          buf[(2 * k + 1) & 7] = cs;
+          if (((2 * k + 2) & 7) == 0) {
+            const int f0 = 2 * F * d + 2 * k + 2 - 8;             // first feature of the chunk
+            *(uint4*)(x0 + (uint32_t)(qq >> 3) * x0_rg + (uint32_t)(f0 / 8) * 128 + (uint32_t)(qq & 7) * 16) =
+                pack8<PREC>(buf);
+          }
+        }
+      }
+    }
+    // ---- forward
+    float h[32];
+    for (int l = 0; l < L; ++l) {
+      pre_mma();
+      if (tid == 0) {
+        const uint32_t a0 = smem_u32(smem + T.w_off[l]), b0 = smem_u32(smem + T.x_off[l]);
+        const uint32_t a_sbo = T.kp[l] * 2 / 16 * 128;
+        const uint32_t id = idesc(AB, kT128Q, 0u, l > 0 ? 1u : 0u);
+        for (int ks = 0; ks < (int)(T.kp[l] / 16); ++ks) {
+          const uint64_t ad = sdesc(a0 + ks * 256, 128, a_sbo);
+          const uint64_t bd = l == 0 ? sdesc(b0 + ks * 256, 128, x0_rg)
+                                     : sdesc(b0 + ks * 2 * kT128RowGroup, kT128RowGroup, 128);
+          mma<false>(tmem + kT128Acc, ad, bd, id, ks > 0 ? 1u : 0u);
+        }
+      }
+      if (!commit_wait()) break;
+      float v[32];
+      tmem_ld16(lane_addr + kT128Acc + 32 * hf, v);
+      tmem_ld16(lane_addr + kT128Acc + 32 * hf + 16, v + 16);
+      if (l < L - 1) {
+        uint8_t* xn = smem + T.x_off[l + 1];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          float r[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) r[i] = fmaxf(v[8 * c + i], 0.f);
+          *(uint4*)(xn + qrow_off(n, 4 * hf + c)) = pack8<PREC>(r);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) h[i] = fmaxf(v[i], 0.f);
+      }
+    }
+    if (*abort_flag) break;
+    // ---- output layer: y[q][c] = sum_n W_out[c][n] h[n][q] (butterfly over the
+    // warp's 32 neurons, then the four warps in order)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float wc = c == 0 ? wo0 : (c == 1 ? wo1 : wo2);
+      float v[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) v[i] = wc * h[i];
+#pragma unroll
+      for (int s = 0; s < 5; ++s) {
+        const int off = 16 >> s, half = 16 >> s;
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+          const float send = up ? v[i] : v[half + i];
+          const float keep = up ? v[half + i] : v[i];
+          v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+      }
+      red[((hf * 4 + lq) * 32 + lane) * 3 + c] = v[0];   // query 32 hf + lane, this warp's neurons
+    }
+    __syncthreads();
+    if (lq == 0) {
+      const int qq = 32 * hf + lane;
+      const int64_t row = row0 + qq;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float y = ((red[((hf * 4 + 0) * 32 + lane) * 3 + c] + red[((hf * 4 + 1) * 32 + lane) * 3 + c]) +
+                         red[((hf * 4 + 2) * 32 + lane) * 3 + c]) + red[((hf * 4 + 3) * 32 + lane) * 3 + c];
+        float g = 0.f;
+        if (row < B) {
+          if (targets) {
+            const float t = targets[3 * row + c];
+            const float den = t * t + 0.01f;
+            const float diff = y - t;
+            lsum += diff * diff / den;
+            g = 2.f * diff / den * inv_n;
+          } else {
+            g = dy_in[3 * row + c];
+          }
+        }
+        dys[4 * qq + c] = g;
+      }
+    }
+    __syncthreads();
+    // ---- dW_out (registers, across tiles) and dZ_{L-1} = rnd((dy W_out) * [rnd(h) > 0])
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float r[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int qi = 8 * c + i;
+        const float4 dq = *(const float4*)(dys + 4 * (32 * hf + qi));
+        dwo0 = fmaf(dq.x, h[qi], dwo0);
+        dwo1 = fmaf(dq.y, h[qi], dwo1);
+        dwo2 = fmaf(dq.z, h[qi], dwo2);
+        const float dh = dq.x * wo0 + dq.y * wo1 + dq.z * wo2;
+        const float hr = PREC == PF_PREC_BF16 ? pff::round_bf16(h[qi]) : pff::round_f16(h[qi]);
+        r[i] = hr > 0.f ? dh : 0.f;
+      }
+      *(uint4*)(dz + qrow_off(n, 4 * hf + c)) = pack8<PREC>(r);
+    }
+    // ---- backward through the hidden layers l = L-1 .. 1
+    for (int l = L - 1; l >= 1; --l) {
+      pre_mma();
+      if (tid == 0) {
+        const uint32_t dz0 = smem_u32(dz), xl = smem_u32(smem + T.x_off[l]), wl = smem_u32(smem + T.w_off[l]);
+        // dW_l [n][k] (+)= dZ_l [n][q] X_l [q][k]: K = the tile's queries
+        const uint32_t idw = idesc(AB, T.kp[l], 0u, 0u);
+        const uint32_t dw_col = (uint32_t)(l - 1) * 128;
+        for (int ks = 0; ks < kT128Q / 16; ++ks)
+          mma<false>(tmem + dw_col, sdesc(dz0 + ks * 256, 128, kT128RowGroup), sdesc(xl + ks * 256, 128, kT128RowGroup),
+                     idw, (first_tile && ks == 0) ? 0u : 1u);
+        // dA_l^T [k][q] = W_l^T [k][n] dZ_l^T [n][q]: K = the layer's output neurons
+        const uint32_t w_rg = T.kp[l] * 2 / 16 * 128;
+        const uint32_t ida = idesc(AB, kT128Q, 1u, 1u);
+        for (int ks = 0; ks < H / 16; ++ks)
+          mma<false>(tmem + kT128Acc, sdesc(wl + ks * 2 * w_rg, w_rg, 128),
+                     sdesc(dz0 + ks * 2 * kT128RowGroup, kT128RowGroup, 128), ida, ks > 0 ? 1u : 0u);
+      }
+      if (!commit_wait()) break;
+      // dZ_{l-1} [k][q] = rnd(dA_l * [X_l > 0]), feature row k = this thread's lane
+      float v[32];
+      tmem_ld16(lane_addr + kT128Acc + 32 * hf, v);
+      tmem_ld16(lane_addr + kT128Acc + 32 * hf + 16, v + 16);
+      const uint8_t* xl = smem + T.x_off[l];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const uint4 raw = *(const uint4*)(xl + qrow_off(n, 4 * hf + c));
+        const uint16_t* hv = (const uint16_t*)&raw;
+        float r[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) r[i] = op_positive(hv[i]) ? v[8 * c + i] : 0.f;
+        *(uint4*)(dz + qrow_off(n, 4 * hf + c)) = pack8<PREC>(r);
+      }
+    }
+    if (*abort_flag) break;
+    // ---- dW_0 of this tile through the free columns [384, 512): features
+    // 0..127, then 128..143, each summed into registers
+    {
+      const uint32_t dz0 = smem_u32(dz), x0 = smem_u32(smem + T.x_off[0]);
+      pre_mma();
+      if (tid == 0) {
+        const uint32_t id = idesc(AB, 128, 0u, 1u);     // features 0..127
+        for (int ks = 0; ks < kT128Q / 16; ++ks)
+          mma<false>(tmem + kT128Acc, sdesc(dz0 + ks * 256, 128, kT128RowGroup),
+                     sdesc(x0 + ks * 2 * x0_rg, x0_rg, 128), id, ks > 0 ? 1u : 0u);
+      }
+      if (!commit_wait()) break;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {                     // warpgroup hf: features 64 hf .. 64 hf + 63
+        float v[16];
+        tmem_ld16(lane_addr + kT128Acc + 64 * hf + 16 * j, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) dw0a[16 * j + i] += v[i];
+      }
+      {
+        tc_fence_before();
+        __syncthreads();                                 // every thread has read the columns
+        tc_fence_after();
+        if (tid == 0) {
+          const uint32_t id = idesc(AB, 16, 0u, 1u);
+          const uint32_t xb = x0 + (128 / 8) * 128;      // features 128.. (MN direction: 128 B per 8)
+          for (int ks = 0; ks < kT128Q / 16; ++ks)
+            mma<false>(tmem + kT128Acc, sdesc(dz0 + ks * 256, 128, kT128RowGroup),
+                       sdesc(xb + ks * 2 * x0_rg, x0_rg, 128), id, ks > 0 ? 1u : 0u);
+        }
+        if (!commit_wait()) break;
+        float v[16];
+        tmem_ld16(lane_addr + kT128Acc, v);               // features 128..143; warpgroup hf takes 8 of them
+#pragma unroll
+        for (int i = 0; i < 8; ++i) dw0b[i] += v[8 * hf + i];
+      }
+    }
+    first_tile = false;
+  }
+  // ---- this CTA's partial gradient row
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  float* part = partial + (size_t)blockIdx.x * (size_t)T.n_params;
+  if (!*abort_flag) {
+    for (int l = 1; l < L; ++l) {
+      float* dst = part + T.layer_off[l] + (int64_t)n * H + 64 * hf;
+      for (int c0 = 0; c0 < 64; c0 += 16) {
+        float v[16];
+        if (first_tile) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] = 0.f;
+        } else {
+          tmem_ld16(lane_addr + (uint32_t)(l - 1) * 128 + 64 * hf + c0, v);
+        }
+#pragma unroll
+        for (int i = 0; i < 16; i += 4) *(float4*)(dst + c0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+      }
+    }
+    float* d0 = part + T.layer_off[0] + (int64_t)n * kp0;
+#pragma unroll
+    for (int i = 0; i < 64; i += 4) *(float4*)(d0 + 64 * hf + i) = make_float4(dw0a[i], dw0a[i + 1], dw0a[i + 2], dw0a[i + 3]);
+#pragma unroll
+    for (int i = 0; i < 8; i += 4) *(float4*)(d0 + 128 + 8 * hf + i) = make_float4(dw0b[i], dw0b[i + 1], dw0b[i + 2], dw0b[i + 3]);
+  }
+  // dW_out: the two warpgroups' sums, added in order
+  __syncthreads();
+  red[(hf * 3 + 0) * H + n] = dwo0;
+  red[(hf * 3 + 1) * H + n] = dwo1;
+  red[(hf * 3 + 2) * H + n] = dwo2;
+  __syncthreads();
+  if (!*abort_flag)
+    for (int i = tid; i < 3 * H; i += kT128Threads) part[T.layer_off[L] + i] = red[i] + red[3 * H + i];
+  if (loss) {
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if (lane == 0 && lsum != 0.f) atomicAdd(loss, lsum * inv_n);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+
 // ---------------------------------------------------------------- weight packing
 // Hidden layer l packed K-major in 8 x 16-byte core matrices:
 //   byte(n, k) = ((n/8) * (kp*eb/16) + (k*eb)/16) * 128 + (n%8) * 16 + (k*eb)%16
@@ -825,6 +1194,43 @@ bool plan(const pf_field* f, TcArgs* A, bool for_train = false) {
 
 }  // namespace
 
+namespace {
+// Shared-memory plan of k_tc_train128 (bf16 / f16, width 128, frequency
+// encoding with 12 frequencies, 2..4 hidden layers).
+bool plan_train128(const pf_field* f, T128Args* T) {
+  if (f->desc.prec != PF_PREC_BF16 && f->desc.prec != PF_PREC_F16) return false;
+  if (f->desc.hidden != 128 || f->desc.encoding == PF_ENC_HASHGRID) return false;
+  const int F = f->desc.in_freqs;
+  if (F != 12) return false;
+  const int L = f->n_layers - 1;
+  if (L < 2 || L > 4) return false;
+  TcArgs A;
+  if (!plan(f, &A, true)) return false;
+  T->n_hidden = L;
+  T->in_freqs = F;
+  T->wq_bytes = A.wq_bytes;
+  for (int l = 0; l < L; ++l) { T->w_off[l] = A.L[l].w_off; T->kp[l] = A.L[l].kp; }
+  if (T->kp[0] != 144) return false;
+  uint32_t off = (A.wq_bytes + 1023) / 1024 * 1024;
+  T->x_off[0] = off;
+  off += kT128Q * T->kp[0] * 2;
+  for (int l = 1; l < L; ++l) { T->x_off[l] = off; off += kT128Q * 128 * 2; }
+  T->dz_off = off;
+  off += kT128Q * 128 * 2;
+  T->wout_off = off;
+  off += 3 * 128 * 4;
+  T->dys_off = off;
+  off += kT128Q * 4 * 4;
+  T->red_off = off;
+  off += 2 * 3 * 128 * 4;                          // >= [2][4][32][3] and [2][3][128] floats
+  T->bar_off = (off + 15) / 16 * 16;
+  T->smem_bytes = T->bar_off + 64;
+  for (int l = 0; l <= f->n_layers; ++l) T->layer_off[l] = f->layer_off[l];
+  T->n_params = f->layer_off[f->n_layers];
+  return T->smem_bytes <= 227 * 1024;
+}
+}  // namespace
+
 pf_status pf_tc_available(const pf_field* f) {
   TcArgs A;
   return plan(f, &A) ? PF_OK : PF_ERR_UNSUPPORTED;
@@ -896,11 +1302,30 @@ bool plan_train(const pf_field* f, TrArgs* T) {
 
 pf_status pf_tc_backward_available(const pf_field* f) {
   TrArgs T;
-  return plan_train(f, &T) ? PF_OK : PF_ERR_UNSUPPORTED;
+  T128Args T2;
+  return (plan_train(f, &T) || plan_train128(f, &T2)) ? PF_OK : PF_ERR_UNSUPPORTED;
 }
 
 pf_status pf_tc_backward(pf_ctx* ctx, const pf_field* f, const float* q, const float* dy, const float* targets,
                          int64_t B, float* dw, float* loss, const uint16_t* x_in, float* dx_out) {
+  T128Args T2;
+  if (plan_train128(f, &T2)) {
+    T2.wq = (const uint8_t*)f->wq;
+    T2.w_out = f->w + f->layer_off[f->n_layers - 1];
+    const int64_t tiles = (B + kT128Q - 1) / kT128Q;
+    const int grid = (int)std::min<int64_t>(tiles, (int64_t)ctx->num_sms);
+    float* partial;
+    PF_TRY(pf_scratch(ctx, WS_ACT, (size_t)grid * T2.n_params * sizeof(float), (void**)&partial));
+    const float inv_n = targets ? 1.0f / (float)(3 * B) : 0.f;
+    auto kern = f->desc.prec == PF_PREC_BF16 ? k_tc_train128<PF_PREC_BF16> : k_tc_train128<PF_PREC_F16>;
+    PF_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T2.smem_bytes));
+    kern<<<grid, kT128Threads, T2.smem_bytes, ctx->stream>>>(T2, q, targets, dy, B, inv_n, partial, loss,
+                                                             ctx->err_dev);
+    PF_CUDA(ctx, cudaGetLastError());
+    k_reduce_partials<<<(unsigned)((T2.n_params + 127) / 128), 128, 0, ctx->stream>>>(partial, grid, T2.n_params, dw);
+    PF_CUDA(ctx, cudaGetLastError());
+    return PF_OK;
+  }
   TrArgs T;
   if (!plan_train(f, &T)) return pf_fail(ctx, PF_ERR_UNSUPPORTED, "field shape not supported by the tensor-core backward");
   if (T.hash && (!x_in || !dx_out)) return pf_fail(ctx, PF_ERR_INVALID_ARG, "hash-grid backward needs its features");
@@ -938,7 +1363,8 @@ pf_status pf_field_pack(pf_ctx* ctx, pf_field* f) {
   TcArgs A;
   const bool tc_fwd = plan(f, &A);
   TrArgs T;
-  const bool tc_bwd = f->desc.prec != PF_PREC_FP8 && plan_train(f, &T);
+  T128Args T2;
+  const bool tc_bwd = f->desc.prec != PF_PREC_FP8 && (plan_train(f, &T) || plan_train128(f, &T2));
   // the float copy rounded to the field precision serves only the SIMT
   // kernels: needed unless every pass of this field runs on tcgen05
   const bool need_wr = !tc_fwd || (f->desc.prec != PF_PREC_FP8 && !tc_bwd);

@@ -211,9 +211,8 @@ __device__ __forceinline__ void camera_samples(Vol V, DevLights L, CamF cam, flo
   base = __shfl_sync(0xffffffffu, base, 0);
   if (valid) {
     uint32_t i = base + __popc(ball & ((1u << lane) - 1u));
-    float th = acosf(fminf(fmaxf(wo.z, -1.f), 1.f)) * 0.318309886183790672f;
-    float ph = atan2f(wo.y, wo.x) * 0.159154943091895336f;
-    if (ph < 0.f) ph = ph + 1.0f;
+    float th, ph;
+    query_angles(wo.x, wo.y, wo.z, &th, &ph);
     cq[6 * (size_t)i + 0] = x.x; cq[6 * (size_t)i + 1] = x.y; cq[6 * (size_t)i + 2] = x.z;
     cq[6 * (size_t)i + 3] = th;  cq[6 * (size_t)i + 4] = ph;  cq[6 * (size_t)i + 5] = g;
     calb[3 * (size_t)i + 0] = alb.x; calb[3 * (size_t)i + 1] = alb.y; calb[3 * (size_t)i + 2] = alb.z;
@@ -778,9 +777,8 @@ __global__ void __launch_bounds__(128) k_raymarch(Vol V, DevLights L, CamF cam, 
   const uint64_t j_end = (EMIT && q) ? off[ray + 1] - base : 0;   // the ray's range (the count pass's)
   float t0, t1;
   if (box_hit(o, d, &t0, &t1)) {
-    const float qth = acosf(fminf(fmaxf(-d.z, -1.f), 1.f)) * 0.318309886183790672f;
-    float qph = atan2f(-d.y, -d.x) * 0.159154943091895336f;
-    if (qph < 0.f) qph = qph + 1.0f;
+    float qth, qph;
+    query_angles(-d.x, -d.y, -d.z, &qth, &qph);
     float tau = 0.f, comp = 0.f;
     const int nseg = (int)ceilf((t1 - t0) / h);
     for (int s = 0; s < nseg; ++s) {
@@ -1213,26 +1211,14 @@ extern "C" pf_status pf_render_pathtraced_noalloc(const pf_volume* vol, const pf
                                                   int use_rr, void* cuda_stream, float* out_rgb_dev, char* err_msg,
                                                   int err_len) {
   put_msg(err_msg, err_len, "%s", "");
-  // argument checks (written out here: no context, no heap)
-  if (!vol || !vol->data_dev || !vol->tf_lut_dev || vol->nx < 1 || vol->ny < 1 || vol->nz < 1 || vol->nx > 8192 ||
-      vol->ny > 8192 || vol->nz > 8192 || vol->dtype < 0 || vol->dtype > 2 || vol->tf_n < 2 || vol->tf_n > 65536 ||
-      ((uintptr_t)vol->tf_lut_dev % 16) || !(vol->sigma_scale >= 0.f) || !(vol->albedo >= 0.f)) {
-    put_msg(err_msg, err_len, "invalid volume");
-    return PF_ERR_INVALID_ARG;
-  }
+  // argument checks: the same volume and light checks as the context entry
+  // points (pf_check_volume / pf_check_lights), without a context
+  if (pf_volume_problem(vol, err_msg, err_len > 0 ? (size_t)err_len : 0)) return PF_ERR_INVALID_ARG;
   if (!vol->brick_majorants_dev) {
     put_msg(err_msg, err_len, "volume->brick_majorants_dev must be set: this entry point does not compute it");
     return PF_ERR_INVALID_ARG;
   }
-  if (!lights || n_lights < 1 || n_lights > PF_MAX_LIGHTS) {
-    put_msg(err_msg, err_len, "need 1..%d lights", PF_MAX_LIGHTS);
-    return PF_ERR_INVALID_ARG;
-  }
-  for (int i = 0; i < n_lights; ++i)
-    if (lights[i].kind != 0 && lights[i].kind != 1) {
-      put_msg(err_msg, err_len, "light %d: unknown kind", i);
-      return PF_ERR_INVALID_ARG;
-    }
+  if (pf_lights_problem(lights, n_lights, err_msg, err_len > 0 ? (size_t)err_len : 0)) return PF_ERR_INVALID_ARG;
   if (!cam || cam->width <= 0 || cam->height <= 0 || !(cam->fovy_deg > 0.f && cam->fovy_deg < 180.f) || spp <= 0 ||
       spp > (1 << 24) || max_bounces < 1 || max_bounces > 1024 || !(g > -1.f && g < 1.f) || !out_rgb_dev) {
     put_msg(err_msg, err_len, "invalid camera, spp, max_bounces, g or output");

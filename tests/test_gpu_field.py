@@ -68,7 +68,7 @@ def test_forward_empty_and_single(pf_ctx):
     assert np.abs(y1 - ref).max() < 1e-5
 
 
-@pytest.mark.parametrize("prec,hidden", [("f32", 64), ("bf16", 64), ("f16", 64)])
+@pytest.mark.parametrize("prec,hidden", [("f32", 64), ("bf16", 64), ("f16", 64), ("f16", 128), ("bf16", 128)])
 def test_backward_matches_oracle(pf_ctx, prec, hidden):
     n_hidden = 4
     fld = api.Field(pf_ctx, 12, hidden, n_hidden, prec, 5.0, seed=4)
@@ -139,10 +139,10 @@ def test_targets_match_oracle(pf_ctx, orc, small_cache):
     np.testing.assert_allclose(lp.cpu().numpy(), F.log_encode(ref, 5.0), rtol=0, atol=2e-6)
 
 
-@pytest.mark.parametrize("prec", ["f32", "bf16"])
-def test_training_reduces_loss(pf_ctx, small_cache, prec):
+@pytest.mark.parametrize("prec,hidden", [("f32", 64), ("bf16", 64), ("f16", 128)])
+def test_training_reduces_loss(pf_ctx, small_cache, prec, hidden):
     sc, cache, oc, csig = small_cache
-    fld = api.Field(pf_ctx, 12, 64, 4, prec, 5.0, seed=8)
+    fld = api.Field(pf_ctx, 12, hidden, 4, prec, 5.0, seed=8)
     loss = fld.train(cache, steps=60, batch=4096, lr=1e-2, seed=3)
     assert np.all(np.isfinite(loss))
     assert loss[-10:].mean() < 0.5 * loss[:5].mean(), (loss[:5], loss[-10:])

@@ -2,21 +2,22 @@
 path-tracing baseline), through the C ABI.
 
   * ray-marched neural renderer, field off, plain-method scene at full size
-    (64^3 blobs, 128^2 x 4 spp): per-pixel relative error <= 1e-4 against the
-    FP64 oracle (error = |a-b| / max(|b|, 1e-3 max|b|)) on all but 0.05% of
-    pixels, <= 3e-4 everywhere (see the conditioning note in the test);
-  * the same with the float32 field on: the field's input position inherits
-    the marcher's float32 rounding (~1e-7) and the 12-frequency encoding
-    multiplies it by up to 2^11 pi (6e-4 in the highest feature), which the
-    Kaiming-initialised layers and the decode (dL/L = 5 ln10 dL') turn into
-    pixel errors of a few 1e-3 with a median below 1e-4;
+    (64^3 blobs, 128^2 x 4 spp): per-pixel relative error (|a-b| / max(|b|,
+    1e-3 max|b|)) <= 2e-6 against the oracle's float32 instantiation of the
+    marcher, and <= 1e-4 against FP64 on every pixel but those where the
+    float32 instantiation itself is off by as much (near-empty fringes);
+  * the same with a float32 field: against the float32 instantiation (same
+    interaction points and float32 field queries) with an FP64 field, every
+    pixel within the bound the field's 1e-5 L' tolerance implies;
   * tracking renderer (delta + ratio tracking), field off, and the path
     tracer: float32 arithmetic identical to the oracle's float32
     instantiation, so pixels agree to float rounding of the final sums
     (also with pooled primary grids and thinned shadow walks);
-  * tensor-core fields (bf16 / f16 / fp8) and the full-size large and mid
-    workloads on sampled rows: operand rounding near boundaries, median
-    <= 5e-3, max <= 0.3 per pixel;
+  * tensor-core fields (bf16 / f16 / fp8, unscaled Kaiming weights): the
+    render epilogue's L' of every camera sample within 2e-2 of the
+    precision-emulated oracle (one sample per pixel, so each pixel exposes
+    its sample); the full-size large and mid workloads on sampled rows:
+    every pixel within the bound that per-sample tolerance implies;
   * edge cases: a camera that misses the box, one pixel, one sample.
 """
 import math
@@ -40,21 +41,38 @@ def _rel_err(a, b):
 
 
 def test_march_direct_matches_oracle_full_size(pf_ctx, orc):
+    """Plain-method scene at full size (64^3 blobs, 128^2 x 4 spp, 0.5-voxel
+    steps).  Against the oracle's float32 instantiation of the marcher (the
+    kernel's precision contract) every pixel agrees to 2e-6.  Against FP64,
+    every pixel is within 1e-4 except where float32 rounding of sigma moves an
+    interaction in a near-empty fringe; each such pixel is reproduced by the
+    float32 instantiation itself (it is the arithmetic, not the kernel)."""
     sc = I.scene_small()
     vol = api.Volume.from_inputs(sc.volume)
     img = api.render_neural(pf_ctx, vol, sc.lights, sc.g, sc.camera, sc.spp, 0.5, seed=7)
     pf_ctx.sync()
+    got = img.cpu().numpy()
+    mirror = orc.render_neural(sc.volume, sc.lights, sc.g, sc.camera, sc.spp, 0.5, 7, fp32=True)
+    assert mirror.max() > 0
+    assert _rel_err(got, mirror).max() <= 2e-6, _rel_err(got, mirror).max()
     ref = orc.render_neural(sc.volume, sc.lights, sc.g, sc.camera, sc.spp, 0.5, 7)
-    err = _rel_err(img.cpu().numpy(), ref).max(-1)
-    assert ref.max() > 0
-    # <= 1e-4 per pixel, except where an interaction lands in a near-empty
-    # fringe: there float32 rounding of sigma (~1e-7 relative) moves the
-    # sampled point by ~1e-7 tau / sigma, which the derivation bounds by 3e-4
-    assert (err > 1e-4).mean() <= 5e-4, (err > 1e-4).sum()
-    assert err.max() <= 3e-4, err.max()
+    den = np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max())
+    err = (np.abs(got - ref) / den).max(-1)
+    err_mirror = (np.abs(mirror - ref) / den).max(-1)
+    off = err > 1e-4
+    assert off.sum() <= 8, off.sum()
+    # every pixel off by more than 1e-4 is off by (nearly) as much in the
+    # float32 instantiation
+    assert np.all(err_mirror[off] > 0.5e-4), err_mirror[off]
+    assert np.all(np.abs(err[off] - err_mirror[off]) <= 1e-5), (err[off], err_mirror[off])
 
 
 def test_march_with_f32_field(pf_ctx, orc):
+    """The marcher with a float32 field: against the oracle's float32
+    instantiation (the same interaction points and, formed the same way in
+    float32, the same field queries) with the field evaluated in FP64, every
+    pixel is within the bound the float32 field's L' tolerance (1e-5 against
+    FP64) implies, plus float rounding of the direct part."""
     from oracle import field as F
     sc = I.scene_small(64, 64, 64, 4)
     vol = api.Volume.from_inputs(sc.volume)
@@ -64,10 +82,12 @@ def test_march_with_f32_field(pf_ctx, orc):
     assert np.array_equal(fld.get_weights().cpu().numpy(), w)   # seeded init is bit-identical
     img = api.render_neural(pf_ctx, vol, sc.lights, sc.g, sc.camera, sc.spp, 0.5, seed=5, field=fld)
     pf_ctx.sync()
-    ref = orc.render_neural(sc.volume, sc.lights, sc.g, sc.camera, sc.spp, 0.5, 5, weights=w.astype(np.float64), desc=desc)
-    err = _rel_err(img.cpu().numpy(), ref)
-    assert np.median(err) < 1e-4
-    assert err.max() <= 5e-3, err.max()
+    ref, cs, Li = orc.render_neural(sc.volume, sc.lights, sc.g, sc.camera, sc.spp, 0.5, 5,
+                                    weights=w.astype(np.float64), desc=desc, fp32=True, return_parts=True)
+    assert Li.max() > 0
+    d, bound = _rows_within_li_bound(img.cpu().numpy(), ref, cs, Li, sc.spp,
+                                     li_rel=math.expm1(5.0 * math.log(10.0) * 1e-5))
+    assert np.all(d <= bound), (d / bound).max()
 
 
 @pytest.mark.parametrize("brick,primary,shadow", [(8, 0, 0), (4, 16, 0), (8, 32, 0), (4, 16, 16), (4, 0, 32)])
@@ -147,99 +167,124 @@ def test_rmse_reduction(pf_ctx):
     assert abs(r - want) < 1e-12 * want
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp8"])
-def test_tracking_with_tensor_core_field(pf_ctx, orc, prec):
-    """Tracking renderer with a tensor-core field: the direct part is the
-    oracle's float32 tracking; the field part follows the precision-emulated
-    oracle (L' within 2e-2, i.e. L_i within ~25%; typically ~1e-3)."""
+def _tc_field(pf_ctx, prec, hidden, seed, cal_seed):
+    """A tensor-core field with the oracle's seeded Kaiming weights (unscaled:
+    L' spans about -5..4, so L_i spans 20 decades) and, for fp8, scales
+    calibrated on the same queries on both sides."""
     from oracle import field as F
-    sc = I.scene_judge(32, 40, 30, 4)
-    vol = api.Volume.from_inputs(sc.volume)
-    hidden = 128 if prec == "fp8" else 64
-    fld = api.Field(pf_ctx, 12, hidden, 4, prec, 5.0, seed=31)
-    desc = F.FieldDesc(12, hidden, 4, {"bf16": F.PREC_BF16, "fp8": F.PREC_FP8}[prec], 5.0, 31)
+    pcode = {"bf16": F.PREC_BF16, "f16": F.PREC_F16, "fp8": F.PREC_FP8}[prec]
+    fld = api.Field(pf_ctx, 12, hidden, 4, prec, 5.0, seed=seed)
+    desc = F.FieldDesc(12, hidden, 4, pcode, 5.0, seed)
     w = F.init_weights(desc).astype(np.float64)
-    # shrink the untrained field's output so decoded radiance stays O(direct)
-    w[-3 * hidden:] *= 0.05
-    wt = torch.from_numpy(w.astype(np.float32)).cuda()
-    fld.set_weights(wt)
+    assert np.array_equal(fld.get_weights().cpu().numpy(), w.astype(np.float32))
     scales = None
     if prec == "fp8":
-        cal = np.random.default_rng(2).uniform(0, 1, (4096, 6)).astype(np.float32)
+        cal = np.random.default_rng(cal_seed).uniform(0, 1, (4096, 6)).astype(np.float32)
         fld.calibrate_fp8(torch.from_numpy(cal).cuda())
         scales = F.fp8_calibrate(w, cal.astype(np.float64), desc)
-    g = 0.3
-    img = api.render_neural(pf_ctx, vol, sc.lights, g, sc.camera, sc.spp, 0.0, seed=8, field=fld)
-    pf_ctx.sync()
-    ref, cs, Li = orc.render_neural(sc.volume, sc.lights, g, sc.camera, sc.spp, 0.0, 8, weights=w, desc=desc,
-                                    scales=scales, fp32=True, return_parts=True)
-    assert Li.max() > 0
-    err = _rel_err(img.cpu().numpy(), ref)
-    assert np.median(err) < 5e-3, np.median(err)
-    assert err.max() < 0.3, err.max()
+    return fld, w, desc, scales
 
 
-def test_large_render_sampled_rows(pf_ctx, orc):
-    """Full-size large-render workload (1024^3 f16 turbulence, 8 lights,
-    1920x1080, 16 spp, fp8 4x128 field, tracking), in the launch the
-    benchmark times; sampled rows are recomputed by the oracle."""
+# the field's L' (Eq. 6 encoding) against the precision-emulated oracle
+TC_LP_TOL = 2e-2
+# a pixel's error allowed by that: |dL_i / L_i| <= exp(psi ln10 tol) - 1
+TC_LI_REL = math.expm1(5.0 * math.log(10.0) * TC_LP_TOL)
+
+
+@pytest.mark.parametrize("prec,hidden", [("bf16", 64), ("f16", 128), ("fp8", 128)])
+def test_tracking_with_tensor_core_field(pf_ctx, orc, prec, hidden):
+    """Tracking renderer with a tensor-core field, one sample per pixel so
+    that each pixel is one camera sample: the render epilogue's L' of every
+    valid sample, recovered from the rendered pixel minus the same render
+    without the field, is within 2e-2 of the precision-emulated oracle's L'
+    at the oracle's (float32-identical) interaction; pixels within the
+    bound that L' tolerance implies."""
     from oracle import field as F
+    sc = I.scene_judge(32, 96, 72, 1)
+    vol = api.Volume.from_inputs(sc.volume)
+    fld, w, desc, scales = _tc_field(pf_ctx, prec, hidden, 31, 2)
+    g = 0.3
+    img = api.render_neural(pf_ctx, vol, sc.lights, g, sc.camera, 1, 0.0, seed=8, field=fld)
+    direct = api.render_neural(pf_ctx, vol, sc.lights, g, sc.camera, 1, 0.0, seed=8)
+    pf_ctx.sync()
+    ref, cs, Li = orc.render_neural(sc.volume, sc.lights, g, sc.camera, 1, 0.0, 8, weights=w, desc=desc,
+                                    scales=scales, fp32=True, return_parts=True)
+    vm = cs["valid"][..., 0]
+    assert vm.sum() > 500
+    alb = cs["albedo"][..., 0, :][vm]
+    a_li = (img.cpu().numpy().astype(np.float64) - direct.cpu().numpy().astype(np.float64))[vm]
+    ali_ref = alb * Li[..., 0, :][vm]
+    q = orc.query_f32(cs["x"][vm], cs["wo"][vm], g)     # the queries as the renderer forms them
+    lp_ref, _ = F.forward(w, q, desc, scales)
+    # L' is recoverable where albedo * L_i is not lost in the float sum with
+    # albedo * L_d (float rounding 6e-8 of the pixel moves L' by < 5e-5 here)
+    pix = np.abs(ref[vm])
+    ok = (alb > 0) & (ali_ref > 1e-4 * pix)
+    assert ok.mean() > 0.5, ok.mean()
+    lp = -np.log10(a_li[ok] / alb[ok]) / desc.psi
+    err = np.abs(lp - lp_ref[ok])
+    assert err.max() <= TC_LP_TOL, (err.max(), np.median(err))
+    # every pixel: within what the L' tolerance allows, plus float rounding
+    d, bound = _rows_within_li_bound(img.cpu().numpy(), ref, cs, Li, 1)
+    assert np.all(d <= bound), (d / bound).max()
+
+
+def _rows_within_li_bound(got, ref_img, cs, Li, spp, li_rel=TC_LI_REL):
+    """Pixels of sampled rows: |got - ref| within the bound a per-sample L'
+    tolerance implies (sum of albedo L_i over the pixel's samples times
+    li_rel = exp(psi ln10 tol) - 1), plus float rounding of the direct part."""
+    ali = (cs["albedo"] * Li).sum(axis=2) / spp
+    direct = (cs["albedo"] * cs["Ld"]).sum(axis=2) / spp
+    d = np.abs(got.astype(np.float64) - ref_img)
+    bound = li_rel * ali + 2e-6 * np.maximum(np.abs(ref_img), 1e-3 * direct.max()) + 1e-30
+    return d, bound
+
+
+@pytest.mark.parametrize("prec", ["f16", "fp8"])
+def test_large_render_sampled_rows(pf_ctx, orc, prec):
+    """Full-size large-render workload (1024^3 f16 turbulence, 8 lights,
+    1920x1080, 16 spp, 4x128 field in f16 or fp8, tracking, the benchmark's
+    majorant bricks), in the launch the benchmark times; sampled rows are
+    recomputed by the oracle and every pixel is within the bound the
+    per-sample L' tolerance implies."""
     vol_t, tf, lights, cams = I.large_scene_parts(1024, device="cuda")
     tf_t = torch.from_numpy(tf).cuda()
-    vol = api.Volume(vol_t.contiguous(), 20.0, 0.9, tf_t, brick=32, brick_primary=64)   # the benchmark's bricks
+    vol = api.Volume(vol_t.contiguous(), 20.0, 0.9, tf_t, brick=32, brick_primary=128)
     vol.attach_brick_majorants(pf_ctx)
-    fld = api.Field(pf_ctx, 12, 128, 4, "fp8", 5.0, seed=5)
-    desc = F.FieldDesc(12, 128, 4, F.PREC_FP8, 5.0, 5)
-    w = F.init_weights(desc).astype(np.float64)
-    w[-3 * 128:] *= 0.05
-    fld.set_weights(torch.from_numpy(w.astype(np.float32)).cuda())
-    cal = np.random.default_rng(3).uniform(0, 1, (4096, 6)).astype(np.float32)
-    fld.calibrate_fp8(torch.from_numpy(cal).cuda())
-    scales = F.fp8_calibrate(w, cal.astype(np.float64), desc)
+    vol.attach_tiled(pf_ctx)
+    fld, w, desc, scales = _tc_field(pf_ctx, prec, 128, 5, 3)
     cam, g = cams[7], I.frame_g(11, 7)
     img = api.render_neural(pf_ctx, vol, lights, g, cam, 16, 0.0, seed=99, field=fld)
     pf_ctx.sync()
-    vh = I.Volume(vol_t.cpu().numpy(), 20.0, 0.9, tf, brick=32, brick_primary=64)
+    vh = I.Volume(vol_t.cpu().numpy(), 20.0, 0.9, tf, brick=32, brick_primary=128)
     for y0 in (500, 700):
-        ref = orc.render_neural(vh, lights, g, cam, 16, 0.0, 99, weights=w, desc=desc, scales=scales, fp32=True,
-                                rows=(y0, y0 + 1))
-        got = img[y0:y0 + 1].cpu().numpy()
-        assert ref.max() > 0
-        err = _rel_err(got, ref)
-        assert np.median(err) < 5e-3 and err.max() < 0.3, (y0, np.median(err), err.max())
+        ref, cs, Li = orc.render_neural(vh, lights, g, cam, 16, 0.0, 99, weights=w, desc=desc, scales=scales,
+                                        fp32=True, rows=(y0, y0 + 1), return_parts=True)
+        assert ref.max() > 0 and Li.max() > 0
+        d, bound = _rows_within_li_bound(img[y0:y0 + 1].cpu().numpy(), ref, cs, Li, 16)
+        assert np.all(d <= bound), (y0, (d / bound).max())
 
 
 @pytest.mark.parametrize("prec", ["f16", "fp8"])
 def test_mid_render_sampled_rows(pf_ctx, orc, prec):
     """Full-size mid-render workload (512^3 u8 blurred noise, 256-node RGBA
     table, 4 point lights, 1024^2 x 4 spp, 4x128 field in f16 or fp8,
-    tracking); sampled rows recomputed by the oracle."""
-    from oracle import field as F
+    tracking); sampled rows recomputed by the oracle, every pixel within the
+    bound the per-sample L' tolerance implies."""
     sc = I.scene_mid(device="cuda")
     data = np.ascontiguousarray(sc.volume.data)
     vol = api.Volume(torch.from_numpy(data).cuda(), sc.volume.sigma_scale, sc.volume.albedo,
                      torch.from_numpy(sc.volume.tf).cuda())
-    pcode = {"f16": F.PREC_F16, "fp8": F.PREC_FP8}[prec]
-    fld = api.Field(pf_ctx, 12, 128, 4, prec, 5.0, seed=8)
-    desc = F.FieldDesc(12, 128, 4, pcode, 5.0, 8)
-    w = F.init_weights(desc).astype(np.float64)
-    w[-3 * 128:] *= 0.05
-    fld.set_weights(torch.from_numpy(w.astype(np.float32)).cuda())
-    scales = None
-    if prec == "fp8":
-        cal = np.random.default_rng(4).uniform(0, 1, (4096, 6)).astype(np.float32)
-        fld.calibrate_fp8(torch.from_numpy(cal).cuda())
-        scales = F.fp8_calibrate(w, cal.astype(np.float64), desc)
+    fld, w, desc, scales = _tc_field(pf_ctx, prec, 128, 8, 4)
     img = api.render_neural(pf_ctx, vol, sc.lights, sc.g, sc.camera, sc.spp, 0.0, seed=41, field=fld)
     pf_ctx.sync()
     vh = I.Volume(data, sc.volume.sigma_scale, sc.volume.albedo, sc.volume.tf)
     for y0 in (300, 512, 811):
-        ref = orc.render_neural(vh, sc.lights, sc.g, sc.camera, sc.spp, 0.0, 41, weights=w, desc=desc,
-                                scales=scales, fp32=True, rows=(y0, y0 + 1))
-        got = img[y0:y0 + 1].cpu().numpy()
-        assert ref.max() > 0
-        err = _rel_err(got, ref)
-        assert np.median(err) < 5e-3 and err.max() < 0.3, (y0, np.median(err), err.max())
+        ref, cs, Li = orc.render_neural(vh, sc.lights, sc.g, sc.camera, sc.spp, 0.0, 41, weights=w, desc=desc,
+                                        scales=scales, fp32=True, rows=(y0, y0 + 1), return_parts=True)
+        assert ref.max() > 0 and Li.max() > 0
+        d, bound = _rows_within_li_bound(img[y0:y0 + 1].cpu().numpy(), ref, cs, Li, sc.spp)
+        assert np.all(d <= bound), (y0, (d / bound).max())
 
 
 def test_tiled_volume_with_ragged_tiles(pf_ctx, orc):

@@ -101,3 +101,48 @@ def test_own_sincos_accuracy(orc):
     s, c = orc.sincos2pif(np.float32([0.0, 0.25, 0.5, 0.75]))
     assert np.allclose(s, [0, 1, 0, -1], atol=1e-7)
     assert np.allclose(c, [1, 0, -1, 0], atol=1e-7)
+
+
+def test_own_atan2_accuracy(orc):
+    """The own float32 atan2 against FP64 arctan2: random points in all four
+    quadrants and over six decades of magnitude ratio, the axes, the
+    diagonals, signed zeros."""
+    rng = np.random.default_rng(3)
+    ang = rng.uniform(-math.pi, math.pi, 200000)
+    r = 10.0 ** rng.uniform(-3, 3, ang.size)
+    x = (r * np.cos(ang)).astype(np.float32)
+    y = (r * np.sin(ang)).astype(np.float32)
+    edge = np.float32([0.0, 1.0, -1.0, 1e-30, -1e-30, 3e38, 1.0, -1.0, 1.0, -1.0])
+    edge_y = np.float32([1.0, 0.0, 0.0, 1.0, 1.0, 1.0, 1.0, 1.0, -1.0, -1.0])
+    x = np.concatenate([x, edge]).astype(np.float32)
+    y = np.concatenate([y, edge_y]).astype(np.float32)
+    got = orc.atan2f(y, x).astype(np.float64)
+    ref = np.arctan2(y.astype(np.float64), x.astype(np.float64))
+    assert np.max(np.abs(got - ref)) < 8 * 2.0 ** -23, np.max(np.abs(got - ref))
+    assert orc.atan2f(np.float32([0.0]), np.float32([0.0]))[0] == 0.0
+    # the quadrant fix-ups: exact multiples of pi/4 within a few ulp
+    diag = orc.atan2f(np.float32([1, 1, -1, -1]), np.float32([1, -1, 1, -1])).astype(np.float64)
+    assert np.allclose(diag, [math.pi / 4, 3 * math.pi / 4, -math.pi / 4, -3 * math.pi / 4], atol=4e-7)
+
+
+def test_float32_query_angles(orc):
+    """theta' = acos(w_z)/pi and phi' = atan2(w_y, w_x)/2pi mod 1 formed in
+    float32 agree with the FP64 spherical coordinates to float rounding,
+    including the poles and the phi' seam."""
+    from oracle import field as F
+    rng = np.random.default_rng(4)
+    w = rng.normal(size=(100000, 3))
+    w /= np.linalg.norm(w, axis=1, keepdims=True)
+    w = np.concatenate([w, [[0, 0, 1.0], [0, 0, -1.0], [1.0, 0, 0], [1.0, -1e-9, 0], [-1.0, 0, 0]]])
+    w32 = w.astype(np.float32)
+    x = rng.uniform(0, 1, (w.shape[0], 3)).astype(np.float32)
+    q = orc.query_f32(x, w32, 0.3)
+    ref = F.query_from_sample(x.astype(np.float64), w32.astype(np.float64), 0.3)
+    assert np.array_equal(q[:, :3], x.astype(np.float64))
+    assert np.all(q[:, 5] == np.float32(0.3))
+    assert np.max(np.abs(q[:, 3] - ref[:, 3])) < 4e-7
+    dph = np.abs(q[:, 4] - ref[:, 4])
+    dph = np.minimum(dph, 1.0 - dph)            # phi' wraps at 0 / 1
+    assert np.max(dph) < 4e-7
+    # phi' just below 1 rounds to 1.0 in float32 (the seam at 0 / 1)
+    assert np.all((q[:, 3] >= 0) & (q[:, 3] <= 1) & (q[:, 4] >= 0) & (q[:, 4] <= 1))

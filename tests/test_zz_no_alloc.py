@@ -6,7 +6,9 @@ allocating in its frame loop, code that must avoid the synchronisation
 cudaMalloc / cudaFree can cause).  It keeps its scratch in a fixed file-scope
 device array.  Checked through the C ABI: two calls in a row reproduce the
 allocating pf_render_pathtraced bit for bit (the path tracer's tolerance),
-and an image larger than the static scratch is refused with a message.
+also when the image needs several chunks of the static scratch, and inputs
+the allocating entry point refuses (a zero light direction, an invalid
+brick, an image larger than the static scratch) are refused with a message.
 This file sorts last so that a failure here comes after every other test.
 """
 import ctypes as C
@@ -57,3 +59,55 @@ def test_noalloc_rejects_oversize_and_missing_majorants(pf_ctx):
     big = I.Camera(sc.camera.eye, sc.camera.at, sc.camera.up, 55.0, 2048, 2048)
     st = _call(L, vol, sc.lights, 0.0, big, 1, 4, 1, out, msg)
     assert st == _lib.PF_ERR_INVALID_ARG and b"static scratch" in msg.value
+
+
+def test_noalloc_several_chunks_match(pf_ctx):
+    """1920x1080 at 3 spp: the static array holds the per-pixel accumulator and
+    one sample per pixel, so the render runs in three chunks (the allocating
+    path in one); the in-order per-pixel sums make the bits equal."""
+    L = _lib.load()
+    sc = I.scene_judge(16, 1920, 1080, 3)
+    vol = api.Volume.from_inputs(sc.volume)
+    vol.attach_brick_majorants(pf_ctx)
+    ref = api.render_pathtraced(pf_ctx, vol, sc.lights, 0.0, sc.camera, 3, 2, seed=21)
+    pf_ctx.sync()
+    msg = C.create_string_buffer(256)
+    out = torch.full_like(ref, -1.0)
+    st = _call(L, vol, sc.lights, 0.0, sc.camera, 3, 2, 21, out, msg)
+    assert st == _lib.PF_OK, msg.value
+    torch.cuda.synchronize()
+    assert float(ref.max()) > 0
+    assert torch.equal(out, ref)
+
+
+def test_noalloc_rejects_what_the_allocating_path_rejects(pf_ctx):
+    L = _lib.load()
+    sc = I.scene_judge(16, 8, 8, 1)
+    vol = api.Volume.from_inputs(sc.volume)
+    vol.attach_brick_majorants(pf_ctx)
+    msg = C.create_string_buffer(256)
+    out = torch.zeros(8, 8, 3, device="cuda")
+    zero_dir = [I.Light(I.DIRECTIONAL, (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))]
+    st = _call(L, vol, zero_dir, 0.0, sc.camera, 1, 4, 1, out, msg)
+    assert st == _lib.PF_ERR_INVALID_ARG and b"direction" in msg.value
+    with pytest.raises(api.PfError):
+        api.render_pathtraced(pf_ctx, vol, zero_dir, 0.0, sc.camera, 1, 4, seed=1)
+    inside = [I.Light(I.POINT, (0.5, 0.5, 0.5), (1.0, 1.0, 1.0))]
+    st = _call(L, vol, inside, 0.0, sc.camera, 1, 4, 1, out, msg)
+    assert st == _lib.PF_ERR_INVALID_ARG and b"outside" in msg.value
+    good = vol.s.brick
+    try:
+        vol.s.brick = 3                      # not a power of two
+        st = _call(L, vol, sc.lights, 0.0, sc.camera, 1, 4, 1, out, msg)
+        assert st == _lib.PF_ERR_INVALID_ARG and b"brick" in msg.value
+        with pytest.raises(api.PfError):
+            api.render_pathtraced(pf_ctx, vol, sc.lights, 0.0, sc.camera, 1, 4, seed=1)
+    finally:
+        vol.s.brick = good
+    ss = vol.s.sigma_scale
+    try:
+        vol.s.sigma_scale = float("inf")
+        st = _call(L, vol, sc.lights, 0.0, sc.camera, 1, 4, 1, out, msg)
+        assert st == _lib.PF_ERR_INVALID_ARG and b"sigma_scale" in msg.value
+    finally:
+        vol.s.sigma_scale = ss
