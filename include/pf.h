@@ -318,6 +318,16 @@ pf_status pf_field_forward(pf_ctx* ctx, const pf_field* field, const float* q_de
  * and f16 fields). */
 pf_status pf_field_backward(pf_ctx* ctx, const pf_field* field, const float* q_dev, const float* dy_dev,
                             int64_t B, float* dw_dev);
+/* The training loss (Sec. 3.5.1, relative MSE (yhat - y)^2 / (y^2 + 0.01)
+ * on L', averaged over the batch and the three outputs) of B queries q_dev
+ * [B*6] against targets_dev [B*3] (L'), and its gradient dw_dev [n_params]
+ * -- the step pf_train_field takes before Adam.  The backward pass runs with
+ * loss scaling: on dy = 2 (yhat - y) / (y^2 + 0.01), 3B times the gradient
+ * of the mean, so that the gradients rounded to a 16-bit field precision
+ * stay in its normal range; the float32 sums are multiplied by 1/(3B).
+ * loss_host (nullable): the loss; synchronises when given. */
+pf_status pf_field_loss_gradient(pf_ctx* ctx, const pf_field* field, const float* q_dev, const float* targets_dev,
+                                 int64_t B, float* dw_dev, float* loss_host);
 /* One Adam step (Sec. 3.5.1) on the field's master weights with gradient
  * grad_dev [n_params]; t = the field's step counter + 1. */
 pf_status pf_field_adam(pf_ctx* ctx, pf_field* field, const float* grad_dev, float lr, float beta1, float beta2,

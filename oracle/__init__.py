@@ -42,6 +42,7 @@ def _declare(L):
     L.orc_lnf.argtypes = [P, P, i64]
     L.orc_sincos2pif.argtypes = [P, P, P, i64]
     L.orc_atan2f.argtypes = [P, P, P, i64]
+    L.orc_encode_f32.argtypes = [P, i64, i32, P]
     L.orc_query_f32.argtypes = [P, P, C.c_float, i64, P]
     L.orc_hg_eval.argtypes = [f64, f64]
     L.orc_hg_eval.restype = f64
@@ -162,6 +163,16 @@ def atan2f(y: np.ndarray, x: np.ndarray) -> np.ndarray:
     out = np.zeros_like(y)
     lib().orc_atan2f(_p(y), _p(x), _p(out), y.size)
     return out
+
+
+def encode_f32(q: np.ndarray, n_freq: int) -> np.ndarray:
+    """The frequency encoding in the float32 steps of the tensor-core fields
+    (own turn-based sine / cosine at k = 0, 4, 8, ..., double-angle formulas
+    in between); (B, 12 n_freq) as float64 (exact)."""
+    q = np.ascontiguousarray(np.asarray(q).reshape(-1, 6), np.float32)
+    out = np.zeros((q.shape[0], 12 * n_freq), np.float32)
+    lib().orc_encode_f32(_p(q), q.shape[0], int(n_freq), _p(out))
+    return out.astype(np.float64)
 
 
 def query_f32(x: np.ndarray, wo: np.ndarray, g: float) -> np.ndarray:

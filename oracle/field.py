@@ -18,8 +18,11 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
   * Optimiser: Adam (Sec. 3.5.1), beta1 0.9, beta2 0.99, exponential decay of
     the learning rate by 0.92 every 25 steps from 70% of the run.
 
-Precision emulation (how the tensor-core field is specified): the input and
-the weights of every hidden layer are rounded to the field precision
+Precision emulation (how the tensor-core field is specified): the encoding
+is taken in the float32 steps of the kernels (encode_f32: own turn-based
+sine / cosine at every fourth frequency, double-angle formulas in between,
+within a few 1e-6 of the exact features); the input and the weights of every
+hidden layer are rounded to the field precision
 (bf16 / fp16 round-to-nearest-even; fp8 e4m3 codes of x / s with per-layer
 power-of-two scales s = 2^ceil(log2(amax/448)), amax taken over the weights
 and over a calibration batch's layer inputs, saturating at +-448); products
@@ -319,8 +322,14 @@ def forward(weights: np.ndarray, q: np.ndarray, desc: FieldDesc, scales=None):
     corners = None
     if desc.encoding == ENC_HASHGRID:
         h, corners = hash_encode(weights, q, desc)
-    else:
+    elif desc.prec == PREC_F32:
         h = encode(q, desc.in_freqs)
+    else:
+        # the tensor-core fields compute the features in float32 before
+        # rounding them to the operand type: the rounding is taken on the
+        # same float32 values (within a few 1e-6 of sin / cos, see encode_f32)
+        from . import encode_f32
+        h = encode_f32(q, desc.in_freqs)
     ins, zs = [], []
     L = len(ws)
     for l, W in enumerate(ws):
@@ -380,6 +389,21 @@ def rel_mse(yhat: np.ndarray, y: np.ndarray, eps: float = 0.01):
     den = y * y + eps
     n = yhat.size
     return float(np.sum(diff * diff / den) / n), 2.0 * diff / den / n
+
+
+def train_gradient(weights: np.ndarray, q: np.ndarray, y: np.ndarray, desc: FieldDesc, scales=None):
+    """The training step's loss and gradient (Sec. 3.5.1): the mean relative
+    MSE of the forward pass against targets y, and its gradient with loss
+    scaling -- the backward pass runs on n times the gradient of the mean
+    (n = the number of outputs), 2 (yhat - y) / (y^2 + eps) per output, so
+    that its gradients rounded to a 16-bit field precision keep their
+    significant bits, and the result is divided by n.  In FP64 without
+    rounding (PREC_F32) the scaling is exact: the result is the plain
+    gradient of the mean."""
+    yh, cache = forward(weights, q, desc, scales)
+    loss, dy = rel_mse(yh, y)
+    n = yh.size
+    return loss, backward(weights, cache, dy * n, desc) / n
 
 
 def lr_at(step: int, steps: int, lr: float, decay: float, start_frac: float, every: int) -> float:

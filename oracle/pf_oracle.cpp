@@ -1036,6 +1036,31 @@ void orc_sincos2pif(const float* u, float* s, float* c, int64_t n) {
     for (int64_t i = 0; i < n; ++i) own_sincos2pif(u[i], s + i, c + i);
 }
 
+// Frequency encoding (Sec. 3.4) of n queries of 6 inputs, F frequencies,
+// features [input][k][sin, cos], in the float32 steps of the tensor-core
+// fields: sin / cos (2^k pi v) at k = 0, 4, 8, ... from the own turn-based
+// sine / cosine of frac(2^(k-1) v); in between by the double-angle formulas
+// sin 2a = 2 sin a cos a, cos 2a = 1 - 2 sin^2 a.
+void orc_encode_f32(const float* q, int64_t n, int F, float* out) {
+    for (int64_t i = 0; i < n; ++i)
+        for (int d = 0; d < 6; ++d) {
+            const float v = q[6 * i + d];
+            float s = 0.0f, c = 1.0f;
+            for (int k = 0; k < F; ++k) {
+                if ((k & 3) == 0) {
+                    const float t = v * std::ldexp(1.0f, k - 1);
+                    own_sincos2pif(t - std::floor(t), &s, &c);
+                } else {
+                    const float s2 = (s * c) * 2.0f;
+                    c = 1.0f - 2.0f * (s * s);
+                    s = s2;
+                }
+                out[(i * 6 + d) * 2 * F + 2 * k] = s;
+                out[(i * 6 + d) * 2 * F + 2 * k + 1] = c;
+            }
+        }
+}
+
 void orc_atan2f(const float* y, const float* x, float* out, int64_t n) {
     for (int64_t i = 0; i < n; ++i) out[i] = own_atan2f(y[i], x[i]);
 }

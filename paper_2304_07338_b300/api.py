@@ -287,6 +287,17 @@ class Field:
         self.ctx.check(self.ctx.lib.pf_field_backward(self.ctx.h, self.h, _ptr(q), _ptr(dy), B, _ptr(dw)))
         return dw
 
+    def loss_gradient(self, q: torch.Tensor, targets: torch.Tensor):
+        """(loss, dw): the training loss on targets (L') and its gradient."""
+        _need(q, torch.float32, name="q")
+        B = q.numel() // 6
+        _need(targets, torch.float32, 3 * B, "targets")
+        dw = torch.empty(self.n_params, dtype=torch.float32, device=q.device)
+        loss = C.c_float()
+        self.ctx.check(self.ctx.lib.pf_field_loss_gradient(self.ctx.h, self.h, _ptr(q), _ptr(targets), B, _ptr(dw),
+                                                           C.byref(loss)))
+        return loss.value, dw
+
     def adam(self, grad: torch.Tensor, lr: float, beta1=0.9, beta2=0.99, eps=1e-8):
         _need(grad, torch.float32, self.n_params, "grad")
         self.ctx.check(self.ctx.lib.pf_field_adam(self.ctx.h, self.h, _ptr(grad), lr, beta1, beta2, eps))

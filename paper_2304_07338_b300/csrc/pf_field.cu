@@ -403,8 +403,12 @@ __global__ void __launch_bounds__(kSimtThreads) k_simt_forward(FieldView F, cons
 // Backward: each thread recomputes its forward, keeps every layer's input,
 // back-propagates dy and accumulates its dW contribution into shared memory
 // partials that are added to global dW once per block.
-// loss mode (targets != nullptr): dy = 2 (yhat - y) / (y^2 + 0.01) * inv_n and
-// the block's loss sum goes to *loss.
+// loss mode (targets != nullptr): the mean relative MSE's gradient with loss
+// scaling -- the pass runs on dy = 2 (yhat - y) / (y^2 + 0.01), 3B times the
+// gradient of the mean, so that its rounded intermediate gradients stay in
+// the normal range of a 16-bit field precision, and the block's float32 dW
+// contributions are multiplied by inv_n = 1/(3B); the block's loss sum goes
+// to *loss.
 __global__ void __launch_bounds__(kBwdThreads) k_simt_backward(FieldView F, const float* __restrict__ q,
                                                             const float* __restrict__ dy_in,
                                                             const float* __restrict__ targets, float inv_n,
@@ -436,12 +440,13 @@ __global__ void __launch_bounds__(kBwdThreads) k_simt_backward(FieldView F, cons
         float den = t * t + 0.01f;
         float diff = y[c] - t;
         lsum += diff * diff / den;
-        g[c] = 2.f * diff / den * inv_n;
+        g[c] = 2.f * diff / den;
       }
     } else {
       for (int c = 0; c < 3; ++c) g[c] = dy_in[3 * b + c];
     }
   }
+  const float gscale = targets ? inv_n : 1.f;     // undoes the loss scaling in float32
   if (loss) {
     for (int off = 16; off > 0; off >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, off);
     if (tid == 0) atomicAdd(loss, lsum * inv_n);
@@ -458,7 +463,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_simt_backward(FieldView F, cons
       int n = e / K, k = e % K;
       float s = 0.f;
       for (int t = 0; t < T; ++t) s = fmaf(dcur[n * T + t], xin[k * T + t], s);
-      atomicAdd(&dw[F.off[l] + e], s);
+      atomicAdd(&dw[F.off[l] + e], s * gscale);
     }
     if (l == 0) {
       if (F.enc == PF_ENC_HASHGRID && act) {
@@ -474,7 +479,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_simt_backward(FieldView F, cons
               float a = 0.f;
               if (f < F.hf)
                 for (int n = 0; n < N; ++n) a = fmaf(dcur[n * T + tid], __ldg(W0 + (size_t)n * K + col + f), a);
-              dx[f] = a;
+              dx[f] = a * gscale;
             }
             if (gi == 0) hash_scatter<3>(F, 0, lv, qq, dx, dw);
             else hash_scatter<2>(F, 1, lv, qq + 3, dx, dw);
@@ -658,7 +663,7 @@ __global__ void k_hash_features(FieldView F, const float* __restrict__ q, int64_
 // Spreads the features' gradient dx [B][2 L F] over the level tables' corners
 // (one thread per (query, grid, level)).
 __global__ void k_hash_scatter(FieldView F, const float* __restrict__ q, const float* __restrict__ dx, int64_t B,
-                               float* __restrict__ dw) {
+                               float scale, float* __restrict__ dw) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int per = 2 * F.hl;
   if (t >= B * per) return;
@@ -669,7 +674,7 @@ __global__ void k_hash_scatter(FieldView F, const float* __restrict__ q, const f
   const float* src = dx + (size_t)b * (2 * F.hl * F.hf) + (size_t)j * F.hf;
   float d[8];
 #pragma unroll
-  for (int f = 0; f < 8; ++f) d[f] = f < F.hf ? src[f] : 0.f;
+  for (int f = 0; f < 8; ++f) d[f] = f < F.hf ? src[f] * scale : 0.f;
   if (gi == 0) hash_scatter<3>(F, 0, l, v, d, dw);
   else hash_scatter<2>(F, 1, l, v, d, dw);
 }
@@ -715,7 +720,8 @@ pf_status pf_field_backward_impl(pf_ctx* ctx, const pf_field* f, const float* q,
     const int64_t n_mlp = f->layer_off[f->n_layers];
     PF_CUDA(ctx, cudaMemsetAsync(dw + n_mlp, 0, (size_t)(f->n_params - n_mlp) * sizeof(float), ctx->stream));
     PF_TRY(pf_tc_backward(ctx, f, q, dy, targets, B, dw, loss, x, dx));
-    k_hash_scatter<<<grid, 256, 0, ctx->stream>>>(F, q, dx, B, dw);
+    // loss mode: the features' gradient is loss-scaled like dW (see below)
+    k_hash_scatter<<<grid, 256, 0, ctx->stream>>>(F, q, dx, B, targets ? 1.0f / (float)(3 * B) : 1.0f, dw);
     PF_CUDA(ctx, cudaGetLastError());
     return PF_OK;
   }
@@ -731,6 +737,23 @@ extern "C" pf_status pf_field_backward(pf_ctx* ctx, const pf_field* f, const flo
   if (f->ctx != ctx) return pf_fail(ctx, PF_ERR_INVALID_ARG, "field belongs to another context");
   DeviceGuard dg(ctx->device);
   return pf_field_backward_impl(ctx, f, q, dy, nullptr, B, dw, nullptr);
+}
+
+extern "C" pf_status pf_field_loss_gradient(pf_ctx* ctx, const pf_field* f, const float* q, const float* targets,
+                                            int64_t B, float* dw, float* loss_host) {
+  if (!ctx || !f || !dw || B <= 0 || !q || !targets)
+    return pf_fail(ctx, PF_ERR_INVALID_ARG, "bad field loss-gradient arguments");
+  if (f->ctx != ctx) return pf_fail(ctx, PF_ERR_INVALID_ARG, "field belongs to another context");
+  DeviceGuard dg(ctx->device);
+  float* loss;
+  PF_TRY(pf_scratch(ctx, WS_LOSS, sizeof(float), (void**)&loss));
+  PF_CUDA(ctx, cudaMemsetAsync(loss, 0, sizeof(float), ctx->stream));
+  PF_TRY(pf_field_backward_impl(ctx, f, q, nullptr, targets, B, dw, loss));
+  if (loss_host) {
+    PF_CUDA(ctx, cudaMemcpyAsync(loss_host, loss, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    PF_TRY(pf_check_error_word(ctx));
+  }
+  return PF_OK;
 }
 
 // ------------------------------------------------------------------ Adam

@@ -104,9 +104,9 @@ __device__ __forceinline__ void store16(uint8_t* tile, uint32_t kp, int r, int c
 
 // Frequency encoding of one query (6 inputs x F frequencies, features ordered
 // [input][k][sin, cos], each times s) into row r of an A tile with K extent
-// kp, zero-padded to kp; features sin/cos(2^k pi v), the argument scaled
-// exactly by ldexpf.  F = 12 (the usual width) is unrolled so that the
-// 16-feature staging buffer stays in registers.
+// kp, zero-padded to kp; features sin/cos(2^k pi v) by pff::freq_next.
+// F = 12 (the usual width) is unrolled so that the 16-feature staging buffer
+// stays in registers.
 template <int PREC>
 __device__ __forceinline__ void encode_query(uint8_t* tile, uint32_t kp, int r, const float qv[6], int F, float s) {
   if (F == 12) {
@@ -114,9 +114,10 @@ __device__ __forceinline__ void encode_query(uint8_t* tile, uint32_t kp, int r, 
 #pragma unroll
     for (int d = 0; d < 6; ++d) {
 #pragma unroll
+      float sn = 0.f, cs = 1.f;
+#pragma unroll
       for (int k = 0; k < 12; ++k) {
-        float sn, cs;
-        sincospif(ldexpf(qv[d], k), &sn, &cs);
+        pff::freq_next(qv[d], k, sn, cs);
         const int f = 24 * d + 2 * k;       // feature index; 16 features per store
         buf[f % 16] = sn * s;
         buf[(f + 1) % 16] = cs * s;
@@ -134,9 +135,9 @@ __device__ __forceinline__ void encode_query(uint8_t* tile, uint32_t kp, int r, 
   float buf[16];
   int nb = 0, col = 0;
   for (int d = 0; d < 6; ++d) {
+    float sn = 0.f, cs = 1.f;
     for (int k = 0; k < F; ++k) {
-      float sn, cs;
-      sincospif(ldexpf(qv[d], k), &sn, &cs);
+      pff::freq_next(qv[d], k, sn, cs);
       buf[nb++] = sn * s;
       buf[nb++] = cs * s;
       if (nb == 16) { store16<PREC>(tile, kp, r, col, buf); col += 16; nb = 0; }
@@ -294,7 +295,9 @@ __global__ void __launch_bounds__(kFwdMaxThreads, 1) k_tc_forward(TcArgs A, cons
 //              A_l x W_l^T -> TMEM, ReLU, operand rounding -> A_{l+1}
 //              (every layer's input tile stays in shared memory);
 //   output   : y = W_out h_L in float32 from registers; relative-MSE gradient
-//              dy = 2 (y - t) / (t^2 + 0.01) / (3B) (or a given dy); loss;
+//              with loss scaling, dy = 2 (y - t) / (t^2 + 0.01) (3B times the
+//              gradient of the mean; 1/(3B) is applied to the float32 dW sums
+//              by k_reduce_partials), or a given dy; loss;
 //              dW_out by one owner thread per weight over the tile's rows
 //              staged in shared memory; dZ_{L-1} = (W_out^T dy) * [h_L > 0];
 //   backward : for l = L-1..0, tcgen05.mma dW_l += dZ_l^T x A_l (both operands
@@ -454,10 +457,10 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_tc_train(TrArgs T, const f
 #pragma unroll
         for (int dd = 0; dd < 3; ++dd) {
           const float v = valid ? __ldg(q + 6 * row + 3 * hf + dd) : 0.f;
+          float sn = 0.f, cs = 1.f;
 #pragma unroll
           for (int k = 0; k < 12; ++k) {
-            float sn, cs;
-            sincospif(ldexpf(v, k), &sn, &cs);
+            pff::freq_next(v, k, sn, cs);
             const int lf = 24 * dd + 2 * k;
             buf[lf % 8] = sn;
             buf[(lf + 1) % 8] = cs;
@@ -532,7 +535,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_tc_train(TrArgs T, const f
               const float den = t * t + 0.01f;
               const float diff = y[c] - t;
               lsum += diff * diff / den;
-              g = 2.f * diff / den * inv_n;
+              g = 2.f * diff / den;             // loss-scaled by 3B (see pf_tc_backward)
             } else {
               g = dy_in[3 * row + c];
             }
@@ -712,10 +715,11 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_tc_train(TrArgs T, const f
   if (warp == 0) tmem_dealloc(tmem, kTrainCols);
 }
 
-// dW = sum over CTAs of the partial rows: four running sums over the CTAs
-// p = 0, 4, 8, ... / 1, 5, 9, ... / ..., each in CTA order, then
+// dW = scale * sum over CTAs of the partial rows: four running sums over the
+// CTAs p = 0, 4, 8, ... / 1, 5, 9, ... / ..., each in CTA order, then
 // (s0 + s1) + (s2 + s3) -- a fixed order, with four independent load chains.
-__global__ void k_reduce_partials(const float* __restrict__ partial, int n_parts, int64_t n, float* __restrict__ dw) {
+__global__ void k_reduce_partials(const float* __restrict__ partial, int n_parts, int64_t n, float scale,
+                                  float* __restrict__ dw) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
@@ -729,7 +733,7 @@ __global__ void k_reduce_partials(const float* __restrict__ partial, int n_parts
   if (p < n_parts) s0 += partial[(size_t)p * n + i];
   if (p + 1 < n_parts) s1 += partial[(size_t)(p + 1) * n + i];
   if (p + 2 < n_parts) s2 += partial[(size_t)(p + 2) * n + i];
-  dw[i] = (s0 + s1) + (s2 + s3);
+  dw[i] = ((s0 + s1) + (s2 + s3)) * scale;
 }
 
 // ---------------------------------------------------------------- training step, width 128
@@ -873,10 +877,10 @@ __global__ void __launch_bounds__(kT128Threads, 1) k_tc_train128(T128Args T, con
         const int64_t row = row0 + qq;
         const float v = row < B ? __ldg(q + 6 * row + d) : 0.f;
         float buf[8];
+        float sn = 0.f, cs = 1.f;
 #pragma unroll
         for (int k = 0; k < F; ++k) {
-          float sn, cs;
-          sincospif(ldexpf(v, k), &sn, &cs);
+          pff::freq_next(v, k, sn, cs);
           buf[(2 * k) & 7] = sn;
           buf[(2 * k + 1) & 7] = cs;
           if (((2 * k + 2) & 7) == 0) {
@@ -957,7 +961,7 @@ __global__ void __launch_bounds__(kT128Threads, 1) k_tc_train128(T128Args T, con
             const float den = t * t + 0.01f;
             const float diff = y - t;
             lsum += diff * diff / den;
-            g = 2.f * diff / den * inv_n;
+            g = 2.f * diff / den;             // loss-scaled by 3B (see pf_tc_backward)
           } else {
             g = dy_in[3 * row + c];
           }
@@ -1322,7 +1326,8 @@ pf_status pf_tc_backward(pf_ctx* ctx, const pf_field* f, const float* q, const f
     kern<<<grid, kT128Threads, T2.smem_bytes, ctx->stream>>>(T2, q, targets, dy, B, inv_n, partial, loss,
                                                              ctx->err_dev);
     PF_CUDA(ctx, cudaGetLastError());
-    k_reduce_partials<<<(unsigned)((T2.n_params + 127) / 128), 128, 0, ctx->stream>>>(partial, grid, T2.n_params, dw);
+    k_reduce_partials<<<(unsigned)((T2.n_params + 127) / 128), 128, 0, ctx->stream>>>(partial, grid, T2.n_params,
+                                                                                     targets ? inv_n : 1.f, dw);
     PF_CUDA(ctx, cudaGetLastError());
     return PF_OK;
   }
@@ -1353,7 +1358,8 @@ pf_status pf_tc_backward(pf_ctx* ctx, const pf_field* f, const float* q, const f
     if (f->desc.prec == PF_PREC_BF16) { PF_TRY(launch(k_tc_train<PF_PREC_BF16, false>)); }
     else { PF_TRY(launch(k_tc_train<PF_PREC_F16, false>)); }
   }
-  k_reduce_partials<<<(unsigned)((T.n_params + 127) / 128), 128, 0, ctx->stream>>>(partial, grid, T.n_params, dw);
+  k_reduce_partials<<<(unsigned)((T.n_params + 127) / 128), 128, 0, ctx->stream>>>(partial, grid, T.n_params,
+                                                                                    targets ? inv_n : 1.f, dw);
   PF_CUDA(ctx, cudaGetLastError());
   return PF_OK;
 }

@@ -7,6 +7,7 @@
   * backward: per-layer gradient error <= 1e-3 (relative, norm-wise) against
     the precision-emulated oracle on a 512-query batch, and the oracle's own
     gradient is pinned by finite differences (tests/test_oracle_field.py);
+    the training loss and its loss-scaled gradient likewise on 4133 queries;
   * Adam step against the closed form;
   * training queries: identical cells and g, positions and angles within
     float32 rounding; radiance estimates within 1e-5 (float32 sums of the
@@ -82,6 +83,28 @@ def test_backward_matches_oracle(pf_ctx, prec, hidden):
     for (a, b) in zip(F.unflatten(dw, desc), F.unflatten(ref, desc)):
         rel = np.linalg.norm(a - b) / np.linalg.norm(b)
         assert rel <= (1e-5 if prec == "f32" else 1e-3), rel
+
+
+@pytest.mark.parametrize("prec,hidden", [("f32", 64), ("bf16", 64), ("f16", 128), ("bf16", 128)])
+def test_loss_gradient_matches_oracle(pf_ctx, prec, hidden):
+    """The training step's loss and gradient (Sec. 3.5.1; the backward pass
+    loss-scaled as in training) against the precision-emulated oracle on
+    4133 queries (several tiles of either tensor-core trainer and a ragged
+    tail) with targets near the prediction: loss within 1e-5 (f32) / 1e-3
+    (16-bit) relative, gradient within 1e-5 / 1e-3 norm-wise per layer."""
+    fld = api.Field(pf_ctx, 12, hidden, 4, prec, 5.0, seed=6)
+    desc = F.FieldDesc(12, hidden, 4, PRECS[prec], 5.0, 6)
+    w = F.init_weights(desc).astype(np.float64)
+    q = _queries(4133, seed=12)
+    y0, _ = F.forward(w, q.astype(np.float64), F.FieldDesc(12, hidden, 4, F.PREC_F32, 5.0, 6))
+    t = (y0 + np.random.default_rng(13).normal(size=y0.shape) * 0.3).astype(np.float32)
+    loss, dw = fld.loss_gradient(torch.from_numpy(q).cuda(), torch.from_numpy(t).cuda())
+    lref, gref = F.train_gradient(w, q.astype(np.float64), t.astype(np.float64), desc)
+    tol = 1e-5 if prec == "f32" else 1e-3
+    assert abs(loss - lref) <= tol * lref, (loss, lref)
+    for a, b in zip(F.unflatten(dw.cpu().numpy(), desc), F.unflatten(gref, desc)):
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        assert rel <= tol, rel
 
 
 def test_autograd_function(pf_ctx):

@@ -153,3 +153,61 @@ def test_fp8_calibration_and_quantised_forward():
     y8, _ = F.forward(w, q, desc, (s_a, s_w))
     y32, _ = F.forward(w, q, F.FieldDesc(12, 32, 2, F.PREC_F32, 5.0, 1))
     assert np.abs(y8 - y32).max() < 0.1 * np.abs(y32).max() + 1e-3
+
+
+def test_float32_encoding_of_the_tensor_core_fields(orc):
+    """The kernels' float32 encoding (anchors at k = 0, 4, 8 from the own
+    turn-based sine / cosine, double-angle formulas in between) against the
+    exact features: within 6e-6 everywhere (three doublings of anchors good
+    to 3e-7), exact at the anchors' simple arguments, negative g handled."""
+    rng = np.random.default_rng(11)
+    q = rng.uniform(0, 1, (20000, 6))
+    q[:, 5] = rng.uniform(-0.9, 0.9, q.shape[0])
+    q = np.concatenate([q, [[0, 0.25, 0.5, 0.75, 1.0, -0.5]]]).astype(np.float32).astype(np.float64)
+    got = orc.encode_f32(q, 12)
+    ref = F.encode(q, 12)
+    assert got.shape == ref.shape
+    assert np.max(np.abs(got - ref)) < 6e-6, np.max(np.abs(got - ref))
+    # k = 0 features are the anchors themselves: 3e-7 (the own sine / cosine)
+    k0 = np.concatenate([np.arange(24 * d, 24 * d + 2) for d in range(6)])
+    assert np.max(np.abs(got[:, k0] - ref[:, k0])) < 3e-7
+    # last row: v = 0 gives sin 0, cos 1 at every k
+    assert np.all(got[-1, 0:24:2] == 0.0) and np.all(got[-1, 1:24:2] == 1.0)
+
+
+def test_train_gradient_is_the_mean_loss_gradient():
+    """Loss scaling does not change the gradient in exact arithmetic: in FP64
+    without operand rounding, train_gradient equals central differences of
+    the mean relative MSE (so the 1/n is applied once, not twice or never)."""
+    desc = F.FieldDesc(in_freqs=2, hidden=8, n_hidden=3, prec=F.PREC_F32)
+    rng = np.random.default_rng(7)
+    w = rng.normal(size=desc.n_params()) * 0.5
+    q = rng.uniform(0, 1, (24, 6))
+    y = rng.uniform(0, 1, (24, 3))
+    loss, g = F.train_gradient(w, q, y, desc)
+    assert abs(loss - F.rel_mse(F.forward(w, q, desc)[0], y)[0]) < 1e-15
+    h = 1e-6
+    for i in rng.choice(w.size, 40, replace=False):
+        wp, wm = w.copy(), w.copy()
+        wp[i] += h
+        wm[i] -= h
+        fd = (F.rel_mse(F.forward(wp, q, desc)[0], y)[0] - F.rel_mse(F.forward(wm, q, desc)[0], y)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1e-3, abs(fd)), (i, fd, g[i])
+
+
+def test_loss_scaled_16_bit_gradient_near_the_unrounded_one():
+    """The f16 emulation's loss-scaled training gradient of a 4x128 field on
+    4096 queries stays within a few % of the unrounded one (the operand
+    rounding of features, activations and gradients), layer by layer."""
+    desc16 = F.FieldDesc(12, 128, 4, F.PREC_F16, 5.0, 3)
+    desc32 = F.FieldDesc(12, 128, 4, F.PREC_F32, 5.0, 3)
+    w = F.init_weights(desc16).astype(np.float64)
+    rng = np.random.default_rng(8)
+    q = rng.uniform(0, 1, (4096, 6))
+    q[:, 5] = rng.choice([-0.75, 0.0, 0.75], q.shape[0])
+    y0, _ = F.forward(w, q, desc32)
+    y = y0 + rng.normal(size=y0.shape) * 0.3          # targets near the prediction
+    _, g32 = F.train_gradient(w, q, y, desc32)
+    _, g16 = F.train_gradient(w, q, y, desc16)
+    for a, b in zip(F.unflatten(g16, desc16), F.unflatten(g32, desc32)):
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) < 0.06
