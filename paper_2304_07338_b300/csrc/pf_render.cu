@@ -79,6 +79,9 @@ __global__ void k_place(const uint32_t* __restrict__ ckey, const uint32_t* __res
   }
 }
 
+// Segments of the ray marcher whose density lookups are issued together.
+constexpr int kMarchAhead = 4;
+
 // -------------------------------------------------------------- camera samples
 // stats (nullable): stats[0] += density lookups, stats[1] += valid samples
 // (= field queries) of the launch.
@@ -124,26 +127,38 @@ __device__ __forceinline__ void camera_samples(Vol V, DevLights L, CamF cam, flo
         const double tau_star_d = -log1p(-(double)b0[3]);
         const float tau_star = (float)tau_star_d;
         float tau = 0.f, comp = 0.f;
-        int nseg = (int)ceilf((t1 - t0) / h);
-        for (int s = 0; s < nseg; ++s) {
-          float s0 = t0 + (float)s * h;
-          float s1 = mn(t0 + (float)(s + 1) * h, t1);
-          float len = s1 - s0;
-          if (!(len > 0.f)) continue;
-          float sg = sigma_at<DT>(V, along(o, d, s0 + b0[2] * len));
-          ++nfetch;
-          float dtau = sg * len;
-          if (sg > 0.f && (tau - comp) + dtau >= tau_star) {
-            double rem = tau_star_d - ((double)tau - (double)comp);
-            float dl = (float)(rem / (double)sg);
-            th = s0 + mn(mx(dl, 0.f), len);
-            hit = true;
-            break;
+        const int nseg = (int)ceilf((t1 - t0) / h);
+        // kMarchAhead segments' lookups are issued together (independent
+        // loads in flight), then taken in order by the same float steps as a
+        // one-at-a-time loop; lookups past the interaction are discarded
+        // (a point beyond the ray's box exit reads density 0)
+        for (int s = 0; s < nseg && !hit; s += kMarchAhead) {
+          float sg[kMarchAhead], s0v[kMarchAhead], lenv[kMarchAhead];
+#pragma unroll
+          for (int j = 0; j < kMarchAhead; ++j) {
+            s0v[j] = t0 + (float)(s + j) * h;
+            lenv[j] = mn(t0 + (float)(s + j + 1) * h, t1) - s0v[j];
+            sg[j] = sigma_at<DT>(V, along(o, d, s0v[j] + b0[2] * lenv[j]));
           }
-          float y = dtau - comp;
-          float t = tau + y;
-          comp = (t - tau) - y;
-          tau = t;
+#pragma unroll
+          for (int j = 0; j < kMarchAhead; ++j) {
+            if (s + j >= nseg || hit) break;
+            const float len = lenv[j];
+            if (!(len > 0.f)) continue;
+            ++nfetch;
+            const float dtau = sg[j] * len;
+            if (sg[j] > 0.f && (tau - comp) + dtau >= tau_star) {
+              const double rem = tau_star_d - ((double)tau - (double)comp);
+              const float dl = (float)(rem / (double)sg[j]);
+              th = s0v[j] + mn(mx(dl, 0.f), len);
+              hit = true;
+              break;
+            }
+            const float y = dtau - comp;
+            const float t = tau + y;
+            comp = (t - tau) - y;
+            tau = t;
+          }
         }
       } else {
         hit = delta_track<DT>(V, o, d, t0, t1, rng, &th, err, nfetch);
@@ -162,17 +177,25 @@ __device__ __forceinline__ void camera_samples(Vol V, DevLights L, CamF cam, flo
           {
             float tau = 0.f, comp = 0.f;
             if (tend > 0.f) {
-              int nseg = (int)ceilf(tend / h);
-              for (int s = 0; s < nseg; ++s) {
-                float s0 = (float)s * h;
-                float s1 = mn((float)(s + 1) * h, tend);
-                float len = s1 - s0;
-                if (!(len > 0.f)) continue;
-                float y = sigma_at<DT>(V, along(x, wl, s0 + jl[l] * len)) * len - comp;
-                ++nfetch;
-                float t = tau + y;
-                comp = (t - tau) - y;
-                tau = t;
+              const int nseg = (int)ceilf(tend / h);
+              for (int s = 0; s < nseg; s += kMarchAhead) {   // lookups ahead, sums in order
+                float sg[kMarchAhead], lenv[kMarchAhead];
+#pragma unroll
+                for (int j = 0; j < kMarchAhead; ++j) {
+                  const float s0 = (float)(s + j) * h;
+                  lenv[j] = mn((float)(s + j + 1) * h, tend) - s0;
+                  sg[j] = sigma_at<DT>(V, along(x, wl, s0 + jl[l] * lenv[j]));
+                }
+#pragma unroll
+                for (int j = 0; j < kMarchAhead; ++j) {
+                  if (s + j >= nseg) break;
+                  if (!(lenv[j] > 0.f)) continue;
+                  const float y = sg[j] * lenv[j] - comp;
+                  ++nfetch;
+                  const float t = tau + y;
+                  comp = (t - tau) - y;
+                  tau = t;
+                }
               }
             }
             T = expf(-(tau - comp));
@@ -809,15 +832,23 @@ __global__ void __launch_bounds__(128) k_raymarch(Vol V, DevLights L, CamF cam, 
               float st = 0.f, sc = 0.f;
               if (tend > 0.f) {
                 const int ns = (int)ceilf(tend / h);
-                for (int m = 0; m < ns; ++m) {
-                  const float m0 = (float)m * h;
-                  const float m1 = mn((float)(m + 1) * h, tend);
-                  const float ml = m1 - m0;
-                  if (!(ml > 0.f)) continue;
-                  const float y = sigma_at<DT>(V, along(x, wl, m0 + jit[ii] * ml)) * ml - sc;
-                  const float t = st + y;
-                  sc = (t - st) - y;
-                  st = t;
+                for (int m = 0; m < ns; m += kMarchAhead) {    // lookups ahead, sums in order
+                  float sg4[kMarchAhead], ml4[kMarchAhead];
+#pragma unroll
+                  for (int u = 0; u < kMarchAhead; ++u) {
+                    const float m0 = (float)(m + u) * h;
+                    ml4[u] = mn((float)(m + u + 1) * h, tend) - m0;
+                    sg4[u] = sigma_at<DT>(V, along(x, wl, m0 + jit[ii] * ml4[u]));
+                  }
+#pragma unroll
+                  for (int u = 0; u < kMarchAhead; ++u) {
+                    if (m + u >= ns) break;
+                    if (!(ml4[u] > 0.f)) continue;
+                    const float y = sg4[u] * ml4[u] - sc;
+                    const float t = st + y;
+                    sc = (t - st) - y;
+                    st = t;
+                  }
                 }
               }
               const float T = expf(-(st - sc));
