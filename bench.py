@@ -85,34 +85,44 @@ class Clocks:
         self.nvml = None
         self.t = None
 
+    # NVML through ctypes (the driver's libnvidia-ml; no Python binding
+    # needed): clock id 1 = SM; clock-event reason bits of nvml.h
+    NVML_CLOCK_SM = 1
+    REASON_BITS = {"hw_slowdown": 0x8, "hw_thermal_slowdown": 0x40, "sw_thermal_slowdown": 0x20,
+                   "sw_power_cap": 0x4}
+
     def _nvml_handle(self):
-        import pynvml
+        import ctypes
         import torch
-        pynvml.nvmlInit()
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit_v2 failed")
+        h = ctypes.c_void_p()
         props = torch.cuda.get_device_properties(self.device)
         bus = getattr(props, "pci_bus_id", None)
+        ok = False
         if bus is not None:
             bus_id = "%08x:%02x:%02x.0" % (getattr(props, "pci_domain_id", 0), bus, getattr(props, "pci_device_id", 0))
-            try:
-                return pynvml, pynvml.nvmlDeviceGetHandleByPciBusId(bus_id.encode())
-            except Exception:
-                pass
-        return pynvml, pynvml.nvmlDeviceGetHandleByIndex(self.device)
+            ok = lib.nvmlDeviceGetHandleByPciBusId_v2(bus_id.encode(), ctypes.byref(h)) == 0
+        if not ok and lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.device), ctypes.byref(h)) != 0:
+            raise RuntimeError("no NVML handle for device %d" % self.device)
+        return lib, h
 
     def _poll_nvml(self):
-        nv, h = self.nvml
-        bits = {"hw_slowdown": nv.nvmlClocksEventReasonHwSlowdown,
-                "hw_thermal_slowdown": nv.nvmlClocksEventReasonHwThermalSlowdown,
-                "sw_thermal_slowdown": nv.nvmlClocksEventReasonSwThermalSlowdown,
-                "sw_power_cap": nv.nvmlClocksEventReasonSwPowerCap}
-        mx = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+        import ctypes
+        lib, h = self.nvml
+        mx = ctypes.c_uint(0)
+        lib.nvmlDeviceGetMaxClockInfo(h, self.NVML_CLOCK_SM, ctypes.byref(mx))
+        sm = ctypes.c_uint(0)
+        r = ctypes.c_ulonglong(0)
+        reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
         while not self.stop_flag.is_set():
-            try:
-                sm = nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)
-                r = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
-                self.samples.append((float(sm), float(mx), [k for k, b in bits.items() if r & b]))
-            except Exception:
+            if lib.nvmlDeviceGetClockInfo(h, self.NVML_CLOCK_SM, ctypes.byref(sm)) != 0 or \
+                    reasons(h, ctypes.byref(r)) != 0:
                 break
+            self.samples.append((float(sm.value), float(mx.value),
+                                 [k for k, b in self.REASON_BITS.items() if r.value & b]))
             time.sleep(0.01)
 
     def start(self):
@@ -451,8 +461,8 @@ def cpu_baseline_plan(vol_host, tf, lights, cams, seed, args, prec, fixed_s=None
       mid render: a 64x64 crop at 1 spp, samples/s extrapolated to a frame
         (1024^2 x 4 spp), the oracle's fixed cost per call counted once;
       large render (all threads): the headline cpu_baseline; one thread:
-        32 pixels of the middle row, its fixed cost per call (the majorant
-        grids, single-threaded either way) taken from the headline's."""
+        the middle row, its fixed cost per call (the majorant grids,
+        single-threaded either way) taken from the headline's."""
     import oracle
     from oracle import field as F
     from paper_2304_07338_b300 import inputs as I
@@ -519,7 +529,7 @@ def cpu_baseline_plan(vol_host, tf, lights, cams, seed, args, prec, fixed_s=None
             if nthr == 1:
                 one = cpu_baseline(vol_host, tf, lights, cams, seed, rows=1, brick=args.brick,
                                    brick_primary=args.brick_primary, brick_shadow=args.brick_shadow,
-                                   cols=(W_ // 2 - 16, W_ // 2 + 16), t_fix=fixed_s, **oracle_field(seed, prec))
+                                   t_fix=fixed_s, **oracle_field(seed, prec))
                 r["large_render_frames_per_s_extrapolated"] = one["value"]
                 r["large_render_sample"] = one["sample"]
         finally:
@@ -672,7 +682,7 @@ def main():
         cam, g = frame(args.warmup + i)
         if i >= 2:
             ctx.stream.wait_event(copied[b])              # buffer b's previous copy is done
-        api.render_neural(ctx, vol, lights, g, cam, SPP, 0.0, seed + 100 + i, field, outs[b])
+        api.render_neural(ctx, vol, lights, g, cam, SPP, args.step_vox, seed + 100 + i, field, outs[b])
         rendered[b].record(ctx.stream)
         copy_stream.wait_event(rendered[b])
         with torch.cuda.stream(copy_stream):
