@@ -102,6 +102,25 @@ __device__ __forceinline__ void store16(uint8_t* tile, uint32_t kp, int r, int c
   }
 }
 
+// 16-bit operands of 16 values of row r with ReLU, applied to the rounded
+// pairs (packed max with +0).
+template <int PREC>
+__device__ __forceinline__ void store16_relu(uint8_t* tile, uint32_t kp, int r, int col, const float v[16]) {
+  uint32_t w[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    if (PREC == PF_PREC_BF16) {
+      __nv_bfloat162 h = __hmax2(__floats2bfloat162_rn(v[2 * i], v[2 * i + 1]), __float2bfloat162_rn(0.f));
+      w[i] = *(uint32_t*)&h;
+    } else {
+      __half2 h = __hmax2(__floats2half2_rn(v[2 * i], v[2 * i + 1]), __float2half2_rn(0.f));
+      w[i] = *(uint32_t*)&h;
+    }
+  }
+  store_chunk(tile, kp * 2, r, col / 8, make_uint4(w[0], w[1], w[2], w[3]));
+  store_chunk(tile, kp * 2, r, col / 8 + 1, make_uint4(w[4], w[5], w[6], w[7]));
+}
+
 // Frequency encoding of one query (6 inputs x F frequencies, features ordered
 // [input][k][sin, cos], each times s) into row r of an A tile with K extent
 // kp, zero-padded to kp; features sin/cos(2^k pi v) by pff::freq_next.
@@ -246,26 +265,38 @@ __global__ void __launch_bounds__(kFwdMaxThreads, 1) k_tc_forward(TcArgs A, cons
       // (fp8; 1 otherwise), so one product by their product is exact too
       const float s_next = (FP8 && !last) ? A.L[l + 1].inv_s_in : 1.f;
       const float sc = last ? Ly.dequant : Ly.dequant * s_next;
-      for (int c0 = 0; c0 < H; c0 += 16) {
-        float v[16];
-        tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
+      for (int c0 = 0; c0 < H; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + lane_base + (uint32_t)c0, v);       // 32 columns, one wait
+        if (FP8) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] * sc, 0.f);
+          for (int i = 0; i < 32; ++i) v[i] *= sc;           // power-of-two scales (1 for 16-bit fields)
+        }
         if (last) {
 #pragma unroll
-          for (int i = 0; i < 16; i += 4) {
+          for (int i = 0; i < 32; i += 4) {
             const float4 w0 = *(const float4*)(w_out + c0 + i);
             const float4 w1 = *(const float4*)(w_out + H + c0 + i);
             const float4 w2 = *(const float4*)(w_out + 2 * H + c0 + i);
-            y0 = fmaf(v[i], w0.x, y0); y0 = fmaf(v[i + 1], w0.y, y0);
-            y0 = fmaf(v[i + 2], w0.z, y0); y0 = fmaf(v[i + 3], w0.w, y0);
-            y1 = fmaf(v[i], w1.x, y1); y1 = fmaf(v[i + 1], w1.y, y1);
-            y1 = fmaf(v[i + 2], w1.z, y1); y1 = fmaf(v[i + 3], w1.w, y1);
-            y2 = fmaf(v[i], w2.x, y2); y2 = fmaf(v[i + 1], w2.y, y2);
-            y2 = fmaf(v[i + 2], w2.z, y2); y2 = fmaf(v[i + 3], w2.w, y2);
+            const float a0 = fmaxf(v[i], 0.f), a1 = fmaxf(v[i + 1], 0.f);
+            const float a2 = fmaxf(v[i + 2], 0.f), a3 = fmaxf(v[i + 3], 0.f);
+            y0 = fmaf(a0, w0.x, y0); y0 = fmaf(a1, w0.y, y0);
+            y0 = fmaf(a2, w0.z, y0); y0 = fmaf(a3, w0.w, y0);
+            y1 = fmaf(a0, w1.x, y1); y1 = fmaf(a1, w1.y, y1);
+            y1 = fmaf(a2, w1.z, y1); y1 = fmaf(a3, w1.w, y1);
+            y2 = fmaf(a0, w2.x, y2); y2 = fmaf(a1, w2.y, y2);
+            y2 = fmaf(a2, w2.z, y2); y2 = fmaf(a3, w2.w, y2);
           }
-        } else {
+        } else if (FP8) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i], 0.f);
           store16<PREC>(a_tile, kp_next, ltid, c0, v);
+          store16<PREC>(a_tile, kp_next, ltid, c0 + 16, v + 16);
+        } else {
+          // rounding is monotonic and 0 is exact, so ReLU after the
+          // rounding equals ReLU before it: one packed max per two values
+          store16_relu<PREC>(a_tile, kp_next, ltid, c0, v);
+          store16_relu<PREC>(a_tile, kp_next, ltid, c0 + 16, v + 16);
         }
       }
     }
@@ -908,8 +939,7 @@ __global__ void __launch_bounds__(kT128Threads, 1) k_tc_train128(T128Args T, con
       }
       if (!commit_wait()) break;
       float v[32];
-      tmem_ld16(lane_addr + kT128Acc + 32 * hf, v);
-      tmem_ld16(lane_addr + kT128Acc + 32 * hf + 16, v + 16);
+      tmem_ld32(lane_addr + kT128Acc + 32 * hf, v);
       if (l < L - 1) {
         uint8_t* xn = smem + T.x_off[l + 1];
 #pragma unroll
@@ -1008,8 +1038,7 @@ __global__ void __launch_bounds__(kT128Threads, 1) k_tc_train128(T128Args T, con
       if (!commit_wait()) break;
       // dZ_{l-1} [k][q] = rnd(dA_l * [X_l > 0]), feature row k = this thread's lane
       float v[32];
-      tmem_ld16(lane_addr + kT128Acc + 32 * hf, v);
-      tmem_ld16(lane_addr + kT128Acc + 32 * hf + 16, v + 16);
+      tmem_ld32(lane_addr + kT128Acc + 32 * hf, v);
       const uint8_t* xl = smem + T.x_off[l];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
