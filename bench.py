@@ -408,6 +408,60 @@ def field_roofline(stage, queries_per_frame, steps, peak_tflops, peak_source):
             "ms_per_frame": ms / max(steps, 1), "peak_source": peak_source}
 
 
+def field_library_reference(queries_per_frame, field_ms, dev, hidden=128, n_hidden=4, freqs=12, reps=5):
+    """The same 4 x 128 field on library kernels, for the frame's number of
+    queries: the hidden layers as a chain of cuBLAS f16 GEMMs (torch.matmul,
+    ReLU between them) with the 3-wide output layer in float32, on inputs
+    already encoded; and the whole pipeline with the frequency encoding as
+    torch elementwise ops.  Best of `reps`, CUDA events.  Timing does not
+    depend on the weight values, so they are random."""
+    import torch
+    n = int(queries_per_frame)
+    if n <= 0:
+        return None
+    g = torch.Generator(device=dev).manual_seed(7)
+    q = torch.rand(n, 6, device=dev, generator=g)
+    k0 = 6 * 2 * freqs
+    ws = [torch.randn(hidden, k0 if l == 0 else hidden, device=dev, generator=g).half() * 0.05
+          for l in range(n_hidden)]
+    w_out = torch.randn(3, hidden, device=dev, generator=g) * 0.05
+    scale = (torch.pi * 2.0 ** torch.arange(freqs, device=dev)).view(1, 1, freqs)
+
+    def encode():
+        a = q.unsqueeze(2) * scale                      # [n][6][F]
+        return torch.stack((torch.sin(a), torch.cos(a)), dim=3).reshape(n, k0).half()
+
+    def chain(x):
+        for w in ws:
+            x = torch.relu(torch.matmul(x, w.t()))
+        return torch.matmul(x.float(), w_out.t())
+
+    x0 = encode()
+
+    def best(fn):
+        fn()
+        torch.cuda.synchronize()
+        t = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            t = min(t, e0.elapsed_time(e1))
+        return t
+
+    chain_ms = best(lambda: chain(x0))
+    full_ms = best(lambda: chain(encode()))
+    del x0, q
+    return {"queries": n, "cublas_chain_ms": chain_ms, "torch_encode_and_chain_ms": full_ms,
+            "k_tc_forward_ms": field_ms,
+            "k_tc_forward_speedup_vs_chain": chain_ms / field_ms if field_ms else None,
+            "k_tc_forward_speedup_vs_full": full_ms / field_ms if field_ms else None,
+            "how": "torch.matmul f16 (cuBLAS) per hidden layer + ReLU, float32 output layer; encoding as torch "
+                   "sin/cos; best of %d, CUDA events" % reps}
+
+
 def handoff_cost(ctx, queries_per_frame, frame_ms, dev):
     """What the pass split costs in HBM traffic: a fused camera-sample +
     field kernel would keep each scattering sample's field input (query 24 B,
@@ -780,6 +834,7 @@ def main():
             line["field_roofline"][name] = variants[name]["field_roofline"]
         line["variants"] = variants
         line["field_handoff"] = handoff_cost(ctx, qpf, ms_per_step, dev)
+        line["field_library_reference"] = field_library_reference(qpf, fld_ms / max(args.steps, 1), dev)
         if not args.no_equal_rmse:
             eq = equal_rmse(ctx, vol, vol_pt, lights, cams, fields, seed, args)
             line["equal_rmse"] = eq

@@ -49,7 +49,7 @@ struct TcArgs {
   const float* w_out;  // [3][H] float32 output layer
   int n_hidden, hidden, in_freqs, prec, kstep;  // kstep = 16 (16-bit) or 32 (fp8)
   int n_groups;        // forward: warpgroups (tiles in flight) per CTA
-  uint32_t a_off, a_bytes, wout_off, bar_off, smem_bytes;
+  uint32_t a_off, a_bytes, wout_off, ypart_off, bar_off, smem_bytes;
   float psi;
   TcLayer L[kMaxLayers];
 };
@@ -132,7 +132,6 @@ __device__ __forceinline__ void encode_query(uint8_t* tile, uint32_t kp, int r, 
     float buf[16];
 #pragma unroll
     for (int d = 0; d < 6; ++d) {
-#pragma unroll
       float sn = 0.f, cs = 1.f;
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
@@ -170,7 +169,43 @@ __device__ __forceinline__ void encode_query(uint8_t* tile, uint32_t kp, int r, 
   }
 }
 
+// Writes 8 values of row r as one 16-byte chunk (16-bit operand types);
+// `chunk` is the K index / 8.
 template <int PREC>
+__device__ __forceinline__ void store8(uint8_t* tile, uint32_t kp, int r, int chunk, const float v[8]) {
+  uint4 q;
+  q.x = pack2<PREC>(v[0], v[1]); q.y = pack2<PREC>(v[2], v[3]);
+  q.z = pack2<PREC>(v[4], v[5]); q.w = pack2<PREC>(v[6], v[7]);
+  store_chunk(tile, kp * 2, r, chunk, q);
+}
+
+// Half of the frequency encoding of one query (16-bit operands, F = 12):
+// inputs 3h..3h+2, i.e. features 72h..72h+71 of the row, the same values as
+// encode_query writes there (nine 16-byte chunks).
+template <int PREC>
+__device__ __forceinline__ void encode_half(uint8_t* tile, uint32_t kp, int r, const float qv[3], int h) {
+  float buf[8];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    float sn = 0.f, cs = 1.f;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      pff::freq_next(qv[d], k, sn, cs);
+      const int f = 24 * d + 2 * k;
+      buf[f % 8] = sn;
+      buf[(f + 1) % 8] = cs;
+      if ((f + 2) % 8 == 0) store8<PREC>(tile, kp, r, (72 * h + f + 2 - 8) / 8, buf);
+    }
+  }
+}
+
+// TPR threads per tile row: 1, or 2 for 16-bit fields whose shared memory
+// holds only two tiles in flight (the f16 / bf16 4 x 128 render field), so
+// that the SM still has 16 warps to switch between.  With TPR = 2 the thread
+// pair (r, r + 128) of a group owns row r; the two threads split the
+// encoding (inputs 0-2 / 3-5) and the epilogue columns (halves of H), and the
+// output layer's two partial sums meet in shared memory.
+template <int PREC, int TPR>
 __global__ void __launch_bounds__(kFwdMaxThreads, 1) k_tc_forward(TcArgs A, const float* __restrict__ q, int64_t B_max,
                                                             const uint32_t* __restrict__ B_dev, float* __restrict__ out,
                                                             const uint32_t* __restrict__ slot_idx,
@@ -180,11 +215,14 @@ __global__ void __launch_bounds__(kFwdMaxThreads, 1) k_tc_forward(TcArgs A, cons
   constexpr uint32_t EB = FP8 ? 1 : 2;
   constexpr uint32_t AB_TYPE = (PREC == PF_PREC_BF16) ? 1u : 0u;   // f16 = 0, bf16 = 1, e4m3 = 0
   extern __shared__ __align__(1024) uint8_t smem[];
+  constexpr int GT = 128 * TPR;                  // threads of a group
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int wg = tid >> 7, ltid = tid & 127;     // warpgroup; its thread = row of its tile
+  const int wg = tid / GT, gtid = tid % GT;      // group; its thread
+  const int ltid = gtid & 127, half = gtid >> 7; // row of the tile; column half (TPR = 2)
   const int NG = A.n_groups;
   uint8_t* a_tile = smem + A.a_off + (uint32_t)wg * A.a_bytes;
   float* w_out = (float*)(smem + A.wout_off);
+  float* ypart = (float*)(smem + A.ypart_off) + (size_t)wg * 3 * kTileM;   // TPR = 2: [3][128] partial outputs
   uint64_t* bars = (uint64_t*)(smem + A.bar_off);          // [0] weights, [1 + g] MMAs of group g
   uint32_t* tmem_slot = (uint32_t*)(smem + A.bar_off + 48);
   int* abort_flag = (int*)(smem + A.bar_off + 52);
@@ -219,12 +257,19 @@ __global__ void __launch_bounds__(kFwdMaxThreads, 1) k_tc_forward(TcArgs A, cons
   const int F = A.in_freqs;
   const uint32_t kp0 = A.L[0].kp;
 
-  for (int64_t tile = (int64_t)blockIdx.x * NG + wg; tile < n_tiles && !*abort_flag;
-       tile += (int64_t)gridDim.x * NG) {
+  // A timed-out wait sets abort_flag; the group stops at its next barrier,
+  // all of its threads alike (the barrier ORs their reads of the flag).
+  bool stop = false;
+  for (int64_t tile = (int64_t)blockIdx.x * NG + wg; tile < n_tiles; tile += (int64_t)gridDim.x * NG) {
     const int64_t row = tile * kTileM + ltid;
     const bool valid = row < B;
     // ---- encoding of this thread's query into the A tile (K = kp0)
-    {
+    if (TPR == 2) {
+      float qv[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) qv[d] = valid ? __ldg(q + 6 * row + 3 * half + d) : 0.f;
+      encode_half<PREC>(a_tile, kp0, ltid, qv, half);
+    } else {
       float qv[6];
 #pragma unroll
       for (int d = 0; d < 6; ++d) qv[d] = valid ? __ldg(q + 6 * row + d) : 0.f;
@@ -236,9 +281,10 @@ __global__ void __launch_bounds__(kFwdMaxThreads, 1) k_tc_forward(TcArgs A, cons
       const TcLayer Ly = A.L[l];
       fence_proxy_async();
       tc_fence_before();
-      named_barrier(1 + wg, 128);
+      stop = named_barrier_or(1 + wg, GT, *abort_flag != 0);
       tc_fence_after();
-      if (ltid == 0) {
+      if (stop) break;
+      if (gtid == 0) {
         const uint32_t a0 = smem_u32(a_tile), b0 = smem_u32(smem + Ly.w_off);
         const uint32_t sbo = (Ly.kp * EB / 16) * 128;
         const uint32_t id = idesc(AB_TYPE, (uint32_t)H);
@@ -258,14 +304,14 @@ __global__ void __launch_bounds__(kFwdMaxThreads, 1) k_tc_forward(TcArgs A, cons
       }
       mma_phase ^= 1u;
       tc_fence_after();
-      if (*abort_flag) break;
       const bool last = (l == A.n_hidden - 1);
       const uint32_t kp_next = last ? 0u : A.L[l + 1].kp;
       // dequantisation and the next layer's input scale are powers of two
       // (fp8; 1 otherwise), so one product by their product is exact too
       const float s_next = (FP8 && !last) ? A.L[l + 1].inv_s_in : 1.f;
       const float sc = last ? Ly.dequant : Ly.dequant * s_next;
-      for (int c0 = 0; c0 < H; c0 += 32) {
+      const int c_lo = half * (H / TPR), c_hi = c_lo + H / TPR;
+      for (int c0 = c_lo; c0 < c_hi; c0 += 32) {
         float v[32];
         tmem_ld32(tmem + lane_base + (uint32_t)c0, v);       // 32 columns, one wait
         if (FP8) {
@@ -300,7 +346,13 @@ __global__ void __launch_bounds__(kFwdMaxThreads, 1) k_tc_forward(TcArgs A, cons
         }
       }
     }
-    if (*abort_flag) break;
+    if (stop) break;
+    if (TPR == 2) {                    // the second half's partial sums join the first's
+      if (half == 1) { ypart[ltid] = y0; ypart[kTileM + ltid] = y1; ypart[2 * kTileM + ltid] = y2; }
+      named_barrier(1 + wg, GT);
+      if (half == 1) continue;
+      y0 = y0 + ypart[ltid]; y1 = y1 + ypart[kTileM + ltid]; y2 = y2 + ypart[2 * kTileM + ltid];
+    }
     if (valid) {
       if (slot_idx) {
         uint32_t sl = slot_idx[row];
@@ -362,15 +414,6 @@ constexpr int kTrainHidden = 64;
 constexpr int kTrainThreads = 256;
 constexpr uint32_t kDK = 128;       // padded neuron extent of the dZ tile
 
-// Writes 8 values of row r as one 16-byte chunk (16-bit operand types);
-// `chunk` is the K index / 8.
-template <int PREC>
-__device__ __forceinline__ void store8(uint8_t* tile, uint32_t kp, int r, int chunk, const float v[8]) {
-  uint4 q;
-  q.x = pack2<PREC>(v[0], v[1]); q.y = pack2<PREC>(v[2], v[3]);
-  q.z = pack2<PREC>(v[4], v[5]); q.w = pack2<PREC>(v[6], v[7]);
-  store_chunk(tile, kp * 2, r, chunk, q);
-}
 
 // One 16-bit operand (bf16 or f16 bits) as a float.
 template <int PREC>
@@ -451,22 +494,25 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_tc_train(TrArgs T, const f
   bool first_tile = true;
   float lsum = 0.f;
 
-  auto sync_mma = [&]() -> bool {
+  // A timed-out wait sets abort_flag; the CTA stops at the next MMA's
+  // barrier, every thread alike (__syncthreads_or over their reads).
+  auto sync_mma = [&]() {
     if (tid == 0) mma_commit(bar_mma);
     bool ok = mbar_wait(bar_mma, phase);
     phase ^= 1u;
     tc_fence_after();
     if (!ok) { atomicOr(err, PFE_ITER_CAP); *abort_flag = 1; }
-    return ok;
   };
-  auto pre_mma = [&]() {
+  auto pre_mma = [&]() -> bool {
     fence_proxy_async();
     tc_fence_before();
-    __syncthreads();
+    const bool s = __syncthreads_or(*abort_flag != 0) != 0;
     tc_fence_after();
+    return s;
   };
+  bool stop = false;
 
-  for (int64_t tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x) {
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int64_t row = tile * kTileM + r;
     const bool valid = row < B;
     // ---- encoding -> A_0
@@ -513,7 +559,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_tc_train(TrArgs T, const f
     float h[HH];
     for (int l = 0; l < L; ++l) {
       const TcLayer Ly = A.L[l];
-      pre_mma();
+      if ((stop = pre_mma())) break;
       if (tid == 0) {
         const uint32_t a0 = smem_u32(smem + T.a_off[l]), b0 = smem_u32(smem + Ly.w_off);
         const uint32_t sbo = (Ly.kp * 2 / 16) * 128;
@@ -521,7 +567,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_tc_train(TrArgs T, const f
         for (int ks = 0; ks < (int)(Ly.kp / 16); ++ks)
           mma<false>(tmem, sdesc(a0 + ks * 256, 128, sbo), sdesc(b0 + ks * 256, 128, sbo), id, ks > 0 ? 1u : 0u);
       }
-      if (!sync_mma()) break;
+      sync_mma();
 #pragma unroll
       for (int g = 0; g < HH / 16; ++g) {
         const int c0 = HH * hf + 16 * g;
@@ -542,7 +588,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_tc_train(TrArgs T, const f
         }
       }
     }
-    if (*abort_flag) break;
+    if (stop) break;
     // ---- output layer (float32 on the unrounded last activation), loss, dy
     {
       float y0 = 0.f, y1 = 0.f, y2 = 0.f;
@@ -613,7 +659,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_tc_train(TrArgs T, const f
     // ---- backward through the hidden layers
     for (int l = L - 1; l >= 0; --l) {
       const TcLayer Ly = A.L[l];
-      pre_mma();
+      if ((stop = pre_mma())) break;
       if (tid == 0) {
         // dW_l (+)= dZ_l^T A_l: A = dZ tile viewed MN-major (M = neurons, K = samples),
         // B = A_l viewed MN-major (N = input features, K = samples); K steps of 16 samples
@@ -638,7 +684,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_tc_train(TrArgs T, const f
           }
         }
       }
-      if (!sync_mma()) break;
+      sync_mma();
       if (l > 0) {
         // dZ_{l-1} = dA_l * [A_l > 0], rounded; A_l is the layer's (rounded)
         // input tile (H wide for l > 0); the pair splits its column groups
@@ -706,14 +752,15 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_tc_train(TrArgs T, const f
         }
       }
     }
+    if (stop) break;
     first_tile = false;
   }
   // ---- per-CTA partial dW: TMEM rows 0..H-1 (lane quarters 0..H/32-1), then dW_out
   tc_fence_before();
-  __syncthreads();
+  const bool aborted = __syncthreads_or(*abort_flag != 0) != 0;
   tc_fence_after();
   float* part = partial + (size_t)blockIdx.x * (size_t)T.n_params;
-  if (!*abort_flag && (warp & 3) < H / 32) {
+  if (!aborted && (warp & 3) < H / 32) {
     const int m = (warp & 3) * 32 + lane;            // output neuron of this lane
     for (int l = 0; l < L; ++l) {
       const uint32_t kpl = A.L[l].kp;
@@ -883,22 +930,25 @@ __global__ void __launch_bounds__(kT128Threads, 1) k_tc_train128(T128Args T, con
   bool first_tile = true;
   const int64_t n_tiles = (B + kT128Q - 1) / kT128Q;
 
-  auto pre_mma = [&]() {
+  // A timed-out wait sets abort_flag; the CTA stops at the next MMA's
+  // barrier, every thread alike (__syncthreads_or over their reads).
+  auto pre_mma = [&]() -> bool {
     fence_proxy_async();
     tc_fence_before();
-    __syncthreads();
+    const bool s = __syncthreads_or(*abort_flag != 0) != 0;
     tc_fence_after();
+    return s;
   };
-  auto commit_wait = [&]() -> bool {
+  auto commit_wait = [&]() {
     if (tid == 0) mma_commit(bar_mma);
     const bool ok = mbar_wait(bar_mma, phase);
     phase ^= 1u;
     tc_fence_after();
     if (!ok) { atomicOr(err, PFE_ITER_CAP); *abort_flag = 1; }
-    return ok;
   };
+  bool stop = false;
 
-  for (int64_t tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x) {
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int64_t row0 = tile * kT128Q;
     // ---- frequency encoding -> X_0 [q][k]: one (query, input) pair per item
     {
@@ -925,7 +975,7 @@ __global__ void __launch_bounds__(kT128Threads, 1) k_tc_train128(T128Args T, con
     // ---- forward
     float h[32];
     for (int l = 0; l < L; ++l) {
-      pre_mma();
+      if ((stop = pre_mma())) break;
       if (tid == 0) {
         const uint32_t a0 = smem_u32(smem + T.w_off[l]), b0 = smem_u32(smem + T.x_off[l]);
         const uint32_t a_sbo = T.kp[l] * 2 / 16 * 128;
@@ -937,7 +987,7 @@ __global__ void __launch_bounds__(kT128Threads, 1) k_tc_train128(T128Args T, con
           mma<false>(tmem + kT128Acc, ad, bd, id, ks > 0 ? 1u : 0u);
         }
       }
-      if (!commit_wait()) break;
+      commit_wait();
       float v[32];
       tmem_ld32(lane_addr + kT128Acc + 32 * hf, v);
       if (l < L - 1) {
@@ -954,7 +1004,7 @@ __global__ void __launch_bounds__(kT128Threads, 1) k_tc_train128(T128Args T, con
         for (int i = 0; i < 32; ++i) h[i] = fmaxf(v[i], 0.f);
       }
     }
-    if (*abort_flag) break;
+    if (stop) break;
     // ---- output layer: y[q][c] = sum_n W_out[c][n] h[n][q] (butterfly over the
     // warp's 32 neurons, then the four warps in order)
 #pragma unroll
@@ -1019,7 +1069,7 @@ __global__ void __launch_bounds__(kT128Threads, 1) k_tc_train128(T128Args T, con
     }
     // ---- backward through the hidden layers l = L-1 .. 1
     for (int l = L - 1; l >= 1; --l) {
-      pre_mma();
+      if ((stop = pre_mma())) break;
       if (tid == 0) {
         const uint32_t dz0 = smem_u32(dz), xl = smem_u32(smem + T.x_off[l]), wl = smem_u32(smem + T.w_off[l]);
         // dW_l [n][k] (+)= dZ_l [n][q] X_l [q][k]: K = the tile's queries
@@ -1035,7 +1085,7 @@ __global__ void __launch_bounds__(kT128Threads, 1) k_tc_train128(T128Args T, con
           mma<false>(tmem + kT128Acc, sdesc(wl + ks * 2 * w_rg, w_rg, 128),
                      sdesc(dz0 + ks * 2 * kT128RowGroup, kT128RowGroup, 128), ida, ks > 0 ? 1u : 0u);
       }
-      if (!commit_wait()) break;
+      commit_wait();
       // dZ_{l-1} [k][q] = rnd(dA_l * [X_l > 0]), feature row k = this thread's lane
       float v[32];
       tmem_ld32(lane_addr + kT128Acc + 32 * hf, v);
@@ -1050,19 +1100,19 @@ __global__ void __launch_bounds__(kT128Threads, 1) k_tc_train128(T128Args T, con
         *(uint4*)(dz + qrow_off(n, 4 * hf + c)) = pack8<PREC>(r);
       }
     }
-    if (*abort_flag) break;
+    if (stop) break;
     // ---- dW_0 of this tile through the free columns [384, 512): features
     // 0..127, then 128..143, each summed into registers
     {
       const uint32_t dz0 = smem_u32(dz), x0 = smem_u32(smem + T.x_off[0]);
-      pre_mma();
+      if ((stop = pre_mma())) break;
       if (tid == 0) {
         const uint32_t id = idesc(AB, 128, 0u, 1u);     // features 0..127
         for (int ks = 0; ks < kT128Q / 16; ++ks)
           mma<false>(tmem + kT128Acc, sdesc(dz0 + ks * 256, 128, kT128RowGroup),
                      sdesc(x0 + ks * 2 * x0_rg, x0_rg, 128), id, ks > 0 ? 1u : 0u);
       }
-      if (!commit_wait()) break;
+      commit_wait();
 #pragma unroll
       for (int j = 0; j < 4; ++j) {                     // warpgroup hf: features 64 hf .. 64 hf + 63
         float v[16];
@@ -1072,8 +1122,9 @@ __global__ void __launch_bounds__(kT128Threads, 1) k_tc_train128(T128Args T, con
       }
       {
         tc_fence_before();
-        __syncthreads();                                 // every thread has read the columns
+        stop = __syncthreads_or(*abort_flag != 0) != 0;  // every thread has read the columns
         tc_fence_after();
+        if (stop) break;
         if (tid == 0) {
           const uint32_t id = idesc(AB, 16, 0u, 1u);
           const uint32_t xb = x0 + (128 / 8) * 128;      // features 128.. (MN direction: 128 B per 8)
@@ -1081,7 +1132,7 @@ __global__ void __launch_bounds__(kT128Threads, 1) k_tc_train128(T128Args T, con
             mma<false>(tmem + kT128Acc, sdesc(dz0 + ks * 256, 128, kT128RowGroup),
                        sdesc(xb + ks * 2 * x0_rg, x0_rg, 128), id, ks > 0 ? 1u : 0u);
         }
-        if (!commit_wait()) break;
+        commit_wait();
         float v[16];
         tmem_ld16(lane_addr + kT128Acc, v);               // features 128..143; warpgroup hf takes 8 of them
 #pragma unroll
@@ -1092,10 +1143,10 @@ __global__ void __launch_bounds__(kT128Threads, 1) k_tc_train128(T128Args T, con
   }
   // ---- this CTA's partial gradient row
   tc_fence_before();
-  __syncthreads();
+  const bool aborted = __syncthreads_or(*abort_flag != 0) != 0;
   tc_fence_after();
   float* part = partial + (size_t)blockIdx.x * (size_t)T.n_params;
-  if (!*abort_flag) {
+  if (!aborted) {
     for (int l = 1; l < L; ++l) {
       float* dst = part + T.layer_off[l] + (int64_t)n * H + 64 * hf;
       for (int c0 = 0; c0 < 64; c0 += 16) {
@@ -1122,7 +1173,7 @@ __global__ void __launch_bounds__(kT128Threads, 1) k_tc_train128(T128Args T, con
   red[(hf * 3 + 1) * H + n] = dwo1;
   red[(hf * 3 + 2) * H + n] = dwo2;
   __syncthreads();
-  if (!*abort_flag)
+  if (!aborted)
     for (int i = tid; i < 3 * H; i += kT128Threads) part[T.layer_off[L] + i] = red[i] + red[3 * H + i];
   if (loss) {
     for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
@@ -1218,7 +1269,8 @@ bool plan(const pf_field* f, TcArgs* A, bool for_train = false) {
   // as many groups (tiles in flight) as TMEM (512 columns) and shared memory allow
   for (A->n_groups = 4; A->n_groups >= 1; A->n_groups /= 2) {
     A->wout_off = A->a_off + (uint32_t)A->n_groups * A->a_bytes;
-    A->bar_off = (A->wout_off + 3 * H * 4 + 15) / 16 * 16;
+    A->ypart_off = (A->wout_off + 3 * H * 4 + 15) / 16 * 16;
+    A->bar_off = A->ypart_off + (uint32_t)A->n_groups * 3 * kTileM * 4;
     A->smem_bytes = A->bar_off + 64;
     if (A->n_groups * H <= 512 && A->smem_bytes <= 227 * 1024) break;
   }
@@ -1278,16 +1330,22 @@ pf_status pf_tc_forward(pf_ctx* ctx, const pf_field* f, const float* q, int64_t 
   A.w_out = f->w + f->layer_off[f->n_layers - 1];
   int64_t tiles = (B_max + kTileM - 1) / kTileM;
   int grid = (int)std::min<int64_t>((tiles + A.n_groups - 1) / A.n_groups, (int64_t)ctx->num_sms);
+  // two threads per row where shared memory holds at most two tiles in
+  // flight (16-bit fields, 12 frequencies: the encoding splits at feature 72)
+  const bool pair = f->desc.prec != PF_PREC_FP8 && A.n_groups <= 2 && A.in_freqs == 12 && A.L[0].kp == 144;
+  const int tpr = pair ? 2 : 1;
   auto launch = [&](auto kern) -> pf_status {
     PF_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)A.smem_bytes));
-    kern<<<grid, kThreads * A.n_groups, A.smem_bytes, ctx->stream>>>(A, q, B_max, B_dev, out, slot_idx, slot_alb,
-                                                                      slot_li, ctx->err_dev);
+    kern<<<grid, kThreads * tpr * A.n_groups, A.smem_bytes, ctx->stream>>>(A, q, B_max, B_dev, out, slot_idx,
+                                                                            slot_alb, slot_li, ctx->err_dev);
     PF_CUDA(ctx, cudaGetLastError());
     return PF_OK;
   };
-  if (f->desc.prec == PF_PREC_BF16) return launch(k_tc_forward<PF_PREC_BF16>);
-  if (f->desc.prec == PF_PREC_F16) return launch(k_tc_forward<PF_PREC_F16>);
-  return launch(k_tc_forward<PF_PREC_FP8>);
+  if (f->desc.prec == PF_PREC_BF16)
+    return pair ? launch(k_tc_forward<PF_PREC_BF16, 2>) : launch(k_tc_forward<PF_PREC_BF16, 1>);
+  if (f->desc.prec == PF_PREC_F16)
+    return pair ? launch(k_tc_forward<PF_PREC_F16, 2>) : launch(k_tc_forward<PF_PREC_F16, 1>);
+  return launch(k_tc_forward<PF_PREC_FP8, 1>);
 }
 
 namespace {
