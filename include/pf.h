@@ -312,6 +312,17 @@ pf_status pf_field_set_weights(pf_ctx* ctx, pf_field* field, const float* src_de
  * amax = max|W| for the weights and max|layer input| over B calibration
  * queries (unquantised pass) for the activations; codes = e4m3(x / s). */
 pf_status pf_field_calibrate_fp8(pf_ctx* ctx, pf_field* field, const float* q_dev, int64_t B);
+/* Frequency encoding gamma (Sec. 3.4) of B field queries, as the tensor-core
+ * fields form it for their first layer (before the operand rounding):
+ * out_dev [B][12 F] = for input d = 0..5 (x, y, z, theta', phi', g), for
+ * k = 0..F-1: sin(2^k pi v_d), cos(2^k pi v_d), float32.  Sine and cosine are
+ * the library's own float32 steps: at k = 0, 4, 8, ... a turn-based
+ * evaluation of frac(2^(k-1) v_d), in between the double-angle formulas
+ * (every feature within 6e-6 of the exact value for |v| <= 1).
+ * q_dev [B*6] and out_dev are device pointers (caller-owned); F = in_freqs in
+ * 1..16.  B = 0 is a no-op; B < 0, a NULL pointer or F out of range is
+ * PF_ERR_INVALID_ARG.  Enqueued on the context's stream. */
+pf_status pf_field_encode(pf_ctx* ctx, const float* q_dev, int64_t B, int in_freqs, float* out_dev);
 /* Field forward pass: out_dev [B*3] = L' predictions for queries q_dev [B*6]. */
 pf_status pf_field_forward(pf_ctx* ctx, const pf_field* field, const float* q_dev, int64_t B, float* out_dev);
 /* Field backward pass: dw_dev [n_params] = sum_b (dL'_b/dW)^T dy_b (f32, bf16

@@ -84,6 +84,7 @@ SIGNATURES = {
     "pf_field_calibrate_fp8": (I, [P, P, P, I64]),
     "pf_field_forward": (I, [P, P, P, I64, P]),
     "pf_field_backward": (I, [P, P, P, P, I64, P]),
+    "pf_field_encode": (I, [P, P, I64, I, P]),
     "pf_field_loss_gradient": (I, [P, P, P, P, I64, P, P]),
     "pf_field_adam": (I, [P, P, P, F, F, F, F]),
     "pf_train_field": (I, [P, P, C.POINTER(PfTrainDesc), P, P]),

@@ -375,6 +375,16 @@ def image_rmse(ctx: Context, a: torch.Tensor, b: torch.Tensor) -> float:
     return out.value
 
 
+def field_encode(ctx: Context, q: torch.Tensor, in_freqs: int = 12) -> torch.Tensor:
+    """Frequency encoding of queries q [B, 6] (float32, device): [B, 12 in_freqs]
+    features, [input][k][sin, cos] (pf_field_encode)."""
+    _need(q, torch.float32, name="q")
+    B = q.numel() // 6
+    out = torch.empty((B, 12 * in_freqs), dtype=torch.float32, device=q.device)
+    ctx.check(ctx.lib.pf_field_encode(ctx.h, _ptr(q), B, int(in_freqs), _ptr(out)))
+    return out
+
+
 class FieldFunction(torch.autograd.Function):
     """Differentiable field evaluation: y = P_phi(q) with gradients w.r.t. the
     flat weight vector w, computed by the library's backward kernel."""

@@ -688,6 +688,53 @@ pf_status pf_field_forward_impl(pf_ctx* ctx, const pf_field* f, const float* q, 
   return pf_simt_forward(ctx, f, q, B_max, B_dev, out, slot_idx, slot_alb, slot_li);
 }
 
+// gamma of one (query, input) pair per thread; a warp's 32 pairs own one
+// contiguous range of 64 F floats, so each lane stages its 2F features in
+// shared memory (rows padded to 2F + 1 floats: no bank conflicts) and the
+// warp then writes the range with consecutive lanes on consecutive floats.
+__global__ void k_field_encode(const float* __restrict__ q, int64_t n_pairs, int F, float* __restrict__ out) {
+  extern __shared__ float pf_enc_stage[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int W = 2 * F, Wp = W + 1;
+  float* st = pf_enc_stage + warp * 32 * Wp;
+  const float inv_w = 1.0f / (float)W;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + warp * 32; base < n_pairs;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + lane;          // pair i = (query i / 6, input i % 6)
+    if (i < n_pairs) {
+      const float v = __ldg(q + i);
+      float s = 0.f, c = 1.f;
+      for (int k = 0; k < F; ++k) {
+        pff::freq_next(v, k, s, c);
+        st[lane * Wp + 2 * k] = s;
+        st[lane * Wp + 2 * k + 1] = c;
+      }
+    }
+    __syncwarp();
+    const int n_out = (int)(n_pairs - base < 32 ? n_pairs - base : 32) * W;
+    float* o = out + base * W;
+    for (int e = lane; e < n_out; e += 32) {
+      const int r = (int)(((float)e + 0.5f) * inv_w);   // e / W (e < 1024: the float quotient cannot cross an integer)
+      o[e] = st[r * Wp + (e - r * W)];
+    }
+    __syncwarp();
+  }
+}
+
+extern "C" pf_status pf_field_encode(pf_ctx* ctx, const float* q, int64_t B, int F, float* out) {
+  if (!ctx) return PF_ERR_INVALID_ARG;
+  if (B < 0 || F < 1 || F > 16) return pf_fail(ctx, PF_ERR_INVALID_ARG, "need B >= 0 and 1 <= in_freqs <= 16");
+  if (B == 0) return PF_OK;
+  if (!q || !out) return pf_fail(ctx, PF_ERR_INVALID_ARG, "q_dev and out_dev must not be NULL");
+  DeviceGuard dg(ctx->device);
+  const int64_t n = B * 6;
+  const size_t smem = (size_t)8 * 32 * (2 * F + 1) * sizeof(float);   // 8 warps per block
+  k_field_encode<<<(unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 8), 256, smem, ctx->stream>>>(
+      q, n, F, out);
+  PF_CUDA(ctx, cudaGetLastError());
+  return PF_OK;
+}
+
 extern "C" pf_status pf_field_forward(pf_ctx* ctx, const pf_field* f, const float* q, int64_t B, float* out) {
   if (!ctx || !f || B < 0) return pf_fail(ctx, PF_ERR_INVALID_ARG, "bad field forward arguments");
   if (B == 0) return PF_OK;

@@ -260,19 +260,37 @@ __global__ void __launch_bounds__(kFwdMaxThreads, 1) k_tc_forward(TcArgs A, cons
   // A timed-out wait sets abort_flag; the group stops at its next barrier,
   // all of its threads alike (the barrier ORs their reads of the flag).
   bool stop = false;
-  for (int64_t tile = (int64_t)blockIdx.x * NG + wg; tile < n_tiles; tile += (int64_t)gridDim.x * NG) {
+  // this thread's query inputs (3 with TPR = 2), loaded one tile ahead so
+  // that the loads are in flight while the group works on the current tile
+  constexpr int NQ = TPR == 2 ? 3 : 6;
+  const int q0 = TPR == 2 ? 3 * half : 0;
+  const int64_t t_step = (int64_t)gridDim.x * NG;
+  float qn[NQ];
+  auto load_q = [&](int64_t t) {
+    const int64_t r = t * kTileM + ltid;
+    const bool ok = t < n_tiles && r < B;
+#pragma unroll
+    for (int d = 0; d < NQ; ++d) qn[d] = ok ? __ldg(q + 6 * r + q0 + d) : 0.f;
+  };
+  load_q((int64_t)blockIdx.x * NG + wg);
+  for (int64_t tile = (int64_t)blockIdx.x * NG + wg; tile < n_tiles; tile += t_step) {
     const int64_t row = tile * kTileM + ltid;
     const bool valid = row < B;
+    float qv[NQ];
+#pragma unroll
+    for (int d = 0; d < NQ; ++d) qv[d] = qn[d];
+    load_q(tile + t_step);
+    // the render epilogue's inputs of this row, also in flight meanwhile
+    uint32_t sl = 0;
+    float al0 = 0.f, al1 = 0.f, al2 = 0.f;
+    if (slot_idx && valid && half == 0) {
+      sl = __ldg(slot_idx + row);
+      al0 = __ldg(slot_alb + 3 * row + 0); al1 = __ldg(slot_alb + 3 * row + 1); al2 = __ldg(slot_alb + 3 * row + 2);
+    }
     // ---- encoding of this thread's query into the A tile (K = kp0)
     if (TPR == 2) {
-      float qv[3];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) qv[d] = valid ? __ldg(q + 6 * row + 3 * half + d) : 0.f;
       encode_half<PREC>(a_tile, kp0, ltid, qv, half);
     } else {
-      float qv[6];
-#pragma unroll
-      for (int d = 0; d < 6; ++d) qv[d] = valid ? __ldg(q + 6 * row + d) : 0.f;
       const float s = FP8 ? A.L[0].inv_s_in : 1.f;   // input scale of layer 0 (fp8)
       encode_query<PREC>(a_tile, kp0, ltid, qv, F, s);
     }
@@ -355,10 +373,9 @@ __global__ void __launch_bounds__(kFwdMaxThreads, 1) k_tc_forward(TcArgs A, cons
     }
     if (valid) {
       if (slot_idx) {
-        uint32_t sl = slot_idx[row];
-        slot_li[3 * (size_t)sl + 0] = slot_alb[3 * row + 0] * exp10f(-A.psi * y0);
-        slot_li[3 * (size_t)sl + 1] = slot_alb[3 * row + 1] * exp10f(-A.psi * y1);
-        slot_li[3 * (size_t)sl + 2] = slot_alb[3 * row + 2] * exp10f(-A.psi * y2);
+        slot_li[3 * (size_t)sl + 0] = al0 * exp10f(-A.psi * y0);
+        slot_li[3 * (size_t)sl + 1] = al1 * exp10f(-A.psi * y1);
+        slot_li[3 * (size_t)sl + 2] = al2 * exp10f(-A.psi * y2);
       } else {
         out[3 * row + 0] = y0;
         out[3 * row + 1] = y1;

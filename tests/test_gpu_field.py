@@ -169,3 +169,38 @@ def test_training_reduces_loss(pf_ctx, small_cache, prec, hidden):
     loss = fld.train(cache, steps=60, batch=4096, lr=1e-2, seed=3)
     assert np.all(np.isfinite(loss))
     assert loss[-10:].mean() < 0.5 * loss[:5].mean(), (loss[:5], loss[-10:])
+
+
+@pytest.mark.parametrize("freqs", [12, 7, 16, 1])
+def test_encoding_matches_float32_oracle(pf_ctx, freqs):
+    """pf_field_encode (Sec. 3.4's gamma in the tensor-core fields' float32
+    steps) is bit-identical to the oracle's float32 encoding, on several
+    launch blocks with a ragged tail and on edge inputs (0, 1, 1/2, values
+    just below 1, negative g, a denormal)."""
+    import oracle
+    q = _queries(3 * 256 + 41, seed=5)
+    edge = np.array([[0.0, 1.0, 0.5, 0.25, np.nextafter(np.float32(1), np.float32(0)), -0.75],
+                     [1e-40, 0.999, 0.125, 0.75, 0.3333333, 0.9],
+                     [0.5, 0.0, 1.0, 0.0625, 0.1, -0.9]], np.float32)
+    q = np.concatenate([q, edge]).astype(np.float32)
+    got = api.field_encode(pf_ctx, torch.from_numpy(q).cuda(), freqs).cpu().numpy()
+    ref = oracle.encode_f32(q, freqs)
+    assert got.shape == (q.shape[0], 12 * freqs)
+    assert np.array_equal(got.astype(np.float64), ref)
+    # and within the pinned accuracy of the exact features
+    k = np.arange(freqs)
+    a = np.pi * (2.0 ** k)[None, None, :] * q.astype(np.float64)[:, :, None]
+    exact = np.stack([np.sin(a), np.cos(a)], axis=3).reshape(q.shape[0], 12 * freqs)
+    assert np.abs(got - exact).max() < 6e-6
+
+
+def test_encoding_refuses_bad_arguments(pf_ctx):
+    q = torch.zeros(6, dtype=torch.float32, device="cuda")
+    out = torch.zeros(12, dtype=torch.float32, device="cuda")
+    lib = pf_ctx.lib
+    assert lib.pf_field_encode(pf_ctx.h, q.data_ptr(), 1, 0, out.data_ptr()) == 1
+    assert lib.pf_field_encode(pf_ctx.h, q.data_ptr(), 1, 17, out.data_ptr()) == 1
+    assert lib.pf_field_encode(pf_ctx.h, q.data_ptr(), -1, 1, out.data_ptr()) == 1
+    assert lib.pf_field_encode(pf_ctx.h, None, 1, 1, out.data_ptr()) == 1
+    assert lib.pf_field_encode(pf_ctx.h, q.data_ptr(), 0, 1, None) == 0     # empty batch: no-op
+    assert api.field_encode(pf_ctx, torch.zeros((0, 6), dtype=torch.float32, device="cuda")).shape == (0, 144)
