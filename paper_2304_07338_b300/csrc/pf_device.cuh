@@ -349,7 +349,10 @@ struct Walk {
   int lx, ly, lz;  // crossings left along each axis before the ray leaves the grid
   int ox, oy, oz;  // linear-index offset of a crossing along each axis
   int idx, na;     // current brick, axis of the next crossing
+  int noff;        // linear-index offset of the next crossing (axis na)
+  bool more;       // the next crossing stays inside the grid
   float m, m_next; // majorants of the current and the next brick
+  float t_exit;    // plane parameter of the next crossing (the current brick's exit)
   __device__ __forceinline__ static float load(const Vol& V, int i) {
     if (S) {
       extern __shared__ float pf_walk_smem[];
@@ -372,11 +375,16 @@ struct Walk {
       l = 0; off = 0; tn = __int_as_float(0x7f800000); dt = tn;
     }
   }
+  // the next crossing: its axis, exit parameter, offset and majorant, chosen
+  // once per brick (the step and the caller's exit test reuse them)
   __device__ __forceinline__ void plan(const Vol& V) {
-    na = (tx <= ty && tx <= tz) ? 0 : (ty <= tz ? 1 : 2);
-    const int left = na == 0 ? lx : (na == 1 ? ly : lz);
-    const int off = na == 0 ? ox : (na == 1 ? oy : oz);
-    m_next = left > 0 ? load(V, idx + off) : 0.0f;
+    const bool bx = tx <= ty && tx <= tz, by = !bx && ty <= tz;
+    na = bx ? 0 : (by ? 1 : 2);
+    const int left = bx ? lx : (by ? ly : lz);
+    noff = bx ? ox : (by ? oy : oz);
+    t_exit = bx ? tx : (by ? ty : tz);
+    more = left > 0;
+    m_next = more ? load(V, idx + noff) : 0.0f;
   }
   __device__ __forceinline__ void init(const Vol& V, V3 o, V3 d, float t) {
     int cx, cy, cz;
@@ -387,15 +395,14 @@ struct Walk {
     m = load(V, idx);
     plan(V);
   }
-  __device__ __forceinline__ float exit_t() const { return na == 0 ? tx : (na == 1 ? ty : tz); }
+  __device__ __forceinline__ float exit_t() const { return t_exit; }
   // step into the next brick (branch-free selects); false when the ray
   // leaves the grid
   __device__ __forceinline__ bool step(const Vol& V) {
+    if (!more) return false;
     const bool ax = na == 0, ay = na == 1, az = na == 2;
-    const int left = ax ? lx : (ay ? ly : lz);
-    if (left == 0) return false;
     lx -= (int)ax; ly -= (int)ay; lz -= (int)az;
-    idx += ax ? ox : (ay ? oy : oz);
+    idx += noff;
     const float sx = tx + dtx, sy = ty + dty, sz = tz + dtz;
     tx = ax ? sx : tx; ty = ay ? sy : ty; tz = az ? sz : tz;
     m = m_next;
