@@ -452,7 +452,7 @@ __device__ __forceinline__ bool delta_track(const Vol& V, V3 o, V3 d, float t, f
   for (;;) {
     float seg = tc - t;
     if (seg < 0.0f) seg = 0.0f;
-    while (!(W.m > 0.0f && tau < W.m * seg)) {
+    while (!(tau < W.m * seg)) {          // tau >= 0: a brick of majorant 0 is crossed
       tau = tau - W.m * seg;
       t = tc;
       if (t >= t_end) return false;
@@ -488,7 +488,7 @@ __device__ __forceinline__ float ratio_track(const Vol& V, V3 o, V3 d, float t_e
   for (;;) {
     float seg = tc - t;
     if (seg < 0.0f) seg = 0.0f;
-    while (!(W.m > 0.0f && tau < W.m * seg)) {
+    while (!(tau < W.m * seg)) {          // tau >= 0: a brick of majorant 0 is crossed
       tau = tau - W.m * seg;
       t = tc;
       if (t >= t_end) return T;

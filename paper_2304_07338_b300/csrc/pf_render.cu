@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(128, 8) k_nee(Vol V, Vol Vw, DevLights L, floa
     while (has && !done && !need_tau && cnt < kNeePool) {
       float seg = tc - t;
       if (seg < 0.0f) seg = 0.0f;
-      if (W.m > 0.0f && tau < W.m * seg) {
+      if (tau < W.m * seg) {           // tau >= 0: never true in a brick of majorant 0
         const float m = W.m;
         t = t + tau / m;
         if (THIN) {

@@ -92,6 +92,17 @@ def test_own_log_accuracy(orc):
     assert orc.lnf(np.float32([1.0]))[0] == 0.0
 
 
+def test_tracking_budgets_are_never_negative(orc):
+    """Every value 1 - u the uniforms can give (u = k 2^-24) has ln <= 0, so
+    the trackers' optical-depth budgets -ln(1 - u) are >= 0 and a brick of
+    majorant 0 never holds a tentative collision (tau < 0 * seg is false);
+    the trackers rely on this instead of testing the majorant."""
+    k = np.arange(1, (1 << 24) + 1, dtype=np.float64)
+    x = (k * 2.0 ** -24).astype(np.float32)
+    y = orc.lnf(x)
+    assert y.max() <= 0.0 and y[-1] == 0.0
+
+
 def test_own_sincos_accuracy(orc):
     u = (np.arange(0, 1 << 24, 97) * 2.0 ** -24).astype(np.float32)
     s, c = orc.sincos2pif(u)
