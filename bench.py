@@ -790,6 +790,8 @@ def main():
     hbm, bf16, bf16s, src = peaks()
     gp = gemm_peaks(dev) if not args.no_extras else {}
     cam_ms, cam_n = stages["camera"]
+    pooled = [e for e in (args.brick_primary, args.brick_shadow) if e > args.brick]
+    grid_launches = len(pooled) + 1 + len(pooled)     # k_pool_majorants per pooled grid, k_border_grid per grid
     nee_ms, nee_n = stages["nee"]
     fld_ms, fld_n = stages["field"]
     cmp_ms, cmp_n = stages["compose"]
@@ -847,8 +849,10 @@ def main():
         "roofline": roof,
         "clocks": clk,
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        # kernels per frame: camera samples; scan (3) + placement + k_nee + k_nee_sum; field; compose
-        "gpu_launches": cam_n + 6 * nee_n + fld_n + cmp_n,
+        # kernels per frame: the pooled grids (camera rays; shadow rays when coarser than
+        # the brick) and the walks' bordered copies of the distinct grids; camera samples;
+        # scan (3) + placement + k_nee + k_nee_sum; field; compose
+        "gpu_launches": grid_launches * cam_n + cam_n + 6 * nee_n + fld_n + cmp_n,
     }
     line["setup"] = setup
     if not args.no_extras:

@@ -181,6 +181,8 @@ struct Vol {
   int tf_n;
   const float* mg;    // brick majorants (x fastest)
   int gx, gy, gz, B;  // brick grid and brick edge (voxels)
+  const float* mgw;   // the same majorants with a border of kBorder zero bricks on every side (the walks' copy)
+  int pgx, pgy;       // its extent along x and y (gx + 2 kBorder, gy + 2 kBorder)
   float wx, wy, wz;   // brick edge in world units, B / n (IEEE division)
   const void* tiled;  // voxels in 4x4x4 tiles (same values), or null
   int tnx, tny;       // tiles along x and y
@@ -339,27 +341,32 @@ constexpr int kMaxTrackSteps = 1 << 24;
 // (plane - o) * inv and each further plane adds w * |inv| (register-only,
 // no division per crossing).  Plane rounding stays far below the half-voxel
 // margin of the brick majorants.  The walk keeps the linear brick index and
-// the number of crossings left per axis, and loads the majorant of the next
-// brick one crossing ahead so that the load's latency overlaps the work in
-// the current brick.  S: the majorants are read from a copy at the start of
-// the block's dynamic shared memory instead of global memory.
-template <bool S>
+// loads the majorant of the next brick one crossing ahead so that the load's
+// latency overlaps the work in the current brick.
+//
+// G: the walk reads V.mgw, the majorants with a border of kBorder = 2 zero
+// bricks.  A ray inside the box ends (t >= t_end, at most the box exit)
+// within rounding of where it leaves the grid, far less than a brick's width
+// in t, so past the grid it enters at most the first border layer (once per
+// axis, near an edge or corner), whose majorant 0 holds no tentative
+// collision and leaves the budget unchanged: no crossing counts are needed.
+// The next brick's majorant is loaded one crossing ahead, from the second
+// layer at most.  !G: the walk reads
+// V.mg and counts the crossings left per axis, ending where the grid ends
+// (for callers that cannot allocate the bordered copy).  Both take the same
+// float steps and give the same results.
+constexpr int kBorder = 2;   // zero bricks around the walks' copy of the brick grid
+template <bool G>
 struct Walk {
   float tx, ty, tz, dtx, dty, dtz;
-  int lx, ly, lz;  // crossings left along each axis before the ray leaves the grid
+  int lx, ly, lz;  // !G: crossings left along each axis before the ray leaves the grid
   int ox, oy, oz;  // linear-index offset of a crossing along each axis
   int idx, na;     // current brick, axis of the next crossing
   int noff;        // linear-index offset of the next crossing (axis na)
-  bool more;       // the next crossing stays inside the grid
+  bool more;       // !G: the next crossing stays inside the grid
   float m, m_next; // majorants of the current and the next brick
   float t_exit;    // plane parameter of the next crossing (the current brick's exit)
-  __device__ __forceinline__ static float load(const Vol& V, int i) {
-    if (S) {
-      extern __shared__ float pf_walk_smem[];
-      return pf_walk_smem[i];
-    }
-    return __ldg(V.mg + i);
-  }
+  __device__ __forceinline__ static float load(const Vol& V, int i) { return __ldg((G ? V.mgw : V.mg) + i); }
   __device__ __forceinline__ static void axis(float o, float d, float t, float w, int g, int stride, int& c, int& l,
                                               int& off, float& tn, float& dt) {
     const float p = o + t * d;
@@ -380,28 +387,33 @@ struct Walk {
   __device__ __forceinline__ void plan(const Vol& V) {
     const bool bx = tx <= ty && tx <= tz, by = !bx && ty <= tz;
     na = bx ? 0 : (by ? 1 : 2);
-    const int left = bx ? lx : (by ? ly : lz);
     noff = bx ? ox : (by ? oy : oz);
     t_exit = bx ? tx : (by ? ty : tz);
-    more = left > 0;
-    m_next = more ? load(V, idx + noff) : 0.0f;
+    if (G) {
+      m_next = load(V, idx + noff);
+    } else {
+      const int left = bx ? lx : (by ? ly : lz);
+      more = left > 0;
+      m_next = more ? load(V, idx + noff) : 0.0f;
+    }
   }
   __device__ __forceinline__ void init(const Vol& V, V3 o, V3 d, float t) {
     int cx, cy, cz;
+    const int sy = G ? V.pgx : V.gx, sz = G ? V.pgx * V.pgy : V.gx * V.gy;
     axis(o.x, d.x, t, V.wx, V.gx, 1, cx, lx, ox, tx, dtx);
-    axis(o.y, d.y, t, V.wy, V.gy, V.gx, cy, ly, oy, ty, dty);
-    axis(o.z, d.z, t, V.wz, V.gz, V.gx * V.gy, cz, lz, oz, tz, dtz);
-    idx = cx + V.gx * (cy + V.gy * cz);
+    axis(o.y, d.y, t, V.wy, V.gy, sy, cy, ly, oy, ty, dty);
+    axis(o.z, d.z, t, V.wz, V.gz, sz, cz, lz, oz, tz, dtz);
+    idx = G ? (cx + kBorder) + sy * (cy + kBorder) + sz * (cz + kBorder) : cx + sy * cy + sz * cz;
     m = load(V, idx);
     plan(V);
   }
   __device__ __forceinline__ float exit_t() const { return t_exit; }
   // step into the next brick (branch-free selects); false when the ray
-  // leaves the grid
+  // leaves the grid (!G only)
   __device__ __forceinline__ bool step(const Vol& V) {
-    if (!more) return false;
+    if (!G && !more) return false;
     const bool ax = na == 0, ay = na == 1, az = na == 2;
-    lx -= (int)ax; ly -= (int)ay; lz -= (int)az;
+    if (!G) { lx -= (int)ax; ly -= (int)ay; lz -= (int)az; }
     idx += noff;
     const float sx = tx + dtx, sy = ty + dty, sz = tz + dtz;
     tx = ax ? sx : tx; ty = ay ? sy : ty; tz = az ? sz : tz;
@@ -440,10 +452,10 @@ struct Uniforms {
 // (expensive) lookups together instead of alternating lookups and
 // (cheap) brick crossings.  Every lane performs the same float operations
 // in the same order as a flat event loop would.
-template <int DT, bool S = false>
+template <int DT, bool G = true>
 __device__ __forceinline__ bool delta_track(const Vol& V, V3 o, V3 d, float t, float t_end, Rng& rng, float* t_hit,
                                             uint32_t* err, uint32_t& fetches) {
-  Walk<S> W;
+  Walk<G> W;
   W.init(V, o, d, t);
   Uniforms U;
   float tau = -own_lnf(1.0f - U.next(rng));
@@ -475,10 +487,10 @@ __device__ __forceinline__ bool delta_track(const Vol& V, V3 o, V3 d, float t, f
 // Ratio-tracking transmittance over [0, t_end) with the brick majorants: at
 // each tentative collision T *= max(0, 1 - sigma_t / majorant); one uniform
 // per tentative collision (its budget).  Same nested loop as delta_track.
-template <int DT, bool S = false>
+template <int DT, bool G = true>
 __device__ __forceinline__ float ratio_track(const Vol& V, V3 o, V3 d, float t_end, Rng& rng, uint32_t* err,
                                              uint32_t& fetches) {
-  Walk<S> W;
+  Walk<G> W;
   W.init(V, o, d, 0.0f);
   Uniforms U;
   float T = 1.0f, t = 0.0f;
@@ -563,10 +575,13 @@ inline pfd::Vol pf_make_vol(const pf_volume* v, float majorant, const float* gri
   V.sigma_scale = v->sigma_scale; V.albedo = v->albedo; V.majorant = majorant;
   V.tf = (const float4*)v->tf_lut_dev; V.tf_n = v->tf_n;
   V.mg = grid;
+  V.mgw = nullptr;
   V.B = B;
   V.gx = (v->nx + B - 1) / B;
   V.gy = (v->ny + B - 1) / B;
   V.gz = (v->nz + B - 1) / B;
+  V.pgx = V.gx + 2 * pfd::kBorder;
+  V.pgy = V.gy + 2 * pfd::kBorder;
   V.wx = (float)B / (float)v->nx;
   V.wy = (float)B / (float)v->ny;
   V.wz = (float)B / (float)v->nz;

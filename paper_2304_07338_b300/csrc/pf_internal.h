@@ -15,7 +15,7 @@ enum : uint32_t { PFE_ITER_CAP = 1u, PFE_NONFINITE = 2u, PFE_OVERFLOW = 4u };
 enum ScratchSlot {
   WS_REDUCE = 0, WS_SCAN, WS_QUERY, WS_TARGET, WS_ACT, WS_GRAD, WS_SAMPLES, WS_SLOT_LD, WS_SLOT_ALB,
   WS_SLOT_LI, WS_COMPACT_Q, WS_COMPACT_IDX, WS_LOSS, WS_MISC, WS_GRID, WS_COMPACT_DIR, WS_CELL_HIST, WS_CELL_OFF, WS_CELL_KEY, WS_CELL_PERM, WS_VMASK, WS_GRID_PRIMARY, WS_GRID_SHADOW, WS_HASH_X, WS_HASH_DX, WS_TRACE_SLOTS, WS_TRACE_POS, WS_TRACE_NREC, WS_TRACE_CURSOR, WS_TRACE_TALLY,
-  WS_TRACE_OPOS, WS_NEE_CONTRIB, WS_KNN_LIST, WS_COUNT
+  WS_TRACE_OPOS, WS_NEE_CONTRIB, WS_KNN_LIST, WS_GRID_WALK, WS_GRID_PRIMARY_WALK, WS_GRID_SHADOW_WALK, WS_COUNT
 };
 
 struct pf_ctx {
@@ -114,6 +114,11 @@ pf_status pf_majorant_impl(pf_ctx* ctx, const pf_volume* vol, float* out);
 pf_status pf_check_lights(pf_ctx* ctx, const pf_light* lights, int n);
 // Brick majorants of a volume: the caller's array, or computed into scratch.
 pf_status pf_grid_for(pf_ctx* ctx, const pf_volume* vol, const float** grid);
+// Copy of a brick-majorant grid (gx x gy x gz, x fastest) with a border of
+// two zero bricks on every side, (gx + 4) x (gy + 4) x (gz + 4): the grid the
+// trackers' walks read (scratch slot `slot`).  PF_ERR_INVALID_ARG when the
+// bordered grid has 2^31 bricks or more.
+pf_status pf_bordered_grid(pf_ctx* ctx, const float* grid, int gx, int gy, int gz, int slot, const float** out);
 
 // Device-wide exclusive scan of u32 counts into u64 offsets (n+1 entries).
 pf_status pf_scan_u32(pf_ctx* ctx, const uint32_t* in, uint64_t* out, int64_t n);

@@ -269,10 +269,13 @@ __global__ void __launch_bounds__(128, 5) k_camera_samples_march(PF_CAMERA_ARGS)
 #undef PF_CAMERA_PASS
 
 // Majorant of the brick of V holding x, its index clamped into brick `widx`
-// of the coarser grid Vw (so that it never exceeds Vw's majorant there).
+// of the coarser grid Vw (so that it never exceeds Vw's majorant there);
+// widx indexes Vw's bordered copy (the walk's), and names a brick inside the
+// grid (a tentative collision never lies in a border brick).
 __device__ __forceinline__ float thin_majorant(const Vol& V, const Vol& Vw, int widx, V3 x) {
   const int f = Vw.B / V.B;
-  const int wx = widx % Vw.gx, wy = (widx / Vw.gx) % Vw.gy, wz = widx / (Vw.gx * Vw.gy);
+  const int wx = widx % Vw.pgx - kBorder, wy = (widx / Vw.pgx) % Vw.pgy - kBorder,
+            wz = widx / (Vw.pgx * Vw.pgy) - kBorder;
   const int cx = min(max((int)floorf(x.x / V.wx), wx * f), min(wx * f + f, V.gx) - 1);
   const int cy = min(max((int)floorf(x.y / V.wy), wy * f), min(wy * f + f, V.gy) - 1);
   const int cz = min(max((int)floorf(x.z / V.wz), wz * f), min(wz * f + f, V.gz) - 1);
@@ -339,7 +342,7 @@ __global__ void __launch_bounds__(128, 8) k_nee(Vol V, Vol Vw, DevLights L, floa
   V3 x = v3(0.5f, 0.5f, 0.5f), wl = v3(0.f, 0.f, 1.f), E = v3(0.f, 0.f, 0.f);
   float ph = 0.f, T = 1.0f, t = 0.0f, tau = 0.0f, tc = 0.0f, tend = 0.0f, d2l = 0.0f;
   int it = 0;
-  Walk<false> W;
+  Walk<true> W;
   Uniforms U;                   // THIN: uniforms drawn in the walk
   int un = 0, ur = 0;           // !THIN: budgets buffered in ptau, read position
   bool need_tau = false;        // !THIN: the next budget is still to be taken
@@ -591,7 +594,7 @@ __global__ void __launch_bounds__(128, 8) k_path_samples(Vol V, DevLights L, Cam
     float t = t0;
     for (int j = 1; j <= max_bounces; ++j) {
       float th;
-      if (!delta_track<DT>(V, o, d, t, t1, rng, &th, err, nfetch)) break;
+      if (!delta_track<DT, false>(V, o, d, t, t1, rng, &th, err, nfetch)) break;
       V3 x = along(o, d, th);
       float sig; V3 alb;
       medium_at<DT>(V, x, &sig, &alb);
@@ -602,7 +605,7 @@ __global__ void __launch_bounds__(128, 8) k_path_samples(Vol V, DevLights L, Cam
         float a0, a1, tend = 0.f;
         if (box_hit(x, wl, &a0, &a1)) tend = mn(a1, dist);
         Rng rs(seed, TAG_SHADOW, shadow_item((uint64_t)pix, j, l), (uint32_t)k);
-        float T = ratio_track<DT>(V, x, wl, tend, rs, err, nfetch);
+        float T = ratio_track<DT, false>(V, x, wl, tend, rs, err, nfetch);
         float ph = hg_eval(g, dot(d, wl));
         Lr = v3(Lr.x + ph * T * E.x, Lr.y + ph * T * E.y, Lr.z + ph * T * E.z);
       }
@@ -1016,6 +1019,13 @@ extern "C" pf_status pf_render_neural(pf_ctx* ctx, const pf_volume* vol, const p
   Vol Vp, Vs;
   PF_TRY(pooled_vol(vol->brick_primary, WS_GRID_PRIMARY, &Vp));
   PF_TRY(pooled_vol(vol->brick_shadow, WS_GRID_SHADOW, &Vs));
+  if (!march) {   // the walks' bordered copies, one per distinct grid
+    PF_TRY(pf_bordered_grid(ctx, V.mg, V.gx, V.gy, V.gz, WS_GRID_WALK, &V.mgw));
+    if (Vp.mg == V.mg) Vp.mgw = V.mgw;
+    else PF_TRY(pf_bordered_grid(ctx, Vp.mg, Vp.gx, Vp.gy, Vp.gz, WS_GRID_PRIMARY_WALK, &Vp.mgw));
+    if (Vs.mg == V.mg) Vs.mgw = V.mgw;
+    else PF_TRY(pf_bordered_grid(ctx, Vs.mg, Vs.gx, Vs.gy, Vs.gz, WS_GRID_SHADOW_WALK, &Vs.mgw));
+  }
   DevLights L = pf_make_lights(lights, n_lights);
   CamF C = make_cam(cam);
   int nmax = std::max(vol->nx, std::max(vol->ny, vol->nz));
@@ -1190,6 +1200,7 @@ extern "C" pf_status pf_render_pathtraced(pf_ctx* ctx, const pf_volume* vol, con
   unsigned long long* next;   // the persistent kernel's sample counter
   PF_TRY(pf_scratch(ctx, WS_MISC, 256, (void**)&next));
   Vol V = pf_make_vol(vol, 0.f, grid);
+  PF_TRY(pf_bordered_grid(ctx, grid, V.gx, V.gy, V.gz, WS_GRID_WALK, &V.mgw));
   DevLights L = pf_make_lights(lights, n_lights);
   CamF C = make_cam(cam);
   StageTimer tm(ctx, PF_STAGE_PATH);

@@ -370,6 +370,29 @@ pf_status pf_grid_for(pf_ctx* ctx, const pf_volume* vol, const float** grid) {
 }
 
 namespace {
+__global__ void k_border_grid(const float* __restrict__ g, int gx, int gy, int gz, int64_t n, float* __restrict__ out) {
+  const int px = gx + 2 * kBorder, py = gy + 2 * kBorder;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % px) - kBorder, j = (int)((e / px) % py) - kBorder, k = (int)(e / ((int64_t)px * py)) - kBorder;
+    const bool in = i >= 0 && i < gx && j >= 0 && j < gy && k >= 0 && k < gz;
+    out[e] = in ? __ldg(g + (int64_t)i + (int64_t)gx * ((int64_t)j + (int64_t)gy * k)) : 0.0f;
+  }
+}
+}  // namespace
+
+pf_status pf_bordered_grid(pf_ctx* ctx, const float* grid, int gx, int gy, int gz, int slot, const float** out) {
+  const int64_t n = (int64_t)(gx + 2 * kBorder) * (gy + 2 * kBorder) * (gz + 2 * kBorder);
+  if (n >= (1ll << 31)) return pf_fail(ctx, PF_ERR_INVALID_ARG, "brick grid too large for the walks (2^31 bricks)");
+  float* b;
+  PF_TRY(pf_scratch(ctx, slot, (size_t)n * sizeof(float), (void**)&b));
+  k_border_grid<<<(unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 8), 256, 0, ctx->stream>>>(
+      grid, gx, gy, gz, n, b);
+  PF_CUDA(ctx, cudaGetLastError());
+  *out = b;
+  return PF_OK;
+}
+
+namespace {
 // Tiled copy: one thread per destination element (tile-major, 64 per tile).
 template <typename T>
 __global__ void k_tile_volume(const T* __restrict__ src, int nx, int ny, int nz, int tnx, int tny, int64_t n,
@@ -477,6 +500,7 @@ extern "C" pf_status pf_build_photon_cache(pf_ctx* ctx, const pf_volume* vol, co
   StageTimer tm(ctx, PF_STAGE_PHOTONS);
   TraceArgs A;
   A.V = pf_make_vol(vol, 0.f, grid);
+  ST(pf_bordered_grid(ctx, grid, A.V.gx, A.V.gy, A.V.gz, WS_GRID_WALK, &A.V.mgw));
   A.L = pf_make_lights(lights, n_lights);
   for (int i = 0; i < 16; ++i) A.g_set[i] = i < n_g ? g_set[i] : 0.f;
   A.n_g = n_g; A.max_bounces = max_bounces; A.res = res; A.use_rr = use_rr; A.N = N; A.seed = seed; A.n_photons = P;
