@@ -102,7 +102,9 @@ typedef struct {
 typedef struct { int kind; float v[3]; float rgb[3]; } pf_light;
 #define PF_MAX_LIGHTS 16
 
-/* Pinhole camera (Algorithm 2 input `camera`); row 0 is the top row. */
+/* Pinhole camera (Algorithm 2 input `camera`); row 0 is the top row.  The
+ * renderers refuse (PF_ERR_INVALID_ARG) a camera with a non-finite eye, at
+ * or up, eye == at, or up parallel to at - eye, and fovy_deg outside (0, 180). */
 typedef struct { float eye[3], at[3], up[3]; float fovy_deg; int width, height; } pf_camera;
 
 /* Photon field (Sec. 3.4): 6-D query (x, y, z, theta', phi', g) with theta',

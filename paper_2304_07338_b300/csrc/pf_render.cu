@@ -950,11 +950,28 @@ pf_status launch_nee(pf_ctx* ctx, const Vol& V, const Vol& Vw, const DevLights& 
 
 }  // namespace
 
+// A finite, non-degenerate camera frame: eye, at and up finite, eye != at,
+// up not parallel to at - eye (the trackers' walks rely on finite rays).
+static bool cam_frame_ok(const pf_camera* cam) {
+  double f[3], up[3], fn = 0.0, un = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    if (!std::isfinite(cam->eye[i]) || !std::isfinite(cam->at[i]) || !std::isfinite(cam->up[i])) return false;
+    f[i] = (double)cam->at[i] - (double)cam->eye[i];
+    up[i] = cam->up[i];
+    fn += f[i] * f[i];
+    un += up[i] * up[i];
+  }
+  const double r0 = f[1] * up[2] - f[2] * up[1], r1 = f[2] * up[0] - f[0] * up[2], r2 = f[0] * up[1] - f[1] * up[0];
+  return fn > 0.0 && r0 * r0 + r1 * r1 + r2 * r2 > 1e-12 * fn * un;
+}
+
 static pf_status check_cam(pf_ctx* ctx, const pf_camera* cam, int spp) {
   if (!cam || cam->width <= 0 || cam->height <= 0 || spp <= 0 || spp > (1 << 24))
     return pf_fail(ctx, PF_ERR_INVALID_ARG, "camera size and spp must be positive (spp < 2^24)");
   if (!(cam->fovy_deg > 0.f && cam->fovy_deg < 180.f))
     return pf_fail(ctx, PF_ERR_INVALID_ARG, "fovy_deg must lie in (0, 180)");
+  if (!cam_frame_ok(cam))
+    return pf_fail(ctx, PF_ERR_INVALID_ARG, "camera needs finite eye, at, up with eye != at and up not parallel to at - eye");
   return PF_OK;
 }
 
@@ -1261,7 +1278,8 @@ extern "C" pf_status pf_render_pathtraced_noalloc(const pf_volume* vol, const pf
     return PF_ERR_INVALID_ARG;
   }
   if (pf_lights_problem(lights, n_lights, err_msg, err_len > 0 ? (size_t)err_len : 0)) return PF_ERR_INVALID_ARG;
-  if (!cam || cam->width <= 0 || cam->height <= 0 || !(cam->fovy_deg > 0.f && cam->fovy_deg < 180.f) || spp <= 0 ||
+  if (!cam || cam->width <= 0 || cam->height <= 0 || !(cam->fovy_deg > 0.f && cam->fovy_deg < 180.f) ||
+      !cam_frame_ok(cam) || spp <= 0 ||
       spp > (1 << 24) || max_bounces < 1 || max_bounces > 1024 || !(g > -1.f && g < 1.f) || !out_rgb_dev) {
     put_msg(err_msg, err_len, "invalid camera, spp, max_bounces, g or output");
     return PF_ERR_INVALID_ARG;

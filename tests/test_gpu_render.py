@@ -156,6 +156,16 @@ def test_edge_cases(pf_ctx, orc):
         api.render_pathtraced(pf_ctx, vol, sc.lights, 0.0, sc.camera, 0, 4, seed=4)
     with pytest.raises(api.PfError):
         api.render_neural(pf_ctx, vol, [], 0.0, sc.camera, 1, 0.5, seed=4)
+    # degenerate camera frames are refused before any launch: eye == at, up
+    # parallel to the view direction, a non-finite component
+    for bad in (I.Camera((0.5, 0.5, 3.0), (0.5, 0.5, 3.0), (0, 1, 0), 30.0, 5, 3),
+                I.Camera((0.5, 0.5, 3.0), (0.5, 0.5, 0.5), (0, 0, 2), 30.0, 5, 3),
+                I.Camera((float("nan"), 0.5, 3.0), (0.5, 0.5, 0.5), (0, 1, 0), 30.0, 5, 3)):
+        for step in (0.0, 0.5):
+            with pytest.raises(api.PfError):
+                api.render_neural(pf_ctx, vol, sc.lights, 0.0, bad, 1, step, seed=4)
+        with pytest.raises(api.PfError):
+            api.render_pathtraced(pf_ctx, vol, sc.lights, 0.0, bad, 1, 4, seed=4)
 
 
 def test_rmse_reduction(pf_ctx):

@@ -111,3 +111,9 @@ def test_noalloc_rejects_what_the_allocating_path_rejects(pf_ctx):
         assert st == _lib.PF_ERR_INVALID_ARG and b"sigma_scale" in msg.value
     finally:
         vol.s.sigma_scale = ss
+    # a degenerate camera frame (eye == at) is refused by both entry points
+    flat = I.Camera((0.5, 0.5, 3.0), (0.5, 0.5, 3.0), (0, 1, 0), 30.0, 8, 8)
+    st = _call(L, vol, sc.lights, 0.0, flat, 1, 4, 1, out, msg)
+    assert st == _lib.PF_ERR_INVALID_ARG and b"camera" in msg.value
+    with pytest.raises(api.PfError):
+        api.render_pathtraced(pf_ctx, vol, sc.lights, 0.0, flat, 1, 4, seed=1)
