@@ -55,7 +55,7 @@ EQ_FRAMES = (0, 15, 30, 45)     # orbit frames of the equal-RMSE comparison
 # of the small case (profiles/k_nee__large_render_512cube_960x540.md); a full
 # launch is scaled by its lookups.  None whenever k_nee changed since the
 # capture.
-NEE_DRAM_BYTES_PER_LOOKUP = (0.842871e9 + 0.069161e9) / 26852954
+NEE_DRAM_BYTES_PER_LOOKUP = (0.822418e9 + 0.062984e9) / 26838016
 FETCH_BYTES = 8 * VOXEL_BYTES   # one trilinear lookup reads 8 voxels
 
 
