@@ -528,6 +528,22 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_tc_train(TrArgs T, const f
     return s;
   };
   bool stop = false;
+  // the frequency-encoded rows' inputs (this thread's three) and targets,
+  // loaded one tile ahead: the next tile's loads are issued after the loss,
+  // so that they arrive during the backward pass
+  const bool ahead = !HASH && F == 12;
+  float qn[3] = {0.f, 0.f, 0.f}, tn[3] = {0.f, 0.f, 0.f};
+  auto load_ahead = [&](int64_t tl) {
+    const int64_t rw = tl * kTileM + r;
+    const bool ok = tl < n_tiles && rw < B;
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd) qn[dd] = ok ? __ldg(q + 6 * rw + 3 * hf + dd) : 0.f;
+    if (targets && hf == 0) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) tn[c] = ok ? __ldg(targets + 3 * rw + c) : 0.f;
+    }
+  };
+  if (ahead) load_ahead(blockIdx.x);
 
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int64_t row = tile * kTileM + r;
@@ -550,7 +566,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_tc_train(TrArgs T, const f
         float buf[8];
 #pragma unroll
         for (int dd = 0; dd < 3; ++dd) {
-          const float v = valid ? __ldg(q + 6 * row + 3 * hf + dd) : 0.f;
+          const float v = qn[dd];
           float sn = 0.f, cs = 1.f;
 #pragma unroll
           for (int k = 0; k < 12; ++k) {
@@ -625,7 +641,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_tc_train(TrArgs T, const f
           float g = 0.f;
           if (valid) {
             if (targets) {
-              const float t = targets[3 * row + c];
+              const float t = ahead ? tn[c] : targets[3 * row + c];
               const float den = t * t + 0.01f;
               const float diff = y[c] - t;
               lsum += diff * diff / den;
@@ -643,6 +659,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_tc_train(TrArgs T, const f
       for (int j = 0; j < HH; ++j) hs[r * H + ((HH * hf + j + r) & (H - 1))] = h[j];
       __syncthreads();
     }
+    if (ahead) load_ahead(tile + gridDim.x);
     const float dy0 = dys[4 * r + 0], dy1 = dys[4 * r + 1], dy2 = dys[4 * r + 2];
     // dW_out[c][n] += sum over the tile's rows of dy_c h_n: one owner thread
     // per (c, n), rows summed in order
@@ -964,16 +981,38 @@ __global__ void __launch_bounds__(kT128Threads, 1) k_tc_train128(T128Args T, con
     if (!ok) { atomicOr(err, PFE_ITER_CAP); *abort_flag = 1; }
   };
   bool stop = false;
+  // this thread's encoding inputs (items tid, tid + 256) and, for lane
+  // quarter 0, its query's targets, loaded one tile ahead: the next tile's
+  // loads are issued after the loss, so that they arrive during the backward
+  constexpr int kItems = (kT128Q * 6 + kT128Threads - 1) / kT128Threads;
+  float qn[kItems], tn[3] = {0.f, 0.f, 0.f};
+  auto load_ahead = [&](int64_t tl) {
+    const int64_t r0 = tl * kT128Q;
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+      const int it = tid + j * kT128Threads;
+      const int64_t row = r0 + (it & (kT128Q - 1));
+      qn[j] = (tl < n_tiles && it < kT128Q * 6 && row < B) ? __ldg(q + 6 * row + it / kT128Q) : 0.f;
+    }
+    if (targets && lq == 0) {
+      const int64_t row = r0 + 32 * hf + lane;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) tn[c] = (tl < n_tiles && row < B) ? __ldg(targets + 3 * row + c) : 0.f;
+    }
+  };
+  load_ahead(blockIdx.x);
 
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int64_t row0 = tile * kT128Q;
     // ---- frequency encoding -> X_0 [q][k]: one (query, input) pair per item
     {
       uint8_t* x0 = smem + T.x_off[0];
-      for (int it = tid; it < kT128Q * 6; it += kT128Threads) {
+#pragma unroll
+      for (int j = 0; j < kItems; ++j) {
+        const int it = tid + j * kT128Threads;
+        if (it >= kT128Q * 6) break;
         const int qq = it & (kT128Q - 1), d = it / kT128Q;
-        const int64_t row = row0 + qq;
-        const float v = row < B ? __ldg(q + 6 * row + d) : 0.f;
+        const float v = qn[j];
         float buf[8];
         float sn = 0.f, cs = 1.f;
 #pragma unroll
@@ -1054,7 +1093,7 @@ __global__ void __launch_bounds__(kT128Threads, 1) k_tc_train128(T128Args T, con
         float g = 0.f;
         if (row < B) {
           if (targets) {
-            const float t = targets[3 * row + c];
+            const float t = tn[c];
             const float den = t * t + 0.01f;
             const float diff = y - t;
             lsum += diff * diff / den;
@@ -1067,6 +1106,7 @@ __global__ void __launch_bounds__(kT128Threads, 1) k_tc_train128(T128Args T, con
       }
     }
     __syncthreads();
+    load_ahead(tile + gridDim.x);
     // ---- dW_out (registers, across tiles) and dZ_{L-1} = rnd((dy W_out) * [rnd(h) > 0])
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
