@@ -83,6 +83,25 @@ __global__ void k_place(const uint32_t* __restrict__ ckey, const uint32_t* __res
 constexpr int kMarchAhead = 4;
 
 // -------------------------------------------------------------- camera samples
+// Sample k of pixel pix = (px, py) for slot = pix * spp + k, in 32-bit
+// arithmetic when every slot index fits (the same quotients as in 64 bits).
+__device__ __forceinline__ void slot_pixel(int64_t slot, int64_t n_slots, int spp, int W, int* k, int64_t* pix,
+                                           int* px, int* py) {
+  if (n_slots <= (int64_t)0xffffffffll) {
+    const uint32_t s = (uint32_t)slot, sp = (uint32_t)spp, w = (uint32_t)W;
+    const uint32_t p = s / sp, y = p / w;
+    *k = (int)(s - p * sp);
+    *pix = (int64_t)p;
+    *py = (int)y;
+    *px = (int)(p - y * w);
+  } else {
+    *k = (int)(slot % spp);
+    *pix = slot / spp;
+    *px = (int)(*pix % W);
+    *py = (int)(*pix / W);
+  }
+}
+
 // stats (nullable): stats[0] += density lookups, stats[1] += valid samples
 // (= field queries) of the launch.
 template <int DT, bool MARCH>
@@ -100,9 +119,9 @@ __device__ __forceinline__ void camera_samples(Vol V, DevLights L, CamF cam, flo
   int valid = 0;
   V3 x = v3(0.f, 0.f, 0.f), wo = x, alb = x, Ld = x;
   if (active) {
-    int k = (int)(slot % spp);
-    int64_t pix = slot / spp;
-    int px = (int)(pix % cam.W), py = (int)(pix / cam.W);
+    int k, px, py;
+    int64_t pix;
+    slot_pixel(slot, n_slots, spp, cam.W, &k, &pix, &px, &py);
     Rng rng(seed, TAG_CAMERA, (uint64_t)pix, (uint32_t)k);
     float b0[4]; rng.uni4(b0);
     V3 o, d;
@@ -579,9 +598,10 @@ __global__ void __launch_bounds__(128, 8) k_path_samples(Vol V, DevLights L, Cam
                                                       unsigned long long* stats) {
   int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (it >= n_items) return;
-  int k = k0 + (int)(it % kc);
-  int64_t pix = it / kc;
-  int px = (int)(pix % cam.W), py = (int)(pix / cam.W);
+  int k, px, py;
+  int64_t pix;
+  slot_pixel(it, n_items, kc, cam.W, &k, &pix, &px, &py);
+  k += k0;
   Rng rng(seed, TAG_CAMERA, (uint64_t)pix, (uint32_t)k);
   float b0[4]; rng.uni4(b0);
   V3 o, d;
@@ -676,9 +696,9 @@ __global__ void __launch_bounds__(128, 8) k_path_persistent(Vol V, DevLights L, 
         const int64_t q = (int64_t)(base + (unsigned long long)__popc(need & ((1u << lane) - 1u)));
         if (q < n_items) {
           it = q; has = true;
-          k = k0 + (int)(it % kc);
-          pix = it / kc;
-          const int px = (int)(pix % cam.W), py = (int)(pix / cam.W);
+          int px, py;
+          slot_pixel(it, n_items, kc, cam.W, &k, &pix, &px, &py);
+          k += k0;
           rng = Rng(seed, TAG_CAMERA, (uint64_t)pix, (uint32_t)k);
           float b0[4]; rng.uni4(b0);
           camera_ray(cam, px, py, b0[0], b0[1], &o, &d);
@@ -789,9 +809,9 @@ __global__ void __launch_bounds__(128) k_raymarch(Vol V, DevLights L, CamF cam, 
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_rays) return;
   const int64_t ray = r0 + i;
-  const int k = (int)(ray % spp);
-  const int64_t pix = ray / spp;
-  const int px = (int)(pix % cam.W), py = (int)(pix / cam.W);
+  int k, px, py;
+  int64_t pix;
+  slot_pixel(ray, r0 + n_rays, spp, cam.W, &k, &pix, &px, &py);
   Rng rng(seed, TAG_CAMERA, (uint64_t)pix, (uint32_t)k);
   float b0[4];
   rng.uni4(b0);
