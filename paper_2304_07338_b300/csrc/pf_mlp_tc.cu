@@ -398,8 +398,10 @@ __global__ void __launch_bounds__(kFwdMaxThreads, 1) k_tc_forward(TcArgs A, cons
 //              with loss scaling, dy = 2 (y - t) / (t^2 + 0.01) (3B times the
 //              gradient of the mean; 1/(3B) is applied to the float32 dW sums
 //              by k_reduce_partials), or a given dy; loss;
-//              dW_out by one owner thread per weight over the tile's rows
-//              staged in shared memory; dZ_{L-1} = (W_out^T dy) * [h_L > 0];
+//              dW_out from registers: products dy_c h_n summed over each
+//              warp's 32 rows by a butterfly reduce-scatter, then over the
+//              four warps of the row quarters in order; dZ_{L-1} =
+//              (W_out^T dy) * [h_L > 0];
 //   backward : for l = L-1..0, tcgen05.mma dW_l += dZ_l^T x A_l (both operands
 //              MN-major views of the row tiles, M padded to 128 neurons) into
 //              a TMEM accumulator that persists across the CTA's tiles, and
@@ -412,7 +414,7 @@ struct TrArgs {
   uint32_t a_off[kMaxLayers];   // shared-memory byte offset of A_l
   uint32_t d_off;           // dZ tile (128 x 128 neurons, padded)
   uint32_t dwo_off;         // dW_out accumulator (3 x H float32)
-  uint32_t hs_off;          // last hidden activations of the tile (128 x H float32, rows rotated)
+  uint32_t part_off;        // dW_out partial sums: [8 warps][3][32] float32
   uint32_t dys_off;         // output-layer gradients of the tile (128 x 4 float32)
   uint32_t dw_col[kMaxLayers];  // TMEM column of dW_l
   uint32_t g_off;           // hash grids: [H] g weights, [H] dW of the g column, [128] g of the rows
@@ -470,7 +472,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_tc_train(TrArgs T, const f
   int* abort_flag = (int*)(smem + A.bar_off + 20);
   const uint32_t bar_w = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]);
   const int L = A.n_hidden;
-  float* hs = (float*)(smem + T.hs_off);
+  float* dwo_part = (float*)(smem + T.part_off);
   float* dys = (float*)(smem + T.dys_off);      // [128][4]: dy of the row
   float* ys = dys + 4 * kTileM;                  // [128][4]: second half's partial output
   float* wg = (float*)(smem + T.g_off);          // hash grids: [H] rounded g weights of layer 0
@@ -653,29 +655,38 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_tc_train(TrArgs T, const f
           dys[4 * r + c] = g;
         }
       }
-      // this thread's columns of the last activation, for dW_out (row r
-      // rotated by r: conflict-free writes and column reads)
-#pragma unroll
-      for (int j = 0; j < HH; ++j) hs[r * H + ((HH * hf + j + r) & (H - 1))] = h[j];
       __syncthreads();
     }
     if (ahead) load_ahead(tile + gridDim.x);
     const float dy0 = dys[4 * r + 0], dy1 = dys[4 * r + 1], dy2 = dys[4 * r + 2];
-    // dW_out[c][n] += sum over the tile's rows of dy_c h_n: one owner thread
-    // per (c, n), rows summed in order
-    for (int o = tid; o < 3 * H; o += kTrainThreads) {
-      const int c = o / H, n = o % H;
-      float acc = 0.f;
-#pragma unroll 8
-      for (int rr = 0; rr < kTileM; ++rr) acc = fmaf(dys[4 * rr + c], hs[rr * H + ((n + rr) & (H - 1))], acc);
-      dwo[o] += acc;
+    // dW_out[c][n] += sum over the tile's rows of dy_c h_n.  Per warp (32
+    // rows, this half's 32 columns) a butterfly reduce-scatter leaves lane j
+    // holding column j's sum over the warp's rows; the four warps of the
+    // half are then added in row order.  dy is 0 on rows past the batch.
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float dc = c == 0 ? dy0 : (c == 1 ? dy1 : dy2);
+      float v[HH];
+#pragma unroll
+      for (int i = 0; i < HH; ++i) v[i] = dc * h[i];
+#pragma unroll
+      for (int st = 0; st < 5; ++st) {
+        const int off = 16 >> st;
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < off; ++i) {
+          const float send = up ? v[i] : v[off + i];
+          const float keep = up ? v[off + i] : v[i];
+          v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+      }
+      dwo_part[(warp * 3 + c) * 32 + lane] = v[0];
     }
-    // hs shares the dZ tile's bytes: from here on it is dead; restore the
-    // tile's zero padding (neurons H .. kDK - 1) before dZ_{L-1} goes in
     __syncthreads();
-    for (int i = tid; i < kTileM * (int)(kDK - H) / 8; i += kTrainThreads) {
-      const int per = (int)(kDK - H) / 8;
-      store_chunk(dtile, kDK * 2, i / per, H / 8 + i % per, make_uint4(0, 0, 0, 0));
+    for (int o = tid; o < 3 * H; o += kTrainThreads) {
+      const int c = o / H, n = o % H, hq = n / HH, j = n % HH;
+      const float* pp = dwo_part + (4 * hq * 3 + c) * 32 + j;  // warps 4 hq .. 4 hq + 3, stride 3 x 32
+      dwo[o] += ((pp[0] + pp[96]) + pp[192]) + pp[288];
     }
     // dZ_{L-1} = (dy W_out) * [rounded h > 0], this thread's columns
 #pragma unroll
@@ -1427,10 +1438,8 @@ bool plan_train(const pf_field* f, TrArgs* T) {
   off = (off + 1023) / 1024 * 1024;
   T->d_off = off;
   off += kTileM * kDK * 2;
-  // the last activations (float32, for dW_out) share the dZ tile's bytes:
-  // they are dead before dZ_{L-1} is written
-  T->hs_off = T->d_off;
-  static_assert(kTileM * kDK * 2 == kTileM * kTrainHidden * 4, "hs must fit the dZ tile");
+  T->part_off = off;                         // dW_out partial sums of the 8 warps
+  off += (kTrainThreads / 32) * 3 * 32 * 4;
   T->f.wout_off = off;
   off += 3 * H * 4;
   T->dwo_off = off;
