@@ -881,7 +881,7 @@ __global__ void __launch_bounds__(128) k_raymarch(Vol V, DevLights L, CamF cam, 
           }
           const V3 w = v3(a * alb.x, a * alb.y, a * alb.z);
           D = v3(D.x + w.x * Ld.x, D.y + w.y * Ld.y, D.z + w.z * Ld.z);
-          if (q && j < j_end) {
+          if (EMIT && q && j < j_end) {
             q[6 * j + 0] = x.x; q[6 * j + 1] = x.y; q[6 * j + 2] = x.z;
             q[6 * j + 3] = qth; q[6 * j + 4] = qph; q[6 * j + 5] = g;
             wgt[3 * j + 0] = w.x; wgt[3 * j + 1] = w.y; wgt[3 * j + 2] = w.z;
