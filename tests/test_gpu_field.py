@@ -107,6 +107,27 @@ def test_loss_gradient_matches_oracle(pf_ctx, prec, hidden):
         assert rel <= tol, rel
 
 
+@pytest.mark.parametrize("prec,hidden,n", [("bf16", 64, 77), ("bf16", 64, 257), ("f16", 128, 33), ("f16", 128, 65)])
+def test_loss_gradient_partial_tiles(pf_ctx, prec, hidden, n):
+    """The tensor-core trainers on batches that end inside a tile (one
+    partial tile only, or one row past whole tiles): rows past the batch must
+    add nothing to the loss or any weight gradient (including the output
+    layer's, summed from registers), and the next tile's inputs are loaded
+    ahead past the end.  Same bars as the full test."""
+    fld = api.Field(pf_ctx, 12, hidden, 4, prec, 5.0, seed=9)
+    desc = F.FieldDesc(12, hidden, 4, PRECS[prec], 5.0, 9)
+    w = F.init_weights(desc).astype(np.float64)
+    q = _queries(n, seed=21)
+    y0, _ = F.forward(w, q.astype(np.float64), F.FieldDesc(12, hidden, 4, F.PREC_F32, 5.0, 9))
+    t = (y0 + np.random.default_rng(22).normal(size=y0.shape) * 0.3).astype(np.float32)
+    loss, dw = fld.loss_gradient(torch.from_numpy(q).cuda(), torch.from_numpy(t).cuda())
+    lref, gref = F.train_gradient(w, q.astype(np.float64), t.astype(np.float64), desc)
+    assert abs(loss - lref) <= 1e-3 * lref, (loss, lref)
+    for a, b in zip(F.unflatten(dw.cpu().numpy(), desc), F.unflatten(gref, desc)):
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        assert rel <= 1e-3, rel
+
+
 def test_autograd_function(pf_ctx):
     fld = api.Field(pf_ctx, 12, 64, 3, "f32", 5.0, seed=2)
     w = fld.get_weights().clone().requires_grad_(True)
