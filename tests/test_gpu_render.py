@@ -168,6 +168,31 @@ def test_edge_cases(pf_ctx, orc):
             api.render_pathtraced(pf_ctx, vol, sc.lights, 0.0, bad, 1, 4, seed=4)
 
 
+@pytest.mark.parametrize("prec", ["f16", "fp8"])
+def test_tracking_with_no_scattering_sample(pf_ctx, prec):
+    """Tracking mode with a tensor-core field where no camera sample
+    scatters (an empty medium; a camera looking away from the box): the NEE
+    pass gets no work items and the field pass reads a query count of zero
+    on the device; the image is black and the context renders normally
+    afterwards."""
+    sc = I.scene_small(16, 12, 10, 3)
+    empty = dataclasses.replace(sc.volume, data=np.zeros_like(sc.volume.data))
+    fld = api.Field(pf_ctx, 12, 128, 4, prec, 5.0, seed=3)
+    if prec == "fp8":
+        q = np.random.default_rng(0).uniform(0.0, 1.0, (512, 6)).astype(np.float32)
+        fld.calibrate_fp8(torch.from_numpy(q).cuda())
+    away = I.Camera((0.5, 0.5, 3.0), (0.5, 0.5, 6.0), (0, 1, 0), 30.0, 12, 10)
+    for v, cam in ((empty, sc.camera), (sc.volume, away)):
+        vol = api.Volume.from_inputs(v)
+        img = api.render_neural(pf_ctx, vol, sc.lights, 0.3, cam, 3, 0.0, seed=2, field=fld)
+        pf_ctx.sync()
+        assert float(img.abs().max()) == 0.0
+    vol = api.Volume.from_inputs(sc.volume)
+    img = api.render_neural(pf_ctx, vol, sc.lights, 0.3, sc.camera, 3, 0.0, seed=2, field=fld)
+    pf_ctx.sync()
+    assert torch.isfinite(img).all() and float(img.max()) > 0.0
+
+
 def test_rmse_reduction(pf_ctx):
     g = torch.Generator().manual_seed(0)
     a = torch.rand(1000003, generator=g).cuda()
