@@ -51,11 +51,12 @@ FIELD_PREC = "f16"              # the paper's field precision (Sec. 4.1); fp8 is
 HELD_OUT_TOL = 0.01     # early stopping: held-out losses this close count as a tie
 VOXEL_BYTES = 2                 # float16
 EQ_FRAMES = (0, 15, 30, 45)     # orbit frames of the equal-RMSE comparison
-# DRAM bytes (read + write) per density lookup of k_nee, from one ncu capture
-# of the small case (profiles/k_nee__large_render_512cube_960x540.md); a full
-# launch is scaled by its lookups.  None whenever k_nee changed since the
-# capture.
-NEE_DRAM_BYTES_PER_LOOKUP = (0.822418e9 + 0.062984e9) / 26838016
+# DRAM bytes (read + write) per density lookup of k_nee at full size, from a
+# one-pass ncu capture of the two counted launches of this workload
+# (profiles/k_nee__large_render_1024cube_1080p_dram.md: 21.14 GB over
+# 2 x 104,918,229 lookups); a launch is scaled by its lookups.  None whenever
+# k_nee changed since the capture.
+NEE_DRAM_BYTES_PER_LOOKUP = 21136791808 / (2 * 104918229)
 FETCH_BYTES = 8 * VOXEL_BYTES   # one trilinear lookup reads 8 voxels
 
 
@@ -819,7 +820,8 @@ def main():
             traffic = lookups * NEE_DRAM_BYTES_PER_LOOKUP
         roof = {"kernel": name, "bound": "hbm", "achieved": achieved,
                 "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
-                "traffic_note": "DRAM bytes per launch, scaled from the small-case ncu capture by lookups"
+                "traffic_note": "DRAM bytes per launch: bytes per lookup from a one-pass ncu capture of two "
+                                "full-size launches, times this run's lookups"
                 if traffic else None,
                 "limiter": "issue-bound divergent control flow, not bandwidth (ncu, small case)"
                 if dominant == "nee" else None,
